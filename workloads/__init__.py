@@ -1,0 +1,219 @@
+"""Seeded synthetic inputs: node permittivity maps and source vectors.
+
+This module is shared by the CPU oracle (``oracle/``) and by the GPU library's
+tests and benchmark. It holds no arithmetic of the method itself (no stencil,
+no PML, no decomposition, no solver): it only turns a geometry description and
+a seed into the two arrays the solver consumes,
+
+* ``eps_node``: real (nx, ny) array, node-averaged relative permittivity.
+  Cells are the squares between nodes; each cell gets the subcell-averaged
+  permittivity of Eq. 8 (8 x 8 subcells, a subcell belongs to the medium that
+  contains its centre) and each node the mean of the four cells that touch it
+  (Eq. 3).  Cells just outside the grid are evaluated from the same geometry.
+* ``b``: complex (nx, ny) right-hand side.  A unit point source at node s is
+  b_s = -1/(dx*dy), so that the discrete field approximates (i/4) H0^(1)(k r)
+  with the e^{-i w t} time convention; an x-directed line source on row js is
+  b_{i,js} = -1/dy for every column i.
+
+Arrays are indexed [i, j] with i along x and j along y, so their C-order
+flattening is the solver's node index g = i*ny + j.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SUBCELLS = 8
+
+
+@dataclasses.dataclass
+class Workload:
+    """One synthetic FDFD problem (grid, materials, sources, decomposition)."""
+
+    name: str
+    nx: int
+    ny: int
+    dx: float
+    dy: float
+    wavelength: float
+    eps_node: np.ndarray            # (nx, ny) float64
+    b: np.ndarray                   # (nrhs, nx, ny) complex128
+    npml: tuple = (20, 20, 20, 20)  # x0, x1, y0, y1 cells
+    pml_order: int = 3
+    pml_R: float = 1e-8
+    nsub: int = 2
+    overlap: int = 8
+    interface_pml: int = 20
+    restart: int = 30
+    rtol: float = 1e-10
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def nrhs(self) -> int:
+        return self.b.shape[0]
+
+
+# --------------------------------------------------------------------------
+# geometry primitives: each returns a boolean "inside" test on point arrays
+# --------------------------------------------------------------------------
+
+def _circle(cx, cy, r):
+    return (lambda x, y: (x - cx) ** 2 + (y - cy) ** 2 <= r * r,
+            (cx - r, cx + r, cy - r, cy + r))
+
+
+def _rect(xa, xb, ya, yb):
+    return (lambda x, y: (x >= xa) & (x <= xb) & (y >= ya) & (y <= yb),
+            (xa, xb, ya, yb))
+
+
+def _ellipse(cx, cy, a, b, theta):
+    ct, st = math.cos(theta), math.sin(theta)
+
+    def inside(x, y):
+        u = (x - cx) * ct + (y - cy) * st
+        v = -(x - cx) * st + (y - cy) * ct
+        return (u / a) ** 2 + (v / b) ** 2 <= 1.0
+
+    r = max(a, b)
+    return inside, (cx - r, cx + r, cy - r, cy + r)
+
+
+def cell_permittivity(nx, ny, dx, dy, background, objects):
+    """Subcell-averaged permittivity of the cells (i, j), i in [-1, nx-1],
+    j in [-1, ny-1]; cell (i, j) spans [i dx, (i+1) dx] x [j dy, (j+1) dy].
+
+    ``objects`` is a list of ((inside, bbox), eps); later objects are painted
+    over earlier ones (they are not expected to overlap except on purpose,
+    e.g. a pillar standing on a substrate)."""
+    cells = np.full((nx + 1, ny + 1), float(background))
+    off = (np.arange(SUBCELLS) + 0.5) / SUBCELLS
+    for (inside, bbox), eps in objects:
+        xa, xb, ya, yb = bbox
+        i0 = max(-1, int(math.floor(xa / dx)) - 1)
+        i1 = min(nx - 1, int(math.ceil(xb / dx)) + 1)
+        j0 = max(-1, int(math.floor(ya / dy)) - 1)
+        j1 = min(ny - 1, int(math.ceil(yb / dy)) + 1)
+        if i1 < i0 or j1 < j0:
+            continue
+        ii = np.arange(i0, i1 + 1)
+        jj = np.arange(j0, j1 + 1)
+        # subcell centres of every cell in the bounding box, chunked by rows
+        for c0 in range(0, len(ii), 256):
+            isub = ii[c0:c0 + 256]
+            xs = (isub[:, None] + off[None, :]) * dx           # (ci, S)
+            ys = (jj[:, None] + off[None, :]) * dy             # (cj, S)
+            X = xs[:, None, :, None]
+            Y = ys[None, :, None, :]
+            inn = inside(X, Y)                                 # (ci, cj, S, S)
+            n_in = inn.reshape(len(isub), len(jj), -1).sum(axis=2)
+            frac = n_in / float(SUBCELLS * SUBCELLS)
+            blk = cells[isub[0] + 1:isub[-1] + 2, j0 + 1:j1 + 2]
+            blk[...] = eps * frac + blk * (1.0 - frac)
+    return cells
+
+
+def node_permittivity(cells):
+    """Mean of the four cells touching each node (Eq. 3)."""
+    return 0.25 * (cells[:-1, :-1] + cells[1:, :-1] + cells[:-1, 1:] + cells[1:, 1:])
+
+
+def point_source(nx, ny, dx, dy, i, j):
+    b = np.zeros((nx, ny), np.complex128)
+    b[i, j] = -1.0 / (dx * dy)
+    return b
+
+
+def line_source_x(nx, ny, dy, j):
+    b = np.zeros((nx, ny), np.complex128)
+    b[:, j] = -1.0 / dy
+    return b
+
+
+# --------------------------------------------------------------------------
+# the workloads
+# --------------------------------------------------------------------------
+
+def cylinder(nx=200, ny=200, ppw=20, eps_cyl=4.0, radius=0.5, src_gap=1.0,
+             npml=20, nsub=2, overlap=8, interface_pml=20, wavelength=1.0):
+    """Dielectric cylinder at the grid centre lit by a unit point source
+    ``src_gap`` wavelengths left of its surface (the small plain-method case:
+    200 x 200 nodes at lambda/20, eps 4, r = 0.5 lambda, 20-cell PML,
+    2 strips with 8-cell overlap and 20-cell interface PML)."""
+    d = wavelength / ppw
+    cx, cy = (nx - 1) * d / 2.0, (ny - 1) * d / 2.0
+    objs = []
+    if eps_cyl != 1.0 and radius > 0:
+        objs.append((_circle(cx, cy, radius * wavelength), eps_cyl))
+    cells = cell_permittivity(nx, ny, d, d, 1.0, objs)
+    eps = node_permittivity(cells)
+    xs = cx - (radius + src_gap) * wavelength
+    si = int(round(xs / d))
+    sj = int(round(cy / d))
+    b = point_source(nx, ny, d, d, si, sj)[None]
+    return Workload("cylinder", nx, ny, d, d, wavelength, eps, b,
+                    npml=(npml,) * 4, nsub=nsub, overlap=overlap,
+                    interface_pml=interface_pml, restart=30, rtol=1e-10,
+                    meta=dict(center=(cx, cy), radius=radius * wavelength,
+                              eps_cyl=eps_cyl, src=(si, sj)))
+
+
+def metalens(nx=4096, ny=1024, ppw=24, seed=1, npml=30, nsub=16, overlap=12,
+             interface_pml=30, wavelength=1.0):
+    """Metalens-like strip: substrate eps 2.085 over the lower 20 % of the
+    rows, a row of eps 12.1 pillars (period 0.5 lambda, height 0.6 lambda
+    rounded to whole cells, seeded widths U[0.1, 0.4] lambda) standing on it,
+    and an x-directed line source inside the substrate 10 cells above the
+    bottom PML (the plain-FP64 metalens case is 4096 x 1024 at lambda/24,
+    30-cell PML, 16 strips, 12-cell overlap)."""
+    rng = np.random.default_rng(seed)
+    d = wavelength / ppw
+    j_sub = int(round(0.2 * ny))
+    y_sub = j_sub * d
+    height = round(0.6 * ppw) * d
+    period = 0.5 * wavelength
+    objs = [(_rect(-2 * d, (nx + 1) * d, -2 * d, y_sub), 2.085)]
+    x_lo, x_hi = npml * d, (nx - 1 - npml) * d
+    n_pillars = int((x_hi - x_lo) / period)
+    widths = rng.uniform(0.1, 0.4, size=n_pillars) * wavelength
+    for k in range(n_pillars):
+        xc = x_lo + (k + 0.5) * period
+        objs.append((_rect(xc - widths[k] / 2, xc + widths[k] / 2, y_sub, y_sub + height), 12.1))
+    cells = cell_permittivity(nx, ny, d, d, 1.0, objs)
+    eps = node_permittivity(cells)
+    b = line_source_x(nx, ny, d, npml + 10)[None]
+    return Workload("metalens", nx, ny, d, d, wavelength, eps, b,
+                    npml=(npml,) * 4, nsub=nsub, overlap=overlap,
+                    interface_pml=interface_pml, restart=50, rtol=1e-8,
+                    meta=dict(seed=seed, n_pillars=n_pillars, j_substrate=j_sub))
+
+
+def random_medium(nx, ny, ppw=20, seed=0, eps_range=(1.0, 4.0), npml=10,
+                  nsub=2, overlap=4, interface_pml=10, nsrc=1, wavelength=1.0):
+    """Smooth random permittivity with seeded point sources away from the PML
+    (small parity and reciprocity cases)."""
+    rng = np.random.default_rng(seed)
+    d = wavelength / ppw
+    cells = rng.uniform(eps_range[0], eps_range[1], size=(nx + 1, ny + 1))
+    eps = node_permittivity(cells)
+    b = np.zeros((nsrc, nx, ny), np.complex128)
+    for r in range(nsrc):
+        i = int(rng.integers(npml + 1, nx - npml - 1))
+        j = int(rng.integers(npml + 1, ny - npml - 1))
+        b[r] = point_source(nx, ny, d, d, i, j)
+    return Workload("random", nx, ny, d, d, wavelength, eps, b,
+                    npml=(npml,) * 4, nsub=nsub, overlap=overlap,
+                    interface_pml=interface_pml, restart=30, rtol=1e-10,
+                    meta=dict(seed=seed))
+
+
+def random_vector(n, seed, nrhs=1):
+    """Seeded complex test vector(s) of length n (operator parity inputs)."""
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((nrhs, n)) + 1j * rng.standard_normal((nrhs, n))).astype(np.complex128)
