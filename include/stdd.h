@@ -1,0 +1,187 @@
+/*
+ * stdd.h -- C ABI of the GB300 overlapping source-transfer DDM solver for
+ * 2-D TM FDFD (arXiv 2509.20801).
+ *
+ * The library solves A e = b (Eq. 4) for the stretched-coordinate PML
+ * Helmholtz operator of Eq. 9 discretised on the 5-point stencil of Eq. 2,
+ * with flexible GMRES(m) right-preconditioned by one Jacobi sweep of the
+ * paper's PML-based overlapping source-transfer iteration (Algorithm 1):
+ *
+ *     M^-1 v = sum_i E_i A_i^-1 R_i^I v,
+ *
+ * where A_i is the operator of strip i closed by its own PML (Sec. 2.3,
+ * Fig. 3), factored once by a nested-dissection multifrontal LU (Sec. 2.4,
+ * Eqs. 22-23) and applied by batched forward/back substitution, R_i^I keeps
+ * the strip's own (non-overlapping) columns, and E_i zero-extends the full
+ * local field (Eq. 21).  Krylov vectors, residuals, Arnoldi and Givens are
+ * FP64 complex; the factors are complex128 or complex64 (set_precision).
+ *
+ * Conventions used by every entry point
+ *   - Grid: nx x ny nodes, PML included.  Node (i, j), i along x, j along y,
+ *     has flat index g = i*ny + j.  Field is zero outside the grid.
+ *   - Complex vectors are interleaved doubles (re, im): a field is 2*nx*ny
+ *     doubles, nrhs fields are stored one after another.
+ *   - Pointers marked "is_device" are device pointers on the context's GPU
+ *     when the flag is 1 and host pointers when it is 0.  Inputs are copied
+ *     (the caller may free them on return); outputs are written into
+ *     caller-owned buffers and are complete when the call returns.
+ *   - Every call returns a status; on failure stdd_last_error() describes it.
+ *     No C++ exception crosses this boundary.  Calls on one context must not
+ *     overlap (a context is used by one thread at a time).
+ *   - Time convention e^{-i w t}: the PML stretch is s = 1 + i sigma/(w eps0)
+ *     (Eq. 10) and a unit point source b_s = -1/(dx dy) gives a field close to
+ *     (i/4) H0^(1)(k r).
+ */
+#ifndef STDD_H
+#define STDD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stdd_ctx stdd_ctx;
+
+typedef enum {
+  STDD_OK = 0,
+  STDD_EINVAL = 1,      /* bad argument or configuration                 */
+  STDD_ESTATE = 2,      /* call out of order (e.g. solve before factor)   */
+  STDD_ENOMEM = 3,      /* device or host allocation failed               */
+  STDD_ECUDA = 4,       /* a CUDA runtime call failed                     */
+  STDD_EPIVOT = 5,      /* zero or non-finite pivot in a front            */
+  STDD_EBREAKDOWN = 6,  /* Krylov breakdown or non-finite residual        */
+  STDD_ENOCONV = 7,     /* maxit reached before rtol (x_out still written) */
+  STDD_ETIMEOUT = 8     /* a bounded device wait gave up                  */
+} stdd_status;
+
+enum {
+  STDD_PREC_FP64 = 0,   /* complex128 factors and substitutions           */
+  STDD_PREC_C64 = 1     /* complex64 factors and substitutions, FP32 math */
+};
+
+enum { STDD_X0_ZERO = 0, STDD_X0_USER = 1 };
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t to run on (NULL: the context creates its own stream).  Every
+ * kernel of the context is launched on that stream. */
+stdd_status stdd_create(stdd_ctx **out, int device, void *cuda_stream);
+void stdd_destroy(stdd_ctx *ctx);
+
+/* Grid of nx x ny nodes with steps dx, dy (same length unit as the
+ * wavelength), Eq. 2.  Invalidates the factors. */
+stdd_status stdd_set_grid(stdd_ctx *ctx, int nx, int ny, double dx, double dy);
+
+/* Node permittivity epsbar (Eq. 3; real, nx*ny doubles, index g).
+ * Requires set_grid.  Copied.  Invalidates the factors. */
+stdd_status stdd_set_permittivity(stdd_ctx *ctx, const double *eps_node, int is_device);
+
+/* Free-space wavelength; k0 = 2 pi / wavelength (Eq. 1).  Invalidates the
+ * factors. */
+stdd_status stdd_set_frequency(stdd_ctx *ctx, double wavelength);
+
+/* Global PML: npml = {x0, x1, y0, y1} cells at the four sides, polynomial
+ * order m and normal-incidence reflection R0 (Eqs. 10-13).  sigma/(w eps0)
+ * = (m+1)(-ln R0)/(2 k0 d) (rho/d)^m with d = L*delta; node u = 1..L of a
+ * PML sits at depth rho = (u - 1/2) delta and half node u + 1/2 at u delta
+ * from the interface.  Invalidates the factors. */
+stdd_status stdd_set_pml(stdd_ctx *ctx, const int npml[4], int order_m, double R0);
+
+/* Strip decomposition along x (Sec. 2.3, Fig. 3).  nsub strips own the node
+ * columns [c_k, c_{k+1}); x_cuts holds c_0 = 0 < c_1 < ... < c_nsub = nx
+ * (nsub+1 ints) or NULL for equal widths (remainder to the first strips).
+ * Each strip's local box extends `overlap` physical columns and then an
+ * `interface_pml`-cell PML into each neighbour; the global x-PML stays with
+ * the end strips and the y-PML with every strip.  overlap + interface_pml
+ * must not exceed a neighbour's width.  Invalidates the factors. */
+stdd_status stdd_set_decomposition(stdd_ctx *ctx, int nsub, const int *x_cuts, int overlap,
+                                   int interface_pml);
+
+/* STDD_PREC_FP64 or STDD_PREC_C64.  Invalidates the factors. */
+stdd_status stdd_set_precision(stdd_ctx *ctx, int mode);
+
+/* nrhs right-hand sides b (Eq. 4), nrhs * 2*nx*ny doubles.  Copied.  Does
+ * not invalidate the factors (the matrix is unchanged). */
+stdd_status stdd_set_sources(stdd_ctx *ctx, int nrhs, const double *b_interleaved, int is_device);
+
+/* Preprocessing of Algorithm 1: nested-dissection symbolic analysis of each
+ * strip shape (host) and numeric multifrontal LU of every strip's A_i
+ * (device, batched over strips and fronts), A_i = P^T L U Q^T (Eq. 22). */
+stdd_status stdd_factor(stdd_ctx *ctx);
+
+typedef struct {
+  int restart;            /* GMRES restart length m (>= 1)                   */
+  int maxit;              /* total inner iterations (or sweeps) allowed     */
+  double rtol;            /* stop at ||b - A x|| / ||b|| <= rtol             */
+  int x0_mode;            /* STDD_X0_ZERO or STDD_X0_USER                    */
+  const double *x0;       /* initial guesses (nrhs fields) if USER          */
+  int x0_is_device;
+  int paper_richardson;   /* 1: run Algorithm 1 itself (Richardson form,
+                             stop when sum_i ||e_i^F|| < rtol * ||e^(0)||,
+                             Eq. 20) instead of FGMRES                       */
+} stdd_solve_opts;
+
+/* Solve every right-hand side; x_out receives nrhs fields.  Returns
+ * STDD_ENOCONV if some right-hand side did not reach rtol within maxit (its
+ * last iterate is still written). */
+stdd_status stdd_solve(stdd_ctx *ctx, const stdd_solve_opts *opts, double *x_out, int is_device);
+
+/* Relative residual history of right-hand side `rhs` of the last solve:
+ * entry 0 is the initial true residual, entry k the estimate after inner
+ * iteration k (FGMRES) or the true residual after sweep k (Richardson).
+ * Copies min(cap, n) values into out (host) and stores n in *n_out. */
+stdd_status stdd_residual_history(stdd_ctx *ctx, int rhs, double *out, int cap, int *n_out);
+
+const char *stdd_last_error(const stdd_ctx *ctx);
+
+/* ---------------------------------------------------------------------
+ * Operator-level entry points (each one step of the hot path).  All take
+ * single complex vectors.
+ * ------------------------------------------------------------------- */
+
+/* y = A x, the global stretched 5-point operator (Eqs. 2, 9).  Needs grid,
+ * permittivity, frequency and PML. */
+stdd_status stdd_apply_operator(stdd_ctx *ctx, const double *x, double *y, int is_device);
+
+/* z = M^-1 v = sum_i E_i A_i^-1 R_i^I v: restriction to owned columns,
+ * batched multifrontal forward/back substitution in every strip, and
+ * synthesis of the full local fields (Algorithm 1 sweep, Eq. 21).  Needs
+ * stdd_factor. */
+stdd_status stdd_apply_preconditioner(stdd_ctx *ctx, const double *v, double *z, int is_device);
+
+/* z = A_k^-1 t for strip k alone; t and z are local fields of
+ * (x1 - x0) * ny complex values, local index (i - x0)*ny + j. */
+stdd_status stdd_local_solve(stdd_ctx *ctx, int strip, const double *t, double *z, int is_device);
+
+/* Columns of strip k: owned [c0, c1), local box [x0, x1). */
+stdd_status stdd_strip_info(const stdd_ctx *ctx, int strip, int *c0, int *c1, int *x0, int *x1);
+
+typedef struct {
+  long long nfronts;          /* fronts over all strips                     */
+  int depth;                  /* levels of the deepest elimination tree     */
+  int max_pivots;             /* largest separator / leaf pivot block       */
+  int max_border;             /* largest front border                       */
+  long long factor_entries;   /* complex entries stored in L and U          */
+  double factor_flops;        /* real flops of the numeric factorization    */
+  double solve_flops;         /* real flops of one M^-1 application         */
+  long long local_dofs;       /* sum of local box sizes                     */
+  long long device_bytes;     /* device memory held by the context          */
+  int iterations;             /* inner iterations of the last solve (rhs 0) */
+  double final_residual;      /* true relative residual (rhs 0)             */
+  double min_pivot;           /* smallest |pivot| seen by the factorization */
+} stdd_stats;
+
+stdd_status stdd_get_stats(stdd_ctx *ctx, stdd_stats *out);
+
+/* Host-only nested-dissection analysis of one W x H box (no GPU needed).
+ * First call with nodes == NULL to get *nfronts and *nnodes; then call
+ * again with arrays of those sizes.  Fronts come in elimination order
+ * (children before parents).  For front f: p[f] pivots and b[f] border
+ * nodes, listed in nodes[off_f .. off_f + p[f] + b[f]) with off_f the
+ * running sum of p + b, pivots first; a node is x*H + y.  parent[f] = -1
+ * for the root; level[f] is the depth from the root. */
+stdd_status stdd_nd_analyze(int W, int H, int leaf_max, int *nfronts, long long *nnodes, int *p,
+                            int *b, int *parent, int *level, int *nodes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STDD_H */

@@ -1,0 +1,235 @@
+"""Thin Python binding of the C ABI in include/stdd.h (ctypes).
+
+Argument marshalling only: every function has the name of the C entry point
+it wraps, takes numpy arrays or torch tensors (complex128 for fields,
+float64 for permittivity) and passes their pointers with ``is_device`` set
+from the tensor's device.  All computation happens in libstdd.so; if the
+library is missing this module raises on import.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstdd.so")
+
+STDD_OK, STDD_EINVAL, STDD_ESTATE, STDD_ENOMEM, STDD_ECUDA = 0, 1, 2, 3, 4
+STDD_EPIVOT, STDD_EBREAKDOWN, STDD_ENOCONV, STDD_ETIMEOUT = 5, 6, 7, 8
+STDD_PREC_FP64, STDD_PREC_C64 = 0, 1
+STDD_X0_ZERO, STDD_X0_USER = 0, 1
+STATUS_NAMES = {0: "STDD_OK", 1: "STDD_EINVAL", 2: "STDD_ESTATE", 3: "STDD_ENOMEM", 4: "STDD_ECUDA",
+                5: "STDD_EPIVOT", 6: "STDD_EBREAKDOWN", 7: "STDD_ENOCONV", 8: "STDD_ETIMEOUT"}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libstdd.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+P = ctypes.POINTER
+
+
+class stdd_solve_opts(ctypes.Structure):
+    _fields_ = [("restart", c_int), ("maxit", c_int), ("rtol", c_double), ("x0_mode", c_int),
+                ("x0", c_void_p), ("x0_is_device", c_int), ("paper_richardson", c_int)]
+
+
+class stdd_stats(ctypes.Structure):
+    _fields_ = [("nfronts", ctypes.c_longlong), ("depth", c_int), ("max_pivots", c_int),
+                ("max_border", c_int), ("factor_entries", ctypes.c_longlong),
+                ("factor_flops", c_double), ("solve_flops", c_double),
+                ("local_dofs", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
+                ("iterations", c_int), ("final_residual", c_double), ("min_pivot", c_double)]
+
+
+_SIGS = {
+    "stdd_create": (c_int, [P(c_void_p), c_int, c_void_p]),
+    "stdd_destroy": (None, [c_void_p]),
+    "stdd_set_grid": (c_int, [c_void_p, c_int, c_int, c_double, c_double]),
+    "stdd_set_permittivity": (c_int, [c_void_p, c_void_p, c_int]),
+    "stdd_set_frequency": (c_int, [c_void_p, c_double]),
+    "stdd_set_pml": (c_int, [c_void_p, P(c_int), c_int, c_double]),
+    "stdd_set_decomposition": (c_int, [c_void_p, c_int, P(c_int), c_int, c_int]),
+    "stdd_set_precision": (c_int, [c_void_p, c_int]),
+    "stdd_set_sources": (c_int, [c_void_p, c_int, c_void_p, c_int]),
+    "stdd_factor": (c_int, [c_void_p]),
+    "stdd_solve": (c_int, [c_void_p, P(stdd_solve_opts), c_void_p, c_int]),
+    "stdd_residual_history": (c_int, [c_void_p, c_int, P(c_double), c_int, P(c_int)]),
+    "stdd_last_error": (ctypes.c_char_p, [c_void_p]),
+    "stdd_apply_operator": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    "stdd_apply_preconditioner": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    "stdd_local_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
+    "stdd_strip_info": (c_int, [c_void_p, c_int, P(c_int), P(c_int), P(c_int), P(c_int)]),
+    "stdd_get_stats": (c_int, [c_void_p, P(stdd_stats)]),
+    "stdd_nd_analyze": (c_int, [c_int, c_int, c_int, P(c_int), P(ctypes.c_longlong), c_void_p, c_void_p,
+                                c_void_p, c_void_p, c_void_p]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+class StddError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(a):
+    """(pointer, is_device) of a numpy array or torch tensor (contiguous)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _check(ctx, st, allow=()):
+    if st != STDD_OK and st not in allow:
+        msg = lib.stdd_last_error(ctx)
+        raise StddError(st, msg.decode() if msg else "")
+    return st
+
+
+def stdd_create(device=0, stream=None):
+    ctx = c_void_p()
+    st = lib.stdd_create(ctypes.byref(ctx), int(device), c_void_p(stream) if stream else None)
+    if st != STDD_OK:
+        raise StddError(st, "stdd_create failed")
+    return ctx
+
+
+def stdd_destroy(ctx):
+    lib.stdd_destroy(ctx)
+
+
+def stdd_set_grid(ctx, nx, ny, dx, dy):
+    return _check(ctx, lib.stdd_set_grid(ctx, int(nx), int(ny), float(dx), float(dy)))
+
+
+def stdd_set_permittivity(ctx, eps):
+    p, dev = _ptr(eps)
+    return _check(ctx, lib.stdd_set_permittivity(ctx, c_void_p(p), dev))
+
+
+def stdd_set_frequency(ctx, wavelength):
+    return _check(ctx, lib.stdd_set_frequency(ctx, float(wavelength)))
+
+
+def stdd_set_pml(ctx, npml, order_m, R0):
+    arr = (c_int * 4)(*[int(v) for v in npml])
+    return _check(ctx, lib.stdd_set_pml(ctx, arr, int(order_m), float(R0)))
+
+
+def stdd_set_decomposition(ctx, nsub, x_cuts, overlap, interface_pml):
+    cuts = None if x_cuts is None else (c_int * (nsub + 1))(*[int(v) for v in x_cuts])
+    return _check(ctx, lib.stdd_set_decomposition(ctx, int(nsub), cuts, int(overlap), int(interface_pml)))
+
+
+def stdd_set_precision(ctx, mode):
+    return _check(ctx, lib.stdd_set_precision(ctx, int(mode)))
+
+
+def stdd_set_sources(ctx, nrhs, b):
+    p, dev = _ptr(b)
+    return _check(ctx, lib.stdd_set_sources(ctx, int(nrhs), c_void_p(p), dev))
+
+
+def stdd_factor(ctx):
+    return _check(ctx, lib.stdd_factor(ctx))
+
+
+def stdd_solve(ctx, x_out, restart=30, maxit=1000, rtol=1e-10, x0=None, paper_richardson=False,
+               allow_noconv=False):
+    o = stdd_solve_opts()
+    o.restart, o.maxit, o.rtol = int(restart), int(maxit), float(rtol)
+    o.paper_richardson = 1 if paper_richardson else 0
+    if x0 is None:
+        o.x0_mode, o.x0, o.x0_is_device = STDD_X0_ZERO, None, 0
+    else:
+        p, dev = _ptr(x0)
+        o.x0_mode, o.x0, o.x0_is_device = STDD_X0_USER, p, dev
+    p, dev = _ptr(x_out)
+    allow = (STDD_ENOCONV,) if allow_noconv else ()
+    return _check(ctx, lib.stdd_solve(ctx, ctypes.byref(o), c_void_p(p), dev), allow)
+
+
+def stdd_residual_history(ctx, rhs=0):
+    n = c_int(0)
+    _check(ctx, lib.stdd_residual_history(ctx, int(rhs), None, 0, ctypes.byref(n)))
+    out = (c_double * max(1, n.value))()
+    _check(ctx, lib.stdd_residual_history(ctx, int(rhs), out, n.value, ctypes.byref(n)))
+    return np.array(out[:n.value])
+
+
+def stdd_last_error(ctx):
+    m = lib.stdd_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def stdd_apply_operator(ctx, x, y):
+    px, dx_ = _ptr(x)
+    py, dy_ = _ptr(y)
+    if dx_ != dy_:
+        raise ValueError("x and y must live on the same side")
+    return _check(ctx, lib.stdd_apply_operator(ctx, c_void_p(px), c_void_p(py), dx_))
+
+
+def stdd_apply_preconditioner(ctx, v, z):
+    pv, dv = _ptr(v)
+    pz, dz = _ptr(z)
+    if dv != dz:
+        raise ValueError("v and z must live on the same side")
+    return _check(ctx, lib.stdd_apply_preconditioner(ctx, c_void_p(pv), c_void_p(pz), dv))
+
+
+def stdd_local_solve(ctx, strip, t, z):
+    pt, dt = _ptr(t)
+    pz, dz = _ptr(z)
+    if dt != dz:
+        raise ValueError("t and z must live on the same side")
+    return _check(ctx, lib.stdd_local_solve(ctx, int(strip), c_void_p(pt), c_void_p(pz), dt))
+
+
+def stdd_strip_info(ctx, strip):
+    v = [c_int() for _ in range(4)]
+    _check(ctx, lib.stdd_strip_info(ctx, int(strip), *[ctypes.byref(x) for x in v]))
+    c0, c1, x0, x1 = (x.value for x in v)
+    return dict(c0=c0, c1=c1, x0=x0, x1=x1)
+
+
+def stdd_get_stats(ctx):
+    s = stdd_stats()
+    _check(ctx, lib.stdd_get_stats(ctx, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in stdd_stats._fields_}
+
+
+def stdd_nd_analyze(W, H, leaf_max=64):
+    """Host-only nested-dissection analysis; returns dict of numpy arrays."""
+    nf = c_int(0)
+    nn = ctypes.c_longlong(0)
+    st = lib.stdd_nd_analyze(int(W), int(H), int(leaf_max), ctypes.byref(nf), ctypes.byref(nn),
+                             None, None, None, None, None)
+    if st != STDD_OK:
+        raise StddError(st, "stdd_nd_analyze failed")
+    p = np.zeros(nf.value, np.int32)
+    b = np.zeros(nf.value, np.int32)
+    parent = np.zeros(nf.value, np.int32)
+    level = np.zeros(nf.value, np.int32)
+    nodes = np.zeros(max(1, nn.value), np.int32)
+    st = lib.stdd_nd_analyze(int(W), int(H), int(leaf_max), ctypes.byref(nf), ctypes.byref(nn),
+                             p.ctypes.data, b.ctypes.data, parent.ctypes.data, level.ctypes.data,
+                             nodes.ctypes.data)
+    if st != STDD_OK:
+        raise StddError(st, "stdd_nd_analyze failed")
+    return dict(p=p, b=b, parent=parent, level=level, nodes=nodes[:nn.value])

@@ -1,0 +1,1003 @@
+// C ABI (include/stdd.h): context, configuration state machine, the
+// preprocessing of Algorithm 1 (symbolic analysis + batched numeric
+// multifrontal factorization) and the flexible GMRES outer iteration whose
+// preconditioner is one Jacobi source-transfer sweep (Algorithm 1's loop
+// body in residual form, Eqs. 18-21).
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/stdd.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "symbolic.h"
+
+using stdd::FrontDev;
+using stdd::LevelInfo;
+using stdd::MfArgs;
+using stdd::Shape;
+using stdd::StripDev;
+using cd = std::complex<double>;
+
+namespace {
+
+struct CudaError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+struct ArgError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+struct StateError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
+#define CK(expr)                                                                         \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      throw CudaError(std::string(#expr) + ": " + cudaGetErrorString(_e));               \
+  } while (0)
+
+// owning device allocation
+struct DBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf &) = delete;
+  DBuf &operator=(const DBuf &) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void alloc(size_t n) {
+    if (n <= bytes && p) return;
+    release();
+    if (n == 0) return;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      (void)cudaGetLastError();
+      throw std::bad_alloc();
+    }
+    bytes = n;
+  }
+  template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// SC-PML stretch on a line of n nodes (Eqs. 10-13): node u = 1..L of a PML
+// at depth (u - 1/2) cells, half node u + 1/2 at depth u cells from the
+// interface; sigma/(w eps0) = (m+1)(-ln R)/(2 k0 L delta) (rho/(L delta))^m.
+void stretch(int n, int Llo, int Lhi, double delta, double k0, int m, double R, std::vector<cd> &s,
+             std::vector<cd> &sh) {
+  auto smax = [&](int L) { return (m + 1) * (-std::log(R)) / (2.0 * k0 * L * delta); };
+  auto sig = [&](double pos) {
+    double v = 0;
+    if (Llo > 0) {
+      const double d = std::max(0.0, (Llo - 0.5) - pos);
+      v += smax(Llo) * std::pow(d / Llo, m);
+    }
+    if (Lhi > 0) {
+      const double d = std::max(0.0, pos - (n - Lhi - 0.5));
+      v += smax(Lhi) * std::pow(d / Lhi, m);
+    }
+    return v;
+  };
+  s.resize(n);
+  sh.resize(n + 1);
+  for (int i = 0; i < n; ++i) s[i] = cd(1.0, sig(i));
+  for (int h = 0; h <= n; ++h) sh[h] = cd(1.0, sig(h - 0.5));
+}
+
+// couplings of row i to i-1 and i+1: 1/(s_i s_{i-+1/2} delta^2)
+void couplings(const std::vector<cd> &s, const std::vector<cd> &sh, double delta, std::vector<double2> &cm,
+               std::vector<double2> &cp) {
+  const int n = (int)s.size();
+  cm.resize(n);
+  cp.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const cd a = 1.0 / (s[i] * sh[i] * delta * delta);
+    const cd b = 1.0 / (s[i] * sh[i + 1] * delta * delta);
+    cm[i] = make_double2(a.real(), a.imag());
+    cp[i] = make_double2(b.real(), b.imag());
+  }
+}
+
+template <typename T> void upload(DBuf &d, const std::vector<T> &h, cudaStream_t st) {
+  d.alloc(std::max<size_t>(1, h.size()) * sizeof(T));
+  if (!h.empty()) CK(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+}
+
+struct StripHost {
+  int c0, c1, x0, x1, Llo, Lhi;
+  int W() const { return x1 - x0; }
+};
+
+}  // namespace
+
+struct stdd_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+
+  // configuration
+  int nx = 0, ny = 0;
+  double dx = 0, dy = 0, wavelength = 0;
+  bool have_eps = false;
+  int npml[4] = {0, 0, 0, 0};
+  int pml_m = 3;
+  double pml_R = 1e-8;
+  bool have_pml = false;
+  int nsub = 0, overlap = 0, ipml = 0;
+  std::vector<int> cuts;
+  int prec = STDD_PREC_FP64;
+  int leaf_max = 64;
+  int nrhs = 0;
+
+  // operator (global) state
+  bool op_ready = false;
+  DBuf d_eps, d_cxm, d_cxp, d_cym, d_cyp;
+  double k0sq = 0;
+
+  // decomposition + factors
+  bool factored = false;
+  std::vector<StripHost> strips;
+  std::map<int, Shape> shapes;
+  std::vector<LevelInfo> levels;
+  DBuf d_strips, d_fronts, d_nodes, d_cmap, d_inv, d_lcxm, d_lcxp, d_colstrip;
+  DBuf d_fac, d_ws[2], d_ub[2], d_tloc, d_flag, d_minpiv;
+  int64_t nloc = 0, nloc_max = 0, ub_elems[2] = {0, 0};
+  int64_t nfronts = 0, factor_entries = 0;
+  double factor_cflops = 0, solve_cflops = 0;
+  int max_p = 0, max_b = 0, depth = 0;
+  double min_pivot = 0;
+  int solve_nrhs_cap = 0;
+
+  // sources and Krylov state
+  DBuf d_b, d_x, d_r, d_V, d_Z, d_w, d_part, d_h, d_nrm, d_y, d_pre, d_fpart;
+  int V_cols = 0;
+  std::vector<std::vector<double>> history;
+  int last_its = 0;
+  double last_res = 0;
+
+  size_t elem() const { return prec == STDD_PREC_FP64 ? sizeof(double2) : sizeof(float2); }
+  int64_t N() const { return (int64_t)nx * ny; }
+
+  void invalidate_factors() { factored = false; }
+  void invalidate_operator() {
+    op_ready = false;
+    factored = false;
+  }
+
+  stdd::GridDev grid() const {
+    stdd::GridDev g;
+    g.nx = nx;
+    g.ny = ny;
+    g.k0sq = k0sq;
+    g.eps = d_eps.as<double>();
+    g.cxm = d_cxm.as<double2>();
+    g.cxp = d_cxp.as<double2>();
+    g.cym = d_cym.as<double2>();
+    g.cyp = d_cyp.as<double2>();
+    return g;
+  }
+
+  void require_operator() {
+    if (nx <= 0) throw StateError("grid not set");
+    if (!have_eps) throw StateError("permittivity not set");
+    if (wavelength <= 0) throw StateError("frequency not set");
+    if (!have_pml) throw StateError("PML not set");
+    if (op_ready) return;
+    const double k0 = 2.0 * M_PI / wavelength;
+    k0sq = k0 * k0;
+    std::vector<cd> sx, sxh, sy, syh;
+    stretch(nx, npml[0], npml[1], dx, k0, pml_m, pml_R, sx, sxh);
+    stretch(ny, npml[2], npml[3], dy, k0, pml_m, pml_R, sy, syh);
+    std::vector<double2> cxm, cxp, cym, cyp;
+    couplings(sx, sxh, dx, cxm, cxp);
+    couplings(sy, syh, dy, cym, cyp);
+    upload(d_cxm, cxm, stream);
+    upload(d_cxp, cxp, stream);
+    upload(d_cym, cym, stream);
+    upload(d_cyp, cyp, stream);
+    CK(cudaStreamSynchronize(stream));
+    op_ready = true;
+  }
+
+  void build_strips() {
+    if (nsub <= 0) throw StateError("decomposition not set");
+    const int ext = overlap + ipml;
+    std::vector<int> c = cuts;
+    if (c.empty()) {
+      c.push_back(0);
+      const int base = nx / nsub, rem = nx % nsub;
+      for (int k = 0; k < nsub; ++k) c.push_back(c.back() + base + (k < rem ? 1 : 0));
+    }
+    strips.clear();
+    for (int k = 0; k < nsub; ++k) {
+      StripHost s;
+      s.c0 = c[k];
+      s.c1 = c[k + 1];
+      s.x0 = k > 0 ? s.c0 - ext : 0;
+      s.x1 = k < nsub - 1 ? s.c1 + ext : nx;
+      s.Llo = k > 0 ? ipml : npml[0];
+      s.Lhi = k < nsub - 1 ? ipml : npml[1];
+      if (k > 0 && ext > c[k] - c[k - 1]) throw ArgError("overlap + interface PML wider than a neighbouring strip");
+      if (k < nsub - 1 && ext > c[k + 2] - c[k + 1])
+        throw ArgError("overlap + interface PML wider than a neighbouring strip");
+      strips.push_back(s);
+    }
+  }
+
+  void factor();
+  void apply_minv(const double2 *v, double2 *z);
+  template <typename R> void factor_t();
+  template <typename R> void solve_levels(int nrhs_);
+  void ensure_solve_buffers(int nr);
+  MfArgs mf_args(int level_parity_cur, bool solve) const;
+  void ensure_krylov(int m);
+  void gmres(int rhs, const stdd_solve_opts &o, double2 *x);
+  void richardson(int rhs, const stdd_solve_opts &o, double2 *x);
+  int64_t device_bytes() const;
+};
+
+MfArgs stdd_ctx::mf_args(int par, bool solve) const {
+  MfArgs a;
+  a.fronts = d_fronts.as<FrontDev>();
+  a.strips = d_strips.as<StripDev>();
+  a.nodes = d_nodes.as<int>();
+  a.cmap = d_cmap.as<int>();
+  a.inv = d_inv.as<int>();
+  a.cxm = d_lcxm.as<double2>();
+  a.cxp = d_lcxp.as<double2>();
+  a.cym = d_cym.as<double2>();
+  a.cyp = d_cyp.as<double2>();
+  a.eps = d_eps.as<double>();
+  a.k0sq = k0sq;
+  a.H = ny;
+  a.fac = d_fac.p;
+  a.ws_cur = d_ws[par].p;
+  a.ws_child = d_ws[par ^ 1].p;
+  a.tloc = d_tloc.p;
+  a.ub_cur = d_ub[par].p;
+  a.ub_child = d_ub[par ^ 1].p;
+  a.flag = d_flag.as<int>();
+  a.min_pivot = d_minpiv.as<double>();
+  (void)solve;
+  return a;
+}
+
+void stdd_ctx::factor() {
+  require_operator();
+  build_strips();
+  factored = false;
+  // ---- symbolic analysis per distinct strip width (host, cached)
+  for (auto &s : strips) {
+    if (!shapes.count(s.W()) || shapes[s.W()].H != ny || shapes[s.W()].leaf_max != leaf_max) {
+      Shape sh;
+      stdd::nd_analyze(s.W(), ny, leaf_max, sh);
+      shapes[s.W()] = std::move(sh);
+    }
+  }
+  // concatenated shape arrays
+  std::map<int, int64_t> node_base, cmap_base, inv_base;
+  std::vector<int> nodes, cmap, inv;
+  for (auto &kv : shapes) {
+    node_base[kv.first] = (int64_t)nodes.size();
+    cmap_base[kv.first] = (int64_t)cmap.size();
+    inv_base[kv.first] = (int64_t)inv.size();
+    nodes.insert(nodes.end(), kv.second.nodes.begin(), kv.second.nodes.end());
+    cmap.insert(cmap.end(), kv.second.cmap.begin(), kv.second.cmap.end());
+    inv.insert(inv.end(), kv.second.inv.begin(), kv.second.inv.end());
+  }
+  // ---- strips: local fields, local x couplings, factor blocks
+  const double k0 = 2.0 * M_PI / wavelength;
+  std::vector<StripDev> sdev(nsub);
+  std::vector<double2> lcxm, lcxp;
+  int64_t vec = 0, fac = 0, coef = 0;
+  depth = 0;
+  max_p = max_b = 0;
+  factor_cflops = solve_cflops = 0;
+  nloc_max = 0;
+  for (int k = 0; k < nsub; ++k) {
+    const StripHost &s = strips[k];
+    const Shape &sh = shapes[s.W()];
+    sdev[k].x0 = s.x0;
+    sdev[k].x1 = s.x1;
+    sdev[k].c0 = s.c0;
+    sdev[k].c1 = s.c1;
+    sdev[k].vec_off = vec;
+    sdev[k].coef_off = coef;
+    sdev[k].fac_off = fac;
+    vec += (int64_t)s.W() * ny;
+    nloc_max = std::max<int64_t>(nloc_max, (int64_t)s.W() * ny);
+    fac += sh.factor_entries;
+    std::vector<cd> sx, sxh;
+    stretch(s.W(), s.Llo, s.Lhi, dx, k0, pml_m, pml_R, sx, sxh);
+    std::vector<double2> cm, cp;
+    couplings(sx, sxh, dx, cm, cp);
+    lcxm.insert(lcxm.end(), cm.begin(), cm.end());
+    lcxp.insert(lcxp.end(), cp.begin(), cp.end());
+    coef += s.W();
+    depth = std::max(depth, sh.depth);
+    max_p = std::max(max_p, sh.max_p);
+    max_b = std::max(max_b, sh.max_b);
+    factor_cflops += sh.factor_cflops;
+    solve_cflops += sh.solve_cflops;
+  }
+  nloc = vec;
+  factor_entries = fac;
+  // ---- front instances, level-major
+  std::vector<std::vector<int>> inst(nsub);
+  for (int k = 0; k < nsub; ++k) inst[k].assign(shapes[strips[k].W()].fronts.size(), -1);
+  std::vector<FrontDev> fr;
+  levels.assign(depth, LevelInfo{0, 0, 0, 0, 0});
+  int64_t ws_need[2] = {0, 0};
+  ub_elems[0] = ub_elems[1] = 0;
+  for (int L = 0; L < depth; ++L) {
+    LevelInfo &li = levels[L];
+    li.f0 = (int)fr.size();
+    int64_t s_run = 0, u_run = 0;
+    for (int k = 0; k < nsub; ++k) {
+      const Shape &sh = shapes[strips[k].W()];
+      for (size_t f = 0; f < sh.fronts.size(); ++f) {
+        const auto &sf = sh.fronts[f];
+        if (sf.level != L) continue;
+        inst[k][f] = (int)fr.size();
+        FrontDev d;
+        d.p = sf.p;
+        d.b = sf.b;
+        d.strip = k;
+        d.child[0] = d.child[1] = -1;
+        d.node_off = node_base[sh.W] + sf.node_off;
+        for (int ci = 0; ci < 2; ++ci) {
+          d.cmap_off[ci] = sf.cmap_off[ci] >= 0 ? cmap_base[sh.W] + sf.cmap_off[ci] : -1;
+          d.inv_off[ci] = sf.inv_off[ci] >= 0 ? inv_base[sh.W] + sf.inv_off[ci] : -1;
+        }
+        d.fac_off = sdev[k].fac_off + sf.fac_off;
+        d.s_off = s_run;
+        d.u_off = u_run;
+        s_run += (int64_t)sf.b * sf.b;
+        u_run += sf.b;
+        li.max_p = std::max(li.max_p, sf.p);
+        li.max_b = std::max(li.max_b, sf.b);
+        li.max_n = std::max(li.max_n, sf.p + sf.b);
+        fr.push_back(d);
+      }
+    }
+    li.nf = (int)fr.size() - li.f0;
+    ws_need[L & 1] = std::max(ws_need[L & 1], s_run);
+    ub_elems[L & 1] = std::max(ub_elems[L & 1], u_run);
+  }
+  // children ids (instances of children are at level + 1, already numbered)
+  for (int k = 0; k < nsub; ++k) {
+    const Shape &sh = shapes[strips[k].W()];
+    for (size_t f = 0; f < sh.fronts.size(); ++f) {
+      FrontDev &d = fr[inst[k][f]];
+      for (int ci = 0; ci < 2; ++ci)
+        if (sh.fronts[f].child[ci] >= 0) d.child[ci] = inst[k][sh.fronts[f].child[ci]];
+    }
+  }
+  nfronts = (int64_t)fr.size();
+  std::vector<int> colstrip(nx);
+  for (int k = 0; k < nsub; ++k)
+    for (int i = strips[k].c0; i < strips[k].c1; ++i) colstrip[i] = k;
+
+  upload(d_strips, sdev, stream);
+  upload(d_fronts, fr, stream);
+  upload(d_nodes, nodes, stream);
+  upload(d_cmap, cmap, stream);
+  upload(d_inv, inv, stream);
+  upload(d_lcxm, lcxm, stream);
+  upload(d_lcxp, lcxp, stream);
+  upload(d_colstrip, colstrip, stream);
+  const size_t E = elem();
+  d_fac.alloc(std::max<int64_t>(1, factor_entries) * E);
+  d_ws[0].alloc(std::max<int64_t>(1, ws_need[0]) * E);
+  d_ws[1].alloc(std::max<int64_t>(1, ws_need[1]) * E);
+  solve_nrhs_cap = 0;
+  d_flag.alloc(sizeof(int));
+  d_minpiv.alloc(sizeof(double));
+  CK(cudaStreamSynchronize(stream));
+  if (prec == STDD_PREC_FP64) factor_t<double>();
+  else factor_t<float>();
+  factored = true;
+}
+
+template <typename R> void stdd_ctx::factor_t() {
+  static bool attrs = false;
+  if (!attrs) {
+    CK(stdd::mf_setup_attributes<double>());
+    CK(stdd::mf_setup_attributes<float>());
+    attrs = true;
+  }
+  CK(cudaMemsetAsync(d_flag.p, 0, sizeof(int), stream));
+  const double inf = INFINITY;
+  CK(cudaMemcpyAsync(d_minpiv.p, &inf, sizeof(double), cudaMemcpyHostToDevice, stream));
+  for (int L = depth - 1; L >= 0; --L) {
+    MfArgs a = mf_args(L & 1, false);
+    stdd::mf_factor_level<R>(a, levels[L], stream);
+    CK(cudaGetLastError());
+  }
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  CK(cudaMemcpyAsync(&min_pivot, d_minpiv.p, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  if (flag) throw std::domain_error("zero or non-finite pivot in a front");
+}
+
+template <typename R> void stdd_ctx::solve_levels(int nr) {
+  ensure_solve_buffers(nr);
+  for (int L = depth - 1; L >= 0; --L) stdd::mf_forward_level<R>(mf_args(L & 1, true), levels[L], nr, nloc, stream);
+  for (int L = 0; L < depth; ++L) stdd::mf_backward_level<R>(mf_args(L & 1, true), levels[L], nr, nloc, stream);
+  CK(cudaGetLastError());
+}
+
+void stdd_ctx::ensure_solve_buffers(int nr) {
+  if (nr <= solve_nrhs_cap) return;
+  const size_t E = elem();
+  d_tloc.alloc(std::max<int64_t>(1, nloc) * nr * E);
+  d_ub[0].alloc(std::max<int64_t>(1, ub_elems[0]) * nr * E);
+  d_ub[1].alloc(std::max<int64_t>(1, ub_elems[1]) * nr * E);
+  solve_nrhs_cap = nr;
+}
+
+// z = M^-1 v: restriction to owned columns, batched forward / back
+// substitution over every strip, synthesis of the full local fields.
+void stdd_ctx::apply_minv(const double2 *v, double2 *z) {
+  ensure_solve_buffers(1);
+  if (prec == STDD_PREC_FP64) {
+    stdd::launch_restrict<double>(d_strips.as<StripDev>(), nsub, nloc_max, ny, nullptr, v, d_tloc.p, stream);
+    solve_levels<double>(1);
+    stdd::launch_synthesize<double>(d_strips.as<StripDev>(), nsub, nx, ny, d_colstrip.as<int>(), d_tloc.p, z,
+                                    stream);
+  } else {
+    stdd::launch_restrict<float>(d_strips.as<StripDev>(), nsub, nloc_max, ny, nullptr, v, d_tloc.p, stream);
+    solve_levels<float>(1);
+    stdd::launch_synthesize<float>(d_strips.as<StripDev>(), nsub, nx, ny, d_colstrip.as<int>(), d_tloc.p, z,
+                                   stream);
+  }
+  CK(cudaGetLastError());
+}
+
+void stdd_ctx::ensure_krylov(int m) {
+  const int64_t n = N();
+  if (V_cols < m) {
+    d_V.alloc((size_t)(m + 1) * n * sizeof(double2));
+    d_Z.alloc((size_t)m * n * sizeof(double2));
+    V_cols = m;
+  }
+  d_x.alloc(n * sizeof(double2));
+  d_r.alloc(n * sizeof(double2));
+  d_w.alloc(n * sizeof(double2));
+  d_part.alloc((size_t)stdd::krylov_partial_blocks() * (m + 2) * sizeof(double2));
+  d_h.alloc((size_t)(2 * (m + 2)) * sizeof(double2));
+  d_nrm.alloc(4 * sizeof(double));
+  d_y.alloc((size_t)(m + 1) * sizeof(double2));
+  d_fpart.alloc((size_t)std::max(1, 2 * nsub) * sizeof(double));
+}
+
+namespace {
+void givens(cd a, cd b, double &c, cd &s) {
+  if (std::abs(b) == 0) {
+    c = 1;
+    s = 0;
+    return;
+  }
+  if (std::abs(a) == 0) {
+    c = 0;
+    s = std::conj(b) / std::abs(b);
+    return;
+  }
+  const double t = std::hypot(std::abs(a), std::abs(b));
+  c = std::abs(a) / t;
+  s = (a / std::abs(a)) * std::conj(b) / t;
+}
+
+double dev_norm(double2 *x, int64_t n, DBuf &part, DBuf &nrm, cudaStream_t st) {
+  stdd::launch_norm2(x, n, reinterpret_cast<double *>(part.p), nrm.as<double>(), st);
+  double v = 0;
+  CK(cudaMemcpyAsync(&v, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return std::sqrt(v);
+}
+}  // namespace
+
+// Restarted flexible GMRES(m), right preconditioned by M^-1 (FP64; CGS2
+// orthogonalisation; Givens rotations and the small triangular solve on the
+// host).  x holds the initial guess on entry and the iterate on exit.
+void stdd_ctx::gmres(int rhs, const stdd_solve_opts &o, double2 *x) {
+  const int m = o.restart;
+  const int64_t n = N();
+  ensure_krylov(m);
+  auto &hist = history[rhs];
+  const double2 *b = d_b.as<double2>() + (int64_t)rhs * n;
+  const double bnorm = dev_norm(const_cast<double2 *>(b), n, d_part, d_nrm, stream);
+  if (bnorm == 0) {
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double2), stream));
+    hist.push_back(0.0);
+    last_res = 0;
+    return;
+  }
+  double2 *V = d_V.as<double2>(), *Z = d_Z.as<double2>(), *r = d_r.as<double2>();
+  double2 *h1 = d_h.as<double2>(), *h2 = h1 + (m + 2);
+  double *nrm = d_nrm.as<double>();
+  double *part = reinterpret_cast<double *>(d_part.p);
+  int its = 0;
+  std::vector<cd> H((size_t)(m + 1) * m), g(m + 1), sn(m), hv(2 * (m + 2));
+  std::vector<double> cs(m);
+  while (true) {
+    stdd::launch_residual(grid(), b, x, r, stream);
+    const double beta = dev_norm(r, n, d_part, d_nrm, stream);
+    if (hist.empty()) hist.push_back(beta / bnorm);
+    last_res = beta / bnorm;
+    if (!std::isfinite(beta)) throw std::range_error("non-finite residual");
+    if (beta / bnorm <= o.rtol || its >= o.maxit) break;
+    stdd::launch_scale(r, nrm, V, n, stream);
+    std::fill(H.begin(), H.end(), cd(0));
+    std::fill(g.begin(), g.end(), cd(0));
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      double2 *vj = V + (int64_t)j * n, *zj = Z + (int64_t)j * n, *w = V + (int64_t)(j + 1) * n;
+      apply_minv(vj, zj);
+      stdd::launch_stencil(grid(), zj, w, stream);
+      stdd::launch_mdot(V, n, j + 1, w, n, d_part.as<double2>(), h1, stream);
+      stdd::launch_maxpy_norm(V, n, j + 1, h1, w, n, part, nrm, stream);
+      stdd::launch_mdot(V, n, j + 1, w, n, d_part.as<double2>(), h2, stream);
+      stdd::launch_maxpy_norm(V, n, j + 1, h2, w, n, part, nrm, stream);
+      double nrm2 = 0;
+      CK(cudaMemcpyAsync(hv.data(), h1, sizeof(double2) * 2 * (m + 2), cudaMemcpyDeviceToHost, stream));
+      CK(cudaMemcpyAsync(&nrm2, nrm, sizeof(double), cudaMemcpyDeviceToHost, stream));
+      CK(cudaStreamSynchronize(stream));
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hv[i] + hv[(m + 2) + i];
+      const double hn = std::sqrt(nrm2);
+      H[(size_t)(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const cd t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)(i + 1) * m + j] = -std::conj(sn[i]) * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = t;
+      }
+      givens(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j], cs[j], sn[j]);
+      const cd hjj = cs[j] * H[(size_t)j * m + j] + sn[j] * H[(size_t)(j + 1) * m + j];
+      H[(size_t)j * m + j] = hjj;
+      H[(size_t)(j + 1) * m + j] = 0;
+      g[j + 1] = -std::conj(sn[j]) * g[j];
+      g[j] = cs[j] * g[j];
+      ++its;
+      k = j + 1;
+      const double est = std::abs(g[j + 1]) / bnorm;
+      hist.push_back(est);
+      if (!std::isfinite(est)) throw std::range_error("non-finite residual estimate");
+      const bool breakdown = !(hn > 0) || std::abs(hjj) == 0;
+      if (!breakdown) stdd::launch_scale(w, nrm, w, n, stream);
+      if (est <= o.rtol || its >= o.maxit || breakdown) break;
+    }
+    // y = R^-1 g, x += Z y
+    std::vector<cd> y(k);
+    for (int i = k - 1; i >= 0; --i) {
+      cd s = g[i];
+      for (int l = i + 1; l < k; ++l) s -= H[(size_t)i * m + l] * y[l];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    std::vector<double2> yd(k);
+    for (int i = 0; i < k; ++i) yd[i] = make_double2(y[i].real(), y[i].imag());
+    CK(cudaMemcpyAsync(d_y.p, yd.data(), sizeof(double2) * k, cudaMemcpyHostToDevice, stream));
+    stdd::launch_maxpy(Z, n, k, d_y.as<double2>(), x, n, stream);
+    CK(cudaStreamSynchronize(stream));
+  }
+  last_its = its;
+}
+
+// Algorithm 1 in residual form: x_{n+1} = x_n + M^-1 (b - A x_n) from x_0,
+// stopping when sum_i ||e_i^F|| < rtol * sum_i ||e_i^(0)|| (Eq. 20, with a
+// relative TOL); the history records the true relative residual per sweep.
+void stdd_ctx::richardson(int rhs, const stdd_solve_opts &o, double2 *x) {
+  const int64_t n = N();
+  ensure_krylov(1);
+  auto &hist = history[rhs];
+  const double2 *b = d_b.as<double2>() + (int64_t)rhs * n;
+  const double bnorm = dev_norm(const_cast<double2 *>(b), n, d_part, d_nrm, stream);
+  double2 *r = d_r.as<double2>(), *z = d_w.as<double2>();
+  double f0 = -1;
+  int its = 0;
+  stdd::launch_residual(grid(), b, x, r, stream);
+  hist.push_back(bnorm > 0 ? dev_norm(r, n, d_part, d_nrm, stream) / bnorm : 0.0);
+  while (its < o.maxit && bnorm > 0) {
+    apply_minv(r, z);
+    // sum_i ||e_i^F|| and sum_i ||e_i|| from the local fields of this sweep
+    if (prec == STDD_PREC_FP64)
+      stdd::launch_strip_norms<double>(d_strips.as<StripDev>(), nsub, ny, d_tloc.p, d_fpart.as<double>(), stream);
+    else
+      stdd::launch_strip_norms<float>(d_strips.as<StripDev>(), nsub, ny, d_tloc.p, d_fpart.as<double>(), stream);
+    std::vector<double> sn2(2 * nsub);
+    CK(cudaMemcpyAsync(sn2.data(), d_fpart.p, sizeof(double) * 2 * nsub, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    double fsum = 0, esum = 0;
+    for (int k = 0; k < nsub; ++k) {
+      fsum += std::sqrt(sn2[2 * k]);
+      esum += std::sqrt(sn2[2 * k + 1]);
+    }
+    if (f0 < 0) f0 = esum;
+    // x += z
+    std::vector<double2> one(1, make_double2(1.0, 0.0));
+    CK(cudaMemcpyAsync(d_y.p, one.data(), sizeof(double2), cudaMemcpyHostToDevice, stream));
+    stdd::launch_maxpy(z, n, 1, d_y.as<double2>(), x, n, stream);
+    ++its;
+    stdd::launch_residual(grid(), b, x, r, stream);
+    const double res = dev_norm(r, n, d_part, d_nrm, stream) / bnorm;
+    hist.push_back(res);
+    last_res = res;
+    if (!std::isfinite(res)) throw std::range_error("non-finite residual");
+    if (fsum < o.rtol * f0) break;
+  }
+  last_its = its;
+}
+
+int64_t stdd_ctx::device_bytes() const {
+  const DBuf *all[] = {&d_eps, &d_cxm, &d_cxp, &d_cym, &d_cyp, &d_strips, &d_fronts, &d_nodes, &d_cmap,
+                       &d_inv, &d_lcxm, &d_lcxp, &d_colstrip, &d_fac, &d_ws[0], &d_ws[1], &d_ub[0],
+                       &d_ub[1], &d_tloc, &d_flag, &d_minpiv, &d_b, &d_x, &d_r, &d_V, &d_Z, &d_w,
+                       &d_part, &d_h, &d_nrm, &d_y, &d_pre, &d_fpart};
+  int64_t s = 0;
+  for (auto *d : all) s += (int64_t)d->bytes;
+  return s;
+}
+
+// ---------------------------------------------------------------- C ABI
+namespace {
+
+template <typename F> stdd_status guarded(stdd_ctx *c, F &&f) {
+  if (!c) return STDD_EINVAL;
+  try {
+    CK(cudaSetDevice(c->device));
+    f();
+    c->err.clear();
+    return STDD_OK;
+  } catch (const ArgError &e) {
+    c->err = e.what();
+    return STDD_EINVAL;
+  } catch (const std::invalid_argument &e) {
+    c->err = e.what();
+    return STDD_EINVAL;
+  } catch (const StateError &e) {
+    c->err = e.what();
+    return STDD_ESTATE;
+  } catch (const CudaError &e) {
+    c->err = e.what();
+    return STDD_ECUDA;
+  } catch (const std::bad_alloc &) {
+    c->err = "out of device or host memory";
+    return STDD_ENOMEM;
+  } catch (const std::domain_error &e) {
+    c->err = e.what();
+    return STDD_EPIVOT;
+  } catch (const std::range_error &e) {
+    c->err = e.what();
+    return STDD_EBREAKDOWN;
+  } catch (const std::exception &e) {
+    c->err = e.what();
+    return STDD_EINVAL;
+  } catch (...) {
+    c->err = "unknown error";
+    return STDD_EINVAL;
+  }
+}
+
+void copy_in(void *dst, const void *src, size_t bytes, int is_device, cudaStream_t st) {
+  CK(cudaMemcpyAsync(dst, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+}
+void copy_out(void *dst, const void *src, size_t bytes, int is_device, cudaStream_t st) {
+  CK(cudaMemcpyAsync(dst, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+
+extern "C" {
+
+stdd_status stdd_create(stdd_ctx **out, int device, void *cuda_stream) {
+  if (!out) return STDD_EINVAL;
+  *out = nullptr;
+  stdd_ctx *c = new (std::nothrow) stdd_ctx();
+  if (!c) return STDD_ENOMEM;
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete c;
+    return STDD_ECUDA;
+  }
+  if (cuda_stream) {
+    c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      (void)cudaGetLastError();
+      delete c;
+      return STDD_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  *out = c;
+  return STDD_OK;
+}
+
+void stdd_destroy(stdd_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+stdd_status stdd_set_grid(stdd_ctx *c, int nx, int ny, double dx, double dy) {
+  return guarded(c, [&] {
+    if (nx < 1 || ny < 1 || !(dx > 0) || !(dy > 0)) throw ArgError("bad grid");
+    if ((int64_t)nx * ny > (int64_t)1 << 31) throw ArgError("grid too large");
+    c->nx = nx;
+    c->ny = ny;
+    c->dx = dx;
+    c->dy = dy;
+    c->have_eps = false;
+    c->nrhs = 0;
+    c->nsub = 0;
+    c->shapes.clear();
+    c->invalidate_operator();
+  });
+}
+
+stdd_status stdd_set_permittivity(stdd_ctx *c, const double *eps, int is_device) {
+  return guarded(c, [&] {
+    if (c->nx <= 0) throw StateError("grid not set");
+    if (!eps) throw ArgError("null permittivity");
+    c->d_eps.alloc(c->N() * sizeof(double));
+    copy_in(c->d_eps.p, eps, c->N() * sizeof(double), is_device, c->stream);
+    CK(cudaStreamSynchronize(c->stream));
+    c->have_eps = true;
+    c->invalidate_factors();
+  });
+}
+
+stdd_status stdd_set_frequency(stdd_ctx *c, double wavelength) {
+  return guarded(c, [&] {
+    if (!(wavelength > 0) || !std::isfinite(wavelength)) throw ArgError("bad wavelength");
+    c->wavelength = wavelength;
+    c->invalidate_operator();
+  });
+}
+
+stdd_status stdd_set_pml(stdd_ctx *c, const int npml[4], int order_m, double R0) {
+  return guarded(c, [&] {
+    if (c->nx <= 0) throw StateError("grid not set");
+    if (!npml || order_m < 0 || !(R0 > 0 && R0 < 1)) throw ArgError("bad PML parameters");
+    for (int s = 0; s < 4; ++s)
+      if (npml[s] < 0) throw ArgError("negative PML width");
+    if (npml[0] + npml[1] > c->nx || npml[2] + npml[3] > c->ny) throw ArgError("PML wider than the grid");
+    std::memcpy(c->npml, npml, sizeof(c->npml));
+    c->pml_m = order_m;
+    c->pml_R = R0;
+    c->have_pml = true;
+    c->invalidate_operator();
+  });
+}
+
+stdd_status stdd_set_decomposition(stdd_ctx *c, int nsub, const int *x_cuts, int overlap, int ipml) {
+  return guarded(c, [&] {
+    if (c->nx <= 0) throw StateError("grid not set");
+    if (nsub < 1 || nsub > c->nx || overlap < 0 || ipml < 0) throw ArgError("bad decomposition");
+    std::vector<int> cuts;
+    if (x_cuts) {
+      cuts.assign(x_cuts, x_cuts + nsub + 1);
+      if (cuts.front() != 0 || cuts.back() != c->nx) throw ArgError("cuts must run from 0 to nx");
+      for (int k = 0; k < nsub; ++k)
+        if (cuts[k + 1] <= cuts[k]) throw ArgError("cuts must increase");
+    }
+    const int old_n = c->nsub, old_o = c->overlap, old_p = c->ipml;
+    const auto old_c = c->cuts;
+    c->nsub = nsub;
+    c->cuts = cuts;
+    c->overlap = overlap;
+    c->ipml = ipml;
+    try {
+      c->build_strips();
+    } catch (...) {
+      c->nsub = old_n;
+      c->cuts = old_c;
+      c->overlap = old_o;
+      c->ipml = old_p;
+      throw;
+    }
+    c->invalidate_factors();
+  });
+}
+
+stdd_status stdd_set_precision(stdd_ctx *c, int mode) {
+  return guarded(c, [&] {
+    if (mode != STDD_PREC_FP64 && mode != STDD_PREC_C64) throw ArgError("unknown precision mode");
+    if (mode != c->prec) {
+      c->prec = mode;
+      c->solve_nrhs_cap = 0;
+      c->invalidate_factors();
+    }
+  });
+}
+
+stdd_status stdd_set_sources(stdd_ctx *c, int nrhs, const double *b, int is_device) {
+  return guarded(c, [&] {
+    if (c->nx <= 0) throw StateError("grid not set");
+    if (nrhs < 1 || !b) throw ArgError("bad sources");
+    const size_t bytes = (size_t)nrhs * c->N() * sizeof(double2);
+    c->d_b.alloc(bytes);
+    copy_in(c->d_b.p, b, bytes, is_device, c->stream);
+    CK(cudaStreamSynchronize(c->stream));
+    c->nrhs = nrhs;
+  });
+}
+
+stdd_status stdd_factor(stdd_ctx *c) {
+  return guarded(c, [&] { c->factor(); });
+}
+
+stdd_status stdd_solve(stdd_ctx *c, const stdd_solve_opts *o, double *x_out, int is_device) {
+  bool noconv = false;
+  stdd_status st = guarded(c, [&] {
+    if (!o || !x_out) throw ArgError("null argument");
+    if (!c->factored) throw StateError("stdd_factor has not run since the last configuration change");
+    if (c->nrhs < 1) throw StateError("no sources set");
+    if (o->restart < 1 || o->restart > 500 || o->maxit < 0 || !(o->rtol >= 0)) throw ArgError("bad solve options");
+    if (o->x0_mode == STDD_X0_USER && !o->x0) throw ArgError("x0 missing");
+    const int64_t n = c->N();
+    c->history.assign(c->nrhs, {});
+    c->ensure_krylov(o->paper_richardson ? 1 : o->restart);
+    for (int q = 0; q < c->nrhs; ++q) {
+      double2 *x = c->d_x.as<double2>();
+      if (o->x0_mode == STDD_X0_USER)
+        copy_in(x, o->x0 + (size_t)q * n * 2, n * sizeof(double2), o->x0_is_device, c->stream);
+      else
+        CK(cudaMemsetAsync(x, 0, n * sizeof(double2), c->stream));
+      if (o->paper_richardson) c->richardson(q, *o, x);
+      else c->gmres(q, *o, x);
+      if (!(c->last_res <= o->rtol) && !o->paper_richardson) noconv = true;
+      copy_out(x_out + (size_t)q * n * 2, x, n * sizeof(double2), is_device, c->stream);
+    }
+  });
+  if (st == STDD_OK && noconv) {
+    c->err = "maxit reached before rtol";
+    return STDD_ENOCONV;
+  }
+  return st;
+}
+
+stdd_status stdd_residual_history(stdd_ctx *c, int rhs, double *out, int cap, int *n_out) {
+  return guarded(c, [&] {
+    if (rhs < 0 || rhs >= (int)c->history.size()) throw ArgError("no history for that right-hand side");
+    const auto &h = c->history[rhs];
+    if (n_out) *n_out = (int)h.size();
+    if (out)
+      for (int i = 0; i < cap && i < (int)h.size(); ++i) out[i] = h[i];
+  });
+}
+
+const char *stdd_last_error(const stdd_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+stdd_status stdd_apply_operator(stdd_ctx *c, const double *x, double *y, int is_device) {
+  return guarded(c, [&] {
+    if (!x || !y) throw ArgError("null vector");
+    c->require_operator();
+    const int64_t n = c->N();
+    c->d_w.alloc(n * sizeof(double2));
+    c->d_r.alloc(n * sizeof(double2));
+    copy_in(c->d_w.p, x, n * sizeof(double2), is_device, c->stream);
+    stdd::launch_stencil(c->grid(), c->d_w.as<double2>(), c->d_r.as<double2>(), c->stream);
+    CK(cudaGetLastError());
+    copy_out(y, c->d_r.p, n * sizeof(double2), is_device, c->stream);
+  });
+}
+
+stdd_status stdd_apply_preconditioner(stdd_ctx *c, const double *v, double *z, int is_device) {
+  return guarded(c, [&] {
+    if (!v || !z) throw ArgError("null vector");
+    if (!c->factored) throw StateError("not factored");
+    const int64_t n = c->N();
+    c->d_w.alloc(n * sizeof(double2));
+    c->d_r.alloc(n * sizeof(double2));
+    copy_in(c->d_w.p, v, n * sizeof(double2), is_device, c->stream);
+    c->apply_minv(c->d_w.as<double2>(), c->d_r.as<double2>());
+    copy_out(z, c->d_r.p, n * sizeof(double2), is_device, c->stream);
+  });
+}
+
+stdd_status stdd_local_solve(stdd_ctx *c, int k, const double *t, double *z, int is_device) {
+  return guarded(c, [&] {
+    if (!t || !z) throw ArgError("null vector");
+    if (!c->factored) throw StateError("not factored");
+    if (k < 0 || k >= c->nsub) throw ArgError("bad strip");
+    const int64_t nl = (int64_t)c->strips[k].W() * c->ny;
+    int64_t off = 0;
+    for (int kk = 0; kk < k; ++kk) off += (int64_t)c->strips[kk].W() * c->ny;
+    c->ensure_solve_buffers(1);
+    c->d_w.alloc(nl * sizeof(double2));
+    copy_in(c->d_w.p, t, nl * sizeof(double2), is_device, c->stream);
+    const size_t E = c->elem();
+    CK(cudaMemsetAsync(c->d_tloc.p, 0, c->nloc * E, c->stream));
+    char *base = c->d_tloc.as<char>() + off * E;
+    if (c->prec == STDD_PREC_FP64) {
+      stdd::launch_to_local<double>(c->d_w.as<double2>(), base, nl, c->stream);
+      c->solve_levels<double>(1);
+      stdd::launch_from_local<double>(base, c->d_w.as<double2>(), nl, c->stream);
+    } else {
+      stdd::launch_to_local<float>(c->d_w.as<double2>(), base, nl, c->stream);
+      c->solve_levels<float>(1);
+      stdd::launch_from_local<float>(base, c->d_w.as<double2>(), nl, c->stream);
+    }
+    CK(cudaGetLastError());
+    copy_out(z, c->d_w.p, nl * sizeof(double2), is_device, c->stream);
+  });
+}
+
+stdd_status stdd_strip_info(const stdd_ctx *cc, int k, int *c0, int *c1, int *x0, int *x1) {
+  stdd_ctx *c = const_cast<stdd_ctx *>(cc);
+  return guarded(c, [&] {
+    if (c->strips.empty()) c->build_strips();
+    if (k < 0 || k >= (int)c->strips.size()) throw ArgError("bad strip");
+    const StripHost &s = c->strips[k];
+    if (c0) *c0 = s.c0;
+    if (c1) *c1 = s.c1;
+    if (x0) *x0 = s.x0;
+    if (x1) *x1 = s.x1;
+  });
+}
+
+stdd_status stdd_get_stats(stdd_ctx *c, stdd_stats *o) {
+  return guarded(c, [&] {
+    if (!o) throw ArgError("null stats");
+    std::memset(o, 0, sizeof(*o));
+    o->nfronts = c->nfronts;
+    o->depth = c->depth;
+    o->max_pivots = c->max_p;
+    o->max_border = c->max_b;
+    o->factor_entries = c->factor_entries;
+    o->factor_flops = 8.0 * c->factor_cflops;
+    o->solve_flops = 8.0 * c->solve_cflops;
+    o->local_dofs = c->nloc;
+    o->device_bytes = c->device_bytes();
+    o->iterations = c->last_its;
+    o->final_residual = c->last_res;
+    o->min_pivot = c->min_pivot;
+  });
+}
+
+stdd_status stdd_nd_analyze(int W, int H, int leaf_max, int *nfronts, long long *nnodes, int *p, int *b,
+                            int *parent, int *level, int *nodes) {
+  try {
+    Shape S;
+    stdd::nd_analyze(W, H, leaf_max, S);
+    if (nfronts) *nfronts = (int)S.fronts.size();
+    if (nnodes) *nnodes = (long long)S.nodes.size();
+    if (nodes) {
+      for (size_t f = 0; f < S.fronts.size(); ++f) {
+        if (p) p[f] = S.fronts[f].p;
+        if (b) b[f] = S.fronts[f].b;
+        if (parent) parent[f] = S.fronts[f].parent;
+        if (level) level[f] = S.fronts[f].level;
+      }
+      std::memcpy(nodes, S.nodes.data(), S.nodes.size() * sizeof(int));
+    }
+    return STDD_OK;
+  } catch (const std::invalid_argument &) {
+    return STDD_EINVAL;
+  } catch (const std::bad_alloc &) {
+    return STDD_ENOMEM;
+  } catch (...) {
+    return STDD_EINVAL;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Shared device-side definitions: complex arithmetic on double2 / float2,
+// the device descriptors of strips and fronts, and launch helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stdd {
+
+// ---------------------------------------------------------------- complex
+template <typename R> struct CT;
+template <> struct CT<double> { using T = double2; };
+template <> struct CT<float> { using T = float2; };
+
+__host__ __device__ __forceinline__ double2 cmk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ float2 cmk(float r, float i) { return make_float2(r, i); }
+
+template <typename C> __host__ __device__ __forceinline__ C czero() { C z; z.x = 0; z.y = 0; return z; }
+
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+// acc + a*b
+template <typename C> __host__ __device__ __forceinline__ C cfma(C a, C b, C acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+// acc - a*b
+template <typename C> __host__ __device__ __forceinline__ C cfms(C a, C b, C acc) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
+// conj(a)*b
+template <typename C> __host__ __device__ __forceinline__ C cconjmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x + a.y * b.y;
+  r.y = a.x * b.y - a.y * b.x;
+  return r;
+}
+template <typename C> __host__ __device__ __forceinline__ auto cabs2(C a) -> decltype(a.x) {
+  return a.x * a.x + a.y * a.y;
+}
+// 1/a by Smith's algorithm (R. L. Smith, CACM 5(8), 1962): scale by the
+// larger component to avoid overflow and underflow.
+template <typename C> __host__ __device__ __forceinline__ C crecip(C a) {
+  C r;
+  if (fabs(a.x) >= fabs(a.y)) {
+    auto t = a.y / a.x;
+    auto d = a.x + a.y * t;
+    r.x = 1 / d;
+    r.y = -t / d;
+  } else {
+    auto t = a.x / a.y;
+    auto d = a.x * t + a.y;
+    r.x = t / d;
+    r.y = -1 / d;
+  }
+  return r;
+}
+
+__device__ __forceinline__ double2 to_c(double2 a, double2) { return a; }
+__device__ __forceinline__ float2 to_c(double2 a, float2) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 to_d(double2 a) { return a; }
+__device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
+
+template <typename C> __device__ __forceinline__ C shfl(C v, int src) {
+  v.x = __shfl_sync(0xffffffffu, v.x, src);
+  v.y = __shfl_sync(0xffffffffu, v.y, src);
+  return v;
+}
+
+// ---------------------------------------------------------- descriptors
+// One strip (subdomain) of the decomposition.
+struct StripDev {
+  int x0, x1;          // local box columns [x0, x1) of the global grid
+  int c0, c1;          // owned columns [c0, c1)
+  int64_t vec_off;     // offset of the strip's local field in the local buffer
+  int64_t coef_off;    // offset of the strip's x coefficients (W entries)
+  int64_t fac_off;     // offset of the strip's factor block (complex entries)
+};
+
+// One front instance (a symbolic front of some strip shape in some strip).
+struct FrontDev {
+  int p, b;            // pivots, border
+  int strip;
+  int child[2];        // front instance ids (same strip), -1 if none
+  int64_t node_off;    // into the shape node array (local node ids x*H + y)
+  int64_t cmap_off[2]; // child's ring index -> this front's index
+  int64_t inv_off[2];  // this front's index -> child's ring index or -1
+  int64_t fac_off;     // absolute offset of [F11 F12] (p x n, col-major, ld p) then F21 (b x p, ld b)
+  int64_t s_off;       // offset of F22 (b x b, col-major) in the level-parity workspace
+  int64_t u_off;       // update vector (b x nrhs) at u_off * nrhs in the solve parity buffer
+};
+
+}  // namespace stdd

@@ -1,0 +1,89 @@
+// Kernel launchers shared by the C-ABI layer (api.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace stdd {
+
+constexpr int MF_NB = 32;             // pivot block of the blocked partial LU
+constexpr int MF_PANEL_THREADS = 128; // rows / columns per panel tile
+
+// Everything a multifrontal kernel needs (device pointers).
+struct MfArgs {
+  const FrontDev *fronts;
+  const StripDev *strips;
+  const int *nodes, *cmap, *inv;
+  const double2 *cxm, *cxp;   // per-strip x couplings, indexed coef_off + local column
+  const double2 *cym, *cyp;   // y couplings, indexed by row
+  const double *eps;          // global node permittivity
+  double k0sq;
+  int H;                      // ny
+  void *fac;                  // factor storage (complex R)
+  void *ws_cur;               // F22 of this level
+  const void *ws_child;       // F22 of the level below
+  void *tloc;                 // local fields, [nrhs][ldt]
+  void *ub_cur;               // forward update vectors of this level
+  const void *ub_child;       // and of the level below
+  int *flag;                  // bit 0: zero / non-finite pivot
+  double *min_pivot;          // min |pivot| (atomicMin on the bit pattern)
+};
+
+struct LevelInfo {
+  int f0, nf;                 // fronts [f0, f0 + nf) of the level
+  int max_p, max_b, max_n;
+};
+
+template <typename R> cudaError_t mf_setup_attributes();
+template <typename R> void mf_factor_level(const MfArgs &a, const LevelInfo &L, cudaStream_t st);
+template <typename R>
+void mf_forward_level(const MfArgs &a, const LevelInfo &L, int nrhs, int64_t ldt, cudaStream_t st);
+template <typename R>
+void mf_backward_level(const MfArgs &a, const LevelInfo &L, int nrhs, int64_t ldt, cudaStream_t st);
+
+// ---- FDFD / DDM vector kernels (kernels_fdfd.cu)
+struct GridDev {
+  int nx, ny;
+  double k0sq;
+  const double *eps;
+  const double2 *cxm, *cxp;   // global x couplings (nx)
+  const double2 *cym, *cyp;   // y couplings (ny)
+};
+// y = A x (global stretched 5-point operator), nrhs vectors of nx*ny
+void launch_stencil(const GridDev &g, const double2 *x, double2 *y, cudaStream_t st);
+// r = b - A x
+void launch_residual(const GridDev &g, const double2 *b, const double2 *x, double2 *r, cudaStream_t st);
+// local[k] = R_k^I v (owned columns of v, zero elsewhere), all strips, R = double or float
+template <typename R>
+void launch_restrict(const StripDev *strips_dev, int nsub, int64_t nloc, int ny, const int *col_strip,
+                     const double2 *v, void *tloc, cudaStream_t st);
+// z = sum_k E_k local[k] (gather form: <= 3 strips per column, fixed order)
+template <typename R>
+void launch_synthesize(const StripDev *strips_dev, int nsub, int nx, int ny, const int *col_strip,
+                       const void *tloc, double2 *z, cudaStream_t st);
+// out[2k] = ||e_k^F||^2, out[2k+1] = ||e_k||^2 of every strip's local field
+template <typename R>
+void launch_strip_norms(const StripDev *strips_dev, int nsub, int ny, const void *tloc, double *out,
+                        cudaStream_t st);
+// local strip k only: tloc_k = t (converted), and back
+template <typename R> void launch_to_local(const double2 *t, void *tloc, int64_t n, cudaStream_t st);
+template <typename R> void launch_from_local(const void *tloc, double2 *z, int64_t n, cudaStream_t st);
+
+// ---- Krylov kernels (kernels_krylov.cu), FP64 complex
+// partial[blk][i] = sum_g conj(V_i[g]) w[g], i < m; then h[i] = sum_blk partial
+void launch_mdot(const double2 *V, int64_t ldv, int m, const double2 *w, int64_t n, double2 *partial,
+                 double2 *h, cudaStream_t st);
+// w -= sum_i h[i] V_i, and nrm2 = ||w||^2 (partials then a fixed-order sum)
+void launch_maxpy_norm(const double2 *V, int64_t ldv, int m, const double2 *h, double2 *w, int64_t n,
+                       double *partial, double *nrm2, cudaStream_t st);
+// x += sum_i y[i] Z_i
+void launch_maxpy(const double2 *Z, int64_t ldz, int m, const double2 *y, double2 *x, int64_t n,
+                  cudaStream_t st);
+// nrm2 = ||x||^2
+void launch_norm2(const double2 *x, int64_t n, double *partial, double *nrm2, cudaStream_t st);
+// y = alpha * x (alpha real, read from device)
+void launch_scale(const double2 *x, const double *inv_norm2, double2 *y, int64_t n, cudaStream_t st);
+int krylov_partial_blocks();
+
+}  // namespace stdd
