@@ -99,12 +99,56 @@ __global__ void __launch_bounds__(256) mf_assemble(MfArgs a, int f0) {
   }
 }
 
+// ------------------------------------------------------ diagonal block k
+// One CTA per front: unblocked LU (no pivoting) of the nbk x nbk block at
+// (k, k), in shared memory, written back in place; zero or non-finite pivots
+// set the flag, |pivot| feeds the running minimum.
+template <typename R>
+__global__ void __launch_bounds__(MF_PANEL_THREADS) mf_diag(MfArgs a, int f0, int k) {
+  using C = typename CT<R>::T;
+  constexpr int NB = MF_NB;
+  __shared__ C D[NB][NB + 1];
+  const FrontDev f = a.fronts[f0 + blockIdx.x];
+  const int p = f.p;
+  if (k >= p) return;
+  const int nbk = min(NB, p - k);
+  C *fac = reinterpret_cast<C *>(a.fac);
+  const int64_t fo = f.fac_off;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < nbk * nbk; idx += blockDim.x) {
+    const int i = idx % nbk, j = idx / nbk;
+    D[i][j] = fac[fo + (int64_t)(k + j) * p + k + i];
+  }
+  __syncthreads();
+  for (int j = 0; j < nbk; ++j) {
+    const C inv = crecip(D[j][j]);
+    for (int i = j + 1 + tid; i < nbk; i += blockDim.x) D[i][j] = cmul(D[i][j], inv);
+    __syncthreads();
+    const int m = nbk - j - 1;
+    for (int idx = tid; idx < m * m; idx += blockDim.x) {
+      const int i = j + 1 + idx % m, l = j + 1 + idx / m;
+      D[i][l] = cfms(D[i][j], D[j][l], D[i][l]);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < nbk * nbk; idx += blockDim.x) {
+    const int i = idx % nbk, j = idx / nbk;
+    fac[fo + (int64_t)(k + j) * p + k + i] = D[i][j];
+  }
+  for (int j = tid; j < nbk; j += blockDim.x) {
+    const C d = D[j][j];
+    const double ad = sqrt((double)cabs2(d));
+    if (!(ad > 0.0) || !cfinite(d)) atomicOr(a.flag, 1);
+    else atomicMin(reinterpret_cast<unsigned long long *>(a.min_pivot),
+                   (unsigned long long)__double_as_longlong(ad));
+  }
+}
+
 // ---------------------------------------------------------- panel step k
-// blockIdx.y = 0 .. ntr-1: row tiles of L (rows k+nbk.. n), solves X U_D = F;
-// blockIdx.y = ntr .. 2 ntr-1: column tiles of U (cols k+nbk .. n), solves
-// L_D Y = F.  Every CTA factors the nbk x nbk diagonal block in shared memory
-// (a few thousand multiply-adds) so that no grid-wide dependency is needed;
-// CTA 0 writes it back.
+// After mf_diag: blockIdx.y = 0 .. ntr-1 are row tiles of L (rows k+nbk ..
+// n) solving X U_D = F; blockIdx.y = ntr .. 2 ntr-1 are column tiles of U
+// (cols k+nbk .. n) solving L_D Y = F.  The factored diagonal block is only
+// read here, so the tiles need no ordering among themselves.
 template <typename R>
 __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_panel(MfArgs a, int f0, int k) {
   using C = typename CT<R>::T;
@@ -122,7 +166,7 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_panel(MfArgs a, int f0, i
   const int rem = n - k - nbk;
   const int ntr = (rem + TILE - 1) / TILE;
   const int t = blockIdx.y;
-  if (t > 0 && t >= 2 * ntr) return;
+  if (t >= 2 * ntr) return;
   C *fac = reinterpret_cast<C *>(a.fac);
   const int64_t fo = f.fac_off;
   const int tid = threadIdx.x;
@@ -132,33 +176,8 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_panel(MfArgs a, int f0, i
     D[i][j] = fac[fo + (int64_t)(k + j) * p + k + i];
   }
   __syncthreads();
-  for (int j = 0; j < nbk; ++j) {
-    const C inv = crecip(D[j][j]);
-    for (int i = j + 1 + tid; i < nbk; i += blockDim.x) D[i][j] = cmul(D[i][j], inv);
-    __syncthreads();
-    const int m = nbk - j - 1;
-    for (int idx = tid; idx < m * m; idx += blockDim.x) {
-      const int i = j + 1 + idx % m, l = j + 1 + idx / m;
-      D[i][l] = cfms(D[i][j], D[j][l], D[i][l]);
-    }
-    __syncthreads();
-  }
   for (int j = tid; j < nbk; j += blockDim.x) dinv[j] = crecip(D[j][j]);
-  if (t == 0) {
-    for (int idx = tid; idx < nbk * nbk; idx += blockDim.x) {
-      const int i = idx % nbk, j = idx / nbk;
-      fac[fo + (int64_t)(k + j) * p + k + i] = D[i][j];
-    }
-    for (int j = tid; j < nbk; j += blockDim.x) {
-      const C d = D[j][j];
-      const double ad = sqrt((double)cabs2(d));
-      if (!(ad > 0.0) || !cfinite(d)) atomicOr(a.flag, 1);
-      else atomicMin(reinterpret_cast<unsigned long long *>(a.min_pivot),
-                     (unsigned long long)__double_as_longlong(ad));
-    }
-  }
   __syncthreads();
-  if (rem <= 0) return;
 
   if (t < ntr) {
     // rows r = k+nbk+t*TILE+tid of column block [k, k+nbk): X = F U_D^-1
@@ -551,6 +570,7 @@ void mf_factor_level(const MfArgs &a, const LevelInfo &L, cudaStream_t st) {
   for (int k = 0; k < L.max_p; k += MF_NB) {
     const int rem = L.max_n - k - 1;
     const int ntr = std::max(1, (rem + MF_PANEL_THREADS - 1) / MF_PANEL_THREADS);
+    mf_diag<R><<<L.nf, MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
     mf_panel<R><<<dim3(L.nf, 2 * ntr), MF_PANEL_THREADS, panel_smem<R>(), st>>>(a, L.f0, k);
     const int nt = std::max(1, (rem + 63) / 64);
     mf_update<R><<<dim3(L.nf, nt * nt), 256, gemm_smem<R>(), st>>>(a, L.f0, k);
