@@ -1,0 +1,443 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 overlapping source-transfer DDM solver.
+
+One step = the whole hot path on one synthetic problem whose inputs are
+already in HBM: numeric multifrontal factorization of every strip, then
+flexible GMRES(50) preconditioned by the batched source-transfer sweep until
+the relative residual is <= 1e-8.  Default workload: the 4096 x 1024
+metalens-like strip at lambda/24 (30-cell PML, 16 strips, 12-cell overlap),
+complex128 factors (the plain-FP64 configuration); the complex64-factor
+variant of the same problem is measured beside it.
+
+Printed: one JSON line (rank 0).  value = MDoF/s = nx*ny*nrhs / (seconds per
+step) / 1e6, summed over ranks (replicas, weak scaling).
+
+--impl reference times the CPU oracle (plain SuperLU strip solves + textbook
+FGMRES) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solve time to 1e-8 residual & MDoF/s: mixed/learned vs plain FP64, one GB300"
+RTOL = 1e-8
+RESTART = 50
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor and tensor), NVIDIA's figure
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "c64"])
+    ap.add_argument("--workload", default="metalens", choices=["metalens", "cylinder"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the other-precision run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    import workloads as W
+    return W.metalens() if name == "metalens" else W.cylinder()
+
+
+def workload_desc(w):
+    return (f"{w.name} {w.nx}x{w.ny} grid ({w.n} DoF) at lambda/{round(w.wavelength / w.dx)}, "
+            f"{w.npml[0]}-cell SC-PML m={w.pml_order} R={w.pml_R:g}, {w.nsub} strips, overlap "
+            f"{w.overlap}, interface PML {w.interface_pml}, {w.nrhs} RHS")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ peaks
+def measured_peaks():
+    peaks = {"hbm_gbs": 6800.0, "source_hbm": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        peaks["hbm_gbs"] = float(mp["hbm_gbs"])
+        peaks["source_hbm"] = "measured (MEASURED_PEAKS.json, copy)"
+    except (OSError, KeyError, ValueError):
+        pass
+    return peaks
+
+
+def gemm_peak(torch, dtype, n, reps=3):
+    """Dense GEMM throughput through cuBLAS (TFLOP/s), best of reps."""
+    a = torch.randn(n, n, dtype=dtype, device="cuda")
+    b = torch.randn(n, n, dtype=dtype, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        torch.matmul(a, b)
+        e.record()
+        e.synchronize()
+        best = max(best, 2.0 * n ** 3 / (s.elapsed_time(e) * 1e-3) / 1e12)
+    del a, b
+    return best
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(w, its, target_s=20.0):
+    """Time the oracle on a bounded sample of workload w: factor two strips
+    (an end strip and an interior strip) with SuperLU and apply each local
+    solve a few times; scale to all strips and to `its` FGMRES iterations,
+    adding the measured CPU cost of one global matvec + Gram-Schmidt step."""
+    import numpy as np
+
+    from oracle.fdfd import Problem
+    from oracle.stddm import DDM
+    t0 = time.perf_counter()
+    P = Problem.from_workload(w)
+    D = DDM.from_workload(w, P)
+    ks = sorted({0, min(1, D.nsub - 1)})
+    t_fac, t_sol, nsol = {}, {}, 3
+    for k in ks:
+        t = time.perf_counter()
+        D.factor(k)
+        t_fac[k] = time.perf_counter() - t
+        v = np.ones(D.strips[k].width * P.ny, complex)
+        t = time.perf_counter()
+        for _ in range(nsol):
+            D.local_solve(k, v)
+        t_sol[k] = (time.perf_counter() - t) / nsol
+    A = P.A
+    x = np.ones(P.n, complex)
+    t = time.perf_counter()
+    for _ in range(3):
+        y = A @ x
+        float(np.vdot(y, x).real)
+    t_mv = (time.perf_counter() - t) / 3
+    sampled = time.perf_counter() - t0
+    end = ks[0]
+    mid = ks[-1]
+    fac_all = t_fac[end] * 2 + t_fac[mid] * max(0, D.nsub - 2) if D.nsub > 1 else t_fac[end]
+    sol_all = t_sol[end] * 2 + t_sol[mid] * max(0, D.nsub - 2) if D.nsub > 1 else t_sol[end]
+    # per FGMRES iteration: one sweep of local solves, one matvec, ~RESTART/2
+    # vectors of Gram-Schmidt (one dot + one axpy each, ~ one matvec of work)
+    per_it = sol_all + t_mv * (1 + RESTART / 2)
+    total = fac_all + its * per_it
+    return dict(total_s=total, factor_s=fac_all, per_iteration_s=per_it, sampled_s=sampled,
+                sample=(f"SuperLU factor of strips {ks} of {D.nsub} + {nsol} local solves each + 3 "
+                        f"matvecs, scaled to {D.nsub} strips and {its} FGMRES iterations"))
+
+
+# ----------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2509_20801_gb300 as S
+    from paper_2509_20801_gb300 import binding as B
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = make_workload(args.workload)
+    N = w.n * w.nrhs
+    peaks = measured_peaks()
+    fp64_tf = gemm_peak(torch, torch.float64, 4096)
+    fp32_tf = gemm_peak(torch, torch.float32, 8192)
+    stream = torch.cuda.Stream(device=dev)
+    eps_d = torch.from_numpy(w.eps_node).to(dev)
+    b_d = torch.from_numpy(w.b).to(dev)
+    x_d = torch.empty_like(b_d)
+    prec = S.STDD_PREC_FP64 if args.precision == "fp64" else S.STDD_PREC_C64
+
+    def make_solver(p):
+        return S.Solver.from_workload(w, eps=eps_d, precision=p, device=local_rank,
+                                      stream=stream.cuda_stream)
+
+    def step(sv):
+        sv.factor()
+        sv.solve(x_d, restart=RESTART, rtol=RTOL, maxit=2000)
+
+    def timed(p, warm, steps, profile):
+        sv = make_solver(p)
+        sv.set_sources(b_d)
+        for _ in range(warm):
+            step(sv)
+        torch.cuda.synchronize()
+        barrier()
+        B.stdd_get_profile(sv.ctx, reset=True)
+        B.stdd_set_profiling(sv.ctx, profile)
+        l0 = B.stdd_get_profile(sv.ctx, reset=True)["launches"]
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            step(sv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ck = clocks.stop()
+        ms = e0.elapsed_time(e1) / steps
+        prof = B.stdd_get_profile(sv.ctx, reset=True)
+        launches = prof["launches"] - l0
+        st = sv.stats()
+        hist = sv.history(0)
+        return sv, ms, prof, launches, st, hist, ck
+
+    sv, ms, prof, launches, st, hist, ck = timed(prec, args.warmup, args.steps, True)
+    its = len(hist) - 1
+    x_main = x_d.clone()
+    r_rel = B.stdd_residual(sv.ctx, x_d[0].reshape(-1).contiguous(), b_d[0].reshape(-1).contiguous(),
+                            torch.empty(w.n, dtype=torch.complex128, device=dev))
+    ms_t = torch.tensor([ms], device=dev)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+
+    # phase rooflines (algorithmic bytes / flops per phase call)
+    steps = args.steps
+    E = st["factor_entries"]
+    elem = 16 if prec == S.STDD_PREC_FP64 else 8
+    phases = {}
+    if prof["minv_calls"]:
+        t = prof["minv_ms"] / prof["minv_calls"] * 1e-3
+        phases["substitution_sweep"] = dict(
+            ms_per_call=t * 1e3, calls_per_step=prof["minv_calls"] / steps,
+            bytes_per_call=E * elem, flops_per_call=st["solve_flops"],
+            gbs=E * elem / t / 1e9, tflops=st["solve_flops"] / t / 1e12)
+    if prof["factor_ms"]:
+        t = prof["factor_ms"] / steps * 1e-3
+        phases["factorization"] = dict(ms_per_call=t * 1e3, calls_per_step=1,
+                                       flops_per_call=st["factor_flops"],
+                                       tflops=st["factor_flops"] / t / 1e12)
+    if prof["matvec_calls"]:
+        t = prof["matvec_ms"] / prof["matvec_calls"] * 1e-3
+        phases["stencil_matvec"] = dict(ms_per_call=t * 1e3, calls_per_step=prof["matvec_calls"] / steps,
+                                        bytes_per_call=40 * w.n, gbs=40 * w.n / t / 1e9)
+    if prof["ortho_calls"]:
+        # CGS2 at basis size j+1: 2 x (dot over j+1 vectors + axpy over j+1
+        # vectors) = 4 (j+1) N complex multiply-adds, reading 4 (j+1) N + 4 N
+        # complex128 values and writing 2 N
+        calls = prof["ortho_calls"]
+        js = [j % RESTART for j in range(its)] * steps
+        fl = sum(8 * 4 * (j + 1) * w.n for j in js)
+        by = sum(16 * ((4 * (j + 1) + 6) * w.n) for j in js)
+        t = prof["ortho_ms"] * 1e-3
+        phases["gram_schmidt"] = dict(ms_per_call=t / calls * 1e3, calls_per_step=calls / steps,
+                                      gbs=by / t / 1e9, tflops=fl / t / 1e12)
+    dom = max(phases, key=lambda k: phases[k]["ms_per_call"] * phases[k]["calls_per_step"])
+    d = phases[dom]
+    if dom == "substitution_sweep" and prec == S.STDD_PREC_C64:
+        roof = dict(bound="hbm", achieved=d["gbs"], peak=peaks["hbm_gbs"], unit="GB/s",
+                    peak_source=peaks["source_hbm"])
+    elif dom == "stencil_matvec":
+        roof = dict(bound="hbm", achieved=d["gbs"], peak=peaks["hbm_gbs"], unit="GB/s",
+                    peak_source=peaks["source_hbm"])
+    else:
+        alu64 = prec == S.STDD_PREC_FP64 or dom == "gram_schmidt"
+        pk = fp64_tf if alu64 else fp32_tf
+        roof = dict(bound="alu", achieved=d["tflops"], peak=pk, unit="TFLOP/s",
+                    peak_source=("measured cuBLAS DGEMM" if alu64 else "measured cuBLAS SGEMM"))
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["traffic"] = None
+
+    out = {
+        "metric": METRIC,
+        "value": N / (ms_max * 1e-3) / 1e6 * world,
+        "unit": "MDoF/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c128" if prec == S.STDD_PREC_FP64 else "c64-factors+c128-krylov",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(w), "precision": args.precision, "rtol": RTOL,
+                   "restart": RESTART, "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (factors %.1f GB, Krylov basis %.1f GB)"
+                         % (E * elem / 1e9, (2 * RESTART + 1) * w.n * 16 / 1e9)},
+        "iterations": its,
+        "final_residual": st["final_residual"],
+        "true_residual_check": r_rel,
+        "t_factor_ms": prof["factor_ms"] / args.steps,
+        "t_solve_ms": prof["solve_ms"] / args.steps,
+        "phases": phases,
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "peaks": {"hbm_gbs": peaks["hbm_gbs"], "fp64_tflops_dgemm": fp64_tf, "fp32_tflops_sgemm": fp32_tf,
+                  "fp64_nominal": FP64_NOMINAL_TFLOPS, "fp32_nominal": FP32_NOMINAL_TFLOPS},
+    }
+    sv.close()
+
+    if not args.no_compare:
+        other = S.STDD_PREC_C64 if prec == S.STDD_PREC_FP64 else S.STDD_PREC_FP64
+        sv2, ms2, prof2, _, st2, hist2, _ = timed(other, 1, 1, True)
+        diff = float(torch.linalg.vector_norm(x_d - x_main) / torch.linalg.vector_norm(x_main))
+        out["compare"] = {"precision": "c64" if other == S.STDD_PREC_C64 else "fp64",
+                          "ms_per_step": ms2, "value": N / (ms2 * 1e-3) / 1e6,
+                          "iterations": len(hist2) - 1, "final_residual": st2["final_residual"],
+                          "t_factor_ms": prof2["factor_ms"], "t_solve_ms": prof2["solve_ms"],
+                          "rel_diff_vs_main": diff}
+        sv2.close()
+
+    if not args.no_e2e:
+        # through the public API with host buffers: permittivity and sources
+        # copied in from pinned memory, the solution copied out, every step
+        eps_h = torch.from_numpy(w.eps_node).pin_memory()
+        b_h = torch.from_numpy(w.b).pin_memory()
+        x_h = torch.empty(w.b.shape, dtype=torch.complex128).pin_memory()
+        sv = make_solver(prec)
+        sv.set_sources(b_h)
+        S.stdd_set_permittivity(sv.ctx, eps_h)
+        sv.factor()
+        sv.solve(x_h, restart=RESTART, rtol=RTOL, maxit=2000)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            S.stdd_set_permittivity(sv.ctx, eps_h)
+            sv.factor()
+            S.stdd_set_sources(sv.ctx, w.nrhs, b_h)
+            sv.solve(x_h, restart=RESTART, rtol=RTOL, maxit=2000)
+        dt = (time.perf_counter() - t0) / args.steps
+        dt_t = torch.tensor([dt], device=dev)
+        if dist is not None:
+            dist.all_reduce(dt_t, op=dist.ReduceOp.MAX)
+        dt = float(dt_t.item())
+        out["e2e"] = {"value": N / dt / 1e6 * world, "unit": "MDoF/s", "ms_per_step": dt * 1e3,
+                      "h2d_bytes_per_step": int(w.eps_node.nbytes + w.b.nbytes),
+                      "d2h_bytes_per_step": int(w.b.nbytes)}
+        sv.close()
+
+    if rank == 0 and not args.no_cpu:
+        smp = oracle_sample(w, its)
+        out["cpu_baseline"] = {"value": N / smp["total_s"] / 1e6, "unit": "MDoF/s", "cores": 1,
+                               "kind": "oracle", "sample": smp["sample"],
+                               "est_total_s": smp["total_s"], "sampled_s": smp["sampled_s"]}
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------- reference
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    w = make_workload(args.workload)
+    N = w.n * w.nrhs
+    # FGMRES(50) iteration count of this preconditioner on these workloads
+    # (the oracle's own GMRES gives the same count: 34 on the metalens strip,
+    # 4 on the cylinder); the sample is scaled to it
+    its_assumed = 34 if w.name == "metalens" else 4
+    vals = []
+    smp = None
+    for _ in range(args.steps):
+        smp = oracle_sample(w, its_assumed)
+        vals.append(smp["total_s"])
+    t = statistics.median(vals)
+    v = N / t / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MDoF/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+           "config": {"workload": workload_desc(w), "precision": "fp64", "rtol": RTOL, "restart": RESTART},
+           "cpu_baseline": {"value": v, "unit": "MDoF/s", "cores": 1, "kind": "oracle",
+                            "sample": smp["sample"]},
+           "e2e": {"value": v, "unit": "MDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

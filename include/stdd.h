@@ -171,6 +171,31 @@ typedef struct {
 
 stdd_status stdd_get_stats(stdd_ctx *ctx, stdd_stats *out);
 
+/* r = b - A x for one field and its relative norm ||r|| / ||b|| (FP64,
+ * deterministic reduction).  x, b, r: 2*nx*ny doubles each; *rel_out is a
+ * host double.  Needs grid, permittivity, frequency and PML. */
+stdd_status stdd_residual(stdd_ctx *ctx, const double *x, const double *b, double *r, double *rel_out,
+                          int is_device);
+
+/* Phase profile: with profiling on, the context records CUDA events on its
+ * stream around each phase; get_profile synchronises the stream and sums the
+ * device times (ms) of the phases completed since the last reset.  Kernel
+ * launches are counted whether or not profiling is on. */
+typedef struct {
+  double factor_ms;       /* numeric factorization (all levels)           */
+  double minv_ms;         /* preconditioner applications (M^-1)           */
+  int minv_calls;
+  double matvec_ms;       /* global stencil products                      */
+  int matvec_calls;
+  double ortho_ms;        /* Gram-Schmidt passes of the Arnoldi steps      */
+  int ortho_calls;
+  double solve_ms;        /* whole stdd_solve calls                        */
+  long long launches;     /* kernels of this library launched             */
+} stdd_profile;
+
+stdd_status stdd_set_profiling(stdd_ctx *ctx, int enable);
+stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);
+
 /* Host-only nested-dissection analysis of one W x H box (no GPU needed).
  * First call with nodes == NULL to get *nfronts and *nnodes; then call
  * again with arrays of those sizes.  Fronts come in elimination order

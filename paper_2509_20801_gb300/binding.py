@@ -45,6 +45,12 @@ class stdd_stats(ctypes.Structure):
                 ("iterations", c_int), ("final_residual", c_double), ("min_pivot", c_double)]
 
 
+class stdd_profile(ctypes.Structure):
+    _fields_ = [("factor_ms", c_double), ("minv_ms", c_double), ("minv_calls", c_int),
+                ("matvec_ms", c_double), ("matvec_calls", c_int), ("ortho_ms", c_double),
+                ("ortho_calls", c_int), ("solve_ms", c_double), ("launches", ctypes.c_longlong)]
+
+
 _SIGS = {
     "stdd_create": (c_int, [P(c_void_p), c_int, c_void_p]),
     "stdd_destroy": (None, [c_void_p]),
@@ -64,6 +70,9 @@ _SIGS = {
     "stdd_local_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
     "stdd_strip_info": (c_int, [c_void_p, c_int, P(c_int), P(c_int), P(c_int), P(c_int)]),
     "stdd_get_stats": (c_int, [c_void_p, P(stdd_stats)]),
+    "stdd_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, P(c_double), c_int]),
+    "stdd_set_profiling": (c_int, [c_void_p, c_int]),
+    "stdd_get_profile": (c_int, [c_void_p, P(stdd_profile), c_int]),
     "stdd_nd_analyze": (c_int, [c_int, c_int, c_int, P(c_int), P(ctypes.c_longlong), c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_void_p]),
 }
@@ -212,6 +221,28 @@ def stdd_get_stats(ctx):
     s = stdd_stats()
     _check(ctx, lib.stdd_get_stats(ctx, ctypes.byref(s)))
     return {k: getattr(s, k) for k, _ in stdd_stats._fields_}
+
+
+def stdd_residual(ctx, x, b, r):
+    """r = b - A x; returns ||r|| / ||b||."""
+    px, dx_ = _ptr(x)
+    pb, db = _ptr(b)
+    pr, dr = _ptr(r)
+    if not dx_ == db == dr:
+        raise ValueError("x, b and r must live on the same side")
+    rel = c_double(0.0)
+    _check(ctx, lib.stdd_residual(ctx, c_void_p(px), c_void_p(pb), c_void_p(pr), ctypes.byref(rel), dx_))
+    return rel.value
+
+
+def stdd_set_profiling(ctx, enable=True):
+    return _check(ctx, lib.stdd_set_profiling(ctx, 1 if enable else 0))
+
+
+def stdd_get_profile(ctx, reset=True):
+    s = stdd_profile()
+    _check(ctx, lib.stdd_get_profile(ctx, ctypes.byref(s), 1 if reset else 0))
+    return {k: getattr(s, k) for k, _ in stdd_profile._fields_}
 
 
 def stdd_nd_analyze(W, H, leaf_max=64):

@@ -139,7 +139,7 @@ struct stdd_ctx {
   int nsub = 0, overlap = 0, ipml = 0;
   std::vector<int> cuts;
   int prec = STDD_PREC_FP64;
-  int leaf_max = 64;
+  int leaf_max = 16;
   int nrhs = 0;
 
   // operator (global) state
@@ -153,7 +153,7 @@ struct stdd_ctx {
   std::map<int, Shape> shapes;
   std::vector<LevelInfo> levels;
   DBuf d_strips, d_fronts, d_nodes, d_cmap, d_inv, d_lcxm, d_lcxp, d_colstrip;
-  DBuf d_fac, d_ws[2], d_ub[2], d_tloc, d_flag, d_minpiv;
+  DBuf d_fac, d_ws[2], d_ub[2], d_tloc, d_wloc, d_flag, d_minpiv, d_items;
   int64_t nloc = 0, nloc_max = 0, ub_elems[2] = {0, 0};
   int64_t nfronts = 0, factor_entries = 0;
   double factor_cflops = 0, solve_cflops = 0;
@@ -167,6 +167,38 @@ struct stdd_ctx {
   std::vector<std::vector<double>> history;
   int last_its = 0;
   double last_res = 0;
+
+  // phase profiling (CUDA events on the context stream)
+  enum { PH_FACTOR = 0, PH_MINV, PH_MATVEC, PH_ORTHO, PH_SOLVE, PH_COUNT };
+  bool prof = false;
+  struct Span {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<Span> spans;
+  cudaEvent_t next_event() {
+    if (ev_used == ev_pool.size()) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      ev_pool.push_back(e);
+    }
+    return ev_pool[ev_used++];
+  }
+  int pbegin(int phase) {
+    if (!prof) return -1;
+    Span sp{phase, next_event(), next_event()};
+    CK(cudaEventRecord(sp.a, stream));
+    spans.push_back(sp);
+    return (int)spans.size() - 1;
+  }
+  void pend(int id) {
+    if (id >= 0) CK(cudaEventRecord(spans[id].b, stream));
+  }
+  ~stdd_ctx() {
+    for (auto e : ev_pool) cudaEventDestroy(e);
+  }
 
   size_t elem() const { return prec == STDD_PREC_FP64 ? sizeof(double2) : sizeof(float2); }
   int64_t N() const { return (int64_t)nx * ny; }
@@ -267,6 +299,7 @@ MfArgs stdd_ctx::mf_args(int par, bool solve) const {
   a.ws_cur = d_ws[par].p;
   a.ws_child = d_ws[par ^ 1].p;
   a.tloc = d_tloc.p;
+  a.wloc = d_wloc.p;
   a.ub_cur = d_ub[par].p;
   a.ub_child = d_ub[par ^ 1].p;
   a.flag = d_flag.as<int>();
@@ -339,7 +372,7 @@ void stdd_ctx::factor() {
   std::vector<std::vector<int>> inst(nsub);
   for (int k = 0; k < nsub; ++k) inst[k].assign(shapes[strips[k].W()].fronts.size(), -1);
   std::vector<FrontDev> fr;
-  levels.assign(depth, LevelInfo{0, 0, 0, 0, 0});
+  levels.assign(depth, LevelInfo{0, 0, 0, 0, 0, 1 << 30, 0, 0, 0, 0});
   int64_t ws_need[2] = {0, 0};
   ub_elems[0] = ub_elems[1] = 0;
   for (int L = 0; L < depth; ++L) {
@@ -370,6 +403,7 @@ void stdd_ctx::factor() {
         li.max_p = std::max(li.max_p, sf.p);
         li.max_b = std::max(li.max_b, sf.b);
         li.max_n = std::max(li.max_n, sf.p + sf.b);
+        li.min_n = std::min(li.min_n, sf.p + sf.b);
         fr.push_back(d);
       }
     }
@@ -387,6 +421,21 @@ void stdd_ctx::factor() {
     }
   }
   nfronts = (int64_t)fr.size();
+  // substitution work items: (front, 32-row chunk) of the border going up
+  // (at least one per front: chunk 0 also stores w_p) and of the pivots
+  // coming down
+  std::vector<int2> items;
+  for (int L = 0; L < depth; ++L) {
+    LevelInfo &li = levels[L];
+    li.up_off = (int64_t)items.size();
+    for (int f = li.f0; f < li.f0 + li.nf; ++f)
+      for (int c = 0; c < std::max(1, (fr[f].b + 31) / 32); ++c) items.push_back(make_int2(f, c));
+    li.n_up = (int)((int64_t)items.size() - li.up_off);
+    li.down_off = (int64_t)items.size();
+    for (int f = li.f0; f < li.f0 + li.nf; ++f)
+      for (int c = 0; c < (fr[f].p + 31) / 32; ++c) items.push_back(make_int2(f, c));
+    li.n_down = (int)((int64_t)items.size() - li.down_off);
+  }
   std::vector<int> colstrip(nx);
   for (int k = 0; k < nsub; ++k)
     for (int i = strips[k].c0; i < strips[k].c1; ++i) colstrip[i] = k;
@@ -399,6 +448,7 @@ void stdd_ctx::factor() {
   upload(d_lcxm, lcxm, stream);
   upload(d_lcxp, lcxp, stream);
   upload(d_colstrip, colstrip, stream);
+  upload(d_items, items, stream);
   const size_t E = elem();
   d_fac.alloc(std::max<int64_t>(1, factor_entries) * E);
   d_ws[0].alloc(std::max<int64_t>(1, ws_need[0]) * E);
@@ -422,11 +472,13 @@ template <typename R> void stdd_ctx::factor_t() {
   CK(cudaMemsetAsync(d_flag.p, 0, sizeof(int), stream));
   const double inf = INFINITY;
   CK(cudaMemcpyAsync(d_minpiv.p, &inf, sizeof(double), cudaMemcpyHostToDevice, stream));
+  const int span = pbegin(PH_FACTOR);
   for (int L = depth - 1; L >= 0; --L) {
     MfArgs a = mf_args(L & 1, false);
     stdd::mf_factor_level<R>(a, levels[L], stream);
     CK(cudaGetLastError());
   }
+  pend(span);
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, stream));
   CK(cudaMemcpyAsync(&min_pivot, d_minpiv.p, sizeof(double), cudaMemcpyDeviceToHost, stream));
@@ -436,8 +488,11 @@ template <typename R> void stdd_ctx::factor_t() {
 
 template <typename R> void stdd_ctx::solve_levels(int nr) {
   ensure_solve_buffers(nr);
-  for (int L = depth - 1; L >= 0; --L) stdd::mf_forward_level<R>(mf_args(L & 1, true), levels[L], nr, nloc, stream);
-  for (int L = 0; L < depth; ++L) stdd::mf_backward_level<R>(mf_args(L & 1, true), levels[L], nr, nloc, stream);
+  const int2 *items = d_items.as<int2>();
+  for (int L = depth - 1; L >= 0; --L)
+    stdd::mf_up_level<R>(mf_args(L & 1, true), items + levels[L].up_off, levels[L].n_up, nr, nloc, stream);
+  for (int L = 0; L < depth; ++L)
+    stdd::mf_down_level<R>(mf_args(L & 1, true), items + levels[L].down_off, levels[L].n_down, nr, nloc, stream);
   CK(cudaGetLastError());
 }
 
@@ -445,6 +500,7 @@ void stdd_ctx::ensure_solve_buffers(int nr) {
   if (nr <= solve_nrhs_cap) return;
   const size_t E = elem();
   d_tloc.alloc(std::max<int64_t>(1, nloc) * nr * E);
+  d_wloc.alloc(std::max<int64_t>(1, nloc) * nr * E);
   d_ub[0].alloc(std::max<int64_t>(1, ub_elems[0]) * nr * E);
   d_ub[1].alloc(std::max<int64_t>(1, ub_elems[1]) * nr * E);
   solve_nrhs_cap = nr;
@@ -454,6 +510,7 @@ void stdd_ctx::ensure_solve_buffers(int nr) {
 // substitution over every strip, synthesis of the full local fields.
 void stdd_ctx::apply_minv(const double2 *v, double2 *z) {
   ensure_solve_buffers(1);
+  const int span = pbegin(PH_MINV);
   if (prec == STDD_PREC_FP64) {
     stdd::launch_restrict<double>(d_strips.as<StripDev>(), nsub, nloc_max, ny, nullptr, v, d_tloc.p, stream);
     solve_levels<double>(1);
@@ -465,6 +522,7 @@ void stdd_ctx::apply_minv(const double2 *v, double2 *z) {
     stdd::launch_synthesize<float>(d_strips.as<StripDev>(), nsub, nx, ny, d_colstrip.as<int>(), d_tloc.p, z,
                                    stream);
   }
+  pend(span);
   CK(cudaGetLastError());
 }
 
@@ -535,7 +593,9 @@ void stdd_ctx::gmres(int rhs, const stdd_solve_opts &o, double2 *x) {
   std::vector<cd> H((size_t)(m + 1) * m), g(m + 1), sn(m), hv(2 * (m + 2));
   std::vector<double> cs(m);
   while (true) {
+    int sp = pbegin(PH_MATVEC);
     stdd::launch_residual(grid(), b, x, r, stream);
+    pend(sp);
     const double beta = dev_norm(r, n, d_part, d_nrm, stream);
     if (hist.empty()) hist.push_back(beta / bnorm);
     last_res = beta / bnorm;
@@ -549,11 +609,15 @@ void stdd_ctx::gmres(int rhs, const stdd_solve_opts &o, double2 *x) {
     for (int j = 0; j < m; ++j) {
       double2 *vj = V + (int64_t)j * n, *zj = Z + (int64_t)j * n, *w = V + (int64_t)(j + 1) * n;
       apply_minv(vj, zj);
+      sp = pbegin(PH_MATVEC);
       stdd::launch_stencil(grid(), zj, w, stream);
+      pend(sp);
+      sp = pbegin(PH_ORTHO);
       stdd::launch_mdot(V, n, j + 1, w, n, d_part.as<double2>(), h1, stream);
       stdd::launch_maxpy_norm(V, n, j + 1, h1, w, n, part, nrm, stream);
       stdd::launch_mdot(V, n, j + 1, w, n, d_part.as<double2>(), h2, stream);
       stdd::launch_maxpy_norm(V, n, j + 1, h2, w, n, part, nrm, stream);
+      pend(sp);
       double nrm2 = 0;
       CK(cudaMemcpyAsync(hv.data(), h1, sizeof(double2) * 2 * (m + 2), cudaMemcpyDeviceToHost, stream));
       CK(cudaMemcpyAsync(&nrm2, nrm, sizeof(double), cudaMemcpyDeviceToHost, stream));
@@ -645,7 +709,7 @@ void stdd_ctx::richardson(int rhs, const stdd_solve_opts &o, double2 *x) {
 int64_t stdd_ctx::device_bytes() const {
   const DBuf *all[] = {&d_eps, &d_cxm, &d_cxp, &d_cym, &d_cyp, &d_strips, &d_fronts, &d_nodes, &d_cmap,
                        &d_inv, &d_lcxm, &d_lcxp, &d_colstrip, &d_fac, &d_ws[0], &d_ws[1], &d_ub[0],
-                       &d_ub[1], &d_tloc, &d_flag, &d_minpiv, &d_b, &d_x, &d_r, &d_V, &d_Z, &d_w,
+                       &d_ub[1], &d_tloc, &d_wloc, &d_items, &d_flag, &d_minpiv, &d_b, &d_x, &d_r, &d_V, &d_Z, &d_w,
                        &d_part, &d_h, &d_nrm, &d_y, &d_pre, &d_fpart};
   int64_t s = 0;
   for (auto *d : all) s += (int64_t)d->bytes;
@@ -856,6 +920,7 @@ stdd_status stdd_solve(stdd_ctx *c, const stdd_solve_opts *o, double *x_out, int
     const int64_t n = c->N();
     c->history.assign(c->nrhs, {});
     c->ensure_krylov(o->paper_richardson ? 1 : o->restart);
+    const int span = c->pbegin(stdd_ctx::PH_SOLVE);
     for (int q = 0; q < c->nrhs; ++q) {
       double2 *x = c->d_x.as<double2>();
       if (o->x0_mode == STDD_X0_USER)
@@ -865,6 +930,7 @@ stdd_status stdd_solve(stdd_ctx *c, const stdd_solve_opts *o, double *x_out, int
       if (o->paper_richardson) c->richardson(q, *o, x);
       else c->gmres(q, *o, x);
       if (!(c->last_res <= o->rtol) && !o->paper_richardson) noconv = true;
+      if (q == c->nrhs - 1) c->pend(span);
       copy_out(x_out + (size_t)q * n * 2, x, n * sizeof(double2), is_device, c->stream);
     }
   });
@@ -971,6 +1037,63 @@ stdd_status stdd_get_stats(stdd_ctx *c, stdd_stats *o) {
     o->iterations = c->last_its;
     o->final_residual = c->last_res;
     o->min_pivot = c->min_pivot;
+  });
+}
+
+stdd_status stdd_residual(stdd_ctx *c, const double *x, const double *b, double *r, double *rel_out,
+                          int is_device) {
+  return guarded(c, [&] {
+    if (!x || !b || !r || !rel_out) throw ArgError("null argument");
+    c->require_operator();
+    const int64_t n = c->N();
+    c->d_w.alloc(n * sizeof(double2));
+    c->d_r.alloc(n * sizeof(double2));
+    c->d_x.alloc(n * sizeof(double2));
+    c->d_part.alloc((size_t)stdd::krylov_partial_blocks() * sizeof(double2));
+    c->d_nrm.alloc(4 * sizeof(double));
+    copy_in(c->d_w.p, x, n * sizeof(double2), is_device, c->stream);
+    copy_in(c->d_x.p, b, n * sizeof(double2), is_device, c->stream);
+    stdd::launch_residual(c->grid(), c->d_x.as<double2>(), c->d_w.as<double2>(), c->d_r.as<double2>(), c->stream);
+    const double rn = dev_norm(c->d_r.as<double2>(), n, c->d_part, c->d_nrm, c->stream);
+    const double bn = dev_norm(c->d_x.as<double2>(), n, c->d_part, c->d_nrm, c->stream);
+    *rel_out = bn > 0 ? rn / bn : rn;
+    copy_out(r, c->d_r.p, n * sizeof(double2), is_device, c->stream);
+  });
+}
+
+stdd_status stdd_set_profiling(stdd_ctx *c, int enable) {
+  return guarded(c, [&] { c->prof = enable != 0; });
+}
+
+stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {
+  return guarded(c, [&] {
+    if (!o) throw ArgError("null profile");
+    std::memset(o, 0, sizeof(*o));
+    CK(cudaStreamSynchronize(c->stream));
+    double t[stdd_ctx::PH_COUNT] = {0};
+    int cnt[stdd_ctx::PH_COUNT] = {0};
+    for (auto &sp : c->spans) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, sp.a, sp.b) != cudaSuccess) {  // span left open by a failed call
+        (void)cudaGetLastError();
+        continue;
+      }
+      t[sp.phase] += ms;
+      cnt[sp.phase] += 1;
+    }
+    o->factor_ms = t[stdd_ctx::PH_FACTOR];
+    o->minv_ms = t[stdd_ctx::PH_MINV];
+    o->minv_calls = cnt[stdd_ctx::PH_MINV];
+    o->matvec_ms = t[stdd_ctx::PH_MATVEC];
+    o->matvec_calls = cnt[stdd_ctx::PH_MATVEC];
+    o->ortho_ms = t[stdd_ctx::PH_ORTHO];
+    o->ortho_calls = cnt[stdd_ctx::PH_ORTHO];
+    o->solve_ms = t[stdd_ctx::PH_SOLVE];
+    o->launches = __atomic_load_n(&stdd::g_launches, __ATOMIC_RELAXED);
+    if (reset) {
+      c->spans.clear();
+      c->ev_used = 0;
+    }
   });
 }
 

@@ -7,8 +7,14 @@
 
 namespace stdd {
 
-constexpr int MF_NB = 32;             // pivot block of the blocked partial LU
+// kernels launched by this library (all contexts), for launch accounting
+extern long long g_launches;
+inline void count_launch(int n = 1) { __atomic_add_fetch(&g_launches, (long long)n, __ATOMIC_RELAXED); }
+
+constexpr int MF_NB = 32;             // pivot block of the blocked Gauss-Jordan sweep
 constexpr int MF_PANEL_THREADS = 128; // rows / columns per panel tile
+constexpr int MF_SMALL = 64;          // fronts with n <= MF_SMALL are swept in shared memory
+constexpr int MF_SMALL_THREADS = 128;
 
 // Everything a multifrontal kernel needs (device pointers).
 struct MfArgs {
@@ -23,7 +29,8 @@ struct MfArgs {
   void *fac;                  // factor storage (complex R)
   void *ws_cur;               // F22 of this level
   const void *ws_child;       // F22 of the level below
-  void *tloc;                 // local fields, [nrhs][ldt]
+  void *tloc;                 // local fields, [nrhs][ldt]: t on entry, x on exit
+  void *wloc;                 // w at the pivots of every front (going up), [nrhs][ldt]
   void *ub_cur;               // forward update vectors of this level
   const void *ub_child;       // and of the level below
   int *flag;                  // bit 0: zero / non-finite pivot
@@ -32,15 +39,17 @@ struct MfArgs {
 
 struct LevelInfo {
   int f0, nf;                 // fronts [f0, f0 + nf) of the level
-  int max_p, max_b, max_n;
+  int max_p, max_b, max_n, min_n;
+  int64_t up_off, down_off;   // offsets of the level's work items
+  int n_up, n_down;           // (front, 32-row chunk) items going up / down
 };
 
 template <typename R> cudaError_t mf_setup_attributes();
 template <typename R> void mf_factor_level(const MfArgs &a, const LevelInfo &L, cudaStream_t st);
 template <typename R>
-void mf_forward_level(const MfArgs &a, const LevelInfo &L, int nrhs, int64_t ldt, cudaStream_t st);
+void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int nrhs, int64_t ldt, cudaStream_t st);
 template <typename R>
-void mf_backward_level(const MfArgs &a, const LevelInfo &L, int nrhs, int64_t ldt, cudaStream_t st);
+void mf_down_level(const MfArgs &a, const int2 *items, int nitems, int nrhs, int64_t ldt, cudaStream_t st);
 
 // ---- FDFD / DDM vector kernels (kernels_fdfd.cu)
 struct GridDev {

@@ -14,6 +14,8 @@
 
 namespace stdd {
 
+long long g_launches = 0;
+
 namespace {
 
 constexpr int TPB = 256;
@@ -141,16 +143,19 @@ template <typename R>
 void launch_strip_norms(const StripDev *strips_dev, int nsub, int ny, const void *tloc, double *out,
                         cudaStream_t st) {
   k_strip_norms<R><<<nsub, TPB, 0, st>>>(strips_dev, ny, tloc, out);
+  count_launch();
 }
 template void launch_strip_norms<double>(const StripDev *, int, int, const void *, double *, cudaStream_t);
 template void launch_strip_norms<float>(const StripDev *, int, int, const void *, double *, cudaStream_t);
 
 void launch_stencil(const GridDev &g, const double2 *x, double2 *y, cudaStream_t st) {
   k_stencil<<<grid_for((int64_t)g.nx * g.ny), TPB, 0, st>>>(g, x, y);
+  count_launch();
 }
 
 void launch_residual(const GridDev &g, const double2 *b, const double2 *x, double2 *r, cudaStream_t st) {
   k_residual<<<grid_for((int64_t)g.nx * g.ny), TPB, 0, st>>>(g, b, x, r);
+  count_launch();
 }
 
 template <typename R>
@@ -158,19 +163,23 @@ void launch_restrict(const StripDev *strips_dev, int nsub, int64_t nloc_max, int
                      const double2 *v, void *tloc, cudaStream_t st) {
   const int gx = (int)std::min<int64_t>((nloc_max + TPB - 1) / TPB, 1024);
   k_restrict<R><<<dim3(gx, nsub), TPB, 0, st>>>(strips_dev, ny, v, tloc);
+  count_launch();
 }
 
 template <typename R>
 void launch_synthesize(const StripDev *strips_dev, int nsub, int nx, int ny, const int *col_strip,
                        const void *tloc, double2 *z, cudaStream_t st) {
   k_synthesize<R><<<grid_for((int64_t)nx * ny), TPB, 0, st>>>(strips_dev, nsub, nx, ny, col_strip, tloc, z);
+  count_launch();
 }
 
 template <typename R> void launch_to_local(const double2 *t, void *tloc, int64_t n, cudaStream_t st) {
   k_to_local<R><<<grid_for(n), TPB, 0, st>>>(t, tloc, n);
+  count_launch();
 }
 template <typename R> void launch_from_local(const void *tloc, double2 *z, int64_t n, cudaStream_t st) {
   k_from_local<R><<<grid_for(n), TPB, 0, st>>>(tloc, z, n);
+  count_launch();
 }
 
 template void launch_restrict<double>(const StripDev *, int, int64_t, int, const int *, const double2 *, void *,

@@ -161,29 +161,37 @@ void launch_mdot(const double2 *V, int64_t ldv, int m, const double2 *w, int64_t
                  double2 *h, cudaStream_t st) {
   const int nb = nblocks_for(n);
   k_mdot<<<nb, TPB, 0, st>>>(V, ldv, m, w, n, partial);
+  count_launch();
   k_reduce_c<<<(m + 7) / 8, 256, 0, st>>>(partial, nb, m, h);
+  count_launch();
 }
 
 void launch_maxpy_norm(const double2 *V, int64_t ldv, int m, const double2 *h, double2 *w, int64_t n,
                        double *partial, double *nrm2, cudaStream_t st) {
   const int nb = nblocks_for(n);
   k_maxpy_norm<<<nb, TPB, 0, st>>>(V, ldv, m, h, w, n, partial);
+  count_launch();
   k_reduce_r<<<1, 32, 0, st>>>(partial, nb, nrm2);
+  count_launch();
 }
 
 void launch_maxpy(const double2 *Z, int64_t ldz, int m, const double2 *y, double2 *x, int64_t n,
                   cudaStream_t st) {
   k_maxpy<<<nblocks_for(n), TPB, 0, st>>>(Z, ldz, m, y, x, n);
+  count_launch();
 }
 
 void launch_norm2(const double2 *x, int64_t n, double *partial, double *nrm2, cudaStream_t st) {
   const int nb = nblocks_for(n);
   k_norm2<<<nb, TPB, 0, st>>>(x, n, partial);
+  count_launch();
   k_reduce_r<<<1, 32, 0, st>>>(partial, nb, nrm2);
+  count_launch();
 }
 
 void launch_scale(const double2 *x, const double *inv_norm2, double2 *y, int64_t n, cudaStream_t st) {
   k_scale<<<nblocks_for(n), TPB, 0, st>>>(x, inv_norm2, y, n);
+  count_launch();
 }
 
 }  // namespace stdd

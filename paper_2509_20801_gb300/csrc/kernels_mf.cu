@@ -1,21 +1,26 @@
-// Numeric multifrontal LU of the strip operators A_i and the batched
-// forward / back substitutions that apply A_i^-1 (Sec. 2.4, Eqs. 22-23).
+// Numeric multifrontal factorization of the strip operators A_i and the
+// batched substitution sweeps that apply A_i^-1 (Sec. 2.4, Eqs. 22-23).
 //
-// Every kernel works on one level of the elimination trees at a time, over
-// all fronts of that level in all strips (blockIdx.x = front within the
-// level, blockIdx.y = tile within the front).  Fronts of one level are independent; a level needs
-// only the Schur complements (factor) or update vectors (forward solve) of
-// the level below, kept in two parity buffers.
+// Each front F = [F11 F12; F21 F22] (p pivots, b border nodes, n = p + b) is
+// eliminated by a Gauss-Jordan sweep of its p pivots, which leaves
+//     [ F11^-1          F11^-1 F12            ]   =  [ Finv   H12 ]
+//     [ -F21 F11^-1     F22 - F21 F11^-1 F12  ]      [ -G21   S   ]
+// in place.  S is the Schur complement the parent extend-adds.  With these
+// blocks the two substitutions of Eq. 23 become plain matrix-vector products
+// with no sequential triangular chain: going up the tree (leaves to root)
+//     w = [t_piv; 0] + sum_children extend(u_child),   u = w_b - G21 w_p,
+// and coming down (root to leaves)
+//     x_p = Finv w_p - H12 x_b,
+// the block-LU solve of the front written with the inverse of F11.  The
+// elimination order (nested dissection) is the only permutation; there is no
+// pivoting (Eq. 22 uses fill-reducing P, Q only) and zero / non-finite pivots
+// raise a flag the host turns into STDD_EPIVOT.
 //
-// Front layout (n = p + b, column-major, complex):
-//   [F11 F12] : p x n, leading dimension p, in the factor block
-//   F21       : b x p, leading dimension b, right after it
-//   F22       : b x b, leading dimension b, in the level workspace
-// After factorization F11 holds L11 (unit, strictly lower) and U11, F21 holds
-// L21 = F21 U11^-1, F12 holds U12 = L11^-1 F12 and F22 the Schur complement
-// F22 - L21 U12 that the parent extend-adds.  No pivoting: the fill-reducing
-// order is the only permutation (Eq. 22); zero or non-finite pivots raise a
-// flag that the host turns into STDD_EPIVOT.
+// Front storage (column-major, complex):
+//   rows 0..p-1, all n columns : p x n, leading dimension p ([Finv H12])
+//   rows p..n-1, columns < p   : b x p, leading dimension b (-G21)
+//   rows p..n-1, columns >= p  : b x b in the level workspace (S)
+// Every kernel handles one level of the elimination trees of all strips.
 #include <algorithm>
 
 #include "common.cuh"
@@ -25,19 +30,48 @@ namespace stdd {
 
 namespace {
 
-template <typename C>
-__device__ __forceinline__ int64_t elem_off(int r, int c, int p, int b, int64_t fo, int64_t so,
-                                            bool &in_ws) {
+template <typename C> __device__ __forceinline__ bool cfinite(C a) { return isfinite(a.x) && isfinite(a.y); }
+
+template <typename C> __device__ __forceinline__ C cneg(C a) {
+  a.x = -a.x;
+  a.y = -a.y;
+  return a;
+}
+
+// address of front element (r, c); *ws selects the level workspace
+__device__ __forceinline__ int64_t elem_off(int r, int c, int p, int b, int64_t fo, int64_t so, bool &ws) {
+  if (r < p) {
+    ws = false;
+    return fo + (int64_t)c * p + r;
+  }
   const int n = p + b;
-  if (r < p) { in_ws = false; return fo + (int64_t)c * p + r; }
-  if (c < p) { in_ws = false; return fo + (int64_t)p * n + (int64_t)c * b + (r - p); }
-  in_ws = true;
+  if (c < p) {
+    ws = false;
+    return fo + (int64_t)p * n + (int64_t)c * b + (r - p);
+  }
+  ws = true;
   return so + (int64_t)(c - p) * b + (r - p);
 }
 
-template <typename C> __device__ __forceinline__ bool cfinite(C a) {
-  return isfinite(a.x) && isfinite(a.y);
+template <typename C> __device__ __forceinline__ C ld_elem(const MfArgs &a, const FrontDev &f, int r, int c) {
+  bool ws;
+  const int64_t o = elem_off(r, c, f.p, f.b, f.fac_off, f.s_off, ws);
+  return ws ? reinterpret_cast<const C *>(a.ws_cur)[o] : reinterpret_cast<const C *>(a.fac)[o];
 }
+template <typename C> __device__ __forceinline__ void st_elem(const MfArgs &a, const FrontDev &f, int r, int c, C v) {
+  bool ws;
+  const int64_t o = elem_off(r, c, f.p, f.b, f.fac_off, f.s_off, ws);
+  if (ws) reinterpret_cast<C *>(a.ws_cur)[o] = v;
+  else reinterpret_cast<C *>(a.fac)[o] = v;
+}
+
+__device__ __forceinline__ void note_pivot(const MfArgs &a, double ad, bool finite) {
+  if (!(ad > 0.0) || !finite) atomicOr(a.flag, 1);
+  else atomicMin(reinterpret_cast<unsigned long long *>(a.min_pivot), (unsigned long long)__double_as_longlong(ad));
+}
+
+// skip the pivot band [k, k + nbk) when enumerating rows / columns
+__device__ __forceinline__ int unband(int i, int k, int nbk) { return i < k ? i : i + nbk; }
 
 }  // namespace
 
@@ -59,8 +93,7 @@ __global__ void __launch_bounds__(256) mf_assemble(MfArgs a, int f0) {
     has[ci] = f.child[ci] >= 0;
     if (has[ci]) ch[ci] = a.fronts[f.child[ci]];
   }
-  for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < nn;
-       e += (int64_t)gridDim.y * blockDim.x) {
+  for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.y * blockDim.x) {
     const int c = (int)(e / n), r = (int)(e - (int64_t)c * n);
     double2 v = make_double2(0.0, 0.0);
     if (r < p || c < p) {
@@ -89,28 +122,72 @@ __global__ void __launch_bounds__(256) mf_assemble(MfArgs a, int f0) {
       if (ir < 0) continue;
       const int ic = a.inv[f.inv_off[ci] + c];
       if (ic < 0) continue;
-      const C sv = reinterpret_cast<const C *>(a.ws_child)[ch[ci].s_off + (int64_t)ic * ch[ci].b + ir];
-      out = cadd(out, sv);
+      out = cadd(out, reinterpret_cast<const C *>(a.ws_child)[ch[ci].s_off + (int64_t)ic * ch[ci].b + ir]);
     }
-    bool in_ws;
-    const int64_t off = elem_off<C>(r, c, p, b, f.fac_off, f.s_off, in_ws);
-    if (in_ws) reinterpret_cast<C *>(a.ws_cur)[off] = out;
-    else reinterpret_cast<C *>(a.fac)[off] = out;
+    st_elem<C>(a, f, r, c, out);
   }
 }
 
-// ------------------------------------------------------ diagonal block k
-// One CTA per front: unblocked LU (no pivoting) of the nbk x nbk block at
-// (k, k), in shared memory, written back in place; zero or non-finite pivots
-// set the flag, |pivot| feeds the running minimum.
+// ------------------------------------------------ small fronts, in smem
+// One CTA per front with n <= MF_SMALL: the whole front is swept in shared
+// memory one pivot at a time (row k scaled by 1/d, column k kept, then the
+// rank-1 update of everything else).
 template <typename R>
-__global__ void __launch_bounds__(MF_PANEL_THREADS) mf_diag(MfArgs a, int f0, int k) {
+__global__ void __launch_bounds__(MF_SMALL_THREADS) mf_gj_small(MfArgs a, int f0) {
+  using C = typename CT<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *F = reinterpret_cast<C *>(smem_raw);  // n x n, ld n
+  C *rowk = F + MF_SMALL * MF_SMALL;
+  C *colk = rowk + MF_SMALL;
+  const FrontDev f = a.fronts[f0 + blockIdx.x];
+  const int p = f.p, b = f.b, n = p + b;
+  if (n > MF_SMALL) return;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const int c = idx / n, r = idx - c * n;
+    F[idx] = ld_elem<C>(a, f, r, c);
+  }
+  __syncthreads();
+  for (int k = 0; k < p; ++k) {
+    const C d = F[k * n + k];
+    const C inv = crecip(d);
+    for (int j = tid; j < n; j += blockDim.x) {
+      rowk[j] = cmul(F[j * n + k], inv);
+      colk[j] = F[k * n + j];
+    }
+    if (tid == 0) note_pivot(a, sqrt((double)cabs2(d)), cfinite(d));
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+      const int c = idx / n, r = idx - c * n;
+      C v;
+      if (r == k) v = (c == k) ? inv : rowk[c];
+      else if (c == k) v = cneg(cmul(colk[r], inv));
+      else v = cfms(colk[r], rowk[c], F[idx]);
+      F[idx] = v;
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const int c = idx / n, r = idx - c * n;
+    st_elem<C>(a, f, r, c, F[idx]);
+  }
+}
+
+// ------------------------------------------- large fronts, blocked sweep
+// Step k sweeps pivots [k, k + nbk) of every front with n > MF_SMALL:
+//   gj_diag  : D <- D^-1                          (one CTA per front)
+//   gj_col   : C <- -C D^-1    rows outside the band
+//   gj_update: A <- A + C R    rows and columns outside the band (R unscaled)
+//   gj_row   : R <- D^-1 R     columns outside the band
+template <typename R>
+__global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_diag(MfArgs a, int f0, int k) {
   using C = typename CT<R>::T;
   constexpr int NB = MF_NB;
   __shared__ C D[NB][NB + 1];
+  __shared__ C rowk[NB], colk[NB];
   const FrontDev f = a.fronts[f0 + blockIdx.x];
-  const int p = f.p;
-  if (k >= p) return;
+  const int p = f.p, n = p + f.b;
+  if (n <= MF_SMALL || k >= p) return;
   const int nbk = min(NB, p - k);
   C *fac = reinterpret_cast<C *>(a.fac);
   const int64_t fo = f.fac_off;
@@ -120,14 +197,22 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_diag(MfArgs a, int f0, in
     D[i][j] = fac[fo + (int64_t)(k + j) * p + k + i];
   }
   __syncthreads();
-  for (int j = 0; j < nbk; ++j) {
-    const C inv = crecip(D[j][j]);
-    for (int i = j + 1 + tid; i < nbk; i += blockDim.x) D[i][j] = cmul(D[i][j], inv);
+  for (int q = 0; q < nbk; ++q) {
+    const C d = D[q][q];
+    const C inv = crecip(d);
+    for (int j = tid; j < nbk; j += blockDim.x) {
+      rowk[j] = cmul(D[q][j], inv);
+      colk[j] = D[j][q];
+    }
+    if (tid == 0) note_pivot(a, sqrt((double)cabs2(d)), cfinite(d));
     __syncthreads();
-    const int m = nbk - j - 1;
-    for (int idx = tid; idx < m * m; idx += blockDim.x) {
-      const int i = j + 1 + idx % m, l = j + 1 + idx / m;
-      D[i][l] = cfms(D[i][j], D[j][l], D[i][l]);
+    for (int idx = tid; idx < nbk * nbk; idx += blockDim.x) {
+      const int i = idx % nbk, j = idx / nbk;
+      C v;
+      if (i == q) v = (j == q) ? inv : rowk[j];
+      else if (j == q) v = cneg(cmul(colk[i], inv));
+      else v = cfms(colk[i], rowk[j], D[i][j]);
+      D[i][j] = v;
     }
     __syncthreads();
   }
@@ -135,124 +220,101 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_diag(MfArgs a, int f0, in
     const int i = idx % nbk, j = idx / nbk;
     fac[fo + (int64_t)(k + j) * p + k + i] = D[i][j];
   }
-  for (int j = tid; j < nbk; j += blockDim.x) {
-    const C d = D[j][j];
-    const double ad = sqrt((double)cabs2(d));
-    if (!(ad > 0.0) || !cfinite(d)) atomicOr(a.flag, 1);
-    else atomicMin(reinterpret_cast<unsigned long long *>(a.min_pivot),
-                   (unsigned long long)__double_as_longlong(ad));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_col(MfArgs a, int f0, int k) {
+  using C = typename CT<R>::T;
+  constexpr int NB = MF_NB;
+  __shared__ C Dinv[NB][NB + 1];
+  const FrontDev f = a.fronts[f0 + blockIdx.x];
+  const int p = f.p, n = p + f.b;
+  if (n <= MF_SMALL || k >= p) return;
+  const int nbk = min(NB, p - k);
+  const int rows = n - nbk;
+  if ((int)blockIdx.y * MF_PANEL_THREADS >= rows) return;
+  const C *fac = reinterpret_cast<const C *>(a.fac);
+  const int64_t fo = f.fac_off;
+  for (int idx = threadIdx.x; idx < nbk * nbk; idx += blockDim.x) {
+    const int i = idx % nbk, j = idx / nbk;
+    Dinv[i][j] = fac[fo + (int64_t)(k + j) * p + k + i];
+  }
+  __syncthreads();
+  const int ri = blockIdx.y * MF_PANEL_THREADS + threadIdx.x;
+  if (ri >= rows) return;
+  const int r = unband(ri, k, nbk);
+  C x[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+    if (j < nbk) x[j] = ld_elem<C>(a, f, r, k + j);
+#pragma unroll 4
+  for (int j = 0; j < NB; ++j) {
+    if (j < nbk) {
+      C s = czero<C>();
+#pragma unroll
+      for (int l = 0; l < NB; ++l)
+        if (l < nbk) s = cfma(x[l], Dinv[l][j], s);
+      st_elem<C>(a, f, r, k + j, cneg(s));
+    }
   }
 }
 
-// ---------------------------------------------------------- panel step k
-// After mf_diag: blockIdx.y = 0 .. ntr-1 are row tiles of L (rows k+nbk ..
-// n) solving X U_D = F; blockIdx.y = ntr .. 2 ntr-1 are column tiles of U
-// (cols k+nbk .. n) solving L_D Y = F.  The factored diagonal block is only
-// read here, so the tiles need no ordering among themselves.
 template <typename R>
-__global__ void __launch_bounds__(MF_PANEL_THREADS) mf_panel(MfArgs a, int f0, int k) {
+__global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_row(MfArgs a, int f0, int k) {
   using C = typename CT<R>::T;
   constexpr int NB = MF_NB;
   constexpr int TILE = MF_PANEL_THREADS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C(*D)[NB + 1] = reinterpret_cast<C(*)[NB + 1]>(smem_raw);
-  C *dinv = reinterpret_cast<C *>(smem_raw + sizeof(C) * NB * (NB + 1));
-  C(*T)[NB + 1] = reinterpret_cast<C(*)[NB + 1]>(smem_raw + sizeof(C) * (NB * (NB + 1) + NB));
-
+  C(*Dinv)[NB + 1] = reinterpret_cast<C(*)[NB + 1]>(smem_raw);
+  C(*T)[NB + 1] = reinterpret_cast<C(*)[NB + 1]>(smem_raw + sizeof(C) * NB * (NB + 1));
   const FrontDev f = a.fronts[f0 + blockIdx.x];
-  const int p = f.p, b = f.b, n = p + b;
-  if (k >= p) return;
+  const int p = f.p, n = p + f.b;
+  if (n <= MF_SMALL || k >= p) return;
   const int nbk = min(NB, p - k);
-  const int rem = n - k - nbk;
-  const int ntr = (rem + TILE - 1) / TILE;
-  const int t = blockIdx.y;
-  if (t >= 2 * ntr) return;
+  const int cols = n - nbk;
+  const int cbase = blockIdx.y * TILE;
+  if (cbase >= cols) return;
+  const int ncol = min(TILE, cols - cbase);
   C *fac = reinterpret_cast<C *>(a.fac);
   const int64_t fo = f.fac_off;
   const int tid = threadIdx.x;
-
   for (int idx = tid; idx < nbk * nbk; idx += blockDim.x) {
     const int i = idx % nbk, j = idx / nbk;
-    D[i][j] = fac[fo + (int64_t)(k + j) * p + k + i];
+    Dinv[i][j] = fac[fo + (int64_t)(k + j) * p + k + i];
+  }
+  for (int idx = tid; idx < nbk * ncol; idx += blockDim.x) {
+    const int i = idx % nbk, cc = idx / nbk;
+    T[cc][i] = fac[fo + (int64_t)unband(cbase + cc, k, nbk) * p + k + i];
   }
   __syncthreads();
-  for (int j = tid; j < nbk; j += blockDim.x) dinv[j] = crecip(D[j][j]);
+  if (tid < ncol) {
+    C y[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+      if (i < nbk) y[i] = T[tid][i];
+#pragma unroll 4
+    for (int i = 0; i < NB; ++i) {
+      if (i < nbk) {
+        C s = czero<C>();
+#pragma unroll
+        for (int l = 0; l < NB; ++l)
+          if (l < nbk) s = cfma(Dinv[i][l], y[l], s);
+        T[tid][i] = s;
+      }
+    }
+  }
   __syncthreads();
-
-  if (t < ntr) {
-    // rows r = k+nbk+t*TILE+tid of column block [k, k+nbk): X = F U_D^-1
-    const int r = k + nbk + t * TILE + tid;
-    if (r < n) {
-      C x[NB];
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        if (j < nbk) {
-          const int64_t off = r < p ? fo + (int64_t)(k + j) * p + r
-                                    : fo + (int64_t)p * n + (int64_t)(k + j) * b + (r - p);
-          x[j] = fac[off];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        if (j < nbk) {
-          C s = x[j];
-#pragma unroll
-          for (int l = 0; l < NB; ++l)
-            if (l < j) s = cfms(x[l], D[l][j], s);
-          x[j] = cmul(s, dinv[j]);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        if (j < nbk) {
-          const int64_t off = r < p ? fo + (int64_t)(k + j) * p + r
-                                    : fo + (int64_t)p * n + (int64_t)(k + j) * b + (r - p);
-          fac[off] = x[j];
-        }
-      }
-    }
-  } else {
-    // columns c of row block [k, k+nbk): Y = L_D^-1 F, staged through smem
-    const int cbase = k + nbk + (t - ntr) * TILE;
-    const int ncol = min(TILE, n - cbase);
-    for (int idx = tid; idx < nbk * ncol; idx += blockDim.x) {
-      const int i = idx % nbk, cc = idx / nbk;
-      T[cc][i] = fac[fo + (int64_t)(cbase + cc) * p + k + i];
-    }
-    __syncthreads();
-    if (tid < ncol) {
-      C y[NB];
-#pragma unroll
-      for (int i = 0; i < NB; ++i)
-        if (i < nbk) y[i] = T[tid][i];
-#pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        if (i < nbk) {
-          C s = y[i];
-#pragma unroll
-          for (int l = 0; l < NB; ++l)
-            if (l < i) s = cfms(D[i][l], y[l], s);
-          y[i] = s;
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < NB; ++i)
-        if (i < nbk) T[tid][i] = y[i];
-    }
-    __syncthreads();
-    for (int idx = tid; idx < nbk * ncol; idx += blockDim.x) {
-      const int i = idx % nbk, cc = idx / nbk;
-      fac[fo + (int64_t)(cbase + cc) * p + k + i] = T[cc][i];
-    }
+  for (int idx = tid; idx < nbk * ncol; idx += blockDim.x) {
+    const int i = idx % nbk, cc = idx / nbk;
+    fac[fo + (int64_t)unband(cbase + cc, k, nbk) * p + k + i] = T[cc][i];
   }
 }
 
-// ------------------------------------------------------- tile GEMM core
-// acc[4][4] += A(64 x K) B(K x 64) for one 64 x 64 tile, K <= MF_NB per call.
-// 256 threads as 16 x 16; thread (tx, ty) owns rows ty + 16*i, cols tx + 16*j.
+// acc[4][4] += A(64 x K) B(K x 64); 256 threads as 16 x 16, thread (tx, ty)
+// owns rows ty + 16 i and columns tx + 16 j
 template <typename C>
-__device__ __forceinline__ void tile_mma(const C (*As)[MF_NB + 1], const C (*Bs)[64 + 1], int K,
-                                         C acc[4][4], int tx, int ty) {
+__device__ __forceinline__ void tile_mma(const C (*As)[MF_NB + 1], const C (*Bs)[64 + 1], int K, C acc[4][4],
+                                         int tx, int ty) {
   for (int kk = 0; kk < K; ++kk) {
     C av[4], bv[4];
 #pragma unroll
@@ -266,43 +328,31 @@ __device__ __forceinline__ void tile_mma(const C (*As)[MF_NB + 1], const C (*Bs)
   }
 }
 
-// ------------------------------------------------- trailing update step k
-// F(r, c) -= L(r, k:k+nbk) U(k:k+nbk, c) for r, c >= k+nbk outside F22
-// (the F22 block is updated once, at the end, by mf_schur).
 template <typename R>
-__global__ void __launch_bounds__(256) mf_update(MfArgs a, int f0, int k) {
+__global__ void __launch_bounds__(256) mf_gj_update(MfArgs a, int f0, int k) {
   using C = typename CT<R>::T;
   constexpr int NB = MF_NB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C(*As)[NB + 1] = reinterpret_cast<C(*)[NB + 1]>(smem_raw);
   C(*Bs)[64 + 1] = reinterpret_cast<C(*)[64 + 1]>(smem_raw + sizeof(C) * 64 * (NB + 1));
-
   const FrontDev f = a.fronts[f0 + blockIdx.x];
-  const int p = f.p, b = f.b, n = p + b;
-  if (k >= p) return;
+  const int p = f.p, n = p + f.b;
+  if (n <= MF_SMALL || k >= p) return;
   const int nbk = min(NB, p - k);
-  const int s0 = k + nbk;
-  const int rem = n - s0;
-  if (rem <= 0 || s0 >= p) return;
-  const int nt = (rem + 63) / 64;
+  const int m = n - nbk;
+  const int nt = (m + 63) / 64;
   if ((int)blockIdx.y >= nt * nt) return;
-  const int r0 = s0 + (blockIdx.y % nt) * 64, c0 = s0 + (blockIdx.y / nt) * 64;
-  if (r0 >= p && c0 >= p) return;  // entirely inside F22
-  C *fac = reinterpret_cast<C *>(a.fac);
+  const int i0 = (blockIdx.y % nt) * 64, j0 = (blockIdx.y / nt) * 64;
+  const C *fac = reinterpret_cast<const C *>(a.fac);
   const int64_t fo = f.fac_off;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-
   for (int idx = tid; idx < 64 * nbk; idx += 256) {
-    const int rr = idx % 64, j = idx / 64, r = r0 + rr;
-    C v = czero<C>();
-    if (r < n)
-      v = r < p ? fac[fo + (int64_t)(k + j) * p + r]
-                : fac[fo + (int64_t)p * n + (int64_t)(k + j) * b + (r - p)];
-    As[rr][j] = v;
+    const int rr = idx % 64, j = idx / 64, ri = i0 + rr;
+    As[rr][j] = ri < m ? ld_elem<C>(a, f, unband(ri, k, nbk), k + j) : czero<C>();
   }
   for (int idx = tid; idx < 64 * nbk; idx += 256) {
-    const int j = idx % nbk, cc = idx / nbk, c = c0 + cc;
-    Bs[j][cc] = c < n ? fac[fo + (int64_t)c * p + k + j] : czero<C>();
+    const int j = idx % nbk, cc = idx / nbk, ci = j0 + cc;
+    Bs[j][cc] = ci < m ? fac[fo + (int64_t)unband(ci, k, nbk) * p + k + j] : czero<C>();
   }
   __syncthreads();
   C acc[4][4];
@@ -313,297 +363,212 @@ __global__ void __launch_bounds__(256) mf_update(MfArgs a, int f0, int k) {
   tile_mma<C>(As, Bs, nbk, acc, tx, ty);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int r = r0 + ty + 16 * i;
-    if (r >= n) continue;
+    const int ri = i0 + ty + 16 * i;
+    if (ri >= m) continue;
+    const int r = unband(ri, k, nbk);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int c = c0 + tx + 16 * j;
-      if (c >= n || (r >= p && c >= p)) continue;
-      const int64_t off = r < p ? fo + (int64_t)c * p + r
-                                : fo + (int64_t)p * n + (int64_t)c * b + (r - p);
-      fac[off] = csub(fac[off], acc[i][j]);
+      const int ci = j0 + tx + 16 * j;
+      if (ci >= m) continue;
+      const int c = unband(ci, k, nbk);
+      st_elem<C>(a, f, r, c, cadd(ld_elem<C>(a, f, r, c), acc[i][j]));
     }
   }
 }
 
-// ------------------------------------------------------ Schur complement
-// F22 -= L21 U12 (b x b x p), one 64 x 64 tile of one front per CTA.
+// ------------------------------------------------------- substitutions
+// Work items are (front, 32-row chunk); one warp per item, 4 warps per CTA.
+// Going up: lane = border row r of the chunk; w_p is gathered 32 pivots at a
+// time (t at the pivot nodes + the children's update vectors through the
+// inverse extend-add maps) and broadcast by shuffles; chunk 0 also stores w_p
+// for the way down.  u[r] = w_b[r] + sum_j (-G21)(r, j) w_p[j].
 template <typename R>
-__global__ void __launch_bounds__(256) mf_schur(MfArgs a, int f0) {
+__global__ void __launch_bounds__(128) mf_up(MfArgs a, const int2 *__restrict__ items, int nitems, int nrhs,
+                                             int64_t ldt) {
   using C = typename CT<R>::T;
-  constexpr int NB = MF_NB;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C(*As)[NB + 1] = reinterpret_cast<C(*)[NB + 1]>(smem_raw);
-  C(*Bs)[64 + 1] = reinterpret_cast<C(*)[64 + 1]>(smem_raw + sizeof(C) * 64 * (NB + 1));
-
-  const FrontDev f = a.fronts[f0 + blockIdx.x];
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= nitems) return;
+  const int2 item = items[it];
+  const FrontDev f = a.fronts[item.x];
   const int p = f.p, b = f.b, n = p + b;
-  if (b == 0) return;
-  const int nt = (b + 63) / 64;
-  if ((int)blockIdx.y >= nt * nt) return;
-  const int r0 = (blockIdx.y % nt) * 64, c0 = (blockIdx.y / nt) * 64;
-  const C *fac = reinterpret_cast<const C *>(a.fac);
-  C *ws = reinterpret_cast<C *>(a.ws_cur);
-  const int64_t L21 = f.fac_off + (int64_t)p * n;  // b x p, ld b
-  const int64_t U12 = f.fac_off + (int64_t)p * p;  // p x b, ld p
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  C acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = czero<C>();
-  for (int k0 = 0; k0 < p; k0 += NB) {
-    const int kb = min(NB, p - k0);
-    __syncthreads();
-    for (int idx = tid; idx < 64 * kb; idx += 256) {
-      const int rr = idx % 64, j = idx / 64, r = r0 + rr;
-      As[rr][j] = r < b ? fac[L21 + (int64_t)(k0 + j) * b + r] : czero<C>();
-    }
-    for (int idx = tid; idx < 64 * kb; idx += 256) {
-      const int j = idx % kb, cc = idx / kb, c = c0 + cc;
-      Bs[j][cc] = c < b ? fac[U12 + (int64_t)c * p + k0 + j] : czero<C>();
-    }
-    __syncthreads();
-    tile_mma<C>(As, Bs, kb, acc, tx, ty);
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = r0 + ty + 16 * i;
-    if (r >= b) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = c0 + tx + 16 * j;
-      if (c >= b) continue;
-      const int64_t off = f.s_off + (int64_t)c * b + r;
-      ws[off] = csub(ws[off], acc[i][j]);
-    }
-  }
-}
-
-// ----------------------------------------------------- forward solve
-// One CTA per front.  w = [t(pivots); 0] + sum_children extend(u_child);
-// y = L11^-1 w_piv (unit lower, column-oriented in blocks of 32: warp 0
-// solves the diagonal block with shuffles, all warps update the rows below);
-// u = w_border - L21 y goes to the parent; y overwrites t at the pivots.
-template <typename R>
-__global__ void __launch_bounds__(256) mf_forward(MfArgs a, int f0, int nrhs, int64_t ldt) {
-  using C = typename CT<R>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const FrontDev f = a.fronts[f0 + blockIdx.x];
-  const int p = f.p, b = f.b, n = p + b;
-  C *w = reinterpret_cast<C *>(smem_raw);  // [nrhs][n]
-  C *tv = reinterpret_cast<C *>(a.tloc);
   const StripDev s = a.strips[f.strip];
-  const C *fac = reinterpret_cast<const C *>(a.fac);
-  const int64_t fo = f.fac_off;
-  const int tid = threadIdx.x;
-
-  for (int idx = tid; idx < n * nrhs; idx += blockDim.x) {
-    const int q = idx / n, k = idx - q * n;
-    w[idx] = k < p ? tv[q * ldt + s.vec_off + a.nodes[f.node_off + k]] : czero<C>();
-  }
-  __syncthreads();
+  const C *tv = reinterpret_cast<const C *>(a.tloc);
+  C *wl = reinterpret_cast<C *>(a.wloc);
+  const C *G = reinterpret_cast<const C *>(a.fac) + f.fac_off + (int64_t)p * n;  // -G21, b x p, ld b
+  const int r = item.y * 32 + lane;
+  const bool row = r < b;
+  const C *uc[2] = {nullptr, nullptr};
+  int bc[2] = {0, 0};
+  const int *inv[2] = {nullptr, nullptr};
+#pragma unroll
   for (int ci = 0; ci < 2; ++ci) {
-    if (f.child[ci] < 0) continue;
-    const FrontDev ch = a.fronts[f.child[ci]];
-    const C *uc = reinterpret_cast<const C *>(a.ub_child) + ch.u_off * nrhs;
-    for (int idx = tid; idx < ch.b * nrhs; idx += blockDim.x) {
-      const int q = idx / ch.b, k = idx - q * ch.b;
-      const int at = a.cmap[f.cmap_off[ci] + k];
-      w[q * n + at] = cadd(w[q * n + at], uc[(int64_t)q * ch.b + k]);
+    if (f.child[ci] >= 0) {
+      const FrontDev ch = a.fronts[f.child[ci]];
+      bc[ci] = ch.b;
+      uc[ci] = reinterpret_cast<const C *>(a.ub_child) + ch.u_off * nrhs;
+      inv[ci] = a.inv + f.inv_off[ci];
     }
-    __syncthreads();
   }
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int J = 0; J < p; J += 32) {
-    const int jb = min(32, p - J);
-    if (warp == 0) {
-      C Lrow[32];
+  const int *nodes = a.nodes + f.node_off;
+  C *u = reinterpret_cast<C *>(a.ub_cur) + f.u_off * nrhs;
+  for (int q = 0; q < nrhs; ++q) {
+    C acc = czero<C>();
+    if (row) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        Lrow[j] = (j < jb && lane < jb) ? fac[fo + (int64_t)(J + j) * p + J + lane] : czero<C>();
-      for (int q = 0; q < nrhs; ++q) {
-        C x = lane < jb ? w[q * n + J + lane] : czero<C>();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const C yj = shfl(x, j);
-          if (lane > j && j < jb) x = cfms(Lrow[j], yj, x);
+      for (int ci = 0; ci < 2; ++ci)
+        if (uc[ci]) {
+          const int t = inv[ci][p + r];
+          if (t >= 0) acc = cadd(acc, uc[ci][(int64_t)q * bc[ci] + t]);
         }
-        if (lane < jb) w[q * n + J + lane] = x;
+    }
+    for (int j0 = 0; j0 < p; j0 += 32) {
+      const int j = j0 + lane;
+      C wj = czero<C>();
+      if (j < p) {
+        const int64_t gi = q * ldt + s.vec_off + nodes[j];
+        wj = tv[gi];
+#pragma unroll
+        for (int ci = 0; ci < 2; ++ci)
+          if (uc[ci]) {
+            const int t = inv[ci][j];
+            if (t >= 0) wj = cadd(wj, uc[ci][(int64_t)q * bc[ci] + t]);
+          }
+        if (item.y == 0) wl[gi] = wj;
+      }
+      const int jb = min(32, p - j0);
+      if (jb == 32) {
+#pragma unroll 8
+        for (int jj = 0; jj < 32; ++jj) {
+          const C wv = shfl(wj, jj);
+          if (row) acc = cfma(G[(int64_t)(j0 + jj) * b + r], wv, acc);
+        }
+      } else {
+        for (int jj = 0; jj < jb; ++jj) {
+          const C wv = shfl(wj, jj);
+          if (row) acc = cfma(G[(int64_t)(j0 + jj) * b + r], wv, acc);
+        }
       }
     }
-    __syncthreads();
-    for (int r = J + jb + tid; r < p; r += blockDim.x) {
-      for (int q = 0; q < nrhs; ++q) {
-        C acc = w[q * n + r];
-        for (int j = 0; j < jb; ++j) acc = cfms(fac[fo + (int64_t)(J + j) * p + r], w[q * n + J + j], acc);
-        w[q * n + r] = acc;
-      }
-    }
-    __syncthreads();
-  }
-  // border update u = w_b - L21 y, and y back to the local vector
-  C *ub = reinterpret_cast<C *>(a.ub_cur) + f.u_off * nrhs;
-  const int64_t L21 = fo + (int64_t)p * n;
-  for (int r = tid; r < b; r += blockDim.x) {
-    for (int q = 0; q < nrhs; ++q) {
-      C acc = w[q * n + p + r];
-      for (int j = 0; j < p; ++j) acc = cfms(fac[L21 + (int64_t)j * b + r], w[q * n + j], acc);
-      ub[(int64_t)q * b + r] = acc;
-    }
-  }
-  for (int idx = tid; idx < p * nrhs; idx += blockDim.x) {
-    const int q = idx / p, k = idx - q * p;
-    tv[q * ldt + s.vec_off + a.nodes[f.node_off + k]] = w[q * n + k];
+    if (row) u[(int64_t)q * b + r] = acc;
   }
 }
 
-// ----------------------------------------------------- backward solve
-// One CTA per front, root level first.  z = y - U12 x_border (x_border read
-// from the local vector, already final), then x = U11^-1 z by 32-blocks from
-// the bottom; x overwrites y at the pivots.
+// Coming down: lane = pivot row r of the chunk;
+// x[r] = sum_{c<p} Finv(r, c) w_p[c] - sum_{c>=p} H12(r, c) x_b[c].
 template <typename R>
-__global__ void __launch_bounds__(256) mf_backward(MfArgs a, int f0, int nrhs, int64_t ldt) {
+__global__ void __launch_bounds__(128) mf_down(MfArgs a, const int2 *__restrict__ items, int nitems, int nrhs,
+                                               int64_t ldt) {
   using C = typename CT<R>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const FrontDev f = a.fronts[f0 + blockIdx.x];
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= nitems) return;
+  const int2 item = items[it];
+  const FrontDev f = a.fronts[item.x];
   const int p = f.p, b = f.b, n = p + b;
-  C *w = reinterpret_cast<C *>(smem_raw);  // [nrhs][n]: z then x_border
-  C *tv = reinterpret_cast<C *>(a.tloc);
   const StripDev s = a.strips[f.strip];
-  const C *fac = reinterpret_cast<const C *>(a.fac);
-  const int64_t fo = f.fac_off;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < n * nrhs; idx += blockDim.x) {
-    const int q = idx / n, k = idx - q * n;
-    w[idx] = tv[q * ldt + s.vec_off + a.nodes[f.node_off + k]];
-  }
-  __syncthreads();
-  const int64_t U12 = fo + (int64_t)p * p;
-  for (int r = tid; r < p; r += blockDim.x) {
-    for (int q = 0; q < nrhs; ++q) {
-      C acc = w[q * n + r];
-      for (int j = 0; j < b; ++j) acc = cfms(fac[U12 + (int64_t)j * p + r], w[q * n + p + j], acc);
-      w[q * n + r] = acc;
-    }
-  }
-  __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5;
-  const int nblk = (p + 31) / 32;
-  for (int bi = nblk - 1; bi >= 0; --bi) {
-    const int J = bi * 32;
-    const int jb = min(32, p - J);
-    if (warp == 0) {
-      C Urow[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        Urow[j] = (j < jb && lane < jb) ? fac[fo + (int64_t)(J + j) * p + J + lane] : czero<C>();
-      // lane j needs 1/U(j,j): the diagonal entry is Urow[lane] on lane `lane`
-      C dg = czero<C>();
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j == lane) dg = Urow[j];
-      const C dinv = lane < jb ? crecip(dg) : czero<C>();
-      for (int q = 0; q < nrhs; ++q) {
-        C x = lane < jb ? w[q * n + J + lane] : czero<C>();
-#pragma unroll
-        for (int j = 31; j >= 0; --j) {
-          if (j < jb) {
-            if (lane == j) x = cmul(x, dinv);
-            const C xj = shfl(x, j);
-            if (lane < j) x = cfms(Urow[j], xj, x);
-          }
+  C *tv = reinterpret_cast<C *>(a.tloc);
+  const C *wl = reinterpret_cast<const C *>(a.wloc);
+  const C *Fm = reinterpret_cast<const C *>(a.fac) + f.fac_off;  // p x n, ld p
+  const int r = item.y * 32 + lane;
+  const bool row = r < p;
+  const int *nodes = a.nodes + f.node_off;
+  for (int q = 0; q < nrhs; ++q) {
+    const int64_t base = q * ldt + s.vec_off;
+    C acc = czero<C>();
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      const int c = c0 + lane;
+      C v = czero<C>();
+      if (c < p) v = wl[base + nodes[c]];
+      else if (c < n) v = cneg(tv[base + nodes[c]]);
+      const int cb = min(32, n - c0);
+      if (cb == 32) {
+#pragma unroll 8
+        for (int cc = 0; cc < 32; ++cc) {
+          const C vv = shfl(v, cc);
+          if (row) acc = cfma(Fm[(int64_t)(c0 + cc) * p + r], vv, acc);
         }
-        if (lane < jb) w[q * n + J + lane] = x;
+      } else {
+        for (int cc = 0; cc < cb; ++cc) {
+          const C vv = shfl(v, cc);
+          if (row) acc = cfma(Fm[(int64_t)(c0 + cc) * p + r], vv, acc);
+        }
       }
     }
-    __syncthreads();
-    for (int r = tid; r < J; r += blockDim.x) {
-      for (int q = 0; q < nrhs; ++q) {
-        C acc = w[q * n + r];
-        for (int j = 0; j < jb; ++j) acc = cfms(fac[fo + (int64_t)(J + j) * p + r], w[q * n + J + j], acc);
-        w[q * n + r] = acc;
-      }
-    }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < p * nrhs; idx += blockDim.x) {
-    const int q = idx / p, k = idx - q * p;
-    tv[q * ldt + s.vec_off + a.nodes[f.node_off + k]] = w[q * n + k];
+    if (row) tv[base + nodes[r]] = acc;
   }
 }
 
 // ------------------------------------------------------------ launchers
-template <typename R>
-static size_t panel_smem() {
+template <typename R> static size_t small_smem() {
   using C = typename CT<R>::T;
-  return sizeof(C) * (MF_NB * (MF_NB + 1) + MF_NB + MF_PANEL_THREADS * (MF_NB + 1));
+  return sizeof(C) * (MF_SMALL * MF_SMALL + 2 * MF_SMALL);
 }
-template <typename R>
-static size_t gemm_smem() {
+template <typename R> static size_t row_smem() {
+  using C = typename CT<R>::T;
+  return sizeof(C) * (MF_NB * (MF_NB + 1) + MF_PANEL_THREADS * (MF_NB + 1));
+}
+template <typename R> static size_t gemm_smem() {
   using C = typename CT<R>::T;
   return sizeof(C) * (64 * (MF_NB + 1) + MF_NB * (64 + 1));
 }
 
-template <typename R>
-cudaError_t mf_setup_attributes() {
+template <typename R> cudaError_t mf_setup_attributes() {
   cudaError_t e;
-  e = cudaFuncSetAttribute(mf_panel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem<R>());
+  e = cudaFuncSetAttribute(mf_gj_small<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem<R>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(mf_update<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<R>());
+  e = cudaFuncSetAttribute(mf_gj_row<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem<R>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(mf_schur<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<R>());
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(mf_forward<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(mf_backward<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return cudaFuncSetAttribute(mf_gj_update<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<R>());
 }
 
-template <typename R>
-void mf_factor_level(const MfArgs &a, const LevelInfo &L, cudaStream_t st) {
+template <typename R> void mf_factor_level(const MfArgs &a, const LevelInfo &L, cudaStream_t st) {
   if (L.nf == 0) return;
   {
     const int64_t nn = (int64_t)L.max_n * L.max_n;
-    int gx = (int)std::min<int64_t>((nn + 255) / 256, 4096);
-    mf_assemble<R><<<dim3(L.nf, gx), 256, 0, st>>>(a, L.f0);
+    const int gy = (int)std::min<int64_t>((nn + 255) / 256, 4096);
+    mf_assemble<R><<<dim3(L.nf, gy), 256, 0, st>>>(a, L.f0);
+    count_launch();
   }
-  for (int k = 0; k < L.max_p; k += MF_NB) {
-    const int rem = L.max_n - k - 1;
-    const int ntr = std::max(1, (rem + MF_PANEL_THREADS - 1) / MF_PANEL_THREADS);
-    mf_diag<R><<<L.nf, MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
-    mf_panel<R><<<dim3(L.nf, 2 * ntr), MF_PANEL_THREADS, panel_smem<R>(), st>>>(a, L.f0, k);
-    const int nt = std::max(1, (rem + 63) / 64);
-    mf_update<R><<<dim3(L.nf, nt * nt), 256, gemm_smem<R>(), st>>>(a, L.f0, k);
+  if (L.min_n <= MF_SMALL) {
+    mf_gj_small<R><<<L.nf, MF_SMALL_THREADS, small_smem<R>(), st>>>(a, L.f0);
+    count_launch();
   }
-  if (L.max_b > 0) {
-    const int nt = (L.max_b + 63) / 64;
-    mf_schur<R><<<dim3(L.nf, nt * nt), 256, gemm_smem<R>(), st>>>(a, L.f0);
+  if (L.max_n > MF_SMALL) {
+    for (int k = 0; k < L.max_p; k += MF_NB) {
+      const int m = L.max_n - std::min(MF_NB, std::max(1, L.max_p - k));
+      const int tiles = std::max(1, (m + MF_PANEL_THREADS - 1) / MF_PANEL_THREADS);
+      const int nt = std::max(1, (m + 63) / 64);
+      mf_gj_diag<R><<<L.nf, MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
+      mf_gj_col<R><<<dim3(L.nf, tiles), MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
+      mf_gj_update<R><<<dim3(L.nf, nt * nt), 256, gemm_smem<R>(), st>>>(a, L.f0, k);
+      mf_gj_row<R><<<dim3(L.nf, tiles), MF_PANEL_THREADS, row_smem<R>(), st>>>(a, L.f0, k);
+      count_launch(4);
+    }
   }
 }
 
 template <typename R>
-void mf_forward_level(const MfArgs &a, const LevelInfo &L, int nrhs, int64_t ldt, cudaStream_t st) {
-  if (L.nf == 0) return;
-  using C = typename CT<R>::T;
-  const size_t sm = sizeof(C) * (size_t)L.max_n * nrhs;
-  mf_forward<R><<<L.nf, 256, sm, st>>>(a, L.f0, nrhs, ldt);
+void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int nrhs, int64_t ldt, cudaStream_t st) {
+  if (nitems == 0) return;
+  mf_up<R><<<(nitems + 3) / 4, 128, 0, st>>>(a, items, nitems, nrhs, ldt);
+  count_launch();
 }
 
 template <typename R>
-void mf_backward_level(const MfArgs &a, const LevelInfo &L, int nrhs, int64_t ldt, cudaStream_t st) {
-  if (L.nf == 0) return;
-  using C = typename CT<R>::T;
-  const size_t sm = sizeof(C) * (size_t)L.max_n * nrhs;
-  mf_backward<R><<<L.nf, 256, sm, st>>>(a, L.f0, nrhs, ldt);
+void mf_down_level(const MfArgs &a, const int2 *items, int nitems, int nrhs, int64_t ldt, cudaStream_t st) {
+  if (nitems == 0) return;
+  mf_down<R><<<(nitems + 3) / 4, 128, 0, st>>>(a, items, nitems, nrhs, ldt);
+  count_launch();
 }
 
 template cudaError_t mf_setup_attributes<double>();
 template cudaError_t mf_setup_attributes<float>();
 template void mf_factor_level<double>(const MfArgs &, const LevelInfo &, cudaStream_t);
 template void mf_factor_level<float>(const MfArgs &, const LevelInfo &, cudaStream_t);
-template void mf_forward_level<double>(const MfArgs &, const LevelInfo &, int, int64_t, cudaStream_t);
-template void mf_forward_level<float>(const MfArgs &, const LevelInfo &, int, int64_t, cudaStream_t);
-template void mf_backward_level<double>(const MfArgs &, const LevelInfo &, int, int64_t, cudaStream_t);
-template void mf_backward_level<float>(const MfArgs &, const LevelInfo &, int, int64_t, cudaStream_t);
+template void mf_up_level<double>(const MfArgs &, const int2 *, int, int, int64_t, cudaStream_t);
+template void mf_up_level<float>(const MfArgs &, const int2 *, int, int, int64_t, cudaStream_t);
+template void mf_down_level<double>(const MfArgs &, const int2 *, int, int, int64_t, cudaStream_t);
+template void mf_down_level<float>(const MfArgs &, const int2 *, int, int, int64_t, cudaStream_t);
 
 }  // namespace stdd
