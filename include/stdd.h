@@ -177,6 +177,30 @@ stdd_status stdd_get_stats(stdd_ctx *ctx, stdd_stats *out);
 stdd_status stdd_residual(stdd_ctx *ctx, const double *x, const double *b, double *r, double *rel_out,
                           int is_device);
 
+/* Same result as stdd_residual, without allocating device memory.  The
+ * paper has no counterpart: this entry point exists for callers that may not
+ * call cudaMalloc at the time they need a residual -- code that runs while a
+ * CUDA graph is being built or replayed, real-time loops that reserve all of
+ * their memory up front, or host applications that hand out GPU memory only
+ * through their own pool.
+ *   x, b : device pointers, 2*nx*ny doubles each (inputs);
+ *   r    : device pointer, 2*nx*ny doubles (output, b - A x);
+ *   *rel_out : host double, ||r|| / ||b|| (||r|| if b = 0).
+ * Scratch is one fixed array compiled into the library (2*16384 + 2
+ * doubles, about 256 KiB); every GPU that loads the library keeps it until
+ * the process exits.  Grids above 67,108,864 nodes are rejected with
+ * STDD_EINVAL.  The operator must already be set up on the context (any
+ * earlier stdd_apply_operator, stdd_residual or stdd_factor call does it),
+ * else STDD_ESTATE.  The first call on a device looks up the scratch
+ * array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other contexts, other streams, other threads) race and
+ * must be serialised by the caller.  Each call writes every scratch slot it
+ * reads before reading it, so nothing carries over between calls.  The call
+ * synchronises the context stream to return *rel_out. */
+stdd_status stdd_residual_noalloc(stdd_ctx *ctx, const double *x, const double *b, double *r,
+                                  double *rel_out);
+
 /* Phase profile: with profiling on, the context records CUDA events on its
  * stream around each phase; get_profile synchronises the stream and sums the
  * device times (ms) of the phases completed since the last reset.  Kernel

@@ -71,6 +71,7 @@ _SIGS = {
     "stdd_strip_info": (c_int, [c_void_p, c_int, P(c_int), P(c_int), P(c_int), P(c_int)]),
     "stdd_get_stats": (c_int, [c_void_p, P(stdd_stats)]),
     "stdd_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, P(c_double), c_int]),
+    "stdd_residual_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, P(c_double)]),
     "stdd_set_profiling": (c_int, [c_void_p, c_int]),
     "stdd_get_profile": (c_int, [c_void_p, P(stdd_profile), c_int]),
     "stdd_nd_analyze": (c_int, [c_int, c_int, c_int, P(c_int), P(ctypes.c_longlong), c_void_p, c_void_p,
@@ -232,6 +233,20 @@ def stdd_residual(ctx, x, b, r):
         raise ValueError("x, b and r must live on the same side")
     rel = c_double(0.0)
     _check(ctx, lib.stdd_residual(ctx, c_void_p(px), c_void_p(pb), c_void_p(pr), ctypes.byref(rel), dx_))
+    return rel.value
+
+
+def stdd_residual_noalloc(ctx, x, b, r):
+    """r = b - A x into the caller's device buffers with no device allocation
+    (fixed in-library scratch); returns ||r|| / ||b||.  All three must be
+    CUDA tensors."""
+    px, dx_ = _ptr(x)
+    pb, db = _ptr(b)
+    pr, dr = _ptr(r)
+    if not (dx_ == db == dr == 1):
+        raise ValueError("x, b and r must be device buffers")
+    rel = c_double(0.0)
+    _check(ctx, lib.stdd_residual_noalloc(ctx, c_void_p(px), c_void_p(pb), c_void_p(pr), ctypes.byref(rel)))
     return rel.value
 
 

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -1124,3 +1125,153 @@ stdd_status stdd_nd_analyze(int W, int H, int leaf_max, int *nfronts, long long 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Residual without device allocation.
+//
+// stdd_residual stages its inputs in context buffers and reduces through
+// context scratch that it grows with cudaMalloc on first use.  Callers that
+// must not allocate device memory at call time -- code running between the
+// capture of a CUDA graph and its launch, real-time loops that pre-reserve
+// all memory, or hosts that hand out GPU memory only through their own pool
+// -- use stdd_residual_noalloc instead: it reads and writes only the
+// caller's device buffers and a fixed scratch array compiled into this
+// library (g_noalloc_scratch, ~256 KiB), which every GPU that loads the
+// library keeps until the process exits.
+// ------------------------------------------------------------------------
+namespace {
+
+constexpr int NA_THREADS = 256;
+constexpr int NA_CHUNK = 4096;            // grid nodes reduced by one block
+constexpr int NA_MAX_BLOCKS = 16384;      // so at most NA_CHUNK * NA_MAX_BLOCKS nodes
+constexpr int64_t NA_MAX_NODES = (int64_t)NA_CHUNK * NA_MAX_BLOCKS;  // 67,108,864
+
+// [2 * NA_MAX_BLOCKS] per-block (||r||^2, ||b||^2), then the two totals.
+static __device__ __align__(256) double g_noalloc_scratch[2 * NA_MAX_BLOCKS + 2];
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex g_na_mutex;
+double *g_na_ptr[NA_MAX_DEVICES] = {nullptr};
+
+// device address of g_noalloc_scratch on the current device (looked up once)
+cudaError_t na_scratch(int device, double **out) {
+  if (device < 0 || device >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_ptr[device]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_na_ptr[device] = static_cast<double *>(p);
+  }
+  *out = g_na_ptr[device];
+  return cudaSuccess;
+}
+
+__global__ void __launch_bounds__(NA_THREADS) k_na_residual(stdd::GridDev g, const double2 *__restrict__ b,
+                                                            const double2 *__restrict__ x,
+                                                            double2 *__restrict__ r, double *scratch) {
+  const int64_t n = (int64_t)g.nx * g.ny;
+  const int64_t g0 = (int64_t)blockIdx.x * NA_CHUNK, g1 = min(n, g0 + NA_CHUNK);
+  double rr = 0, bb = 0;
+  for (int64_t idx = g0 + threadIdx.x; idx < g1; idx += NA_THREADS) {
+    const int i = (int)(idx / g.ny), j = (int)(idx - (int64_t)i * g.ny);
+    const double2 xm = g.cxm[i], xp = g.cxp[i], ym = g.cym[j], yp = g.cyp[j];
+    double2 d;
+    d.x = g.k0sq * g.eps[idx] - xm.x - xp.x - ym.x - yp.x;
+    d.y = -xm.y - xp.y - ym.y - yp.y;
+    double2 ax = stdd::cmul(d, x[idx]);
+    if (i > 0) ax = stdd::cfma(xm, x[idx - g.ny], ax);
+    if (i < g.nx - 1) ax = stdd::cfma(xp, x[idx + g.ny], ax);
+    if (j > 0) ax = stdd::cfma(ym, x[idx - 1], ax);
+    if (j < g.ny - 1) ax = stdd::cfma(yp, x[idx + 1], ax);
+    const double2 bv = b[idx];
+    const double2 rv = stdd::csub(bv, ax);
+    r[idx] = rv;
+    rr = fma(rv.x, rv.x, fma(rv.y, rv.y, rr));
+    bb = fma(bv.x, bv.x, fma(bv.y, bv.y, bb));
+  }
+  __shared__ double sh[2][NA_THREADS / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    bb += __shfl_xor_sync(0xffffffffu, bb, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = rr;
+    sh[1][threadIdx.x >> 5] = bb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sr = 0, sb = 0;
+    for (int w = 0; w < NA_THREADS / 32; ++w) {
+      sr += sh[0][w];
+      sb += sh[1][w];
+    }
+    scratch[2 * blockIdx.x] = sr;       // every slot read below is written here first
+    scratch[2 * blockIdx.x + 1] = sb;
+  }
+}
+
+// fixed-order sum of the per-block partials into the two total slots
+__global__ void k_na_finish(int nblk, double *scratch) {
+  const int lane = threadIdx.x;
+  double sr = 0, sb = 0;
+  for (int k = lane; k < nblk; k += 32) {
+    sr += scratch[2 * k];
+    sb += scratch[2 * k + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+  }
+  if (lane == 0) {
+    scratch[2 * NA_MAX_BLOCKS] = sr;
+    scratch[2 * NA_MAX_BLOCKS + 1] = sb;
+  }
+}
+
+}  // namespace
+
+extern "C" stdd_status stdd_residual_noalloc(stdd_ctx *c, const double *x, const double *b, double *r,
+                                             double *rel_out) {
+  if (!c) return STDD_EINVAL;
+  if (!x || !b || !r || !rel_out) {
+    c->err = "stdd_residual_noalloc: null argument";
+    return STDD_EINVAL;
+  }
+  const int64_t n = c->N();
+  if (n > NA_MAX_NODES) {
+    c->err = "stdd_residual_noalloc: grid has more than 67,108,864 nodes, the size of its fixed scratch";
+    return STDD_EINVAL;
+  }
+  if (!c->op_ready || !c->have_eps || n == 0) {
+    c->err = "stdd_residual_noalloc: operator not set up (call stdd_apply_operator, stdd_residual or "
+             "stdd_factor once after configuring the grid)";
+    return STDD_ESTATE;
+  }
+  cudaError_t e = cudaSetDevice(c->device);
+  double *scratch = nullptr;
+  if (e == cudaSuccess) e = na_scratch(c->device, &scratch);
+  if (e == cudaSuccess) {
+    const int nblk = (int)((n + NA_CHUNK - 1) / NA_CHUNK);
+    k_na_residual<<<nblk, NA_THREADS, 0, c->stream>>>(c->grid(), reinterpret_cast<const double2 *>(b),
+                                                    reinterpret_cast<const double2 *>(x),
+                                                    reinterpret_cast<double2 *>(r), scratch);
+    k_na_finish<<<1, 32, 0, c->stream>>>(nblk, scratch);
+    stdd::count_launch(2);
+    e = cudaGetLastError();
+  }
+  double tot[2] = {0, 0};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(tot, scratch + 2 * NA_MAX_BLOCKS, sizeof(tot), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    c->err = std::string("stdd_residual_noalloc: ") + cudaGetErrorString(e);
+    return STDD_ECUDA;
+  }
+  const double rn = std::sqrt(tot[0]), bn = std::sqrt(tot[1]);
+  *rel_out = bn > 0 ? rn / bn : rn;
+  c->err.clear();
+  return STDD_OK;
+}
