@@ -97,10 +97,8 @@ void nd_analyze(int W, int H, int leaf_max, Shape &S) {
     f.fac_off = off;
     const int64_t p = f.p, b = f.b, n = p + b;
     off += p * (p + 2 * b);
-    // right-looking elimination of p pivots from an n x n front
-    double macs = 0;
-    for (int64_t k = 0; k < p; ++k) macs += double(n - 1 - k) * double(n - 1 - k);
-    S.factor_cflops += macs;
+    // Gauss-Jordan sweep of p pivots over the whole n x n front
+    S.factor_cflops += double(p) * double(n) * double(n);
     S.solve_cflops += double(p) * double(p) + 2.0 * double(p) * double(b);
     if (f.level + 1 > S.depth) S.depth = f.level + 1;
     if (f.p > S.max_p) S.max_p = f.p;

@@ -35,7 +35,7 @@ struct Shape {
   std::vector<int> inv;
   int depth = 0;                    // number of levels
   int64_t factor_entries = 0;       // sum p*(p + 2b)
-  double factor_cflops = 0;         // complex multiply-adds of the factorization
+  double factor_cflops = 0;         // complex multiply-adds of the factorization (sum p n^2)
   double solve_cflops = 0;          // complex multiply-adds of one fwd+bwd solve
   int max_p = 0, max_b = 0;
 };
