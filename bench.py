@@ -45,7 +45,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "c64"])
-    ap.add_argument("--workload", default="metalens", choices=["metalens", "cylinder"])
+    ap.add_argument("--workload", default="metalens", choices=["metalens", "metalens-small", "cylinder"],
+                    help="metalens: 4096x1024, 16 strips (the benchmark); metalens-small: 1024x1024, 4 strips "
+                         "(profiling captures); cylinder: 200x200, 2 strips")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -54,7 +56,11 @@ def parse():
 
 def make_workload(name):
     import workloads as W
-    return W.metalens() if name == "metalens" else W.cylinder()
+    if name == "metalens":
+        return W.metalens()
+    if name == "metalens-small":
+        return W.metalens(nx=1024, ny=1024, nsub=4)
+    return W.cylinder()
 
 
 def workload_desc(w):
@@ -292,31 +298,55 @@ def run_ours(args, rank, world, local_rank):
         phases["stencil_matvec"] = dict(ms_per_call=t * 1e3, calls_per_step=prof["matvec_calls"] / steps,
                                         bytes_per_call=40 * w.n, gbs=40 * w.n / t / 1e9)
     if prof["ortho_calls"]:
-        # CGS2 at basis size j+1: 2 x (dot over j+1 vectors + axpy over j+1
-        # vectors) = 4 (j+1) N complex multiply-adds, reading 4 (j+1) N + 4 N
-        # complex128 values and writing 2 N
+        # one classical Gram-Schmidt pass at basis size m = j+1: a multi-dot
+        # (m N complex multiply-adds, reading m+1 vectors) and a multi-axpy
+        # (m N, reading m+1 vectors and writing one); the first pass also
+        # forms ||w||^2.  Second passes (selective reorthogonalisation) are
+        # counted from the solver's statistics, assumed at the mean basis size.
         calls = prof["ortho_calls"]
-        js = [j % RESTART for j in range(its)] * steps
-        fl = sum(8 * 4 * (j + 1) * w.n for j in js)
-        by = sum(16 * ((4 * (j + 1) + 6) * w.n) for j in js)
+        js = [j % RESTART for j in range(its)]
+        extra = st.get("reorth_passes", 0)
+        mean_m = sum(j + 1 for j in js) / max(1, len(js))
+        fl = (sum(16 * (j + 1) * w.n for j in js) + extra * 16 * mean_m * w.n) * steps
+        by = (sum(16 * (2 * (j + 1) + 3) * w.n for j in js) + extra * 16 * (2 * mean_m + 3) * w.n) * steps
         t = prof["ortho_ms"] * 1e-3
         phases["gram_schmidt"] = dict(ms_per_call=t / calls * 1e3, calls_per_step=calls / steps,
-                                      gbs=by / t / 1e9, tflops=fl / t / 1e12)
-    dom = max(phases, key=lambda k: phases[k]["ms_per_call"] * phases[k]["calls_per_step"])
-    d = phases[dom]
-    if dom == "substitution_sweep" and prec == S.STDD_PREC_C64:
-        roof = dict(bound="hbm", achieved=d["gbs"], peak=peaks["hbm_gbs"], unit="GB/s",
-                    peak_source=peaks["source_hbm"])
-    elif dom == "stencil_matvec":
-        roof = dict(bound="hbm", achieved=d["gbs"], peak=peaks["hbm_gbs"], unit="GB/s",
-                    peak_source=peaks["source_hbm"])
-    else:
-        alu64 = prec == S.STDD_PREC_FP64 or dom == "gram_schmidt"
-        pk = fp64_tf if alu64 else fp32_tf
-        roof = dict(bound="alu", achieved=d["tflops"], peak=pk, unit="TFLOP/s",
-                    peak_source=("measured cuBLAS DGEMM" if alu64 else "measured cuBLAS SGEMM"))
-    roof["frac"] = roof["achieved"] / roof["peak"]
+                                      reorth_passes_per_step=extra, gbs=by / t / 1e9, tflops=fl / t / 1e12)
+    # per-kernel rooflines from the launch-by-launch profile: the two
+    # Gauss-Jordan elimination kernels (flops, ALU-bound) and the two
+    # substitution sweeps (factor bytes; FP64 arithmetic is ALU-bound on this
+    # part at 0.5 flop/byte, complex64 is HBM-bound)
+    alu_pk = fp64_tf if prec == S.STDD_PREC_FP64 else fp32_tf
+    alu_src = "measured cuBLAS DGEMM" if prec == S.STDD_PREC_FP64 else "measured cuBLAS SGEMM"
+    kernels = {}
+
+    def add_kernel(name, ms, calls, units, kind):
+        if not calls:
+            return
+        t = ms * 1e-3 / calls
+        u = units / calls
+        if kind == "flops":
+            k = dict(bound="alu", achieved=u / t / 1e12, peak=alu_pk, unit="TFLOP/s", peak_source=alu_src)
+        elif prec == S.STDD_PREC_FP64:   # sweep, complex128: 8 flops per 16-byte entry
+            k = dict(bound="alu", achieved=u / 2 / t / 1e12, peak=fp64_tf, unit="TFLOP/s",
+                     peak_source="measured cuBLAS DGEMM")
+        else:
+            k = dict(bound="hbm", achieved=u / t / 1e9, peak=peaks["hbm_gbs"], unit="GB/s",
+                     peak_source=peaks["source_hbm"])
+        k.update(frac=k["achieved"] / k["peak"], ms_per_step=ms / steps, launches_per_step=calls / steps,
+                 units_per_launch=u, unit_kind=kind, ms_per_launch=t * 1e3)
+        kernels[name] = k
+
+    tname = "double" if prec == S.STDD_PREC_FP64 else "float"
+    add_kernel(f"mf_gj_update<{tname}>", prof["update_ms"], prof["update_calls"], prof["update_flops"], "flops")
+    add_kernel(f"mf_gj_small<{tname}>", prof["small_ms"], prof["small_calls"], prof["small_flops"], "flops")
+    add_kernel(f"mf_down<{tname}>", prof["down_ms"], prof["down_calls"], prof["down_bytes"], "bytes")
+    add_kernel(f"mf_up<{tname}>", prof["up_ms"], prof["up_calls"], prof["up_bytes"], "bytes")
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    d = kernels[dom]
+    roof = {k: d[k] for k in ("bound", "achieved", "peak", "unit", "frac", "peak_source")}
     roof["kernel"] = dom
+    roof["units_per_launch"] = d["units_per_launch"]
     roof["traffic"] = None
 
     out = {
@@ -342,6 +372,7 @@ def run_ours(args, rank, world, local_rank):
         "t_factor_ms": prof["factor_ms"] / args.steps,
         "t_solve_ms": prof["solve_ms"] / args.steps,
         "phases": phases,
+        "kernels": kernels,
         "roofline": roof,
         "gpu_launches": int(launches),
         "clocks": ck,

@@ -167,6 +167,7 @@ typedef struct {
   int iterations;             /* inner iterations of the last solve (rhs 0) */
   double final_residual;      /* true relative residual (rhs 0)             */
   double min_pivot;           /* smallest |pivot| seen by the factorization */
+  int reorth_passes;          /* second Gram-Schmidt passes in the last solve */
 } stdd_stats;
 
 stdd_status stdd_get_stats(stdd_ctx *ctx, stdd_stats *out);
@@ -215,6 +216,17 @@ typedef struct {
   int ortho_calls;
   double solve_ms;        /* whole stdd_solve calls                        */
   long long launches;     /* kernels of this library launched             */
+  /* the dominant kernels, launch by launch, with their algorithmic work:
+   * small-front and blocked-update eliminations (real flops), the upward
+   * and downward substitution sweeps (factor bytes read) */
+  double small_ms, small_flops;
+  int small_calls;
+  double update_ms, update_flops;
+  int update_calls;
+  double up_ms, up_bytes;
+  int up_calls;
+  double down_ms, down_bytes;
+  int down_calls;
 } stdd_profile;
 
 stdd_status stdd_set_profiling(stdd_ctx *ctx, int enable);

@@ -42,13 +42,18 @@ class stdd_stats(ctypes.Structure):
                 ("max_border", c_int), ("factor_entries", ctypes.c_longlong),
                 ("factor_flops", c_double), ("solve_flops", c_double),
                 ("local_dofs", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
-                ("iterations", c_int), ("final_residual", c_double), ("min_pivot", c_double)]
+                ("iterations", c_int), ("final_residual", c_double), ("min_pivot", c_double),
+                ("reorth_passes", c_int)]
 
 
 class stdd_profile(ctypes.Structure):
     _fields_ = [("factor_ms", c_double), ("minv_ms", c_double), ("minv_calls", c_int),
                 ("matvec_ms", c_double), ("matvec_calls", c_int), ("ortho_ms", c_double),
-                ("ortho_calls", c_int), ("solve_ms", c_double), ("launches", ctypes.c_longlong)]
+                ("ortho_calls", c_int), ("solve_ms", c_double), ("launches", ctypes.c_longlong),
+                ("small_ms", c_double), ("small_flops", c_double), ("small_calls", c_int),
+                ("update_ms", c_double), ("update_flops", c_double), ("update_calls", c_int),
+                ("up_ms", c_double), ("up_bytes", c_double), ("up_calls", c_int),
+                ("down_ms", c_double), ("down_bytes", c_double), ("down_calls", c_int)]
 
 
 _SIGS = {

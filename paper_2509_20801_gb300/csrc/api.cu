@@ -166,11 +166,11 @@ struct stdd_ctx {
   DBuf d_b, d_x, d_r, d_V, d_Z, d_w, d_part, d_h, d_nrm, d_y, d_pre, d_fpart;
   int V_cols = 0;
   std::vector<std::vector<double>> history;
-  int last_its = 0;
+  int last_its = 0, last_reorth = 0;
   double last_res = 0;
 
   // phase profiling (CUDA events on the context stream)
-  enum { PH_FACTOR = 0, PH_MINV, PH_MATVEC, PH_ORTHO, PH_SOLVE, PH_COUNT };
+  enum { PH_FACTOR = 0, PH_MINV, PH_MATVEC, PH_ORTHO, PH_SOLVE, PH_K0, PH_COUNT = PH_K0 + stdd::K_COUNT };
   bool prof = false;
   struct Span {
     int phase;
@@ -200,6 +200,32 @@ struct stdd_ctx {
   ~stdd_ctx() {
     for (auto e : ev_pool) cudaEventDestroy(e);
   }
+
+  // per-launch profiling of the dominant kernels: algorithmic work per
+  // launch from the host front list (flops for the eliminations, factor
+  // bytes for the substitution sweeps)
+  std::vector<double> unit_small, unit_up, unit_down;       // per level
+  std::vector<std::vector<double>> unit_update;             // per level, per step
+  std::vector<double> span_units;                           // parallel to spans
+  struct Hook : stdd::LaunchHook {
+    stdd_ctx *c = nullptr;
+    int open = -1;
+    void before(int kind, int level, int k) override {
+      if (!c->prof) return;
+      open = c->pbegin(PH_K0 + kind);
+      double u = 0;
+      if (kind == stdd::K_SMALL) u = c->unit_small[level];
+      else if (kind == stdd::K_UPDATE) u = c->unit_update[level][k / stdd::MF_NB];
+      else if (kind == stdd::K_UP) u = c->unit_up[level];
+      else u = c->unit_down[level];
+      c->span_units.resize(c->spans.size(), 0.0);
+      c->span_units[open] = u;
+    }
+    void after(int, int, int) override {
+      if (open >= 0) c->pend(open);
+      open = -1;
+    }
+  } hook;
 
   size_t elem() const { return prec == STDD_PREC_FP64 ? sizeof(double2) : sizeof(float2); }
   int64_t N() const { return (int64_t)nx * ny; }
@@ -373,7 +399,7 @@ void stdd_ctx::factor() {
   std::vector<std::vector<int>> inst(nsub);
   for (int k = 0; k < nsub; ++k) inst[k].assign(shapes[strips[k].W()].fronts.size(), -1);
   std::vector<FrontDev> fr;
-  levels.assign(depth, LevelInfo{0, 0, 0, 0, 0, 1 << 30, 0, 0, 0, 0});
+  levels.assign(depth, LevelInfo{0, 0, 0, 0, 0, 1 << 30, 0, 0, 0, 0, 32, 32, 1, 1});
   int64_t ws_need[2] = {0, 0};
   ub_elems[0] = ub_elems[1] = 0;
   for (int L = 0; L < depth; ++L) {
@@ -422,19 +448,54 @@ void stdd_ctx::factor() {
     }
   }
   nfronts = (int64_t)fr.size();
-  // substitution work items: (front, 32-row chunk) of the border going up
-  // (at least one per front: chunk 0 also stores w_p) and of the pivots
-  // coming down
+  // algorithmic work per launch for the profiler
+  {
+    const double E = (double)elem();
+    unit_small.assign(depth, 0.0);
+    unit_up.assign(depth, 0.0);
+    unit_down.assign(depth, 0.0);
+    unit_update.assign(depth, {});
+    for (int L = 0; L < depth; ++L) {
+      const LevelInfo &li = levels[L];
+      unit_update[L].assign((li.max_p + stdd::MF_NB - 1) / stdd::MF_NB + 1, 0.0);
+      for (int f = li.f0; f < li.f0 + li.nf; ++f) {
+        const double p = fr[f].p, b = fr[f].b, n = p + b;
+        unit_up[L] += E * b * p;
+        unit_down[L] += E * p * n;
+        if (n <= stdd::MF_SMALL) {
+          unit_small[L] += 8.0 * p * n * n;
+        } else {
+          for (int k = 0; k < fr[f].p; k += stdd::MF_NB) {
+            const double nbk = std::min(stdd::MF_NB, fr[f].p - k);
+            unit_update[L][k / stdd::MF_NB] += 8.0 * (n - nbk) * (n - nbk) * nbk;
+          }
+        }
+      }
+    }
+  }
+  // substitution work items: (front, row chunk) of the border going up (at
+  // least one per front: chunk 0 also stores w_p) and of the pivots coming
+  // down.  Levels whose row counts fit in 16 use 16-lane row groups (two
+  // fronts per warp); wide fronts split their columns over up to 8 row groups.
+  auto pow2_split = [](int cols, int rows) {
+    int want = (cols + 4 * rows - 1) / (4 * rows), s = 1;
+    while (s < want && s < 8) s *= 2;
+    return s;
+  };
   std::vector<int2> items;
   for (int L = 0; L < depth; ++L) {
     LevelInfo &li = levels[L];
+    li.rows_up = li.max_b <= 16 ? 16 : 32;
+    li.rows_down = li.max_p <= 16 ? 16 : 32;
+    li.split_up = pow2_split(li.max_p, li.rows_up);
+    li.split_down = pow2_split(li.max_n, li.rows_down);
     li.up_off = (int64_t)items.size();
     for (int f = li.f0; f < li.f0 + li.nf; ++f)
-      for (int c = 0; c < std::max(1, (fr[f].b + 31) / 32); ++c) items.push_back(make_int2(f, c));
+      for (int c = 0; c < std::max(1, (fr[f].b + li.rows_up - 1) / li.rows_up); ++c) items.push_back(make_int2(f, c));
     li.n_up = (int)((int64_t)items.size() - li.up_off);
     li.down_off = (int64_t)items.size();
     for (int f = li.f0; f < li.f0 + li.nf; ++f)
-      for (int c = 0; c < (fr[f].p + 31) / 32; ++c) items.push_back(make_int2(f, c));
+      for (int c = 0; c < (fr[f].p + li.rows_down - 1) / li.rows_down; ++c) items.push_back(make_int2(f, c));
     li.n_down = (int)((int64_t)items.size() - li.down_off);
   }
   std::vector<int> colstrip(nx);
@@ -476,7 +537,8 @@ template <typename R> void stdd_ctx::factor_t() {
   const int span = pbegin(PH_FACTOR);
   for (int L = depth - 1; L >= 0; --L) {
     MfArgs a = mf_args(L & 1, false);
-    stdd::mf_factor_level<R>(a, levels[L], stream);
+    hook.c = this;
+    stdd::mf_factor_level<R>(a, levels[L], L, stream, &hook);
     CK(cudaGetLastError());
   }
   pend(span);
@@ -490,10 +552,21 @@ template <typename R> void stdd_ctx::factor_t() {
 template <typename R> void stdd_ctx::solve_levels(int nr) {
   ensure_solve_buffers(nr);
   const int2 *items = d_items.as<int2>();
-  for (int L = depth - 1; L >= 0; --L)
-    stdd::mf_up_level<R>(mf_args(L & 1, true), items + levels[L].up_off, levels[L].n_up, nr, nloc, stream);
-  for (int L = 0; L < depth; ++L)
-    stdd::mf_down_level<R>(mf_args(L & 1, true), items + levels[L].down_off, levels[L].n_down, nr, nloc, stream);
+  hook.c = this;
+  for (int L = depth - 1; L >= 0; --L) {
+    const LevelInfo &li = levels[L];
+    hook.before(stdd::K_UP, L, 0);
+    stdd::mf_up_level<R>(mf_args(L & 1, true), items + li.up_off, li.n_up, li.rows_up, li.split_up, nr, nloc,
+                         stream);
+    hook.after(stdd::K_UP, L, 0);
+  }
+  for (int L = 0; L < depth; ++L) {
+    const LevelInfo &li = levels[L];
+    hook.before(stdd::K_DOWN, L, 0);
+    stdd::mf_down_level<R>(mf_args(L & 1, true), items + li.down_off, li.n_down, li.rows_down, li.split_down, nr,
+                           nloc, stream);
+    hook.after(stdd::K_DOWN, L, 0);
+  }
   CK(cudaGetLastError());
 }
 
@@ -590,7 +663,7 @@ void stdd_ctx::gmres(int rhs, const stdd_solve_opts &o, double2 *x) {
   double2 *h1 = d_h.as<double2>(), *h2 = h1 + (m + 2);
   double *nrm = d_nrm.as<double>();
   double *part = reinterpret_cast<double *>(d_part.p);
-  int its = 0;
+  int its = 0, reorth = 0;
   std::vector<cd> H((size_t)(m + 1) * m), g(m + 1), sn(m), hv(2 * (m + 2));
   std::vector<double> cs(m);
   while (true) {
@@ -613,17 +686,27 @@ void stdd_ctx::gmres(int rhs, const stdd_solve_opts &o, double2 *x) {
       sp = pbegin(PH_MATVEC);
       stdd::launch_stencil(grid(), zj, w, stream);
       pend(sp);
+      // classical Gram-Schmidt; a second pass only when the first one shrank
+      // ||w|| below 1/sqrt(2) of its value (Daniel-Gragg-Kaufman-Stewart)
       sp = pbegin(PH_ORTHO);
-      stdd::launch_mdot(V, n, j + 1, w, n, d_part.as<double2>(), h1, stream);
+      stdd::launch_mdot(V, n, j + 1, w, n, d_part.as<double2>(), h1, stream, 1);
       stdd::launch_maxpy_norm(V, n, j + 1, h1, w, n, part, nrm, stream);
-      stdd::launch_mdot(V, n, j + 1, w, n, d_part.as<double2>(), h2, stream);
-      stdd::launch_maxpy_norm(V, n, j + 1, h2, w, n, part, nrm, stream);
-      pend(sp);
       double nrm2 = 0;
-      CK(cudaMemcpyAsync(hv.data(), h1, sizeof(double2) * 2 * (m + 2), cudaMemcpyDeviceToHost, stream));
+      CK(cudaMemcpyAsync(hv.data(), h1, sizeof(double2) * (j + 2), cudaMemcpyDeviceToHost, stream));
       CK(cudaMemcpyAsync(&nrm2, nrm, sizeof(double), cudaMemcpyDeviceToHost, stream));
       CK(cudaStreamSynchronize(stream));
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hv[i] + hv[(m + 2) + i];
+      const double before2 = hv[j + 1].real();
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hv[i];
+      if (nrm2 < 0.5 * before2) {
+        stdd::launch_mdot(V, n, j + 1, w, n, d_part.as<double2>(), h2, stream);
+        stdd::launch_maxpy_norm(V, n, j + 1, h2, w, n, part, nrm, stream);
+        CK(cudaMemcpyAsync(hv.data() + (m + 2), h2, sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost, stream));
+        CK(cudaMemcpyAsync(&nrm2, nrm, sizeof(double), cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += hv[(m + 2) + i];
+        ++reorth;
+      }
+      pend(sp);
       const double hn = std::sqrt(nrm2);
       H[(size_t)(j + 1) * m + j] = hn;
       for (int i = 0; i < j; ++i) {
@@ -660,6 +743,7 @@ void stdd_ctx::gmres(int rhs, const stdd_solve_opts &o, double2 *x) {
     CK(cudaStreamSynchronize(stream));
   }
   last_its = its;
+  last_reorth = reorth;
 }
 
 // Algorithm 1 in residual form: x_{n+1} = x_n + M^-1 (b - A x_n) from x_0,
@@ -1038,6 +1122,7 @@ stdd_status stdd_get_stats(stdd_ctx *c, stdd_stats *o) {
     o->iterations = c->last_its;
     o->final_residual = c->last_res;
     o->min_pivot = c->min_pivot;
+    o->reorth_passes = c->last_reorth;
   });
 }
 
@@ -1071,9 +1156,11 @@ stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {
     if (!o) throw ArgError("null profile");
     std::memset(o, 0, sizeof(*o));
     CK(cudaStreamSynchronize(c->stream));
-    double t[stdd_ctx::PH_COUNT] = {0};
+    double t[stdd_ctx::PH_COUNT] = {0}, units[stdd_ctx::PH_COUNT] = {0};
     int cnt[stdd_ctx::PH_COUNT] = {0};
-    for (auto &sp : c->spans) {
+    c->span_units.resize(c->spans.size(), 0.0);
+    for (size_t si = 0; si < c->spans.size(); ++si) {
+      const auto &sp = c->spans[si];
       float ms = 0;
       if (cudaEventElapsedTime(&ms, sp.a, sp.b) != cudaSuccess) {  // span left open by a failed call
         (void)cudaGetLastError();
@@ -1081,7 +1168,21 @@ stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {
       }
       t[sp.phase] += ms;
       cnt[sp.phase] += 1;
+      units[sp.phase] += c->span_units[si];
     }
+    const int K0 = stdd_ctx::PH_K0;
+    o->small_ms = t[K0 + stdd::K_SMALL];
+    o->small_flops = units[K0 + stdd::K_SMALL];
+    o->small_calls = cnt[K0 + stdd::K_SMALL];
+    o->update_ms = t[K0 + stdd::K_UPDATE];
+    o->update_flops = units[K0 + stdd::K_UPDATE];
+    o->update_calls = cnt[K0 + stdd::K_UPDATE];
+    o->up_ms = t[K0 + stdd::K_UP];
+    o->up_bytes = units[K0 + stdd::K_UP];
+    o->up_calls = cnt[K0 + stdd::K_UP];
+    o->down_ms = t[K0 + stdd::K_DOWN];
+    o->down_bytes = units[K0 + stdd::K_DOWN];
+    o->down_calls = cnt[K0 + stdd::K_DOWN];
     o->factor_ms = t[stdd_ctx::PH_FACTOR];
     o->minv_ms = t[stdd_ctx::PH_MINV];
     o->minv_calls = cnt[stdd_ctx::PH_MINV];
@@ -1093,6 +1194,7 @@ stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {
     o->launches = __atomic_load_n(&stdd::g_launches, __ATOMIC_RELAXED);
     if (reset) {
       c->spans.clear();
+      c->span_units.clear();
       c->ev_used = 0;
     }
   });

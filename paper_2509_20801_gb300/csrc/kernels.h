@@ -14,7 +14,7 @@ inline void count_launch(int n = 1) { __atomic_add_fetch(&g_launches, (long long
 constexpr int MF_NB = 32;             // pivot block of the blocked Gauss-Jordan sweep
 constexpr int MF_PANEL_THREADS = 128; // rows / columns per panel tile
 constexpr int MF_SMALL = 64;          // fronts with n <= MF_SMALL are swept in shared memory
-constexpr int MF_SMALL_THREADS = 128;
+constexpr int MF_SMALL_WARPS = 4;    // small fronts (one warp each) per CTA
 
 // Everything a multifrontal kernel needs (device pointers).
 struct MfArgs {
@@ -41,15 +41,28 @@ struct LevelInfo {
   int f0, nf;                 // fronts [f0, f0 + nf) of the level
   int max_p, max_b, max_n, min_n;
   int64_t up_off, down_off;   // offsets of the level's work items
-  int n_up, n_down;           // (front, 32-row chunk) items going up / down
+  int n_up, n_down;           // (front, row chunk) items going up / down
+  int rows_up, rows_down;     // rows per item: 16 or 32
+  int split_up, split_down;   // row groups sharing one item's columns (1..8)
+};
+
+// Optional per-launch observer (phase profiling): kind is one of the K_*
+// values, level the tree level, k the pivot-block step (factorization).
+enum { K_SMALL = 0, K_UPDATE = 1, K_UP = 2, K_DOWN = 3, K_COUNT = 4 };
+struct LaunchHook {
+  virtual void before(int kind, int level, int k) = 0;
+  virtual void after(int kind, int level, int k) = 0;
 };
 
 template <typename R> cudaError_t mf_setup_attributes();
-template <typename R> void mf_factor_level(const MfArgs &a, const LevelInfo &L, cudaStream_t st);
 template <typename R>
-void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int nrhs, int64_t ldt, cudaStream_t st);
+void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_t st, LaunchHook *hook = nullptr);
 template <typename R>
-void mf_down_level(const MfArgs &a, const int2 *items, int nitems, int nrhs, int64_t ldt, cudaStream_t st);
+void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
+                 cudaStream_t st);
+template <typename R>
+void mf_down_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
+                   cudaStream_t st);
 
 // ---- FDFD / DDM vector kernels (kernels_fdfd.cu)
 struct GridDev {
@@ -80,9 +93,10 @@ template <typename R> void launch_to_local(const double2 *t, void *tloc, int64_t
 template <typename R> void launch_from_local(const void *tloc, double2 *z, int64_t n, cudaStream_t st);
 
 // ---- Krylov kernels (kernels_krylov.cu), FP64 complex
-// partial[blk][i] = sum_g conj(V_i[g]) w[g], i < m; then h[i] = sum_blk partial
+// partial[blk][i] = sum_g conj(V_i[g]) w[g], i < m; then h[i] = sum_blk partial.
+// With self_norm, h[m] = (||w||^2, 0) as well.
 void launch_mdot(const double2 *V, int64_t ldv, int m, const double2 *w, int64_t n, double2 *partial,
-                 double2 *h, cudaStream_t st);
+                 double2 *h, cudaStream_t st, int self_norm = 0);
 // w -= sum_i h[i] V_i, and nrm2 = ||w||^2 (partials then a fixed-order sum)
 void launch_maxpy_norm(const double2 *V, int64_t ldv, int m, const double2 *h, double2 *w, int64_t n,
                        double *partial, double *nrm2, cudaStream_t st);

@@ -39,12 +39,24 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
   return s;
 }
 
+// partial[blk][i] = sum conj(V_i) w over the block's chunk, i < m; with
+// self_norm, partial[blk][m] = (sum |w|^2, 0)
 __global__ void __launch_bounds__(TPB) k_mdot(const double2 *__restrict__ V, int64_t ldv, int m,
                                               const double2 *__restrict__ w, int64_t n,
-                                              double2 *__restrict__ partial) {
+                                              double2 *__restrict__ partial, int self_norm) {
   __shared__ double sh[TPB / 32];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t g0 = (int64_t)blockIdx.x * chunk, g1 = min(n, g0 + chunk);
+  const int mt = m + (self_norm ? 1 : 0);
+  if (self_norm) {
+    double a = 0;
+    for (int64_t g = g0 + threadIdx.x; g < g1; g += TPB) {
+      const double2 wv = w[g];
+      a = fma(wv.x, wv.x, fma(wv.y, wv.y, a));
+    }
+    const double sa = block_sum(a, sh);
+    if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * mt + m] = make_double2(sa, 0.0);
+  }
   for (int i0 = 0; i0 < m; i0 += GROUP) {
     const int gi = min(GROUP, m - i0);
     double2 acc[GROUP];
@@ -65,7 +77,7 @@ __global__ void __launch_bounds__(TPB) k_mdot(const double2 *__restrict__ V, int
       if (q < gi) {
         const double sr = block_sum(acc[q].x, sh);
         const double si = block_sum(acc[q].y, sh);
-        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * m + i0 + q] = make_double2(sr, si);
+        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * mt + i0 + q] = make_double2(sr, si);
       }
     }
   }
@@ -158,11 +170,12 @@ inline int nblocks_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<in
 int krylov_partial_blocks() { return NBLK; }
 
 void launch_mdot(const double2 *V, int64_t ldv, int m, const double2 *w, int64_t n, double2 *partial,
-                 double2 *h, cudaStream_t st) {
+                 double2 *h, cudaStream_t st, int self_norm) {
   const int nb = nblocks_for(n);
-  k_mdot<<<nb, TPB, 0, st>>>(V, ldv, m, w, n, partial);
+  k_mdot<<<nb, TPB, 0, st>>>(V, ldv, m, w, n, partial, self_norm);
   count_launch();
-  k_reduce_c<<<(m + 7) / 8, 256, 0, st>>>(partial, nb, m, h);
+  const int mt = m + (self_norm ? 1 : 0);
+  k_reduce_c<<<(mt + 7) / 8, 256, 0, st>>>(partial, nb, mt, h);
   count_launch();
 }
 

@@ -76,16 +76,55 @@ __device__ __forceinline__ int unband(int i, int k, int nbk) { return i < k ? i 
 }  // namespace
 
 // ------------------------------------------------------------- assembly
-// F = A-entries of this front (rows or columns that are pivots here) plus the
-// children's Schur complements placed by the inverse extend-add maps.
+// Entry (r, c) of front f before elimination: the A-entry if row or column
+// is a pivot here (Eq. 2 with the stretched couplings of Eq. 9, strip-local
+// x couplings), plus the children's Schur complements placed by the inverse
+// extend-add maps.
+template <typename C>
+__device__ __forceinline__ C front_entry(const MfArgs &a, const FrontDev &f, const StripDev &s, const FrontDev *ch,
+                                         const bool *has, int r, int c) {
+  const int p = f.p, H = a.H;
+  double2 v = make_double2(0.0, 0.0);
+  if (r < p || c < p) {
+    const int u = a.nodes[f.node_off + r], w = a.nodes[f.node_off + c];
+    const int ux = u / H, uy = u - ux * H;
+    if (u == w) {
+      const double2 xm = a.cxm[s.coef_off + ux], xp = a.cxp[s.coef_off + ux];
+      const double2 ym = a.cym[uy], yp = a.cyp[uy];
+      v.x = a.k0sq * a.eps[(int64_t)(s.x0 + ux) * H + uy] - xm.x - xp.x - ym.x - yp.x;
+      v.y = -xm.y - xp.y - ym.y - yp.y;
+    } else if (w == u - H) {
+      v = a.cxm[s.coef_off + ux];
+    } else if (w == u + H) {
+      v = a.cxp[s.coef_off + ux];
+    } else if (w == u - 1 && uy > 0) {
+      v = a.cym[uy];
+    } else if (w == u + 1 && uy < H - 1) {
+      v = a.cyp[uy];
+    }
+  }
+  C out = to_c(v, C());
+#pragma unroll
+  for (int ci = 0; ci < 2; ++ci) {
+    if (!has[ci]) continue;
+    const int ir = a.inv[f.inv_off[ci] + r];
+    if (ir < 0) continue;
+    const int ic = a.inv[f.inv_off[ci] + c];
+    if (ic < 0) continue;
+    out = cadd(out, reinterpret_cast<const C *>(a.ws_child)[ch[ci].s_off + (int64_t)ic * ch[ci].b + ir]);
+  }
+  return out;
+}
+
+// Large fronts (n > MF_SMALL): write the assembled front to its storage.
 template <typename R>
 __global__ void __launch_bounds__(256) mf_assemble(MfArgs a, int f0) {
   using C = typename CT<R>::T;
   const FrontDev f = a.fronts[f0 + blockIdx.x];
-  const int p = f.p, b = f.b, n = p + b;
+  const int n = f.p + f.b;
+  if (n <= MF_SMALL) return;
   const int64_t nn = (int64_t)n * n;
   const StripDev s = a.strips[f.strip];
-  const int H = a.H;
   FrontDev ch[2];
   bool has[2];
 #pragma unroll
@@ -95,69 +134,52 @@ __global__ void __launch_bounds__(256) mf_assemble(MfArgs a, int f0) {
   }
   for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.y * blockDim.x) {
     const int c = (int)(e / n), r = (int)(e - (int64_t)c * n);
-    double2 v = make_double2(0.0, 0.0);
-    if (r < p || c < p) {
-      const int u = a.nodes[f.node_off + r], w = a.nodes[f.node_off + c];
-      const int ux = u / H, uy = u - ux * H;
-      if (u == w) {
-        const double2 xm = a.cxm[s.coef_off + ux], xp = a.cxp[s.coef_off + ux];
-        const double2 ym = a.cym[uy], yp = a.cyp[uy];
-        v.x = a.k0sq * a.eps[(int64_t)(s.x0 + ux) * H + uy] - xm.x - xp.x - ym.x - yp.x;
-        v.y = -xm.y - xp.y - ym.y - yp.y;
-      } else if (w == u - H) {
-        v = a.cxm[s.coef_off + ux];
-      } else if (w == u + H) {
-        v = a.cxp[s.coef_off + ux];
-      } else if (w == u - 1 && uy > 0) {
-        v = a.cym[uy];
-      } else if (w == u + 1 && uy < H - 1) {
-        v = a.cyp[uy];
-      }
-    }
-    C out = to_c(v, C());
-#pragma unroll
-    for (int ci = 0; ci < 2; ++ci) {
-      if (!has[ci]) continue;
-      const int ir = a.inv[f.inv_off[ci] + r];
-      if (ir < 0) continue;
-      const int ic = a.inv[f.inv_off[ci] + c];
-      if (ic < 0) continue;
-      out = cadd(out, reinterpret_cast<const C *>(a.ws_child)[ch[ci].s_off + (int64_t)ic * ch[ci].b + ir]);
-    }
-    st_elem<C>(a, f, r, c, out);
+    st_elem<C>(a, f, r, c, front_entry<C>(a, f, s, ch, has, r, c));
   }
 }
 
 // ------------------------------------------------ small fronts, in smem
-// One CTA per front with n <= MF_SMALL: the whole front is swept in shared
-// memory one pivot at a time (row k scaled by 1/d, column k kept, then the
-// rank-1 update of everything else).
+// One warp per front with n <= MF_SMALL (blockDim.x / 32 fronts per CTA): the
+// front is assembled straight into shared memory, swept one pivot at a time
+// (row k scaled by 1/d, column k kept, rank-1 update of everything else) and
+// only the results are written out.  ldn is the level's largest small n.
 template <typename R>
-__global__ void __launch_bounds__(MF_SMALL_THREADS) mf_gj_small(MfArgs a, int f0) {
+__global__ void __launch_bounds__(32 * MF_SMALL_WARPS) mf_gj_small(MfArgs a, int f0, int nf, int ldn) {
+  const int wpc = blockDim.x >> 5;
   using C = typename CT<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *F = reinterpret_cast<C *>(smem_raw);  // n x n, ld n
-  C *rowk = F + MF_SMALL * MF_SMALL;
-  C *colk = rowk + MF_SMALL;
-  const FrontDev f = a.fronts[f0 + blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  C *F = reinterpret_cast<C *>(smem_raw) + (size_t)warp * (ldn * ldn + 2 * ldn);  // n x n, ld n
+  C *rowk = F + ldn * ldn;
+  C *colk = rowk + ldn;
+  const int fi = blockIdx.x * wpc + warp;
+  if (fi >= nf) return;
+  const FrontDev f = a.fronts[f0 + fi];
   const int p = f.p, b = f.b, n = p + b;
-  if (n > MF_SMALL) return;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < n * n; idx += blockDim.x) {
-    const int c = idx / n, r = idx - c * n;
-    F[idx] = ld_elem<C>(a, f, r, c);
+  if (n > MF_SMALL || n > ldn) return;
+  const StripDev s = a.strips[f.strip];
+  FrontDev ch[2];
+  bool has[2];
+#pragma unroll
+  for (int ci = 0; ci < 2; ++ci) {
+    has[ci] = f.child[ci] >= 0;
+    if (has[ci]) ch[ci] = a.fronts[f.child[ci]];
   }
-  __syncthreads();
+  for (int idx = lane; idx < n * n; idx += 32) {
+    const int c = idx / n, r = idx - c * n;
+    F[idx] = front_entry<C>(a, f, s, ch, has, r, c);
+  }
+  __syncwarp();
   for (int k = 0; k < p; ++k) {
     const C d = F[k * n + k];
     const C inv = crecip(d);
-    for (int j = tid; j < n; j += blockDim.x) {
+    for (int j = lane; j < n; j += 32) {
       rowk[j] = cmul(F[j * n + k], inv);
       colk[j] = F[k * n + j];
     }
-    if (tid == 0) note_pivot(a, sqrt((double)cabs2(d)), cfinite(d));
-    __syncthreads();
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    if (lane == 0) note_pivot(a, sqrt((double)cabs2(d)), cfinite(d));
+    __syncwarp();
+    for (int idx = lane; idx < n * n; idx += 32) {
       const int c = idx / n, r = idx - c * n;
       C v;
       if (r == k) v = (c == k) ? inv : rowk[c];
@@ -165,9 +187,9 @@ __global__ void __launch_bounds__(MF_SMALL_THREADS) mf_gj_small(MfArgs a, int f0
       else v = cfms(colk[r], rowk[c], F[idx]);
       F[idx] = v;
     }
-    __syncthreads();
+    __syncwarp();
   }
-  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+  for (int idx = lane; idx < n * n; idx += 32) {
     const int c = idx / n, r = idx - c * n;
     st_elem<C>(a, f, r, c, F[idx]);
   }
@@ -377,132 +399,209 @@ __global__ void __launch_bounds__(256) mf_gj_update(MfArgs a, int f0, int k) {
 }
 
 // ------------------------------------------------------- substitutions
-// Work items are (front, 32-row chunk); one warp per item, 4 warps per CTA.
-// Going up: lane = border row r of the chunk; w_p is gathered 32 pivots at a
-// time (t at the pivot nodes + the children's update vectors through the
-// inverse extend-add maps) and broadcast by shuffles; chunk 0 also stores w_p
-// for the way down.  u[r] = w_b[r] + sum_j (-G21)(r, j) w_p[j].
-template <typename R>
-__global__ void __launch_bounds__(128) mf_up(MfArgs a, const int2 *__restrict__ items, int nitems, int nrhs,
-                                             int64_t ldt) {
+// Work items are (front, chunk of ROWS rows).  ROWS lanes ("row group") own
+// the ROWS rows of an item, lane = row; a 256-thread CTA holds 256/ROWS row
+// groups.  With split > 1 the row groups of one item take consecutive
+// slices of the columns and their partial sums are added in a fixed order
+// through shared memory (deterministic).  Column values are gathered ROWS at
+// a time, one per lane, and broadcast by shuffles within the row group.
+template <int W, typename C> __device__ __forceinline__ C shfl_w(unsigned mask, C v, int src) {
+  v.x = __shfl_sync(mask, v.x, src, W);
+  v.y = __shfl_sync(mask, v.y, src, W);
+  return v;
+}
+
+// Going up: lane = border row r; w_p = t at the pivot nodes + the children's
+// update vectors through the inverse extend-add maps; the chunk-0 item also
+// stores w_p for the way down.  u[r] = w_b[r] + sum_j (-G21)(r, j) w_p[j].
+template <typename R, int ROWS>
+__global__ void __launch_bounds__(256) mf_up(MfArgs a, const int2 *__restrict__ items, int nitems, int split,
+                                             int nrhs, int64_t ldt) {
   using C = typename CT<R>::T;
-  const int lane = threadIdx.x & 31;
-  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (it >= nitems) return;
-  const int2 item = items[it];
-  const FrontDev f = a.fronts[item.x];
-  const int p = f.p, b = f.b, n = p + b;
-  const StripDev s = a.strips[f.strip];
-  const C *tv = reinterpret_cast<const C *>(a.tloc);
-  C *wl = reinterpret_cast<C *>(a.wloc);
-  const C *G = reinterpret_cast<const C *>(a.fac) + f.fac_off + (int64_t)p * n;  // -G21, b x p, ld b
-  const int r = item.y * 32 + lane;
-  const bool row = r < b;
+  constexpr int GROUPS = 256 / ROWS;
+  __shared__ C part[256];
+  const int g = threadIdx.x / ROWS, lane = threadIdx.x % ROWS;
+  const int ipc = GROUPS / split;
+  const int il = g / split, sidx = g - il * split;
+  const int it = blockIdx.x * ipc + il;
+  const bool active = it < nitems;
+  const unsigned mask = ROWS == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+  int p = 0, b = 0, r = 0, j0s = 0, j0e = 0, chunk = 0;
+  bool row = false;
+  const C *G = nullptr;
   const C *uc[2] = {nullptr, nullptr};
   int bc[2] = {0, 0};
   const int *inv[2] = {nullptr, nullptr};
+  const int *nodes = nullptr;
+  int64_t voff = 0;
+  C *u = nullptr;
+  if (active) {
+    const int2 item = items[it];
+    const FrontDev f = a.fronts[item.x];
+    p = f.p;
+    b = f.b;
+    chunk = item.y;
+    const int n = p + b;
+    voff = a.strips[f.strip].vec_off;
+    G = reinterpret_cast<const C *>(a.fac) + f.fac_off + (int64_t)p * n;  // -G21, b x p, ld b
+    r = item.y * ROWS + lane;
+    row = r < b;
 #pragma unroll
-  for (int ci = 0; ci < 2; ++ci) {
-    if (f.child[ci] >= 0) {
-      const FrontDev ch = a.fronts[f.child[ci]];
-      bc[ci] = ch.b;
-      uc[ci] = reinterpret_cast<const C *>(a.ub_child) + ch.u_off * nrhs;
-      inv[ci] = a.inv + f.inv_off[ci];
+    for (int ci = 0; ci < 2; ++ci) {
+      if (f.child[ci] >= 0) {
+        const FrontDev ch = a.fronts[f.child[ci]];
+        bc[ci] = ch.b;
+        uc[ci] = reinterpret_cast<const C *>(a.ub_child) + ch.u_off * nrhs;
+        inv[ci] = a.inv + f.inv_off[ci];
+      }
     }
+    nodes = a.nodes + f.node_off;
+    u = reinterpret_cast<C *>(a.ub_cur) + f.u_off * nrhs;
+    const int nch = (p + ROWS - 1) / ROWS;
+    j0s = (sidx * nch / split) * ROWS;
+    j0e = ((sidx + 1) * nch / split) * ROWS;
   }
-  const int *nodes = a.nodes + f.node_off;
-  C *u = reinterpret_cast<C *>(a.ub_cur) + f.u_off * nrhs;
+  const C *tv = reinterpret_cast<const C *>(a.tloc);
+  C *wl = reinterpret_cast<C *>(a.wloc);
   for (int q = 0; q < nrhs; ++q) {
     C acc = czero<C>();
-    if (row) {
-#pragma unroll
-      for (int ci = 0; ci < 2; ++ci)
-        if (uc[ci]) {
-          const int t = inv[ci][p + r];
-          if (t >= 0) acc = cadd(acc, uc[ci][(int64_t)q * bc[ci] + t]);
-        }
-    }
-    for (int j0 = 0; j0 < p; j0 += 32) {
-      const int j = j0 + lane;
-      C wj = czero<C>();
-      if (j < p) {
-        const int64_t gi = q * ldt + s.vec_off + nodes[j];
-        wj = tv[gi];
+    if (active) {
+      if (row && sidx == 0) {
 #pragma unroll
         for (int ci = 0; ci < 2; ++ci)
           if (uc[ci]) {
-            const int t = inv[ci][j];
-            if (t >= 0) wj = cadd(wj, uc[ci][(int64_t)q * bc[ci] + t]);
+            const int t = inv[ci][p + r];
+            if (t >= 0) acc = cadd(acc, uc[ci][(int64_t)q * bc[ci] + t]);
           }
-        if (item.y == 0) wl[gi] = wj;
       }
-      const int jb = min(32, p - j0);
-      if (jb == 32) {
-#pragma unroll 8
-        for (int jj = 0; jj < 32; ++jj) {
-          const C wv = shfl(wj, jj);
-          if (row) acc = cfma(G[(int64_t)(j0 + jj) * b + r], wv, acc);
+      for (int j0 = j0s; j0 < j0e; j0 += ROWS) {
+        const int j = j0 + lane;
+        C wj = czero<C>();
+        if (j < p) {
+          const int64_t gi = q * ldt + voff + nodes[j];
+          wj = tv[gi];
+#pragma unroll
+          for (int ci = 0; ci < 2; ++ci)
+            if (uc[ci]) {
+              const int t = inv[ci][j];
+              if (t >= 0) wj = cadd(wj, uc[ci][(int64_t)q * bc[ci] + t]);
+            }
+          if (chunk == 0) wl[gi] = wj;
         }
-      } else {
-        for (int jj = 0; jj < jb; ++jj) {
-          const C wv = shfl(wj, jj);
-          if (row) acc = cfma(G[(int64_t)(j0 + jj) * b + r], wv, acc);
+        const int jb = min(ROWS, p - j0);
+        if (jb == ROWS) {
+#pragma unroll 8
+          for (int jj = 0; jj < ROWS; ++jj) {
+            const C wv = shfl_w<ROWS>(mask, wj, jj);
+            if (row) acc = cfma(G[(int64_t)(j0 + jj) * b + r], wv, acc);
+          }
+        } else {
+          for (int jj = 0; jj < jb; ++jj) {
+            const C wv = shfl_w<ROWS>(mask, wj, jj);
+            if (row) acc = cfma(G[(int64_t)(j0 + jj) * b + r], wv, acc);
+          }
         }
       }
     }
-    if (row) u[(int64_t)q * b + r] = acc;
+    if (split > 1) {
+      part[threadIdx.x] = acc;
+      __syncthreads();
+      if (active && row && sidx == 0) {
+        C sum = acc;
+        for (int t = 1; t < split; ++t) sum = cadd(sum, part[(il * split + t) * ROWS + lane]);
+        u[(int64_t)q * b + r] = sum;
+      }
+      __syncthreads();
+    } else if (active && row) {
+      u[(int64_t)q * b + r] = acc;
+    }
   }
 }
 
-// Coming down: lane = pivot row r of the chunk;
+// Coming down: lane = pivot row r;
 // x[r] = sum_{c<p} Finv(r, c) w_p[c] - sum_{c>=p} H12(r, c) x_b[c].
-template <typename R>
-__global__ void __launch_bounds__(128) mf_down(MfArgs a, const int2 *__restrict__ items, int nitems, int nrhs,
-                                               int64_t ldt) {
+template <typename R, int ROWS>
+__global__ void __launch_bounds__(256) mf_down(MfArgs a, const int2 *__restrict__ items, int nitems, int split,
+                                               int nrhs, int64_t ldt) {
   using C = typename CT<R>::T;
-  const int lane = threadIdx.x & 31;
-  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (it >= nitems) return;
-  const int2 item = items[it];
-  const FrontDev f = a.fronts[item.x];
-  const int p = f.p, b = f.b, n = p + b;
-  const StripDev s = a.strips[f.strip];
+  constexpr int GROUPS = 256 / ROWS;
+  __shared__ C part[256];
+  const int g = threadIdx.x / ROWS, lane = threadIdx.x % ROWS;
+  const int ipc = GROUPS / split;
+  const int il = g / split, sidx = g - il * split;
+  const int it = blockIdx.x * ipc + il;
+  const bool active = it < nitems;
+  const unsigned mask = ROWS == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+  int p = 0, n = 0, r = 0, c0s = 0, c0e = 0;
+  bool row = false;
+  const C *Fm = nullptr;
+  const int *nodes = nullptr;
+  int64_t voff = 0;
+  if (active) {
+    const int2 item = items[it];
+    const FrontDev f = a.fronts[item.x];
+    p = f.p;
+    n = p + f.b;
+    voff = a.strips[f.strip].vec_off;
+    Fm = reinterpret_cast<const C *>(a.fac) + f.fac_off;  // p x n, ld p
+    r = item.y * ROWS + lane;
+    row = r < p;
+    nodes = a.nodes + f.node_off;
+    const int nch = (n + ROWS - 1) / ROWS;
+    c0s = (sidx * nch / split) * ROWS;
+    c0e = ((sidx + 1) * nch / split) * ROWS;
+  }
   C *tv = reinterpret_cast<C *>(a.tloc);
   const C *wl = reinterpret_cast<const C *>(a.wloc);
-  const C *Fm = reinterpret_cast<const C *>(a.fac) + f.fac_off;  // p x n, ld p
-  const int r = item.y * 32 + lane;
-  const bool row = r < p;
-  const int *nodes = a.nodes + f.node_off;
   for (int q = 0; q < nrhs; ++q) {
-    const int64_t base = q * ldt + s.vec_off;
+    const int64_t base = q * ldt + voff;
     C acc = czero<C>();
-    for (int c0 = 0; c0 < n; c0 += 32) {
-      const int c = c0 + lane;
-      C v = czero<C>();
-      if (c < p) v = wl[base + nodes[c]];
-      else if (c < n) v = cneg(tv[base + nodes[c]]);
-      const int cb = min(32, n - c0);
-      if (cb == 32) {
+    if (active) {
+      for (int c0 = c0s; c0 < c0e; c0 += ROWS) {
+        const int c = c0 + lane;
+        C v = czero<C>();
+        if (c < p) v = wl[base + nodes[c]];
+        else if (c < n) v = cneg(tv[base + nodes[c]]);
+        const int cb = min(ROWS, n - c0);
+        if (cb == ROWS) {
 #pragma unroll 8
-        for (int cc = 0; cc < 32; ++cc) {
-          const C vv = shfl(v, cc);
-          if (row) acc = cfma(Fm[(int64_t)(c0 + cc) * p + r], vv, acc);
-        }
-      } else {
-        for (int cc = 0; cc < cb; ++cc) {
-          const C vv = shfl(v, cc);
-          if (row) acc = cfma(Fm[(int64_t)(c0 + cc) * p + r], vv, acc);
+          for (int cc = 0; cc < ROWS; ++cc) {
+            const C vv = shfl_w<ROWS>(mask, v, cc);
+            if (row) acc = cfma(Fm[(int64_t)(c0 + cc) * p + r], vv, acc);
+          }
+        } else {
+          for (int cc = 0; cc < cb; ++cc) {
+            const C vv = shfl_w<ROWS>(mask, v, cc);
+            if (row) acc = cfma(Fm[(int64_t)(c0 + cc) * p + r], vv, acc);
+          }
         }
       }
     }
-    if (row) tv[base + nodes[r]] = acc;
+    if (split > 1) {
+      part[threadIdx.x] = acc;
+      __syncthreads();
+      if (active && row && sidx == 0) {
+        C sum = acc;
+        for (int t = 1; t < split; ++t) sum = cadd(sum, part[(il * split + t) * ROWS + lane]);
+        tv[base + nodes[r]] = sum;
+      }
+      __syncthreads();
+    } else if (active && row) {
+      tv[base + nodes[r]] = acc;
+    }
   }
 }
 
 // ------------------------------------------------------------ launchers
-template <typename R> static size_t small_smem() {
+// fronts per CTA for the small kernel: as many warps as fit in ~200 KB
+template <typename R> static int small_wpc(int ldn) {
   using C = typename CT<R>::T;
-  return sizeof(C) * (MF_SMALL * MF_SMALL + 2 * MF_SMALL);
+  const size_t per = sizeof(C) * (size_t)(ldn * ldn + 2 * ldn);
+  return (int)std::max<size_t>(1, std::min<size_t>(MF_SMALL_WARPS, (200u << 10) / per));
+}
+template <typename R> static size_t small_smem(int ldn) {
+  using C = typename CT<R>::T;
+  return sizeof(C) * small_wpc<R>(ldn) * (size_t)(ldn * ldn + 2 * ldn);
 }
 template <typename R> static size_t row_smem() {
   using C = typename CT<R>::T;
@@ -515,33 +614,38 @@ template <typename R> static size_t gemm_smem() {
 
 template <typename R> cudaError_t mf_setup_attributes() {
   cudaError_t e;
-  e = cudaFuncSetAttribute(mf_gj_small<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem<R>());
+  e = cudaFuncSetAttribute(mf_gj_small<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(mf_gj_row<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem<R>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(mf_gj_update<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<R>());
 }
 
-template <typename R> void mf_factor_level(const MfArgs &a, const LevelInfo &L, cudaStream_t st) {
+template <typename R>
+void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_t st, LaunchHook *hook) {
   if (L.nf == 0) return;
-  {
+  if (L.min_n <= MF_SMALL) {
+    const int ldn = std::min(L.max_n, MF_SMALL);
+    const int wpc = small_wpc<R>(ldn);
+    if (hook) hook->before(K_SMALL, level, 0);
+    mf_gj_small<R><<<(L.nf + wpc - 1) / wpc, 32 * wpc, small_smem<R>(ldn), st>>>(a, L.f0, L.nf, ldn);
+    if (hook) hook->after(K_SMALL, level, 0);
+    count_launch();
+  }
+  if (L.max_n > MF_SMALL) {
     const int64_t nn = (int64_t)L.max_n * L.max_n;
     const int gy = (int)std::min<int64_t>((nn + 255) / 256, 4096);
     mf_assemble<R><<<dim3(L.nf, gy), 256, 0, st>>>(a, L.f0);
     count_launch();
-  }
-  if (L.min_n <= MF_SMALL) {
-    mf_gj_small<R><<<L.nf, MF_SMALL_THREADS, small_smem<R>(), st>>>(a, L.f0);
-    count_launch();
-  }
-  if (L.max_n > MF_SMALL) {
     for (int k = 0; k < L.max_p; k += MF_NB) {
       const int m = L.max_n - std::min(MF_NB, std::max(1, L.max_p - k));
       const int tiles = std::max(1, (m + MF_PANEL_THREADS - 1) / MF_PANEL_THREADS);
       const int nt = std::max(1, (m + 63) / 64);
       mf_gj_diag<R><<<L.nf, MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
       mf_gj_col<R><<<dim3(L.nf, tiles), MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
+      if (hook) hook->before(K_UPDATE, level, k);
       mf_gj_update<R><<<dim3(L.nf, nt * nt), 256, gemm_smem<R>(), st>>>(a, L.f0, k);
+      if (hook) hook->after(K_UPDATE, level, k);
       mf_gj_row<R><<<dim3(L.nf, tiles), MF_PANEL_THREADS, row_smem<R>(), st>>>(a, L.f0, k);
       count_launch(4);
     }
@@ -549,26 +653,34 @@ template <typename R> void mf_factor_level(const MfArgs &a, const LevelInfo &L, 
 }
 
 template <typename R>
-void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int nrhs, int64_t ldt, cudaStream_t st) {
+void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
+                 cudaStream_t st) {
   if (nitems == 0) return;
-  mf_up<R><<<(nitems + 3) / 4, 128, 0, st>>>(a, items, nitems, nrhs, ldt);
+  const int ipc = (256 / rows) / split;
+  const int grid = (nitems + ipc - 1) / ipc;
+  if (rows == 16) mf_up<R, 16><<<grid, 256, 0, st>>>(a, items, nitems, split, nrhs, ldt);
+  else mf_up<R, 32><<<grid, 256, 0, st>>>(a, items, nitems, split, nrhs, ldt);
   count_launch();
 }
 
 template <typename R>
-void mf_down_level(const MfArgs &a, const int2 *items, int nitems, int nrhs, int64_t ldt, cudaStream_t st) {
+void mf_down_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
+                   cudaStream_t st) {
   if (nitems == 0) return;
-  mf_down<R><<<(nitems + 3) / 4, 128, 0, st>>>(a, items, nitems, nrhs, ldt);
+  const int ipc = (256 / rows) / split;
+  const int grid = (nitems + ipc - 1) / ipc;
+  if (rows == 16) mf_down<R, 16><<<grid, 256, 0, st>>>(a, items, nitems, split, nrhs, ldt);
+  else mf_down<R, 32><<<grid, 256, 0, st>>>(a, items, nitems, split, nrhs, ldt);
   count_launch();
 }
 
 template cudaError_t mf_setup_attributes<double>();
 template cudaError_t mf_setup_attributes<float>();
-template void mf_factor_level<double>(const MfArgs &, const LevelInfo &, cudaStream_t);
-template void mf_factor_level<float>(const MfArgs &, const LevelInfo &, cudaStream_t);
-template void mf_up_level<double>(const MfArgs &, const int2 *, int, int, int64_t, cudaStream_t);
-template void mf_up_level<float>(const MfArgs &, const int2 *, int, int, int64_t, cudaStream_t);
-template void mf_down_level<double>(const MfArgs &, const int2 *, int, int, int64_t, cudaStream_t);
-template void mf_down_level<float>(const MfArgs &, const int2 *, int, int, int64_t, cudaStream_t);
+template void mf_factor_level<double>(const MfArgs &, const LevelInfo &, int, cudaStream_t, LaunchHook *);
+template void mf_factor_level<float>(const MfArgs &, const LevelInfo &, int, cudaStream_t, LaunchHook *);
+template void mf_up_level<double>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t);
+template void mf_up_level<float>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t);
+template void mf_down_level<double>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t);
+template void mf_down_level<float>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t);
 
 }  // namespace stdd
