@@ -4,6 +4,8 @@
 // preconditioner is one Jacobi source-transfer sweep (Algorithm 1's loop
 // body in residual form, Eqs. 18-21).
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <complex>
 #include <cstring>
 #include <map>
@@ -207,12 +209,15 @@ struct stdd_ctx {
   std::vector<double> unit_small, unit_up, unit_down;       // per level
   std::vector<std::vector<double>> unit_update;             // per level, per step
   std::vector<double> span_units;                           // parallel to spans
+  std::vector<int> span_level;                              // parallel to spans
   struct Hook : stdd::LaunchHook {
     stdd_ctx *c = nullptr;
     int open = -1;
     void before(int kind, int level, int k) override {
       if (!c->prof) return;
       open = c->pbegin(PH_K0 + kind);
+      c->span_level.resize(c->spans.size(), -1);
+      c->span_level[open] = level;
       double u = 0;
       if (kind == stdd::K_SMALL) u = c->unit_small[level];
       else if (kind == stdd::K_UPDATE) u = c->unit_update[level][k / stdd::MF_NB];
@@ -297,10 +302,18 @@ struct stdd_ctx {
   }
 
   void factor();
+  void build_structure();
+  void upload_local_couplings();
+  bool struct_ready = false;
+  std::vector<int64_t> struct_key;
   void apply_minv(const double2 *v, double2 *z);
   template <typename R> void factor_t();
   template <typename R> void solve_levels(int nrhs_);
+  template <typename R> void autotune();
   void ensure_solve_buffers(int nr);
+  // sweep launch configurations chosen by timing, keyed by the level shape
+  std::map<std::vector<int64_t>, int> tuned;
+  bool autotune_on = true;
   MfArgs mf_args(int level_parity_cur, bool solve) const;
   void ensure_krylov(int m);
   void gmres(int rhs, const stdd_solve_opts &o, double2 *x);
@@ -335,10 +348,52 @@ MfArgs stdd_ctx::mf_args(int par, bool solve) const {
   return a;
 }
 
+// Strip-local x couplings (local PML at interior sides, global PML at the
+// domain ends), re-derived at every factorization (they depend on the
+// frequency and the PML, not on the structure).
+void stdd_ctx::upload_local_couplings() {
+  const double k0 = 2.0 * M_PI / wavelength;
+  std::vector<double2> lcxm, lcxp;
+  for (int k = 0; k < nsub; ++k) {
+    const StripHost &s = strips[k];
+    std::vector<cd> sx, sxh;
+    stretch(s.W(), s.Llo, s.Lhi, dx, k0, pml_m, pml_R, sx, sxh);
+    std::vector<double2> cm, cp;
+    couplings(sx, sxh, dx, cm, cp);
+    lcxm.insert(lcxm.end(), cm.begin(), cm.end());
+    lcxp.insert(lcxp.end(), cp.begin(), cp.end());
+  }
+  upload(d_lcxm, lcxm, stream);
+  upload(d_lcxp, lcxp, stream);
+}
+
 void stdd_ctx::factor() {
   require_operator();
   build_strips();
   factored = false;
+  std::vector<int64_t> key = {nx, ny, nsub, overlap, ipml, prec, leaf_max};
+  key.insert(key.end(), cuts.begin(), cuts.end());
+  if (!struct_ready || key != struct_key) {
+    struct_ready = false;
+    build_structure();
+    struct_key = key;
+    struct_ready = true;
+  }
+  upload_local_couplings();
+  CK(cudaStreamSynchronize(stream));
+  if (prec == STDD_PREC_FP64) factor_t<double>();
+  else factor_t<float>();
+  factored = true;
+  if (autotune_on) {
+    if (prec == STDD_PREC_FP64) autotune<double>();
+    else autotune<float>();
+  }
+}
+
+// Everything that depends only on the grid, the decomposition and the
+// precision: symbolic analysis, strip and front descriptors, work items,
+// device buffers.  Cached across factorizations of the same structure.
+void stdd_ctx::build_structure() {
   // ---- symbolic analysis per distinct strip width (host, cached)
   for (auto &s : strips) {
     if (!shapes.count(s.W()) || shapes[s.W()].H != ny || shapes[s.W()].leaf_max != leaf_max) {
@@ -359,9 +414,7 @@ void stdd_ctx::factor() {
     inv.insert(inv.end(), kv.second.inv.begin(), kv.second.inv.end());
   }
   // ---- strips: local fields, local x couplings, factor blocks
-  const double k0 = 2.0 * M_PI / wavelength;
   std::vector<StripDev> sdev(nsub);
-  std::vector<double2> lcxm, lcxp;
   int64_t vec = 0, fac = 0, coef = 0;
   depth = 0;
   max_p = max_b = 0;
@@ -380,12 +433,6 @@ void stdd_ctx::factor() {
     vec += (int64_t)s.W() * ny;
     nloc_max = std::max<int64_t>(nloc_max, (int64_t)s.W() * ny);
     fac += sh.factor_entries;
-    std::vector<cd> sx, sxh;
-    stretch(s.W(), s.Llo, s.Lhi, dx, k0, pml_m, pml_R, sx, sxh);
-    std::vector<double2> cm, cp;
-    couplings(sx, sxh, dx, cm, cp);
-    lcxm.insert(lcxm.end(), cm.begin(), cm.end());
-    lcxp.insert(lcxp.end(), cp.begin(), cp.end());
     coef += s.W();
     depth = std::max(depth, sh.depth);
     max_p = std::max(max_p, sh.max_p);
@@ -480,6 +527,7 @@ void stdd_ctx::factor() {
   auto pow2_split = [](int cols, int rows) {
     int want = (cols + 4 * rows - 1) / (4 * rows), s = 1;
     while (s < want && s < 8) s *= 2;
+    if ((cols + stdd::MF_SEG - 1) / stdd::MF_SEG > stdd::MF_MAXSEG) s = 1;
     return s;
   };
   std::vector<int2> items;
@@ -507,8 +555,6 @@ void stdd_ctx::factor() {
   upload(d_nodes, nodes, stream);
   upload(d_cmap, cmap, stream);
   upload(d_inv, inv, stream);
-  upload(d_lcxm, lcxm, stream);
-  upload(d_lcxp, lcxp, stream);
   upload(d_colstrip, colstrip, stream);
   upload(d_items, items, stream);
   const size_t E = elem();
@@ -519,9 +565,61 @@ void stdd_ctx::factor() {
   d_flag.alloc(sizeof(int));
   d_minpiv.alloc(sizeof(double));
   CK(cudaStreamSynchronize(stream));
-  if (prec == STDD_PREC_FP64) factor_t<double>();
-  else factor_t<float>();
-  factored = true;
+}
+
+// Column split of every substitution level, chosen by timing each admissible
+// split (1, 2, 4, 8 row groups per item) on the real fronts; the result is
+// cached per level shape and does not change the arithmetic (fixed
+// summation segments), only the speed.
+template <typename R> void stdd_ctx::autotune() {
+  ensure_solve_buffers(1);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int2 *items = d_items.as<int2>();
+  for (int L = 0; L < depth; ++L) {
+    LevelInfo &li = levels[L];
+    for (int dir = 0; dir < 2; ++dir) {
+      const int rows = dir == 0 ? li.rows_up : li.rows_down;
+      const int cols = dir == 0 ? li.max_p : li.max_n;
+      const int nitems = dir == 0 ? li.n_up : li.n_down;
+      if (nitems == 0) continue;
+      const std::vector<int64_t> key = {dir, (int64_t)sizeof(R), li.nf, li.max_p, li.max_b, li.min_n, nitems, rows};
+      auto hit = tuned.find(key);
+      int best = dir == 0 ? li.split_up : li.split_down;
+      if (hit != tuned.end()) {
+        best = hit->second;
+      } else {
+        float best_ms = 1e30f;
+        for (int sp = 1; sp <= 8; sp *= 2) {
+          if (sp > 256 / rows) break;
+          if (sp > 1 && (cols + stdd::MF_SEG - 1) / stdd::MF_SEG > stdd::MF_MAXSEG) break;
+          float ms_min = 1e30f;
+          for (int rep = 0; rep < 3; ++rep) {
+            MfArgs a = mf_args(L & 1, true);
+            CK(cudaEventRecord(e0, stream));
+            if (dir == 0) stdd::mf_up_level<R>(a, items + li.up_off, nitems, rows, sp, 1, nloc, stream);
+            else stdd::mf_down_level<R>(a, items + li.down_off, nitems, rows, sp, 1, nloc, stream);
+            CK(cudaEventRecord(e1, stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            ms_min = std::min(ms_min, ms);
+          }
+          if (ms_min < best_ms) {
+            best_ms = ms_min;
+            best = sp;
+          }
+        }
+        tuned[key] = best;
+      }
+      if (dir == 0) li.split_up = best;
+      else li.split_down = best;
+    }
+  }
+  CK(cudaEventDestroy(e0));
+  CK(cudaEventDestroy(e1));
+  CK(cudaGetLastError());
 }
 
 template <typename R> void stdd_ctx::factor_t() {
@@ -555,6 +653,7 @@ template <typename R> void stdd_ctx::solve_levels(int nr) {
   hook.c = this;
   for (int L = depth - 1; L >= 0; --L) {
     const LevelInfo &li = levels[L];
+    stdd::mf_up_gather_level<R>(mf_args(L & 1, true), li, nr, nloc, stream);
     hook.before(stdd::K_UP, L, 0);
     stdd::mf_up_level<R>(mf_args(L & 1, true), items + li.up_off, li.n_up, li.rows_up, li.split_up, nr, nloc,
                          stream);
@@ -1171,6 +1270,26 @@ stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {
       units[sp.phase] += c->span_units[si];
     }
     const int K0 = stdd_ctx::PH_K0;
+    if (std::getenv("STDD_PROFILE_LEVELS")) {   // per-level breakdown on stderr
+      c->span_level.resize(c->spans.size(), -1);
+      std::map<std::pair<int, int>, std::pair<double, double>> lv;
+      for (size_t si = 0; si < c->spans.size(); ++si) {
+        if (c->span_level[si] < 0) continue;
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, c->spans[si].a, c->spans[si].b) != cudaSuccess) {
+          (void)cudaGetLastError();
+          continue;
+        }
+        auto &e = lv[{c->spans[si].phase - K0, c->span_level[si]}];
+        e.first += ms;
+        e.second += c->span_units[si];
+      }
+      static const char *names[] = {"small", "update", "up", "down"};
+      for (auto &kv : lv)
+        std::fprintf(stderr, "level-profile %s L%d ms %.3f units %.4g rate %.4g\n", names[kv.first.first],
+                     kv.first.second, kv.second.first, kv.second.second,
+                     kv.second.second / (kv.second.first * 1e-3));
+    }
     o->small_ms = t[K0 + stdd::K_SMALL];
     o->small_flops = units[K0 + stdd::K_SMALL];
     o->small_calls = cnt[K0 + stdd::K_SMALL];
@@ -1195,6 +1314,7 @@ stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {
     if (reset) {
       c->spans.clear();
       c->span_units.clear();
+      c->span_level.clear();
       c->ev_used = 0;
     }
   });

@@ -14,7 +14,8 @@ inline void count_launch(int n = 1) { __atomic_add_fetch(&g_launches, (long long
 constexpr int MF_NB = 32;             // pivot block of the blocked Gauss-Jordan sweep
 constexpr int MF_PANEL_THREADS = 128; // rows / columns per panel tile
 constexpr int MF_SMALL = 64;          // fronts with n <= MF_SMALL are swept in shared memory
-constexpr int MF_SMALL_WARPS = 4;    // small fronts (one warp each) per CTA
+constexpr int MF_SEG = 128;           // columns per fixed summation segment of the sweeps
+constexpr int MF_MAXSEG = 16;         // segments an item may have when its columns are split
 
 // Everything a multifrontal kernel needs (device pointers).
 struct MfArgs {
@@ -57,6 +58,8 @@ struct LaunchHook {
 template <typename R> cudaError_t mf_setup_attributes();
 template <typename R>
 void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_t st, LaunchHook *hook = nullptr);
+template <typename R>
+void mf_up_gather_level(const MfArgs &a, const LevelInfo &L, int nrhs, int64_t ldt, cudaStream_t st);
 template <typename R>
 void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
                  cudaStream_t st);

@@ -139,24 +139,38 @@ __global__ void __launch_bounds__(256) mf_assemble(MfArgs a, int f0) {
 }
 
 // ------------------------------------------------ small fronts, in smem
-// One warp per front with n <= MF_SMALL (blockDim.x / 32 fronts per CTA): the
-// front is assembled straight into shared memory, swept one pivot at a time
-// (row k scaled by 1/d, column k kept, rank-1 update of everything else) and
-// only the results are written out.  ldn is the level's largest small n.
-template <typename R>
-__global__ void __launch_bounds__(32 * MF_SMALL_WARPS) mf_gj_small(MfArgs a, int f0, int nf, int ldn) {
-  const int wpc = blockDim.x >> 5;
+// Fronts with n <= MF_SMALL are assembled straight into shared memory,
+// swept one pivot at a time (row k scaled by 1/d, column k kept, rank-1
+// update of everything else) and written out.  TPF threads work on one
+// front: 32 (a warp, blockDim/32 fronts per CTA) for n <= 32, else the whole
+// CTA (TPF = blockDim), so that the shared memory per resident warp stays
+// small.  ldn is the level's largest small n.
+template <int TPF> __device__ __forceinline__ void front_sync() {
+  if (TPF == 32) __syncwarp();
+  else __syncthreads();
+}
+
+template <typename R, int TPF>
+__global__ void __launch_bounds__(128) mf_gj_small(MfArgs a, int f0, int nf, int ldn) {
   using C = typename CT<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  C *F = reinterpret_cast<C *>(smem_raw) + (size_t)warp * (ldn * ldn + 2 * ldn);  // n x n, ld n
+  const int fpc = blockDim.x / TPF;                 // fronts per CTA
+  const int slot = threadIdx.x / TPF, t = threadIdx.x % TPF;
+  C *F = reinterpret_cast<C *>(smem_raw) + (size_t)slot * (ldn * ldn + 2 * ldn);  // n x n, ld n
   C *rowk = F + ldn * ldn;
   C *colk = rowk + ldn;
-  const int fi = blockIdx.x * wpc + warp;
-  if (fi >= nf) return;
-  const FrontDev f = a.fronts[f0 + fi];
-  const int p = f.p, b = f.b, n = p + b;
-  if (n > MF_SMALL || n > ldn) return;
+  const int fi = blockIdx.x * fpc + slot;
+  bool live = fi < nf;
+  FrontDev f;
+  int p = 0, n = 0;
+  if (live) {
+    f = a.fronts[f0 + fi];
+    p = f.p;
+    n = p + f.b;
+    live = n <= MF_SMALL && n <= ldn;
+  }
+  if (TPF == 32 && !live) return;   // warp-private work: leaving is safe
+  if (TPF > 32 && !live) return;    // whole CTA is this front
   const StripDev s = a.strips[f.strip];
   FrontDev ch[2];
   bool has[2];
@@ -165,21 +179,25 @@ __global__ void __launch_bounds__(32 * MF_SMALL_WARPS) mf_gj_small(MfArgs a, int
     has[ci] = f.child[ci] >= 0;
     if (has[ci]) ch[ci] = a.fronts[f.child[ci]];
   }
-  for (int idx = lane; idx < n * n; idx += 32) {
+  for (int idx = t; idx < n * n; idx += TPF) {
     const int c = idx / n, r = idx - c * n;
     F[idx] = front_entry<C>(a, f, s, ch, has, r, c);
   }
-  __syncwarp();
+  front_sync<TPF>();
+  double dmin = INFINITY;
+  bool bad = false;
   for (int k = 0; k < p; ++k) {
     const C d = F[k * n + k];
     const C inv = crecip(d);
-    for (int j = lane; j < n; j += 32) {
+    for (int j = t; j < n; j += TPF) {
       rowk[j] = cmul(F[j * n + k], inv);
       colk[j] = F[k * n + j];
     }
-    if (lane == 0) note_pivot(a, sqrt((double)cabs2(d)), cfinite(d));
-    __syncwarp();
-    for (int idx = lane; idx < n * n; idx += 32) {
+    const double ad = sqrt((double)cabs2(d));
+    bad |= !(ad > 0.0) || !cfinite(d);
+    dmin = fmin(dmin, ad);
+    front_sync<TPF>();
+    for (int idx = t; idx < n * n; idx += TPF) {
       const int c = idx / n, r = idx - c * n;
       C v;
       if (r == k) v = (c == k) ? inv : rowk[c];
@@ -187,9 +205,10 @@ __global__ void __launch_bounds__(32 * MF_SMALL_WARPS) mf_gj_small(MfArgs a, int
       else v = cfms(colk[r], rowk[c], F[idx]);
       F[idx] = v;
     }
-    __syncwarp();
+    front_sync<TPF>();
   }
-  for (int idx = lane; idx < n * n; idx += 32) {
+  if (t == 0) note_pivot(a, bad ? 0.0 : dmin, !bad);
+  for (int idx = t; idx < n * n; idx += TPF) {
     const int c = idx / n, r = idx - c * n;
     st_elem<C>(a, f, r, c, F[idx]);
   }
@@ -219,6 +238,8 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_diag(MfArgs a, int f0,
     D[i][j] = fac[fo + (int64_t)(k + j) * p + k + i];
   }
   __syncthreads();
+  double dmin = INFINITY;
+  bool bad = false;
   for (int q = 0; q < nbk; ++q) {
     const C d = D[q][q];
     const C inv = crecip(d);
@@ -226,7 +247,9 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_diag(MfArgs a, int f0,
       rowk[j] = cmul(D[q][j], inv);
       colk[j] = D[j][q];
     }
-    if (tid == 0) note_pivot(a, sqrt((double)cabs2(d)), cfinite(d));
+    const double ad = sqrt((double)cabs2(d));
+    bad |= !(ad > 0.0) || !cfinite(d);
+    dmin = fmin(dmin, ad);
     __syncthreads();
     for (int idx = tid; idx < nbk * nbk; idx += blockDim.x) {
       const int i = idx % nbk, j = idx / nbk;
@@ -238,6 +261,7 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_diag(MfArgs a, int f0,
     }
     __syncthreads();
   }
+  if (tid == 0) note_pivot(a, bad ? 0.0 : dmin, !bad);
   for (int idx = tid; idx < nbk * nbk; idx += blockDim.x) {
     const int i = idx % nbk, j = idx / nbk;
     fac[fo + (int64_t)(k + j) * p + k + i] = D[i][j];
@@ -401,37 +425,126 @@ __global__ void __launch_bounds__(256) mf_gj_update(MfArgs a, int f0, int k) {
 // ------------------------------------------------------- substitutions
 // Work items are (front, chunk of ROWS rows).  ROWS lanes ("row group") own
 // the ROWS rows of an item, lane = row; a 256-thread CTA holds 256/ROWS row
-// groups.  With split > 1 the row groups of one item take consecutive
-// slices of the columns and their partial sums are added in a fixed order
-// through shared memory (deterministic).  Column values are gathered ROWS at
-// a time, one per lane, and broadcast by shuffles within the row group.
+// groups.  Columns are summed in fixed segments of MF_SEG columns: each
+// segment's sum starts from zero and the segment sums are added in column
+// order, so the result does not depend on how many row groups share an item
+// (split) -- split only decides which group computes which segments.  With
+// split > 1 the segment sums meet in shared memory and the first group of
+// the item adds them.  Column values are gathered ROWS at a time (one per
+// lane) and broadcast by shuffles; each lane keeps MF_UNROLL matrix loads in
+// flight.
 template <int W, typename C> __device__ __forceinline__ C shfl_w(unsigned mask, C v, int src) {
   v.x = __shfl_sync(mask, v.x, src, W);
   v.y = __shfl_sync(mask, v.y, src, W);
   return v;
 }
 
-// Going up: lane = border row r; w_p = t at the pivot nodes + the children's
-// update vectors through the inverse extend-add maps; the chunk-0 item also
-// stores w_p for the way down.  u[r] = w_b[r] + sum_j (-G21)(r, j) w_p[j].
+// sum over columns [c0, c1) of M(r, c) * vec(c) for one segment; M(r, c) at
+// M[c * ld + r]; vec(c) comes from gather(c) (zero past the end).
+template <int ROWS, typename C, typename Gather>
+__device__ __forceinline__ C seg_dot(const C *__restrict__ M, int64_t ld, int r, bool row, int c0, int c1, int lane,
+                                     unsigned mask, Gather gather) {
+  constexpr int U = sizeof(C) == 16 ? 8 : 32;  // FP64 is ALU-bound: fewer loads, more warps
+  constexpr int UU = U < ROWS ? U : ROWS;
+  C acc = czero<C>();
+  for (int cb = c0; cb < c1; cb += ROWS) {
+    const int c = cb + lane;
+    const C v = c < c1 ? gather(c) : czero<C>();
+    const int nv = min(ROWS, c1 - cb);
+    if (nv == ROWS) {
+#pragma unroll
+      for (int u0 = 0; u0 < ROWS; u0 += UU) {
+        C m[UU];
+#pragma unroll
+        for (int u = 0; u < UU; ++u) m[u] = row ? M[(int64_t)(cb + u0 + u) * ld + r] : czero<C>();
+#pragma unroll
+        for (int u = 0; u < UU; ++u) acc = cfma(m[u], shfl_w<ROWS>(mask, v, u0 + u), acc);
+      }
+    } else {
+      // ragged last chunk: only the valid columns (no multiply-adds by zero)
+      int u = 0;
+      for (; u + 4 <= nv; u += 4) {
+        C m[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) m[t] = row ? M[(int64_t)(cb + u + t) * ld + r] : czero<C>();
+#pragma unroll
+        for (int t = 0; t < 4; ++t) acc = cfma(m[t], shfl_w<ROWS>(mask, v, u + t), acc);
+      }
+      for (; u < nv; ++u) {
+        const C m = row ? M[(int64_t)(cb + u) * ld + r] : czero<C>();
+        acc = cfma(m, shfl_w<ROWS>(mask, v, u), acc);
+      }
+    }
+  }
+  return acc;
+}
+
+// Going up, part 1: one warp per front forms w = [t at the pivots; 0] plus
+// the children's update vectors (inverse extend-add maps); w_p goes to the
+// pivot slots of wloc (kept for the way down) and w_b is the initial value
+// of the front's update vector.
+template <typename R>
+__global__ void __launch_bounds__(256) mf_up_gather(MfArgs a, int f0, int nf, int nrhs, int64_t ldt) {
+  using C = typename CT<R>::T;
+  const int lane = threadIdx.x & 31;
+  const int fi = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (fi >= nf) return;
+  const FrontDev f = a.fronts[f0 + fi];
+  const int p = f.p, b = f.b, n = p + b;
+  const int64_t voff = a.strips[f.strip].vec_off;
+  const C *uc[2] = {nullptr, nullptr};
+  int bc[2] = {0, 0};
+  const int *inv[2] = {nullptr, nullptr};
+#pragma unroll
+  for (int ci = 0; ci < 2; ++ci) {
+    if (f.child[ci] >= 0) {
+      const FrontDev ch = a.fronts[f.child[ci]];
+      bc[ci] = ch.b;
+      uc[ci] = reinterpret_cast<const C *>(a.ub_child) + ch.u_off * nrhs;
+      inv[ci] = a.inv + f.inv_off[ci];
+    }
+  }
+  const int *nodes = a.nodes + f.node_off;
+  const C *tv = reinterpret_cast<const C *>(a.tloc);
+  C *wl = reinterpret_cast<C *>(a.wloc);
+  C *u = reinterpret_cast<C *>(a.ub_cur) + f.u_off * nrhs;
+  for (int q = 0; q < nrhs; ++q) {
+    for (int k = lane; k < n; k += 32) {
+      C w = czero<C>();
+      int64_t gi = 0;
+      if (k < p) {
+        gi = q * ldt + voff + nodes[k];
+        w = tv[gi];
+      }
+#pragma unroll
+      for (int ci = 0; ci < 2; ++ci)
+        if (uc[ci]) {
+          const int t = inv[ci][k];
+          if (t >= 0) w = cadd(w, uc[ci][(int64_t)q * bc[ci] + t]);
+        }
+      if (k < p) wl[gi] = w;
+      else u[(int64_t)q * b + (k - p)] = w;
+    }
+  }
+}
+
+// Going up, part 2: lane = border row r;
+// u[r] = w_b[r] + sum_j (-G21)(r, j) w_p[j]  (w_b already in u).
 template <typename R, int ROWS>
-__global__ void __launch_bounds__(256) mf_up(MfArgs a, const int2 *__restrict__ items, int nitems, int split,
-                                             int nrhs, int64_t ldt) {
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_up(MfArgs a, const int2 *__restrict__ items,
+                                                                     int nitems, int split, int nrhs, int64_t ldt) {
   using C = typename CT<R>::T;
   constexpr int GROUPS = 256 / ROWS;
-  __shared__ C part[256];
+  __shared__ C part[MF_MAXSEG * 256 / 2];
   const int g = threadIdx.x / ROWS, lane = threadIdx.x % ROWS;
   const int ipc = GROUPS / split;
   const int il = g / split, sidx = g - il * split;
   const int it = blockIdx.x * ipc + il;
   const bool active = it < nitems;
   const unsigned mask = ROWS == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
-  int p = 0, b = 0, r = 0, j0s = 0, j0e = 0, chunk = 0;
+  int p = 0, b = 0, r = 0, seg0 = 0, seg1 = 0, nseg = 0;
   bool row = false;
   const C *G = nullptr;
-  const C *uc[2] = {nullptr, nullptr};
-  int bc[2] = {0, 0};
-  const int *inv[2] = {nullptr, nullptr};
   const int *nodes = nullptr;
   int64_t voff = 0;
   C *u = nullptr;
@@ -440,80 +553,38 @@ __global__ void __launch_bounds__(256) mf_up(MfArgs a, const int2 *__restrict__ 
     const FrontDev f = a.fronts[item.x];
     p = f.p;
     b = f.b;
-    chunk = item.y;
-    const int n = p + b;
     voff = a.strips[f.strip].vec_off;
-    G = reinterpret_cast<const C *>(a.fac) + f.fac_off + (int64_t)p * n;  // -G21, b x p, ld b
+    G = reinterpret_cast<const C *>(a.fac) + f.fac_off + (int64_t)p * (p + b);  // -G21, b x p, ld b
     r = item.y * ROWS + lane;
     row = r < b;
-#pragma unroll
-    for (int ci = 0; ci < 2; ++ci) {
-      if (f.child[ci] >= 0) {
-        const FrontDev ch = a.fronts[f.child[ci]];
-        bc[ci] = ch.b;
-        uc[ci] = reinterpret_cast<const C *>(a.ub_child) + ch.u_off * nrhs;
-        inv[ci] = a.inv + f.inv_off[ci];
-      }
-    }
     nodes = a.nodes + f.node_off;
     u = reinterpret_cast<C *>(a.ub_cur) + f.u_off * nrhs;
-    const int nch = (p + ROWS - 1) / ROWS;
-    j0s = (sidx * nch / split) * ROWS;
-    j0e = ((sidx + 1) * nch / split) * ROWS;
+    nseg = (p + MF_SEG - 1) / MF_SEG;
+    seg0 = sidx * nseg / split;
+    seg1 = (sidx + 1) * nseg / split;
   }
-  const C *tv = reinterpret_cast<const C *>(a.tloc);
-  C *wl = reinterpret_cast<C *>(a.wloc);
+  const C *wl = reinterpret_cast<const C *>(a.wloc);
   for (int q = 0; q < nrhs; ++q) {
-    C acc = czero<C>();
+    const int64_t base = q * ldt + voff;
+    C total = czero<C>();
     if (active) {
-      if (row && sidx == 0) {
-#pragma unroll
-        for (int ci = 0; ci < 2; ++ci)
-          if (uc[ci]) {
-            const int t = inv[ci][p + r];
-            if (t >= 0) acc = cadd(acc, uc[ci][(int64_t)q * bc[ci] + t]);
-          }
-      }
-      for (int j0 = j0s; j0 < j0e; j0 += ROWS) {
-        const int j = j0 + lane;
-        C wj = czero<C>();
-        if (j < p) {
-          const int64_t gi = q * ldt + voff + nodes[j];
-          wj = tv[gi];
-#pragma unroll
-          for (int ci = 0; ci < 2; ++ci)
-            if (uc[ci]) {
-              const int t = inv[ci][j];
-              if (t >= 0) wj = cadd(wj, uc[ci][(int64_t)q * bc[ci] + t]);
-            }
-          if (chunk == 0) wl[gi] = wj;
-        }
-        const int jb = min(ROWS, p - j0);
-        if (jb == ROWS) {
-#pragma unroll 8
-          for (int jj = 0; jj < ROWS; ++jj) {
-            const C wv = shfl_w<ROWS>(mask, wj, jj);
-            if (row) acc = cfma(G[(int64_t)(j0 + jj) * b + r], wv, acc);
-          }
-        } else {
-          for (int jj = 0; jj < jb; ++jj) {
-            const C wv = shfl_w<ROWS>(mask, wj, jj);
-            if (row) acc = cfma(G[(int64_t)(j0 + jj) * b + r], wv, acc);
-          }
-        }
+      if (row && sidx == 0) total = u[(int64_t)q * b + r];
+      auto gather = [&](int j) { return wl[base + nodes[j]]; };
+      for (int sg = seg0; sg < seg1; ++sg) {
+        const C sv = seg_dot<ROWS, C>(G, b, r, row, sg * MF_SEG, min(p, (sg + 1) * MF_SEG), lane, mask, gather);
+        if (split == 1) total = cadd(total, sv);
+        else part[(il * MF_MAXSEG + sg) * ROWS + lane] = sv;
       }
     }
     if (split > 1) {
-      part[threadIdx.x] = acc;
       __syncthreads();
       if (active && row && sidx == 0) {
-        C sum = acc;
-        for (int t = 1; t < split; ++t) sum = cadd(sum, part[(il * split + t) * ROWS + lane]);
-        u[(int64_t)q * b + r] = sum;
+        for (int sg = 0; sg < nseg; ++sg) total = cadd(total, part[(il * MF_MAXSEG + sg) * ROWS + lane]);
+        u[(int64_t)q * b + r] = total;
       }
       __syncthreads();
     } else if (active && row) {
-      u[(int64_t)q * b + r] = acc;
+      u[(int64_t)q * b + r] = total;
     }
   }
 }
@@ -521,18 +592,18 @@ __global__ void __launch_bounds__(256) mf_up(MfArgs a, const int2 *__restrict__ 
 // Coming down: lane = pivot row r;
 // x[r] = sum_{c<p} Finv(r, c) w_p[c] - sum_{c>=p} H12(r, c) x_b[c].
 template <typename R, int ROWS>
-__global__ void __launch_bounds__(256) mf_down(MfArgs a, const int2 *__restrict__ items, int nitems, int split,
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_down(MfArgs a, const int2 *__restrict__ items, int nitems, int split,
                                                int nrhs, int64_t ldt) {
   using C = typename CT<R>::T;
   constexpr int GROUPS = 256 / ROWS;
-  __shared__ C part[256];
+  __shared__ C part[MF_MAXSEG * 256 / 2];
   const int g = threadIdx.x / ROWS, lane = threadIdx.x % ROWS;
   const int ipc = GROUPS / split;
   const int il = g / split, sidx = g - il * split;
   const int it = blockIdx.x * ipc + il;
   const bool active = it < nitems;
   const unsigned mask = ROWS == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
-  int p = 0, n = 0, r = 0, c0s = 0, c0e = 0;
+  int p = 0, n = 0, r = 0, seg0 = 0, seg1 = 0, nseg = 0;
   bool row = false;
   const C *Fm = nullptr;
   const int *nodes = nullptr;
@@ -547,61 +618,42 @@ __global__ void __launch_bounds__(256) mf_down(MfArgs a, const int2 *__restrict_
     r = item.y * ROWS + lane;
     row = r < p;
     nodes = a.nodes + f.node_off;
-    const int nch = (n + ROWS - 1) / ROWS;
-    c0s = (sidx * nch / split) * ROWS;
-    c0e = ((sidx + 1) * nch / split) * ROWS;
+    nseg = (n + MF_SEG - 1) / MF_SEG;
+    seg0 = sidx * nseg / split;
+    seg1 = (sidx + 1) * nseg / split;
   }
   C *tv = reinterpret_cast<C *>(a.tloc);
   const C *wl = reinterpret_cast<const C *>(a.wloc);
   for (int q = 0; q < nrhs; ++q) {
     const int64_t base = q * ldt + voff;
-    C acc = czero<C>();
+    C total = czero<C>();
     if (active) {
-      for (int c0 = c0s; c0 < c0e; c0 += ROWS) {
-        const int c = c0 + lane;
-        C v = czero<C>();
-        if (c < p) v = wl[base + nodes[c]];
-        else if (c < n) v = cneg(tv[base + nodes[c]]);
-        const int cb = min(ROWS, n - c0);
-        if (cb == ROWS) {
-#pragma unroll 8
-          for (int cc = 0; cc < ROWS; ++cc) {
-            const C vv = shfl_w<ROWS>(mask, v, cc);
-            if (row) acc = cfma(Fm[(int64_t)(c0 + cc) * p + r], vv, acc);
-          }
-        } else {
-          for (int cc = 0; cc < cb; ++cc) {
-            const C vv = shfl_w<ROWS>(mask, v, cc);
-            if (row) acc = cfma(Fm[(int64_t)(c0 + cc) * p + r], vv, acc);
-          }
-        }
+      auto gather = [&](int c) { return c < p ? wl[base + nodes[c]] : cneg(tv[base + nodes[c]]); };
+      for (int sg = seg0; sg < seg1; ++sg) {
+        const C sv = seg_dot<ROWS, C>(Fm, p, r, row, sg * MF_SEG, min(n, (sg + 1) * MF_SEG), lane, mask, gather);
+        if (split == 1) total = cadd(total, sv);
+        else part[(il * MF_MAXSEG + sg) * ROWS + lane] = sv;
       }
     }
     if (split > 1) {
-      part[threadIdx.x] = acc;
       __syncthreads();
       if (active && row && sidx == 0) {
-        C sum = acc;
-        for (int t = 1; t < split; ++t) sum = cadd(sum, part[(il * split + t) * ROWS + lane]);
-        tv[base + nodes[r]] = sum;
+        for (int sg = 0; sg < nseg; ++sg) total = cadd(total, part[(il * MF_MAXSEG + sg) * ROWS + lane]);
+        tv[base + nodes[r]] = total;
       }
       __syncthreads();
     } else if (active && row) {
-      tv[base + nodes[r]] = acc;
+      tv[base + nodes[r]] = total;
     }
   }
 }
 
 // ------------------------------------------------------------ launchers
-// fronts per CTA for the small kernel: as many warps as fit in ~200 KB
-template <typename R> static int small_wpc(int ldn) {
+// small-front launch shape: a warp per front (4 per CTA) up to n = 32, one
+// 128-thread CTA per front above
+template <typename R> static size_t small_smem(int ldn, int fpc) {
   using C = typename CT<R>::T;
-  const size_t per = sizeof(C) * (size_t)(ldn * ldn + 2 * ldn);
-  return (int)std::max<size_t>(1, std::min<size_t>(MF_SMALL_WARPS, (200u << 10) / per));
-}
-template <typename R> static size_t small_smem(int ldn) {
-  using C = typename CT<R>::T;
-  return sizeof(C) * small_wpc<R>(ldn) * (size_t)(ldn * ldn + 2 * ldn);
+  return sizeof(C) * fpc * (size_t)(ldn * ldn + 2 * ldn);
 }
 template <typename R> static size_t row_smem() {
   using C = typename CT<R>::T;
@@ -614,7 +666,9 @@ template <typename R> static size_t gemm_smem() {
 
 template <typename R> cudaError_t mf_setup_attributes() {
   cudaError_t e;
-  e = cudaFuncSetAttribute(mf_gj_small<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10);
+  e = cudaFuncSetAttribute(mf_gj_small<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(mf_gj_small<R, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(mf_gj_row<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem<R>());
   if (e != cudaSuccess) return e;
@@ -626,9 +680,12 @@ void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_
   if (L.nf == 0) return;
   if (L.min_n <= MF_SMALL) {
     const int ldn = std::min(L.max_n, MF_SMALL);
-    const int wpc = small_wpc<R>(ldn);
     if (hook) hook->before(K_SMALL, level, 0);
-    mf_gj_small<R><<<(L.nf + wpc - 1) / wpc, 32 * wpc, small_smem<R>(ldn), st>>>(a, L.f0, L.nf, ldn);
+    if (ldn <= 32) {
+      mf_gj_small<R, 32><<<(L.nf + 3) / 4, 128, small_smem<R>(ldn, 4), st>>>(a, L.f0, L.nf, ldn);
+    } else {
+      mf_gj_small<R, 128><<<L.nf, 128, small_smem<R>(ldn, 1), st>>>(a, L.f0, L.nf, ldn);
+    }
     if (hook) hook->after(K_SMALL, level, 0);
     count_launch();
   }
@@ -650,6 +707,13 @@ void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_
       count_launch(4);
     }
   }
+}
+
+template <typename R>
+void mf_up_gather_level(const MfArgs &a, const LevelInfo &L, int nrhs, int64_t ldt, cudaStream_t st) {
+  if (L.nf == 0) return;
+  mf_up_gather<R><<<(L.nf + 7) / 8, 256, 0, st>>>(a, L.f0, L.nf, nrhs, ldt);
+  count_launch();
 }
 
 template <typename R>
@@ -678,6 +742,8 @@ template cudaError_t mf_setup_attributes<double>();
 template cudaError_t mf_setup_attributes<float>();
 template void mf_factor_level<double>(const MfArgs &, const LevelInfo &, int, cudaStream_t, LaunchHook *);
 template void mf_factor_level<float>(const MfArgs &, const LevelInfo &, int, cudaStream_t, LaunchHook *);
+template void mf_up_gather_level<double>(const MfArgs &, const LevelInfo &, int, int64_t, cudaStream_t);
+template void mf_up_gather_level<float>(const MfArgs &, const LevelInfo &, int, int64_t, cudaStream_t);
 template void mf_up_level<double>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t);
 template void mf_up_level<float>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t);
 template void mf_down_level<double>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t);
