@@ -229,7 +229,22 @@ typedef struct {
   int down_calls;
 } stdd_profile;
 
-stdd_status stdd_set_profiling(stdd_ctx *ctx, int enable);
+/* level 0: off; 1: phase spans (factor, M^-1, matvec, Gram-Schmidt,
+ * solve); 2: also one span per launch of the dominant kernels (this
+ * bypasses the CUDA graphs of the M^-1 application). */
+stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
+
+/* Execution options; none of them changes a computed value.
+ *   STDD_OPT_GRAPHS   (default 1): replay captured CUDA graphs of the M^-1
+ *                     application (one graph per input/output buffer pair,
+ *                     captured on first use; the first use must not happen
+ *                     inside the caller's own stream capture).
+ *   STDD_OPT_AUTOTUNE (default 1): choose the substitution launch shapes per
+ *                     tree level by timing them once per level shape.
+ *   STDD_OPT_LEAF     (default 16): nested-dissection leaf size in nodes
+ *                     (changes the factorization, invalidates factors). */
+enum { STDD_OPT_GRAPHS = 1, STDD_OPT_AUTOTUNE = 2, STDD_OPT_LEAF = 3 };
+stdd_status stdd_set_option(stdd_ctx *ctx, int option, int value);
 stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);
 
 /* Host-only nested-dissection analysis of one W x H box (no GPU needed).

@@ -78,6 +78,7 @@ _SIGS = {
     "stdd_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, P(c_double), c_int]),
     "stdd_residual_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, P(c_double)]),
     "stdd_set_profiling": (c_int, [c_void_p, c_int]),
+    "stdd_set_option": (c_int, [c_void_p, c_int, c_int]),
     "stdd_get_profile": (c_int, [c_void_p, P(stdd_profile), c_int]),
     "stdd_nd_analyze": (c_int, [c_int, c_int, c_int, P(c_int), P(ctypes.c_longlong), c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_void_p]),
@@ -255,8 +256,16 @@ def stdd_residual_noalloc(ctx, x, b, r):
     return rel.value
 
 
-def stdd_set_profiling(ctx, enable=True):
-    return _check(ctx, lib.stdd_set_profiling(ctx, 1 if enable else 0))
+STDD_OPT_GRAPHS, STDD_OPT_AUTOTUNE, STDD_OPT_LEAF = 1, 2, 3
+
+
+def stdd_set_profiling(ctx, level=1):
+    """0 off, 1 phase spans, 2 phase + per-launch kernel spans (graphs off)."""
+    return _check(ctx, lib.stdd_set_profiling(ctx, int(level)))
+
+
+def stdd_set_option(ctx, option, value):
+    return _check(ctx, lib.stdd_set_option(ctx, int(option), int(value)))
 
 
 def stdd_get_profile(ctx, reset=True):

@@ -173,7 +173,7 @@ struct stdd_ctx {
 
   // phase profiling (CUDA events on the context stream)
   enum { PH_FACTOR = 0, PH_MINV, PH_MATVEC, PH_ORTHO, PH_SOLVE, PH_K0, PH_COUNT = PH_K0 + stdd::K_COUNT };
-  bool prof = false;
+  int prof = 0;  // 0 off, 1 phase spans, 2 phase + per-launch kernel spans
   struct Span {
     int phase;
     cudaEvent_t a, b;
@@ -200,6 +200,7 @@ struct stdd_ctx {
     if (id >= 0) CK(cudaEventRecord(spans[id].b, stream));
   }
   ~stdd_ctx() {
+    clear_graphs();
     for (auto e : ev_pool) cudaEventDestroy(e);
   }
 
@@ -214,7 +215,7 @@ struct stdd_ctx {
     stdd_ctx *c = nullptr;
     int open = -1;
     void before(int kind, int level, int k) override {
-      if (!c->prof) return;
+      if (c->prof < 2) return;
       open = c->pbegin(PH_K0 + kind);
       c->span_level.resize(c->spans.size(), -1);
       c->span_level[open] = level;
@@ -307,6 +308,18 @@ struct stdd_ctx {
   bool struct_ready = false;
   std::vector<int64_t> struct_key;
   void apply_minv(const double2 *v, double2 *z);
+  void enqueue_minv(const double2 *v, double2 *z);
+  // captured CUDA graphs of M^-1 applications, keyed by (input, output)
+  struct GraphEntry {
+    cudaGraphExec_t exec;
+    long long kernels;
+  };
+  std::map<std::pair<const void *, void *>, GraphEntry> minv_graphs;
+  bool use_graphs = true;
+  void clear_graphs() {
+    for (auto &kv : minv_graphs) cudaGraphExecDestroy(kv.second.exec);
+    minv_graphs.clear();
+  }
   template <typename R> void factor_t();
   template <typename R> void solve_levels(int nrhs_);
   template <typename R> void autotune();
@@ -371,6 +384,7 @@ void stdd_ctx::factor() {
   require_operator();
   build_strips();
   factored = false;
+  clear_graphs();
   std::vector<int64_t> key = {nx, ny, nsub, overlap, ipml, prec, leaf_max};
   key.insert(key.end(), cuts.begin(), cuts.end());
   if (!struct_ready || key != struct_key) {
@@ -671,6 +685,7 @@ template <typename R> void stdd_ctx::solve_levels(int nr) {
 
 void stdd_ctx::ensure_solve_buffers(int nr) {
   if (nr <= solve_nrhs_cap) return;
+  clear_graphs();
   const size_t E = elem();
   d_tloc.alloc(std::max<int64_t>(1, nloc) * nr * E);
   d_wloc.alloc(std::max<int64_t>(1, nloc) * nr * E);
@@ -684,6 +699,40 @@ void stdd_ctx::ensure_solve_buffers(int nr) {
 void stdd_ctx::apply_minv(const double2 *v, double2 *z) {
   ensure_solve_buffers(1);
   const int span = pbegin(PH_MINV);
+  // replay a captured graph of the whole application (one per input/output
+  // pair); per-launch profiling needs the individual launches
+  if (use_graphs && prof < 2) {
+    const auto key = std::make_pair(static_cast<const void *>(v), static_cast<void *>(z));
+    auto it = minv_graphs.find(key);
+    if (it == minv_graphs.end()) {
+      const long long before = __atomic_load_n(&stdd::g_launches, __ATOMIC_RELAXED);
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+      enqueue_minv(v, z);
+      const cudaError_t ce = cudaStreamEndCapture(stream, &g);
+      if (ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        throw CudaError(std::string("graph capture: ") + cudaGetErrorString(ce));
+      }
+      cudaGraphExec_t ex = nullptr;
+      const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) throw CudaError(std::string("graph instantiate: ") + cudaGetErrorString(ie));
+      const long long kernels = __atomic_load_n(&stdd::g_launches, __ATOMIC_RELAXED) - before;
+      __atomic_add_fetch(&stdd::g_launches, -kernels, __ATOMIC_RELAXED);  // counted at replay
+      it = minv_graphs.emplace(key, GraphEntry{ex, kernels}).first;
+    }
+    CK(cudaGraphLaunch(it->second.exec, stream));
+    stdd::count_launch((int)it->second.kernels);
+    pend(span);
+    return;
+  }
+  enqueue_minv(v, z);
+  pend(span);
+  CK(cudaGetLastError());
+}
+
+void stdd_ctx::enqueue_minv(const double2 *v, double2 *z) {
   if (prec == STDD_PREC_FP64) {
     stdd::launch_restrict<double>(d_strips.as<StripDev>(), nsub, nloc_max, ny, nullptr, v, d_tloc.p, stream);
     solve_levels<double>(1);
@@ -695,7 +744,6 @@ void stdd_ctx::apply_minv(const double2 *v, double2 *z) {
     stdd::launch_synthesize<float>(d_strips.as<StripDev>(), nsub, nx, ny, d_colstrip.as<int>(), d_tloc.p, z,
                                    stream);
   }
-  pend(span);
   CK(cudaGetLastError());
 }
 
@@ -1246,8 +1294,36 @@ stdd_status stdd_residual(stdd_ctx *c, const double *x, const double *b, double 
   });
 }
 
-stdd_status stdd_set_profiling(stdd_ctx *c, int enable) {
-  return guarded(c, [&] { c->prof = enable != 0; });
+stdd_status stdd_set_profiling(stdd_ctx *c, int level) {
+  return guarded(c, [&] {
+    if (level < 0 || level > 2) throw ArgError("profiling level must be 0, 1 or 2");
+    c->prof = level;
+  });
+}
+
+stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
+  return guarded(c, [&] {
+    switch (option) {
+      case STDD_OPT_GRAPHS:
+        c->use_graphs = value != 0;
+        if (!c->use_graphs) c->clear_graphs();
+        break;
+      case STDD_OPT_AUTOTUNE:
+        c->autotune_on = value != 0;
+        break;
+      case STDD_OPT_LEAF:
+        if (value < 1 || value > 4096) throw ArgError("leaf size out of range");
+        if (value != c->leaf_max) {
+          c->leaf_max = value;
+          c->shapes.clear();
+          c->struct_ready = false;
+          c->invalidate_factors();
+        }
+        break;
+      default:
+        throw ArgError("unknown option");
+    }
+  });
 }
 
 stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {

@@ -213,3 +213,42 @@ def test_deterministic(rnd):
         outs.append(x.cpu().numpy())
         s.close()
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_graphs_and_autotune_do_not_change_results(rnd):
+    """CUDA-graph replay of M^-1 and the autotuned substitution launch shapes
+    only change speed: results are bitwise identical with and without them."""
+    from paper_2509_20801_gb300 import (STDD_OPT_AUTOTUNE, STDD_OPT_GRAPHS, stdd_apply_preconditioner,
+                                        stdd_set_option)
+    w, P, D = rnd
+    v = torch.from_numpy(W.random_vector(P.n, seed=8)[0]).to(DEV)
+    outs = []
+    for graphs, tune in ((1, 1), (0, 1), (1, 0), (0, 0)):
+        s = _solver(w)
+        stdd_set_option(s.ctx, STDD_OPT_GRAPHS, graphs)
+        stdd_set_option(s.ctx, STDD_OPT_AUTOTUNE, tune)
+        s.factor()
+        z = torch.empty_like(v)
+        for _ in range(2):                 # second call replays the captured graph
+            stdd_apply_preconditioner(s.ctx, v, z)
+        s.set_sources(torch.from_numpy(w.b).to(DEV))
+        x = torch.empty(w.b.shape, dtype=torch.complex128, device=DEV)
+        s.solve(x, restart=20, rtol=1e-10, maxit=200)
+        outs.append((z.cpu().numpy(), x.cpu().numpy()))
+        s.close()
+    for z, x in outs[1:]:
+        assert np.array_equal(z, outs[0][0]) and np.array_equal(x, outs[0][1])
+
+
+@pytest.mark.parametrize("leaf", [4, 64])
+def test_other_leaf_sizes_match_oracle(leaf, cyl):
+    from paper_2509_20801_gb300 import STDD_OPT_LEAF, stdd_apply_preconditioner, stdd_set_option
+    w, P, D = cyl
+    s = _solver(w)
+    stdd_set_option(s.ctx, STDD_OPT_LEAF, leaf)
+    s.factor()
+    v = W.random_vector(P.n, seed=6)[0]
+    z = torch.empty(P.n, dtype=torch.complex128, device=DEV)
+    stdd_apply_preconditioner(s.ctx, torch.from_numpy(v).to(DEV), z)
+    assert _rel(z.cpu().numpy(), D.apply_Minv(v)) < 1e-10
+    s.close()
