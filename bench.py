@@ -48,18 +48,19 @@ def parse():
     ap.add_argument("--workload", default="metalens", choices=["metalens", "metalens-small", "cylinder"],
                     help="metalens: 4096x1024, 16 strips (the benchmark); metalens-small: 1024x1024, 4 strips "
                          "(profiling captures); cylinder: 200x200, 2 strips")
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per step (line sources)")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
-def make_workload(name):
+def make_workload(name, nrhs=1):
     import workloads as W
     if name == "metalens":
-        return W.metalens()
+        return W.metalens(nrhs=nrhs)
     if name == "metalens-small":
-        return W.metalens(nx=1024, ny=1024, nsub=4)
+        return W.metalens(nx=1024, ny=1024, nsub=4, nrhs=nrhs)
     return W.cylinder()
 
 
@@ -221,7 +222,7 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.nrhs)
     N = w.n * w.nrhs
     peaks = measured_peaks()
     fp64_tf = gemm_peak(torch, torch.float64, 4096)

@@ -166,7 +166,8 @@ struct stdd_ctx {
 
   // sources and Krylov state
   DBuf d_b, d_x, d_r, d_V, d_Z, d_w, d_part, d_h, d_nrm, d_y, d_pre, d_fpart;
-  int V_cols = 0;
+  int V_cols = 0, V_rhs = 0;
+  bool last_noconv = false;
   std::vector<std::vector<double>> history;
   int last_its = 0, last_reorth = 0;
   double last_res = 0;
@@ -308,13 +309,14 @@ struct stdd_ctx {
   bool struct_ready = false;
   std::vector<int64_t> struct_key;
   void apply_minv(const double2 *v, double2 *z);
-  void enqueue_minv(const double2 *v, double2 *z);
+  void apply_minv_multi(const std::vector<const double2 *> &vs, const std::vector<double2 *> &zs);
+  void enqueue_minv(const std::vector<const double2 *> &vs, const std::vector<double2 *> &zs);
   // captured CUDA graphs of M^-1 applications, keyed by (input, output)
   struct GraphEntry {
     cudaGraphExec_t exec;
     long long kernels;
   };
-  std::map<std::pair<const void *, void *>, GraphEntry> minv_graphs;
+  std::map<std::vector<const void *>, GraphEntry> minv_graphs;
   bool use_graphs = true;
   void clear_graphs() {
     for (auto &kv : minv_graphs) cudaGraphExecDestroy(kv.second.exec);
@@ -329,7 +331,7 @@ struct stdd_ctx {
   bool autotune_on = true;
   MfArgs mf_args(int level_parity_cur, bool solve) const;
   void ensure_krylov(int m);
-  void gmres(int rhs, const stdd_solve_opts &o, double2 *x);
+  void gmres_multi(const stdd_solve_opts &o);
   void richardson(int rhs, const stdd_solve_opts &o, double2 *x);
   int64_t device_bytes() const;
 };
@@ -694,21 +696,33 @@ void stdd_ctx::ensure_solve_buffers(int nr) {
   solve_nrhs_cap = nr;
 }
 
-// z = M^-1 v: restriction to owned columns, batched forward / back
-// substitution over every strip, synthesis of the full local fields.
+// z_i = M^-1 v_i for every pair: restriction of each v_i to the strips'
+// owned columns (local slot i), batched upward / downward sweeps over all
+// strips and all slots, synthesis of the full local fields into z_i.
 void stdd_ctx::apply_minv(const double2 *v, double2 *z) {
-  ensure_solve_buffers(1);
+  std::vector<const double2 *> vs{v};
+  std::vector<double2 *> zs{z};
+  apply_minv_multi(vs, zs);
+}
+
+void stdd_ctx::apply_minv_multi(const std::vector<const double2 *> &vs, const std::vector<double2 *> &zs) {
+  const int na = (int)vs.size();
+  ensure_solve_buffers(na);
   const int span = pbegin(PH_MINV);
-  // replay a captured graph of the whole application (one per input/output
-  // pair); per-launch profiling needs the individual launches
+  // replay a captured graph of the whole application (one per list of
+  // buffers); per-launch profiling needs the individual launches
   if (use_graphs && prof < 2) {
-    const auto key = std::make_pair(static_cast<const void *>(v), static_cast<void *>(z));
+    std::vector<const void *> key;
+    for (int i = 0; i < na; ++i) {
+      key.push_back(vs[i]);
+      key.push_back(zs[i]);
+    }
     auto it = minv_graphs.find(key);
     if (it == minv_graphs.end()) {
       const long long before = __atomic_load_n(&stdd::g_launches, __ATOMIC_RELAXED);
       cudaGraph_t g = nullptr;
       CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-      enqueue_minv(v, z);
+      enqueue_minv(vs, zs);
       const cudaError_t ce = cudaStreamEndCapture(stream, &g);
       if (ce != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -727,40 +741,52 @@ void stdd_ctx::apply_minv(const double2 *v, double2 *z) {
     pend(span);
     return;
   }
-  enqueue_minv(v, z);
+  enqueue_minv(vs, zs);
   pend(span);
   CK(cudaGetLastError());
 }
 
-void stdd_ctx::enqueue_minv(const double2 *v, double2 *z) {
+void stdd_ctx::enqueue_minv(const std::vector<const double2 *> &vs, const std::vector<double2 *> &zs) {
+  const int na = (int)vs.size();
+  const size_t E = elem();
+  auto slot = [&](int i) { return static_cast<void *>(d_tloc.as<char>() + (size_t)i * nloc * E); };
   if (prec == STDD_PREC_FP64) {
-    stdd::launch_restrict<double>(d_strips.as<StripDev>(), nsub, nloc_max, ny, nullptr, v, d_tloc.p, stream);
-    solve_levels<double>(1);
-    stdd::launch_synthesize<double>(d_strips.as<StripDev>(), nsub, nx, ny, d_colstrip.as<int>(), d_tloc.p, z,
-                                    stream);
+    for (int i = 0; i < na; ++i)
+      stdd::launch_restrict<double>(d_strips.as<StripDev>(), nsub, nloc_max, ny, nullptr, vs[i], slot(i), stream);
+    solve_levels<double>(na);
+    for (int i = 0; i < na; ++i)
+      stdd::launch_synthesize<double>(d_strips.as<StripDev>(), nsub, nx, ny, d_colstrip.as<int>(), slot(i), zs[i],
+                                      stream);
   } else {
-    stdd::launch_restrict<float>(d_strips.as<StripDev>(), nsub, nloc_max, ny, nullptr, v, d_tloc.p, stream);
-    solve_levels<float>(1);
-    stdd::launch_synthesize<float>(d_strips.as<StripDev>(), nsub, nx, ny, d_colstrip.as<int>(), d_tloc.p, z,
-                                   stream);
+    for (int i = 0; i < na; ++i)
+      stdd::launch_restrict<float>(d_strips.as<StripDev>(), nsub, nloc_max, ny, nullptr, vs[i], slot(i), stream);
+    solve_levels<float>(na);
+    for (int i = 0; i < na; ++i)
+      stdd::launch_synthesize<float>(d_strips.as<StripDev>(), nsub, nx, ny, d_colstrip.as<int>(), slot(i), zs[i],
+                                     stream);
   }
   CK(cudaGetLastError());
 }
 
 void stdd_ctx::ensure_krylov(int m) {
   const int64_t n = N();
-  if (V_cols < m) {
-    d_V.alloc((size_t)(m + 1) * n * sizeof(double2));
-    d_Z.alloc((size_t)m * n * sizeof(double2));
+  const int nq = std::max(1, nrhs);
+  if (V_cols < m || V_rhs < nq) {
+    d_V.release();
+    d_Z.release();
+    d_V.alloc((size_t)(m + 1) * n * nq * sizeof(double2));
+    d_Z.alloc((size_t)m * n * nq * sizeof(double2));
     V_cols = m;
+    V_rhs = nq;
+    clear_graphs();
   }
-  d_x.alloc(n * sizeof(double2));
+  d_x.alloc(n * nq * sizeof(double2));
   d_r.alloc(n * sizeof(double2));
   d_w.alloc(n * sizeof(double2));
   d_part.alloc((size_t)stdd::krylov_partial_blocks() * (m + 2) * sizeof(double2));
-  d_h.alloc((size_t)(2 * (m + 2)) * sizeof(double2));
-  d_nrm.alloc(4 * sizeof(double));
-  d_y.alloc((size_t)(m + 1) * sizeof(double2));
+  d_h.alloc((size_t)(2 * (m + 2)) * nq * sizeof(double2));
+  d_nrm.alloc((4 + 2 * (size_t)nq) * sizeof(double));
+  d_y.alloc((size_t)(m + 1) * nq * sizeof(double2));
   d_fpart.alloc((size_t)std::max(1, 2 * nsub) * sizeof(double));
 }
 
@@ -790,107 +816,170 @@ double dev_norm(double2 *x, int64_t n, DBuf &part, DBuf &nrm, cudaStream_t st) {
 }
 }  // namespace
 
-// Restarted flexible GMRES(m), right preconditioned by M^-1 (FP64; CGS2
-// orthogonalisation; Givens rotations and the small triangular solve on the
-// host).  x holds the initial guess on entry and the iterate on exit.
-void stdd_ctx::gmres(int rhs, const stdd_solve_opts &o, double2 *x) {
-  const int m = o.restart;
+// Restarted flexible GMRES(m), right preconditioned by M^-1, for every
+// right-hand side at once: each has its own basis V_q, Z_q, Hessenberg
+// matrix, Givens rotations and restart cycle, and they advance in lockstep
+// so that one batched M^-1 application serves all systems still iterating.
+// FP64 throughout; classical Gram-Schmidt with a second pass when the first
+// one shrank ||w|| below 1/sqrt(2) of its value (Daniel-Gragg-Kaufman-
+// Stewart); Givens rotations and the small triangular solves on the host.
+// d_x holds the initial guesses on entry and the iterates on exit.
+void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
+  const int m = o.restart, nq = nrhs;
   const int64_t n = N();
   ensure_krylov(m);
-  auto &hist = history[rhs];
-  const double2 *b = d_b.as<double2>() + (int64_t)rhs * n;
-  const double bnorm = dev_norm(const_cast<double2 *>(b), n, d_part, d_nrm, stream);
-  if (bnorm == 0) {
-    CK(cudaMemsetAsync(x, 0, n * sizeof(double2), stream));
-    hist.push_back(0.0);
-    last_res = 0;
-    return;
-  }
-  double2 *V = d_V.as<double2>(), *Z = d_Z.as<double2>(), *r = d_r.as<double2>();
-  double2 *h1 = d_h.as<double2>(), *h2 = h1 + (m + 2);
-  double *nrm = d_nrm.as<double>();
+  double2 *Vb = d_V.as<double2>(), *Zb = d_Z.as<double2>(), *X = d_x.as<double2>(), *r = d_r.as<double2>();
+  double *nrm_base = d_nrm.as<double>();
   double *part = reinterpret_cast<double *>(d_part.p);
-  int its = 0, reorth = 0;
-  std::vector<cd> H((size_t)(m + 1) * m), g(m + 1), sn(m), hv(2 * (m + 2));
-  std::vector<double> cs(m);
+  auto V = [&](int q, int j) { return Vb + ((int64_t)q * (m + 1) + j) * n; };
+  auto Z = [&](int q, int j) { return Zb + ((int64_t)q * m + j) * n; };
+  auto h1 = [&](int q) { return d_h.as<double2>() + (size_t)q * 2 * (m + 2); };
+  auto h2 = [&](int q) { return h1(q) + (m + 2); };
+  auto nrmq = [&](int q) { return nrm_base + 4 + 2 * q; };
+  struct St {
+    std::vector<cd> H, g, sn, hv;
+    std::vector<double> cs;
+    double bnorm = 0, nrm2 = 0, res = 0;
+    int its = 0, reorth = 0, k = 0;
+    bool done = false;
+  };
+  std::vector<St> S(nq);
+  for (int q = 0; q < nq; ++q) {
+    St &t = S[q];
+    t.H.assign((size_t)(m + 1) * m, 0);
+    t.g.assign(m + 1, 0);
+    t.sn.assign(m, 0);
+    t.cs.assign(m, 0);
+    t.hv.assign(2 * (m + 2), 0);
+    const double2 *b = d_b.as<double2>() + (int64_t)q * n;
+    t.bnorm = dev_norm(const_cast<double2 *>(b), n, d_part, d_nrm, stream);
+    if (t.bnorm == 0) {
+      CK(cudaMemsetAsync(X + (int64_t)q * n, 0, n * sizeof(double2), stream));
+      history[q].push_back(0.0);
+      t.done = true;
+    }
+  }
   while (true) {
-    int sp = pbegin(PH_MATVEC);
-    stdd::launch_residual(grid(), b, x, r, stream);
-    pend(sp);
-    const double beta = dev_norm(r, n, d_part, d_nrm, stream);
-    if (hist.empty()) hist.push_back(beta / bnorm);
-    last_res = beta / bnorm;
-    if (!std::isfinite(beta)) throw std::range_error("non-finite residual");
-    if (beta / bnorm <= o.rtol || its >= o.maxit) break;
-    stdd::launch_scale(r, nrm, V, n, stream);
-    std::fill(H.begin(), H.end(), cd(0));
-    std::fill(g.begin(), g.end(), cd(0));
-    g[0] = beta;
-    int k = 0;
-    for (int j = 0; j < m; ++j) {
-      double2 *vj = V + (int64_t)j * n, *zj = Z + (int64_t)j * n, *w = V + (int64_t)(j + 1) * n;
-      apply_minv(vj, zj);
-      sp = pbegin(PH_MATVEC);
-      stdd::launch_stencil(grid(), zj, w, stream);
+    // restart cycle: true residuals, first basis vectors
+    std::vector<int> act;
+    for (int q = 0; q < nq; ++q) {
+      St &t = S[q];
+      if (t.done) continue;
+      const double2 *b = d_b.as<double2>() + (int64_t)q * n;
+      int sp = pbegin(PH_MATVEC);
+      stdd::launch_residual(grid(), b, X + (int64_t)q * n, r, stream);
       pend(sp);
-      // classical Gram-Schmidt; a second pass only when the first one shrank
-      // ||w|| below 1/sqrt(2) of its value (Daniel-Gragg-Kaufman-Stewart)
+      const double beta = dev_norm(r, n, d_part, d_nrm, stream);
+      if (history[q].empty()) history[q].push_back(beta / t.bnorm);
+      t.res = beta / t.bnorm;
+      if (!std::isfinite(beta)) throw std::range_error("non-finite residual");
+      if (t.res <= o.rtol || t.its >= o.maxit) {
+        t.done = true;
+        continue;
+      }
+      stdd::launch_scale(r, d_nrm.as<double>(), V(q, 0), n, stream);
+      std::fill(t.H.begin(), t.H.end(), cd(0));
+      std::fill(t.g.begin(), t.g.end(), cd(0));
+      t.g[0] = beta;
+      t.k = 0;
+      act.push_back(q);
+    }
+    if (act.empty()) break;
+    std::vector<int> inner = act;
+    for (int j = 0; j < m && !inner.empty(); ++j) {
+      std::vector<const double2 *> vs;
+      std::vector<double2 *> zs;
+      for (int q : inner) {
+        vs.push_back(V(q, j));
+        zs.push_back(Z(q, j));
+      }
+      apply_minv_multi(vs, zs);
+      int sp = pbegin(PH_MATVEC);
+      for (int q : inner) stdd::launch_stencil(grid(), Z(q, j), V(q, j + 1), stream);
+      pend(sp);
       sp = pbegin(PH_ORTHO);
-      stdd::launch_mdot(V, n, j + 1, w, n, d_part.as<double2>(), h1, stream, 1);
-      stdd::launch_maxpy_norm(V, n, j + 1, h1, w, n, part, nrm, stream);
-      double nrm2 = 0;
-      CK(cudaMemcpyAsync(hv.data(), h1, sizeof(double2) * (j + 2), cudaMemcpyDeviceToHost, stream));
-      CK(cudaMemcpyAsync(&nrm2, nrm, sizeof(double), cudaMemcpyDeviceToHost, stream));
+      for (int q : inner) {
+        double2 *w = V(q, j + 1);
+        stdd::launch_mdot(V(q, 0), n, j + 1, w, n, d_part.as<double2>(), h1(q), stream, 1);
+        stdd::launch_maxpy_norm(V(q, 0), n, j + 1, h1(q), w, n, part, nrmq(q), stream);
+        CK(cudaMemcpyAsync(S[q].hv.data(), h1(q), sizeof(double2) * (j + 2), cudaMemcpyDeviceToHost, stream));
+        CK(cudaMemcpyAsync(&S[q].nrm2, nrmq(q), sizeof(double), cudaMemcpyDeviceToHost, stream));
+      }
       CK(cudaStreamSynchronize(stream));
-      const double before2 = hv[j + 1].real();
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hv[i];
-      if (nrm2 < 0.5 * before2) {
-        stdd::launch_mdot(V, n, j + 1, w, n, d_part.as<double2>(), h2, stream);
-        stdd::launch_maxpy_norm(V, n, j + 1, h2, w, n, part, nrm, stream);
-        CK(cudaMemcpyAsync(hv.data() + (m + 2), h2, sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost, stream));
-        CK(cudaMemcpyAsync(&nrm2, nrm, sizeof(double), cudaMemcpyDeviceToHost, stream));
-        CK(cudaStreamSynchronize(stream));
-        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += hv[(m + 2) + i];
-        ++reorth;
+      std::vector<int> again;
+      for (int q : inner) {
+        St &t = S[q];
+        for (int i = 0; i <= j; ++i) t.H[(size_t)i * m + j] = t.hv[i];
+        if (t.nrm2 < 0.5 * t.hv[j + 1].real()) again.push_back(q);
+      }
+      for (int q : again) {
+        double2 *w = V(q, j + 1);
+        stdd::launch_mdot(V(q, 0), n, j + 1, w, n, d_part.as<double2>(), h2(q), stream);
+        stdd::launch_maxpy_norm(V(q, 0), n, j + 1, h2(q), w, n, part, nrmq(q), stream);
+        CK(cudaMemcpyAsync(S[q].hv.data() + (m + 2), h2(q), sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost,
+                           stream));
+        CK(cudaMemcpyAsync(&S[q].nrm2, nrmq(q), sizeof(double), cudaMemcpyDeviceToHost, stream));
+      }
+      if (!again.empty()) CK(cudaStreamSynchronize(stream));
+      for (int q : again) {
+        St &t = S[q];
+        for (int i = 0; i <= j; ++i) t.H[(size_t)i * m + j] += t.hv[(m + 2) + i];
+        ++t.reorth;
       }
       pend(sp);
-      const double hn = std::sqrt(nrm2);
-      H[(size_t)(j + 1) * m + j] = hn;
-      for (int i = 0; i < j; ++i) {
-        const cd t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
-        H[(size_t)(i + 1) * m + j] = -std::conj(sn[i]) * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = t;
+      std::vector<int> next;
+      for (int q : inner) {
+        St &t = S[q];
+        std::vector<cd> &H = t.H;
+        const double hn = std::sqrt(t.nrm2);
+        H[(size_t)(j + 1) * m + j] = hn;
+        for (int i = 0; i < j; ++i) {
+          const cd a = t.cs[i] * H[(size_t)i * m + j] + t.sn[i] * H[(size_t)(i + 1) * m + j];
+          H[(size_t)(i + 1) * m + j] = -std::conj(t.sn[i]) * H[(size_t)i * m + j] + t.cs[i] * H[(size_t)(i + 1) * m + j];
+          H[(size_t)i * m + j] = a;
+        }
+        givens(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j], t.cs[j], t.sn[j]);
+        const cd hjj = t.cs[j] * H[(size_t)j * m + j] + t.sn[j] * H[(size_t)(j + 1) * m + j];
+        H[(size_t)j * m + j] = hjj;
+        H[(size_t)(j + 1) * m + j] = 0;
+        t.g[j + 1] = -std::conj(t.sn[j]) * t.g[j];
+        t.g[j] = t.cs[j] * t.g[j];
+        ++t.its;
+        t.k = j + 1;
+        const double est = std::abs(t.g[j + 1]) / t.bnorm;
+        history[q].push_back(est);
+        if (!std::isfinite(est)) throw std::range_error("non-finite residual estimate");
+        const bool breakdown = !(hn > 0) || std::abs(hjj) == 0;
+        if (!breakdown) stdd::launch_scale(V(q, j + 1), nrmq(q), V(q, j + 1), n, stream);
+        if (!(est <= o.rtol || t.its >= o.maxit || breakdown)) next.push_back(q);
       }
-      givens(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j], cs[j], sn[j]);
-      const cd hjj = cs[j] * H[(size_t)j * m + j] + sn[j] * H[(size_t)(j + 1) * m + j];
-      H[(size_t)j * m + j] = hjj;
-      H[(size_t)(j + 1) * m + j] = 0;
-      g[j + 1] = -std::conj(sn[j]) * g[j];
-      g[j] = cs[j] * g[j];
-      ++its;
-      k = j + 1;
-      const double est = std::abs(g[j + 1]) / bnorm;
-      hist.push_back(est);
-      if (!std::isfinite(est)) throw std::range_error("non-finite residual estimate");
-      const bool breakdown = !(hn > 0) || std::abs(hjj) == 0;
-      if (!breakdown) stdd::launch_scale(w, nrm, w, n, stream);
-      if (est <= o.rtol || its >= o.maxit || breakdown) break;
+      inner.swap(next);
     }
-    // y = R^-1 g, x += Z y
-    std::vector<cd> y(k);
-    for (int i = k - 1; i >= 0; --i) {
-      cd s = g[i];
-      for (int l = i + 1; l < k; ++l) s -= H[(size_t)i * m + l] * y[l];
-      y[i] = s / H[(size_t)i * m + i];
+    // x_q += Z_q y_q with y_q = R_q^-1 g_q
+    for (int q : act) {
+      St &t = S[q];
+      const int k = t.k;
+      std::vector<cd> y(k);
+      for (int i = k - 1; i >= 0; --i) {
+        cd sum = t.g[i];
+        for (int l = i + 1; l < k; ++l) sum -= t.H[(size_t)i * m + l] * y[l];
+        y[i] = sum / t.H[(size_t)i * m + i];
+      }
+      std::vector<double2> yd(k);
+      for (int i = 0; i < k; ++i) yd[i] = make_double2(y[i].real(), y[i].imag());
+      double2 *yq = d_y.as<double2>() + (size_t)q * (m + 1);
+      CK(cudaMemcpyAsync(yq, yd.data(), sizeof(double2) * k, cudaMemcpyHostToDevice, stream));
+      stdd::launch_maxpy(Z(q, 0), n, k, yq, X + (int64_t)q * n, n, stream);
     }
-    std::vector<double2> yd(k);
-    for (int i = 0; i < k; ++i) yd[i] = make_double2(y[i].real(), y[i].imag());
-    CK(cudaMemcpyAsync(d_y.p, yd.data(), sizeof(double2) * k, cudaMemcpyHostToDevice, stream));
-    stdd::launch_maxpy(Z, n, k, d_y.as<double2>(), x, n, stream);
     CK(cudaStreamSynchronize(stream));
   }
-  last_its = its;
-  last_reorth = reorth;
+  last_noconv = false;
+  for (int q = 0; q < nq; ++q)
+    if (!(S[q].res <= o.rtol)) last_noconv = true;
+  last_its = S[0].its;
+  last_reorth = 0;
+  for (int q = 0; q < nq; ++q) last_reorth += S[q].reorth;
+  last_res = S[0].res;
 }
 
 // Algorithm 1 in residual form: x_{n+1} = x_n + M^-1 (b - A x_n) from x_0,
@@ -1153,18 +1242,21 @@ stdd_status stdd_solve(stdd_ctx *c, const stdd_solve_opts *o, double *x_out, int
     c->history.assign(c->nrhs, {});
     c->ensure_krylov(o->paper_richardson ? 1 : o->restart);
     const int span = c->pbegin(stdd_ctx::PH_SOLVE);
+    double2 *X = c->d_x.as<double2>();
     for (int q = 0; q < c->nrhs; ++q) {
-      double2 *x = c->d_x.as<double2>();
       if (o->x0_mode == STDD_X0_USER)
-        copy_in(x, o->x0 + (size_t)q * n * 2, n * sizeof(double2), o->x0_is_device, c->stream);
+        copy_in(X + (int64_t)q * n, o->x0 + (size_t)q * n * 2, n * sizeof(double2), o->x0_is_device, c->stream);
       else
-        CK(cudaMemsetAsync(x, 0, n * sizeof(double2), c->stream));
-      if (o->paper_richardson) c->richardson(q, *o, x);
-      else c->gmres(q, *o, x);
-      if (!(c->last_res <= o->rtol) && !o->paper_richardson) noconv = true;
-      if (q == c->nrhs - 1) c->pend(span);
-      copy_out(x_out + (size_t)q * n * 2, x, n * sizeof(double2), is_device, c->stream);
+        CK(cudaMemsetAsync(X + (int64_t)q * n, 0, n * sizeof(double2), c->stream));
     }
+    if (o->paper_richardson) {
+      for (int q = 0; q < c->nrhs; ++q) c->richardson(q, *o, X + (int64_t)q * n);
+    } else {
+      c->gmres_multi(*o);
+      noconv = c->last_noconv;
+    }
+    c->pend(span);
+    copy_out(x_out, X, (size_t)c->nrhs * n * sizeof(double2), is_device, c->stream);
   });
   if (st == STDD_OK && noconv) {
     c->err = "maxit reached before rtol";

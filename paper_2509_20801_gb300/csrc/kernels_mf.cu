@@ -439,17 +439,22 @@ template <int W, typename C> __device__ __forceinline__ C shfl_w(unsigned mask, 
   return v;
 }
 
-// sum over columns [c0, c1) of M(r, c) * vec(c) for one segment; M(r, c) at
-// M[c * ld + r]; vec(c) comes from gather(c) (zero past the end).
-template <int ROWS, typename C, typename Gather>
-__device__ __forceinline__ C seg_dot(const C *__restrict__ M, int64_t ld, int r, bool row, int c0, int c1, int lane,
-                                     unsigned mask, Gather gather) {
-  constexpr int U = sizeof(C) == 16 ? 8 : 32;  // FP64 is ALU-bound: fewer loads, more warps
+// acc[q] = sum over columns [c0, c1) of M(r, c) * vec_q(c), q < NR, for one
+// segment; M(r, c) at M[c * ld + r]; vec_q(c) comes from gather(c, q).
+// Each matrix entry is loaded once for all NR right-hand sides.
+template <int ROWS, int NR, typename C, typename Gather>
+__device__ __forceinline__ void seg_dot(const C *__restrict__ M, int64_t ld, int r, bool row, int c0, int c1,
+                                        int lane, unsigned mask, Gather gather, C (&acc)[NR]) {
+  constexpr int U0 = sizeof(C) == 16 ? 8 : 32;  // FP64 is ALU-bound: fewer loads, more warps
+  constexpr int U = NR > 1 ? (U0 / NR > 4 ? U0 / NR : 4) : U0;
   constexpr int UU = U < ROWS ? U : ROWS;
-  C acc = czero<C>();
+#pragma unroll
+  for (int q = 0; q < NR; ++q) acc[q] = czero<C>();
   for (int cb = c0; cb < c1; cb += ROWS) {
     const int c = cb + lane;
-    const C v = c < c1 ? gather(c) : czero<C>();
+    C v[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) v[q] = c < c1 ? gather(c, q) : czero<C>();
     const int nv = min(ROWS, c1 - cb);
     if (nv == ROWS) {
 #pragma unroll
@@ -458,7 +463,9 @@ __device__ __forceinline__ C seg_dot(const C *__restrict__ M, int64_t ld, int r,
 #pragma unroll
         for (int u = 0; u < UU; ++u) m[u] = row ? M[(int64_t)(cb + u0 + u) * ld + r] : czero<C>();
 #pragma unroll
-        for (int u = 0; u < UU; ++u) acc = cfma(m[u], shfl_w<ROWS>(mask, v, u0 + u), acc);
+        for (int u = 0; u < UU; ++u)
+#pragma unroll
+          for (int q = 0; q < NR; ++q) acc[q] = cfma(m[u], shfl_w<ROWS>(mask, v[q], u0 + u), acc[q]);
       }
     } else {
       // ragged last chunk: only the valid columns (no multiply-adds by zero)
@@ -468,15 +475,17 @@ __device__ __forceinline__ C seg_dot(const C *__restrict__ M, int64_t ld, int r,
 #pragma unroll
         for (int t = 0; t < 4; ++t) m[t] = row ? M[(int64_t)(cb + u + t) * ld + r] : czero<C>();
 #pragma unroll
-        for (int t = 0; t < 4; ++t) acc = cfma(m[t], shfl_w<ROWS>(mask, v, u + t), acc);
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int q = 0; q < NR; ++q) acc[q] = cfma(m[t], shfl_w<ROWS>(mask, v[q], u + t), acc[q]);
       }
       for (; u < nv; ++u) {
         const C m = row ? M[(int64_t)(cb + u) * ld + r] : czero<C>();
-        acc = cfma(m, shfl_w<ROWS>(mask, v, u), acc);
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[q] = cfma(m, shfl_w<ROWS>(mask, v[q], u), acc[q]);
       }
     }
   }
-  return acc;
 }
 
 // Going up, part 1: one warp per front forms w = [t at the pivots; 0] plus
@@ -530,7 +539,8 @@ __global__ void __launch_bounds__(256) mf_up_gather(MfArgs a, int f0, int nf, in
 
 // Going up, part 2: lane = border row r;
 // u[r] = w_b[r] + sum_j (-G21)(r, j) w_p[j]  (w_b already in u).
-template <typename R, int ROWS>
+// NR right-hand sides share every matrix load (NR > 1 requires split == 1).
+template <typename R, int ROWS, int NR>
 __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_up(MfArgs a, const int2 *__restrict__ items,
                                                                      int nitems, int split, int nrhs, int64_t ldt) {
   using C = typename CT<R>::T;
@@ -564,36 +574,50 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_up(MfArgs a, c
     seg1 = (sidx + 1) * nseg / split;
   }
   const C *wl = reinterpret_cast<const C *>(a.wloc);
-  for (int q = 0; q < nrhs; ++q) {
-    const int64_t base = q * ldt + voff;
-    C total = czero<C>();
+  for (int q0 = 0; q0 < nrhs; q0 += NR) {
+    C total[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) total[q] = czero<C>();
     if (active) {
-      if (row && sidx == 0) total = u[(int64_t)q * b + r];
-      auto gather = [&](int j) { return wl[base + nodes[j]]; };
+      if (row && sidx == 0)
+#pragma unroll
+        for (int q = 0; q < NR; ++q)
+          if (q0 + q < nrhs) total[q] = u[(int64_t)(q0 + q) * b + r];
+      auto gather = [&](int j, int q) {
+        return q0 + q < nrhs ? wl[(q0 + q) * ldt + voff + nodes[j]] : czero<C>();
+      };
       for (int sg = seg0; sg < seg1; ++sg) {
-        const C sv = seg_dot<ROWS, C>(G, b, r, row, sg * MF_SEG, min(p, (sg + 1) * MF_SEG), lane, mask, gather);
-        if (split == 1) total = cadd(total, sv);
-        else part[(il * MF_MAXSEG + sg) * ROWS + lane] = sv;
+        C sv[NR];
+        seg_dot<ROWS, NR, C>(G, b, r, row, sg * MF_SEG, min(p, (sg + 1) * MF_SEG), lane, mask, gather, sv);
+        if (split == 1) {
+#pragma unroll
+          for (int q = 0; q < NR; ++q) total[q] = cadd(total[q], sv[q]);
+        } else {
+          part[(il * MF_MAXSEG + sg) * ROWS + lane] = sv[0];
+        }
       }
     }
     if (split > 1) {
       __syncthreads();
       if (active && row && sidx == 0) {
-        for (int sg = 0; sg < nseg; ++sg) total = cadd(total, part[(il * MF_MAXSEG + sg) * ROWS + lane]);
-        u[(int64_t)q * b + r] = total;
+        for (int sg = 0; sg < nseg; ++sg) total[0] = cadd(total[0], part[(il * MF_MAXSEG + sg) * ROWS + lane]);
+        u[(int64_t)q0 * b + r] = total[0];
       }
       __syncthreads();
     } else if (active && row) {
-      u[(int64_t)q * b + r] = total;
+#pragma unroll
+      for (int q = 0; q < NR; ++q)
+        if (q0 + q < nrhs) u[(int64_t)(q0 + q) * b + r] = total[q];
     }
   }
 }
 
 // Coming down: lane = pivot row r;
 // x[r] = sum_{c<p} Finv(r, c) w_p[c] - sum_{c>=p} H12(r, c) x_b[c].
-template <typename R, int ROWS>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_down(MfArgs a, const int2 *__restrict__ items, int nitems, int split,
-                                               int nrhs, int64_t ldt) {
+template <typename R, int ROWS, int NR>
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_down(MfArgs a, const int2 *__restrict__ items,
+                                                                       int nitems, int split, int nrhs,
+                                                                       int64_t ldt) {
   using C = typename CT<R>::T;
   constexpr int GROUPS = 256 / ROWS;
   __shared__ C part[MF_MAXSEG * 256 / 2];
@@ -624,26 +648,38 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_down(MfArgs a,
   }
   C *tv = reinterpret_cast<C *>(a.tloc);
   const C *wl = reinterpret_cast<const C *>(a.wloc);
-  for (int q = 0; q < nrhs; ++q) {
-    const int64_t base = q * ldt + voff;
-    C total = czero<C>();
+  for (int q0 = 0; q0 < nrhs; q0 += NR) {
+    C total[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) total[q] = czero<C>();
     if (active) {
-      auto gather = [&](int c) { return c < p ? wl[base + nodes[c]] : cneg(tv[base + nodes[c]]); };
+      auto gather = [&](int c, int q) {
+        if (q0 + q >= nrhs) return czero<C>();
+        const int64_t base = (q0 + q) * ldt + voff;
+        return c < p ? wl[base + nodes[c]] : cneg(tv[base + nodes[c]]);
+      };
       for (int sg = seg0; sg < seg1; ++sg) {
-        const C sv = seg_dot<ROWS, C>(Fm, p, r, row, sg * MF_SEG, min(n, (sg + 1) * MF_SEG), lane, mask, gather);
-        if (split == 1) total = cadd(total, sv);
-        else part[(il * MF_MAXSEG + sg) * ROWS + lane] = sv;
+        C sv[NR];
+        seg_dot<ROWS, NR, C>(Fm, p, r, row, sg * MF_SEG, min(n, (sg + 1) * MF_SEG), lane, mask, gather, sv);
+        if (split == 1) {
+#pragma unroll
+          for (int q = 0; q < NR; ++q) total[q] = cadd(total[q], sv[q]);
+        } else {
+          part[(il * MF_MAXSEG + sg) * ROWS + lane] = sv[0];
+        }
       }
     }
     if (split > 1) {
       __syncthreads();
       if (active && row && sidx == 0) {
-        for (int sg = 0; sg < nseg; ++sg) total = cadd(total, part[(il * MF_MAXSEG + sg) * ROWS + lane]);
-        tv[base + nodes[r]] = total;
+        for (int sg = 0; sg < nseg; ++sg) total[0] = cadd(total[0], part[(il * MF_MAXSEG + sg) * ROWS + lane]);
+        tv[q0 * ldt + voff + nodes[r]] = total[0];
       }
       __syncthreads();
     } else if (active && row) {
-      tv[base + nodes[r]] = total;
+#pragma unroll
+      for (int q = 0; q < NR; ++q)
+        if (q0 + q < nrhs) tv[(q0 + q) * ldt + voff + nodes[r]] = total[q];
     }
   }
 }
@@ -720,10 +756,17 @@ template <typename R>
 void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
                  cudaStream_t st) {
   if (nitems == 0) return;
+  if (nrhs > 1) split = 1;  // several right-hand sides: every group keeps its segments in registers
   const int ipc = (256 / rows) / split;
   const int grid = (nitems + ipc - 1) / ipc;
-  if (rows == 16) mf_up<R, 16><<<grid, 256, 0, st>>>(a, items, nitems, split, nrhs, ldt);
-  else mf_up<R, 32><<<grid, 256, 0, st>>>(a, items, nitems, split, nrhs, ldt);
+  const int nr = (nrhs >= 4 && sizeof(R) == 4) ? 4 : (nrhs >= 2 ? 2 : 1);
+#define STDD_UP(RW, NRV) mf_up<R, RW, NRV><<<grid, 256, 0, st>>>(a, items, nitems, split, nrhs, ldt)
+  if (rows == 16) {
+    if (nr == 4) STDD_UP(16, 4); else if (nr == 2) STDD_UP(16, 2); else STDD_UP(16, 1);
+  } else {
+    if (nr == 4) STDD_UP(32, 4); else if (nr == 2) STDD_UP(32, 2); else STDD_UP(32, 1);
+  }
+#undef STDD_UP
   count_launch();
 }
 
@@ -731,10 +774,17 @@ template <typename R>
 void mf_down_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
                    cudaStream_t st) {
   if (nitems == 0) return;
+  if (nrhs > 1) split = 1;
   const int ipc = (256 / rows) / split;
   const int grid = (nitems + ipc - 1) / ipc;
-  if (rows == 16) mf_down<R, 16><<<grid, 256, 0, st>>>(a, items, nitems, split, nrhs, ldt);
-  else mf_down<R, 32><<<grid, 256, 0, st>>>(a, items, nitems, split, nrhs, ldt);
+  const int nr = (nrhs >= 4 && sizeof(R) == 4) ? 4 : (nrhs >= 2 ? 2 : 1);
+#define STDD_DOWN(RW, NRV) mf_down<R, RW, NRV><<<grid, 256, 0, st>>>(a, items, nitems, split, nrhs, ldt)
+  if (rows == 16) {
+    if (nr == 4) STDD_DOWN(16, 4); else if (nr == 2) STDD_DOWN(16, 2); else STDD_DOWN(16, 1);
+  } else {
+    if (nr == 4) STDD_DOWN(32, 4); else if (nr == 2) STDD_DOWN(32, 2); else STDD_DOWN(32, 1);
+  }
+#undef STDD_DOWN
   count_launch();
 }
 

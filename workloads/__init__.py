@@ -165,13 +165,14 @@ def cylinder(nx=200, ny=200, ppw=20, eps_cyl=4.0, radius=0.5, src_gap=1.0,
 
 
 def metalens(nx=4096, ny=1024, ppw=24, seed=1, npml=30, nsub=16, overlap=12,
-             interface_pml=30, wavelength=1.0):
+             interface_pml=30, wavelength=1.0, nrhs=1):
     """Metalens-like strip: substrate eps 2.085 over the lower 20 % of the
     rows, a row of eps 12.1 pillars (period 0.5 lambda, height 0.6 lambda
     rounded to whole cells, seeded widths U[0.1, 0.4] lambda) standing on it,
     and an x-directed line source inside the substrate 10 cells above the
     bottom PML (the plain-FP64 metalens case is 4096 x 1024 at lambda/24,
-    30-cell PML, 16 strips, 12-cell overlap)."""
+    30-cell PML, 16 strips, 12-cell overlap).  With nrhs > 1 the extra
+    right-hand sides are line sources on the next rows, 3 cells apart."""
     rng = np.random.default_rng(seed)
     d = wavelength / ppw
     j_sub = int(round(0.2 * ny))
@@ -187,7 +188,7 @@ def metalens(nx=4096, ny=1024, ppw=24, seed=1, npml=30, nsub=16, overlap=12,
         objs.append((_rect(xc - widths[k] / 2, xc + widths[k] / 2, y_sub, y_sub + height), 12.1))
     cells = cell_permittivity(nx, ny, d, d, 1.0, objs)
     eps = node_permittivity(cells)
-    b = line_source_x(nx, ny, d, npml + 10)[None]
+    b = np.stack([line_source_x(nx, ny, d, npml + 10 + 3 * k) for k in range(nrhs)])
     return Workload("metalens", nx, ny, d, d, wavelength, eps, b,
                     npml=(npml,) * 4, nsub=nsub, overlap=overlap,
                     interface_pml=interface_pml, restart=50, rtol=1e-8,
