@@ -44,11 +44,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "c64"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "c64", "bf16", "fp16"],
+                    help="factor precision: complex128, complex64, or complex64 with tensor-core (tcgen05) "
+                         "front updates from BF16 / FP16 inputs")
     ap.add_argument("--workload", default="metalens", choices=["metalens", "metalens-small", "cylinder"],
                     help="metalens: 4096x1024, 16 strips (the benchmark); metalens-small: 1024x1024, 4 strips "
                          "(profiling captures); cylinder: 200x200, 2 strips")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per step (line sources)")
+    ap.add_argument("--maxit", type=int, default=2000, help="FGMRES iteration limit per right-hand side")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -129,12 +132,14 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ peaks
 def measured_peaks():
-    peaks = {"hbm_gbs": 6800.0, "source_hbm": "fallback"}
+    peaks = {"hbm_gbs": 6800.0, "source_hbm": "fallback", "bf16_tflops": 1900.0, "source_bf16": "fallback"}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             mp = json.load(f)
         peaks["hbm_gbs"] = float(mp["hbm_gbs"])
         peaks["source_hbm"] = "measured (MEASURED_PEAKS.json, copy)"
+        peaks["bf16_tflops"] = float(mp["bf16_tflops_sustained"])
+        peaks["source_bf16"] = "measured (MEASURED_PEAKS.json, cuBLAS bf16 sustained; FP16 dense rate is the same)"
     except (OSError, KeyError, ValueError):
         pass
     return peaks
@@ -231,7 +236,8 @@ def run_ours(args, rank, world, local_rank):
     eps_d = torch.from_numpy(w.eps_node).to(dev)
     b_d = torch.from_numpy(w.b).to(dev)
     x_d = torch.empty_like(b_d)
-    prec = S.STDD_PREC_FP64 if args.precision == "fp64" else S.STDD_PREC_C64
+    prec = {"fp64": S.STDD_PREC_FP64, "c64": S.STDD_PREC_C64, "bf16": S.STDD_PREC_C64_BF16,
+            "fp16": S.STDD_PREC_C64_FP16}[args.precision]
 
     def make_solver(p):
         return S.Solver.from_workload(w, eps=eps_d, precision=p, device=local_rank,
@@ -239,7 +245,7 @@ def run_ours(args, rank, world, local_rank):
 
     def step(sv):
         sv.factor()
-        sv.solve(x_d, restart=RESTART, rtol=RTOL, maxit=2000)
+        return sv.solve(x_d, restart=RESTART, rtol=RTOL, maxit=args.maxit, allow_noconv=True) == B.STDD_OK
 
     def timed(p, warm, steps, profile):
         """warm-up, then `steps` timed steps with phase spans (level 1: the
@@ -333,6 +339,7 @@ def run_ours(args, rank, world, local_rank):
     # part at 0.5 flop/byte, complex64 is HBM-bound)
     alu_pk = fp64_tf if prec == S.STDD_PREC_FP64 else fp32_tf
     alu_src = "measured cuBLAS DGEMM" if prec == S.STDD_PREC_FP64 else "measured cuBLAS SGEMM"
+    tensor = prec in (S.STDD_PREC_C64_BF16, S.STDD_PREC_C64_FP16)
     kernels = {}
 
     def add_kernel(name, ms, calls, units, kind):
@@ -342,7 +349,10 @@ def run_ours(args, rank, world, local_rank):
             return
         t = ms * 1e-3 / calls
         u = units / calls
-        if kind == "flops":
+        if kind == "tensor":
+            k = dict(bound="tensor", achieved=u / t / 1e12, peak=peaks["bf16_tflops"], unit="TFLOP/s",
+                     peak_source=peaks["source_bf16"])
+        elif kind == "flops":
             k = dict(bound="alu", achieved=u / t / 1e12, peak=alu_pk, unit="TFLOP/s", peak_source=alu_src)
         elif prec == S.STDD_PREC_FP64:   # sweep, complex128: 8 flops per 16-byte entry
             k = dict(bound="alu", achieved=u / 2 / t / 1e12, peak=fp64_tf, unit="TFLOP/s",
@@ -355,7 +365,12 @@ def run_ours(args, rank, world, local_rank):
         kernels[name] = k
 
     tname = "double" if prec == S.STDD_PREC_FP64 else "float"
-    add_kernel(f"mf_gj_update<{tname}>", kprof["update_ms"], kprof["update_calls"], kprof["update_flops"], "flops")
+    if tensor:
+        add_kernel(f"mf_gj_update_tc<{args.precision}>", kprof["update_ms"], kprof["update_calls"],
+                   kprof["update_flops"], "tensor")
+    else:
+        add_kernel(f"mf_gj_update<{tname}>", kprof["update_ms"], kprof["update_calls"], kprof["update_flops"],
+                   "flops")
     add_kernel(f"mf_gj_small<{tname}>", kprof["small_ms"], kprof["small_calls"], kprof["small_flops"], "flops")
     add_kernel(f"mf_down<{tname}>", kprof["down_ms"], kprof["down_calls"], kprof["down_bytes"], "bytes")
     add_kernel(f"mf_up<{tname}>", kprof["up_ms"], kprof["up_calls"], kprof["up_bytes"], "bytes")
@@ -379,13 +394,16 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "c128" if prec == S.STDD_PREC_FP64 else "c64-factors+c128-krylov",
+        "dtype": {S.STDD_PREC_FP64: "c128", S.STDD_PREC_C64: "c64-factors+c128-krylov",
+                  S.STDD_PREC_C64_BF16: "c64-factors(bf16 tensor-core updates)+c128-krylov",
+                  S.STDD_PREC_C64_FP16: "c64-factors(fp16 tensor-core updates)+c128-krylov"}[prec],
         "data": "synthetic",
         "config": {"workload": workload_desc(w), "precision": args.precision, "rtol": RTOL,
                    "restart": RESTART, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (factors %.1f GB, Krylov basis %.1f GB)"
                          % (E * elem / 1e9, (2 * RESTART + 1) * w.n * 16 / 1e9)},
         "iterations": its,
+        "converged": bool(st["final_residual"] <= RTOL),
         "final_residual": st["final_residual"],
         "true_residual_check": r_rel,
         "t_factor_ms": prof["factor_ms"] / args.steps,
@@ -421,14 +439,14 @@ def run_ours(args, rank, world, local_rank):
         sv.set_sources(b_h)
         S.stdd_set_permittivity(sv.ctx, eps_h)
         sv.factor()
-        sv.solve(x_h, restart=RESTART, rtol=RTOL, maxit=2000)
+        sv.solve(x_h, restart=RESTART, rtol=RTOL, maxit=args.maxit, allow_noconv=True)
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             S.stdd_set_permittivity(sv.ctx, eps_h)
             sv.factor()
             S.stdd_set_sources(sv.ctx, w.nrhs, b_h)
-            sv.solve(x_h, restart=RESTART, rtol=RTOL, maxit=2000)
+            sv.solve(x_h, restart=RESTART, rtol=RTOL, maxit=args.maxit, allow_noconv=True)
         dt = (time.perf_counter() - t0) / args.steps
         dt_t = torch.tensor([dt], device=dev)
         if dist is not None:

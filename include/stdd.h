@@ -54,8 +54,12 @@ typedef enum {
 } stdd_status;
 
 enum {
-  STDD_PREC_FP64 = 0,   /* complex128 factors and substitutions           */
-  STDD_PREC_C64 = 1     /* complex64 factors and substitutions, FP32 math */
+  STDD_PREC_FP64 = 0,     /* complex128 factors and substitutions           */
+  STDD_PREC_C64 = 1,      /* complex64 factors and substitutions, FP32 math */
+  STDD_PREC_C64_BF16 = 2, /* complex64, large-front updates on the tensor
+                             cores with BF16 inputs, FP32 accumulation     */
+  STDD_PREC_C64_FP16 = 3  /* same with FP16 inputs (power-of-two scaling per
+                             64 x 128 tile keeps them in range)            */
 };
 
 enum { STDD_X0_ZERO = 0, STDD_X0_USER = 1 };
@@ -95,7 +99,8 @@ stdd_status stdd_set_pml(stdd_ctx *ctx, const int npml[4], int order_m, double R
 stdd_status stdd_set_decomposition(stdd_ctx *ctx, int nsub, const int *x_cuts, int overlap,
                                    int interface_pml);
 
-/* STDD_PREC_FP64 or STDD_PREC_C64.  Invalidates the factors. */
+/* One of STDD_PREC_*.  Invalidates the factors.  The Krylov iteration,
+ * residuals and the returned fields are FP64 in every mode. */
 stdd_status stdd_set_precision(stdd_ctx *ctx, int mode);
 
 /* nrhs right-hand sides b (Eq. 4), nrhs * 2*nx*ny doubles.  Copied.  Does
@@ -246,6 +251,12 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
 enum { STDD_OPT_GRAPHS = 1, STDD_OPT_AUTOTUNE = 2, STDD_OPT_LEAF = 3 };
 stdd_status stdd_set_option(stdd_ctx *ctx, int option, int value);
 stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);
+
+/* Diagnostic: one 64 x 128 complex tile product on the tensor cores
+ * (tcgen05, the kernel path of STDD_PREC_C64_BF16 / _FP16) against a
+ * double-precision host reference.  fmt 0 = FP16, 1 = BF16.  *rel_err =
+ * max |error| / max |result|.  No counterpart in the paper. */
+stdd_status stdd_tc_selftest(int device, int fmt, double *rel_err);
 
 /* Host-only nested-dissection analysis of one W x H box (no GPU needed).
  * First call with nodes == NULL to get *nfronts and *nnodes; then call

@@ -8,7 +8,7 @@ problem.  Importing this package fails if libstdd.so has not been built.
 from __future__ import annotations
 
 from . import binding as _b
-from .binding import (STDD_PREC_C64, STDD_PREC_FP64, StddError, stdd_apply_operator,  # noqa: F401
+from .binding import (STDD_PREC_C64, STDD_PREC_C64_BF16, STDD_PREC_C64_FP16, STDD_PREC_FP64, StddError, stdd_apply_operator,  # noqa: F401
                       stdd_apply_preconditioner, stdd_create, stdd_destroy, stdd_factor,
                       stdd_get_profile, stdd_get_stats, stdd_last_error, stdd_residual,
                       stdd_residual_noalloc,
@@ -16,7 +16,7 @@ from .binding import (STDD_PREC_C64, STDD_PREC_FP64, StddError, stdd_apply_opera
                       STDD_OPT_LEAF, stdd_local_solve, stdd_nd_analyze,
                       stdd_residual_history, stdd_set_decomposition, stdd_set_frequency,
                       stdd_set_grid, stdd_set_permittivity, stdd_set_pml, stdd_set_precision,
-                      stdd_set_sources, stdd_solve, stdd_strip_info)
+                      stdd_set_sources, stdd_solve, stdd_strip_info, stdd_tc_selftest)
 
 LIB_PATH = _b.LIB_PATH
 

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libstdd.so")
 
 STDD_OK, STDD_EINVAL, STDD_ESTATE, STDD_ENOMEM, STDD_ECUDA = 0, 1, 2, 3, 4
 STDD_EPIVOT, STDD_EBREAKDOWN, STDD_ENOCONV, STDD_ETIMEOUT = 5, 6, 7, 8
-STDD_PREC_FP64, STDD_PREC_C64 = 0, 1
+STDD_PREC_FP64, STDD_PREC_C64, STDD_PREC_C64_BF16, STDD_PREC_C64_FP16 = 0, 1, 2, 3
 STDD_X0_ZERO, STDD_X0_USER = 0, 1
 STATUS_NAMES = {0: "STDD_OK", 1: "STDD_EINVAL", 2: "STDD_ESTATE", 3: "STDD_ENOMEM", 4: "STDD_ECUDA",
                 5: "STDD_EPIVOT", 6: "STDD_EBREAKDOWN", 7: "STDD_ENOCONV", 8: "STDD_ETIMEOUT"}
@@ -80,6 +80,7 @@ _SIGS = {
     "stdd_set_profiling": (c_int, [c_void_p, c_int]),
     "stdd_set_option": (c_int, [c_void_p, c_int, c_int]),
     "stdd_get_profile": (c_int, [c_void_p, P(stdd_profile), c_int]),
+    "stdd_tc_selftest": (c_int, [c_int, c_int, P(c_double)]),
     "stdd_nd_analyze": (c_int, [c_int, c_int, c_int, P(c_int), P(ctypes.c_longlong), c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_void_p]),
 }
@@ -272,6 +273,15 @@ def stdd_get_profile(ctx, reset=True):
     s = stdd_profile()
     _check(ctx, lib.stdd_get_profile(ctx, ctypes.byref(s), 1 if reset else 0))
     return {k: getattr(s, k) for k, _ in stdd_profile._fields_}
+
+
+def stdd_tc_selftest(device=0, fmt=1):
+    """Relative error of one tensor-core tile product (fmt 0 FP16, 1 BF16)."""
+    e = c_double(0.0)
+    st = lib.stdd_tc_selftest(int(device), int(fmt), ctypes.byref(e))
+    if st != STDD_OK:
+        raise StddError(st, "stdd_tc_selftest failed")
+    return e.value
 
 
 def stdd_nd_analyze(W, H, leaf_max=64):

@@ -39,6 +39,9 @@ struct ArgError : std::runtime_error {
 struct StateError : std::runtime_error {
   using std::runtime_error::runtime_error;
 };
+struct TimeoutError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
 
 #define CK(expr)                                                                         \
   do {                                                                                   \
@@ -235,6 +238,8 @@ struct stdd_ctx {
   } hook;
 
   size_t elem() const { return prec == STDD_PREC_FP64 ? sizeof(double2) : sizeof(float2); }
+  // tensor-core input format of the large-front updates (-1: CUDA cores)
+  int tc_fmt() const { return prec == STDD_PREC_C64_FP16 ? 0 : (prec == STDD_PREC_C64_BF16 ? 1 : -1); }
   int64_t N() const { return (int64_t)nx * ny; }
 
   void invalidate_factors() { factored = false; }
@@ -643,6 +648,7 @@ template <typename R> void stdd_ctx::factor_t() {
   if (!attrs) {
     CK(stdd::mf_setup_attributes<double>());
     CK(stdd::mf_setup_attributes<float>());
+    CK(stdd::tc_setup_attributes());
     attrs = true;
   }
   CK(cudaMemsetAsync(d_flag.p, 0, sizeof(int), stream));
@@ -652,7 +658,7 @@ template <typename R> void stdd_ctx::factor_t() {
   for (int L = depth - 1; L >= 0; --L) {
     MfArgs a = mf_args(L & 1, false);
     hook.c = this;
-    stdd::mf_factor_level<R>(a, levels[L], L, stream, &hook);
+    stdd::mf_factor_level<R>(a, levels[L], L, stream, &hook, tc_fmt());
     CK(cudaGetLastError());
   }
   pend(span);
@@ -660,7 +666,8 @@ template <typename R> void stdd_ctx::factor_t() {
   CK(cudaMemcpyAsync(&flag, d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, stream));
   CK(cudaMemcpyAsync(&min_pivot, d_minpiv.p, sizeof(double), cudaMemcpyDeviceToHost, stream));
   CK(cudaStreamSynchronize(stream));
-  if (flag) throw std::domain_error("zero or non-finite pivot in a front");
+  if (flag & 2) throw TimeoutError("a tensor-core tile did not complete within its wait limit");
+  if (flag & 1) throw std::domain_error("zero or non-finite pivot in a front");
 }
 
 template <typename R> void stdd_ctx::solve_levels(int nr) {
@@ -1059,6 +1066,9 @@ template <typename F> stdd_status guarded(stdd_ctx *c, F &&f) {
   } catch (const CudaError &e) {
     c->err = e.what();
     return STDD_ECUDA;
+  } catch (const TimeoutError &e) {
+    c->err = e.what();
+    return STDD_ETIMEOUT;
   } catch (const std::bad_alloc &) {
     c->err = "out of device or host memory";
     return STDD_ENOMEM;
@@ -1205,7 +1215,7 @@ stdd_status stdd_set_decomposition(stdd_ctx *c, int nsub, const int *x_cuts, int
 
 stdd_status stdd_set_precision(stdd_ctx *c, int mode) {
   return guarded(c, [&] {
-    if (mode != STDD_PREC_FP64 && mode != STDD_PREC_C64) throw ArgError("unknown precision mode");
+    if (mode < STDD_PREC_FP64 || mode > STDD_PREC_C64_FP16) throw ArgError("unknown precision mode");
     if (mode != c->prec) {
       c->prec = mode;
       c->solve_nrhs_cap = 0;
@@ -1486,6 +1496,23 @@ stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {
       c->ev_used = 0;
     }
   });
+}
+
+stdd_status stdd_tc_selftest(int device, int fmt, double *rel_err) {
+  if (!rel_err || (fmt != 0 && fmt != 1)) return STDD_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return STDD_ECUDA;
+  }
+  cudaError_t e = cudaSuccess;
+  const double r = stdd::tc_selftest(fmt, &e);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return STDD_ECUDA;
+  }
+  if (r == -1.0) return STDD_ETIMEOUT;
+  *rel_err = r;
+  return STDD_OK;
 }
 
 stdd_status stdd_nd_analyze(int W, int H, int leaf_max, int *nfronts, long long *nnodes, int *p, int *b,

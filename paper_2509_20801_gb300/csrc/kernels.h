@@ -56,8 +56,15 @@ struct LaunchHook {
 };
 
 template <typename R> cudaError_t mf_setup_attributes();
+// tc_fmt: -1 CUDA-core updates; 0 / 1 tensor-core updates with FP16 / BF16 inputs
 template <typename R>
-void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_t st, LaunchHook *hook = nullptr);
+void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_t st, LaunchHook *hook = nullptr,
+                     int tc_fmt = -1);
+
+// ---- tensor-core front updates (kernels_tc.cu), complex64 fronts only
+cudaError_t tc_setup_attributes();
+void mf_tc_update_launch(const MfArgs &a, const LevelInfo &L, int k, int fmt, cudaStream_t st);
+double tc_selftest(int fmt, cudaError_t *err);
 template <typename R>
 void mf_up_gather_level(const MfArgs &a, const LevelInfo &L, int nrhs, int64_t ldt, cudaStream_t st);
 template <typename R>

@@ -712,7 +712,8 @@ template <typename R> cudaError_t mf_setup_attributes() {
 }
 
 template <typename R>
-void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_t st, LaunchHook *hook) {
+void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_t st, LaunchHook *hook,
+                     int tc_fmt) {
   if (L.nf == 0) return;
   if (L.min_n <= MF_SMALL) {
     const int ldn = std::min(L.max_n, MF_SMALL);
@@ -737,7 +738,8 @@ void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_
       mf_gj_diag<R><<<L.nf, MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
       mf_gj_col<R><<<dim3(L.nf, tiles), MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
       if (hook) hook->before(K_UPDATE, level, k);
-      mf_gj_update<R><<<dim3(L.nf, nt * nt), 256, gemm_smem<R>(), st>>>(a, L.f0, k);
+      if (tc_fmt >= 0 && sizeof(R) == 4) mf_tc_update_launch(a, L, k, tc_fmt, st);
+      else mf_gj_update<R><<<dim3(L.nf, nt * nt), 256, gemm_smem<R>(), st>>>(a, L.f0, k);
       if (hook) hook->after(K_UPDATE, level, k);
       mf_gj_row<R><<<dim3(L.nf, tiles), MF_PANEL_THREADS, row_smem<R>(), st>>>(a, L.f0, k);
       count_launch(4);
@@ -790,8 +792,8 @@ void mf_down_level(const MfArgs &a, const int2 *items, int nitems, int rows, int
 
 template cudaError_t mf_setup_attributes<double>();
 template cudaError_t mf_setup_attributes<float>();
-template void mf_factor_level<double>(const MfArgs &, const LevelInfo &, int, cudaStream_t, LaunchHook *);
-template void mf_factor_level<float>(const MfArgs &, const LevelInfo &, int, cudaStream_t, LaunchHook *);
+template void mf_factor_level<double>(const MfArgs &, const LevelInfo &, int, cudaStream_t, LaunchHook *, int);
+template void mf_factor_level<float>(const MfArgs &, const LevelInfo &, int, cudaStream_t, LaunchHook *, int);
 template void mf_up_gather_level<double>(const MfArgs &, const LevelInfo &, int, int64_t, cudaStream_t);
 template void mf_up_gather_level<float>(const MfArgs &, const LevelInfo &, int, int64_t, cudaStream_t);
 template void mf_up_level<double>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t);

@@ -1,0 +1,344 @@
+// Tensor-core (tcgen05, sm_103a) front updates for the mixed-precision path.
+//
+// The blocked Gauss-Jordan step adds C R to the trailing part of a front,
+// C (m x 32) and R (32 x m) complex.  Here one CTA computes a 64 x 128 complex
+// tile of C R as ONE real GEMM through the 2 x 2 real embedding
+//     [Re; Im](C R) = [Cr -Ci; Ci Cr] [Rr; Ri]
+// (M = 128 real rows, K = 64 real, N = 128), inputs rounded to BF16 or FP16
+// after a power-of-two scaling per tile (exact, undone after the product;
+// it keeps FP16 inside its range), products accumulated in FP32 in tensor
+// memory (TMEM), and the tile added to the front in FP32.
+//
+// Operands are staged by the threads (they need the conversion) in the
+// canonical no-swizzle K-major layout: 8 x 16-byte core matrices, element
+// (row, k) at (row/8)*SBO + (k/8)*LBO + (row%8)*16 + (k%8)*2 bytes with
+// LBO = 128 (K-adjacent core matrices) and SBO = 1024 (row-adjacent).  One
+// thread issues the four K = 16 MMAs, commits them to an mbarrier, and all
+// threads wait for it with an iteration limit; a timeout sets an error flag
+// and skips the tile instead of hanging.  Each warp then reads its 32 TMEM
+// lanes (32x32b shape) and updates its rows.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <random>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace stdd {
+
+namespace {
+
+constexpr int TC_MC = 64;            // complex rows per tile (128 real)
+constexpr int TC_N = 128;            // complex columns per tile
+constexpr int TC_KC = 32;            // complex K (one Gauss-Jordan block)
+constexpr int TC_KR = 2 * TC_KC;     // real K
+constexpr int TC_OPBYTES = 128 * TC_KR * 2;  // one operand: 128 rows x 64 halves = 16 KiB
+constexpr uint32_t TC_TMEM_COLS = 128;
+constexpr long long TC_WAIT_LIMIT = 1ll << 20;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// byte offset of element (row, k) in an operand tile (K-major, no swizzle)
+__device__ __forceinline__ uint32_t op_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  const uint64_t lbo = 128, sbo = 1024;
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = fmt (0 F16, 1 BF16),
+// both K-major, M = 128, N = TC_N
+__device__ __forceinline__ uint32_t instr_desc(int fmt) {
+  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+template <int FMT> __device__ __forceinline__ uint16_t to_half_bits(float x) {
+  if (FMT == 1) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+  return __half_as_ushort(__float2half_rn(x));
+}
+
+// power-of-two exponent e with |x| * 2^e in [1, 2) for the largest |x| (0 if x = 0)
+__device__ __forceinline__ int scale_exp(float amax) {
+  if (!(amax > 0.f) || !isfinite(amax)) return 0;
+  int e;
+  frexpf(amax, &e);  // amax = f * 2^e, f in [0.5, 1)
+  return 1 - e;
+}
+
+// Shared state of one tile CTA (128 threads).
+struct TileSmem {
+  uint8_t A[TC_OPBYTES];
+  uint8_t B[TC_OPBYTES];
+  unsigned long long mbar;
+  uint32_t tmem;
+  float red[8];
+};
+
+// One 64 x 128 complex tile D = C R on the tensor cores.  cload(rr, j) gives
+// C(rr, j), rload(cc, j) gives R(j, cc) (zero outside the tile); sink(rr, cc,
+// comp, v) receives component comp (0 re, 1 im) of D(rr, cc).  Returns false
+// if the completion wait timed out.
+template <int FMT, typename CLoad, typename RLoad, typename Sink>
+__device__ bool tc_tile(TileSmem &sm, int kc, CLoad cload, RLoad rload, Sink sink) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&sm.tmem)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sm.mbar)));
+  // per-tile power-of-two scales from the largest component of C and R
+  float ma = 0.f, mb = 0.f;
+  for (int idx = tid; idx < TC_MC * kc; idx += 128) {
+    const float2 v = cload(idx % TC_MC, idx / TC_MC);
+    ma = fmaxf(ma, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  for (int idx = tid; idx < TC_N * kc; idx += 128) {
+    const float2 v = rload(idx % TC_N, idx / TC_N);
+    mb = fmaxf(mb, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+    mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  }
+  if (lane == 0) {
+    sm.red[warp] = ma;
+    sm.red[4 + warp] = mb;
+  }
+  __syncthreads();
+  const int ea = scale_exp(fmaxf(fmaxf(sm.red[0], sm.red[1]), fmaxf(sm.red[2], sm.red[3])));
+  const int eb = scale_exp(fmaxf(fmaxf(sm.red[4], sm.red[5]), fmaxf(sm.red[6], sm.red[7])));
+  // stage the embedded operands: A row 2rr = [Cr, -Ci], row 2rr+1 = [Ci, Cr];
+  // B row cc (K-major) = [Rr, Ri] per complex k
+  for (int idx = tid; idx < TC_MC * TC_KC; idx += 128) {
+    const int rr = idx % TC_MC, j = idx / TC_MC;
+    float2 v = j < kc ? cload(rr, j) : make_float2(0.f, 0.f);
+    v.x = ldexpf(v.x, ea);
+    v.y = ldexpf(v.y, ea);
+    const uint16_t re = to_half_bits<FMT>(v.x), im = to_half_bits<FMT>(v.y), nim = to_half_bits<FMT>(-v.y);
+    *reinterpret_cast<uint16_t *>(sm.A + op_off(2 * rr, 2 * j)) = re;
+    *reinterpret_cast<uint16_t *>(sm.A + op_off(2 * rr, 2 * j + 1)) = nim;
+    *reinterpret_cast<uint16_t *>(sm.A + op_off(2 * rr + 1, 2 * j)) = im;
+    *reinterpret_cast<uint16_t *>(sm.A + op_off(2 * rr + 1, 2 * j + 1)) = re;
+  }
+  for (int idx = tid; idx < TC_N * TC_KC; idx += 128) {
+    const int cc = idx % TC_N, j = idx / TC_N;
+    float2 v = j < kc ? rload(cc, j) : make_float2(0.f, 0.f);
+    *reinterpret_cast<uint16_t *>(sm.B + op_off(cc, 2 * j)) = to_half_bits<FMT>(ldexpf(v.x, eb));
+    *reinterpret_cast<uint16_t *>(sm.B + op_off(cc, 2 * j + 1)) = to_half_bits<FMT>(ldexpf(v.y, eb));
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = sm.tmem;
+  if (tid == 0) {
+    const uint32_t idesc = instr_desc(FMT);
+    const uint32_t a0 = smem_u32(sm.A), b0 = smem_u32(sm.B);
+#pragma unroll
+    for (int s = 0; s < TC_KR / 16; ++s)
+      mma_f16(tmem, smem_desc(a0 + s * 256), smem_desc(b0 + s * 256), idesc, s > 0 ? 1u : 0u);
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     smem_u32(&sm.mbar))
+                 : "memory");
+  }
+  bool done = false;
+  for (long long it = 0; it < TC_WAIT_LIMIT && !done; ++it) done = mbar_try_wait(smem_u32(&sm.mbar), 0);
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (done) {
+    const float inv = ldexpf(1.f, -(ea + eb));
+    const int drow = warp * 32 + lane;       // D row = TMEM lane
+    const int rr = drow >> 1, comp = drow & 1;
+    for (int c0 = 0; c0 < TC_N; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int u = 0; u < 32; ++u) sink(rr, c0 + u, comp, __uint_as_float(v[u]) * inv);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS));
+  return done;
+}
+
+// element addressing of the front layout (see kernels_mf.cu)
+__device__ __forceinline__ float2 *front_ptr(const MfArgs &a, const FrontDev &f, int r, int c) {
+  const int p = f.p, b = f.b, n = p + b;
+  float2 *fac = reinterpret_cast<float2 *>(a.fac);
+  if (r < p) return fac + f.fac_off + (int64_t)c * p + r;
+  if (c < p) return fac + f.fac_off + (int64_t)p * n + (int64_t)c * b + (r - p);
+  return reinterpret_cast<float2 *>(a.ws_cur) + f.s_off + (int64_t)(c - p) * b + (r - p);
+}
+__device__ __forceinline__ int unband_tc(int i, int k, int nbk) { return i < k ? i : i + nbk; }
+
+// Gauss-Jordan step k of every large front: A(r, c) += C'(r, band) R(band, c)
+// for r, c outside the pivot band, C' the (already scaled) column panel and R
+// the (not yet scaled) row panel.  grid = (fronts, 64 x 128 tiles).
+template <int FMT>
+__global__ void __launch_bounds__(128) mf_gj_update_tc(MfArgs a, int f0, int k) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  TileSmem &sm = *reinterpret_cast<TileSmem *>(smem_raw);
+  const FrontDev f = a.fronts[f0 + blockIdx.x];
+  const int p = f.p, n = p + f.b;
+  if (n <= MF_SMALL || k >= p) return;
+  const int nbk = min(MF_NB, p - k);
+  const int m = n - nbk;
+  const int nti = (m + TC_MC - 1) / TC_MC, ntj = (m + TC_N - 1) / TC_N;
+  if ((int)blockIdx.y >= nti * ntj) return;
+  const int i0 = (blockIdx.y % nti) * TC_MC, j0 = (blockIdx.y / nti) * TC_N;
+  auto cload = [&](int rr, int j) -> float2 {
+    const int ri = i0 + rr;
+    return ri < m ? *front_ptr(a, f, unband_tc(ri, k, nbk), k + j) : make_float2(0.f, 0.f);
+  };
+  auto rload = [&](int cc, int j) -> float2 {
+    const int ci = j0 + cc;
+    return ci < m ? *front_ptr(a, f, k + j, unband_tc(ci, k, nbk)) : make_float2(0.f, 0.f);
+  };
+  auto sink = [&](int rr, int cc, int comp, float v) {
+    const int ri = i0 + rr, ci = j0 + cc;
+    if (ri < m && ci < m) {
+      float *e = reinterpret_cast<float *>(front_ptr(a, f, unband_tc(ri, k, nbk), unband_tc(ci, k, nbk)));
+      e[comp] += v;
+    }
+  };
+  if (!tc_tile<FMT>(sm, nbk, cload, rload, sink) && threadIdx.x == 0) atomicOr(a.flag, 2);
+}
+
+// Self-test tile: D = C R with C (64 x 32) and R (32 x 128) column-major.
+template <int FMT>
+__global__ void __launch_bounds__(128) tc_selftest_kernel(const float2 *C, const float2 *R, float2 *D, int *flag) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  TileSmem &sm = *reinterpret_cast<TileSmem *>(smem_raw);
+  auto cload = [&](int rr, int j) { return C[j * TC_MC + rr]; };
+  auto rload = [&](int cc, int j) { return R[cc * TC_KC + j]; };
+  auto sink = [&](int rr, int cc, int comp, float v) { reinterpret_cast<float *>(&D[cc * TC_MC + rr])[comp] = v; };
+  if (!tc_tile<FMT>(sm, TC_KC, cload, rload, sink) && threadIdx.x == 0) atomicOr(flag, 2);
+}
+
+}  // namespace
+
+// 56 KiB per CTA keeps at most 4 tile CTAs on an SM: 4 x 128 TMEM columns
+// = the SM's 512, so no allocation ever has to wait for another CTA
+size_t tc_smem_bytes() { return std::max<size_t>(sizeof(TileSmem) + 1024, 56u << 10); }
+
+template <int FMT> cudaError_t tc_setup_attributes_fmt() {
+  cudaError_t e = cudaFuncSetAttribute(mf_gj_update_tc<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc_smem_bytes());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tc_selftest_kernel<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_smem_bytes());
+}
+
+cudaError_t tc_setup_attributes() {
+  cudaError_t e = tc_setup_attributes_fmt<0>();
+  if (e != cudaSuccess) return e;
+  return tc_setup_attributes_fmt<1>();
+}
+
+void mf_tc_update_launch(const MfArgs &a, const LevelInfo &L, int k, int fmt, cudaStream_t st) {
+  const int m = L.max_n - std::min(MF_NB, std::max(1, L.max_p - k));
+  const int tiles = std::max(1, ((m + TC_MC - 1) / TC_MC) * ((m + TC_N - 1) / TC_N));
+  if (fmt == 1) mf_gj_update_tc<1><<<dim3(L.nf, tiles), 128, tc_smem_bytes(), st>>>(a, L.f0, k);
+  else mf_gj_update_tc<0><<<dim3(L.nf, tiles), 128, tc_smem_bytes(), st>>>(a, L.f0, k);
+  count_launch();
+}
+
+// Host-side check of one tensor-core tile against a double-precision
+// reference; returns the largest |error| / max |D| or a negative value if the
+// device reported a timeout.
+double tc_selftest(int fmt, cudaError_t *err) {
+  std::mt19937 rng(12345);
+  std::normal_distribution<float> nd(0.f, 1.f);
+  std::vector<float2> C(TC_MC * TC_KC), R(TC_KC * TC_N), D(TC_MC * TC_N);
+  for (auto &v : C) v = make_float2(nd(rng), nd(rng));
+  for (auto &v : R) v = make_float2(nd(rng), nd(rng));
+  float2 *dC = nullptr, *dR = nullptr, *dD = nullptr;
+  int *dflag = nullptr;
+  *err = cudaSuccess;
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess && *err == cudaSuccess) *err = e;
+    return e == cudaSuccess;
+  };
+  bool ok = ck(tc_setup_attributes()) && ck(cudaMalloc(&dC, C.size() * sizeof(float2))) &&
+            ck(cudaMalloc(&dR, R.size() * sizeof(float2))) && ck(cudaMalloc(&dD, D.size() * sizeof(float2))) &&
+            ck(cudaMalloc(&dflag, sizeof(int)));
+  int flag = 0;
+  if (ok) {
+    ok = ck(cudaMemcpy(dC, C.data(), C.size() * sizeof(float2), cudaMemcpyHostToDevice)) &&
+         ck(cudaMemcpy(dR, R.data(), R.size() * sizeof(float2), cudaMemcpyHostToDevice)) &&
+         ck(cudaMemset(dD, 0, D.size() * sizeof(float2))) && ck(cudaMemset(dflag, 0, sizeof(int)));
+  }
+  if (ok) {
+    if (fmt == 1) tc_selftest_kernel<1><<<1, 128, tc_smem_bytes()>>>(dC, dR, dD, dflag);
+    else tc_selftest_kernel<0><<<1, 128, tc_smem_bytes()>>>(dC, dR, dD, dflag);
+    ok = ck(cudaGetLastError()) && ck(cudaDeviceSynchronize()) &&
+         ck(cudaMemcpy(D.data(), dD, D.size() * sizeof(float2), cudaMemcpyDeviceToHost)) &&
+         ck(cudaMemcpy(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost));
+  }
+  cudaFree(dC);
+  cudaFree(dR);
+  cudaFree(dD);
+  cudaFree(dflag);
+  if (!ok) return -2.0;
+  if (flag) return -1.0;
+  double emax = 0, dmax = 0;
+  for (int cc = 0; cc < TC_N; ++cc)
+    for (int rr = 0; rr < TC_MC; ++rr) {
+      double re = 0, im = 0;
+      for (int j = 0; j < TC_KC; ++j) {
+        const float2 a = C[j * TC_MC + rr], b = R[cc * TC_KC + j];
+        re += (double)a.x * b.x - (double)a.y * b.y;
+        im += (double)a.x * b.y + (double)a.y * b.x;
+      }
+      const float2 d = D[cc * TC_MC + rr];
+      emax = std::max(emax, std::max(std::fabs(d.x - re), std::fabs(d.y - im)));
+      dmax = std::max(dmax, std::max(std::fabs(re), std::fabs(im)));
+    }
+  return emax / dmax;
+}
+
+}  // namespace stdd
