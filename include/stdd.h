@@ -62,7 +62,13 @@ enum {
                              64 x 128 tile keeps them in range)            */
 };
 
-enum { STDD_X0_ZERO = 0, STDD_X0_USER = 1 };
+enum {
+  STDD_X0_ZERO = 0,   /* x0 = 0                                            */
+  STDD_X0_USER = 1,   /* x0 given by the caller                            */
+  STDD_X0_LEARNED = 2 /* x0 from the network attached by
+                         stdd_set_learned_guess, scaled to the minimal
+                         residual; zero guess where it does not help       */
+};
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a
  * cudaStream_t to run on (NULL: the context creates its own stream).  Every
@@ -116,7 +122,7 @@ typedef struct {
   int restart;            /* GMRES restart length m (>= 1)                   */
   int maxit;              /* total inner iterations (or sweeps) allowed     */
   double rtol;            /* stop at ||b - A x|| / ||b|| <= rtol             */
-  int x0_mode;            /* STDD_X0_ZERO or STDD_X0_USER                    */
+  int x0_mode;            /* STDD_X0_ZERO, STDD_X0_USER or STDD_X0_LEARNED   */
   const double *x0;       /* initial guesses (nrhs fields) if USER          */
   int x0_is_device;
   int paper_richardson;   /* 1: run Algorithm 1 itself (Richardson form,
@@ -267,6 +273,95 @@ stdd_status stdd_tc_selftest(int device, int fmt, double *rel_err);
  * for the root; level[f] is the depth from the root. */
 stdd_status stdd_nd_analyze(int W, int H, int leaf_max, int *nfronts, long long *nnodes, int *p,
                             int *b, int *parent, int *level, int *nodes);
+
+/* ---------------------------------------------------------------------
+ * Learned initial guess.  No counterpart in the paper: a convolutional
+ * encoder-decoder maps (permittivity, Re b, Im b) on the grid to an initial
+ * field for the Krylov iteration, which still runs to the same tolerance --
+ * the zero-guess method remains both the fallback and the judge of the
+ * guess.
+ *
+ * Network with L levels and channels c_l = min(c0 * 2^l, cmax):
+ *   encoder level l: conv3x3 + ReLU, conv3x3 + ReLU (= skip_l); the input of
+ *     level 0 is the 3-channel image, of level l > 0 the 2x2 average pool of
+ *     skip_{l-1};
+ *   decoder level l = L-2 .. 0: nearest 2x upsampling of the level below,
+ *     conv3x3 (c_{l+1} -> c_l) + ReLU, plus skip_l, conv3x3 + ReLU;
+ *   output: conv3x3 (c_0 -> 2), no activation.
+ * Convolutions: 3x3, stride 1, zero padding, cross-correlation
+ *   out[co](y, x) = bias[co] + sum_ci sum_ky,kx w[co][ci][ky][kx] *
+ *                   in[ci](y + ky - 1, x + kx - 1).
+ * Parameters: one float array, layer by layer in the order above (encoder
+ * 0 first conv, second conv, encoder 1 ..., decoder L-2 upsampled conv,
+ * second conv, ..., decoder 0, output), each layer its weights
+ * [cout][cin][3][3] then its bias [cout].
+ * Images: float, NCHW, [batch][channel][H][W] row-major; H and W multiples
+ * of 2^(L-1).  The solver's node (i, j) is image row j, column i.
+ * Arithmetic: the weights used by forward and backward passes are the FP32
+ * master weights rounded to BF16 (bf16_weights = 1) or the FP32 weights
+ * themselves (0); activations and accumulation are FP32.
+ * Loss: mean squared error over all outputs of the batch.  Optimiser: Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8) on the FP32 master weights.
+ * ------------------------------------------------------------------- */
+typedef struct stdd_nn stdd_nn;
+
+/* Create a network on `device` (stream as in stdd_create), weights He-normal
+ * from `seed` (output layer scaled by 0.1), biases zero.  levels 1..8,
+ * 1 <= base_channels <= max_channels. */
+stdd_status stdd_nn_create(stdd_nn **out, int device, void *cuda_stream, int levels, int base_channels,
+                           int max_channels, int bf16_weights, unsigned long long seed);
+void stdd_nn_destroy(stdd_nn *nn);
+/* Number of floats in the parameter array (-1 for NULL). */
+long long stdd_nn_num_params(const stdd_nn *nn);
+/* Copy the FP32 master parameters out / in (host arrays of num_params
+ * floats).  set_params also resets nothing else (Adam moments are kept). */
+stdd_status stdd_nn_get_params(stdd_nn *nn, float *host);
+stdd_status stdd_nn_set_params(stdd_nn *nn, const float *host);
+/* output[batch][2][H][W] = network(input[batch][3][H][W]); device pointers. */
+stdd_status stdd_nn_forward(stdd_nn *nn, int batch, int H, int W, const float *input, float *output);
+/* Loss and its gradient with respect to every parameter for one batch
+ * (input, target: device pointers, target [batch][2][H][W]); *loss_out
+ * (host, may be NULL) and grad_host (host, num_params floats, may be NULL)
+ * receive them.  Parameters are not changed. */
+stdd_status stdd_nn_gradient(stdd_nn *nn, int batch, int H, int W, const float *input, const float *target,
+                             float *loss_out, float *grad_host);
+/* One Adam step with learning rate lr on the batch; *loss_out (host, may be
+ * NULL) receives the loss before the step. */
+stdd_status stdd_nn_train_step(stdd_nn *nn, int batch, int H, int W, const float *input, const float *target,
+                               float lr, float *loss_out);
+/* Network images of one problem, with the normalisation the solver's
+ * STDD_X0_LEARNED guess uses (device pointers; eps: nx*ny doubles, b and x:
+ * 2*nx*ny doubles, node (i, j) at i*ny + j):
+ *   input[3][H][W]:  (eps - 1) / 10, Re b / s, Im b / s at row j, column i;
+ *   target[2][H][W]: Re x / (s * unit), Im x / (s * unit) (skipped if x is
+ *                    NULL), s = max over nodes of max(|Re b|, |Im b|).
+ * H >= ny and W >= nx; pixels outside the grid are zero.  The solver uses
+ * unit = dx * dy. */
+stdd_status stdd_nn_make_images(stdd_nn *nn, int nx, int ny, double unit, const double *eps, const double *b,
+                                const double *x, int H, int W, float *input, float *target);
+const char *stdd_nn_last_error(const stdd_nn *nn);
+
+/* Attach a network (or NULL to detach) as the context's STDD_X0_LEARNED
+ * guess; the network must live on the context's device and outlive its use.
+ * For right-hand side b the start is built in three steps:
+ *   y  = network((eps - 1) / 10, Re b / s, Im b / s) * s * dx * dy,
+ *        s = max over nodes of max(|Re b|, |Im b|) (the grid is zero-padded
+ *        to a multiple of 2^(L-1) for the network);
+ *   x  = y + M^-1 (b - A y): one sweep of the preconditioner from y (one
+ *        batched application for all right-hand sides), which removes the
+ *        short-range error the network leaves and keeps its long-range
+ *        field;
+ *   x0 = alpha x with alpha = (A x)^H b / ||A x||^2, the factor that
+ *        minimises ||b - alpha A x||.
+ * If that residual is not below ||b|| (or is not finite) the zero guess is
+ * used.  The sweep is not counted in the iteration count. */
+stdd_status stdd_set_learned_guess(stdd_ctx *ctx, stdd_nn *nn);
+
+/* After a solve with STDD_X0_LEARNED: for right-hand side `rhs`, the
+ * relative residuals ||b - A y|| / ||b|| of the raw network field and
+ * ||b - alpha A x|| / ||b|| of the start, and whether the start was used
+ * (1) or replaced by zero (0).  Any output pointer may be NULL. */
+stdd_status stdd_learned_guess_info(stdd_ctx *ctx, int rhs, double *raw_rel, double *scaled_rel, int *used);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libstdd.so")
 STDD_OK, STDD_EINVAL, STDD_ESTATE, STDD_ENOMEM, STDD_ECUDA = 0, 1, 2, 3, 4
 STDD_EPIVOT, STDD_EBREAKDOWN, STDD_ENOCONV, STDD_ETIMEOUT = 5, 6, 7, 8
 STDD_PREC_FP64, STDD_PREC_C64, STDD_PREC_C64_BF16, STDD_PREC_C64_FP16 = 0, 1, 2, 3
-STDD_X0_ZERO, STDD_X0_USER = 0, 1
+STDD_X0_ZERO, STDD_X0_USER, STDD_X0_LEARNED = 0, 1, 2
 STATUS_NAMES = {0: "STDD_OK", 1: "STDD_EINVAL", 2: "STDD_ESTATE", 3: "STDD_ENOMEM", 4: "STDD_ECUDA",
                 5: "STDD_EPIVOT", 6: "STDD_EBREAKDOWN", 7: "STDD_ENOCONV", 8: "STDD_ETIMEOUT"}
 
@@ -83,6 +83,20 @@ _SIGS = {
     "stdd_tc_selftest": (c_int, [c_int, c_int, P(c_double)]),
     "stdd_nd_analyze": (c_int, [c_int, c_int, c_int, P(c_int), P(ctypes.c_longlong), c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_void_p]),
+    "stdd_nn_create": (c_int, [P(c_void_p), c_int, c_void_p, c_int, c_int, c_int, c_int, ctypes.c_ulonglong]),
+    "stdd_nn_destroy": (None, [c_void_p]),
+    "stdd_nn_num_params": (ctypes.c_longlong, [c_void_p]),
+    "stdd_nn_get_params": (c_int, [c_void_p, c_void_p]),
+    "stdd_nn_set_params": (c_int, [c_void_p, c_void_p]),
+    "stdd_nn_forward": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
+    "stdd_nn_gradient": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, P(ctypes.c_float), c_void_p]),
+    "stdd_nn_train_step": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, ctypes.c_float,
+                                   P(ctypes.c_float)]),
+    "stdd_nn_make_images": (c_int, [c_void_p, c_int, c_int, c_double, c_void_p, c_void_p, c_void_p, c_int, c_int,
+                                    c_void_p, c_void_p]),
+    "stdd_nn_last_error": (ctypes.c_char_p, [c_void_p]),
+    "stdd_set_learned_guess": (c_int, [c_void_p, c_void_p]),
+    "stdd_learned_guess_info": (c_int, [c_void_p, c_int, P(c_double), P(c_double), P(c_int)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -173,6 +187,10 @@ def stdd_solve(ctx, x_out, restart=30, maxit=1000, rtol=1e-10, x0=None, paper_ri
     o.paper_richardson = 1 if paper_richardson else 0
     if x0 is None:
         o.x0_mode, o.x0, o.x0_is_device = STDD_X0_ZERO, None, 0
+    elif isinstance(x0, str):
+        if x0 != "learned":
+            raise ValueError("x0 must be None, 'learned' or a field array")
+        o.x0_mode, o.x0, o.x0_is_device = STDD_X0_LEARNED, None, 0
     else:
         p, dev = _ptr(x0)
         o.x0_mode, o.x0, o.x0_is_device = STDD_X0_USER, p, dev
@@ -303,3 +321,113 @@ def stdd_nd_analyze(W, H, leaf_max=64):
     if st != STDD_OK:
         raise StddError(st, "stdd_nd_analyze failed")
     return dict(p=p, b=b, parent=parent, level=level, nodes=nodes[:nn.value])
+
+
+# ---- learned initial guess ------------------------------------------------
+
+def _check_nn(nn, st):
+    if st != STDD_OK:
+        msg = lib.stdd_nn_last_error(nn) if nn else b"network not created"
+        raise StddError(st, msg.decode() if msg else "")
+    return st
+
+
+def stdd_nn_create(device=0, stream=None, levels=6, base_channels=32, max_channels=256, bf16_weights=True, seed=0):
+    h = c_void_p()
+    st = lib.stdd_nn_create(ctypes.byref(h), int(device), stream, int(levels), int(base_channels),
+                            int(max_channels), 1 if bf16_weights else 0, int(seed))
+    if st != STDD_OK:
+        raise StddError(st, "stdd_nn_create failed")
+    return h
+
+
+def stdd_nn_destroy(nn):
+    lib.stdd_nn_destroy(nn)
+
+
+def stdd_nn_num_params(nn):
+    return int(lib.stdd_nn_num_params(nn))
+
+
+def stdd_nn_get_params(nn):
+    out = np.empty(stdd_nn_num_params(nn), np.float32)
+    _check_nn(nn, lib.stdd_nn_get_params(nn, out.ctypes.data))
+    return out
+
+
+def stdd_nn_set_params(nn, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.size != stdd_nn_num_params(nn):
+        raise ValueError("parameter array has the wrong size")
+    return _check_nn(nn, lib.stdd_nn_set_params(nn, a.ctypes.data))
+
+
+def _dev_f32(t, name):
+    p, dev = _ptr(t)
+    if not dev:
+        raise ValueError(f"{name} must be a device tensor")
+    if getattr(t, "dtype", None) is not None and str(t.dtype) != "torch.float32":
+        raise TypeError(f"{name} must be float32")
+    return p
+
+
+def stdd_nn_forward(nn, inp, out):
+    """out[N, 2, H, W] = network(inp[N, 3, H, W]) (device float32 tensors)."""
+    N, C, H, W = inp.shape
+    if C != 3 or tuple(out.shape) != (N, 2, H, W):
+        raise ValueError("input must be [N, 3, H, W] and output [N, 2, H, W]")
+    return _check_nn(nn, lib.stdd_nn_forward(nn, N, H, W, _dev_f32(inp, "input"), _dev_f32(out, "output")))
+
+
+def stdd_nn_gradient(nn, inp, target):
+    """(loss, gradient array) of the mean squared error for one batch."""
+    N, C, H, W = inp.shape
+    if C != 3 or tuple(target.shape) != (N, 2, H, W):
+        raise ValueError("input must be [N, 3, H, W] and target [N, 2, H, W]")
+    loss = ctypes.c_float(0)
+    g = np.empty(stdd_nn_num_params(nn), np.float32)
+    _check_nn(nn, lib.stdd_nn_gradient(nn, N, H, W, _dev_f32(inp, "input"), _dev_f32(target, "target"),
+                                       ctypes.byref(loss), g.ctypes.data))
+    return float(loss.value), g
+
+
+def stdd_nn_train_step(nn, inp, target, lr):
+    N, C, H, W = inp.shape
+    if C != 3 or tuple(target.shape) != (N, 2, H, W):
+        raise ValueError("input must be [N, 3, H, W] and target [N, 2, H, W]")
+    loss = ctypes.c_float(0)
+    _check_nn(nn, lib.stdd_nn_train_step(nn, N, H, W, _dev_f32(inp, "input"), _dev_f32(target, "target"),
+                                         float(lr), ctypes.byref(loss)))
+    return float(loss.value)
+
+
+def stdd_nn_make_images(nn, unit, eps, b, x, inp, target=None):
+    """Fill inp[3, H, W] (and target[2, H, W] if x is given) from the device
+    fields eps (nx, ny) float64, b and x (nx, ny) complex128."""
+    nx, ny = eps.shape
+    _, H, W = inp.shape
+    pe, de = _ptr(eps)
+    pb, db = _ptr(b)
+    px, dxx = _ptr(x) if x is not None else (None, 1)
+    if not (de and db and dxx):
+        raise ValueError("fields must be device tensors")
+    pt = _dev_f32(target, "target") if x is not None else None
+    return _check_nn(nn, lib.stdd_nn_make_images(nn, nx, ny, float(unit), pe, pb, px, H, W,
+                                                 _dev_f32(inp, "input"), pt))
+
+
+def stdd_nn_last_error(nn):
+    m = lib.stdd_nn_last_error(nn)
+    return m.decode() if m else ""
+
+
+def stdd_set_learned_guess(ctx, nn):
+    return _check(ctx, lib.stdd_set_learned_guess(ctx, nn))
+
+
+def stdd_learned_guess_info(ctx, rhs=0):
+    """(raw relative residual, scaled relative residual, used) of the last
+    learned guess for right-hand side rhs."""
+    a, b, u = c_double(0), c_double(0), c_int(0)
+    _check(ctx, lib.stdd_learned_guess_info(ctx, int(rhs), ctypes.byref(a), ctypes.byref(b), ctypes.byref(u)))
+    return a.value, b.value, bool(u.value)

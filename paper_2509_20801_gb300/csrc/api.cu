@@ -169,6 +169,11 @@ struct stdd_ctx {
 
   // sources and Krylov state
   DBuf d_b, d_x, d_r, d_V, d_Z, d_w, d_part, d_h, d_nrm, d_y, d_pre, d_fpart;
+  // learned initial guess
+  stdd_nn *learned = nullptr;
+  DBuf d_guess, d_gscr;
+  std::vector<double> lg_raw, lg_scaled;
+  std::vector<int> lg_used;
   int V_cols = 0, V_rhs = 0;
   bool last_noconv = false;
   std::vector<std::vector<double>> history;
@@ -338,6 +343,7 @@ struct stdd_ctx {
   void ensure_krylov(int m);
   void gmres_multi(const stdd_solve_opts &o);
   void richardson(int rhs, const stdd_solve_opts &o, double2 *x);
+  void learned_guesses(double2 *X);  // all right-hand sides
   int64_t device_bytes() const;
 };
 
@@ -1038,13 +1044,62 @@ int64_t stdd_ctx::device_bytes() const {
   const DBuf *all[] = {&d_eps, &d_cxm, &d_cxp, &d_cym, &d_cyp, &d_strips, &d_fronts, &d_nodes, &d_cmap,
                        &d_inv, &d_lcxm, &d_lcxp, &d_colstrip, &d_fac, &d_ws[0], &d_ws[1], &d_ub[0],
                        &d_ub[1], &d_tloc, &d_wloc, &d_items, &d_flag, &d_minpiv, &d_b, &d_x, &d_r, &d_V, &d_Z, &d_w,
-                       &d_part, &d_h, &d_nrm, &d_y, &d_pre, &d_fpart};
+                       &d_part, &d_h, &d_nrm, &d_y, &d_pre, &d_fpart, &d_guess, &d_gscr};
   int64_t s = 0;
   for (auto *d : all) s += (int64_t)d->bytes;
   return s;
 }
 
 // ---------------------------------------------------------------- C ABI
+void stdd_ctx::learned_guesses(double2 *X) {
+  if (!learned) throw StateError("STDD_X0_LEARNED needs a network (stdd_set_learned_guess)");
+  const int64_t n = N();
+  d_guess.alloc((size_t)2 * nrhs * n * sizeof(double2));
+  d_gscr.alloc((stdd::NN_PART + 8) * sizeof(double));
+  double *scr = d_gscr.as<double>();
+  double2 *R = d_guess.as<double2>(), *Zs = R + (int64_t)nrhs * n;
+  std::vector<double> bnorm(nrhs), raw(nrhs);
+  std::vector<const double2 *> vs;
+  std::vector<double2 *> zs;
+  for (int q = 0; q < nrhs; ++q) {
+    const double2 *b = d_b.as<double2>() + (int64_t)q * n;
+    double2 *x = X + (int64_t)q * n, *r = R + (int64_t)q * n;
+    // network field y, then its residual r = b - A y
+    stdd::nn_guess_field(learned, d_eps.as<double>(), b, nx, ny, dx * dy, x, scr, stream);
+    stdd::launch_residual(grid(), b, x, r, stream);
+    bnorm[q] = dev_norm(const_cast<double2 *>(b), n, d_part, d_nrm, stream);
+    raw[q] = bnorm[q] > 0 ? dev_norm(r, n, d_part, d_nrm, stream) / bnorm[q] : 0.0;
+    vs.push_back(r);
+    zs.push_back(Zs + (int64_t)q * n);
+  }
+  // one sweep of the method from y: x0 = y + M^-1 (b - A y), all right-hand
+  // sides in one preconditioner application
+  apply_minv_multi(vs, zs);
+  for (int q = 0; q < nrhs; ++q) {
+    const double2 *b = d_b.as<double2>() + (int64_t)q * n;
+    double2 *x = X + (int64_t)q * n, *Ax = R + (int64_t)q * n;
+    stdd::nn_zadd(zs[q], x, n, stream);
+    stdd::launch_stencil(grid(), x, Ax, stream);
+    stdd::nn_fit(Ax, b, n, scr, scr + stdd::NN_PART + 4, stream);
+    double h[4];
+    CK(cudaMemcpyAsync(h, scr + stdd::NN_PART + 4, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    // with alpha = (A x0)^H b / |A x0|^2, ||b - alpha A x0||^2 = |b|^2 - |(A x0)^H b|^2 / |A x0|^2
+    const double bb = h[3], aa = h[2], dr = h[0], di = h[1];
+    double scaled = 1;
+    bool use = false;
+    if (bb > 0 && aa > 0 && std::isfinite(aa) && std::isfinite(dr) && std::isfinite(di)) {
+      scaled = std::sqrt(std::max(0.0, 1.0 - (dr * dr + di * di) / (aa * bb)));
+      use = scaled < 1.0 - 1e-12;
+    }
+    lg_raw[q] = raw[q];
+    lg_scaled[q] = use ? scaled : 1.0;
+    lg_used[q] = use ? 1 : 0;
+    if (use) stdd::nn_zscale(x, n, dr / aa, di / aa, stream);
+    else CK(cudaMemsetAsync(x, 0, n * sizeof(double2), stream));
+  }
+}
+
 namespace {
 
 template <typename F> stdd_status guarded(stdd_ctx *c, F &&f) {
@@ -1248,16 +1303,24 @@ stdd_status stdd_solve(stdd_ctx *c, const stdd_solve_opts *o, double *x_out, int
     if (c->nrhs < 1) throw StateError("no sources set");
     if (o->restart < 1 || o->restart > 500 || o->maxit < 0 || !(o->rtol >= 0)) throw ArgError("bad solve options");
     if (o->x0_mode == STDD_X0_USER && !o->x0) throw ArgError("x0 missing");
+    if (o->x0_mode < STDD_X0_ZERO || o->x0_mode > STDD_X0_LEARNED) throw ArgError("bad x0_mode");
     const int64_t n = c->N();
     c->history.assign(c->nrhs, {});
+    c->lg_raw.assign(c->nrhs, 0.0);
+    c->lg_scaled.assign(c->nrhs, 1.0);
+    c->lg_used.assign(c->nrhs, 0);
     c->ensure_krylov(o->paper_richardson ? 1 : o->restart);
     const int span = c->pbegin(stdd_ctx::PH_SOLVE);
     double2 *X = c->d_x.as<double2>();
-    for (int q = 0; q < c->nrhs; ++q) {
-      if (o->x0_mode == STDD_X0_USER)
-        copy_in(X + (int64_t)q * n, o->x0 + (size_t)q * n * 2, n * sizeof(double2), o->x0_is_device, c->stream);
-      else
-        CK(cudaMemsetAsync(X + (int64_t)q * n, 0, n * sizeof(double2), c->stream));
+    if (o->x0_mode == STDD_X0_LEARNED) {
+      c->learned_guesses(X);
+    } else {
+      for (int q = 0; q < c->nrhs; ++q) {
+        if (o->x0_mode == STDD_X0_USER)
+          copy_in(X + (int64_t)q * n, o->x0 + (size_t)q * n * 2, n * sizeof(double2), o->x0_is_device, c->stream);
+        else
+          CK(cudaMemsetAsync(X + (int64_t)q * n, 0, n * sizeof(double2), c->stream));
+      }
     }
     if (o->paper_richardson) {
       for (int q = 0; q < c->nrhs; ++q) c->richardson(q, *o, X + (int64_t)q * n);
@@ -1495,6 +1558,22 @@ stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {
       c->span_level.clear();
       c->ev_used = 0;
     }
+  });
+}
+
+stdd_status stdd_set_learned_guess(stdd_ctx *c, stdd_nn *nn) {
+  return guarded(c, [&] {
+    if (nn && stdd::nn_device(nn) != c->device) throw ArgError("network lives on another device");
+    c->learned = nn;
+  });
+}
+
+stdd_status stdd_learned_guess_info(stdd_ctx *c, int rhs, double *raw_rel, double *scaled_rel, int *used) {
+  return guarded(c, [&] {
+    if (rhs < 0 || rhs >= (int)c->lg_used.size()) throw ArgError("no guess recorded for that right-hand side");
+    if (raw_rel) *raw_rel = c->lg_raw[rhs];
+    if (scaled_rel) *scaled_rel = c->lg_scaled[rhs];
+    if (used) *used = c->lg_used[rhs];
   });
 }
 

@@ -119,4 +119,45 @@ void launch_norm2(const double2 *x, int64_t n, double *partial, double *nrm2, cu
 void launch_scale(const double2 *x, const double *inv_norm2, double2 *y, int64_t n, cudaStream_t st);
 int krylov_partial_blocks();
 
+// ---- learned initial guess (kernels_nn.cu): FP32 NCHW activations
+// out = conv3x3(in) + bias (zero padding, optional ReLU); flip = 1 applies
+// the input gradient of the convolution with weights w[Cout'][Cin'] instead
+void nn_conv(const float *in, int Cin, const float *w, const float *bias, float *out, int Cout, int N, int H, int W,
+             bool relu, bool flip, cudaStream_t st);
+// gw += weight gradient, gb += bias gradient (accumulated: zero them first)
+void nn_conv_wgrad(const float *in, int Cin, const float *gout, int Cout, int N, int H, int W, float *gw, float *gb,
+                   cudaStream_t st);
+void nn_relu_mask(const float *y, float *g, int64_t n, cudaStream_t st);  // g = 0 where y <= 0
+void nn_pool2(const float *in, float *out, int64_t planes, int H, int W, cudaStream_t st);       // H, W of in
+void nn_pool2_bwd(const float *gout, float *gin, int64_t planes, int H, int W, cudaStream_t st);  // H, W of gin
+void nn_up2(const float *in, float *out, int64_t planes, int H, int W, cudaStream_t st);         // H, W of out
+void nn_up2_bwd(const float *gout, float *gin, int64_t planes, int H, int W, cudaStream_t st);   // H, W of gout
+void nn_axpy(const float *x, float *y, float a, int64_t n, cudaStream_t st);
+// loss += sum (p - t)^2 / n, g = 2 (p - t) / n
+void nn_mse(const float *p, const float *t, float *g, int64_t n, float *loss, cudaStream_t st);
+void nn_adam(float *w, float *wb, const float *g, float *m, float *v, int64_t n, float lr, int step, bool bf16,
+             cudaStream_t st);
+void nn_round(const float *w, float *wb, int64_t n, bool bf16, cudaStream_t st);
+void nn_input(const double *eps, const double2 *b, const double *scale, float *out, int nx, int ny, int Wp, int Hp,
+              cudaStream_t st);
+void nn_output(const float *out, const double *scale, double unit, double2 *x0, int nx, int ny, int Wp, int Hp,
+               cudaStream_t st);
+void nn_target(const double2 *x, const double *scale, double unit, float *out, int nx, int ny, int Wp, int Hp,
+               cudaStream_t st);
+void nn_absmax(const double2 *b, int64_t n, double *part, double *out, cudaStream_t st);
+void nn_fit(const double2 *a, const double2 *b, int64_t n, double *part, double *out4, cudaStream_t st);
+void nn_zscale(double2 *x, int64_t n, double ar, double ai, cudaStream_t st);  // x *= ar + i ai
+void nn_zadd(const double2 *z, double2 *x, int64_t n, cudaStream_t st);              // x += z
+constexpr int NN_PART = 4 * 608;  // doubles of scratch nn_absmax / nn_fit need
+
+}  // namespace stdd
+
+// The network object (nn.cu); the solver asks it for a raw field guess.
+struct stdd_nn;
+namespace stdd {
+int nn_device(const stdd_nn *nn);
+// x0 = network(eps, b) * max(|Re b|, |Im b|) * unit on the nx x ny grid;
+// scratch holds NN_PART doubles + 1
+void nn_guess_field(stdd_nn *nn, const double *eps, const double2 *b, int nx, int ny, double unit, double2 *x0,
+                    double *scratch, cudaStream_t st);
 }  // namespace stdd

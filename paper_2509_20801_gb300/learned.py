@@ -1,0 +1,195 @@
+"""Learned initial guess: the network object, training-data generation with
+the solver itself, training, and the comparison with the zero guess.
+
+Every numerical step runs in libstdd.so (network forward/backward/Adam,
+image preparation, the DDM solves); torch provides device memory only.
+The network is described in include/stdd.h (stdd_nn_*)."""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import binding as _b
+
+
+class Network:
+    """Encoder-decoder guess network on one GPU (see stdd_nn_create)."""
+
+    def __init__(self, levels=6, base_channels=32, max_channels=256, bf16_weights=True, seed=0, device=0,
+                 stream=None):
+        self.levels, self.base, self.cmax = int(levels), int(base_channels), int(max_channels)
+        self.bf16 = bool(bf16_weights)
+        self.device = int(device)
+        self.h = _b.stdd_nn_create(device, stream, levels, base_channels, max_channels, bf16_weights, seed)
+
+    @property
+    def multiple(self):
+        """Image sides must be multiples of this."""
+        return 1 << (self.levels - 1)
+
+    def num_params(self):
+        return _b.stdd_nn_num_params(self.h)
+
+    def get_params(self):
+        return _b.stdd_nn_get_params(self.h)
+
+    def set_params(self, p):
+        _b.stdd_nn_set_params(self.h, p)
+
+    def save(self, path):
+        np.savez(path, params=self.get_params(), levels=self.levels, base=self.base, cmax=self.cmax,
+                 bf16=self.bf16)
+
+    @classmethod
+    def load(cls, path, device=0, stream=None):
+        z = np.load(path)
+        net = cls(int(z["levels"]), int(z["base"]), int(z["cmax"]), bool(z["bf16"]), device=device, stream=stream)
+        net.set_params(z["params"])
+        return net
+
+    def forward(self, inp, out):
+        _b.stdd_nn_forward(self.h, inp, out)
+
+    def gradient(self, inp, target):
+        return _b.stdd_nn_gradient(self.h, inp, target)
+
+    def train_step(self, inp, target, lr):
+        return _b.stdd_nn_train_step(self.h, inp, target, lr)
+
+    def images(self, unit, eps, b, x, inp, target=None):
+        _b.stdd_nn_make_images(self.h, unit, eps, b, x, inp, target)
+
+    def image_shape(self, nx, ny):
+        f = self.multiple
+        return -(-ny // f) * f, -(-nx // f) * f
+
+    def close(self):
+        if self.h is not None:
+            _b.stdd_nn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _solver(w, precision, device):
+    from . import Solver
+    import torch
+    dev = torch.device("cuda", device)
+    eps = torch.from_numpy(w.eps_node).to(dev)
+    s = Solver.from_workload(w, eps=eps, precision=precision, device=device)
+    return s, eps
+
+
+def solve_workload(w, precision=_b.STDD_PREC_FP64, rtol=None, restart=None, maxit=1000, device=0, x0=None,
+                   net=None):
+    """Factor and solve every right-hand side of workload w on the GPU.
+    Returns (x [nrhs, nx, ny] complex128 device tensor, info dict)."""
+    import torch
+    dev = torch.device("cuda", device)
+    s, eps = _solver(w, precision, device)
+    try:
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s.factor()
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        b = torch.from_numpy(w.b).to(dev)
+        s.set_sources(b)
+        if net is not None:
+            _b.stdd_set_learned_guess(s.ctx, net.h)
+        x = torch.empty_like(b)
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+        st = s.solve(x, restart=restart or w.restart, rtol=rtol or w.rtol, maxit=maxit, x0=x0,
+                     allow_noconv=True)
+        torch.cuda.synchronize(dev)
+        t3 = time.perf_counter()
+        hist = [s.history(q) for q in range(w.nrhs)]
+        info = dict(factor_s=t1 - t0, solve_s=t3 - t2, converged=st == _b.STDD_OK,
+                    iterations=[len(h) - 1 for h in hist], r0=[float(h[0]) for h in hist],
+                    final=[float(h[-1]) for h in hist])
+        if x0 == "learned":
+            g = [_b.stdd_learned_guess_info(s.ctx, q) for q in range(w.nrhs)]
+            info["guess_raw"] = [a for a, _, _ in g]
+            info["guess_scaled"] = [c for _, c, _ in g]
+            info["guess_used"] = [u for _, _, u in g]
+        return x, info
+    finally:
+        s.close()
+
+
+def make_dataset(net, workloads, H, W, precision=_b.STDD_PREC_FP64, rtol=1e-8, device=0, log=None):
+    """Solve each workload's right-hand sides with the DDM and turn every
+    (eps, b, x) into a network image pair.  Returns (inputs [S, 3, H, W],
+    targets [S, 2, H, W]) float32 device tensors and the solve infos."""
+    import torch
+    dev = torch.device("cuda", device)
+    S = sum(w.nrhs for w in workloads)
+    inputs = torch.zeros((S, 3, H, W), dtype=torch.float32, device=dev)
+    targets = torch.zeros((S, 2, H, W), dtype=torch.float32, device=dev)
+    infos, k = [], 0
+    for wi, w in enumerate(workloads):
+        if w.nx > W or w.ny > H:
+            raise ValueError("workload larger than the image")
+        x, info = solve_workload(w, precision=precision, rtol=rtol, device=device)
+        infos.append(info)
+        eps = torch.from_numpy(w.eps_node).to(dev)
+        b = torch.from_numpy(w.b).to(dev)
+        for q in range(w.nrhs):
+            net.images(w.dx * w.dy, eps, b[q], x[q], inputs[k], targets[k])
+            k += 1
+        if log and (wi % 16 == 0 or wi + 1 == len(workloads)):
+            log(f"dataset: {wi + 1}/{len(workloads)} geometries, {k} samples")
+    return inputs, targets, infos
+
+
+def train(net, inputs, targets, epochs=10, batch=8, lr=1e-3, lr_final=None, seed=0, log=None):
+    """Adam on the mean squared error, shuffled mini-batches (samples are
+    copied into one batch buffer).  lr decays geometrically to lr_final.
+    Returns the per-step losses."""
+    import torch
+    S = inputs.shape[0]
+    batch = min(batch, S)
+    rng = np.random.default_rng(seed)
+    bi = torch.empty((batch,) + tuple(inputs.shape[1:]), dtype=inputs.dtype, device=inputs.device)
+    bt = torch.empty((batch,) + tuple(targets.shape[1:]), dtype=targets.dtype, device=targets.device)
+    steps = epochs * (S // batch)
+    lr_final = lr if lr_final is None else lr_final
+    decay = (lr_final / lr) ** (1.0 / max(1, steps - 1))
+    losses, step = [], 0
+    for ep in range(epochs):
+        perm = rng.permutation(S)
+        for k0 in range(0, S - batch + 1, batch):
+            for j, i in enumerate(perm[k0:k0 + batch]):
+                bi[j].copy_(inputs[int(i)])
+                bt[j].copy_(targets[int(i)])
+            losses.append(net.train_step(bi, bt, lr * decay ** step))
+            step += 1
+        if log:
+            log(f"epoch {ep + 1}/{epochs}: loss {np.mean(losses[-max(1, S // batch):]):.4e}")
+    return losses
+
+
+def compare(net, workloads, precision=_b.STDD_PREC_C64, rtol=1e-8, device=0):
+    """Solve each workload with the zero guess and with the learned guess
+    (same precision and tolerance); per right-hand side: iterations, solve
+    times and the guess's residuals."""
+    rows = []
+    for w in workloads:
+        xz, iz = solve_workload(w, precision=precision, rtol=rtol, device=device)
+        xl, il = solve_workload(w, precision=precision, rtol=rtol, device=device, x0="learned", net=net)
+        for q in range(w.nrhs):
+            rows.append(dict(nx=w.nx, ny=w.ny, seed=w.meta.get("seed"), rhs=q,
+                             its_zero=iz["iterations"][q], its_learned=il["iterations"][q],
+                             # preconditioner applications: the learned start spends one sweep
+                             minv_zero=iz["iterations"][q], minv_learned=il["iterations"][q] + 1,
+                             solve_s_zero=iz["solve_s"] / w.nrhs, solve_s_learned=il["solve_s"] / w.nrhs,
+                             guess_raw=il["guess_raw"][q], guess_scaled=il["guess_scaled"][q],
+                             guess_used=il["guess_used"][q], conv_zero=iz["converged"],
+                             conv_learned=il["converged"], x_zero=xz[q], x_learned=xl[q]))
+    return rows

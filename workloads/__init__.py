@@ -214,6 +214,63 @@ def random_medium(nx, ny, ppw=20, seed=0, eps_range=(1.0, 4.0), npml=10,
                     meta=dict(seed=seed))
 
 
+def ellipses(nx, ny, seed, ppw=24, npml=20, overlap=8, interface_pml=20, nsub=None, nrhs=1,
+             sources="mixed", fill=(0.15, 0.30), eps_range=(2.0, 12.1), axes=(0.2, 1.0),
+             keep=0.5, wavelength=1.0, rtol=1e-8, restart=30):
+    """Vacuum with seeded non-overlapping dielectric ellipses (the batched and
+    learned-guess geometries): semi-axes U[axes] wavelengths, random angle,
+    eps U[eps_range] each, painted until the ellipses' total area reaches a
+    fill fraction drawn from U[fill] of the non-PML area (or 400 placement
+    attempts run out).  Ellipses are kept ``keep`` wavelengths from the PML
+    and are separated by their circumscribed circles.  The number of strips
+    is drawn from [2, max(2, min(8, nx // 128))] unless given.  Sources:
+    ``"point"`` (unit point sources at random nodes at least ``keep`` from
+    the PML), ``"line"`` (x-directed line sources on random rows) or
+    ``"mixed"`` (each right-hand side one or the other, equally likely)."""
+    rng = np.random.default_rng(seed)
+    d = wavelength / ppw
+    x_lo, x_hi = npml * d + keep * wavelength, (nx - 1 - npml) * d - keep * wavelength
+    y_lo, y_hi = npml * d + keep * wavelength, (ny - 1 - npml) * d - keep * wavelength
+    area = max(0.0, ((nx - 1 - 2 * npml) * d)) * max(0.0, ((ny - 1 - 2 * npml) * d))
+    target = rng.uniform(*fill) * area
+    placed, objs, got = [], [], 0.0
+    for _ in range(400):
+        if got >= target or x_hi <= x_lo or y_hi <= y_lo:
+            break
+        a, b = rng.uniform(*axes, size=2) * wavelength
+        r = max(a, b)
+        if x_hi - x_lo <= 2 * r or y_hi - y_lo <= 2 * r:
+            continue
+        cx = rng.uniform(x_lo + r, x_hi - r)
+        cy = rng.uniform(y_lo + r, y_hi - r)
+        th = rng.uniform(0, math.pi)
+        if any((cx - px) ** 2 + (cy - py) ** 2 < (r + pr) ** 2 for px, py, pr in placed):
+            continue
+        placed.append((cx, cy, r))
+        objs.append((_ellipse(cx, cy, a, b, th), float(rng.uniform(*eps_range))))
+        got += math.pi * a * b
+    cells = cell_permittivity(nx, ny, d, d, 1.0, objs)
+    eps = node_permittivity(cells)
+    if nsub is None:
+        nsub = int(rng.integers(2, max(2, min(8, nx // 128)) + 1))
+    i_lo, i_hi = npml + int(math.ceil(keep * ppw)), nx - 1 - npml - int(math.ceil(keep * ppw))
+    j_lo, j_hi = npml + int(math.ceil(keep * ppw)), ny - 1 - npml - int(math.ceil(keep * ppw))
+    b = np.zeros((nrhs, nx, ny), np.complex128)
+    kinds = []
+    for q in range(nrhs):
+        kind = sources if sources != "mixed" else ("point" if rng.random() < 0.5 else "line")
+        if kind == "point":
+            b[q] = point_source(nx, ny, d, d, int(rng.integers(i_lo, i_hi + 1)), int(rng.integers(j_lo, j_hi + 1)))
+        else:
+            b[q] = line_source_x(nx, ny, d, int(rng.integers(j_lo, j_hi + 1)))
+        kinds.append(kind)
+    return Workload("ellipses", nx, ny, d, d, wavelength, eps, b,
+                    npml=(npml,) * 4, nsub=nsub, overlap=overlap,
+                    interface_pml=interface_pml, restart=restart, rtol=rtol,
+                    meta=dict(seed=seed, n_ellipses=len(objs), fill=got / area if area else 0.0,
+                              sources=kinds))
+
+
 def random_vector(n, seed, nrhs=1):
     """Seeded complex test vector(s) of length n (operator parity inputs)."""
     rng = np.random.default_rng(seed)
