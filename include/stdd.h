@@ -297,19 +297,31 @@ stdd_status stdd_nd_analyze(int W, int H, int leaf_max, int *nfronts, long long 
  * [cout][cin][3][3] then its bias [cout].
  * Images: float, NCHW, [batch][channel][H][W] row-major; H and W multiples
  * of 2^(L-1).  The solver's node (i, j) is image row j, column i.
- * Arithmetic: the weights used by forward and backward passes are the FP32
- * master weights rounded to BF16 (bf16_weights = 1) or the FP32 weights
- * themselves (0); activations and accumulation are FP32.
+ * Arithmetic (mode): the weights used by forward and backward passes are the
+ * FP32 master weights rounded to BF16, or the FP32 weights themselves
+ * (STDD_NN_FP32); activations are FP32 and rounded to BF16 only as
+ * tensor-core operands (STDD_NN_TC); accumulation is FP32.
  * Loss: mean squared error over all outputs of the batch.  Optimiser: Adam
  * (beta1 0.9, beta2 0.999, eps 1e-8) on the FP32 master weights.
  * ------------------------------------------------------------------- */
 typedef struct stdd_nn stdd_nn;
 
+enum {
+  STDD_NN_FP32 = 0,       /* FP32 weights, CUDA-core convolutions (exact-layout
+                             reference mode)                                 */
+  STDD_NN_BF16 = 1,       /* BF16-rounded weights, FP32 activations, CUDA cores */
+  STDD_NN_TC = 2          /* BF16 weights and activations in the convolutions
+                             on the tensor cores (tcgen05), FP32 accumulation;
+                             weight gradients on CUDA cores in FP32; at most
+                             256 channels                                    */
+};
+
 /* Create a network on `device` (stream as in stdd_create), weights He-normal
  * from `seed` (output layer scaled by 0.1), biases zero.  levels 1..8,
- * 1 <= base_channels <= max_channels. */
+ * 1 <= base_channels <= max_channels, mode one of STDD_NN_*.  A tensor-core
+ * wait that times out makes the call that launched it return STDD_ECUDA. */
 stdd_status stdd_nn_create(stdd_nn **out, int device, void *cuda_stream, int levels, int base_channels,
-                           int max_channels, int bf16_weights, unsigned long long seed);
+                           int max_channels, int mode, unsigned long long seed);
 void stdd_nn_destroy(stdd_nn *nn);
 /* Number of floats in the parameter array (-1 for NULL). */
 long long stdd_nn_num_params(const stdd_nn *nn);

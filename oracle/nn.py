@@ -127,9 +127,26 @@ def up2_T(g):
 
 # ---------------------------------------------------------------- network
 
-def forward(params, x, L, c0, cmax, round_bf16=False):
-    """Network output [N, 2, H, W] and the cache the backward pass needs."""
+def _conv(x, W, b):
+    return conv3x3(x, W, b)
+
+
+def _conv_backward(x, W, gout):
+    return conv3x3_backward(x, W, gout)
+
+
+def forward(params, x, L, c0, cmax, round_bf16=False, round_act=False):
+    """Network output [N, 2, H, W] and the cache the backward pass needs.
+    round_bf16 rounds the weights to BF16; round_act also rounds every
+    convolution's input to BF16 (the operand rounding of the tensor-core
+    mode; it makes the loss piecewise constant, so finite differences do not
+    apply to it)."""
     p = bf16_round(params) if round_bf16 else params
+    if round_act:
+        def conv3x3(v, W, b):
+            return _conv(bf16_round(v), W, b)
+    else:
+        conv3x3 = _conv
     layers = unpack(p, L, c0, cmax)
     enc = [(layers[2 * l], layers[2 * l + 1]) for l in range(L)]
     dec = {}
@@ -159,6 +176,7 @@ def forward(params, x, L, c0, cmax, round_bf16=False):
         cache["d"][l] = d
     cache["last"] = d
     cache["enc"], cache["dec"], cache["out_layer"] = enc, dec, out_layer
+    cache["round_act"] = round_act
     return conv3x3(d, *out_layer), cache
 
 
@@ -166,6 +184,15 @@ def backward(cache, gout, L):
     """Flat parameter gradient and input gradient for output gradient gout
     (the chain rule through forward() in reverse order)."""
     enc, dec, out_layer = cache["enc"], cache["dec"], cache["out_layer"]
+    if cache.get("round_act"):
+        # tensor-core mode: the input-gradient convolution reads BF16 output
+        # gradients, the weight gradient the FP32 ones
+        def conv3x3_backward(x, W, gout):
+            gx, _, _ = _conv_backward(x, W, bf16_round(gout))
+            _, gW, gb = _conv_backward(x, W, gout)
+            return gx, gW, gb
+    else:
+        conv3x3_backward = _conv_backward
     grads = {}
     gd, gW, gb = conv3x3_backward(cache["last"], out_layer[0], gout)
     grads["out"] = (gW, gb)
@@ -210,8 +237,8 @@ def mse(pred, target):
     return float((d * d).sum() / d.size), 2.0 * d / d.size
 
 
-def loss_and_grad(params, x, target, L, c0, cmax, round_bf16=False):
-    out, cache = forward(params, x, L, c0, cmax, round_bf16)
+def loss_and_grad(params, x, target, L, c0, cmax, round_bf16=False, round_act=False):
+    out, cache = forward(params, x, L, c0, cmax, round_bf16, round_act)
     loss, g = mse(out, target)
     gp, gx = backward(cache, g, L)
     return loss, gp, gx

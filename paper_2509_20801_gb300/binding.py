@@ -20,6 +20,7 @@ STDD_OK, STDD_EINVAL, STDD_ESTATE, STDD_ENOMEM, STDD_ECUDA = 0, 1, 2, 3, 4
 STDD_EPIVOT, STDD_EBREAKDOWN, STDD_ENOCONV, STDD_ETIMEOUT = 5, 6, 7, 8
 STDD_PREC_FP64, STDD_PREC_C64, STDD_PREC_C64_BF16, STDD_PREC_C64_FP16 = 0, 1, 2, 3
 STDD_X0_ZERO, STDD_X0_USER, STDD_X0_LEARNED = 0, 1, 2
+STDD_NN_FP32, STDD_NN_BF16, STDD_NN_TC = 0, 1, 2
 STATUS_NAMES = {0: "STDD_OK", 1: "STDD_EINVAL", 2: "STDD_ESTATE", 3: "STDD_ENOMEM", 4: "STDD_ECUDA",
                 5: "STDD_EPIVOT", 6: "STDD_EBREAKDOWN", 7: "STDD_ENOCONV", 8: "STDD_ETIMEOUT"}
 
@@ -332,10 +333,10 @@ def _check_nn(nn, st):
     return st
 
 
-def stdd_nn_create(device=0, stream=None, levels=6, base_channels=32, max_channels=256, bf16_weights=True, seed=0):
+def stdd_nn_create(device=0, stream=None, levels=6, base_channels=32, max_channels=256, mode=STDD_NN_TC, seed=0):
     h = c_void_p()
     st = lib.stdd_nn_create(ctypes.byref(h), int(device), stream, int(levels), int(base_channels),
-                            int(max_channels), 1 if bf16_weights else 0, int(seed))
+                            int(max_channels), int(mode), int(seed))
     if st != STDD_OK:
         raise StddError(st, "stdd_nn_create failed")
     return h

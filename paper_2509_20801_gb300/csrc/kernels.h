@@ -150,6 +150,18 @@ void nn_zscale(double2 *x, int64_t n, double ar, double ai, cudaStream_t st);  /
 void nn_zadd(const double2 *z, double2 *x, int64_t n, cudaStream_t st);              // x += z
 constexpr int NN_PART = 4 * 608;  // doubles of scratch nn_absmax / nn_fit need
 
+// ---- tensor-core convolutions (kernels_nn_tc.cu): BF16 operands, FP32
+// accumulation; Cout <= 256.  Weights are packed per layer by nn_pack_weights
+// (flip = the layer's input-gradient convolution) into nn_tc_packed_elems
+// halves.  flag |= 1 if a wait timed out.
+cudaError_t nn_tc_setup();
+int nn_tc_npad(int Cout);
+int nn_tc_nchunks(int Cin);
+int64_t nn_tc_packed_elems(int Cin, int Cout);
+void nn_pack_weights(const float *w, int CinL, int CoutL, bool flip, uint16_t *out, cudaStream_t st);
+void nn_conv_tc(const float *in, int Cin, const uint16_t *wp, const float *bias, float *out, int Cout, int N, int H,
+                int W, bool relu, int *flag, cudaStream_t st);
+
 }  // namespace stdd
 
 // The network object (nn.cu); the solver asks it for a raw field guess.

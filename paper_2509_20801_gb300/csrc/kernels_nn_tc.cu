@@ -1,0 +1,248 @@
+// Tensor-core (tcgen05) 3x3 convolutions of the learned-guess network: the
+// forward pass and the input gradient (the same convolution with the
+// weights transposed and flipped), as implicit GEMMs with BF16 operands and
+// FP32 accumulation in TMEM.
+//
+// One CTA (256 threads) computes a 16 x 16 pixel tile for all output
+// channels (N = Cout rounded up to 16, at most 256) as two M = 128 halves
+// (16 rows x 8 columns each, accumulators side by side in TMEM).  The input
+// channels are consumed in chunks of 16 (K = 16 per MMA); per chunk the
+// threads stage the 18 x 18 halo of the tile as BF16, channel-innermost in
+// two 8-channel planes, and one thread issues 9 taps x 2 halves MMAs.  With
+// the halo rows 18 pixels apart, the A operand of tap (ky, kx) is the halo
+// viewed from pixel (ky, kx): core matrices of 8 consecutive pixels x 8
+// channels, SBO = one halo row (288 B), LBO = one channel plane, so no
+// im2col copy is made.  The B operand (weights) is packed once per weight
+// update into the exact shared-memory order and arrives by one bulk copy per
+// chunk.  Activations and weights are double-buffered: chunk c+1 is staged
+// while the MMAs of chunk c run.  Every wait has an iteration limit; a
+// timeout sets the error flag and the CTA stops cleanly.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_ptx.cuh"
+
+namespace stdd {
+
+namespace {
+
+constexpr int CT_T = 16;                        // tile side (pixels)
+constexpr int CT_HP = CT_T + 2;                 // halo pitch (pixels)
+constexpr int CT_PLANE = CT_HP * CT_HP * 16;    // one 8-channel plane: 5184 B
+constexpr int CT_ACT = 2 * CT_PLANE;            // one stage of activations
+constexpr long long CT_WAIT = 1ll << 22;
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
+__host__ __device__ inline int tmem_cols_for(int Npad) {
+  int c = 32;
+  while (c < 2 * Npad) c <<= 1;
+  return c;
+}
+
+struct ConvTcArgs {
+  const float *in;
+  int Cin;
+  const uint16_t *wp;    // packed weights [chunk][tap][cg][Npad][8] BF16
+  int Npad, nchunks;
+  const float *bias;
+  float *out;
+  int Cout, H, W, relu;
+  int *flag;
+};
+
+__global__ void __launch_bounds__(256) k_conv3x3_tc(ConvTcArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  const int wbytes = 288 * a.Npad;
+  uint8_t *act0 = sm;
+  uint8_t *wst0 = sm + 2 * CT_ACT;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * CT_ACT + 2 * wbytes);  // w[2], mma[2]
+  uint32_t *tm = reinterpret_cast<uint32_t *>(bars + 4);
+  int *abort_flag = reinterpret_cast<int *>(tm + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tiles_x = (a.W + CT_T - 1) / CT_T;
+  const int x0 = (blockIdx.x % tiles_x) * CT_T, y0 = (blockIdx.x / tiles_x) * CT_T;
+  const int n = blockIdx.y;
+  const int cols = tmem_cols_for(a.Npad);
+  const uint32_t bar0 = tcx::smem_u32(&bars[0]);
+  auto bw = [&](int s) { return bar0 + 8u * (uint32_t)s; };        // weight copies landed
+  auto bm = [&](int s) { return bar0 + 16u + 8u * (uint32_t)s; };  // MMAs of the stage done
+  if (warp == 0) tcx::tmem_alloc(tcx::smem_u32(tm), (uint32_t)cols);
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) tcx::mbar_init(tcx::smem_u32(&bars[i]), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  tcx::fence_before();
+  __syncthreads();
+  tcx::fence_after();
+  const uint32_t tmem = *tm;
+  const uint32_t idesc = tcx::instr_desc_f16(1, 128, a.Npad);
+  const int64_t plane = (int64_t)a.H * a.W;
+  const float *inb = a.in + (int64_t)n * a.Cin * plane;
+  bool ok = true;
+  int issued = 0;   // chunks whose MMAs were committed
+  for (int c = 0; c < a.nchunks; ++c) {
+    const int s = c & 1;
+    uint8_t *act = act0 + s * CT_ACT;
+    uint8_t *wst = wst0 + s * wbytes;
+    // stage s is free once the MMAs of chunk c - 2 completed
+    if (c >= 2 && !tcx::mbar_wait(bm(s), ((c - 2) >> 1) & 1, CT_WAIT)) ok = false;
+    if (!__syncthreads_and(ok && !*abort_flag)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) {
+      tcx::mbar_expect_tx(bw(s), (uint32_t)wbytes);
+      tcx::bulk_g2s(tcx::smem_u32(wst), a.wp + (size_t)c * (wbytes / 2), (uint32_t)wbytes, bw(s));
+    }
+    // halo tile of 16 channels: items (plane cg, halo row, halo column)
+    for (int it = tid; it < 2 * CT_HP * CT_HP; it += 256) {
+      const int cg = it / (CT_HP * CT_HP), r = it % (CT_HP * CT_HP);
+      const int hr = r / CT_HP, hc = r % CT_HP;
+      const int y = y0 - 1 + hr, x = x0 - 1 + hc;
+      const bool in_img = y >= 0 && y < a.H && x >= 0 && x < a.W;
+      const int ci0 = c * 16 + cg * 8;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        v[j] = (in_img && ci0 + j < a.Cin) ? inb[(int64_t)(ci0 + j) * plane + (int64_t)y * a.W + x] : 0.f;
+      *reinterpret_cast<uint4 *>(act + cg * CT_PLANE + (hr * CT_HP + hc) * 16) =
+          make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                     pack_bf16x2(v[6], v[7]));
+    }
+    tcx::fence_proxy_async();
+    tcx::fence_before();
+    __syncthreads();
+    tcx::fence_after();
+    if (tid == 0) {
+      if (tcx::mbar_wait(bw(s), (c >> 1) & 1, CT_WAIT)) {
+        const uint32_t a_base = tcx::smem_u32(act), b_base = tcx::smem_u32(wst);
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+          const int ky = tap / 3, kx = tap % 3;
+          const uint64_t bdesc = tcx::smem_desc(b_base + tap * a.Npad * 32, a.Npad * 16, 128);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint64_t adesc =
+                tcx::smem_desc(a_base + (ky * CT_HP + 8 * h + kx) * 16, CT_PLANE, CT_HP * 16);
+            tcx::mma_f16(tmem + (uint32_t)(h * a.Npad), adesc, bdesc, idesc, (c > 0 || tap > 0) ? 1u : 0u);
+          }
+        }
+      } else {
+        *abort_flag = 1;
+        // the copy may still land: give it one more bounded wait
+        tcx::mbar_wait(bw(s), (c >> 1) & 1, CT_WAIT);
+      }
+      tcx::mma_commit(bm(s));
+    }
+    issued = c + 1;
+  }
+  // all MMAs done: the last commit covers every earlier one
+  if (issued > 0) {
+    const int last = issued - 1;
+    if (!tcx::mbar_wait(bm(last & 1), (last >> 1) & 1, CT_WAIT)) ok = false;
+  }
+  ok = __syncthreads_and(ok && !*abort_flag);
+  tcx::fence_after();
+  if (ok) {
+    // warp w reads TMEM lanes 32 (w % 4) .. +31 (pixels of its quarter) of
+    // half w / 4; pixel m = 32 (w % 4) + lane is row m / 8, column m % 8
+    const int q = warp & 3, h = warp >> 2;
+    const int m = 32 * q + lane;
+    const int y = y0 + (m >> 3), x = x0 + 8 * h + (m & 7);
+    const bool store = y < a.H && x < a.W;
+    float *outp = a.out + (int64_t)n * a.Cout * plane + (int64_t)y * a.W + x;
+    for (int c0 = 0; c0 < a.Npad; c0 += 16) {
+      uint32_t v[16];
+      tcx::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * a.Npad + c0), v);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int co = c0 + u;
+        if (store && co < a.Cout) {
+          float r = __uint_as_float(v[u]) + (a.bias ? a.bias[co] : 0.f);
+          if (a.relu) r = fmaxf(r, 0.f);
+          outp[(int64_t)co * plane] = r;
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(a.flag, 1);
+  }
+  tcx::fence_before();
+  __syncthreads();
+  if (warp == 0) tcx::tmem_dealloc(tmem, (uint32_t)cols);
+}
+
+// Pack one layer's weights for k_conv3x3_tc: element (chunk c, tap t, plane
+// cg, n, j) is B(n, k = 16 c + 8 cg + j) of tap t.  Forward: B = w[n][k][t];
+// flipped (input gradient of the layer): B = w[k][n][8 - t].  Values are
+// rounded to BF16; entries outside the channel counts are zero.
+__global__ void k_pack_w(const float *__restrict__ w, int CinL, int CoutL, int flip, uint16_t *__restrict__ out,
+                         int Npad, int nchunks) {
+  const int Cin = flip ? CoutL : CinL, Cout = flip ? CinL : CoutL;
+  const int64_t total = (int64_t)nchunks * 9 * 2 * Npad * 8;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx % 8);
+    const int nn = (int)((idx / 8) % Npad);
+    const int cg = (int)((idx / (8 * Npad)) % 2);
+    const int tap = (int)((idx / (16 * Npad)) % 9);
+    const int c = (int)(idx / (144 * (int64_t)Npad));
+    const int ci = c * 16 + cg * 8 + j;
+    float v = 0.f;
+    if (ci < Cin && nn < Cout) {
+      if (!flip) v = w[((int64_t)nn * CinL + ci) * 9 + tap];
+      else v = w[((int64_t)ci * CinL + nn) * 9 + (8 - tap)];
+    }
+    out[idx] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  }
+}
+
+}  // namespace
+
+int nn_tc_npad(int Cout) { return (Cout + 15) / 16 * 16; }
+int nn_tc_nchunks(int Cin) { return (Cin + 15) / 16; }
+int64_t nn_tc_packed_elems(int Cin, int Cout) { return (int64_t)nn_tc_nchunks(Cin) * 9 * 2 * nn_tc_npad(Cout) * 8; }
+
+cudaError_t nn_tc_setup() {
+  return cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * CT_ACT + 576 * 256 + 64);
+}
+
+void nn_pack_weights(const float *w, int CinL, int CoutL, bool flip, uint16_t *out, cudaStream_t st) {
+  const int Cin = flip ? CoutL : CinL, Cout = flip ? CinL : CoutL;
+  const int64_t total = nn_tc_packed_elems(Cin, Cout);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 8));
+  k_pack_w<<<grid, 256, 0, st>>>(w, CinL, CoutL, flip ? 1 : 0, out, nn_tc_npad(Cout), nn_tc_nchunks(Cin));
+  count_launch();
+}
+
+void nn_conv_tc(const float *in, int Cin, const uint16_t *wp, const float *bias, float *out, int Cout, int N, int H,
+                int W, bool relu, int *flag, cudaStream_t st) {
+  ConvTcArgs a;
+  a.in = in;
+  a.Cin = Cin;
+  a.wp = wp;
+  a.Npad = nn_tc_npad(Cout);
+  a.nchunks = nn_tc_nchunks(Cin);
+  a.bias = bias;
+  a.out = out;
+  a.Cout = Cout;
+  a.H = H;
+  a.W = W;
+  a.relu = relu ? 1 : 0;
+  a.flag = flag;
+  const int tiles = ((W + CT_T - 1) / CT_T) * ((H + CT_T - 1) / CT_T);
+  const size_t smem = 2 * CT_ACT + 2 * 288 * (size_t)a.Npad + 64;
+  k_conv3x3_tc<<<dim3(tiles, N), 256, smem, st>>>(a);
+  count_launch();
+}
+
+}  // namespace stdd

@@ -64,6 +64,8 @@ struct Layer {
   int64_t woff, boff;
 };
 
+bool g_tc_ready = false;
+
 }  // namespace
 
 struct stdd_nn {
@@ -71,7 +73,13 @@ struct stdd_nn {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int L = 0, c0 = 0, cmax = 0;
-  bool bf16 = true;
+  int mode = STDD_NN_TC;
+  bool bf16 = true;          // weights rounded to BF16 (modes 1 and 2)
+  // tensor-core mode: per layer, packed BF16 weights of the forward and of
+  // the input-gradient convolution
+  std::vector<int64_t> pk_fwd, pk_bwd;
+  uint16_t *packed = nullptr;
+  int *d_flag = nullptr;
   std::vector<int> ch;
   std::vector<Layer> layers;  // enc A/B per level, dec C/D per level (L-2..0), out
   int64_t nparams = 0;
@@ -100,8 +108,17 @@ struct stdd_nn {
   }
   size_t sz(int l, int c) const { return (size_t)aN * c * (aH >> l) * (aW >> l); }
 
-  void build(int levels, int base, int maxc, bool use_bf16, unsigned long long seed) {
+  ~stdd_nn() {
+    if (packed) cudaFree(packed);
+    if (d_flag) cudaFree(d_flag);
+  }
+
+  void build(int levels, int base, int maxc, int use_mode, unsigned long long seed) {
     if (levels < 1 || levels > 8 || base < 1 || maxc < base) throw std::invalid_argument("bad network shape");
+    if (use_mode < STDD_NN_FP32 || use_mode > STDD_NN_TC) throw std::invalid_argument("bad network mode");
+    if (use_mode == STDD_NN_TC && maxc > 256) throw std::invalid_argument("tensor-core mode allows at most 256 channels");
+    mode = use_mode;
+    const bool use_bf16 = mode != STDD_NN_FP32;
     L = levels;
     c0 = base;
     cmax = maxc;
@@ -142,9 +159,68 @@ struct stdd_nn {
     NCK(cudaMemcpyAsync(w.p, h.data(), nparams * sizeof(float), cudaMemcpyHostToDevice, stream));
     NCK(cudaMemsetAsync(m.p, 0, nparams * sizeof(float), stream));
     NCK(cudaMemsetAsync(v.p, 0, nparams * sizeof(float), stream));
+    if (cudaMalloc(&d_flag, sizeof(int)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      throw std::bad_alloc();
+    }
+    NCK(cudaMemsetAsync(d_flag, 0, sizeof(int), stream));
+    if (mode == STDD_NN_TC) {
+      if (!g_tc_ready) {
+        NCK(stdd::nn_tc_setup());
+        g_tc_ready = true;
+      }
+      int64_t off = 0;
+      for (const Layer &ly : layers) {
+        pk_fwd.push_back(off);
+        off += stdd::nn_tc_packed_elems(ly.cin, ly.cout);
+        pk_bwd.push_back(off);
+        off += stdd::nn_tc_packed_elems(ly.cout, ly.cin);
+      }
+      if (cudaMalloc(&packed, std::max<int64_t>(1, off) * sizeof(uint16_t)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        throw std::bad_alloc();
+      }
+    }
     stdd::nn_round(w.p, wb.p, nparams, bf16, stream);
+    repack();
     NCK(cudaStreamSynchronize(stream));
     step = 0;
+  }
+
+  // tensor-core operand copies of the current (BF16-rounded) weights
+  void repack() {
+    if (mode != STDD_NN_TC) return;
+    for (size_t i = 0; i < layers.size(); ++i) {
+      const Layer &ly = layers[i];
+      stdd::nn_pack_weights(wb.p + ly.woff, ly.cin, ly.cout, false, packed + pk_fwd[i], stream);
+      stdd::nn_pack_weights(wb.p + ly.woff, ly.cin, ly.cout, true, packed + pk_bwd[i], stream);
+    }
+  }
+
+  size_t layer_index(const Layer &ly) const { return (size_t)(&ly - layers.data()); }
+
+  // out = conv(in) with layer ly (forward) or its input gradient (flip)
+  void conv(const float *in, const Layer &ly, float *out, int N, int H, int W, bool relu, bool flip,
+            cudaStream_t st) {
+    const int cin = flip ? ly.cout : ly.cin, cout = flip ? ly.cin : ly.cout;
+    if (mode == STDD_NN_TC) {
+      const size_t i = layer_index(ly);
+      stdd::nn_conv_tc(in, cin, packed + (flip ? pk_bwd[i] : pk_fwd[i]), flip ? nullptr : wb.p + ly.boff, out, cout,
+                       N, H, W, relu, d_flag, st);
+    } else {
+      stdd::nn_conv(in, cin, wb.p + ly.woff, flip ? nullptr : wb.p + ly.boff, out, cout, N, H, W, relu, flip, st);
+    }
+  }
+
+  // throws if a tensor-core wait timed out since the last check (syncs st)
+  void check_flag(cudaStream_t st) {
+    int f = 0;
+    NCK(cudaMemcpyAsync(&f, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NCK(cudaStreamSynchronize(st));
+    if (f) {
+      NCK(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
+      throw NnError("tensor-core convolution timed out");
+    }
   }
 
   void check_shape(int N, int H, int W) const {
@@ -178,8 +254,6 @@ struct stdd_nn {
     act["gd"].alloc(big);
   }
 
-  const float *Wt(const Layer &ly) const { return wb.p + ly.woff; }
-  const float *Bs(const Layer &ly) const { return wb.p + ly.boff; }
 
   // forward pass; returns the output buffer (N x 2 x H x W)
   void forward(int N, int H, int W, const float *in, float *out, cudaStream_t st) {
@@ -194,21 +268,21 @@ struct stdd_nn {
         src = A("pool", l);
         cin = ch[l - 1];
       }
-      stdd::nn_conv(src, cin, Wt(encA(l)), Bs(encA(l)), A("encA", l), ch[l], N, h, wd, true, false, st);
-      stdd::nn_conv(A("encA", l), ch[l], Wt(encB(l)), Bs(encB(l)), A("skip", l), ch[l], N, h, wd, true, false, st);
+      conv(src, encA(l), A("encA", l), N, h, wd, true, false, st);
+      conv(A("encA", l), encB(l), A("skip", l), N, h, wd, true, false, st);
     }
     for (int l = L - 2; l >= 0; --l) {
       const int h = H >> l, wd = W >> l;
       const float *deeper = (l + 1 == L - 1) ? A("skip", L - 1) : A("d", l + 1);
       stdd::nn_up2(deeper, A("up", l), (int64_t)N * ch[l + 1], h, wd, st);
-      stdd::nn_conv(A("up", l), ch[l + 1], Wt(decC(l)), Bs(decC(l)), A("decC", l), ch[l], N, h, wd, true, false, st);
+      conv(A("up", l), decC(l), A("decC", l), N, h, wd, true, false, st);
       const size_t cnt = sz(l, ch[l]);
       NCK(cudaMemcpyAsync(A("sum", l), A("decC", l), cnt * sizeof(float), cudaMemcpyDeviceToDevice, st));
       stdd::nn_axpy(A("skip", l), A("sum", l), 1.f, (int64_t)cnt, st);
-      stdd::nn_conv(A("sum", l), ch[l], Wt(decD(l)), Bs(decD(l)), A("d", l), ch[l], N, h, wd, true, false, st);
+      conv(A("sum", l), decD(l), A("d", l), N, h, wd, true, false, st);
     }
     const float *last = L > 1 ? A("d", 0) : A("skip", 0);
-    stdd::nn_conv(last, ch[0], Wt(outL()), Bs(outL()), out, 2, N, H, W, false, false, st);
+    conv(last, outL(), out, N, H, W, false, false, st);
     NCK(cudaGetLastError());
   }
 
@@ -227,7 +301,7 @@ struct stdd_nn {
     // output layer
     const float *last = L > 1 ? A("d", 0) : A("skip", 0);
     stdd::nn_conv_wgrad(last, ch[0], gout, 2, N, H, W, g.p + outL().woff, g.p + outL().boff, st);
-    stdd::nn_conv(gout, 2, Wt(outL()), nullptr, gd, ch[0], N, H, W, false, true, st);  // grad of d_0
+    conv(gout, outL(), gd, N, H, W, false, true, st);  // grad of d_0
     for (int l = 0; l < L; ++l)
       NCK(cudaMemsetAsync(A("gskip", l), 0, sz(l, ch[l]) * sizeof(float), st));
     if (L == 1) {
@@ -239,11 +313,11 @@ struct stdd_nn {
       const size_t cnt = sz(l, ch[l]);
       stdd::nn_relu_mask(A("d", l), gd, (int64_t)cnt, st);
       stdd::nn_conv_wgrad(A("sum", l), ch[l], gd, ch[l], N, h, wd, g.p + decD(l).woff, g.p + decD(l).boff, st);
-      stdd::nn_conv(gd, ch[l], Wt(decD(l)), nullptr, t1, ch[l], N, h, wd, false, true, st);  // grad of sum
+      conv(gd, decD(l), t1, N, h, wd, false, true, st);  // grad of sum
       stdd::nn_axpy(t1, A("gskip", l), 1.f, (int64_t)cnt, st);
       stdd::nn_relu_mask(A("decC", l), t1, (int64_t)cnt, st);
       stdd::nn_conv_wgrad(A("up", l), ch[l + 1], t1, ch[l], N, h, wd, g.p + decC(l).woff, g.p + decC(l).boff, st);
-      stdd::nn_conv(t1, ch[l], Wt(decC(l)), nullptr, t2, ch[l + 1], N, h, wd, false, true, st);  // grad of up
+      conv(t1, decC(l), t2, N, h, wd, false, true, st);  // grad of up
       stdd::nn_up2_bwd(t2, gd, (int64_t)N * ch[l + 1], h, wd, st);  // grad of d_{l+1}
       if (l + 1 == L - 1)
         stdd::nn_axpy(gd, A("gskip", L - 1), 1.f, (int64_t)sz(L - 1, ch[L - 1]), st);
@@ -255,13 +329,13 @@ struct stdd_nn {
       float *gs = A("gskip", l);
       stdd::nn_relu_mask(A("skip", l), gs, (int64_t)cnt, st);
       stdd::nn_conv_wgrad(A("encA", l), ch[l], gs, ch[l], N, h, wd, g.p + encB(l).woff, g.p + encB(l).boff, st);
-      stdd::nn_conv(gs, ch[l], Wt(encB(l)), nullptr, t1, ch[l], N, h, wd, false, true, st);  // grad of encA
+      conv(gs, encB(l), t1, N, h, wd, false, true, st);  // grad of encA
       stdd::nn_relu_mask(A("encA", l), t1, (int64_t)cnt, st);
       const float *src = l > 0 ? A("pool", l) : in;
       const int cin = l > 0 ? ch[l - 1] : 3;
       stdd::nn_conv_wgrad(src, cin, t1, ch[l], N, h, wd, g.p + encA(l).woff, g.p + encA(l).boff, st);
       if (l > 0) {
-        stdd::nn_conv(t1, ch[l], Wt(encA(l)), nullptr, t2, cin, N, h, wd, false, true, st);  // grad of pool
+        conv(t1, encA(l), t2, N, h, wd, false, true, st);  // grad of pool
         stdd::nn_pool2_bwd(t2, t1, (int64_t)N * cin, H >> (l - 1), W >> (l - 1), st);
         stdd::nn_axpy(t1, A("gskip", l - 1), 1.f, (int64_t)sz(l - 1, ch[l - 1]), st);
       }
@@ -284,6 +358,7 @@ void nn_guess_field(stdd_nn *nn, const double *eps, const double2 *b, int nx, in
   nn_absmax(b, (int64_t)nx * ny, scratch, scale, st);
   nn_input(eps, b, scale, in, nx, ny, Wp, Hp, st);
   nn->forward(1, Hp, Wp, in, out, st);
+  nn->check_flag(st);
   nn_output(out, scale, unit, x0, nx, ny, Wp, Hp, st);
   NCK(cudaGetLastError());
 }
@@ -316,7 +391,7 @@ template <typename F> stdd_status nn_guard(stdd_nn *nn, F &&f) {
 extern "C" {
 
 stdd_status stdd_nn_create(stdd_nn **out, int device, void *cuda_stream, int levels, int base_channels,
-                           int max_channels, int bf16_weights, unsigned long long seed) {
+                           int max_channels, int mode, unsigned long long seed) {
   if (!out) return STDD_EINVAL;
   *out = nullptr;
   stdd_nn *nn = new (std::nothrow) stdd_nn();
@@ -337,7 +412,7 @@ stdd_status stdd_nn_create(stdd_nn **out, int device, void *cuda_stream, int lev
     }
     nn->own_stream = true;
   }
-  const stdd_status st = nn_guard(nn, [&] { nn->build(levels, base_channels, max_channels, bf16_weights != 0, seed); });
+  const stdd_status st = nn_guard(nn, [&] { nn->build(levels, base_channels, max_channels, mode, seed); });
   if (st != STDD_OK) {
     if (nn->own_stream) cudaStreamDestroy(nn->stream);
     delete nn;
@@ -370,6 +445,7 @@ stdd_status stdd_nn_set_params(stdd_nn *nn, const float *host) {
     if (!host) throw std::invalid_argument("null buffer");
     NCK(cudaMemcpyAsync(nn->w.p, host, nn->nparams * sizeof(float), cudaMemcpyHostToDevice, nn->stream));
     stdd::nn_round(nn->w.p, nn->wb.p, nn->nparams, nn->bf16, nn->stream);
+    nn->repack();
     NCK(cudaStreamSynchronize(nn->stream));
   });
 }
@@ -378,7 +454,7 @@ stdd_status stdd_nn_forward(stdd_nn *nn, int batch, int H, int W, const float *i
   return nn_guard(nn, [&] {
     if (!input || !output) throw std::invalid_argument("null buffer");
     nn->forward(batch, H, W, input, output, nn->stream);
-    NCK(cudaStreamSynchronize(nn->stream));
+    nn->check_flag(nn->stream);
   });
 }
 
@@ -391,7 +467,7 @@ stdd_status stdd_nn_gradient(stdd_nn *nn, int batch, int H, int W, const float *
     if (loss_out) NCK(cudaMemcpyAsync(loss_out, nn->loss.p, sizeof(float), cudaMemcpyDeviceToHost, nn->stream));
     if (grad_host)
       NCK(cudaMemcpyAsync(grad_host, nn->g.p, nn->nparams * sizeof(float), cudaMemcpyDeviceToHost, nn->stream));
-    NCK(cudaStreamSynchronize(nn->stream));
+    nn->check_flag(nn->stream);
   });
 }
 
@@ -403,8 +479,9 @@ stdd_status stdd_nn_train_step(stdd_nn *nn, int batch, int H, int W, const float
     nn->backward(batch, H, W, input, target);
     ++nn->step;
     stdd::nn_adam(nn->w.p, nn->wb.p, nn->g.p, nn->m.p, nn->v.p, nn->nparams, lr, nn->step, nn->bf16, nn->stream);
+    nn->repack();
     if (loss_out) NCK(cudaMemcpyAsync(loss_out, nn->loss.p, sizeof(float), cudaMemcpyDeviceToHost, nn->stream));
-    NCK(cudaStreamSynchronize(nn->stream));
+    nn->check_flag(nn->stream);
   });
 }
 

@@ -16,12 +16,13 @@ from . import binding as _b
 class Network:
     """Encoder-decoder guess network on one GPU (see stdd_nn_create)."""
 
-    def __init__(self, levels=6, base_channels=32, max_channels=256, bf16_weights=True, seed=0, device=0,
-                 stream=None):
+    MODES = {"fp32": _b.STDD_NN_FP32, "bf16": _b.STDD_NN_BF16, "tc": _b.STDD_NN_TC}
+
+    def __init__(self, levels=6, base_channels=32, max_channels=256, mode="tc", seed=0, device=0, stream=None):
         self.levels, self.base, self.cmax = int(levels), int(base_channels), int(max_channels)
-        self.bf16 = bool(bf16_weights)
+        self.mode = mode
         self.device = int(device)
-        self.h = _b.stdd_nn_create(device, stream, levels, base_channels, max_channels, bf16_weights, seed)
+        self.h = _b.stdd_nn_create(device, stream, levels, base_channels, max_channels, self.MODES[mode], seed)
 
     @property
     def multiple(self):
@@ -39,12 +40,12 @@ class Network:
 
     def save(self, path):
         np.savez(path, params=self.get_params(), levels=self.levels, base=self.base, cmax=self.cmax,
-                 bf16=self.bf16)
+                 mode=self.mode)
 
     @classmethod
     def load(cls, path, device=0, stream=None):
         z = np.load(path)
-        net = cls(int(z["levels"]), int(z["base"]), int(z["cmax"]), bool(z["bf16"]), device=device, stream=stream)
+        net = cls(int(z["levels"]), int(z["base"]), int(z["cmax"]), str(z["mode"]), device=device, stream=stream)
         net.set_params(z["params"])
         return net
 
@@ -173,6 +174,27 @@ def train(net, inputs, targets, epochs=10, batch=8, lr=1e-3, lr_final=None, seed
         if log:
             log(f"epoch {ep + 1}/{epochs}: loss {np.mean(losses[-max(1, S // batch):]):.4e}")
     return losses
+
+
+def field_error(net, workloads, fields, device=0):
+    """Relative L2 error of the network's field against solved fields, per
+    right-hand side, in the network's normalised units (image pixels outside
+    the grid are zero on both sides)."""
+    import torch
+    dev = torch.device("cuda", device)
+    errs = []
+    for w, x in zip(workloads, fields):
+        H, Wd = net.image_shape(w.nx, w.ny)
+        inp = torch.empty((1, 3, H, Wd), dtype=torch.float32, device=dev)
+        tgt = torch.empty((1, 2, H, Wd), dtype=torch.float32, device=dev)
+        out = torch.empty((1, 2, H, Wd), dtype=torch.float32, device=dev)
+        eps = torch.from_numpy(w.eps_node).to(dev)
+        b = torch.from_numpy(w.b).to(dev)
+        for q in range(w.nrhs):
+            net.images(w.dx * w.dy, eps, b[q], x[q], inp[0], tgt[0])
+            net.forward(inp, out)
+            errs.append(float(torch.linalg.vector_norm(out - tgt) / torch.linalg.vector_norm(tgt)))
+    return errs
 
 
 def compare(net, workloads, precision=_b.STDD_PREC_C64, rtol=1e-8, device=0):
