@@ -51,6 +51,8 @@ def parse():
                     help="metalens: 4096x1024, 16 strips (the benchmark); metalens-small: 1024x1024, 4 strips "
                          "(profiling captures); cylinder: 200x200, 2 strips")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per step (line sources)")
+    ap.add_argument("--order", default="additive", choices=["additive", "multiplicative"],
+                    help="preconditioner order: additive (Algorithm 1, the benchmark) or symmetric multiplicative")
     ap.add_argument("--maxit", type=int, default=2000, help="FGMRES iteration limit per right-hand side")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -240,8 +242,9 @@ def run_ours(args, rank, world, local_rank):
             "fp16": S.STDD_PREC_C64_FP16}[args.precision]
 
     def make_solver(p):
-        return S.Solver.from_workload(w, eps=eps_d, precision=p, device=local_rank,
-                                      stream=stream.cuda_stream)
+        sv = S.Solver.from_workload(w, eps=eps_d, precision=p, device=local_rank, stream=stream.cuda_stream)
+        S.stdd_set_option(sv.ctx, S.STDD_OPT_ORDER, 1 if args.order == "multiplicative" else 0)
+        return sv
 
     def step(sv):
         sv.factor()
@@ -398,7 +401,7 @@ def run_ours(args, rank, world, local_rank):
                   S.STDD_PREC_C64_BF16: "c64-factors(bf16 tensor-core updates)+c128-krylov",
                   S.STDD_PREC_C64_FP16: "c64-factors(fp16 tensor-core updates)+c128-krylov"}[prec],
         "data": "synthetic",
-        "config": {"workload": workload_desc(w), "precision": args.precision, "rtol": RTOL,
+        "config": {"workload": workload_desc(w), "precision": args.precision, "order": args.order, "rtol": RTOL,
                    "restart": RESTART, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (factors %.1f GB, Krylov basis %.1f GB)"
                          % (E * elem / 1e9, (2 * RESTART + 1) * w.n * 16 / 1e9)},

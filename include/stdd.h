@@ -253,8 +253,18 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *   STDD_OPT_AUTOTUNE (default 1): choose the substitution launch shapes per
  *                     tree level by timing them once per level shape.
  *   STDD_OPT_LEAF     (default 16): nested-dissection leaf size in nodes
- *                     (changes the factorization, invalidates factors). */
-enum { STDD_OPT_GRAPHS = 1, STDD_OPT_AUTOTUNE = 2, STDD_OPT_LEAF = 3 };
+ *                     (changes the factorization, invalidates factors).
+ * and one that changes the preconditioner (not the solution):
+ *   STDD_OPT_ORDER    (default 0): 0 = the additive order of Algorithm 1,
+ *                     M^-1 v = sum_i E_i A_i^-1 R_i^I v, all strips at once;
+ *                     1 = symmetric multiplicative order, strips one after
+ *                     another forward then backward (k = 0..n-1, n-2..0),
+ *                     each solving for the current residual:
+ *                     z += E_k A_k^-1 R_k^I (v - A z), starting from z = 0
+ *                     (the layer-by-layer transfer of the original source
+ *                     transfer method, Sec. 1).  In paper_richardson mode
+ *                     the stationary iteration uses the chosen order. */
+enum { STDD_OPT_GRAPHS = 1, STDD_OPT_AUTOTUNE = 2, STDD_OPT_LEAF = 3, STDD_OPT_ORDER = 4 };
 stdd_status stdd_set_option(stdd_ctx *ctx, int option, int value);
 stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);
 

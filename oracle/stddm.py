@@ -163,6 +163,20 @@ class DDM:
             out += self.extend(k, z)
         return out
 
+    def apply_Minv_multiplicative(self, v):
+        """The symmetric multiplicative order of the same local solves (the
+        layer-by-layer source transfer the method comes from, Sec. 1): strips
+        one after another, forward then backward (k = 0..n-1, n-2..0), each
+        solving for the residual left by the previous ones,
+        z <- z + E_k A_k^-1 R_k^I (v - A z), from z = 0."""
+        v = np.asarray(v, dtype=np.complex128)
+        z = np.zeros(self.prob.n, np.complex128)
+        order = list(range(self.nsub)) + list(range(self.nsub - 2, -1, -1))
+        for k in order:
+            r = v - self.prob.A @ z
+            z = z + self.extend(k, self.local_solve(k, self.restrict_owned(k, r)))
+        return z
+
     def transfer(self, p, i, e_i):
         """T_pi(e_i) = R_p^I A (E_i e_i) (Eq. 17 under the reading above), as
         a local vector of strip p."""

@@ -328,12 +328,21 @@ struct stdd_ctx {
   };
   std::map<std::vector<const void *>, GraphEntry> minv_graphs;
   bool use_graphs = true;
+  int order = 0;  // preconditioner order: 0 additive (Algorithm 1), 1 symmetric multiplicative
+  // per level, per strip: first front, first upward and downward work item
+  // (fronts and items of a level are grouped by strip), plus a host copy of
+  // the strip descriptors
+  std::vector<std::vector<int>> lvl_front, lvl_up, lvl_down;
+  std::vector<StripDev> strips_host;
   void clear_graphs() {
     for (auto &kv : minv_graphs) cudaGraphExecDestroy(kv.second.exec);
     minv_graphs.clear();
   }
   template <typename R> void factor_t();
   template <typename R> void solve_levels(int nrhs_);
+  template <typename R> void solve_strip_levels(int k, int nrhs_);
+  template <typename R> void enqueue_minv_multiplicative(const std::vector<const double2 *> &vs,
+                                                         const std::vector<double2 *> &zs);
   template <typename R> void autotune();
   void ensure_solve_buffers(int nr);
   // sweep launch configurations chosen by timing, keyed by the level shape
@@ -474,13 +483,18 @@ void stdd_ctx::build_structure() {
   for (int k = 0; k < nsub; ++k) inst[k].assign(shapes[strips[k].W()].fronts.size(), -1);
   std::vector<FrontDev> fr;
   levels.assign(depth, LevelInfo{0, 0, 0, 0, 0, 1 << 30, 0, 0, 0, 0, 32, 32, 1, 1});
+  lvl_front.assign(depth, {});
+  lvl_up.assign(depth, std::vector<int>(nsub + 1, 0));
+  lvl_down.assign(depth, std::vector<int>(nsub + 1, 0));
   int64_t ws_need[2] = {0, 0};
   ub_elems[0] = ub_elems[1] = 0;
   for (int L = 0; L < depth; ++L) {
     LevelInfo &li = levels[L];
     li.f0 = (int)fr.size();
     int64_t s_run = 0, u_run = 0;
+    lvl_front[L].assign(nsub + 1, 0);
     for (int k = 0; k < nsub; ++k) {
+      lvl_front[L][k] = (int)fr.size();
       const Shape &sh = shapes[strips[k].W()];
       for (size_t f = 0; f < sh.fronts.size(); ++f) {
         const auto &sf = sh.fronts[f];
@@ -509,6 +523,7 @@ void stdd_ctx::build_structure() {
       }
     }
     li.nf = (int)fr.size() - li.f0;
+    lvl_front[L][nsub] = (int)fr.size();
     ws_need[L & 1] = std::max(ws_need[L & 1], s_run);
     ub_elems[L & 1] = std::max(ub_elems[L & 1], u_run);
   }
@@ -565,18 +580,28 @@ void stdd_ctx::build_structure() {
     li.split_up = pow2_split(li.max_p, li.rows_up);
     li.split_down = pow2_split(li.max_n, li.rows_down);
     li.up_off = (int64_t)items.size();
-    for (int f = li.f0; f < li.f0 + li.nf; ++f)
-      for (int c = 0; c < std::max(1, (fr[f].b + li.rows_up - 1) / li.rows_up); ++c) items.push_back(make_int2(f, c));
+    for (int k = 0; k <= nsub; ++k) {
+      lvl_up[L][k] = (int)((int64_t)items.size() - li.up_off);
+      if (k == nsub) break;
+      for (int f = lvl_front[L][k]; f < lvl_front[L][k + 1]; ++f)
+        for (int c = 0; c < std::max(1, (fr[f].b + li.rows_up - 1) / li.rows_up); ++c)
+          items.push_back(make_int2(f, c));
+    }
     li.n_up = (int)((int64_t)items.size() - li.up_off);
     li.down_off = (int64_t)items.size();
-    for (int f = li.f0; f < li.f0 + li.nf; ++f)
-      for (int c = 0; c < (fr[f].p + li.rows_down - 1) / li.rows_down; ++c) items.push_back(make_int2(f, c));
+    for (int k = 0; k <= nsub; ++k) {
+      lvl_down[L][k] = (int)((int64_t)items.size() - li.down_off);
+      if (k == nsub) break;
+      for (int f = lvl_front[L][k]; f < lvl_front[L][k + 1]; ++f)
+        for (int c = 0; c < (fr[f].p + li.rows_down - 1) / li.rows_down; ++c) items.push_back(make_int2(f, c));
+    }
     li.n_down = (int)((int64_t)items.size() - li.down_off);
   }
   std::vector<int> colstrip(nx);
   for (int k = 0; k < nsub; ++k)
     for (int i = strips[k].c0; i < strips[k].c1; ++i) colstrip[i] = k;
 
+  strips_host = sdev;
   upload(d_strips, sdev, stream);
   upload(d_fronts, fr, stream);
   upload(d_nodes, nodes, stream);
@@ -698,6 +723,49 @@ template <typename R> void stdd_ctx::solve_levels(int nr) {
   CK(cudaGetLastError());
 }
 
+// Forward and back substitution of strip k alone: the level kernels of
+// solve_levels on the strip's subrange of fronts and work items.
+template <typename R> void stdd_ctx::solve_strip_levels(int k, int nr) {
+  const int2 *items = d_items.as<int2>();
+  for (int L = depth - 1; L >= 0; --L) {
+    LevelInfo li = levels[L];
+    li.f0 = lvl_front[L][k];
+    li.nf = lvl_front[L][k + 1] - lvl_front[L][k];
+    if (li.nf == 0) continue;
+    stdd::mf_up_gather_level<R>(mf_args(L & 1, true), li, nr, nloc, stream);
+    stdd::mf_up_level<R>(mf_args(L & 1, true), items + li.up_off + lvl_up[L][k], lvl_up[L][k + 1] - lvl_up[L][k],
+                         li.rows_up, li.split_up, nr, nloc, stream);
+  }
+  for (int L = 0; L < depth; ++L) {
+    const LevelInfo &li = levels[L];
+    const int cnt = lvl_down[L][k + 1] - lvl_down[L][k];
+    if (cnt == 0) continue;
+    stdd::mf_down_level<R>(mf_args(L & 1, true), items + li.down_off + lvl_down[L][k], cnt, li.rows_down,
+                           li.split_down, nr, nloc, stream);
+  }
+  CK(cudaGetLastError());
+}
+
+// Symmetric multiplicative order: z = 0, then for k = 0 .. n-1, n-2 .. 0:
+// z += E_k A_k^-1 R_k^I (v - A z), every slot i with its own (v_i, z_i).
+template <typename R>
+void stdd_ctx::enqueue_minv_multiplicative(const std::vector<const double2 *> &vs, const std::vector<double2 *> &zs) {
+  const int na = (int)vs.size();
+  const size_t E = elem();
+  const stdd::GridDev g = grid();
+  auto slot = [&](int i) { return static_cast<void *>(d_tloc.as<char>() + (size_t)i * nloc * E); };
+  for (int i = 0; i < na; ++i) CK(cudaMemsetAsync(zs[i], 0, (size_t)N() * sizeof(double2), stream));
+  std::vector<int> seq;
+  for (int k = 0; k < nsub; ++k) seq.push_back(k);
+  for (int k = nsub - 2; k >= 0; --k) seq.push_back(k);
+  for (int k : seq) {
+    for (int i = 0; i < na; ++i) stdd::launch_restrict_residual_strip<R>(g, strips_host[k], vs[i], zs[i], slot(i), stream);
+    solve_strip_levels<R>(k, na);
+    for (int i = 0; i < na; ++i) stdd::launch_add_strip<R>(strips_host[k], ny, slot(i), zs[i], stream);
+  }
+  CK(cudaGetLastError());
+}
+
 void stdd_ctx::ensure_solve_buffers(int nr) {
   if (nr <= solve_nrhs_cap) return;
   clear_graphs();
@@ -762,6 +830,11 @@ void stdd_ctx::apply_minv_multi(const std::vector<const double2 *> &vs, const st
 void stdd_ctx::enqueue_minv(const std::vector<const double2 *> &vs, const std::vector<double2 *> &zs) {
   const int na = (int)vs.size();
   const size_t E = elem();
+  if (order == 1) {
+    if (prec == STDD_PREC_FP64) enqueue_minv_multiplicative<double>(vs, zs);
+    else enqueue_minv_multiplicative<float>(vs, zs);
+    return;
+  }
   auto slot = [&](int i) { return static_cast<void *>(d_tloc.as<char>() + (size_t)i * nloc * E); };
   if (prec == STDD_PREC_FP64) {
     for (int i = 0; i < na; ++i)
@@ -1475,6 +1548,13 @@ stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
         break;
       case STDD_OPT_AUTOTUNE:
         c->autotune_on = value != 0;
+        break;
+      case STDD_OPT_ORDER:
+        if (value != 0 && value != 1) throw ArgError("order must be 0 (additive) or 1 (multiplicative)");
+        if (value != c->order) {
+          c->order = value;
+          c->clear_graphs();
+        }
         break;
       case STDD_OPT_LEAF:
         if (value < 1 || value > 4096) throw ArgError("leaf size out of range");

@@ -98,6 +98,12 @@ void launch_synthesize(const StripDev *strips_dev, int nsub, int nx, int ny, con
 template <typename R>
 void launch_strip_norms(const StripDev *strips_dev, int nsub, int ny, const void *tloc, double *out,
                         cudaStream_t st);
+// one strip (multiplicative order): its local source R_s^I (v - A z), and
+// z += E_s e_s (tloc is the base of all strips' local fields)
+template <typename R>
+void launch_restrict_residual_strip(const GridDev &g, const StripDev &s, const double2 *v, const double2 *z,
+                                    void *tloc, cudaStream_t st);
+template <typename R> void launch_add_strip(const StripDev &s, int ny, const void *tloc, double2 *z, cudaStream_t st);
 // local strip k only: tloc_k = t (converted), and back
 template <typename R> void launch_to_local(const double2 *t, void *tloc, int64_t n, cudaStream_t st);
 template <typename R> void launch_from_local(const void *tloc, double2 *z, int64_t n, cudaStream_t st);

@@ -83,6 +83,31 @@ __global__ void __launch_bounds__(TPB) k_synthesize(const StripDev *__restrict__
   }
 }
 
+// one strip s: t = R_s^I (v - A z) on its local box (zero off the owned
+// columns), the source of its local solve in the multiplicative order
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_restrict_residual_strip(GridDev g, StripDev s, const double2 *__restrict__ v,
+                                                                 const double2 *__restrict__ z, void *tloc) {
+  using C = typename CT<R>::T;
+  const int64_t nl = (int64_t)(s.x1 - s.x0) * g.ny;
+  const int64_t lo = (int64_t)(s.c0 - s.x0) * g.ny, hi = (int64_t)(s.c1 - s.x0) * g.ny;
+  const int64_t g0 = (int64_t)s.x0 * g.ny;
+  C *t = reinterpret_cast<C *>(tloc) + s.vec_off;
+  for (int64_t l = (int64_t)blockIdx.x * TPB + threadIdx.x; l < nl; l += (int64_t)gridDim.x * TPB)
+    t[l] = (l >= lo && l < hi) ? to_c(csub(v[g0 + l], apply_row(g, z, g0 + l)), C()) : czero<C>();
+}
+
+// z += E_s e_s: the strip's full local field added on its local box
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_add_strip(StripDev s, int ny, const void *tloc, double2 *__restrict__ z) {
+  using C = typename CT<R>::T;
+  const C *t = reinterpret_cast<const C *>(tloc) + s.vec_off;
+  const int64_t nl = (int64_t)(s.x1 - s.x0) * ny;
+  double2 *zs = z + (int64_t)s.x0 * ny;
+  for (int64_t l = (int64_t)blockIdx.x * TPB + threadIdx.x; l < nl; l += (int64_t)gridDim.x * TPB)
+    zs[l] = cadd(zs[l], to_d(t[l]));
+}
+
 template <typename R>
 __global__ void __launch_bounds__(TPB) k_to_local(const double2 *__restrict__ v, void *tloc, int64_t n) {
   using C = typename CT<R>::T;
@@ -181,6 +206,23 @@ template <typename R> void launch_from_local(const void *tloc, double2 *z, int64
   k_from_local<R><<<grid_for(n), TPB, 0, st>>>(tloc, z, n);
   count_launch();
 }
+
+template <typename R>
+void launch_restrict_residual_strip(const GridDev &g, const StripDev &s, const double2 *v, const double2 *z,
+                                    void *tloc, cudaStream_t st) {
+  k_restrict_residual_strip<R><<<grid_for((int64_t)(s.x1 - s.x0) * g.ny), TPB, 0, st>>>(g, s, v, z, tloc);
+  count_launch();
+}
+template <typename R> void launch_add_strip(const StripDev &s, int ny, const void *tloc, double2 *z, cudaStream_t st) {
+  k_add_strip<R><<<grid_for((int64_t)(s.x1 - s.x0) * ny), TPB, 0, st>>>(s, ny, tloc, z);
+  count_launch();
+}
+template void launch_restrict_residual_strip<double>(const GridDev &, const StripDev &, const double2 *,
+                                                     const double2 *, void *, cudaStream_t);
+template void launch_restrict_residual_strip<float>(const GridDev &, const StripDev &, const double2 *,
+                                                    const double2 *, void *, cudaStream_t);
+template void launch_add_strip<double>(const StripDev &, int, const void *, double2 *, cudaStream_t);
+template void launch_add_strip<float>(const StripDev &, int, const void *, double2 *, cudaStream_t);
 
 template void launch_restrict<double>(const StripDev *, int, int64_t, int, const int *, const double2 *, void *,
                                       cudaStream_t);

@@ -215,3 +215,107 @@ def compare(net, workloads, precision=_b.STDD_PREC_C64, rtol=1e-8, device=0):
                              guess_used=il["guess_used"][q], conv_zero=iz["converged"],
                              conv_learned=il["converged"], x_zero=xz[q], x_learned=xl[q]))
     return rows
+
+
+def experiment(n_train=4000, train_side=512, n_eval=256, eval_shape=(1024, 512), levels=6, base=32, cmax=256,
+               train_seconds=300.0, batch=8, lr=1e-3, lr_final=1e-4, rhs_per_geometry=8, train_seed=4,
+               eval_seed=5, precision=_b.STDD_PREC_C64, rtol=1e-8, device=0, log=print):
+    """Train a guess network on fields the FP64 DDM computes for seeded
+    ellipse geometries (n_train fields, rhs_per_geometry random point or line
+    sources per geometry, train_side^2 grids), then compare zero and learned
+    starts on n_eval held-out instances of eval_shape (one source each) at
+    the given precision and tolerance.  Geometry g of a set uses seed
+    set_seed * 1_000_000 + g.  Returns a summary dict."""
+    import torch
+    import workloads as W
+    t_all = time.perf_counter()
+    net = Network(levels, base, cmax, mode="tc", seed=train_seed, device=device)
+    n_geo = -(-n_train // rhs_per_geometry)
+    train_w = [W.ellipses(train_side, train_side, seed=train_seed * 1_000_000 + g, nrhs=rhs_per_geometry)
+               for g in range(n_geo)]
+    H, Wd = net.image_shape(train_side, train_side)
+    t0 = time.perf_counter()
+    inp, tgt, infos = make_dataset(net, train_w, H, Wd, precision=_b.STDD_PREC_FP64, rtol=rtol, device=device,
+                                   log=log)
+    t_data = time.perf_counter() - t0
+    inp, tgt = inp[:n_train], tgt[:n_train]
+    # epochs from the time budget, measured on the first steps
+    bi, bt = inp[:batch].contiguous(), tgt[:batch].contiguous()
+    net.train_step(bi, bt, 1e-7)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        net.train_step(bi, bt, 1e-7)
+    torch.cuda.synchronize()
+    t_step = (time.perf_counter() - t0) / 3
+    epochs = max(1, int(train_seconds / (t_step * (n_train // batch))))
+    t0 = time.perf_counter()
+    losses = train(net, inp, tgt, epochs=epochs, batch=batch, lr=lr, lr_final=lr_final, seed=train_seed, log=log)
+    t_train = time.perf_counter() - t0
+    del inp, tgt, bi, bt
+    torch.cuda.empty_cache()
+    nx, ny = eval_shape
+    eval_w = [W.ellipses(nx, ny, seed=eval_seed * 1_000_000 + g, nrhs=1) for g in range(n_eval)]
+    rows = compare(net, eval_w, precision=precision, rtol=rtol, device=device)
+    ref = [r["x_zero"][None] for r in rows]
+    ferr = field_error(net, eval_w, ref, device=device)
+    iz = np.array([r["its_zero"] for r in rows])
+    il = np.array([r["its_learned"] for r in rows])
+    tz = np.array([r["solve_s_zero"] for r in rows])
+    tl = np.array([r["solve_s_learned"] for r in rows])
+    used = np.array([r["guess_used"] for r in rows])
+    # forward time of the network at the evaluation size
+    Hh, Ww = net.image_shape(nx, ny)
+    xi = torch.zeros((1, 3, Hh, Ww), dtype=torch.float32, device=f"cuda:{device}")
+    xo = torch.empty((1, 2, Hh, Ww), dtype=torch.float32, device=f"cuda:{device}")
+    for _ in range(3):
+        net.forward(xi, xo)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(10):
+        net.forward(xi, xo)
+    torch.cuda.synchronize()
+    t_fwd = (time.perf_counter() - t0) / 10
+    summary = dict(
+        network=dict(levels=levels, base_channels=base, max_channels=cmax, params=net.num_params(), mode="tc"),
+        train=dict(fields=int(n_train), side=train_side, geometries=n_geo, epochs=epochs, batch=batch,
+                   step_ms=t_step * 1e3, data_s=t_data, train_s=t_train, loss_first=float(np.mean(losses[:50])),
+                   loss_last=float(np.mean(losses[-50:])), ddm_iterations_mean=float(
+                       np.mean([np.mean(i["iterations"]) for i in infos]))),
+        eval=dict(instances=len(rows), shape=list(eval_shape), precision=int(precision), rtol=rtol,
+                  field_error_median=float(np.median(ferr)), start_residual_median=float(
+                      np.median([r["guess_scaled"] for r in rows])), used_fraction=float(used.mean()),
+                  its_zero_mean=float(iz.mean()), its_learned_mean=float(il.mean()),
+                  minv_zero_mean=float(iz.mean()), minv_learned_mean=float(il.mean() + 1),
+                  solve_ms_zero_mean=float(tz.mean() * 1e3), solve_ms_learned_mean=float(tl.mean() * 1e3),
+                  forward_ms=t_fwd * 1e3, fewer_iterations_fraction=float((il + 1 < iz).mean()),
+                  all_converged=bool(all(r["conv_zero"] and r["conv_learned"] for r in rows))),
+        wall_s=time.perf_counter() - t_all)
+    net.close()
+    return summary
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    ap = argparse.ArgumentParser(description="train the guess network and compare it with the zero guess")
+    ap.add_argument("--train", type=int, default=4000)
+    ap.add_argument("--train-side", type=int, default=512)
+    ap.add_argument("--eval", type=int, default=256)
+    ap.add_argument("--eval-shape", default="1024x512")
+    ap.add_argument("--net", default="6,32,256", help="levels,base,max channels")
+    ap.add_argument("--train-seconds", type=float, default=300.0)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    L, c0, cm = (int(v) for v in a.net.split(","))
+    ex, ey = (int(v) for v in a.eval_shape.split("x"))
+    res = experiment(a.train, a.train_side, a.eval, (ex, ey), L, c0, cm, a.train_seconds,
+                     log=lambda m: print(m, file=sys.stderr, flush=True))
+    line = json.dumps(res)
+    print(line)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(line + "\n")

@@ -12,6 +12,11 @@
   a_n = d_n [k1 J_n'(k1 a) J_n(k0 a) - k0 J_n(k1 a) J_n'(k0 a)]
           / [k0 J_n(k1 a) H_n'(k0 a) - k1 J_n'(k1 a) H_n(k0 a)],
   from continuity of u and du/dr at r = a.
+* ``mie_plane_wave``: scattered field of the plane wave exp(i k0 x) on the
+  same cylinder: exp(i k0 x) = exp(i k0 cx) sum_n i^n J_n(k0 r) e^{i n phi}
+  (Jacobi-Anger about the centre), scattered coefficients exp(i k0 cx) i^n b_n
+  b_n = [m J_n'(m k0 a) J_n(k0 a) - J_n(m k0 a) J_n'(k0 a)]
+        / [J_n(m k0 a) H_n'(k0 a) - m J_n'(m k0 a) H_n(k0 a)],  m = sqrt(eps1).
 """
 import math
 
@@ -45,3 +50,17 @@ def mie_point_source(x, y, cx, cy, a, eps1, xs, ys, k0):
         an = dn * (k1 * j1p * j0 - k0 * j1 * j0p) / (k0 * j1 * h0p - k1 * j1p * h0)
         u = u + an * ss.hankel1(n, k0 * r) * np.exp(1j * n * ph)
     return u
+
+
+def mie_plane_wave(x, y, cx, cy, a, eps1, k0):
+    m = math.sqrt(eps1)
+    r = np.hypot(x - cx, y - cy)
+    ph = np.arctan2(y - cy, x - cx)
+    x0, x1 = k0 * a, m * k0 * a
+    nmax = int(x1) + 20
+    u = np.zeros(np.shape(r), complex)
+    for n in range(-nmax, nmax + 1):
+        bn = (m * ss.jvp(n, x1) * ss.jv(n, x0) - ss.jv(n, x1) * ss.jvp(n, x0)) / (
+            ss.jv(n, x1) * ss.h1vp(n, x0) - m * ss.jvp(n, x1) * ss.hankel1(n, x0))
+        u = u + (1j ** n) * bn * ss.hankel1(n, k0 * r) * np.exp(1j * n * ph)
+    return u * np.exp(1j * k0 * cx)

@@ -15,7 +15,7 @@ import pytest
 import workloads as W
 from oracle import fdfd
 from oracle.fdfd import Problem, sigma_hat_max, stretch_profile
-from tests.analytic import discrete_line_source_1d, hankel_green, mie_point_source
+from tests.analytic import discrete_line_source_1d, hankel_green, mie_plane_wave, mie_point_source
 
 K0 = 2 * math.pi
 
@@ -119,6 +119,37 @@ def test_mie_series_dielectric_cylinder():
     assert e20 < 0.12          # measured 0.096
     assert e40 < 0.03          # measured 0.023
     assert e20 / e40 > 3.5     # second order: subcell averaging works
+
+
+def _scattering_error(ppw, radius=0.5):
+    n = 6 * ppw
+    w = W.cylinder_scattering(n=n, ppw=ppw, radius=radius, npml=20, nsub=2)
+    P = Problem.from_workload(w)
+    u = P.solve(w.b[0].ravel()).reshape(n, n)
+    h = w.dx
+    cx, cy = w.meta["center"]
+    a = w.meta["radius"]
+    I, J = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    X, Y = I * h, J * h
+    r = np.hypot(X - cx, Y - cy)
+    m = (r >= a + 0.25) & (r <= a + 1.5)
+    ex = mie_plane_wave(X[m], Y[m], cx, cy, a, 4.0, K0)
+    return np.linalg.norm(u[m] - ex) / np.linalg.norm(ex)
+
+
+def test_plane_wave_scattering_matches_mie():
+    # the paper's first example (Eq. 7 scattered-field source, eps 4 cylinder)
+    # at r = lambda / 2 on a 6 x 6 lambda grid, and its 2x refinement
+    e20, e40 = _scattering_error(20), _scattering_error(40)
+    assert e20 < 0.2 and e40 < 0.05, (e20, e40)     # measured 0.168, 0.040
+    assert e20 / e40 > 3.5, (e20, e40)              # second order
+
+
+def test_plane_wave_source_is_zero_in_air():
+    w = W.cylinder_scattering(n=120, ppw=20, radius=1.0, npml=20, nsub=2)
+    air = np.isclose(w.eps_node, 1.0)
+    assert air.any() and not np.abs(w.b[0][air]).any()
+    assert np.abs(w.b[0][~air]).min() > 0
 
 
 def _reciprocity_pair(problem_cls=Problem):

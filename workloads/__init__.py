@@ -164,6 +164,39 @@ def cylinder(nx=200, ny=200, ppw=20, eps_cyl=4.0, radius=0.5, src_gap=1.0,
                               eps_cyl=eps_cyl, src=(si, sj)))
 
 
+def plane_wave_source(eps_node, dx, dy, wavelength, angle=0.0):
+    """Scattered-field source of a plane wave in air (Eq. 7):
+    b = -k0^2 (eps - 1) E_inc at every node, E_inc = exp(i k0 (x cos a +
+    y sin a)) with node (i, j) at (i dx, j dy).  Zero wherever eps = 1, so the
+    scatterer must stay out of the PML."""
+    k0 = 2 * math.pi / wavelength
+    nx, ny = eps_node.shape
+    x = np.arange(nx)[:, None] * dx
+    y = np.arange(ny)[None, :] * dy
+    einc = np.exp(1j * k0 * (x * math.cos(angle) + y * math.sin(angle)))
+    return -(k0 ** 2) * (eps_node - 1.0) * einc
+
+
+def cylinder_scattering(n=6000, ppw=40, radius=9.0, eps_cyl=4.0, npml=20, nsub=64, overlap=8,
+                        interface_pml=20, wavelength=1.0, restart=30, rtol=1e-8):
+    """The paper's first example: plane-wave (along +x) scattering by a
+    dielectric cylinder of radius ``radius`` wavelengths, eps 4, at the centre
+    of an n x n grid at lambda/ppw, solved for the scattered field (Eq. 7).
+    The default 6000 x 6000 grid at 40 points per wavelength is the paper's
+    ~36 million unknowns; PML 20 cells, overlap 8, interface PML 20 cells."""
+    d = wavelength / ppw
+    cx = cy = (n - 1) * d / 2.0
+    if radius * wavelength > cx - (npml + 1) * d:
+        raise ValueError("cylinder reaches the PML")
+    cells = cell_permittivity(n, n, d, d, 1.0, [(_circle(cx, cy, radius * wavelength), eps_cyl)])
+    eps = node_permittivity(cells)
+    b = plane_wave_source(eps, d, d, wavelength)[None]
+    return Workload("cylinder-scattering", n, n, d, d, wavelength, eps, b,
+                    npml=(npml,) * 4, nsub=nsub, overlap=overlap, interface_pml=interface_pml,
+                    restart=restart, rtol=rtol,
+                    meta=dict(center=(cx, cy), radius=radius * wavelength, eps_cyl=eps_cyl))
+
+
 def metalens(nx=4096, ny=1024, ppw=24, seed=1, npml=30, nsub=16, overlap=12,
              interface_pml=30, wavelength=1.0, nrhs=1):
     """Metalens-like strip: substrate eps 2.085 over the lower 20 % of the
