@@ -35,6 +35,27 @@ METRIC = "solve time to 1e-8 residual & MDoF/s: mixed/learned vs plain FP64, one
 RTOL = 1e-8
 RESTART = 50
 FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor and tensor), NVIDIA's figure
+
+# DRAM bytes (read + write) per algorithmic unit of a kernel, from one ncu
+# capture of all its launches in one factorization of the benchmark workload
+# (summary in the named profile); used only while the kernel's source file
+# still has the recorded SHA-256, else the roofline's traffic is null.
+NCU_TRAFFIC = {}
+
+
+def ncu_traffic(kernel, units_per_launch):
+    import hashlib
+    rec = NCU_TRAFFIC.get(kernel)
+    if not rec:
+        return None
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), rec["source"])
+    try:
+        with open(path, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
+                return None
+    except OSError:
+        return None
+    return rec["bytes_per_unit"] * units_per_launch
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 
 
@@ -51,8 +72,9 @@ def parse():
                     help="metalens: 4096x1024, 16 strips (the benchmark); metalens-small: 1024x1024, 4 strips "
                          "(profiling captures); cylinder: 200x200, 2 strips")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per step (line sources)")
-    ap.add_argument("--order", default="additive", choices=["additive", "multiplicative"],
-                    help="preconditioner order: additive (Algorithm 1, the benchmark) or symmetric multiplicative")
+    ap.add_argument("--order", default="additive", choices=["additive", "multiplicative", "red-black"],
+                    help="preconditioner order: additive (Algorithm 1, the benchmark), symmetric multiplicative, "
+                         "or red-black")
     ap.add_argument("--maxit", type=int, default=2000, help="FGMRES iteration limit per right-hand side")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -241,20 +263,22 @@ def run_ours(args, rank, world, local_rank):
     prec = {"fp64": S.STDD_PREC_FP64, "c64": S.STDD_PREC_C64, "bf16": S.STDD_PREC_C64_BF16,
             "fp16": S.STDD_PREC_C64_FP16}[args.precision]
 
-    def make_solver(p):
+    orders = {"additive": 0, "multiplicative": 1, "red-black": 2}
+
+    def make_solver(p, order=None):
         sv = S.Solver.from_workload(w, eps=eps_d, precision=p, device=local_rank, stream=stream.cuda_stream)
-        S.stdd_set_option(sv.ctx, S.STDD_OPT_ORDER, 1 if args.order == "multiplicative" else 0)
+        S.stdd_set_option(sv.ctx, S.STDD_OPT_ORDER, orders[order or args.order])
         return sv
 
     def step(sv):
         sv.factor()
         return sv.solve(x_d, restart=RESTART, rtol=RTOL, maxit=args.maxit, allow_noconv=True) == B.STDD_OK
 
-    def timed(p, warm, steps, profile):
-        """warm-up, then `steps` timed steps with phase spans (level 1: the
-        M^-1 graphs stay on); then one more step with per-launch kernel
-        spans (level 2) for the kernel rooflines."""
-        sv = make_solver(p)
+    def timed(p, warm, steps, profile, order=None):
+        """warm-up, then `steps` timed steps, with phase spans if profile >= 1
+        (the M^-1 graphs stay on); with profile = 2 one more step with
+        per-launch kernel spans (level 2) for the kernel rooflines."""
+        sv = make_solver(p, order)
         sv.set_sources(b_d)
         for _ in range(warm):
             step(sv)
@@ -262,6 +286,7 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         B.stdd_get_profile(sv.ctx, reset=True)
         B.stdd_set_profiling(sv.ctx, 1 if profile else 0)
+        kernel_step = profile == 2
         l0 = B.stdd_get_profile(sv.ctx, reset=True)["launches"]
         clocks = ClockSampler(local_rank)
         clocks.start()
@@ -279,7 +304,7 @@ def run_ours(args, rank, world, local_rank):
         st = sv.stats()
         hist = sv.history(0)
         kprof = None
-        if profile:
+        if kernel_step:
             B.stdd_set_profiling(sv.ctx, 2)
             k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             k0.record(stream)
@@ -291,7 +316,7 @@ def run_ours(args, rank, world, local_rank):
             B.stdd_set_profiling(sv.ctx, 0)
         return sv, ms, prof, launches, st, hist, ck, kprof
 
-    sv, ms, prof, launches, st, hist, ck, kprof = timed(prec, args.warmup, args.steps, True)
+    sv, ms, prof, launches, st, hist, ck, kprof = timed(prec, args.warmup, args.steps, 2)
     its = len(hist) - 1
     x_main = x_d.clone()
     r_rel = B.stdd_residual(sv.ctx, x_d[0].reshape(-1).contiguous(), b_d[0].reshape(-1).contiguous(),
@@ -384,7 +409,8 @@ def run_ours(args, rank, world, local_rank):
     roof["units_per_launch"] = d["units_per_launch"]
     roof["measured_over"] = ("one extra step after the timed region with a CUDA-event span around every launch "
                              "(graphs bypassed); profiled step %.1f ms" % kprof["step_ms"])
-    roof["traffic"] = None
+    roof["traffic"] = ncu_traffic(dom, d["units_per_launch"])
+    roof["traffic_source"] = NCU_TRAFFIC.get(dom, {}).get("profile") if roof["traffic"] is not None else None
 
     out = {
         "metric": METRIC,
@@ -423,7 +449,7 @@ def run_ours(args, rank, world, local_rank):
 
     if not args.no_compare:
         other = S.STDD_PREC_C64 if prec == S.STDD_PREC_FP64 else S.STDD_PREC_FP64
-        sv2, ms2, prof2, _, st2, hist2, _, _ = timed(other, 1, 1, True)
+        sv2, ms2, prof2, _, st2, hist2, _, _ = timed(other, 1, 1, 1)
         diff = float(torch.linalg.vector_norm(x_d - x_main) / torch.linalg.vector_norm(x_main))
         out["compare"] = {"precision": "c64" if other == S.STDD_PREC_C64 else "fp64",
                           "ms_per_step": ms2, "value": N / (ms2 * 1e-3) / 1e6,
@@ -431,6 +457,19 @@ def run_ours(args, rank, world, local_rank):
                           "t_factor_ms": prof2["factor_ms"], "t_solve_ms": prof2["solve_ms"],
                           "rel_diff_vs_main": diff}
         sv2.close()
+        # the other strip orders of the same method (same precision as the
+        # main line): symmetric multiplicative and red-black, one step each
+        out["orders"] = {}
+        for name in orders:
+            if name == args.order:
+                continue
+            sv3, ms3, prof3, _, st3, hist3, _, _ = timed(prec, 1, 1, 1, order=name)
+            diff = float(torch.linalg.vector_norm(x_d - x_main) / torch.linalg.vector_norm(x_main))
+            out["orders"][name] = {"ms_per_step": ms3, "value": N / (ms3 * 1e-3) / 1e6,
+                                   "iterations": len(hist3) - 1, "final_residual": st3["final_residual"],
+                                   "t_factor_ms": prof3["factor_ms"], "t_solve_ms": prof3["solve_ms"],
+                                   "rel_diff_vs_main": diff}
+            sv3.close()
 
     if not args.no_e2e:
         # through the public API with host buffers: permittivity and sources

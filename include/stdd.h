@@ -262,8 +262,15 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     each solving for the current residual:
  *                     z += E_k A_k^-1 R_k^I (v - A z), starting from z = 0
  *                     (the layer-by-layer transfer of the original source
- *                     transfer method, Sec. 1).  In paper_richardson mode
- *                     the stationary iteration uses the chosen order. */
+ *                     transfer method, Sec. 1); 2 = red-black: the even
+ *                     strips all at once, then the odd strips, each group
+ *                     solving for the residual left by the previous one
+ *                     (the same as solving them one by one, since a strip's
+ *                     local box never reaches the owned columns of the next
+ *                     strip of its colour: needs every interior strip wider
+ *                     than overlap + interface PML + 1, else STDD_EINVAL
+ *                     when it is applied).  In paper_richardson mode the
+ *                     stationary iteration uses the chosen order. */
 enum { STDD_OPT_GRAPHS = 1, STDD_OPT_AUTOTUNE = 2, STDD_OPT_LEAF = 3, STDD_OPT_ORDER = 4 };
 stdd_status stdd_set_option(stdd_ctx *ctx, int option, int value);
 stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);

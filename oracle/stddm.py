@@ -163,15 +163,19 @@ class DDM:
             out += self.extend(k, z)
         return out
 
-    def apply_Minv_multiplicative(self, v):
-        """The symmetric multiplicative order of the same local solves (the
-        layer-by-layer source transfer the method comes from, Sec. 1): strips
-        one after another, forward then backward (k = 0..n-1, n-2..0), each
-        solving for the residual left by the previous ones,
-        z <- z + E_k A_k^-1 R_k^I (v - A z), from z = 0."""
+    def apply_Minv_multiplicative(self, v, order=None):
+        """A multiplicative order of the same local solves (the layer-by-layer
+        source transfer the method comes from, Sec. 1): strips one after
+        another, each solving for the residual left by the previous ones,
+        z <- z + E_k A_k^-1 R_k^I (v - A z), from z = 0.  Default order: the
+        symmetric sweep k = 0..n-1, n-2..0; "red-black": the even strips, then
+        the odd strips."""
         v = np.asarray(v, dtype=np.complex128)
         z = np.zeros(self.prob.n, np.complex128)
-        order = list(range(self.nsub)) + list(range(self.nsub - 2, -1, -1))
+        if order is None:
+            order = list(range(self.nsub)) + list(range(self.nsub - 2, -1, -1))
+        elif order == "red-black":
+            order = list(range(0, self.nsub, 2)) + list(range(1, self.nsub, 2))
         for k in order:
             r = v - self.prob.A @ z
             z = z + self.extend(k, self.local_solve(k, self.restrict_owned(k, r)))

@@ -328,10 +328,14 @@ struct stdd_ctx {
   };
   std::map<std::vector<const void *>, GraphEntry> minv_graphs;
   bool use_graphs = true;
-  int order = 0;  // preconditioner order: 0 additive (Algorithm 1), 1 symmetric multiplicative
-  // per level, per strip: first front, first upward and downward work item
-  // (fronts and items of a level are grouped by strip), plus a host copy of
-  // the strip descriptors
+  // preconditioner order: 0 additive (Algorithm 1), 1 symmetric
+  // multiplicative, 2 red-black (even strips together, then odd strips)
+  int order = 0;
+  // Within a level, fronts and work items are grouped by strip, strips in
+  // the order perm (even strips first, then odd), so every single strip and
+  // both colour groups are contiguous ranges.  pos[k] = position of strip k;
+  // per level and position: first front, first upward / downward item.
+  std::vector<int> perm, pos;
   std::vector<std::vector<int>> lvl_front, lvl_up, lvl_down;
   std::vector<StripDev> strips_host;
   void clear_graphs() {
@@ -340,9 +344,10 @@ struct stdd_ctx {
   }
   template <typename R> void factor_t();
   template <typename R> void solve_levels(int nrhs_);
-  template <typename R> void solve_strip_levels(int k, int nrhs_);
+  template <typename R> void solve_range_levels(int j0, int j1, int nrhs_);
   template <typename R> void enqueue_minv_multiplicative(const std::vector<const double2 *> &vs,
                                                          const std::vector<double2 *> &zs);
+  void check_red_black() const;
   template <typename R> void autotune();
   void ensure_solve_buffers(int nr);
   // sweep launch configurations chosen by timing, keyed by the level shape
@@ -483,6 +488,11 @@ void stdd_ctx::build_structure() {
   for (int k = 0; k < nsub; ++k) inst[k].assign(shapes[strips[k].W()].fronts.size(), -1);
   std::vector<FrontDev> fr;
   levels.assign(depth, LevelInfo{0, 0, 0, 0, 0, 1 << 30, 0, 0, 0, 0, 32, 32, 1, 1});
+  perm.clear();
+  for (int k = 0; k < nsub; k += 2) perm.push_back(k);
+  for (int k = 1; k < nsub; k += 2) perm.push_back(k);
+  pos.assign(nsub, 0);
+  for (int j = 0; j < nsub; ++j) pos[perm[j]] = j;
   lvl_front.assign(depth, {});
   lvl_up.assign(depth, std::vector<int>(nsub + 1, 0));
   lvl_down.assign(depth, std::vector<int>(nsub + 1, 0));
@@ -493,8 +503,9 @@ void stdd_ctx::build_structure() {
     li.f0 = (int)fr.size();
     int64_t s_run = 0, u_run = 0;
     lvl_front[L].assign(nsub + 1, 0);
-    for (int k = 0; k < nsub; ++k) {
-      lvl_front[L][k] = (int)fr.size();
+    for (int j = 0; j < nsub; ++j) {
+      const int k = perm[j];
+      lvl_front[L][j] = (int)fr.size();
       const Shape &sh = shapes[strips[k].W()];
       for (size_t f = 0; f < sh.fronts.size(); ++f) {
         const auto &sf = sh.fronts[f];
@@ -723,31 +734,46 @@ template <typename R> void stdd_ctx::solve_levels(int nr) {
   CK(cudaGetLastError());
 }
 
-// Forward and back substitution of strip k alone: the level kernels of
-// solve_levels on the strip's subrange of fronts and work items.
-template <typename R> void stdd_ctx::solve_strip_levels(int k, int nr) {
+// Forward and back substitution of the strips at positions [j0, j1) of
+// perm alone: the level kernels of solve_levels on their subrange of fronts
+// and work items.
+template <typename R> void stdd_ctx::solve_range_levels(int j0, int j1, int nr) {
   const int2 *items = d_items.as<int2>();
   for (int L = depth - 1; L >= 0; --L) {
     LevelInfo li = levels[L];
-    li.f0 = lvl_front[L][k];
-    li.nf = lvl_front[L][k + 1] - lvl_front[L][k];
+    li.f0 = lvl_front[L][j0];
+    li.nf = lvl_front[L][j1] - lvl_front[L][j0];
     if (li.nf == 0) continue;
     stdd::mf_up_gather_level<R>(mf_args(L & 1, true), li, nr, nloc, stream);
-    stdd::mf_up_level<R>(mf_args(L & 1, true), items + li.up_off + lvl_up[L][k], lvl_up[L][k + 1] - lvl_up[L][k],
+    stdd::mf_up_level<R>(mf_args(L & 1, true), items + li.up_off + lvl_up[L][j0], lvl_up[L][j1] - lvl_up[L][j0],
                          li.rows_up, li.split_up, nr, nloc, stream);
   }
   for (int L = 0; L < depth; ++L) {
     const LevelInfo &li = levels[L];
-    const int cnt = lvl_down[L][k + 1] - lvl_down[L][k];
+    const int cnt = lvl_down[L][j1] - lvl_down[L][j0];
     if (cnt == 0) continue;
-    stdd::mf_down_level<R>(mf_args(L & 1, true), items + li.down_off + lvl_down[L][k], cnt, li.rows_down,
+    stdd::mf_down_level<R>(mf_args(L & 1, true), items + li.down_off + lvl_down[L][j0], cnt, li.rows_down,
                            li.split_down, nr, nloc, stream);
   }
   CK(cudaGetLastError());
 }
 
-// Symmetric multiplicative order: z = 0, then for k = 0 .. n-1, n-2 .. 0:
-// z += E_k A_k^-1 R_k^I (v - A z), every slot i with its own (v_i, z_i).
+// Strips of one colour may be solved together only if none of them changes
+// the residual another one reads: the local box of strip k (with its stencil
+// reach of one column) must stay clear of the owned columns of strip k + 2.
+void stdd_ctx::check_red_black() const {
+  for (int k = 0; k + 2 < nsub; ++k)
+    if (strips[k].x1 + 1 > strips[k + 2].c0 || strips[k + 2].x0 - 1 < strips[k].c1)
+      throw ArgError("red-black order needs every interior strip wider than overlap + interface PML + 1");
+}
+
+// Multiplicative orders: z = 0, then group by group (a group = positions
+// [j0, j1) of perm): every strip k of the group solves for the current
+// residual, z += E_k A_k^-1 R_k^I (v - A z), all of them from the same z.
+// Order 1: single strips k = 0 .. n-1, n-2 .. 0 (symmetric sweep); order 2:
+// the even strips, then the odd strips (red-black; the same as solving them
+// one by one because same-colour strips do not interact, check_red_black).
+// Every slot i has its own (v_i, z_i).
 template <typename R>
 void stdd_ctx::enqueue_minv_multiplicative(const std::vector<const double2 *> &vs, const std::vector<double2 *> &zs) {
   const int na = (int)vs.size();
@@ -755,13 +781,22 @@ void stdd_ctx::enqueue_minv_multiplicative(const std::vector<const double2 *> &v
   const stdd::GridDev g = grid();
   auto slot = [&](int i) { return static_cast<void *>(d_tloc.as<char>() + (size_t)i * nloc * E); };
   for (int i = 0; i < na; ++i) CK(cudaMemsetAsync(zs[i], 0, (size_t)N() * sizeof(double2), stream));
-  std::vector<int> seq;
-  for (int k = 0; k < nsub; ++k) seq.push_back(k);
-  for (int k = nsub - 2; k >= 0; --k) seq.push_back(k);
-  for (int k : seq) {
-    for (int i = 0; i < na; ++i) stdd::launch_restrict_residual_strip<R>(g, strips_host[k], vs[i], zs[i], slot(i), stream);
-    solve_strip_levels<R>(k, na);
-    for (int i = 0; i < na; ++i) stdd::launch_add_strip<R>(strips_host[k], ny, slot(i), zs[i], stream);
+  std::vector<std::pair<int, int>> groups;
+  if (order == 2) {
+    const int ne = (nsub + 1) / 2;
+    groups.push_back({0, ne});
+    if (nsub > 1) groups.push_back({ne, nsub});
+  } else {
+    for (int k = 0; k < nsub; ++k) groups.push_back({pos[k], pos[k] + 1});
+    for (int k = nsub - 2; k >= 0; --k) groups.push_back({pos[k], pos[k] + 1});
+  }
+  for (const auto &gr : groups) {
+    for (int j = gr.first; j < gr.second; ++j)
+      for (int i = 0; i < na; ++i)
+        stdd::launch_restrict_residual_strip<R>(g, strips_host[perm[j]], vs[i], zs[i], slot(i), stream);
+    solve_range_levels<R>(gr.first, gr.second, na);
+    for (int j = gr.first; j < gr.second; ++j)
+      for (int i = 0; i < na; ++i) stdd::launch_add_strip<R>(strips_host[perm[j]], ny, slot(i), zs[i], stream);
   }
   CK(cudaGetLastError());
 }
@@ -830,7 +865,8 @@ void stdd_ctx::apply_minv_multi(const std::vector<const double2 *> &vs, const st
 void stdd_ctx::enqueue_minv(const std::vector<const double2 *> &vs, const std::vector<double2 *> &zs) {
   const int na = (int)vs.size();
   const size_t E = elem();
-  if (order == 1) {
+  if (order != 0) {
+    if (order == 2) check_red_black();
     if (prec == STDD_PREC_FP64) enqueue_minv_multiplicative<double>(vs, zs);
     else enqueue_minv_multiplicative<float>(vs, zs);
     return;
@@ -1550,7 +1586,8 @@ stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
         c->autotune_on = value != 0;
         break;
       case STDD_OPT_ORDER:
-        if (value != 0 && value != 1) throw ArgError("order must be 0 (additive) or 1 (multiplicative)");
+        if (value < 0 || value > 2)
+          throw ArgError("order must be 0 (additive), 1 (symmetric multiplicative) or 2 (red-black)");
         if (value != c->order) {
           c->order = value;
           c->clear_graphs();

@@ -29,6 +29,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tc_ptx.cuh"
 
 namespace stdd {
 
@@ -42,57 +43,21 @@ constexpr int TC_OPBYTES = 128 * TC_KR * 2;  // one operand: 128 rows x 64 halve
 constexpr uint32_t TC_TMEM_COLS = 128;
 constexpr long long TC_WAIT_LIMIT = 1ll << 20;
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
+using tcx::mbar_try_wait;
+using tcx::mma_f16;
+using tcx::smem_u32;
+using tcx::tmem_ld32;
 
 // byte offset of element (row, k) in an operand tile (K-major, no swizzle)
 __device__ __forceinline__ uint32_t op_off(int row, int k) {
   return (uint32_t)((row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  const uint64_t lbo = 128, sbo = 1024;
-  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | (1ull << 46);
-}
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) { return tcx::smem_desc(addr, 128, 1024); }
 
 // kind::f16 instruction descriptor: D = F32, A = B = fmt (0 F16, 1 BF16),
 // both K-major, M = 128, N = TC_N
-__device__ __forceinline__ uint32_t instr_desc(int fmt) {
-  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(TC_N >> 3) << 17) |
-         ((uint32_t)(128 >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(addr), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-}
+__device__ __forceinline__ uint32_t instr_desc(int fmt) { return tcx::instr_desc_f16(fmt, 128, TC_N); }
 
 template <int FMT> __device__ __forceinline__ uint16_t to_half_bits(float x) {
   if (FMT == 1) return __bfloat16_as_ushort(__float2bfloat16_rn(x));

@@ -197,23 +197,46 @@ def field_error(net, workloads, fields, device=0):
     return errs
 
 
-def compare(net, workloads, precision=_b.STDD_PREC_C64, rtol=1e-8, device=0):
-    """Solve each workload with the zero guess and with the learned guess
-    (same precision and tolerance); per right-hand side: iterations, solve
-    times and the guess's residuals."""
+def compare(net, workloads, precision=_b.STDD_PREC_C64, rtol=1e-8, restart=None, maxit=1000, device=0):
+    """Solve each workload with the zero start and with the learned start on
+    the same factorization (same precision and tolerance); per right-hand
+    side: iterations, preconditioner applications, solve times (CUDA events)
+    and the start's residuals."""
+    import torch
+    dev = torch.device("cuda", device)
     rows = []
     for w in workloads:
-        xz, iz = solve_workload(w, precision=precision, rtol=rtol, device=device)
-        xl, il = solve_workload(w, precision=precision, rtol=rtol, device=device, x0="learned", net=net)
+        s, _ = _solver(w, precision, device)
+        try:
+            s.factor()
+            b = torch.from_numpy(w.b).to(dev)
+            s.set_sources(b)
+            _b.stdd_set_learned_guess(s.ctx, net.h)
+            res = {}
+            for mode in (None, "learned"):
+                x = torch.empty_like(b)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                e0.record()
+                st = s.solve(x, restart=restart or w.restart, rtol=rtol, maxit=maxit, x0=mode, allow_noconv=True)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                hist = [s.history(q) for q in range(w.nrhs)]
+                info = dict(x=x, ms=e0.elapsed_time(e1), ok=st == _b.STDD_OK, its=[len(h) - 1 for h in hist])
+                if mode:
+                    info["g"] = [_b.stdd_learned_guess_info(s.ctx, q) for q in range(w.nrhs)]
+                res[mode] = info
+        finally:
+            s.close()
+        z, l = res[None], res["learned"]
         for q in range(w.nrhs):
             rows.append(dict(nx=w.nx, ny=w.ny, seed=w.meta.get("seed"), rhs=q,
-                             its_zero=iz["iterations"][q], its_learned=il["iterations"][q],
+                             its_zero=z["its"][q], its_learned=l["its"][q],
                              # preconditioner applications: the learned start spends one sweep
-                             minv_zero=iz["iterations"][q], minv_learned=il["iterations"][q] + 1,
-                             solve_s_zero=iz["solve_s"] / w.nrhs, solve_s_learned=il["solve_s"] / w.nrhs,
-                             guess_raw=il["guess_raw"][q], guess_scaled=il["guess_scaled"][q],
-                             guess_used=il["guess_used"][q], conv_zero=iz["converged"],
-                             conv_learned=il["converged"], x_zero=xz[q], x_learned=xl[q]))
+                             minv_zero=z["its"][q], minv_learned=l["its"][q] + 1,
+                             solve_s_zero=z["ms"] / 1e3 / w.nrhs, solve_s_learned=l["ms"] / 1e3 / w.nrhs,
+                             guess_raw=l["g"][q][0], guess_scaled=l["g"][q][1], guess_used=l["g"][q][2],
+                             conv_zero=z["ok"], conv_learned=l["ok"], x_zero=z["x"][q], x_learned=l["x"][q]))
     return rows
 
 
@@ -309,7 +332,38 @@ if __name__ == "__main__":
     ap.add_argument("--net", default="6,32,256", help="levels,base,max channels")
     ap.add_argument("--train-seconds", type=float, default=300.0)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--bench-forward", default=None, metavar="WxH",
+                    help="only time the network forward at this image size (random weights) and exit")
     a = ap.parse_args()
+    if a.bench_forward:
+        import torch
+        L, c0, cm = (int(v) for v in a.net.split(","))
+        fw, fh = (int(v) for v in a.bench_forward.split("x"))
+        net = Network(L, c0, cm, mode="tc")
+        fh, fw = net.image_shape(fw, fh)
+        xi = torch.randn((1, 3, fh, fw), dtype=torch.float32, device="cuda:0")
+        xo = torch.empty((1, 2, fh, fw), dtype=torch.float32, device="cuda:0")
+        for _ in range(3):
+            net.forward(xi, xo)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(10):
+            net.forward(xi, xo)
+        ev[1].record()
+        torch.cuda.synchronize()
+        flops = 0
+        ch = [min(cm, c0 << lv) for lv in range(L)]
+        for lv in range(L):
+            px = (fh >> lv) * (fw >> lv)
+            cin = 3 if lv == 0 else ch[lv - 1]
+            flops += 2 * 9 * px * (cin * ch[lv] + ch[lv] * ch[lv])
+            if lv < L - 1:
+                flops += 2 * 9 * px * (ch[lv + 1] * ch[lv] + ch[lv] * ch[lv])
+        flops += 2 * 9 * fh * fw * ch[0] * 2
+        ms = ev[0].elapsed_time(ev[1]) / 10
+        print(json.dumps(dict(image=[fw, fh], forward_ms=ms, conv_gflop=flops / 1e9, tflops=flops / ms / 1e9)))
+        net.close()
+        sys.exit(0)
     L, c0, cm = (int(v) for v in a.net.split(","))
     ex, ey = (int(v) for v in a.eval_shape.split("x"))
     res = experiment(a.train, a.train_side, a.eval, (ex, ey), L, c0, cm, a.train_seconds,

@@ -12,7 +12,8 @@ clear of the PML (the series is evaluated here, outside the library).  One JSON 
 count on stdout.
 
     python -m paper_2509_20801_gb300.table1 [--n 6000] [--nsub 2,4,8,16,32,64]
-        [--precision fp64|c64] [--richardson]
+        [--precision fp64|c64] [--order additive|multiplicative|red-black] [--restart m]
+        [--richardson]
 """
 from __future__ import annotations
 
@@ -26,6 +27,7 @@ import numpy as np
 from . import binding as _b
 
 PRECISIONS = {"fp64": _b.STDD_PREC_FP64, "c64": _b.STDD_PREC_C64, "fp16": _b.STDD_PREC_C64_FP16}
+ORDERS = {"additive": 0, "multiplicative": 1, "red-black": 2}
 
 
 def mie_scattered(x, y, cx, cy, a, eps1, k0):
@@ -62,7 +64,7 @@ def sample_ring(w, count, seed=0):
 
 
 def run(n=6000, ppw=40, radius=9.0, nsubs=(2, 4, 8, 16, 32, 64), precision="fp64", rtol=1e-8, restart=30,
-        maxit=1000, richardson=False, samples=4000, device=0, out=sys.stdout, log=None):
+        maxit=1000, richardson=False, samples=4000, device=0, out=sys.stdout, log=None, order="additive"):
     import torch
     import workloads as W
     from . import Solver
@@ -82,6 +84,7 @@ def run(n=6000, ppw=40, radius=9.0, nsubs=(2, 4, 8, 16, 32, 64), precision="fp64
         s = Solver(w.nx, w.ny, w.dx, w.dy, w.wavelength, eps, npml=w.npml, pml_order=w.pml_order,
                    pml_R=w.pml_R, nsub=ns, overlap=w.overlap, interface_pml=w.interface_pml,
                    precision=PRECISIONS[precision], device=device)
+        _b.stdd_set_option(s.ctx, _b.STDD_OPT_ORDER, ORDERS[order])
         try:
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             torch.cuda.synchronize(dev)
@@ -95,7 +98,8 @@ def run(n=6000, ppw=40, radius=9.0, nsubs=(2, 4, 8, 16, 32, 64), precision="fp64
             hist = s.history(0)
             stats = s.stats()
             got = x[0].cpu().numpy()[si, sj]
-            row = dict(nsub=ns, unknowns=w.n, unknowns_per_strip=w.n // ns, precision=precision,
+            row = dict(nsub=ns, unknowns=w.n, unknowns_per_strip=w.n // ns, precision=precision, order=order,
+                       restart=restart,
                        factor_s=ev[0].elapsed_time(ev[1]) / 1e3, solve_s=ev[1].elapsed_time(ev[2]) / 1e3,
                        iterations=len(hist) - 1, converged=st == _b.STDD_OK, final_residual=float(hist[-1]),
                        device_gb=stats["device_bytes"] / 1e9, factor_entries=stats["factor_entries"],
@@ -130,6 +134,9 @@ if __name__ == "__main__":
     ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--richardson", action="store_true")
+    ap.add_argument("--order", default="additive", choices=sorted(ORDERS))
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--maxit", type=int, default=1000)
     a = ap.parse_args()
-    run(a.n, a.ppw, a.radius, tuple(int(v) for v in a.nsub.split(",")), a.precision, a.rtol,
-        richardson=a.richardson, log=lambda m: print(m, file=sys.stderr, flush=True))
+    run(a.n, a.ppw, a.radius, tuple(int(v) for v in a.nsub.split(",")), a.precision, a.rtol, a.restart,
+        a.maxit, a.richardson, order=a.order, log=lambda m: print(m, file=sys.stderr, flush=True))

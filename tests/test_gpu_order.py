@@ -42,17 +42,18 @@ def strip6():
     return w, P, DDM.from_workload(w, P)
 
 
-@pytest.mark.parametrize("graphs", [1, 0])
-def test_multiplicative_preconditioner_matches_oracle(rnd, graphs):
+@pytest.mark.parametrize("order,graphs", [(1, 1), (1, 0), (2, 1), (2, 0)])
+def test_multiplicative_preconditioner_matches_oracle(rnd, order, graphs):
     from paper_2509_20801_gb300 import STDD_OPT_GRAPHS, stdd_apply_preconditioner, stdd_set_option
     w, P, D = rnd
-    s = _solver(w)
+    s = _solver(w, order=order)
     stdd_set_option(s.ctx, STDD_OPT_GRAPHS, graphs)
     s.factor()
     v = W.random_vector(P.n, seed=6)[0]
     z = torch.empty(P.n, dtype=torch.complex128, device=DEV)
     stdd_apply_preconditioner(s.ctx, torch.from_numpy(v).to(DEV), z)
-    assert _rel(z.cpu().numpy(), D.apply_Minv_multiplicative(v)) < 1e-10
+    ref = D.apply_Minv_multiplicative(v, order=None if order == 1 else "red-black")
+    assert _rel(z.cpu().numpy(), ref) < 1e-10
     s.close()
 
 
@@ -79,7 +80,7 @@ def test_fgmres_with_multiplicative_order(strip6, precision):
     b = torch.from_numpy(w.b).to(DEV)
     ref = P.solve(w.b[0].ravel())
     its = {}
-    for order in (0, 1):
+    for order in (0, 1, 2):
         s = _solver(w, precision=precision, order=order)
         s.factor()
         s.set_sources(b)
@@ -94,4 +95,4 @@ def test_fgmres_with_multiplicative_order(strip6, precision):
                      flexible=True)
     if precision == 0:
         assert abs(its[1] - (len(oh) - 1)) <= 1
-    assert its[1] < its[0]
+    assert its[1] < its[2] < its[0]

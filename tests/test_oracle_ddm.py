@@ -250,3 +250,18 @@ def test_multiplicative_order_converges_in_fewer_iterations():
                       flexible=True)
     assert np.linalg.norm(xm - ref) < 1e-7 * np.linalg.norm(ref)
     assert len(hm) < len(ha)
+
+
+def test_red_black_groups_can_be_solved_together():
+    """Same-colour strips do not interact: solving all even strips from one
+    residual, then all odd ones, equals the sequential red-black order."""
+    w = W.random_medium(90, 20, ppw=20, seed=23, npml=4, nsub=6, overlap=3, interface_pml=4)
+    prob = Problem.from_workload(w)
+    ddm = DDM.from_workload(w, prob)
+    v = W.random_vector(prob.n, seed=24)[0]
+    z = np.zeros(prob.n, complex)
+    for colour in (0, 1):
+        r = v - prob.A @ z
+        z = z + sum(ddm.extend(k, ddm.local_solve(k, ddm.restrict_owned(k, r))) for k in range(colour, 6, 2))
+    ref = ddm.apply_Minv_multiplicative(v, order="red-black")
+    assert np.linalg.norm(z - ref) < 1e-12 * np.linalg.norm(ref)
