@@ -72,6 +72,8 @@ def parse():
                     help="metalens: 4096x1024, 16 strips (the benchmark); metalens-small: 1024x1024, 4 strips "
                          "(profiling captures); cylinder: 200x200, 2 strips")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per step (line sources)")
+    ap.add_argument("--band", type=int, default=0, choices=[0, 1],
+                    help="1: band-space FGMRES (FP64 factors, additive order; same iterates, band-sized vectors)")
     ap.add_argument("--order", default="additive", choices=["additive", "multiplicative", "red-black"],
                     help="preconditioner order: additive (Algorithm 1, the benchmark), symmetric multiplicative, "
                          "or red-black")
@@ -265,20 +267,23 @@ def run_ours(args, rank, world, local_rank):
 
     orders = {"additive": 0, "multiplicative": 1, "red-black": 2}
 
-    def make_solver(p, order=None):
+    def make_solver(p, order=None, band=None):
         sv = S.Solver.from_workload(w, eps=eps_d, precision=p, device=local_rank, stream=stream.cuda_stream)
-        S.stdd_set_option(sv.ctx, S.STDD_OPT_ORDER, orders[order or args.order])
+        order = order or args.order
+        S.stdd_set_option(sv.ctx, S.STDD_OPT_ORDER, orders[order])
+        band = args.band if band is None else band
+        S.stdd_set_option(sv.ctx, S.STDD_OPT_BAND, 1 if (band and p == S.STDD_PREC_FP64 and order == "additive") else 0)
         return sv
 
     def step(sv):
         sv.factor()
         return sv.solve(x_d, restart=RESTART, rtol=RTOL, maxit=args.maxit, allow_noconv=True) == B.STDD_OK
 
-    def timed(p, warm, steps, profile, order=None):
+    def timed(p, warm, steps, profile, order=None, band=None):
         """warm-up, then `steps` timed steps, with phase spans if profile >= 1
         (the M^-1 graphs stay on); with profile = 2 one more step with
         per-launch kernel spans (level 2) for the kernel rooflines."""
-        sv = make_solver(p, order)
+        sv = make_solver(p, order, band)
         sv.set_sources(b_d)
         for _ in range(warm):
             step(sv)
@@ -427,7 +432,8 @@ def run_ours(args, rank, world, local_rank):
                   S.STDD_PREC_C64_BF16: "c64-factors(bf16 tensor-core updates)+c128-krylov",
                   S.STDD_PREC_C64_FP16: "c64-factors(fp16 tensor-core updates)+c128-krylov"}[prec],
         "data": "synthetic",
-        "config": {"workload": workload_desc(w), "precision": args.precision, "order": args.order, "rtol": RTOL,
+        "config": {"workload": workload_desc(w), "precision": args.precision, "order": args.order,
+                   "krylov_space": "band" if args.band else "full", "rtol": RTOL,
                    "restart": RESTART, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (factors %.1f GB, Krylov basis %.1f GB)"
                          % (E * elem / 1e9, (2 * RESTART + 1) * w.n * 16 / 1e9)},
@@ -470,6 +476,15 @@ def run_ours(args, rank, world, local_rank):
                                    "t_factor_ms": prof3["factor_ms"], "t_solve_ms": prof3["solve_ms"],
                                    "rel_diff_vs_main": diff}
             sv3.close()
+        # the same iteration in band space (FP64 additive) or not
+        if prec == S.STDD_PREC_FP64 and args.order == "additive":
+            sv4, ms4, prof4, _, st4, hist4, _, _ = timed(prec, 1, 1, 1, band=0 if args.band else 1)
+            diff = float(torch.linalg.vector_norm(x_d - x_main) / torch.linalg.vector_norm(x_main))
+            out["band_space" if not args.band else "full_space"] = {
+                "ms_per_step": ms4, "value": N / (ms4 * 1e-3) / 1e6, "iterations": len(hist4) - 1,
+                "final_residual": st4["final_residual"], "t_factor_ms": prof4["factor_ms"],
+                "t_solve_ms": prof4["solve_ms"], "rel_diff_vs_main": diff}
+            sv4.close()
 
     if not args.no_e2e:
         # through the public API with host buffers: permittivity and sources

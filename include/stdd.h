@@ -270,8 +270,24 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     strip of its colour: needs every interior strip wider
  *                     than overlap + interface PML + 1, else STDD_EINVAL
  *                     when it is applied).  In paper_richardson mode the
- *                     stationary iteration uses the chosen order. */
-enum { STDD_OPT_GRAPHS = 1, STDD_OPT_AUTOTUNE = 2, STDD_OPT_LEAF = 3, STDD_OPT_ORDER = 4 };
+ *                     stationary iteration uses the chosen order.
+ * and one that changes how FGMRES works (same iterates in exact arithmetic):
+ *   STDD_OPT_BAND     (default 0): 1 = band-space FGMRES.  For the additive
+ *                     order, A M^-1 - I maps everything into the interface
+ *                     bands (the overlap and interface-PML columns around
+ *                     each interface, plus one), so with r0 = b - A x0 the
+ *                     solve runs GMRES on the band system
+ *                     (I + T) s = -T r0, T = A M^-1 - I, and returns
+ *                     x = x0 + M^-1 (r0 + s).  Krylov vectors hold only the
+ *                     band columns, and each band application of M^-1 skips
+ *                     the subtrees with no band sources (going up) and the
+ *                     fronts off the band (coming down).  Its residuals are
+ *                     the true residuals because the local solves are exact,
+ *                     so it needs FP64 factors and the additive order
+ *                     (else stdd_solve returns STDD_EINVAL).  It costs one
+ *                     full application before the iteration (counted as the
+ *                     first iteration) and one after. */
+enum { STDD_OPT_GRAPHS = 1, STDD_OPT_AUTOTUNE = 2, STDD_OPT_LEAF = 3, STDD_OPT_ORDER = 4, STDD_OPT_BAND = 5 };
 stdd_status stdd_set_option(stdd_ctx *ctx, int option, int value);
 stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);
 

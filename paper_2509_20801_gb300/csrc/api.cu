@@ -3,6 +3,7 @@
 // multifrontal factorization) and the flexible GMRES outer iteration whose
 // preconditioner is one Jacobi source-transfer sweep (Algorithm 1's loop
 // body in residual form, Eqs. 18-21).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -338,6 +339,27 @@ struct stdd_ctx {
   std::vector<int> perm, pos;
   std::vector<std::vector<int>> lvl_front, lvl_up, lvl_down;
   std::vector<StripDev> strips_host;
+  std::vector<FrontDev> fronts_host;   // host copies for the band analysis
+  std::vector<int> nodes_host;
+  // band-space FGMRES (STDD_OPT_BAND): interface bands as column intervals,
+  // the column -> band offset map, and per level the work items of the
+  // fronts a band vector needs (upward: subtree holds band sources;
+  // downward: pivots on the widened band, and their ancestors)
+  bool use_band = false, band_ready = false;
+  std::vector<int2> band_iv, band_iv1;
+  std::vector<int64_t> band_off, band_off1;
+  int64_t band_n = 0, band_n1 = 0;
+  DBuf d_band_iv, d_band_off, d_band_iv1, d_band_off1, d_colband, d_items_band, d_fb, d_sb;
+  std::vector<int64_t> lvl_bup_off, lvl_bdown_off;
+  std::vector<int> lvl_bup_n, lvl_bdown_n;
+  void build_band();
+  stdd::BandDev band_dev() const {
+    return stdd::BandDev{d_band_iv.as<int2>(), d_band_off.as<int64_t>(), (int)band_iv.size(), band_n,
+                         d_band_iv1.as<int2>(), d_band_off1.as<int64_t>(), (int)band_iv1.size(), band_n1};
+  }
+  void solve_levels_band(int nr);
+  void enqueue_op_band(const std::vector<const double2 *> &ss, const std::vector<double2 *> &ys);
+  void apply_op_band(const std::vector<const double2 *> &ss, const std::vector<double2 *> &ys);
   void clear_graphs() {
     for (auto &kv : minv_graphs) cudaGraphExecDestroy(kv.second.exec);
     minv_graphs.clear();
@@ -613,6 +635,9 @@ void stdd_ctx::build_structure() {
     for (int i = strips[k].c0; i < strips[k].c1; ++i) colstrip[i] = k;
 
   strips_host = sdev;
+  fronts_host = fr;
+  nodes_host = nodes;
+  band_ready = false;
   upload(d_strips, sdev, stream);
   upload(d_fronts, fr, stream);
   upload(d_nodes, nodes, stream);
@@ -801,6 +826,187 @@ void stdd_ctx::enqueue_minv_multiplicative(const std::vector<const double2 *> &v
   CK(cudaGetLastError());
 }
 
+// Band analysis.  For the additive order, A M^-1 v - v vanishes outside the
+// interface bands (the transfer identity): around the interface at column c
+// between strips k and k+1 the band is [c - e_l - 1, c + e_r + 1), e_r the
+// columns strip k's box reaches past c, e_l those strip k+1's box reaches
+// before it (the stencil adds one).  A band vector's sources reach strip k
+// only on its owned band columns, and the band values of A M^-1 v need the
+// synthesized field on the band widened by one column.
+void stdd_ctx::build_band() {
+  if (band_ready) return;
+  std::vector<std::pair<int, int>> ivs;  // [first, last) columns
+  for (int k = 0; k + 1 < nsub; ++k) {
+    const int c = strips[k].c1;
+    const int er = strips[k].x1 - c, el = c - strips[k + 1].x0;
+    ivs.push_back({std::max(0, c - el - 1), std::min(nx, c + er + 1)});
+  }
+  auto merge = [](std::vector<std::pair<int, int>> v) {
+    std::sort(v.begin(), v.end());
+    std::vector<std::pair<int, int>> out;
+    for (auto &p : v) {
+      if (!out.empty() && p.first <= out.back().second) out.back().second = std::max(out.back().second, p.second);
+      else out.push_back(p);
+    }
+    return out;
+  };
+  const auto b0 = merge(ivs);
+  std::vector<std::pair<int, int>> w1;
+  for (auto &p : b0) w1.push_back({std::max(0, p.first - 1), std::min(nx, p.second + 1)});
+  const auto b1 = merge(w1);
+  auto lay = [&](const std::vector<std::pair<int, int>> &b, std::vector<int2> &iv, std::vector<int64_t> &off) {
+    iv.clear();
+    off.clear();
+    int64_t o = 0;
+    for (auto &p : b) {
+      iv.push_back(make_int2(p.first, p.second - p.first));
+      off.push_back(o);
+      o += (int64_t)(p.second - p.first) * ny;
+    }
+    if (iv.empty()) {  // one strip: no band (keep the arrays non-empty)
+      iv.push_back(make_int2(0, 0));
+      off.push_back(0);
+    }
+    return o;
+  };
+  band_n = lay(b0, band_iv, band_off);
+  band_n1 = lay(b1, band_iv1, band_off1);
+  std::vector<int64_t> colband(nx, -1);
+  std::vector<char> in1(nx, 0);
+  for (size_t k = 0; k < b0.size(); ++k)
+    for (int c = b0[k].first; c < b0[k].second; ++c) colband[c] = band_off[k] + (int64_t)(c - b0[k].first) * ny;
+  for (auto &p : b1)
+    for (int c = p.first; c < p.second; ++c) in1[c] = 1;
+  // active fronts; children come after their parents in the level-major list
+  const int64_t nf = (int64_t)fronts_host.size();
+  std::vector<char> up(nf, 0), dn(nf, 0);
+  for (int64_t f = nf - 1; f >= 0; --f) {
+    const FrontDev &d = fronts_host[f];
+    const StripHost &st = strips[d.strip];
+    bool u = false, w = false;
+    for (int q = 0; q < d.p && !(u && w); ++q) {
+      const int col = st.x0 + nodes_host[d.node_off + q] / ny;
+      if (col >= st.c0 && col < st.c1 && colband[col] >= 0) u = true;
+      if (in1[col]) w = true;
+    }
+    for (int ci = 0; ci < 2; ++ci)
+      if (d.child[ci] >= 0) {
+        u = u || up[d.child[ci]];
+        w = w || dn[d.child[ci]];
+      }
+    up[f] = u;
+    dn[f] = w;
+  }
+  std::vector<int2> items;
+  lvl_bup_off.assign(depth, 0);
+  lvl_bdown_off.assign(depth, 0);
+  lvl_bup_n.assign(depth, 0);
+  lvl_bdown_n.assign(depth, 0);
+  for (int L = 0; L < depth; ++L) {
+    const LevelInfo &li = levels[L];
+    lvl_bup_off[L] = (int64_t)items.size();
+    for (int f = li.f0; f < li.f0 + li.nf; ++f)
+      if (up[f])
+        for (int c = 0; c < std::max(1, (fronts_host[f].b + li.rows_up - 1) / li.rows_up); ++c)
+          items.push_back(make_int2(f, c));
+    lvl_bup_n[L] = (int)((int64_t)items.size() - lvl_bup_off[L]);
+    lvl_bdown_off[L] = (int64_t)items.size();
+    for (int f = li.f0; f < li.f0 + li.nf; ++f)
+      if (dn[f])
+        for (int c = 0; c < (fronts_host[f].p + li.rows_down - 1) / li.rows_down; ++c)
+          items.push_back(make_int2(f, c));
+    lvl_bdown_n[L] = (int)((int64_t)items.size() - lvl_bdown_off[L]);
+  }
+  if (items.empty()) items.push_back(make_int2(0, 0));
+  upload(d_band_iv, band_iv, stream);
+  upload(d_band_off, band_off, stream);
+  upload(d_band_iv1, band_iv1, stream);
+  upload(d_band_off1, band_off1, stream);
+  upload(d_colband, colband, stream);
+  upload(d_items_band, items, stream);
+  CK(cudaStreamSynchronize(stream));
+  band_ready = true;
+}
+
+// Substitution sweeps for band sources: the gather over every front (it
+// writes zeros where a subtree has no source), the upward GEMVs of the
+// fronts with sources in their subtree, the downward ones of the fronts the
+// widened band needs.
+void stdd_ctx::solve_levels_band(int nr) {
+  ensure_solve_buffers(nr);
+  const int2 *items = d_items_band.as<int2>();
+  for (int L = depth - 1; L >= 0; --L) {
+    const LevelInfo &li = levels[L];
+    stdd::mf_up_gather_level<double>(mf_args(L & 1, true), li, nr, nloc, stream);
+    stdd::mf_up_level<double>(mf_args(L & 1, true), items + lvl_bup_off[L], lvl_bup_n[L], li.rows_up, li.split_up,
+                              nr, nloc, stream);
+  }
+  for (int L = 0; L < depth; ++L) {
+    const LevelInfo &li = levels[L];
+    stdd::mf_down_level<double>(mf_args(L & 1, true), items + lvl_bdown_off[L], lvl_bdown_n[L], li.rows_down,
+                                li.split_down, nr, nloc, stream);
+  }
+  CK(cudaGetLastError());
+}
+
+// y_i = (A M^-1 G(s_i))|band = (I + T) s_i for band vectors s_i; the
+// synthesized fields go to the Z storage (unused by the band iteration).
+void stdd_ctx::enqueue_op_band(const std::vector<const double2 *> &ss, const std::vector<double2 *> &ys) {
+  const int na = (int)ss.size();
+  const size_t E = elem();
+  const stdd::BandDev bd = band_dev();
+  auto slot = [&](int i) { return static_cast<void *>(d_tloc.as<char>() + (size_t)i * nloc * E); };
+  for (int i = 0; i < na; ++i)
+    stdd::launch_restrict_band<double>(d_strips.as<StripDev>(), nsub, nloc_max, ny, d_colband.as<int64_t>(), ss[i],
+                                       slot(i), stream);
+  solve_levels_band(na);
+  for (int i = 0; i < na; ++i) {
+    double2 *zg = d_Z.as<double2>() + (int64_t)i * N();
+    stdd::launch_synthesize_band<double>(d_strips.as<StripDev>(), nsub, ny, d_colstrip.as<int>(), bd, slot(i), zg,
+                                         stream);
+    stdd::launch_stencil_band(grid(), bd, zg, nullptr, false, false, ys[i], stream);
+  }
+  CK(cudaGetLastError());
+}
+
+void stdd_ctx::apply_op_band(const std::vector<const double2 *> &ss, const std::vector<double2 *> &ys) {
+  const int na = (int)ss.size();
+  ensure_solve_buffers(na);
+  const int span = pbegin(PH_MINV);
+  if (use_graphs && prof < 2) {
+    std::vector<const void *> key{reinterpret_cast<const void *>(1)};  // tag: band operator
+    for (int i = 0; i < na; ++i) {
+      key.push_back(ss[i]);
+      key.push_back(ys[i]);
+    }
+    auto it = minv_graphs.find(key);
+    if (it == minv_graphs.end()) {
+      const long long before = __atomic_load_n(&stdd::g_launches, __ATOMIC_RELAXED);
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+      enqueue_op_band(ss, ys);
+      const cudaError_t ce = cudaStreamEndCapture(stream, &g);
+      if (ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        throw CudaError(std::string("graph capture: ") + cudaGetErrorString(ce));
+      }
+      cudaGraphExec_t ex = nullptr;
+      const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) throw CudaError(std::string("graph instantiate: ") + cudaGetErrorString(ie));
+      const long long kernels = __atomic_load_n(&stdd::g_launches, __ATOMIC_RELAXED) - before;
+      __atomic_add_fetch(&stdd::g_launches, -kernels, __ATOMIC_RELAXED);
+      it = minv_graphs.emplace(key, GraphEntry{ex, kernels}).first;
+    }
+    CK(cudaGraphLaunch(it->second.exec, stream));
+    stdd::count_launch((int)it->second.kernels);
+  } else {
+    enqueue_op_band(ss, ys);
+  }
+  pend(span);
+  CK(cudaGetLastError());
+}
+
 void stdd_ctx::ensure_solve_buffers(int nr) {
   if (nr <= solve_nrhs_cap) return;
   clear_graphs();
@@ -946,15 +1152,37 @@ double dev_norm(double2 *x, int64_t n, DBuf &part, DBuf &nrm, cudaStream_t st) {
 // one shrank ||w|| below 1/sqrt(2) of its value (Daniel-Gragg-Kaufman-
 // Stewart); Givens rotations and the small triangular solves on the host.
 // d_x holds the initial guesses on entry and the iterates on exit.
+// Band mode (STDD_OPT_BAND; FP64 factors, additive order): with
+// r0 = b - A x0 and T = A M^-1 - I, whose range is the interface bands, the
+// right-preconditioned iterate x = x0 + M^-1 (r0 + s) has the residual
+// b - A x = -(T r0 + (I + T) s) on the bands and zero elsewhere, so GMRES
+// runs on the band system (I + T) s = -T r0 with band-sized vectors and
+// partial sweeps; its residuals are the true ones.  One full application
+// before (for T r0) and one after (for x); the first counts as an
+// iteration.
 void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
   const int m = o.restart, nq = nrhs;
-  const int64_t n = N();
+  bool band = use_band;
+  const int64_t NN = N();
   ensure_krylov(m);
+  if (band) {
+    build_band();
+    band = band_n > 0;  // one strip: no bands, the standard iteration
+  }
+  const int64_t n = band ? band_n : NN;
   double2 *Vb = d_V.as<double2>(), *Zb = d_Z.as<double2>(), *X = d_x.as<double2>(), *r = d_r.as<double2>();
   double *nrm_base = d_nrm.as<double>();
   double *part = reinterpret_cast<double *>(d_part.p);
   auto V = [&](int q, int j) { return Vb + ((int64_t)q * (m + 1) + j) * n; };
-  auto Z = [&](int q, int j) { return Zb + ((int64_t)q * m + j) * n; };
+  auto Z = [&](int q, int j) { return band ? V(q, j) : Zb + ((int64_t)q * m + j) * n; };
+  if (band) {
+    d_fb.alloc((size_t)std::max<int64_t>(1, n) * nq * sizeof(double2));
+    d_sb.alloc((size_t)std::max<int64_t>(1, n) * nq * sizeof(double2));
+  }
+  auto FB = [&](int q) { return d_fb.as<double2>() + (int64_t)q * n; };
+  auto SB = [&](int q) { return d_sb.as<double2>() + (int64_t)q * n; };
+  // x (full field, standard mode) or s (band vector, band mode) of rhs q
+  auto XS = [&](int q) { return band ? SB(q) : X + (int64_t)q * NN; };
   auto h1 = [&](int q) { return d_h.as<double2>() + (size_t)q * 2 * (m + 2); };
   auto h2 = [&](int q) { return h1(q) + (m + 2); };
   auto nrmq = [&](int q) { return nrm_base + 4 + 2 * q; };
@@ -973,23 +1201,57 @@ void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
     t.sn.assign(m, 0);
     t.cs.assign(m, 0);
     t.hv.assign(2 * (m + 2), 0);
-    const double2 *b = d_b.as<double2>() + (int64_t)q * n;
-    t.bnorm = dev_norm(const_cast<double2 *>(b), n, d_part, d_nrm, stream);
+    const double2 *b = d_b.as<double2>() + (int64_t)q * NN;
+    t.bnorm = dev_norm(const_cast<double2 *>(b), NN, d_part, d_nrm, stream);
     if (t.bnorm == 0) {
-      CK(cudaMemsetAsync(X + (int64_t)q * n, 0, n * sizeof(double2), stream));
+      CK(cudaMemsetAsync(X + (int64_t)q * NN, 0, NN * sizeof(double2), stream));
       history[q].push_back(0.0);
       t.done = true;
     }
   }
+  if (band) {
+    // r0 = b - A x0 (in the V storage), z = M^-1 r0 (in Z), f = (r0 - A z)|band
+    std::vector<const double2 *> rs;
+    std::vector<double2 *> zs;
+    std::vector<int> qs;
+    for (int q = 0; q < nq; ++q) {
+      if (S[q].done) continue;
+      double2 *r0 = Vb + (int64_t)q * NN;
+      stdd::launch_residual(grid(), d_b.as<double2>() + (int64_t)q * NN, X + (int64_t)q * NN, r0, stream);
+      history[q].push_back(dev_norm(r0, NN, d_part, d_nrm, stream) / S[q].bnorm);
+      rs.push_back(r0);
+      zs.push_back(Zb + (int64_t)q * NN);
+      qs.push_back(q);
+    }
+    if (!qs.empty()) apply_minv_multi(rs, zs);
+    const stdd::BandDev bd = band_dev();
+    for (size_t i = 0; i < qs.size(); ++i) {
+      const int q = qs[i];
+      stdd::launch_stencil_band(grid(), bd, zs[i], rs[i], true, true, FB(q), stream);
+      CK(cudaMemsetAsync(SB(q), 0, std::max<int64_t>(1, n) * sizeof(double2), stream));
+      history[q].push_back(dev_norm(FB(q), n, d_part, d_nrm, stream) / S[q].bnorm);
+      S[q].its = 1;
+    }
+  }
+  std::vector<char> s_zero(nq, 1);
   while (true) {
     // restart cycle: true residuals, first basis vectors
     std::vector<int> act;
     for (int q = 0; q < nq; ++q) {
       St &t = S[q];
       if (t.done) continue;
-      const double2 *b = d_b.as<double2>() + (int64_t)q * n;
       int sp = pbegin(PH_MATVEC);
-      stdd::launch_residual(grid(), b, X + (int64_t)q * n, r, stream);
+      if (band) {
+        // r = f - (I + T) s, the true residual on the band
+        if (s_zero[q]) {
+          CK(cudaMemcpyAsync(r, FB(q), n * sizeof(double2), cudaMemcpyDeviceToDevice, stream));
+        } else {
+          apply_op_band({SB(q)}, {V(q, 0)});
+          stdd::launch_vsub(FB(q), V(q, 0), r, n, stream);
+        }
+      } else {
+        stdd::launch_residual(grid(), d_b.as<double2>() + (int64_t)q * NN, X + (int64_t)q * NN, r, stream);
+      }
       pend(sp);
       const double beta = dev_norm(r, n, d_part, d_nrm, stream);
       if (history[q].empty()) history[q].push_back(beta / t.bnorm);
@@ -1015,11 +1277,17 @@ void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
         vs.push_back(V(q, j));
         zs.push_back(Z(q, j));
       }
-      apply_minv_multi(vs, zs);
-      int sp = pbegin(PH_MATVEC);
-      for (int q : inner) stdd::launch_stencil(grid(), Z(q, j), V(q, j + 1), stream);
-      pend(sp);
-      sp = pbegin(PH_ORTHO);
+      if (band) {
+        std::vector<double2 *> ws;
+        for (int q : inner) ws.push_back(V(q, j + 1));
+        apply_op_band(vs, ws);
+      } else {
+        apply_minv_multi(vs, zs);
+        int sp = pbegin(PH_MATVEC);
+        for (int q : inner) stdd::launch_stencil(grid(), Z(q, j), V(q, j + 1), stream);
+        pend(sp);
+      }
+      int sp = pbegin(PH_ORTHO);
       for (int q : inner) {
         double2 *w = V(q, j + 1);
         stdd::launch_mdot(V(q, 0), n, j + 1, w, n, d_part.as<double2>(), h1(q), stream, 1);
@@ -1091,8 +1359,28 @@ void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
       for (int i = 0; i < k; ++i) yd[i] = make_double2(y[i].real(), y[i].imag());
       double2 *yq = d_y.as<double2>() + (size_t)q * (m + 1);
       CK(cudaMemcpyAsync(yq, yd.data(), sizeof(double2) * k, cudaMemcpyHostToDevice, stream));
-      stdd::launch_maxpy(Z(q, 0), n, k, yq, X + (int64_t)q * n, n, stream);
+      stdd::launch_maxpy(Z(q, 0), n, k, yq, XS(q), n, stream);
+      s_zero[q] = 0;
     }
+    CK(cudaStreamSynchronize(stream));
+  }
+  if (band) {
+    // x = x0 + M^-1 (r0 + s): r0 again (in V storage), plus the band s
+    std::vector<const double2 *> rs;
+    std::vector<double2 *> zs;
+    std::vector<int> qs;
+    const stdd::BandDev bd = band_dev();
+    for (int q = 0; q < nq; ++q) {
+      if (S[q].bnorm == 0) continue;
+      double2 *r0 = Vb + (int64_t)q * NN;
+      stdd::launch_residual(grid(), d_b.as<double2>() + (int64_t)q * NN, X + (int64_t)q * NN, r0, stream);
+      if (n > 0) stdd::launch_band_scatter_add(bd, ny, SB(q), r0, stream);
+      rs.push_back(r0);
+      zs.push_back(Zb + (int64_t)q * NN);
+      qs.push_back(q);
+    }
+    if (!qs.empty()) apply_minv_multi(rs, zs);
+    for (size_t i = 0; i < qs.size(); ++i) stdd::nn_zadd(zs[i], X + (int64_t)qs[i] * NN, NN, stream);
     CK(cudaStreamSynchronize(stream));
   }
   last_noconv = false;
@@ -1413,6 +1701,8 @@ stdd_status stdd_solve(stdd_ctx *c, const stdd_solve_opts *o, double *x_out, int
     if (o->restart < 1 || o->restart > 500 || o->maxit < 0 || !(o->rtol >= 0)) throw ArgError("bad solve options");
     if (o->x0_mode == STDD_X0_USER && !o->x0) throw ArgError("x0 missing");
     if (o->x0_mode < STDD_X0_ZERO || o->x0_mode > STDD_X0_LEARNED) throw ArgError("bad x0_mode");
+    if (c->use_band && !o->paper_richardson && (c->prec != STDD_PREC_FP64 || c->order != 0))
+      throw ArgError("band-space FGMRES needs FP64 factors and the additive order");
     const int64_t n = c->N();
     c->history.assign(c->nrhs, {});
     c->lg_raw.assign(c->nrhs, 0.0);
@@ -1592,6 +1882,9 @@ stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
           c->order = value;
           c->clear_graphs();
         }
+        break;
+      case STDD_OPT_BAND:
+        c->use_band = value != 0;
         break;
       case STDD_OPT_LEAF:
         if (value < 1 || value > 4096) throw ArgError("leaf size out of range");

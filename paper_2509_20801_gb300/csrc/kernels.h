@@ -108,6 +108,34 @@ template <typename R> void launch_add_strip(const StripDev &s, int ny, const voi
 template <typename R> void launch_to_local(const double2 *t, void *tloc, int64_t n, cudaStream_t st);
 template <typename R> void launch_from_local(const void *tloc, double2 *z, int64_t n, cudaStream_t st);
 
+// ---- band space (band-space FGMRES): the interface bands as column
+// intervals iv[k] = (first column, width), element offsets off[k]; n
+// elements.  iv1 / off1 / n1: the same widened by one column each side.
+struct BandDev {
+  const int2 *iv;
+  const int64_t *off;
+  int niv;
+  int64_t n;
+  const int2 *iv1;
+  const int64_t *off1;
+  int niv1;
+  int64_t n1;
+};
+// every strip's owned part of the band vector s (zero elsewhere) into tloc
+template <typename R>
+void launch_restrict_band(const StripDev *strips_dev, int nsub, int64_t nloc_max, int ny, const int64_t *colband,
+                          const double2 *s, void *tloc, cudaStream_t st);
+// z = sum_k E_k local[k] on the widened band only
+template <typename R>
+void launch_synthesize_band(const StripDev *strips_dev, int nsub, int ny, const int *col_strip, const BandDev &b,
+                            const void *tloc, double2 *z, cudaStream_t st);
+// y = +-((A z)|band - sub) (sub: global or band vector, or null)
+void launch_stencil_band(const GridDev &g, const BandDev &b, const double2 *z, const double2 *sub, bool sub_global,
+                         bool neg, double2 *y, cudaStream_t st);
+void launch_vsub(const double2 *a, const double2 *b, double2 *r, int64_t n, cudaStream_t st);  // r = a - b
+void launch_band_gather(const BandDev &b, int ny, const double2 *x, double2 *y, cudaStream_t st);      // y = x|band
+void launch_band_scatter_add(const BandDev &b, int ny, const double2 *y, double2 *x, cudaStream_t st); // x += y
+
 // ---- Krylov kernels (kernels_krylov.cu), FP64 complex
 // partial[blk][i] = sum_g conj(V_i[g]) w[g], i < m; then h[i] = sum_blk partial.
 // With self_norm, h[m] = (||w||^2, 0) as well.

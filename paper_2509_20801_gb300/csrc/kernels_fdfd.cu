@@ -108,6 +108,98 @@ __global__ void __launch_bounds__(TPB) k_add_strip(StripDev s, int ny, const voi
     zs[l] = cadd(zs[l], to_d(t[l]));
 }
 
+// ---- band space: vectors on a union of column intervals (first column,
+// width); element bi of the band vector <-> global node, the interval found
+// by binary search over the element offsets
+__device__ __forceinline__ int64_t band_node(int64_t bi, const int2 *__restrict__ iv, const int64_t *__restrict__ off,
+                                           int niv, int ny) {
+  int lo = 0, hi = niv - 1;  // largest k with off[k] <= bi
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= bi) lo = mid;
+    else hi = mid - 1;
+  }
+  return (int64_t)iv[lo].x * ny + (bi - off[lo]);
+}
+
+// every strip's local source R_s^I G(s): the band vector s placed on its
+// columns (colband = band offset of a column's first element, -1 off the
+// band), kept on the strip's owned columns
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_restrict_band(const StripDev *__restrict__ strips, int ny,
+                                                       const int64_t *__restrict__ colband,
+                                                       const double2 *__restrict__ s, void *tloc) {
+  using C = typename CT<R>::T;
+  const StripDev st = strips[blockIdx.y];
+  const int64_t nl = (int64_t)(st.x1 - st.x0) * ny;
+  const int64_t lo = (int64_t)(st.c0 - st.x0) * ny, hi = (int64_t)(st.c1 - st.x0) * ny;
+  C *t = reinterpret_cast<C *>(tloc) + st.vec_off;
+  for (int64_t l = (int64_t)blockIdx.x * TPB + threadIdx.x; l < nl; l += (int64_t)gridDim.x * TPB) {
+    C v = czero<C>();
+    if (l >= lo && l < hi) {
+      const int col = st.x0 + (int)(l / ny);
+      const int64_t cb = colband[col];
+      if (cb >= 0) v = to_c(s[cb + l % ny], C());
+    }
+    t[l] = v;
+  }
+}
+
+// z = sum_k E_k local[k] on the band's columns widened by one (the nodes the
+// stencil on the band reads), gather form as k_synthesize
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_synthesize_band(const StripDev *__restrict__ strips, int nsub, int ny,
+                                                         const int *__restrict__ col_strip, const int2 *__restrict__ iv,
+                                                         const int64_t *__restrict__ off, int niv, int64_t nb,
+                                                         const void *tloc, double2 *__restrict__ z) {
+  using C = typename CT<R>::T;
+  const C *t = reinterpret_cast<const C *>(tloc);
+  for (int64_t bi = (int64_t)blockIdx.x * TPB + threadIdx.x; bi < nb; bi += (int64_t)gridDim.x * TPB) {
+    const int64_t g = band_node(bi, iv, off, niv, ny);
+    const int i = (int)(g / ny);
+    const int k = col_strip[i];
+    double2 acc = make_double2(0.0, 0.0);
+    for (int kk = max(0, k - 1); kk <= min(nsub - 1, k + 1); ++kk) {
+      const StripDev s = strips[kk];
+      if (i >= s.x0 && i < s.x1) acc = cadd(acc, to_d(t[s.vec_off + g - (int64_t)s.x0 * ny]));
+    }
+    z[g] = acc;
+  }
+}
+
+// y[bi] = +-((A z)(g) - (sub ? sub[g or bi] : 0)) on the band: sub_global
+// selects whether sub is a global (1) or a band (0) vector, neg the sign
+__global__ void __launch_bounds__(TPB) k_stencil_band(GridDev g, const int2 *__restrict__ iv,
+                                                      const int64_t *__restrict__ off, int niv, int64_t nb,
+                                                      const double2 *__restrict__ z, const double2 *__restrict__ sub,
+                                                      int sub_global, int neg, double2 *__restrict__ y) {
+  for (int64_t bi = (int64_t)blockIdx.x * TPB + threadIdx.x; bi < nb; bi += (int64_t)gridDim.x * TPB) {
+    const int64_t gi = band_node(bi, iv, off, niv, g.ny);
+    double2 v = apply_row(g, z, gi);
+    if (sub) v = csub(v, sub[sub_global ? gi : bi]);
+    if (neg) v = make_double2(-v.x, -v.y);
+    y[bi] = v;
+  }
+}
+
+// r = a - b (band vectors)
+__global__ void __launch_bounds__(TPB) k_vsub(const double2 *__restrict__ a, const double2 *__restrict__ b,
+                                              double2 *__restrict__ r, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TPB)
+    r[i] = csub(a[i], b[i]);
+}
+
+// band <-> global: y[bi] = x[g] (gather), or x[g] += y[bi] (scatter-add)
+__global__ void __launch_bounds__(TPB) k_band_copy(const int2 *__restrict__ iv, const int64_t *__restrict__ off,
+                                                   int niv, int64_t nb, int ny, double2 *__restrict__ x,
+                                                   double2 *__restrict__ y, int to_band) {
+  for (int64_t bi = (int64_t)blockIdx.x * TPB + threadIdx.x; bi < nb; bi += (int64_t)gridDim.x * TPB) {
+    const int64_t gi = band_node(bi, iv, off, niv, ny);
+    if (to_band) y[bi] = x[gi];
+    else x[gi] = cadd(x[gi], y[bi]);
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(TPB) k_to_local(const double2 *__restrict__ v, void *tloc, int64_t n) {
   using C = typename CT<R>::T;
@@ -223,6 +315,43 @@ template void launch_restrict_residual_strip<float>(const GridDev &, const Strip
                                                     const double2 *, void *, cudaStream_t);
 template void launch_add_strip<double>(const StripDev &, int, const void *, double2 *, cudaStream_t);
 template void launch_add_strip<float>(const StripDev &, int, const void *, double2 *, cudaStream_t);
+
+template <typename R>
+void launch_restrict_band(const StripDev *strips_dev, int nsub, int64_t nloc_max, int ny, const int64_t *colband,
+                          const double2 *s, void *tloc, cudaStream_t st) {
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((nloc_max + TPB - 1) / TPB, 152 * 4)), nsub);
+  k_restrict_band<R><<<grid, TPB, 0, st>>>(strips_dev, ny, colband, s, tloc);
+  count_launch();
+}
+template <typename R>
+void launch_synthesize_band(const StripDev *strips_dev, int nsub, int ny, const int *col_strip, const BandDev &b,
+                            const void *tloc, double2 *z, cudaStream_t st) {
+  k_synthesize_band<R><<<grid_for(b.n1), TPB, 0, st>>>(strips_dev, nsub, ny, col_strip, b.iv1, b.off1, b.niv1, b.n1,
+                                                        tloc, z);
+  count_launch();
+}
+void launch_stencil_band(const GridDev &g, const BandDev &b, const double2 *z, const double2 *sub, bool sub_global,
+                         bool neg, double2 *y, cudaStream_t st) {
+  k_stencil_band<<<grid_for(b.n), TPB, 0, st>>>(g, b.iv, b.off, b.niv, b.n, z, sub, sub_global ? 1 : 0, neg ? 1 : 0,
+                                                 y);
+  count_launch();
+}
+void launch_vsub(const double2 *a, const double2 *b, double2 *r, int64_t n, cudaStream_t st) {
+  k_vsub<<<grid_for(n), TPB, 0, st>>>(a, b, r, n);
+  count_launch();
+}
+void launch_band_gather(const BandDev &b, int ny, const double2 *x, double2 *y, cudaStream_t st) {
+  k_band_copy<<<grid_for(b.n), TPB, 0, st>>>(b.iv, b.off, b.niv, b.n, ny, const_cast<double2 *>(x), y, 1);
+  count_launch();
+}
+void launch_band_scatter_add(const BandDev &b, int ny, const double2 *y, double2 *x, cudaStream_t st) {
+  k_band_copy<<<grid_for(b.n), TPB, 0, st>>>(b.iv, b.off, b.niv, b.n, ny, x, const_cast<double2 *>(y), 0);
+  count_launch();
+}
+template void launch_restrict_band<double>(const StripDev *, int, int64_t, int, const int64_t *, const double2 *,
+                                           void *, cudaStream_t);
+template void launch_synthesize_band<double>(const StripDev *, int, int, const int *, const BandDev &, const void *,
+                                             double2 *, cudaStream_t);
 
 template void launch_restrict<double>(const StripDev *, int, int64_t, int, const int *, const double2 *, void *,
                                       cudaStream_t);

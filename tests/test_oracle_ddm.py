@@ -265,3 +265,49 @@ def test_red_black_groups_can_be_solved_together():
         z = z + sum(ddm.extend(k, ddm.local_solve(k, ddm.restrict_owned(k, r))) for k in range(colour, 6, 2))
     ref = ddm.apply_Minv_multiplicative(v, order="red-black")
     assert np.linalg.norm(z - ref) < 1e-12 * np.linalg.norm(ref)
+
+
+def _band_columns(ddm, nx):
+    """Interface bands: [c - e_l - 1, c + e_r + 1) around each interface c,
+    e_r / e_l the columns the neighbouring local boxes reach past it."""
+    cols = set()
+    for k in range(ddm.nsub - 1):
+        a, b = ddm.strips[k], ddm.strips[k + 1]
+        c = a.c1
+        cols.update(range(max(0, c - (c - b.x0) - 1), min(nx, c + (a.x1 - c) + 1)))
+    return sorted(cols)
+
+
+def test_band_space_system_gives_the_solution():
+    """T = A M^-1 - I maps into the interface bands, and with r0 = b - A x0
+    the band system (I + T_B) s = -(T r0)|_B gives x = x0 + M^-1 (r0 + s)
+    with A x = b (dense, on a small 4-strip problem)."""
+    w = W.random_medium(44, 10, ppw=20, seed=25, npml=3, nsub=4, overlap=2, interface_pml=3)
+    prob = Problem.from_workload(w)
+    ddm = DDM.from_workload(w, prob)
+    n, ny = prob.n, prob.ny
+    A = prob.A.toarray()
+    cols = _band_columns(ddm, prob.nx)
+    B = np.array([c * ny + j for c in cols for j in range(ny)])
+    off = np.setdiff1d(np.arange(n), B)
+    rng = np.random.default_rng(26)
+    for _ in range(3):
+        v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        Tv = A @ ddm.apply_Minv(v) - v
+        assert np.abs(Tv[off]).max() < 1e-11 * np.abs(Tv).max()
+    # the band system
+    b = w.b[0].ravel()
+    x0 = 1e-3 * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+    r0 = b - A @ x0
+    TB = np.zeros((len(B), len(B)), complex)
+    for i, bi in enumerate(B):
+        e = np.zeros(n, complex)
+        e[bi] = 1.0
+        TB[:, i] = (A @ ddm.apply_Minv(e) - e)[B]
+    f = -(A @ ddm.apply_Minv(r0) - r0)[B]
+    sB = np.linalg.solve(np.eye(len(B)) + TB, f)
+    s = np.zeros(n, complex)
+    s[B] = sB
+    x = x0 + ddm.apply_Minv(r0 + s)
+    assert np.linalg.norm(A @ x - b) < 1e-10 * np.linalg.norm(b)
+    assert np.linalg.norm(x - prob.solve(b)) < 1e-9 * np.linalg.norm(x)
