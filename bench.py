@@ -72,7 +72,7 @@ def parse():
                     help="metalens: 4096x1024, 16 strips (the benchmark); metalens-small: 1024x1024, 4 strips "
                          "(profiling captures); cylinder: 200x200, 2 strips")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per step (line sources)")
-    ap.add_argument("--band", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--band", type=int, default=1, choices=[0, 1],
                     help="1: band-space FGMRES (FP64 factors, additive order; same iterates, band-sized vectors)")
     ap.add_argument("--order", default="additive", choices=["additive", "multiplicative", "red-black"],
                     help="preconditioner order: additive (Algorithm 1, the benchmark), symmetric multiplicative, "
