@@ -40,7 +40,14 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor and tensor), NVIDIA's fi
 # capture of all its launches in one factorization of the benchmark workload
 # (summary in the named profile); used only while the kernel's source file
 # still has the recorded SHA-256, else the roofline's traffic is null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "mf_gj_update<double>": {
+        "bytes_per_unit": 75923110656 / 416732096864.0,  # DRAM bytes / algorithmic flops, 50 launches
+        "source": "paper_2509_20801_gb300/csrc/kernels_mf.cu",
+        "sha256": "44bdf97aba7a58306a6b5216dfa394c614951f77e0d93f01ab4c1be9771b1f3c",
+        "profile": "profiles/ncu_dram_mf_gj_update_fp64_metalens.md",
+    },
+}
 
 
 def ncu_traffic(kernel, units_per_launch):
@@ -72,6 +79,7 @@ def parse():
                     help="metalens: 4096x1024, 16 strips (the benchmark); metalens-small: 1024x1024, 4 strips "
                          "(profiling captures); cylinder: 200x200, 2 strips")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per step (line sources)")
+    ap.add_argument("--leaf", type=int, default=16, help="nested-dissection leaf size (nodes)")
     ap.add_argument("--band", type=int, default=1, choices=[0, 1],
                     help="1: band-space FGMRES (FP64 factors, additive order; same iterates, band-sized vectors)")
     ap.add_argument("--order", default="additive", choices=["additive", "multiplicative", "red-black"],
@@ -271,6 +279,8 @@ def run_ours(args, rank, world, local_rank):
         sv = S.Solver.from_workload(w, eps=eps_d, precision=p, device=local_rank, stream=stream.cuda_stream)
         order = order or args.order
         S.stdd_set_option(sv.ctx, S.STDD_OPT_ORDER, orders[order])
+        if args.leaf != 16:
+            S.stdd_set_option(sv.ctx, S.STDD_OPT_LEAF, args.leaf)
         band = args.band if band is None else band
         S.stdd_set_option(sv.ctx, S.STDD_OPT_BAND, 1 if (band and p == S.STDD_PREC_FP64 and order == "additive") else 0)
         return sv
@@ -433,7 +443,7 @@ def run_ours(args, rank, world, local_rank):
                   S.STDD_PREC_C64_FP16: "c64-factors(fp16 tensor-core updates)+c128-krylov"}[prec],
         "data": "synthetic",
         "config": {"workload": workload_desc(w), "precision": args.precision, "order": args.order,
-                   "krylov_space": "band" if args.band else "full", "rtol": RTOL,
+                   "krylov_space": "band" if args.band else "full", "leaf": args.leaf, "rtol": RTOL,
                    "restart": RESTART, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (factors %.1f GB, Krylov basis %.1f GB)"
                          % (E * elem / 1e9, (2 * RESTART + 1) * w.n * 16 / 1e9)},
