@@ -357,7 +357,7 @@ struct stdd_ctx {
     return stdd::BandDev{d_band_iv.as<int2>(), d_band_off.as<int64_t>(), (int)band_iv.size(), band_n,
                          d_band_iv1.as<int2>(), d_band_off1.as<int64_t>(), (int)band_iv1.size(), band_n1};
   }
-  void solve_levels_band(int nr);
+  template <typename R> void solve_levels_band(int nr);
   void enqueue_op_band(const std::vector<const double2 *> &ss, const std::vector<double2 *> &ys);
   void apply_op_band(const std::vector<const double2 *> &ss, const std::vector<double2 *> &ys);
   void clear_graphs() {
@@ -932,19 +932,19 @@ void stdd_ctx::build_band() {
 // writes zeros where a subtree has no source), the upward GEMVs of the
 // fronts with sources in their subtree, the downward ones of the fronts the
 // widened band needs.
-void stdd_ctx::solve_levels_band(int nr) {
+template <typename R> void stdd_ctx::solve_levels_band(int nr) {
   ensure_solve_buffers(nr);
   const int2 *items = d_items_band.as<int2>();
   for (int L = depth - 1; L >= 0; --L) {
     const LevelInfo &li = levels[L];
-    stdd::mf_up_gather_level<double>(mf_args(L & 1, true), li, nr, nloc, stream);
-    stdd::mf_up_level<double>(mf_args(L & 1, true), items + lvl_bup_off[L], lvl_bup_n[L], li.rows_up, li.split_up,
-                              nr, nloc, stream);
+    stdd::mf_up_gather_level<R>(mf_args(L & 1, true), li, nr, nloc, stream);
+    stdd::mf_up_level<R>(mf_args(L & 1, true), items + lvl_bup_off[L], lvl_bup_n[L], li.rows_up, li.split_up, nr,
+                         nloc, stream);
   }
   for (int L = 0; L < depth; ++L) {
     const LevelInfo &li = levels[L];
-    stdd::mf_down_level<double>(mf_args(L & 1, true), items + lvl_bdown_off[L], lvl_bdown_n[L], li.rows_down,
-                                li.split_down, nr, nloc, stream);
+    stdd::mf_down_level<R>(mf_args(L & 1, true), items + lvl_bdown_off[L], lvl_bdown_n[L], li.rows_down,
+                           li.split_down, nr, nloc, stream);
   }
   CK(cudaGetLastError());
 }
@@ -956,14 +956,25 @@ void stdd_ctx::enqueue_op_band(const std::vector<const double2 *> &ss, const std
   const size_t E = elem();
   const stdd::BandDev bd = band_dev();
   auto slot = [&](int i) { return static_cast<void *>(d_tloc.as<char>() + (size_t)i * nloc * E); };
-  for (int i = 0; i < na; ++i)
-    stdd::launch_restrict_band<double>(d_strips.as<StripDev>(), nsub, nloc_max, ny, d_colband.as<int64_t>(), ss[i],
-                                       slot(i), stream);
-  solve_levels_band(na);
+  const bool fp64 = prec == STDD_PREC_FP64;
+  for (int i = 0; i < na; ++i) {
+    if (fp64)
+      stdd::launch_restrict_band<double>(d_strips.as<StripDev>(), nsub, nloc_max, ny, d_colband.as<int64_t>(), ss[i],
+                                         slot(i), stream);
+    else
+      stdd::launch_restrict_band<float>(d_strips.as<StripDev>(), nsub, nloc_max, ny, d_colband.as<int64_t>(), ss[i],
+                                        slot(i), stream);
+  }
+  if (fp64) solve_levels_band<double>(na);
+  else solve_levels_band<float>(na);
   for (int i = 0; i < na; ++i) {
     double2 *zg = d_Z.as<double2>() + (int64_t)i * N();
-    stdd::launch_synthesize_band<double>(d_strips.as<StripDev>(), nsub, ny, d_colstrip.as<int>(), bd, slot(i), zg,
-                                         stream);
+    if (fp64)
+      stdd::launch_synthesize_band<double>(d_strips.as<StripDev>(), nsub, ny, d_colstrip.as<int>(), bd, slot(i), zg,
+                                           stream);
+    else
+      stdd::launch_synthesize_band<float>(d_strips.as<StripDev>(), nsub, ny, d_colstrip.as<int>(), bd, slot(i), zg,
+                                          stream);
     stdd::launch_stencil_band(grid(), bd, zg, nullptr, false, false, ys[i], stream);
   }
   CK(cudaGetLastError());
@@ -1152,14 +1163,18 @@ double dev_norm(double2 *x, int64_t n, DBuf &part, DBuf &nrm, cudaStream_t st) {
 // one shrank ||w|| below 1/sqrt(2) of its value (Daniel-Gragg-Kaufman-
 // Stewart); Givens rotations and the small triangular solves on the host.
 // d_x holds the initial guesses on entry and the iterates on exit.
-// Band mode (STDD_OPT_BAND; FP64 factors, additive order): with
-// r0 = b - A x0 and T = A M^-1 - I, whose range is the interface bands, the
-// right-preconditioned iterate x = x0 + M^-1 (r0 + s) has the residual
-// b - A x = -(T r0 + (I + T) s) on the bands and zero elsewhere, so GMRES
-// runs on the band system (I + T) s = -T r0 with band-sized vectors and
-// partial sweeps; its residuals are the true ones.  One full application
-// before (for T r0) and one after (for x); the first counts as an
-// iteration.
+// Band mode (STDD_OPT_BAND, additive order): with r0 = b - A x0 and
+// T = A M^-1 - I, whose range is the interface bands when the local solves
+// are exact, the right-preconditioned iterate x = x0 + M^-1 (r0 + s) has the
+// residual b - A x = -(T r0 + (I + T) s) on the bands and zero elsewhere, so
+// GMRES runs on the band system (I + T) s = -T r0 with band-sized vectors
+// and partial sweeps.  One full application before (for T r0, counted as an
+// iteration) and one after (for x).  Each such cycle ends with the true
+// residual of the new x; with FP64 factors it equals the band residual and
+// one cycle suffices, with complex64 factors the local solves leave an error
+// of their own precision off the bands, so the cycle stops early (band
+// residual 1e-5 of the cycle's start) and cycles repeat from the new x
+// (iterative refinement) until the true residual reaches rtol.
 void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
   const int m = o.restart, nq = nrhs;
   bool band = use_band;
@@ -1189,7 +1204,7 @@ void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
   struct St {
     std::vector<cd> H, g, sn, hv;
     std::vector<double> cs;
-    double bnorm = 0, nrm2 = 0, res = 0;
+    double bnorm = 0, nrm2 = 0, res = 0, tgt = 0;  // tgt: absolute residual target of the iteration
     int its = 0, reorth = 0, k = 0;
     bool done = false;
   };
@@ -1203,37 +1218,53 @@ void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
     t.hv.assign(2 * (m + 2), 0);
     const double2 *b = d_b.as<double2>() + (int64_t)q * NN;
     t.bnorm = dev_norm(const_cast<double2 *>(b), NN, d_part, d_nrm, stream);
+    t.tgt = o.rtol * t.bnorm;
     if (t.bnorm == 0) {
       CK(cudaMemsetAsync(X + (int64_t)q * NN, 0, NN * sizeof(double2), stream));
       history[q].push_back(0.0);
       t.done = true;
     }
   }
+  const bool exact = prec == STDD_PREC_FP64;
+  std::vector<char> s_zero(nq, 1);
+  for (int cycle = 0;; ++cycle) {
+  std::vector<int> cyc;  // right-hand sides iterating in this band cycle
   if (band) {
-    // r0 = b - A x0 (in the V storage), z = M^-1 r0 (in Z), f = (r0 - A z)|band
+    // true residual r0 = b - A x (in the V storage); if not yet at rtol:
+    // z = M^-1 r0 (in Z), f = (r0 - A z)|band, s = 0
     std::vector<const double2 *> rs;
     std::vector<double2 *> zs;
-    std::vector<int> qs;
     for (int q = 0; q < nq; ++q) {
-      if (S[q].done) continue;
+      St &t = S[q];
+      if (t.done) continue;
       double2 *r0 = Vb + (int64_t)q * NN;
       stdd::launch_residual(grid(), d_b.as<double2>() + (int64_t)q * NN, X + (int64_t)q * NN, r0, stream);
-      history[q].push_back(dev_norm(r0, NN, d_part, d_nrm, stream) / S[q].bnorm);
+      const double rn = dev_norm(r0, NN, d_part, d_nrm, stream) / t.bnorm;
+      history[q].push_back(rn);
+      t.res = rn;
+      if (!std::isfinite(rn)) throw std::range_error("non-finite residual");
+      if (rn <= o.rtol || t.its >= o.maxit) {
+        t.done = true;
+        continue;
+      }
       rs.push_back(r0);
       zs.push_back(Zb + (int64_t)q * NN);
-      qs.push_back(q);
+      cyc.push_back(q);
     }
-    if (!qs.empty()) apply_minv_multi(rs, zs);
+    if (cyc.empty()) break;
+    apply_minv_multi(rs, zs);
     const stdd::BandDev bd = band_dev();
-    for (size_t i = 0; i < qs.size(); ++i) {
-      const int q = qs[i];
+    for (size_t i = 0; i < cyc.size(); ++i) {
+      const int q = cyc[i];
+      St &t = S[q];
       stdd::launch_stencil_band(grid(), bd, zs[i], rs[i], true, true, FB(q), stream);
       CK(cudaMemsetAsync(SB(q), 0, std::max<int64_t>(1, n) * sizeof(double2), stream));
-      history[q].push_back(dev_norm(FB(q), n, d_part, d_nrm, stream) / S[q].bnorm);
-      S[q].its = 1;
+      history[q].push_back(dev_norm(FB(q), n, d_part, d_nrm, stream) / t.bnorm);
+      t.its += 1;
+      t.tgt = exact ? o.rtol * t.bnorm : std::max(o.rtol * t.bnorm, 1e-5 * t.res * t.bnorm);
+      s_zero[q] = 1;
     }
   }
-  std::vector<char> s_zero(nq, 1);
   while (true) {
     // restart cycle: true residuals, first basis vectors
     std::vector<int> act;
@@ -1257,7 +1288,7 @@ void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
       if (history[q].empty()) history[q].push_back(beta / t.bnorm);
       t.res = beta / t.bnorm;
       if (!std::isfinite(beta)) throw std::range_error("non-finite residual");
-      if (t.res <= o.rtol || t.its >= o.maxit) {
+      if (beta <= t.tgt || t.its >= o.maxit) {
         t.done = true;
         continue;
       }
@@ -1341,7 +1372,7 @@ void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
         if (!std::isfinite(est)) throw std::range_error("non-finite residual estimate");
         const bool breakdown = !(hn > 0) || std::abs(hjj) == 0;
         if (!breakdown) stdd::launch_scale(V(q, j + 1), nrmq(q), V(q, j + 1), n, stream);
-        if (!(est <= o.rtol || t.its >= o.maxit || breakdown)) next.push_back(q);
+        if (!(est * t.bnorm <= t.tgt || t.its >= o.maxit || breakdown)) next.push_back(q);
       }
       inner.swap(next);
     }
@@ -1364,25 +1395,26 @@ void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
     }
     CK(cudaStreamSynchronize(stream));
   }
-  if (band) {
-    // x = x0 + M^-1 (r0 + s): r0 again (in V storage), plus the band s
+  if (!band) break;
+  {
+    // x = x + M^-1 (r0 + s): r0 again (in V storage), plus the band s
     std::vector<const double2 *> rs;
     std::vector<double2 *> zs;
-    std::vector<int> qs;
     const stdd::BandDev bd = band_dev();
-    for (int q = 0; q < nq; ++q) {
-      if (S[q].bnorm == 0) continue;
+    for (int q : cyc) {
       double2 *r0 = Vb + (int64_t)q * NN;
       stdd::launch_residual(grid(), d_b.as<double2>() + (int64_t)q * NN, X + (int64_t)q * NN, r0, stream);
-      if (n > 0) stdd::launch_band_scatter_add(bd, ny, SB(q), r0, stream);
+      stdd::launch_band_scatter_add(bd, ny, SB(q), r0, stream);
       rs.push_back(r0);
       zs.push_back(Zb + (int64_t)q * NN);
-      qs.push_back(q);
     }
-    if (!qs.empty()) apply_minv_multi(rs, zs);
-    for (size_t i = 0; i < qs.size(); ++i) stdd::nn_zadd(zs[i], X + (int64_t)qs[i] * NN, NN, stream);
+    apply_minv_multi(rs, zs);
+    for (size_t i = 0; i < cyc.size(); ++i) stdd::nn_zadd(zs[i], X + (int64_t)cyc[i] * NN, NN, stream);
     CK(cudaStreamSynchronize(stream));
+    // the next cycle starts from the true residual of the new x
+    for (int q : cyc) S[q].done = false;
   }
+  }  // cycles
   last_noconv = false;
   for (int q = 0; q < nq; ++q)
     if (!(S[q].res <= o.rtol)) last_noconv = true;
@@ -1701,8 +1733,8 @@ stdd_status stdd_solve(stdd_ctx *c, const stdd_solve_opts *o, double *x_out, int
     if (o->restart < 1 || o->restart > 500 || o->maxit < 0 || !(o->rtol >= 0)) throw ArgError("bad solve options");
     if (o->x0_mode == STDD_X0_USER && !o->x0) throw ArgError("x0 missing");
     if (o->x0_mode < STDD_X0_ZERO || o->x0_mode > STDD_X0_LEARNED) throw ArgError("bad x0_mode");
-    if (c->use_band && !o->paper_richardson && (c->prec != STDD_PREC_FP64 || c->order != 0))
-      throw ArgError("band-space FGMRES needs FP64 factors and the additive order");
+    if (c->use_band && !o->paper_richardson && c->order != 0)
+      throw ArgError("band-space FGMRES needs the additive order");
     const int64_t n = c->N();
     c->history.assign(c->nrhs, {});
     c->lg_raw.assign(c->nrhs, 0.0);

@@ -350,8 +350,12 @@ void launch_band_scatter_add(const BandDev &b, int ny, const double2 *y, double2
 }
 template void launch_restrict_band<double>(const StripDev *, int, int64_t, int, const int64_t *, const double2 *,
                                            void *, cudaStream_t);
+template void launch_restrict_band<float>(const StripDev *, int, int64_t, int, const int64_t *, const double2 *,
+                                          void *, cudaStream_t);
 template void launch_synthesize_band<double>(const StripDev *, int, int, const int *, const BandDev &, const void *,
                                              double2 *, cudaStream_t);
+template void launch_synthesize_band<float>(const StripDev *, int, int, const int *, const BandDev &, const void *,
+                                            double2 *, cudaStream_t);
 
 template void launch_restrict<double>(const StripDev *, int, int64_t, int, const int *, const double2 *, void *,
                                       cudaStream_t);
