@@ -281,18 +281,14 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     x = x0 + M^-1 (r0 + s).  Krylov vectors hold only the
  *                     band columns, and each band application of M^-1 skips
  *                     the subtrees with no band sources (going up) and the
- *                     fronts off the band (coming down).  With FP64 factors
- *                     the band residuals are the true residuals (the local
- *                     solves are exact); with complex64 factors the local
- *                     solves leave an error of their precision off the
- *                     bands, so each band solve stops at 1e-5 of its starting
- *                     residual and is repeated from the new iterate until
- *                     the true residual reaches rtol (iterative refinement).
- *                     Each band solve costs one full application before it
- *                     (counted as an iteration) and one after; the residual
- *                     history records the true residual at the start of each
- *                     and at the end.  Needs the additive order (else
- *                     stdd_solve returns STDD_EINVAL). */
+ *                     fronts off the band (coming down).  Its residuals are
+ *                     the true residuals because the local solves are exact,
+ *                     so it needs FP64 factors and the additive order (else
+ *                     stdd_solve returns STDD_EINVAL): complex64 local solves
+ *                     leave too large an error off the bands.  It costs one
+ *                     full application before the iteration (counted as the
+ *                     first iteration) and one after; the residual history
+ *                     ends with the true residual of the returned field. */
 enum { STDD_OPT_GRAPHS = 1, STDD_OPT_AUTOTUNE = 2, STDD_OPT_LEAF = 3, STDD_OPT_ORDER = 4, STDD_OPT_BAND = 5 };
 stdd_status stdd_set_option(stdd_ctx *ctx, int option, int value);
 stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);

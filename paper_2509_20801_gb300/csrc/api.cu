@@ -1169,12 +1169,10 @@ double dev_norm(double2 *x, int64_t n, DBuf &part, DBuf &nrm, cudaStream_t st) {
 // residual b - A x = -(T r0 + (I + T) s) on the bands and zero elsewhere, so
 // GMRES runs on the band system (I + T) s = -T r0 with band-sized vectors
 // and partial sweeps.  One full application before (for T r0, counted as an
-// iteration) and one after (for x).  Each such cycle ends with the true
-// residual of the new x; with FP64 factors it equals the band residual and
-// one cycle suffices, with complex64 factors the local solves leave an error
-// of their own precision off the bands, so the cycle stops early (band
-// residual 1e-5 of the cycle's start) and cycles repeat from the new x
-// (iterative refinement) until the true residual reaches rtol.
+// iteration) and one after (for x).  The cycle ends with the true residual
+// of the new x, which equals the band residual up to rounding (FP64 local
+// solves); should rounding leave it above rtol, another cycle starts from
+// the new x.
 void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
   const int m = o.restart, nq = nrhs;
   bool band = use_band;
@@ -1225,7 +1223,6 @@ void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
       t.done = true;
     }
   }
-  const bool exact = prec == STDD_PREC_FP64;
   std::vector<char> s_zero(nq, 1);
   for (int cycle = 0;; ++cycle) {
   std::vector<int> cyc;  // right-hand sides iterating in this band cycle
@@ -1261,7 +1258,7 @@ void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
       CK(cudaMemsetAsync(SB(q), 0, std::max<int64_t>(1, n) * sizeof(double2), stream));
       history[q].push_back(dev_norm(FB(q), n, d_part, d_nrm, stream) / t.bnorm);
       t.its += 1;
-      t.tgt = exact ? o.rtol * t.bnorm : std::max(o.rtol * t.bnorm, 1e-5 * t.res * t.bnorm);
+      t.tgt = o.rtol * t.bnorm;
       s_zero[q] = 1;
     }
   }
@@ -1733,8 +1730,8 @@ stdd_status stdd_solve(stdd_ctx *c, const stdd_solve_opts *o, double *x_out, int
     if (o->restart < 1 || o->restart > 500 || o->maxit < 0 || !(o->rtol >= 0)) throw ArgError("bad solve options");
     if (o->x0_mode == STDD_X0_USER && !o->x0) throw ArgError("x0 missing");
     if (o->x0_mode < STDD_X0_ZERO || o->x0_mode > STDD_X0_LEARNED) throw ArgError("bad x0_mode");
-    if (c->use_band && !o->paper_richardson && c->order != 0)
-      throw ArgError("band-space FGMRES needs the additive order");
+    if (c->use_band && !o->paper_richardson && (c->prec != STDD_PREC_FP64 || c->order != 0))
+      throw ArgError("band-space FGMRES needs FP64 factors and the additive order");
     const int64_t n = c->N();
     c->history.assign(c->nrhs, {});
     c->lg_raw.assign(c->nrhs, 0.0);

