@@ -1,0 +1,104 @@
+"""The batched uneven workload: many seeded ellipse geometries of different
+sizes, each with several point sources, solved one geometry after another on
+one stream (within a geometry the kernels are batched over all strips, fronts
+and right-hand sides and the preconditioner is replayed as a CUDA graph).
+
+Geometry g uses seed 3 * 1_000_000 + g; its size is drawn (seed 3) from the
+given shapes, its strips from [2, min(8, nx / 128)].  Per geometry: factor and
+solve times (CUDA events), iterations, and the true residual of every field
+(library residual call).  The summary reports the throughput over the whole
+batch, MDoF/s = sum of nx * ny * nrhs / total time.
+
+    python -m paper_2509_20801_gb300.batched [--count 48] [--nrhs 8] [--precision c64]
+        [--order additive|multiplicative|red-black] [--restart m] [--maxit k]
+"""
+from __future__ import annotations
+
+import json
+import sys
+import time
+
+import numpy as np
+
+from . import binding as _b
+
+SHAPES = ((256, 256), (512, 512), (1024, 512), (2048, 512), (2048, 1024))
+PRECISIONS = {"fp64": _b.STDD_PREC_FP64, "c64": _b.STDD_PREC_C64}
+ORDERS = {"additive": 0, "multiplicative": 1, "red-black": 2}
+
+
+def geometries(count=48, nrhs=8, shapes=SHAPES, seed=3):
+    import workloads as W
+    rng = np.random.default_rng(seed)
+    picks = rng.integers(0, len(shapes), count)
+    return [W.ellipses(shapes[k][0], shapes[k][1], seed=seed * 1_000_000 + g, nrhs=nrhs, sources="point")
+            for g, k in enumerate(picks)]
+
+
+def run(count=48, nrhs=8, precision="c64", rtol=1e-8, restart=30, maxit=1000, device=0, shapes=SHAPES,
+        out=None, log=None, order="additive"):
+    import torch
+    from . import Solver
+    dev = torch.device("cuda", device)
+    t0 = time.perf_counter()
+    ws = geometries(count, nrhs, shapes)
+    if log:
+        log(f"{len(ws)} geometries: {time.perf_counter() - t0:.1f} s")
+    rows = []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for g, w in enumerate(ws):
+        s = Solver.from_workload(w, eps=torch.from_numpy(w.eps_node).to(dev), precision=PRECISIONS[precision],
+                                 device=device)
+        _b.stdd_set_option(s.ctx, _b.STDD_OPT_ORDER, ORDERS[order])
+        try:
+            b = torch.from_numpy(w.b).to(dev)
+            x = torch.empty_like(b)
+            torch.cuda.synchronize(dev)
+            ev[0].record()
+            s.factor()
+            ev[1].record()
+            s.set_sources(b)
+            st = s.solve(x, restart=restart, rtol=rtol, maxit=maxit, allow_noconv=True)
+            ev[2].record()
+            torch.cuda.synchronize(dev)
+            r = torch.empty(w.n, dtype=torch.complex128, device=dev)
+            res = [_b.stdd_residual(s.ctx, x[q].reshape(-1).contiguous(), b[q].reshape(-1).contiguous(), r)
+                   for q in range(w.nrhs)]
+            its = [len(s.history(q)) - 1 for q in range(w.nrhs)]
+            row = dict(g=g, nx=w.nx, ny=w.ny, nsub=w.nsub, nrhs=w.nrhs, factor_ms=ev[0].elapsed_time(ev[1]),
+                       solve_ms=ev[1].elapsed_time(ev[2]), iterations_max=max(its),
+                       iterations_mean=float(np.mean(its)), converged=st == _b.STDD_OK,
+                       max_true_residual=float(max(res)))
+        finally:
+            s.close()
+        rows.append(row)
+        if out:
+            print(json.dumps(row), file=out, flush=True)
+    dof = sum(r["nx"] * r["ny"] * r["nrhs"] for r in rows)
+    tms = sum(r["factor_ms"] + r["solve_ms"] for r in rows)
+    summary = dict(geometries=len(rows), rhs_per_geometry=nrhs, precision=precision, order=order, restart=restart,
+                   maxit=maxit, rtol=rtol,
+                   unknowns=sum(r["nx"] * r["ny"] for r in rows), dof_rhs=dof, total_ms=tms,
+                   factor_ms=sum(r["factor_ms"] for r in rows), solve_ms=sum(r["solve_ms"] for r in rows),
+                   mdof_per_s=dof / (tms * 1e-3) / 1e6, all_converged=all(r["converged"] for r in rows),
+                   max_true_residual=max(r["max_true_residual"] for r in rows),
+                   iterations_mean=float(np.mean([r["iterations_mean"] for r in rows])))
+    return rows, summary
+
+
+if __name__ == "__main__":
+    import argparse
+    import os
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    ap = argparse.ArgumentParser(description="batched uneven workload: many geometries, several sources each")
+    ap.add_argument("--count", type=int, default=48)
+    ap.add_argument("--nrhs", type=int, default=8)
+    ap.add_argument("--precision", default="c64", choices=sorted(PRECISIONS))
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--order", default="additive", choices=sorted(ORDERS))
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--maxit", type=int, default=1000)
+    a = ap.parse_args()
+    _, summ = run(a.count, a.nrhs, a.precision, a.rtol, a.restart, a.maxit, out=sys.stderr,
+                  log=lambda m: print(m, file=sys.stderr, flush=True), order=a.order)
+    print(json.dumps(summ))
