@@ -193,8 +193,12 @@ int nn_tc_npad(int Cout);
 int nn_tc_nchunks(int Cin);
 int64_t nn_tc_packed_elems(int Cin, int Cout);
 void nn_pack_weights(const float *w, int CinL, int CoutL, bool flip, uint16_t *out, cudaStream_t st);
+// part: scratch for split-K partial sums (nn_tc_ksplit(...) x N x Cout x H x W
+// floats), or null for no split; small images split their input channels
+// over several CTAs and a second kernel adds the slices in fixed order
+int nn_tc_ksplit(int Cin, int Cout, int N, int H, int W);
 void nn_conv_tc(const float *in, int Cin, const uint16_t *wp, const float *bias, float *out, int Cout, int N, int H,
-                int W, bool relu, int *flag, cudaStream_t st);
+                int W, bool relu, int *flag, cudaStream_t st, float *part);
 
 }  // namespace stdd
 

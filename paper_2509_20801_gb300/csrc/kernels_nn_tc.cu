@@ -35,6 +35,7 @@ constexpr int CT_HP = CT_T + 2;                 // halo pitch (pixels)
 constexpr int CT_PLANE = CT_HP * CT_HP * 16;    // one 8-channel plane: 5184 B
 constexpr int CT_ACT = 2 * CT_PLANE;            // one stage of activations
 constexpr long long CT_WAIT = 1ll << 22;
+constexpr int CT_ITEMS = (2 * CT_HP * CT_HP + 255) / 256;  // halo items per thread and chunk (3)
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
@@ -56,6 +57,7 @@ struct ConvTcArgs {
   float *out;
   int Cout, H, W, relu;
   int *flag;
+  float *part;    // split-K: partial sums [gridDim.z][N][Cout][H][W], or null
 };
 
 __global__ void __launch_bounds__(256) k_conv3x3_tc(ConvTcArgs a) {
@@ -70,6 +72,9 @@ __global__ void __launch_bounds__(256) k_conv3x3_tc(ConvTcArgs a) {
   const int tiles_x = (a.W + CT_T - 1) / CT_T;
   const int x0 = (blockIdx.x % tiles_x) * CT_T, y0 = (blockIdx.x / tiles_x) * CT_T;
   const int n = blockIdx.y;
+  // split-K: this CTA takes input-channel chunks [cb, ce)
+  const int cb = (int)((int64_t)blockIdx.z * a.nchunks / gridDim.z);
+  const int ce = (int)((int64_t)(blockIdx.z + 1) * a.nchunks / gridDim.z);
   const int cols = tmem_cols_for(a.Npad);
   const uint32_t bar0 = tcx::smem_u32(&bars[0]);
   auto bw = [&](int s) { return bar0 + 8u * (uint32_t)s; };        // weight copies landed
@@ -89,12 +94,13 @@ __global__ void __launch_bounds__(256) k_conv3x3_tc(ConvTcArgs a) {
   const float *inb = a.in + (int64_t)n * a.Cin * plane;
   bool ok = true;
   int issued = 0;   // chunks whose MMAs were committed
-  for (int c = 0; c < a.nchunks; ++c) {
-    const int s = c & 1;
+  for (int c = cb; c < ce; ++c) {
+    const int lc = c - cb;  // local chunk count: stages and barrier phases
+    const int s = lc & 1;
     uint8_t *act = act0 + s * CT_ACT;
     uint8_t *wst = wst0 + s * wbytes;
     // stage s is free once the MMAs of chunk c - 2 completed
-    if (c >= 2 && !tcx::mbar_wait(bm(s), ((c - 2) >> 1) & 1, CT_WAIT)) ok = false;
+    if (lc >= 2 && !tcx::mbar_wait(bm(s), ((lc - 2) >> 1) & 1, CT_WAIT)) ok = false;
     if (!__syncthreads_and(ok && !*abort_flag)) {
       ok = false;
       break;
@@ -103,27 +109,40 @@ __global__ void __launch_bounds__(256) k_conv3x3_tc(ConvTcArgs a) {
       tcx::mbar_expect_tx(bw(s), (uint32_t)wbytes);
       tcx::bulk_g2s(tcx::smem_u32(wst), a.wp + (size_t)c * (wbytes / 2), (uint32_t)wbytes, bw(s));
     }
-    // halo tile of 16 channels: items (plane cg, halo row, halo column)
-    for (int it = tid; it < 2 * CT_HP * CT_HP; it += 256) {
-      const int cg = it / (CT_HP * CT_HP), r = it % (CT_HP * CT_HP);
-      const int hr = r / CT_HP, hc = r % CT_HP;
-      const int y = y0 - 1 + hr, x = x0 - 1 + hc;
-      const bool in_img = y >= 0 && y < a.H && x >= 0 && x < a.W;
-      const int ci0 = c * 16 + cg * 8;
-      float v[8];
+    // halo tile of 16 channels: items (plane cg, halo row, halo column),
+    // at most CT_ITEMS per thread; every load of a thread is issued before
+    // any is converted, so their latencies overlap
+    {
+      float v[CT_ITEMS][8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        v[j] = (in_img && ci0 + j < a.Cin) ? inb[(int64_t)(ci0 + j) * plane + (int64_t)y * a.W + x] : 0.f;
-      *reinterpret_cast<uint4 *>(act + cg * CT_PLANE + (hr * CT_HP + hc) * 16) =
-          make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                     pack_bf16x2(v[6], v[7]));
+      for (int u = 0; u < CT_ITEMS; ++u) {
+        const int it = tid + u * 256;
+        const int cg = it / (CT_HP * CT_HP), r = it % (CT_HP * CT_HP);
+        const int y = y0 - 1 + r / CT_HP, x = x0 - 1 + r % CT_HP;
+        const bool ok_item = it < 2 * CT_HP * CT_HP && y >= 0 && y < a.H && x >= 0 && x < a.W;
+        const int ci0 = c * 16 + cg * 8;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          v[u][j] = (ok_item && ci0 + j < a.Cin) ? __ldg(inb + (int64_t)(ci0 + j) * plane + (int64_t)y * a.W + x)
+                                                 : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < CT_ITEMS; ++u) {
+        const int it = tid + u * 256;
+        if (it < 2 * CT_HP * CT_HP) {
+          const int cg = it / (CT_HP * CT_HP), r = it % (CT_HP * CT_HP);
+          *reinterpret_cast<uint4 *>(act + cg * CT_PLANE + r * 16) =
+              make_uint4(pack_bf16x2(v[u][0], v[u][1]), pack_bf16x2(v[u][2], v[u][3]),
+                         pack_bf16x2(v[u][4], v[u][5]), pack_bf16x2(v[u][6], v[u][7]));
+        }
+      }
     }
     tcx::fence_proxy_async();
     tcx::fence_before();
     __syncthreads();
     tcx::fence_after();
     if (tid == 0) {
-      if (tcx::mbar_wait(bw(s), (c >> 1) & 1, CT_WAIT)) {
+      if (tcx::mbar_wait(bw(s), (lc >> 1) & 1, CT_WAIT)) {
         const uint32_t a_base = tcx::smem_u32(act), b_base = tcx::smem_u32(wst);
 #pragma unroll 1
         for (int tap = 0; tap < 9; ++tap) {
@@ -133,17 +152,17 @@ __global__ void __launch_bounds__(256) k_conv3x3_tc(ConvTcArgs a) {
           for (int h = 0; h < 2; ++h) {
             const uint64_t adesc =
                 tcx::smem_desc(a_base + (ky * CT_HP + 8 * h + kx) * 16, CT_PLANE, CT_HP * 16);
-            tcx::mma_f16(tmem + (uint32_t)(h * a.Npad), adesc, bdesc, idesc, (c > 0 || tap > 0) ? 1u : 0u);
+            tcx::mma_f16(tmem + (uint32_t)(h * a.Npad), adesc, bdesc, idesc, (lc > 0 || tap > 0) ? 1u : 0u);
           }
         }
       } else {
         *abort_flag = 1;
         // the copy may still land: give it one more bounded wait
-        tcx::mbar_wait(bw(s), (c >> 1) & 1, CT_WAIT);
+        tcx::mbar_wait(bw(s), (lc >> 1) & 1, CT_WAIT);
       }
       tcx::mma_commit(bm(s));
     }
-    issued = c + 1;
+    issued = lc + 1;
   }
   // all MMAs done: the last commit covers every earlier one
   if (issued > 0) {
@@ -159,7 +178,9 @@ __global__ void __launch_bounds__(256) k_conv3x3_tc(ConvTcArgs a) {
     const int m = 32 * q + lane;
     const int y = y0 + (m >> 3), x = x0 + 8 * h + (m & 7);
     const bool store = y < a.H && x < a.W;
-    float *outp = a.out + (int64_t)n * a.Cout * plane + (int64_t)y * a.W + x;
+    const bool split = a.part != nullptr;
+    float *outp = (split ? a.part + (int64_t)blockIdx.z * gridDim.y * a.Cout * plane : a.out) +
+                  (int64_t)n * a.Cout * plane + (int64_t)y * a.W + x;
     for (int c0 = 0; c0 < a.Npad; c0 += 16) {
       uint32_t v[16];
       tcx::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * a.Npad + c0), v);
@@ -167,8 +188,11 @@ __global__ void __launch_bounds__(256) k_conv3x3_tc(ConvTcArgs a) {
       for (int u = 0; u < 16; ++u) {
         const int co = c0 + u;
         if (store && co < a.Cout) {
-          float r = __uint_as_float(v[u]) + (a.bias ? a.bias[co] : 0.f);
-          if (a.relu) r = fmaxf(r, 0.f);
+          float r = __uint_as_float(v[u]);
+          if (!split) {
+            r += a.bias ? a.bias[co] : 0.f;
+            if (a.relu) r = fmaxf(r, 0.f);
+          }
           outp[(int64_t)co * plane] = r;
         }
       }
@@ -179,6 +203,17 @@ __global__ void __launch_bounds__(256) k_conv3x3_tc(ConvTcArgs a) {
   tcx::fence_before();
   __syncthreads();
   if (warp == 0) tcx::tmem_dealloc(tmem, (uint32_t)cols);
+}
+
+// split-K epilogue: out = act(bias + sum over the slices, in slice order)
+__global__ void k_splitk_finish(const float *__restrict__ part, int ks, int64_t count, int64_t plane, int Cout,
+                                const float *__restrict__ bias, int relu, float *__restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    float r = 0.f;
+    for (int z = 0; z < ks; ++z) r += part[(int64_t)z * count + i];
+    if (bias) r += bias[(int)((i / plane) % Cout)];
+    out[i] = relu ? fmaxf(r, 0.f) : r;
+  }
 }
 
 // Pack one layer's weights for k_conv3x3_tc: element (chunk c, tap t, plane
@@ -224,8 +259,15 @@ void nn_pack_weights(const float *w, int CinL, int CoutL, bool flip, uint16_t *o
   count_launch();
 }
 
+int nn_tc_ksplit(int Cin, int Cout, int N, int H, int W) {
+  const int tiles = ((W + CT_T - 1) / CT_T) * ((H + CT_T - 1) / CT_T) * N;
+  const int nch = nn_tc_nchunks(Cin);
+  if (tiles >= 76 || nch < 2) return 1;  // half a wave or more: no split
+  return std::max(1, std::min(nch, 152 / tiles));
+}
+
 void nn_conv_tc(const float *in, int Cin, const uint16_t *wp, const float *bias, float *out, int Cout, int N, int H,
-                int W, bool relu, int *flag, cudaStream_t st) {
+                int W, bool relu, int *flag, cudaStream_t st, float *part) {
   ConvTcArgs a;
   a.in = in;
   a.Cin = Cin;
@@ -239,10 +281,19 @@ void nn_conv_tc(const float *in, int Cin, const uint16_t *wp, const float *bias,
   a.W = W;
   a.relu = relu ? 1 : 0;
   a.flag = flag;
+  a.part = nullptr;
   const int tiles = ((W + CT_T - 1) / CT_T) * ((H + CT_T - 1) / CT_T);
   const size_t smem = 2 * CT_ACT + 2 * 288 * (size_t)a.Npad + 64;
-  k_conv3x3_tc<<<dim3(tiles, N), 256, smem, st>>>(a);
+  const int ks = part ? nn_tc_ksplit(Cin, Cout, N, H, W) : 1;
+  a.part = ks > 1 ? part : nullptr;
+  k_conv3x3_tc<<<dim3(tiles, N, ks), 256, smem, st>>>(a);
   count_launch();
+  if (ks > 1) {
+    const int64_t count = (int64_t)N * Cout * H * W;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152 * 8));
+    k_splitk_finish<<<grid, 256, 0, st>>>(part, ks, count, (int64_t)H * W, Cout, bias, relu ? 1 : 0, out);
+    count_launch();
+  }
 }
 
 }  // namespace stdd

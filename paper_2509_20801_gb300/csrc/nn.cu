@@ -206,7 +206,7 @@ struct stdd_nn {
     if (mode == STDD_NN_TC) {
       const size_t i = layer_index(ly);
       stdd::nn_conv_tc(in, cin, packed + (flip ? pk_bwd[i] : pk_fwd[i]), flip ? nullptr : wb.p + ly.boff, out, cout,
-                       N, H, W, relu, d_flag, st);
+                       N, H, W, relu, d_flag, st, act["ksplit"].p);
     } else {
       stdd::nn_conv(in, cin, wb.p + ly.woff, flip ? nullptr : wb.p + ly.boff, out, cout, N, H, W, relu, flip, st);
     }
@@ -252,6 +252,29 @@ struct stdd_nn {
     act["t2"].alloc(big);
     act["gout"].alloc(sz(0, 2));
     act["gd"].alloc(big);
+    if (mode == STDD_NN_TC) {
+      // split-K scratch: the largest (slices x output) over every layer in
+      // both directions at its level's size
+      size_t need = 1;
+      auto take = [&](const Layer &ly, int l) {
+        const int h = H >> l, w = W >> l;
+        for (int flip = 0; flip < 2; ++flip) {
+          const int ci = flip ? ly.cout : ly.cin, co = flip ? ly.cin : ly.cout;
+          const size_t ks = (size_t)stdd::nn_tc_ksplit(ci, co, N, h, w);
+          if (ks > 1) need = std::max(need, ks * N * co * (size_t)h * w);
+        }
+      };
+      for (int l = 0; l < L; ++l) {
+        take(encA(l), l);
+        take(encB(l), l);
+        if (l < L - 1) {
+          take(decC(l), l);
+          take(decD(l), l);
+        }
+      }
+      take(outL(), 0);
+      act["ksplit"].alloc(need);
+    }
   }
 
 
