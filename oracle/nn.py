@@ -185,12 +185,15 @@ def backward(cache, gout, L):
     (the chain rule through forward() in reverse order)."""
     enc, dec, out_layer = cache["enc"], cache["dec"], cache["out_layer"]
     if cache.get("round_act"):
-        # tensor-core mode: the input-gradient convolution reads BF16 output
-        # gradients, the weight gradient the FP32 ones
+        # tensor-core mode: both gradient convolutions read BF16 output
+        # gradients; the weight gradient also reads the BF16-rounded layer
+        # input; the bias gradient sums the unrounded output gradients
         def conv3x3_backward(x, W, gout):
-            gx, _, _ = _conv_backward(x, W, bf16_round(gout))
-            _, gW, gb = _conv_backward(x, W, gout)
-            return gx, gW, gb
+            gr = bf16_round(gout)
+            gx, _, _ = _conv_backward(x, W, gr)
+            _, gW, _ = _conv_backward(bf16_round(x), W, gr)
+            return gx, gW, gout.sum(axis=(0, 2, 3))
+
     else:
         conv3x3_backward = _conv_backward
     grads = {}

@@ -197,6 +197,10 @@ void nn_pack_weights(const float *w, int CinL, int CoutL, bool flip, uint16_t *o
 // floats), or null for no split; small images split their input channels
 // over several CTAs and a second kernel adds the slices in fixed order
 int nn_tc_ksplit(int Cin, int Cout, int N, int H, int W);
+// weight gradient on the tensor cores (BF16 operands, FP32 accumulation):
+// gw += ..., gb += ... (accumulated with atomics: zero them first)
+void nn_conv_wgrad_tc(const float *in, int Cin, const float *gout, int Cout, int N, int H, int W, float *gw,
+                      float *gb, int *flag, cudaStream_t st);
 void nn_conv_tc(const float *in, int Cin, const uint16_t *wp, const float *bias, float *out, int Cout, int N, int H,
                 int W, bool relu, int *flag, cudaStream_t st, float *part);
 

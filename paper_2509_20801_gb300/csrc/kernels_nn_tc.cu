@@ -216,6 +216,166 @@ __global__ void k_splitk_finish(const float *__restrict__ part, int ks, int64_t 
   }
 }
 
+// ---- weight gradient on the tensor cores
+// gw[co][ci][t] += sum over pixels p of gout[co](p) in[ci](p + shift_t), one
+// GEMM per tap t = 3 ky + kx with M = 128 output channels, N = 32 input
+// channels, K = pixels.  A CTA walks a contiguous range of 64-pixel row
+// segments (image n, row y, columns x0 .. x0 + 63; past the row end zero):
+// the output-gradient segment is the A tile, and the three input rows
+// y - 1 .. y + 1 (with a one-pixel halo) are written straight into the nine
+// tap-shifted B tiles.  The nine accumulators (32 TMEM columns each) stay
+// in TMEM across the CTA's segments; the epilogue adds them to gw with FP32
+// atomics (CTAs split the pixels).  The bias gradient (sum of gout) is
+// taken from the FP32 values while staging, by the CTAs of the first input
+// channel tile.
+constexpr int WG_M = 128, WG_N = 32, WG_K = 64;
+constexpr int WG_A = WG_M * WG_K * 2;          // 16 KiB
+constexpr int WG_BT = WG_N * WG_K * 2;         // 4 KiB per tap
+constexpr int WG_STAGE = WG_A + 9 * WG_BT;     // 52 KiB
+constexpr int WG_SMEM = 2 * WG_STAGE + 64;
+
+// byte offset of (row, k) in a K-major tile of 64 K (core matrices 8 x 16 B)
+__device__ __forceinline__ uint32_t wg_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+struct WgradTcArgs {
+  const float *in, *gout;
+  int Cin, Cout, N, H, W;
+  float *gw, *gb;
+  int *flag;
+};
+
+__global__ void __launch_bounds__(256, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ float gbs[WG_M];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * WG_STAGE);  // mma[2]
+  uint32_t *tm = reinterpret_cast<uint32_t *>(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int co0 = blockIdx.x * WG_M, ci0 = blockIdx.y * WG_N;
+  const int spr = (a.W + WG_K - 1) / WG_K;
+  const int64_t total = (int64_t)a.N * a.H * spr;
+  const int64_t g0 = blockIdx.z * total / gridDim.z, g1 = (blockIdx.z + 1) * total / gridDim.z;
+  const bool do_bias = a.gb && blockIdx.y == 0;
+  const uint32_t bar0 = tcx::smem_u32(&bars[0]);
+  auto bm = [&](int st) { return bar0 + 8u * (uint32_t)st; };
+  if (warp == 0) tcx::tmem_alloc(tcx::smem_u32(tm), 512);
+  if (tid < WG_M) gbs[tid] = 0.f;
+  if (tid == 0) {
+    tcx::mbar_init(bm(0), 1);
+    tcx::mbar_init(bm(1), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  tcx::fence_before();
+  __syncthreads();
+  tcx::fence_after();
+  const uint32_t tmem = *tm;
+  const uint32_t idesc = tcx::instr_desc_f16(1, WG_M, WG_N);
+  const int64_t plane = (int64_t)a.H * a.W;
+  bool ok = true;
+  int issued = 0;
+  for (int64_t g = g0; g < g1; ++g) {
+    const int lc = (int)(g - g0), st = lc & 1;
+    uint8_t *As = sm + st * WG_STAGE, *Bs = As + WG_A;
+    if (lc >= 2 && !tcx::mbar_wait(bm(st), ((lc - 2) >> 1) & 1, CT_WAIT)) ok = false;
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    const int n = (int)(g / ((int64_t)a.H * spr));
+    const int rem = (int)(g % ((int64_t)a.H * spr));
+    const int y = rem / spr, x0 = (rem % spr) * WG_K;
+    // A: output gradient, items (group of 8 pixels, channel); a quarter
+    // warp stores 8 consecutive channels' 16-byte rows (one core matrix)
+    for (int it = tid; it < WG_M * (WG_K / 8); it += 256) {
+      const int co = it & (WG_M - 1), kg = it >> 7;
+      float v[8];
+      const bool cv = co0 + co < a.Cout;
+      const float *src = a.gout + ((int64_t)n * a.Cout + co0 + co) * plane + (int64_t)y * a.W;
+      float bsum = 0.f;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int x = x0 + kg * 8 + j;
+        v[j] = (cv && x < a.W) ? __ldg(src + x) : 0.f;
+        bsum += v[j];
+      }
+      if (do_bias && cv) atomicAdd(&gbs[co], bsum);
+      *reinterpret_cast<uint4 *>(As + wg_off(co, kg * 8)) =
+          make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                     pack_bf16x2(v[6], v[7]));
+    }
+    // B: items (input channel, row ky, group of 8 pixels); the ten input
+    // pixels x0 - 1 + 8 kg .. x0 + 8 kg + 8 of row y + ky - 1 give the
+    // group's 8 K elements of the three taps (ky, kx): element k = 8 kg + m
+    // of tap kx is pixel x0 + k + kx - 1, i.e. the (m + kx)-th loaded value
+    for (int it = tid; it < WG_N * 3 * (WG_K / 8); it += 256) {
+      const int ci = it & (WG_N - 1), r = it >> 5;
+      const int ky = r >> 3, kg = r & 7;
+      const int yy = y + ky - 1;
+      const bool rv = ci0 + ci < a.Cin && yy >= 0 && yy < a.H;
+      const float *src = a.in + ((int64_t)n * a.Cin + ci0 + ci) * plane + (int64_t)yy * a.W;
+      uint32_t hv[10];
+#pragma unroll
+      for (int j = 0; j < 10; ++j) {
+        const int xx = x0 - 1 + kg * 8 + j;
+        const float v = (rv && xx >= 0 && xx < a.W) ? __ldg(src + xx) : 0.f;
+        hv[j] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+      }
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx)
+        *reinterpret_cast<uint4 *>(Bs + (ky * 3 + kx) * WG_BT + wg_off(ci, kg * 8)) =
+            make_uint4(hv[kx] | (hv[kx + 1] << 16), hv[kx + 2] | (hv[kx + 3] << 16),
+                       hv[kx + 4] | (hv[kx + 5] << 16), hv[kx + 6] | (hv[kx + 7] << 16));
+    }
+    tcx::fence_proxy_async();
+    tcx::fence_before();
+    __syncthreads();
+    tcx::fence_after();
+    if (tid == 0) {
+      const uint32_t a_base = tcx::smem_u32(As), b_base = tcx::smem_u32(Bs);
+#pragma unroll 1
+      for (int t = 0; t < 9; ++t)
+#pragma unroll
+        for (int s4 = 0; s4 < WG_K / 16; ++s4)
+          tcx::mma_f16(tmem + (uint32_t)(t * WG_N), tcx::smem_desc(a_base + s4 * 256, 128, 1024),
+                       tcx::smem_desc(b_base + t * WG_BT + s4 * 256, 128, 1024), idesc,
+                       (lc > 0 || s4 > 0) ? 1u : 0u);
+      tcx::mma_commit(bm(st));
+    }
+    issued = lc + 1;
+  }
+  if (issued > 0) {
+    const int last = issued - 1;
+    if (!tcx::mbar_wait(bm(last & 1), (last >> 1) & 1, CT_WAIT)) ok = false;
+  }
+  ok = __syncthreads_and(ok);
+  tcx::fence_after();
+  if (ok && issued > 0) {
+    // warp w: TMEM lanes 32 (w % 4) .. (output channels), half w / 4 of
+    // the 9 x 32 columns
+    const int q = warp & 3, h = warp >> 2;
+    const int co = 32 * q + lane;
+    const bool cv = co0 + co < a.Cout;
+    for (int j = 0; j < 9; ++j) {
+      const int c0 = h * 144 + j * 16;
+      uint32_t v[16];
+      tcx::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int c = c0 + u, t = c >> 5, ci = c & 31;
+        if (cv && ci0 + ci < a.Cin)
+          atomicAdd(&a.gw[((int64_t)(co0 + co) * a.Cin + ci0 + ci) * 9 + t], __uint_as_float(v[u]));
+      }
+    }
+    if (do_bias && tid < WG_M && co0 + tid < a.Cout) atomicAdd(&a.gb[co0 + tid], gbs[tid]);
+  } else if (!ok && tid == 0) {
+    atomicOr(a.flag, 1);
+  }
+  tcx::fence_before();
+  __syncthreads();
+  if (warp == 0) tcx::tmem_dealloc(tmem, 512);
+}
+
 // Pack one layer's weights for k_conv3x3_tc: element (chunk c, tap t, plane
 // cg, n, j) is B(n, k = 16 c + 8 cg + j) of tap t.  Forward: B = w[n][k][t];
 // flipped (input gradient of the layer): B = w[k][n][8 - t].  Values are
@@ -248,7 +408,21 @@ int nn_tc_nchunks(int Cin) { return (Cin + 15) / 16; }
 int64_t nn_tc_packed_elems(int Cin, int Cout) { return (int64_t)nn_tc_nchunks(Cin) * 9 * 2 * nn_tc_npad(Cout) * 8; }
 
 cudaError_t nn_tc_setup() {
-  return cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * CT_ACT + 576 * 256 + 64);
+  const cudaError_t e =
+      cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * CT_ACT + 576 * 256 + 64);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_conv3x3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM);
+}
+
+void nn_conv_wgrad_tc(const float *in, int Cin, const float *gout, int Cout, int N, int H, int W, float *gw,
+                      float *gb, int *flag, cudaStream_t st) {
+  WgradTcArgs a{in, gout, Cin, Cout, N, H, W, gw, gb, flag};
+  const int cot = (Cout + WG_M - 1) / WG_M, cit = (Cin + WG_N - 1) / WG_N;
+  const int64_t segs = (int64_t)N * H * ((W + WG_K - 1) / WG_K);
+  const int64_t want = std::max<int64_t>(1, (2 * 152 + cot * cit - 1) / (cot * cit));
+  const int ks = (int)std::max<int64_t>(1, std::min<int64_t>(segs, want));
+  k_conv3x3_wgrad_tc<<<dim3(cot, cit, ks), 256, WG_SMEM, st>>>(a);
+  count_launch();
 }
 
 void nn_pack_weights(const float *w, int CinL, int CoutL, bool flip, uint16_t *out, cudaStream_t st) {

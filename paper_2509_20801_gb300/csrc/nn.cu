@@ -213,6 +213,15 @@ struct stdd_nn {
   }
 
   // throws if a tensor-core wait timed out since the last check (syncs st)
+  // weight and bias gradient of one convolution (accumulated into gw, gb)
+  void wgrad(const float *in, int cin, const float *gout, int cout, int N, int H, int W, float *gw, float *gb,
+             cudaStream_t st) {
+    if (mode == STDD_NN_TC)
+      stdd::nn_conv_wgrad_tc(in, cin, gout, cout, N, H, W, gw, gb, d_flag, st);
+    else
+      stdd::nn_conv_wgrad(in, cin, gout, cout, N, H, W, gw, gb, st);
+  }
+
   void check_flag(cudaStream_t st) {
     int f = 0;
     NCK(cudaMemcpyAsync(&f, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -323,7 +332,7 @@ struct stdd_nn {
     float *t1 = act["t1"].p, *t2 = act["t2"].p, *gd = act["gd"].p;
     // output layer
     const float *last = L > 1 ? A("d", 0) : A("skip", 0);
-    stdd::nn_conv_wgrad(last, ch[0], gout, 2, N, H, W, g.p + outL().woff, g.p + outL().boff, st);
+    wgrad(last, ch[0], gout, 2, N, H, W, g.p + outL().woff, g.p + outL().boff, st);
     conv(gout, outL(), gd, N, H, W, false, true, st);  // grad of d_0
     for (int l = 0; l < L; ++l)
       NCK(cudaMemsetAsync(A("gskip", l), 0, sz(l, ch[l]) * sizeof(float), st));
@@ -335,11 +344,11 @@ struct stdd_nn {
       const int h = H >> l, wd = W >> l;
       const size_t cnt = sz(l, ch[l]);
       stdd::nn_relu_mask(A("d", l), gd, (int64_t)cnt, st);
-      stdd::nn_conv_wgrad(A("sum", l), ch[l], gd, ch[l], N, h, wd, g.p + decD(l).woff, g.p + decD(l).boff, st);
+      wgrad(A("sum", l), ch[l], gd, ch[l], N, h, wd, g.p + decD(l).woff, g.p + decD(l).boff, st);
       conv(gd, decD(l), t1, N, h, wd, false, true, st);  // grad of sum
       stdd::nn_axpy(t1, A("gskip", l), 1.f, (int64_t)cnt, st);
       stdd::nn_relu_mask(A("decC", l), t1, (int64_t)cnt, st);
-      stdd::nn_conv_wgrad(A("up", l), ch[l + 1], t1, ch[l], N, h, wd, g.p + decC(l).woff, g.p + decC(l).boff, st);
+      wgrad(A("up", l), ch[l + 1], t1, ch[l], N, h, wd, g.p + decC(l).woff, g.p + decC(l).boff, st);
       conv(t1, decC(l), t2, N, h, wd, false, true, st);  // grad of up
       stdd::nn_up2_bwd(t2, gd, (int64_t)N * ch[l + 1], h, wd, st);  // grad of d_{l+1}
       if (l + 1 == L - 1)
@@ -351,12 +360,12 @@ struct stdd_nn {
       const size_t cnt = sz(l, ch[l]);
       float *gs = A("gskip", l);
       stdd::nn_relu_mask(A("skip", l), gs, (int64_t)cnt, st);
-      stdd::nn_conv_wgrad(A("encA", l), ch[l], gs, ch[l], N, h, wd, g.p + encB(l).woff, g.p + encB(l).boff, st);
+      wgrad(A("encA", l), ch[l], gs, ch[l], N, h, wd, g.p + encB(l).woff, g.p + encB(l).boff, st);
       conv(gs, encB(l), t1, N, h, wd, false, true, st);  // grad of encA
       stdd::nn_relu_mask(A("encA", l), t1, (int64_t)cnt, st);
       const float *src = l > 0 ? A("pool", l) : in;
       const int cin = l > 0 ? ch[l - 1] : 3;
-      stdd::nn_conv_wgrad(src, cin, t1, ch[l], N, h, wd, g.p + encA(l).woff, g.p + encA(l).boff, st);
+      wgrad(src, cin, t1, ch[l], N, h, wd, g.p + encA(l).woff, g.p + encA(l).boff, st);
       if (l > 0) {
         conv(t1, encA(l), t2, N, h, wd, false, true, st);  // grad of pool
         stdd::nn_pool2_bwd(t2, t1, (int64_t)N * cin, H >> (l - 1), W >> (l - 1), st);

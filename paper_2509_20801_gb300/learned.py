@@ -334,21 +334,31 @@ if __name__ == "__main__":
     ap.add_argument("--out", default=None)
     ap.add_argument("--bench-forward", default=None, metavar="WxH",
                     help="only time the network forward at this image size (random weights) and exit")
+    ap.add_argument("--bench-train", default=None, metavar="WxHxB",
+                    help="only time training steps (forward, backward, Adam) on B images of W x H and exit")
+    ap.add_argument("--mode", default="tc", choices=("tc", "bf16", "fp32"))
     a = ap.parse_args()
-    if a.bench_forward:
+    if a.bench_forward or a.bench_train:
         import torch
         L, c0, cm = (int(v) for v in a.net.split(","))
-        fw, fh = (int(v) for v in a.bench_forward.split("x"))
-        net = Network(L, c0, cm, mode="tc")
+        spec = [int(v) for v in (a.bench_forward or a.bench_train).split("x")]
+        fw, fh, nb = spec[0], spec[1], (spec[2] if len(spec) > 2 else 1)
+        net = Network(L, c0, cm, mode=a.mode)
         fh, fw = net.image_shape(fw, fh)
-        xi = torch.randn((1, 3, fh, fw), dtype=torch.float32, device="cuda:0")
-        xo = torch.empty((1, 2, fh, fw), dtype=torch.float32, device="cuda:0")
+        xi = torch.randn((nb, 3, fh, fw), dtype=torch.float32, device="cuda:0")
+        xo = torch.randn((nb, 2, fh, fw), dtype=torch.float32, device="cuda:0")
+        if a.bench_forward:
+            step = lambda: net.forward(xi, xo)  # noqa: E731
+        else:
+            xo.mul_(0.1)
+            step = lambda: net.train_step(xi, xo, 1e-4)  # noqa: E731
         for _ in range(3):
-            net.forward(xi, xo)
+            step()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
         ev[0].record()
         for _ in range(10):
-            net.forward(xi, xo)
+            step()
         ev[1].record()
         torch.cuda.synchronize()
         flops = 0
@@ -360,8 +370,16 @@ if __name__ == "__main__":
             if lv < L - 1:
                 flops += 2 * 9 * px * (ch[lv + 1] * ch[lv] + ch[lv] * ch[lv])
         flops += 2 * 9 * fh * fw * ch[0] * 2
+        flops *= nb
         ms = ev[0].elapsed_time(ev[1]) / 10
-        print(json.dumps(dict(image=[fw, fh], forward_ms=ms, conv_gflop=flops / 1e9, tflops=flops / ms / 1e9)))
+        if a.bench_forward:
+            print(json.dumps(dict(image=[fw, fh], mode=a.mode, forward_ms=ms, conv_gflop=flops / 1e9,
+                                  tflops=flops / ms / 1e9)))
+        else:
+            # forward, input gradient and weight gradient: three times the
+            # forward's convolution work
+            print(json.dumps(dict(image=[fw, fh], batch=nb, mode=a.mode, train_step_ms=ms,
+                                  conv_gflop=3 * flops / 1e9, tflops=3 * flops / ms / 1e9)))
         net.close()
         sys.exit(0)
     L, c0, cm = (int(v) for v in a.net.split(","))
