@@ -197,6 +197,8 @@ void nn_pack_weights(const float *w, int CinL, int CoutL, bool flip, uint16_t *o
 // floats), or null for no split; small images split their input channels
 // over several CTAs and a second kernel adds the slices in fixed order
 int nn_tc_ksplit(int Cin, int Cout, int N, int H, int W);
+// number of SMs of the current device (queried once)
+int nn_num_sms();
 // weight gradient on the tensor cores (BF16 operands, FP32 accumulation):
 // gw += ..., gb += ... (accumulated with atomics: zero them first)
 void nn_conv_wgrad_tc(const float *in, int Cin, const float *gout, int Cout, int N, int H, int W, float *gw,

@@ -1,7 +1,9 @@
 // Tensor-core (tcgen05) 3x3 convolutions of the learned-guess network: the
-// forward pass and the input gradient (the same convolution with the
-// weights transposed and flipped), as implicit GEMMs with BF16 operands and
-// FP32 accumulation in TMEM.
+// forward pass, the input gradient (the same convolution with the weights
+// transposed and flipped) and the weight gradient, as implicit GEMMs with
+// BF16 operands and FP32 accumulation in TMEM.  The weight-gradient kernel
+// is described at its definition; the rest of this header is about the
+// forward kernel.
 //
 // One CTA (256 threads) computes a 16 x 16 pixel tile for all output
 // channels (N = Cout rounded up to 16, at most 256) as two M = 128 halves
@@ -21,6 +23,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <stdexcept>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -219,24 +222,61 @@ __global__ void k_splitk_finish(const float *__restrict__ part, int ks, int64_t 
 // ---- weight gradient on the tensor cores
 // gw[co][ci][t] += sum over pixels p of gout[co](p) in[ci](p + shift_t), one
 // GEMM per tap t = 3 ky + kx with M = 128 output channels, N = 32 input
-// channels, K = pixels.  A CTA walks a contiguous range of 64-pixel row
-// segments (image n, row y, columns x0 .. x0 + 63; past the row end zero):
-// the output-gradient segment is the A tile, and the three input rows
-// y - 1 .. y + 1 (with a one-pixel halo) are written straight into the nine
-// tap-shifted B tiles.  The nine accumulators (32 TMEM columns each) stay
-// in TMEM across the CTA's segments; the epilogue adds them to gw with FP32
-// atomics (CTAs split the pixels).  The bias gradient (sum of gout) is
-// taken from the FP32 values while staging, by the CTAs of the first input
-// channel tile.
+// channels, K = pixels.  A CTA walks down one 64-pixel column strip (columns
+// x0 .. x0 + 63, past the row end zero) over a contiguous range of (image,
+// row) steps; the CTAs of all strips of a row range run side by side, so the
+// one-pixel halos they share are read from L2.  Per step the output-gradient
+// row segment is the A tile, and the input rows y - 1 .. y + 1 come from a
+// ring of four rows in shared memory, each stored in its three horizontal
+// shifts (tap kx reads pixel x + kx - 1), so every input row is converted
+// once per strip.  The FP32 rows arrive through a ring of D raw slots filled
+// by cp.async D - 1 steps ahead (each thread copies and later converts the
+// same 16-byte pieces, so only its own copies need to have landed); the
+// conversion writes BF16 into the K-major operand tiles, whose K core
+// matrices sit 144 bytes apart (a 16-byte pad that makes the 8-byte stores of
+// a half warp hit 32 distinct banks).  The nine accumulators (32 TMEM
+// columns each) stay in TMEM; the epilogue adds them to gw with FP32 atomics
+// (CTAs split the rows).  The three shifts of a ring row are contiguous, so
+// the taps of one kernel row ky are a single MMA with N = 96.  The bias
+// gradient (sum of gout) is summed from the FP32 values by the CTAs of the
+// first input-channel tile.
 constexpr int WG_M = 128, WG_N = 32, WG_K = 64;
-constexpr int WG_A = WG_M * WG_K * 2;          // 16 KiB
-constexpr int WG_BT = WG_N * WG_K * 2;         // 4 KiB per tap
-constexpr int WG_STAGE = WG_A + 9 * WG_BT;     // 52 KiB
-constexpr int WG_SMEM = 2 * WG_STAGE + 64;
+constexpr int WG_LBO = 144, WG_SBO = 8 * WG_LBO;
+constexpr int WG_A = (WG_M / 8) * WG_SBO;      // 18 KiB, one output-gradient row segment
+constexpr int WG_BT = (WG_N / 8) * WG_SBO;     // 4.5 KiB, one input row in one shift
+constexpr int WG_OPS = 2 * WG_A + 4 * 3 * WG_BT;
+constexpr int WG_RAW_B = WG_N * WG_K * 4 + WG_N * 2 * 4;  // input row + its two halo pixels
 
-// byte offset of (row, k) in a K-major tile of 64 K (core matrices 8 x 16 B)
+template <int AROWS>
+struct WgCfg {
+  static constexpr int D = AROWS <= 32 ? 6 : 3;             // raw slots (prefetch depth D - 1)
+  static constexpr int RAW = AROWS * WG_K * 4 + WG_RAW_B;   // one raw slot
+  static constexpr int BAR = WG_OPS + D * RAW;
+  static constexpr int SMEM = BAR + 64;
+};
+static_assert(WgCfg<128>::SMEM <= 227 * 1024 && WgCfg<32>::SMEM <= 227 * 1024, "weight-gradient smem");
+static_assert(WgCfg<32>::SMEM > 114 * 1024, "one CTA per SM (each holds 512 TMEM columns)");
+
 __device__ __forceinline__ uint32_t wg_off(int row, int k) {
-  return (uint32_t)((row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+  return (uint32_t)((row >> 3) * WG_SBO + (k >> 3) * WG_LBO + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint2 pack4_bf16(float a, float b, float c, float d) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+  return make_uint2(*reinterpret_cast<const uint32_t *>(&lo), *reinterpret_cast<const uint32_t *>(&hi));
+}
+
+// cp.async of `bytes` (0 .. 16) valid bytes into a 16-byte slot, rest zero
+__device__ __forceinline__ void cpa16(uint32_t dst, const void *src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cpa4(uint32_t dst, const void *src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 struct WgradTcArgs {
@@ -244,23 +284,33 @@ struct WgradTcArgs {
   int Cin, Cout, N, H, W;
   float *gw, *gb;
   int *flag;
+  int cit, strips, chunks;
+  int vec;  // rows 16-byte aligned (W % 4 == 0 and aligned bases)
 };
 
+template <int AROWS>
 __global__ void __launch_bounds__(256, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
+  using C = WgCfg<AROWS>;
+  constexpr int D = C::D, JA = AROWS / 16;
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ float gbs[WG_M];
-  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * WG_STAGE);  // mma[2]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::BAR);  // mma[2]
   uint32_t *tm = reinterpret_cast<uint32_t *>(bars + 2);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int co0 = blockIdx.x * WG_M, ci0 = blockIdx.y * WG_N;
-  const int spr = (a.W + WG_K - 1) / WG_K;
-  const int64_t total = (int64_t)a.N * a.H * spr;
-  const int64_t g0 = blockIdx.z * total / gridDim.z, g1 = (blockIdx.z + 1) * total / gridDim.z;
-  const bool do_bias = a.gb && blockIdx.y == 0;
-  const uint32_t bar0 = tcx::smem_u32(&bars[0]);
+  uint8_t *ring = sm + 2 * WG_A, *raw = sm + WG_OPS;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = tid & 15, r16 = tid >> 4;
+  const int co0 = (blockIdx.x / a.cit) * WG_M, ci0 = (blockIdx.x % a.cit) * WG_N;
+  const int strip = blockIdx.y % a.strips, chunk = blockIdx.y / a.strips;
+  const int x0 = strip * WG_K;
+  const int64_t nh = (int64_t)a.N * a.H;
+  const int64_t r0 = chunk * nh / a.chunks, r1 = (chunk + 1) * nh / a.chunks;
+  const int steps = (int)(r1 - r0);
+  const bool do_bias = a.gb && ci0 == 0;
+  const int64_t plane = (int64_t)a.H * a.W;
+  const uint32_t bar0 = tcx::smem_u32(&bars[0]), raw_s = tcx::smem_u32(raw);
   auto bm = [&](int st) { return bar0 + 8u * (uint32_t)st; };
   if (warp == 0) tcx::tmem_alloc(tcx::smem_u32(tm), 512);
-  if (tid < WG_M) gbs[tid] = 0.f;
+  // A rows AROWS .. 127 stay zero in both slots
+  if (AROWS < WG_M)
+    for (int i = tid; i < 2 * WG_A / 16; i += 256) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     tcx::mbar_init(bm(0), 1);
     tcx::mbar_init(bm(1), 1);
@@ -270,80 +320,176 @@ __global__ void __launch_bounds__(256, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
   __syncthreads();
   tcx::fence_after();
   const uint32_t tmem = *tm;
-  const uint32_t idesc = tcx::instr_desc_f16(1, WG_M, WG_N);
-  const int64_t plane = (int64_t)a.H * a.W;
+  const uint32_t idesc = tcx::instr_desc_f16(1, WG_M, 3 * WG_N);
+
+  // this thread's pieces: output-gradient rows r16 + 16 j (j < JA) and input
+  // rows r16 + 16 j (j < 2), pixels x0 + 4q .. x0 + 4q + 3, at image 0, row 0
+  // (a step adds n * C * plane + y * W); invalid channels copy nothing
+  const int xq = x0 + 4 * q;
+  const int nbx = max(0, min(4, a.W - xq)) * 4;  // valid bytes of the piece
+  const float *pa[JA];
+  bool va[JA];
+#pragma unroll
+  for (int j = 0; j < JA; ++j) {
+    va[j] = co0 + r16 + 16 * j < a.Cout;
+    pa[j] = a.gout + (int64_t)(va[j] ? co0 + r16 + 16 * j : 0) * plane + xq;
+  }
+  const float *pb[2];
+  bool vb[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    vb[j] = ci0 + r16 + 16 * j < a.Cin;
+    pb[j] = a.in + (int64_t)(vb[j] ? ci0 + r16 + 16 * j : 0) * plane + xq;
+  }
+  const bool hl = q == 0 && x0 > 0, hr = q == 15 && x0 + WG_K < a.W;
+  const int64_t cpa_stride = (int64_t)a.Cout * plane, cpb_stride = (int64_t)a.Cin * plane;
+  // four pixels from p into a 16-byte raw slot, nb valid bytes, rest zero
+  auto copy4 = [&](uint32_t dst, const float *p, int nb) {
+    if (a.vec) {
+      cpa16(dst, nb ? p : a.in, nb);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const bool ok = 4 * e < nb;
+        cpa4(dst + 4 * e, ok ? p + e : a.in, ok ? 4 : 0);
+      }
+    }
+  };
+  // input row yb of image n into the B part of raw slot `slot`; halo pixels
+  // x0 - 1 (by lane q = 0) and x0 + 64 (by lane q = 15)
+  auto issue_b = [&](uint32_t slot, int n, int yb) {
+    const bool rv = yb >= 0 && yb < a.H;
+    const int64_t o = n * cpb_stride + (int64_t)(rv ? yb : 0) * a.W;
+    const uint32_t b = slot + AROWS * WG_K * 4;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int ci = r16 + 16 * j;
+      const bool v = rv && vb[j];
+      copy4(b + (uint32_t)(ci * WG_K + 4 * q) * 4, pb[j] + o, v ? nbx : 0);
+      const uint32_t h = b + WG_N * WG_K * 4 + (uint32_t)ci * 8;
+      // lane 0's piece starts at x0, lane 15's at x0 + 60
+      if (q == 0) cpa4(h, v && hl ? pb[j] + o - 1 : a.in, v && hl ? 4 : 0);
+      if (q == 15) cpa4(h + 4, v && hr ? pb[j] + o + 4 : a.in, v && hr ? 4 : 0);
+    }
+  };
+  auto issue = [&](int s, int n, int y) {
+    const uint32_t slot = raw_s + (uint32_t)((s % D) * C::RAW);
+    const int64_t o = n * cpa_stride + (int64_t)y * a.W;
+#pragma unroll
+    for (int j = 0; j < JA; ++j)
+      copy4(slot + (uint32_t)((r16 + 16 * j) * WG_K + 4 * q) * 4, pa[j] + o, va[j] ? nbx : 0);
+    issue_b(slot, n, y + 1);
+  };
+  // raw input row of `slot` (this thread's pieces) into ring row `rs`
+  auto convert_b = [&](const uint8_t *slot, int rs) {
+    const float *b = reinterpret_cast<const float *>(slot + AROWS * WG_K * 4);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int ci = r16 + 16 * j;
+      const float4 v = *reinterpret_cast<const float4 *>(b + ci * WG_K + 4 * q);
+      const float up = __shfl_up_sync(0xffffffffu, v.w, 1, 16);
+      const float dn = __shfl_down_sync(0xffffffffu, v.x, 1, 16);
+      const float *h = b + WG_N * WG_K + 2 * ci;
+      const float left = q == 0 ? h[0] : up, right = q == 15 ? h[1] : dn;
+      uint8_t *t = ring + rs * 3 * WG_BT + wg_off(ci, 4 * q);
+      *reinterpret_cast<uint2 *>(t) = pack4_bf16(left, v.x, v.y, v.z);
+      *reinterpret_cast<uint2 *>(t + WG_BT) = pack4_bf16(v.x, v.y, v.z, v.w);
+      *reinterpret_cast<uint2 *>(t + 2 * WG_BT) = pack4_bf16(v.y, v.z, v.w, right);
+    }
+  };
+
+  // cursors: (n, y) of the step being computed and of the step being fetched
+  int n = (int)(r0 / a.H), y = (int)(r0 % a.H);
+  int pn = n, py = y;
+#pragma unroll
+  for (int s = 0; s < D - 1; ++s) {
+    if (s < steps) {
+      issue(s, pn, py);
+      if (++py == a.H) py = 0, ++pn;
+    }
+    cpa_commit();
+  }
+  float bsum[JA];
+#pragma unroll
+  for (int j = 0; j < JA; ++j) bsum[j] = 0.f;
   bool ok = true;
   int issued = 0;
-  for (int64_t g = g0; g < g1; ++g) {
-    const int lc = (int)(g - g0), st = lc & 1;
-    uint8_t *As = sm + st * WG_STAGE, *Bs = As + WG_A;
-    if (lc >= 2 && !tcx::mbar_wait(bm(st), ((lc - 2) >> 1) & 1, CT_WAIT)) ok = false;
+  for (int lc = 0; lc < steps; ++lc) {
+    if (lc + D - 1 < steps) {
+      issue(lc + D - 1, pn, py);
+      if (++py == a.H) py = 0, ++pn;
+    }
+    cpa_commit();
+    const bool restart = lc == 0 || y == 0;
+    // the A slot and the ring slot written here were last read by step
+    // lc - 2 (or, at a restart, by any earlier step)
+    // (every thread waits itself; a timed-out wait is caught by the barrier
+    // before the MMAs, which then are not issued)
+    if (restart && lc >= 1) {
+      if (!tcx::mbar_wait(bm((lc - 1) & 1), ((lc - 1) >> 1) & 1, CT_WAIT)) ok = false;
+    } else if (lc >= 2) {
+      if (!tcx::mbar_wait(bm(lc & 1), ((lc - 2) >> 1) & 1, CT_WAIT)) ok = false;
+    }
+    if (restart) {
+      // rows y - 1 and y through the slot of step lc + D - 1 (not yet
+      // issued: its copies are issued one step later)
+      const uint32_t spare = raw_s + (uint32_t)(((lc + D - 1) % D) * C::RAW);
+      const uint8_t *sp = raw + ((lc + D - 1) % D) * C::RAW;
+      if (lc + D - 1 < steps) {
+        // the spare slot is in flight for step lc + D - 1: drain it first
+        cpa_wait<0>();
+      }
+      issue_b(spare, n, y - 1);
+      cpa_commit();
+      cpa_wait<0>();
+      convert_b(sp, (y - 1) & 3);
+      issue_b(spare, n, y);
+      cpa_commit();
+      cpa_wait<0>();
+      convert_b(sp, y & 3);
+      if (lc + D - 1 < steps) {
+        issue(lc + D - 1, n + (int)((y + D - 1) / a.H), (y + D - 1) % a.H);
+        cpa_commit();
+      }
+    }
+    cpa_wait<D - 1>();
+    const uint8_t *slot = raw + (lc % D) * C::RAW;
+    uint8_t *As = sm + (lc & 1) * WG_A;
+#pragma unroll
+    for (int j = 0; j < JA; ++j) {
+      const int co = r16 + 16 * j;
+      const float4 v = *reinterpret_cast<const float4 *>(slot + (co * WG_K + 4 * q) * 4);
+      *reinterpret_cast<uint2 *>(As + wg_off(co, 4 * q)) = pack4_bf16(v.x, v.y, v.z, v.w);
+      bsum[j] += (v.x + v.y) + (v.z + v.w);
+    }
+    convert_b(slot, (y + 1) & 3);
+    tcx::fence_proxy_async();
+    tcx::fence_before();
     if (!__syncthreads_and(ok)) {
       ok = false;
       break;
     }
-    const int n = (int)(g / ((int64_t)a.H * spr));
-    const int rem = (int)(g % ((int64_t)a.H * spr));
-    const int y = rem / spr, x0 = (rem % spr) * WG_K;
-    // A: output gradient, items (group of 8 pixels, channel); a quarter
-    // warp stores 8 consecutive channels' 16-byte rows (one core matrix)
-    for (int it = tid; it < WG_M * (WG_K / 8); it += 256) {
-      const int co = it & (WG_M - 1), kg = it >> 7;
-      float v[8];
-      const bool cv = co0 + co < a.Cout;
-      const float *src = a.gout + ((int64_t)n * a.Cout + co0 + co) * plane + (int64_t)y * a.W;
-      float bsum = 0.f;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int x = x0 + kg * 8 + j;
-        v[j] = (cv && x < a.W) ? __ldg(src + x) : 0.f;
-        bsum += v[j];
-      }
-      if (do_bias && cv) atomicAdd(&gbs[co], bsum);
-      *reinterpret_cast<uint4 *>(As + wg_off(co, kg * 8)) =
-          make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                     pack_bf16x2(v[6], v[7]));
-    }
-    // B: items (input channel, row ky, group of 8 pixels); the ten input
-    // pixels x0 - 1 + 8 kg .. x0 + 8 kg + 8 of row y + ky - 1 give the
-    // group's 8 K elements of the three taps (ky, kx): element k = 8 kg + m
-    // of tap kx is pixel x0 + k + kx - 1, i.e. the (m + kx)-th loaded value
-    for (int it = tid; it < WG_N * 3 * (WG_K / 8); it += 256) {
-      const int ci = it & (WG_N - 1), r = it >> 5;
-      const int ky = r >> 3, kg = r & 7;
-      const int yy = y + ky - 1;
-      const bool rv = ci0 + ci < a.Cin && yy >= 0 && yy < a.H;
-      const float *src = a.in + ((int64_t)n * a.Cin + ci0 + ci) * plane + (int64_t)yy * a.W;
-      uint32_t hv[10];
-#pragma unroll
-      for (int j = 0; j < 10; ++j) {
-        const int xx = x0 - 1 + kg * 8 + j;
-        const float v = (rv && xx >= 0 && xx < a.W) ? __ldg(src + xx) : 0.f;
-        hv[j] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
-      }
-#pragma unroll
-      for (int kx = 0; kx < 3; ++kx)
-        *reinterpret_cast<uint4 *>(Bs + (ky * 3 + kx) * WG_BT + wg_off(ci, kg * 8)) =
-            make_uint4(hv[kx] | (hv[kx + 1] << 16), hv[kx + 2] | (hv[kx + 3] << 16),
-                       hv[kx + 4] | (hv[kx + 5] << 16), hv[kx + 6] | (hv[kx + 7] << 16));
-    }
-    tcx::fence_proxy_async();
-    tcx::fence_before();
-    __syncthreads();
     tcx::fence_after();
     if (tid == 0) {
-      const uint32_t a_base = tcx::smem_u32(As), b_base = tcx::smem_u32(Bs);
-#pragma unroll 1
-      for (int t = 0; t < 9; ++t)
+      // the three shifts of a ring row are stored back to back, so one MMA
+      // with N = 96 (rows kx * 32 + ci) covers the taps (ky, 0 .. 2), and its
+      // accumulator columns ky * 96 + kx * 32 + ci are those of tap 3 ky + kx
+      const uint64_t ad = tcx::smem_desc(tcx::smem_u32(As), WG_LBO, WG_SBO);
+      const uint64_t bd = tcx::smem_desc(tcx::smem_u32(ring), WG_LBO, WG_SBO);
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky) {
+        const uint64_t bt = bd + (uint64_t)(((((y + ky - 1) & 3) * 3) * WG_BT) >> 4);
 #pragma unroll
         for (int s4 = 0; s4 < WG_K / 16; ++s4)
-          tcx::mma_f16(tmem + (uint32_t)(t * WG_N), tcx::smem_desc(a_base + s4 * 256, 128, 1024),
-                       tcx::smem_desc(b_base + t * WG_BT + s4 * 256, 128, 1024), idesc,
-                       (lc > 0 || s4 > 0) ? 1u : 0u);
-      tcx::mma_commit(bm(st));
+          tcx::mma_f16(tmem + (uint32_t)(ky * 3 * WG_N), ad + (uint64_t)(s4 * 2 * WG_LBO / 16),
+                       bt + (uint64_t)(s4 * 2 * WG_LBO / 16), idesc, (lc > 0 || s4 > 0) ? 1u : 0u);
+      }
+      tcx::mma_commit(bm(lc & 1));
     }
     issued = lc + 1;
+    if (++y == a.H) y = 0, ++n;
   }
+  cpa_wait<0>();
   if (issued > 0) {
     const int last = issued - 1;
     if (!tcx::mbar_wait(bm(last & 1), (last >> 1) & 1, CT_WAIT)) ok = false;
@@ -351,23 +497,34 @@ __global__ void __launch_bounds__(256, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
   ok = __syncthreads_and(ok);
   tcx::fence_after();
   if (ok && issued > 0) {
-    // warp w: TMEM lanes 32 (w % 4) .. (output channels), half w / 4 of
-    // the 9 x 32 columns
-    const int q = warp & 3, h = warp >> 2;
-    const int co = 32 * q + lane;
-    const bool cv = co0 + co < a.Cout;
-    for (int j = 0; j < 9; ++j) {
-      const int c0 = h * 144 + j * 16;
-      uint32_t v[16];
-      tcx::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+    if (do_bias) {
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int c = c0 + u, t = c >> 5, ci = c & 31;
-        if (cv && ci0 + ci < a.Cin)
-          atomicAdd(&a.gw[((int64_t)(co0 + co) * a.Cin + ci0 + ci) * 9 + t], __uint_as_float(v[u]));
+      for (int j = 0; j < JA; ++j) {
+        float v = bsum[j];
+#pragma unroll
+        for (int o = 8; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
+        const int co = r16 + 16 * j;
+        if (q == 0 && co0 + co < a.Cout) atomicAdd(&a.gb[co0 + co], v);
       }
     }
-    if (do_bias && tid < WG_M && co0 + tid < a.Cout) atomicAdd(&a.gb[co0 + tid], gbs[tid]);
+    // warp w: TMEM lanes 32 (w % 4) .. (output channels), half w / 4 of
+    // the 9 x 32 columns
+    const int qw = warp & 3, h = warp >> 2;
+    const int co = 32 * qw + lane;
+    if (32 * qw < AROWS) {
+      const bool cv = co0 + co < a.Cout;
+      for (int j = 0; j < 9; ++j) {
+        const int c0 = h * 144 + j * 16;
+        uint32_t v[16];
+        tcx::tmem_ld16(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int c = c0 + u, t = c >> 5, ci = c & 31;
+          if (cv && ci0 + ci < a.Cin)
+            atomicAdd(&a.gw[((int64_t)(co0 + co) * a.Cin + ci0 + ci) * 9 + t], __uint_as_float(v[u]));
+        }
+      }
+    }
   } else if (!ok && tid == 0) {
     atomicOr(a.flag, 1);
   }
@@ -411,17 +568,41 @@ cudaError_t nn_tc_setup() {
   const cudaError_t e =
       cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * CT_ACT + 576 * 256 + 64);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_conv3x3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM);
+  const cudaError_t e2 =
+      cudaFuncSetAttribute(k_conv3x3_wgrad_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, WgCfg<32>::SMEM);
+  if (e2 != cudaSuccess) return e2;
+  return cudaFuncSetAttribute(k_conv3x3_wgrad_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              WgCfg<128>::SMEM);
+}
+
+int nn_num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int d = 0, v = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess ||
+        v <= 0)
+      throw std::runtime_error("cannot query the SM count");
+    n = v;
+  }
+  return n;
 }
 
 void nn_conv_wgrad_tc(const float *in, int Cin, const float *gout, int Cout, int N, int H, int W, float *gw,
                       float *gb, int *flag, cudaStream_t st) {
-  WgradTcArgs a{in, gout, Cin, Cout, N, H, W, gw, gb, flag};
   const int cot = (Cout + WG_M - 1) / WG_M, cit = (Cin + WG_N - 1) / WG_N;
-  const int64_t segs = (int64_t)N * H * ((W + WG_K - 1) / WG_K);
-  const int64_t want = std::max<int64_t>(1, (2 * 152 + cot * cit - 1) / (cot * cit));
-  const int ks = (int)std::max<int64_t>(1, std::min<int64_t>(segs, want));
-  k_conv3x3_wgrad_tc<<<dim3(cot, cit, ks), 256, WG_SMEM, st>>>(a);
+  const int strips = (W + WG_K - 1) / WG_K;
+  // one wave: every SM takes at most one CTA; the CTAs of one row range
+  // cover all strips
+  const int64_t nh = (int64_t)N * H;
+  const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(nh, nn_num_sms() / (cot * cit * strips)));
+  const int vec = (W % 4 == 0) && (reinterpret_cast<uintptr_t>(in) % 16 == 0) &&
+                  (reinterpret_cast<uintptr_t>(gout) % 16 == 0);
+  WgradTcArgs a{in, gout, Cin, Cout, N, H, W, gw, gb, flag, cit, strips, chunks, vec};
+  const dim3 grid(cot * cit, strips * chunks);
+  if (Cout <= 32)
+    k_conv3x3_wgrad_tc<32><<<grid, 256, WgCfg<32>::SMEM, st>>>(a);
+  else
+    k_conv3x3_wgrad_tc<128><<<grid, 256, WgCfg<128>::SMEM, st>>>(a);
   count_launch();
 }
 

@@ -74,6 +74,13 @@ def test_forward_and_gradient_match_oracle(case, bf16):
 TC_CASES = CASES + [
     # 8 input chunks, 256 output channels (the widest tile)
     (2, 128, 256, 1, 32, 48),
+    # weight gradient: three 64-pixel column strips with a 5-pixel ragged
+    # one, rows not 16-byte aligned (W odd), two images (the row walk
+    # restarts per strip and image)
+    (1, 32, 32, 2, 9, 133),
+    # two levels with 136 and 68 pixel rows, 136 output channels (two
+    # 128-channel tiles, the second ragged)
+    (2, 40, 136, 3, 20, 136),
 ]
 
 
