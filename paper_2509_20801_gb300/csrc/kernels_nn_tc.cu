@@ -241,6 +241,7 @@ __global__ void k_splitk_finish(const float *__restrict__ part, int ks, int64_t 
 // gradient (sum of gout) is summed from the FP32 values by the CTAs of the
 // first input-channel tile.
 constexpr int WG_M = 128, WG_N = 32, WG_K = 64;
+constexpr int WG_T = 512, WG_RP = WG_T / 16;  // threads; rows per pass (16 threads per row)
 constexpr int WG_LBO = 144, WG_SBO = 8 * WG_LBO;
 constexpr int WG_A = (WG_M / 8) * WG_SBO;      // 18 KiB, one output-gradient row segment
 constexpr int WG_BT = (WG_N / 8) * WG_SBO;     // 4.5 KiB, one input row in one shift
@@ -289,9 +290,9 @@ struct WgradTcArgs {
 };
 
 template <int AROWS>
-__global__ void __launch_bounds__(256, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
+__global__ void __launch_bounds__(WG_T, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
   using C = WgCfg<AROWS>;
-  constexpr int D = C::D, JA = AROWS / 16;
+  constexpr int D = C::D, JA = AROWS / WG_RP, JB = WG_N / WG_RP;
   extern __shared__ __align__(1024) uint8_t sm[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::BAR);  // mma[2]
   uint32_t *tm = reinterpret_cast<uint32_t *>(bars + 2);
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(256, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
   if (warp == 0) tcx::tmem_alloc(tcx::smem_u32(tm), 512);
   // A rows AROWS .. 127 stay zero in both slots
   if (AROWS < WG_M)
-    for (int i = tid; i < 2 * WG_A / 16; i += 256) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < 2 * WG_A / 16; i += WG_T) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     tcx::mbar_init(bm(0), 1);
     tcx::mbar_init(bm(1), 1);
@@ -322,8 +323,8 @@ __global__ void __launch_bounds__(256, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
   const uint32_t tmem = *tm;
   const uint32_t idesc = tcx::instr_desc_f16(1, WG_M, 3 * WG_N);
 
-  // this thread's pieces: output-gradient rows r16 + 16 j (j < JA) and input
-  // rows r16 + 16 j (j < 2), pixels x0 + 4q .. x0 + 4q + 3, at image 0, row 0
+  // this thread's pieces: output-gradient rows r16 + 32 j (j < JA) and input
+  // rows r16 + 32 j (j < JB), pixels x0 + 4q .. x0 + 4q + 3, at image 0, row 0
   // (a step adds n * C * plane + y * W); invalid channels copy nothing
   const int xq = x0 + 4 * q;
   const int nbx = max(0, min(4, a.W - xq)) * 4;  // valid bytes of the piece
@@ -331,15 +332,15 @@ __global__ void __launch_bounds__(256, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
   bool va[JA];
 #pragma unroll
   for (int j = 0; j < JA; ++j) {
-    va[j] = co0 + r16 + 16 * j < a.Cout;
-    pa[j] = a.gout + (int64_t)(va[j] ? co0 + r16 + 16 * j : 0) * plane + xq;
+    va[j] = co0 + r16 + WG_RP * j < a.Cout;
+    pa[j] = a.gout + (int64_t)(va[j] ? co0 + r16 + WG_RP * j : 0) * plane + xq;
   }
-  const float *pb[2];
-  bool vb[2];
+  const float *pb[JB];
+  bool vb[JB];
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    vb[j] = ci0 + r16 + 16 * j < a.Cin;
-    pb[j] = a.in + (int64_t)(vb[j] ? ci0 + r16 + 16 * j : 0) * plane + xq;
+  for (int j = 0; j < JB; ++j) {
+    vb[j] = ci0 + r16 + WG_RP * j < a.Cin;
+    pb[j] = a.in + (int64_t)(vb[j] ? ci0 + r16 + WG_RP * j : 0) * plane + xq;
   }
   const bool hl = q == 0 && x0 > 0, hr = q == 15 && x0 + WG_K < a.W;
   const int64_t cpa_stride = (int64_t)a.Cout * plane, cpb_stride = (int64_t)a.Cin * plane;
@@ -362,8 +363,8 @@ __global__ void __launch_bounds__(256, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
     const int64_t o = n * cpb_stride + (int64_t)(rv ? yb : 0) * a.W;
     const uint32_t b = slot + AROWS * WG_K * 4;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int ci = r16 + 16 * j;
+    for (int j = 0; j < JB; ++j) {
+      const int ci = r16 + WG_RP * j;
       const bool v = rv && vb[j];
       copy4(b + (uint32_t)(ci * WG_K + 4 * q) * 4, pb[j] + o, v ? nbx : 0);
       const uint32_t h = b + WG_N * WG_K * 4 + (uint32_t)ci * 8;
@@ -377,15 +378,15 @@ __global__ void __launch_bounds__(256, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
     const int64_t o = n * cpa_stride + (int64_t)y * a.W;
 #pragma unroll
     for (int j = 0; j < JA; ++j)
-      copy4(slot + (uint32_t)((r16 + 16 * j) * WG_K + 4 * q) * 4, pa[j] + o, va[j] ? nbx : 0);
+      copy4(slot + (uint32_t)((r16 + WG_RP * j) * WG_K + 4 * q) * 4, pa[j] + o, va[j] ? nbx : 0);
     issue_b(slot, n, y + 1);
   };
   // raw input row of `slot` (this thread's pieces) into ring row `rs`
   auto convert_b = [&](const uint8_t *slot, int rs) {
     const float *b = reinterpret_cast<const float *>(slot + AROWS * WG_K * 4);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int ci = r16 + 16 * j;
+    for (int j = 0; j < JB; ++j) {
+      const int ci = r16 + WG_RP * j;
       const float4 v = *reinterpret_cast<const float4 *>(b + ci * WG_K + 4 * q);
       const float up = __shfl_up_sync(0xffffffffu, v.w, 1, 16);
       const float dn = __shfl_down_sync(0xffffffffu, v.x, 1, 16);
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(256, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
     uint8_t *As = sm + (lc & 1) * WG_A;
 #pragma unroll
     for (int j = 0; j < JA; ++j) {
-      const int co = r16 + 16 * j;
+      const int co = r16 + WG_RP * j;
       const float4 v = *reinterpret_cast<const float4 *>(slot + (co * WG_K + 4 * q) * 4);
       *reinterpret_cast<uint2 *>(As + wg_off(co, 4 * q)) = pack4_bf16(v.x, v.y, v.z, v.w);
       bsum[j] += (v.x + v.y) + (v.z + v.w);
@@ -503,18 +504,18 @@ __global__ void __launch_bounds__(256, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
         float v = bsum[j];
 #pragma unroll
         for (int o = 8; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
-        const int co = r16 + 16 * j;
+        const int co = r16 + WG_RP * j;
         if (q == 0 && co0 + co < a.Cout) atomicAdd(&a.gb[co0 + co], v);
       }
     }
-    // warp w: TMEM lanes 32 (w % 4) .. (output channels), half w / 4 of
-    // the 9 x 32 columns
+    // warp w: TMEM lanes 32 (w % 4) .. (output channels), the 16-column
+    // groups w / 4, w / 4 + 4, ... of the 9 x 32 columns
     const int qw = warp & 3, h = warp >> 2;
     const int co = 32 * qw + lane;
     if (32 * qw < AROWS) {
       const bool cv = co0 + co < a.Cout;
-      for (int j = 0; j < 9; ++j) {
-        const int c0 = h * 144 + j * 16;
+      for (int jj = h; jj < 9 * WG_N / 16; jj += WG_T / 128) {
+        const int c0 = jj * 16;
         uint32_t v[16];
         tcx::tmem_ld16(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)c0, v);
 #pragma unroll
@@ -600,9 +601,9 @@ void nn_conv_wgrad_tc(const float *in, int Cin, const float *gout, int Cout, int
   WgradTcArgs a{in, gout, Cin, Cout, N, H, W, gw, gb, flag, cit, strips, chunks, vec};
   const dim3 grid(cot * cit, strips * chunks);
   if (Cout <= 32)
-    k_conv3x3_wgrad_tc<32><<<grid, 256, WgCfg<32>::SMEM, st>>>(a);
+    k_conv3x3_wgrad_tc<32><<<grid, WG_T, WgCfg<32>::SMEM, st>>>(a);
   else
-    k_conv3x3_wgrad_tc<128><<<grid, 256, WgCfg<128>::SMEM, st>>>(a);
+    k_conv3x3_wgrad_tc<128><<<grid, WG_T, WgCfg<128>::SMEM, st>>>(a);
   count_launch();
 }
 
