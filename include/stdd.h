@@ -179,6 +179,7 @@ typedef struct {
   double final_residual;      /* true relative residual (rhs 0)             */
   double min_pivot;           /* smallest |pivot| seen by the factorization */
   int reorth_passes;          /* second Gram-Schmidt passes in the last solve */
+  long long raised_pivots;    /* pivots raised to the static-pivot floor    */
 } stdd_stats;
 
 stdd_status stdd_get_stats(stdd_ctx *ctx, stdd_stats *out);
@@ -288,8 +289,30 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     leave too large an error off the bands.  It costs one
  *                     full application before the iteration (counted as the
  *                     first iteration) and one after; the residual history
- *                     ends with the true residual of the returned field. */
-enum { STDD_OPT_GRAPHS = 1, STDD_OPT_AUTOTUNE = 2, STDD_OPT_LEAF = 3, STDD_OPT_ORDER = 4, STDD_OPT_BAND = 5 };
+ *                     ends with the true residual of the returned field.
+ * and one that changes the factors (and so the preconditioner, not the
+ * solution):
+ *   STDD_OPT_STATIC_PIVOT (default 0): static pivoting of the front
+ *                     sweeps.  k in 1..15: a pivot whose modulus is below
+ *                     10^-k (2/dx^2 + 2/dy^2) is replaced by that floor
+ *                     times its phase (the factors are then those of A + E,
+ *                     E diagonal with one entry per raised pivot; the count
+ *                     is in stdd_stats.raised_pivots); 0: off (the plain
+ *                     elimination of Eq. 22).  The sweep has no pivoting,
+ *                     and nested dissection eliminates each box with its
+ *                     separators held fixed, i.e. as a closed cavity; near a
+ *                     cavity resonance the pivot block is near-singular and
+ *                     the elimination's growth, harmless in FP64, can ruin
+ *                     complex64 factors (high-index guided-wave geometries).
+ *                     Invalidates the factors. */
+enum {
+  STDD_OPT_GRAPHS = 1,
+  STDD_OPT_AUTOTUNE = 2,
+  STDD_OPT_LEAF = 3,
+  STDD_OPT_ORDER = 4,
+  STDD_OPT_BAND = 5,
+  STDD_OPT_STATIC_PIVOT = 6
+};
 stdd_status stdd_set_option(stdd_ctx *ctx, int option, int value);
 stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);
 

@@ -44,7 +44,7 @@ class stdd_stats(ctypes.Structure):
                 ("factor_flops", c_double), ("solve_flops", c_double),
                 ("local_dofs", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
                 ("iterations", c_int), ("final_residual", c_double), ("min_pivot", c_double),
-                ("reorth_passes", c_int)]
+                ("reorth_passes", c_int), ("raised_pivots", ctypes.c_longlong)]
 
 
 class stdd_profile(ctypes.Structure):
@@ -277,6 +277,7 @@ def stdd_residual_noalloc(ctx, x, b, r):
 
 
 STDD_OPT_GRAPHS, STDD_OPT_AUTOTUNE, STDD_OPT_LEAF, STDD_OPT_ORDER, STDD_OPT_BAND = 1, 2, 3, 4, 5
+STDD_OPT_STATIC_PIVOT = 6
 
 
 def stdd_set_profiling(ctx, level=1):

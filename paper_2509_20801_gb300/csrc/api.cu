@@ -160,12 +160,16 @@ struct stdd_ctx {
   std::map<int, Shape> shapes;
   std::vector<LevelInfo> levels;
   DBuf d_strips, d_fronts, d_nodes, d_cmap, d_inv, d_lcxm, d_lcxp, d_colstrip;
-  DBuf d_fac, d_ws[2], d_ub[2], d_tloc, d_wloc, d_flag, d_minpiv, d_items;
+  DBuf d_fac, d_ws[2], d_ub[2], d_tloc, d_wloc, d_flag, d_minpiv, d_nraised, d_items;
   int64_t nloc = 0, nloc_max = 0, ub_elems[2] = {0, 0};
   int64_t nfronts = 0, factor_entries = 0;
   double factor_cflops = 0, solve_cflops = 0;
   int max_p = 0, max_b = 0, depth = 0;
   double min_pivot = 0;
+  long long raised_pivots = 0;
+  // static pivoting: 0 = off, k > 0 = floor 10^-k of the stencil scale
+  int static_pivot = 0;
+  double pivot_floor() const;
   int solve_nrhs_cap = 0;
 
   // sources and Krylov state
@@ -383,6 +387,13 @@ struct stdd_ctx {
   int64_t device_bytes() const;
 };
 
+// Static-pivot floor: 10^-k times the modulus scale of the stencil's
+// diagonal, 2/dx^2 + 2/dy^2.
+double stdd_ctx::pivot_floor() const {
+  if (static_pivot <= 0) return 0.0;
+  return std::pow(10.0, -static_pivot) * (2.0 / (dx * dx) + 2.0 / (dy * dy));
+}
+
 MfArgs stdd_ctx::mf_args(int par, bool solve) const {
   MfArgs a;
   a.fronts = d_fronts.as<FrontDev>();
@@ -406,6 +417,8 @@ MfArgs stdd_ctx::mf_args(int par, bool solve) const {
   a.ub_child = d_ub[par ^ 1].p;
   a.flag = d_flag.as<int>();
   a.min_pivot = d_minpiv.as<double>();
+  a.piv_floor = pivot_floor();
+  a.n_raised = d_nraised.as<unsigned long long>();
   (void)solve;
   return a;
 }
@@ -652,6 +665,7 @@ void stdd_ctx::build_structure() {
   solve_nrhs_cap = 0;
   d_flag.alloc(sizeof(int));
   d_minpiv.alloc(sizeof(double));
+  d_nraised.alloc(sizeof(unsigned long long));
   CK(cudaStreamSynchronize(stream));
 }
 
@@ -719,6 +733,7 @@ template <typename R> void stdd_ctx::factor_t() {
     attrs = true;
   }
   CK(cudaMemsetAsync(d_flag.p, 0, sizeof(int), stream));
+  CK(cudaMemsetAsync(d_nraised.p, 0, sizeof(unsigned long long), stream));
   const double inf = INFINITY;
   CK(cudaMemcpyAsync(d_minpiv.p, &inf, sizeof(double), cudaMemcpyHostToDevice, stream));
   const int span = pbegin(PH_FACTOR);
@@ -732,7 +747,10 @@ template <typename R> void stdd_ctx::factor_t() {
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, stream));
   CK(cudaMemcpyAsync(&min_pivot, d_minpiv.p, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  unsigned long long nr = 0;
+  CK(cudaMemcpyAsync(&nr, d_nraised.p, sizeof(nr), cudaMemcpyDeviceToHost, stream));
   CK(cudaStreamSynchronize(stream));
+  raised_pivots = (long long)nr;
   if (flag & 2) throw TimeoutError("a tensor-core tile did not complete within its wait limit");
   if (flag & 1) throw std::domain_error("zero or non-finite pivot in a front");
 }
@@ -1863,6 +1881,7 @@ stdd_status stdd_get_stats(stdd_ctx *c, stdd_stats *o) {
     o->final_residual = c->last_res;
     o->min_pivot = c->min_pivot;
     o->reorth_passes = c->last_reorth;
+    o->raised_pivots = c->raised_pivots;
   });
 }
 
@@ -1914,6 +1933,13 @@ stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
         break;
       case STDD_OPT_BAND:
         c->use_band = value != 0;
+        break;
+      case STDD_OPT_STATIC_PIVOT:
+        if (value < 0 || value > 15) throw ArgError("static pivot exponent must be 0 .. 15");
+        if (value != c->static_pivot) {
+          c->static_pivot = value;
+          c->invalidate_factors();
+        }
         break;
       case STDD_OPT_LEAF:
         if (value < 1 || value > 4096) throw ArgError("leaf size out of range");

@@ -36,6 +36,8 @@ struct MfArgs {
   const void *ub_child;       // and of the level below
   int *flag;                  // bit 0: zero / non-finite pivot
   double *min_pivot;          // min |pivot| (atomicMin on the bit pattern)
+  double piv_floor;           // static pivoting: |pivot| < piv_floor is raised to it (0: off)
+  unsigned long long *n_raised;  // pivots raised
 };
 
 struct LevelInfo {

@@ -14,7 +14,14 @@
 // the block-LU solve of the front written with the inverse of F11.  The
 // elimination order (nested dissection) is the only permutation; there is no
 // pivoting (Eq. 22 uses fill-reducing P, Q only) and zero / non-finite pivots
-// raise a flag the host turns into STDD_EPIVOT.
+// raise a flag the host turns into STDD_EPIVOT.  Optionally (static
+// pivoting, an option of the context) a pivot smaller in modulus
+// than a floor is replaced by the floor times its phase before it is used:
+// the sweep then factors A + E, E diagonal with one entry per raised pivot,
+// and the outer FGMRES absorbs the low-rank difference.  This bounds the
+// element growth that near-singular pivot blocks cause without pivoting
+// (nested dissection eliminates each box with its separators held fixed,
+// i.e. a closed cavity, and high-index boxes can sit near a resonance).
 //
 // Front storage (column-major, complex):
 //   rows 0..p-1, all n columns : p x n, leading dimension p ([Finv H12])
@@ -63,6 +70,24 @@ template <typename C> __device__ __forceinline__ void st_elem(const MfArgs &a, c
   const int64_t o = elem_off(r, c, f.p, f.b, f.fac_off, f.s_off, ws);
   if (ws) reinterpret_cast<C *>(a.ws_cur)[o] = v;
   else reinterpret_cast<C *>(a.fac)[o] = v;
+}
+
+// the pivot actually used: d, or the floor with d's phase when |d| < floor
+template <typename C> __device__ __forceinline__ C floor_pivot(const MfArgs &a, C d, bool &raised) {
+  raised = false;
+  if (!(a.piv_floor > 0.0) || !cfinite(d)) return d;
+  const double ad = sqrt((double)cabs2(d));
+  if (!(ad < a.piv_floor)) return d;
+  raised = true;
+  C r;
+  if (ad > 0.0) {
+    r.x = (decltype(r.x))((double)d.x * (a.piv_floor / ad));
+    r.y = (decltype(r.y))((double)d.y * (a.piv_floor / ad));
+  } else {
+    r.x = (decltype(r.x))a.piv_floor;
+    r.y = 0;
+  }
+  return r;
 }
 
 __device__ __forceinline__ void note_pivot(const MfArgs &a, double ad, bool finite) {
@@ -187,15 +212,18 @@ __global__ void __launch_bounds__(128) mf_gj_small(MfArgs a, int f0, int nf, int
   double dmin = INFINITY;
   bool bad = false;
   for (int k = 0; k < p; ++k) {
-    const C d = F[k * n + k];
+    const C d0 = F[k * n + k];
+    bool raised;
+    const C d = floor_pivot(a, d0, raised);
     const C inv = crecip(d);
     for (int j = t; j < n; j += TPF) {
       rowk[j] = cmul(F[j * n + k], inv);
       colk[j] = F[k * n + j];
     }
-    const double ad = sqrt((double)cabs2(d));
-    bad |= !(ad > 0.0) || !cfinite(d);
+    const double ad = sqrt((double)cabs2(d0));
+    bad |= !(ad > 0.0) || !cfinite(d0);
     dmin = fmin(dmin, ad);
+    if (raised && t == 0) atomicAdd(a.n_raised, 1ull);
     front_sync<TPF>();
     for (int idx = t; idx < n * n; idx += TPF) {
       const int c = idx / n, r = idx - c * n;
@@ -241,15 +269,18 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_diag(MfArgs a, int f0,
   double dmin = INFINITY;
   bool bad = false;
   for (int q = 0; q < nbk; ++q) {
-    const C d = D[q][q];
+    const C d0 = D[q][q];
+    bool raised;
+    const C d = floor_pivot(a, d0, raised);
     const C inv = crecip(d);
     for (int j = tid; j < nbk; j += blockDim.x) {
       rowk[j] = cmul(D[q][j], inv);
       colk[j] = D[j][q];
     }
-    const double ad = sqrt((double)cabs2(d));
-    bad |= !(ad > 0.0) || !cfinite(d);
+    const double ad = sqrt((double)cabs2(d0));
+    bad |= !(ad > 0.0) || !cfinite(d0);
     dmin = fmin(dmin, ad);
+    if (raised && tid == 0) atomicAdd(a.n_raised, 1ull);
     __syncthreads();
     for (int idx = tid; idx < nbk * nbk; idx += blockDim.x) {
       const int i = idx % nbk, j = idx / nbk;

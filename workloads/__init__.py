@@ -304,6 +304,148 @@ def ellipses(nx, ny, seed, ppw=24, npml=20, overlap=8, interface_pml=20, nsub=No
                               sources=kinds))
 
 
+def _sbend(y0, dy, xs, length):
+    """Centre line of a raised-cosine S-bend: y0 for x <= xs, y0 + dy for
+    x >= xs + length, y0 + dy (1 - cos(pi t)) / 2 with t = (x - xs) / length
+    in between (dy = 0: a straight guide).  Returns (y(x), dy/dx, ymin, ymax)."""
+    length = max(length, 1e-12)
+
+    def yc(x):
+        t = np.clip((x - xs) / length, 0.0, 1.0)
+        return y0 + dy * 0.5 * (1.0 - np.cos(np.pi * t))
+
+    def slope(x):
+        t = np.clip((x - xs) / length, 0.0, 1.0)
+        return dy * 0.5 * np.pi / length * np.sin(np.pi * t)
+
+    return yc, slope, min(y0, y0 + dy), max(y0, y0 + dy)
+
+
+def _guides(xa, xb, arms, half):
+    """Union of waveguide cores along the arms' centre lines for xa <= x < xb:
+    a point belongs to a core if its vertical distance to a centre line is at
+    most half * sqrt(1 + slope^2) (half the width measured normal to the
+    line).  One object per x slab, so where arms overlap (a splitter's two
+    branches leaving one guide) the subcell average sees their union."""
+    def inside(x, y):
+        m = np.zeros(np.broadcast(x, y).shape, bool)
+        for yc, sl, _, _ in arms:
+            m |= np.abs(y - yc(x)) <= half * np.sqrt(1.0 + sl(x) ** 2)
+        return m & (x >= xa) & (x < xb)
+
+    smax = max(float(np.max(np.abs(sl(np.linspace(xa, xb, 257))))) for _, sl, _, _ in arms)
+    pad = half * math.sqrt(1.0 + smax ** 2) + 1e-9
+    return inside, (xa, xb, min(a[2] for a in arms) - pad, max(a[3] for a in arms) + pad)
+
+
+def slab_mode(eps_line, dy, wavelength):
+    """Fundamental mode of a 1-D cross-section for an Ez field travelling
+    along x: the eigenvector of largest eigenvalue beta^2 of
+    (E[j+1] - 2 E[j] + E[j-1]) / dy^2 + k0^2 eps[j] E[j] = beta^2 E[j] with
+    E = 0 beyond both ends (the guided mode has decayed there).  Returns beta
+    and the profile scaled to a positive peak of 1."""
+    from scipy.linalg import eigh_tridiagonal
+    k0 = 2 * math.pi / wavelength
+    eps_line = np.asarray(eps_line, float)
+    n = eps_line.size
+    diag = -2.0 / dy ** 2 + k0 ** 2 * eps_line
+    off = np.full(n - 1, 1.0 / dy ** 2)
+    val, vec = eigh_tridiagonal(diag, off, select="i", select_range=(n - 1, n - 1))
+    phi = vec[:, 0]
+    phi = phi / phi[np.argmax(np.abs(phi))]
+    return math.sqrt(val[0]), phi
+
+
+def waveguide_network(nx=8192, ny=2048, ppw=24, seed=2, npml=32, nsub=32, overlap=16, interface_pml=32,
+                      width=0.45, eps_core=12.1, eps_clad=2.085, wavelength=1.0, rtol=1e-8, restart=50):
+    """Silicon-like waveguide network: eps_core cores ``width`` wavelengths
+    wide in eps_clad cladding, guides running along x from the left PML to the
+    right one.  An input guide on the centre row splits at four seeded Y
+    splitters (1 -> 2 -> 4 -> 5 branches: two branches leave one guide as
+    raised-cosine S-bends of opposite offsets) and eight seeded S-bends shift
+    single branches (four between the second and third splitter stage, four
+    after the last).  The layout scales with the grid (positions and offsets
+    are fractions of its size; the full case is 8192 x 2048 at lambda/24,
+    32-cell PML, 32 strips, overlap 16).  The source is the guide's
+    fundamental mode: ``slab_mode`` of the permittivity column 12 cells right
+    of the left PML, placed on that column as a y-directed line current
+    b[i, j] = -phi_j / dx (it radiates the mode both ways; the left-going
+    half leaves through the PML)."""
+    rng = np.random.default_rng(seed)
+    d = wavelength / ppw
+    Lx, Ly = (nx - 1) * d, (ny - 1) * d
+    half = 0.5 * width * wavelength
+
+    def at(f, jit):  # an x position on a cell edge
+        return round((f + rng.uniform(-jit, jit)) * Lx / d) * d
+
+    x1, x2, x3, x4, x5 = (at(0.088, 0.015), at(0.264, 0.015), at(0.41, 0.015), at(0.586, 0.015),
+                          at(0.732, 0.015))
+    xend = (nx + 2) * d
+    d1, d2, d3 = 0.1875 * Ly, 0.094 * Ly, 0.047 * Ly
+    ys = [round(0.5 * Ly / d) * d]
+    slabs = [(-2 * d, x1, [_sbend(ys[0], 0.0, 0.0, 1.0)])]
+    # splitter 1 and the two splitters of stage 2
+    arms = [_sbend(y, s * d1, x1, 0.117 * Lx) for y in ys for s in (-1, 1)]
+    slabs.append((x1, x2, arms))
+    ys = sorted(y + s * d1 for y in ys for s in (-1, 1))
+    arms = [_sbend(y, s * d2, x2, 0.088 * Lx) for y in ys for s in (-1, 1)]
+    slabs.append((x2, x3, arms))
+    ys = sorted(y + s * d2 for y in ys for s in (-1, 1))
+    # four S-bends
+    arms, nys = [], []
+    for y in ys:
+        xs = x3 + rng.uniform(0.0, 0.03) * Lx
+        length = min(rng.uniform(0.073, 0.117) * Lx, x4 - xs - d)
+        off = rng.uniform(-1.0, 1.0) * 0.035 * Ly
+        arms.append(_sbend(y, off, xs, length))
+        nys.append(y + off)
+    slabs.append((x3, x4, arms))
+    ys = nys
+    # splitter 4 on one branch
+    k3 = int(rng.integers(len(ys)))
+    arms, nys = [], []
+    for k, y in enumerate(ys):
+        if k == k3:
+            arms += [_sbend(y, s * d3, x4, 0.073 * Lx) for s in (-1, 1)]
+            nys += [y - d3, y + d3]
+        else:
+            arms.append(_sbend(y, 0.0, x4, 1.0))
+            nys.append(y)
+    slabs.append((x4, x5, arms))
+    ys = sorted(nys)
+    # four S-bends on four of the five branches
+    pick = set(int(v) for v in rng.choice(len(ys), 4, replace=False))
+    arms, nys = [], []
+    for k, y in enumerate(ys):
+        if k in pick:
+            xs = x5 + rng.uniform(0.0, 0.03) * Lx
+            off = rng.uniform(-1.0, 1.0) * 0.023 * Ly
+            arms.append(_sbend(y, off, xs, rng.uniform(0.073, 0.117) * Lx))
+            nys.append(y + off)
+        else:
+            arms.append(_sbend(y, 0.0, x5, 1.0))
+            nys.append(y)
+    slabs.append((x5, xend, arms))
+    ys = sorted(nys)
+    gap = min(b - a for a, b in zip(ys, ys[1:])) - width * wavelength
+    if gap <= 0 or ys[0] - half <= (npml + 1) * d or ys[-1] + half >= Ly - (npml + 1) * d:
+        raise ValueError("grid too small for the waveguide network")
+    objs = [(_guides(xa, xb, arms, half), eps_core) for xa, xb, arms in slabs]
+    cells = cell_permittivity(nx, ny, d, d, eps_clad, objs)
+    eps = node_permittivity(cells)
+    i_src = npml + 12
+    beta, phi = slab_mode(eps[i_src], d, wavelength)
+    b = np.zeros((1, nx, ny), np.complex128)
+    b[0, i_src, :] = -phi / d
+    return Workload("waveguide-network", nx, ny, d, d, wavelength, eps, b,
+                    npml=(npml,) * 4, nsub=nsub, overlap=overlap, interface_pml=interface_pml,
+                    restart=restart, rtol=rtol,
+                    meta=dict(seed=seed, splitters=4, sbends=8, branches=len(ys), outputs=ys,
+                              min_gap=gap, x_stages=(x1, x2, x3, x4, x5), i_src=i_src, beta=beta,
+                              neff=beta / (2 * math.pi / wavelength)))
+
+
 def random_vector(n, seed, nrhs=1):
     """Seeded complex test vector(s) of length n (operator parity inputs)."""
     rng = np.random.default_rng(seed)
