@@ -42,9 +42,9 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor and tensor), NVIDIA's fi
 # still has the recorded SHA-256, else the roofline's traffic is null.
 NCU_TRAFFIC = {
     "mf_gj_update<double>": {
-        "bytes_per_unit": 75923110656 / 416732096864.0,  # DRAM bytes / algorithmic flops, 50 launches
+        "bytes_per_unit": 75926832640 / 416732096864.0,  # DRAM bytes / algorithmic flops, 50 launches
         "source": "paper_2509_20801_gb300/csrc/kernels_mf.cu",
-        "sha256": "44bdf97aba7a58306a6b5216dfa394c614951f77e0d93f01ab4c1be9771b1f3c",
+        "sha256": "bee4b8b5967dbffec7efd18af0d498f69fdbc008e90778d3446b16233da963a5",
         "profile": "profiles/ncu_dram_mf_gj_update_fp64_metalens.md",
     },
 }
