@@ -234,14 +234,19 @@ __global__ void k_splitk_finish(const float *__restrict__ part, int ks, int64_t 
 // same 16-byte pieces, so only its own copies need to have landed); the
 // conversion writes BF16 into the K-major operand tiles, whose K core
 // matrices sit 144 bytes apart (a 16-byte pad that makes the 8-byte stores of
-// a half warp hit 32 distinct banks).  The nine accumulators (32 TMEM
+// a half warp hit 32 distinct banks).  Sixteen converter warps hand each
+// row to a seventeenth warp through a "full" mbarrier; that warp issues the
+// row's MMAs and commits them to an "empty" mbarrier, which the converters
+// wait on two rows later before reusing the row's shared-memory slots (no
+// CTA-wide barrier per row).  The nine accumulators (32 TMEM
 // columns each) stay in TMEM; the epilogue adds them to gw with FP32 atomics
 // (CTAs split the rows).  The three shifts of a ring row are contiguous, so
 // the taps of one kernel row ky are a single MMA with N = 96.  The bias
 // gradient (sum of gout) is summed from the FP32 values by the CTAs of the
 // first input-channel tile.
 constexpr int WG_M = 128, WG_N = 32, WG_K = 64;
-constexpr int WG_T = 512, WG_RP = WG_T / 16;  // threads; rows per pass (16 threads per row)
+constexpr int WG_T = 512, WG_RP = WG_T / 16;  // converter threads; rows per pass (16 threads per row)
+constexpr int WG_THREADS = WG_T + 32;          // plus the MMA warp
 constexpr int WG_LBO = 144, WG_SBO = 8 * WG_LBO;
 constexpr int WG_A = (WG_M / 8) * WG_SBO;      // 18 KiB, one output-gradient row segment
 constexpr int WG_BT = (WG_N / 8) * WG_SBO;     // 4.5 KiB, one input row in one shift
@@ -290,12 +295,13 @@ struct WgradTcArgs {
 };
 
 template <int AROWS>
-__global__ void __launch_bounds__(WG_T, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
+__global__ void __launch_bounds__(WG_THREADS, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
   using C = WgCfg<AROWS>;
   constexpr int D = C::D, JA = AROWS / WG_RP, JB = WG_N / WG_RP;
   extern __shared__ __align__(1024) uint8_t sm[];
-  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::BAR);  // mma[2]
-  uint32_t *tm = reinterpret_cast<uint32_t *>(bars + 2);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::BAR);  // empty[2] (MMA commits), full[2]
+  uint32_t *tm = reinterpret_cast<uint32_t *>(bars + 4);
+  int *mma_ok = reinterpret_cast<int *>(bars + 5);
   uint8_t *ring = sm + 2 * WG_A, *raw = sm + WG_OPS;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = tid & 15, r16 = tid >> 4;
   const int co0 = (blockIdx.x / a.cit) * WG_M, ci0 = (blockIdx.x % a.cit) * WG_N;
@@ -308,13 +314,17 @@ __global__ void __launch_bounds__(WG_T, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
   const int64_t plane = (int64_t)a.H * a.W;
   const uint32_t bar0 = tcx::smem_u32(&bars[0]), raw_s = tcx::smem_u32(raw);
   auto bm = [&](int st) { return bar0 + 8u * (uint32_t)st; };
+  auto bf = [&](int st) { return bar0 + 16u + 8u * (uint32_t)st; };
   if (warp == 0) tcx::tmem_alloc(tcx::smem_u32(tm), 512);
   // A rows AROWS .. 127 stay zero in both slots
   if (AROWS < WG_M)
-    for (int i = tid; i < 2 * WG_A / 16; i += WG_T) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < 2 * WG_A / 16; i += WG_THREADS) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     tcx::mbar_init(bm(0), 1);
     tcx::mbar_init(bm(1), 1);
+    tcx::mbar_init(bf(0), WG_T);
+    tcx::mbar_init(bf(1), WG_T);
+    *mma_ok = 1;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   tcx::fence_before();
@@ -402,102 +412,117 @@ __global__ void __launch_bounds__(WG_T, 1) k_conv3x3_wgrad_tc(WgradTcArgs a) {
   // cursors: (n, y) of the step being computed and of the step being fetched
   int n = (int)(r0 / a.H), y = (int)(r0 % a.H);
   int pn = n, py = y;
-#pragma unroll
-  for (int s = 0; s < D - 1; ++s) {
-    if (s < steps) {
-      issue(s, pn, py);
-      if (++py == a.H) py = 0, ++pn;
-    }
-    cpa_commit();
-  }
   float bsum[JA];
 #pragma unroll
   for (int j = 0; j < JA; ++j) bsum[j] = 0.f;
   bool ok = true;
   int issued = 0;
-  for (int lc = 0; lc < steps; ++lc) {
-    if (lc + D - 1 < steps) {
-      issue(lc + D - 1, pn, py);
-      if (++py == a.H) py = 0, ++pn;
-    }
-    cpa_commit();
-    const bool restart = lc == 0 || y == 0;
-    // the A slot and the ring slot written here were last read by step
-    // lc - 2 (or, at a restart, by any earlier step)
-    // (every thread waits itself; a timed-out wait is caught by the barrier
-    // before the MMAs, which then are not issued)
-    if (restart && lc >= 1) {
-      if (!tcx::mbar_wait(bm((lc - 1) & 1), ((lc - 1) >> 1) & 1, CT_WAIT)) ok = false;
-    } else if (lc >= 2) {
-      if (!tcx::mbar_wait(bm(lc & 1), ((lc - 2) >> 1) & 1, CT_WAIT)) ok = false;
-    }
-    if (restart) {
-      // rows y - 1 and y through the slot of step lc + D - 1 (not yet
-      // issued: its copies are issued one step later)
-      const uint32_t spare = raw_s + (uint32_t)(((lc + D - 1) % D) * C::RAW);
-      const uint8_t *sp = raw + ((lc + D - 1) % D) * C::RAW;
-      if (lc + D - 1 < steps) {
-        // the spare slot is in flight for step lc + D - 1: drain it first
-        cpa_wait<0>();
+  if (warp == WG_T / 32) {
+    // the MMA warp: row lc's operands are complete when all converter
+    // threads have arrived on full[lc & 1]
+    if (lane == 0) {
+      for (int lc = 0; lc < steps; ++lc) {
+        if (!tcx::mbar_wait(bf(lc & 1), (lc >> 1) & 1, CT_WAIT)) {
+          *mma_ok = 0;
+          break;
+        }
+        tcx::fence_after();
+        // the three shifts of a ring row are stored back to back, so one MMA
+        // with N = 96 (rows kx * 32 + ci) covers the taps (ky, 0 .. 2), and
+        // its accumulator columns ky * 96 + kx * 32 + ci are those of tap
+        // 3 ky + kx
+        const uint64_t ad = tcx::smem_desc(tcx::smem_u32(sm + (lc & 1) * WG_A), WG_LBO, WG_SBO);
+        const uint64_t bd = tcx::smem_desc(tcx::smem_u32(ring), WG_LBO, WG_SBO);
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky) {
+          const uint64_t bt = bd + (uint64_t)(((((y + ky - 1) & 3) * 3) * WG_BT) >> 4);
+#pragma unroll
+          for (int s4 = 0; s4 < WG_K / 16; ++s4)
+            tcx::mma_f16(tmem + (uint32_t)(ky * 3 * WG_N), ad + (uint64_t)(s4 * 2 * WG_LBO / 16),
+                         bt + (uint64_t)(s4 * 2 * WG_LBO / 16), idesc, (lc > 0 || s4 > 0) ? 1u : 0u);
+        }
+        tcx::mma_commit(bm(lc & 1));
+        if (++y == a.H) y = 0;
       }
-      issue_b(spare, n, y - 1);
+    }
+    __syncwarp();
+    issued = steps;
+  } else {
+#pragma unroll
+    for (int s = 0; s < D - 1; ++s) {
+      if (s < steps) {
+        issue(s, pn, py);
+        if (++py == a.H) py = 0, ++pn;
+      }
       cpa_commit();
-      cpa_wait<0>();
-      convert_b(sp, (y - 1) & 3);
-      issue_b(spare, n, y);
-      cpa_commit();
-      cpa_wait<0>();
-      convert_b(sp, y & 3);
+    }
+    for (int lc = 0; lc < steps; ++lc) {
       if (lc + D - 1 < steps) {
-        issue(lc + D - 1, n + (int)((y + D - 1) / a.H), (y + D - 1) % a.H);
+        issue(lc + D - 1, pn, py);
+        if (++py == a.H) py = 0, ++pn;
+      }
+      cpa_commit();
+      const bool restart = lc == 0 || y == 0;
+      // the A slot and the ring slot written here were last read by step
+      // lc - 2 (or, at a restart, by any earlier step); a warp leaves the
+      // loop together when one of its lanes' waits timed out
+      if (restart && lc >= 1) {
+        if (!tcx::mbar_wait(bm((lc - 1) & 1), ((lc - 1) >> 1) & 1, CT_WAIT)) ok = false;
+      } else if (lc >= 2) {
+        if (!tcx::mbar_wait(bm(lc & 1), ((lc - 2) >> 1) & 1, CT_WAIT)) ok = false;
+      }
+      if (!__all_sync(0xffffffffu, ok)) {
+        ok = false;
+        break;
+      }
+      if (restart) {
+        // rows y - 1 and y through the slot of step lc + D - 1 (its copies
+        // are issued again afterwards)
+        const uint32_t spare = raw_s + (uint32_t)(((lc + D - 1) % D) * C::RAW);
+        const uint8_t *sp = raw + ((lc + D - 1) % D) * C::RAW;
+        if (lc + D - 1 < steps) {
+          // the spare slot is in flight for step lc + D - 1: drain it first
+          cpa_wait<0>();
+        }
+        issue_b(spare, n, y - 1);
         cpa_commit();
+        cpa_wait<0>();
+        convert_b(sp, (y - 1) & 3);
+        issue_b(spare, n, y);
+        cpa_commit();
+        cpa_wait<0>();
+        convert_b(sp, y & 3);
+        if (lc + D - 1 < steps) {
+          issue(lc + D - 1, n + (int)((y + D - 1) / a.H), (y + D - 1) % a.H);
+          cpa_commit();
+        }
       }
-    }
-    cpa_wait<D - 1>();
-    const uint8_t *slot = raw + (lc % D) * C::RAW;
-    uint8_t *As = sm + (lc & 1) * WG_A;
+      cpa_wait<D - 1>();
+      const uint8_t *slot = raw + (lc % D) * C::RAW;
+      uint8_t *As = sm + (lc & 1) * WG_A;
 #pragma unroll
-    for (int j = 0; j < JA; ++j) {
-      const int co = r16 + WG_RP * j;
-      const float4 v = *reinterpret_cast<const float4 *>(slot + (co * WG_K + 4 * q) * 4);
-      *reinterpret_cast<uint2 *>(As + wg_off(co, 4 * q)) = pack4_bf16(v.x, v.y, v.z, v.w);
-      bsum[j] += (v.x + v.y) + (v.z + v.w);
-    }
-    convert_b(slot, (y + 1) & 3);
-    tcx::fence_proxy_async();
-    tcx::fence_before();
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
-    tcx::fence_after();
-    if (tid == 0) {
-      // the three shifts of a ring row are stored back to back, so one MMA
-      // with N = 96 (rows kx * 32 + ci) covers the taps (ky, 0 .. 2), and its
-      // accumulator columns ky * 96 + kx * 32 + ci are those of tap 3 ky + kx
-      const uint64_t ad = tcx::smem_desc(tcx::smem_u32(As), WG_LBO, WG_SBO);
-      const uint64_t bd = tcx::smem_desc(tcx::smem_u32(ring), WG_LBO, WG_SBO);
-#pragma unroll
-      for (int ky = 0; ky < 3; ++ky) {
-        const uint64_t bt = bd + (uint64_t)(((((y + ky - 1) & 3) * 3) * WG_BT) >> 4);
-#pragma unroll
-        for (int s4 = 0; s4 < WG_K / 16; ++s4)
-          tcx::mma_f16(tmem + (uint32_t)(ky * 3 * WG_N), ad + (uint64_t)(s4 * 2 * WG_LBO / 16),
-                       bt + (uint64_t)(s4 * 2 * WG_LBO / 16), idesc, (lc > 0 || s4 > 0) ? 1u : 0u);
+      for (int j = 0; j < JA; ++j) {
+        const int co = r16 + WG_RP * j;
+        const float4 v = *reinterpret_cast<const float4 *>(slot + (co * WG_K + 4 * q) * 4);
+        *reinterpret_cast<uint2 *>(As + wg_off(co, 4 * q)) = pack4_bf16(v.x, v.y, v.z, v.w);
+        bsum[j] += (v.x + v.y) + (v.z + v.w);
       }
-      tcx::mma_commit(bm(lc & 1));
+      convert_b(slot, (y + 1) & 3);
+      // make the generic-proxy stores visible to the MMAs, then hand the row over
+      tcx::fence_proxy_async();
+      tcx::mbar_arrive(bf(lc & 1));
+      issued = lc + 1;
+      if (++y == a.H) y = 0, ++n;
     }
-    issued = lc + 1;
-    if (++y == a.H) y = 0, ++n;
   }
   cpa_wait<0>();
   if (issued > 0) {
     const int last = issued - 1;
     if (!tcx::mbar_wait(bm(last & 1), (last >> 1) & 1, CT_WAIT)) ok = false;
   }
-  ok = __syncthreads_and(ok);
+  ok = __syncthreads_and(ok && issued == steps) && *mma_ok;
   tcx::fence_after();
-  if (ok && issued > 0) {
+  if (ok && steps > 0 && warp < WG_T / 32) {
     if (do_bias) {
 #pragma unroll
       for (int j = 0; j < JA; ++j) {
@@ -601,9 +626,9 @@ void nn_conv_wgrad_tc(const float *in, int Cin, const float *gout, int Cout, int
   WgradTcArgs a{in, gout, Cin, Cout, N, H, W, gw, gb, flag, cit, strips, chunks, vec};
   const dim3 grid(cot * cit, strips * chunks);
   if (Cout <= 32)
-    k_conv3x3_wgrad_tc<32><<<grid, WG_T, WgCfg<32>::SMEM, st>>>(a);
+    k_conv3x3_wgrad_tc<32><<<grid, WG_THREADS, WgCfg<32>::SMEM, st>>>(a);
   else
-    k_conv3x3_wgrad_tc<128><<<grid, WG_T, WgCfg<128>::SMEM, st>>>(a);
+    k_conv3x3_wgrad_tc<128><<<grid, WG_THREADS, WgCfg<128>::SMEM, st>>>(a);
   count_launch();
 }
 

@@ -60,6 +60,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, long l
   return false;
 }
 
+// arrive on an mbarrier (release semantics at CTA scope)
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
 }
