@@ -243,6 +243,22 @@ def oracle_sample(w, its, target_s=20.0):
 
 
 # ----------------------------------------------------------------- ours
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest of the ranks' values, on every rank (the value itself
+    without a process group): step times are taken as the slowest rank's."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, seconds_max, world):
+    """Aggregate rate of `world` replicas that each process units_per_rank
+    units in at most seconds_max seconds (weak scaling)."""
+    return units_per_rank * world / seconds_max
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -336,10 +352,7 @@ def run_ours(args, rank, world, local_rank):
     x_main = x_d.clone()
     r_rel = B.stdd_residual(sv.ctx, x_d[0].reshape(-1).contiguous(), b_d[0].reshape(-1).contiguous(),
                             torch.empty(w.n, dtype=torch.complex128, device=dev))
-    ms_t = torch.tensor([ms], device=dev)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, dist, dev)
 
     # phase rooflines (algorithmic bytes / flops per phase call)
     steps = args.steps
@@ -429,7 +442,7 @@ def run_ours(args, rank, world, local_rank):
 
     out = {
         "metric": METRIC,
-        "value": N / (ms_max * 1e-3) / 1e6 * world,
+        "value": whole_job_rate(N, ms_max * 1e-3, world) / 1e6,
         "unit": "MDoF/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -515,11 +528,8 @@ def run_ours(args, rank, world, local_rank):
             S.stdd_set_sources(sv.ctx, w.nrhs, b_h)
             sv.solve(x_h, restart=RESTART, rtol=RTOL, maxit=args.maxit, allow_noconv=True)
         dt = (time.perf_counter() - t0) / args.steps
-        dt_t = torch.tensor([dt], device=dev)
-        if dist is not None:
-            dist.all_reduce(dt_t, op=dist.ReduceOp.MAX)
-        dt = float(dt_t.item())
-        out["e2e"] = {"value": N / dt / 1e6 * world, "unit": "MDoF/s", "ms_per_step": dt * 1e3,
+        dt = max_over_ranks(dt, dist, dev)
+        out["e2e"] = {"value": whole_job_rate(N, dt, world) / 1e6, "unit": "MDoF/s", "ms_per_step": dt * 1e3,
                       "h2d_bytes_per_step": int(w.eps_node.nbytes + w.b.nbytes),
                       "d2h_bytes_per_step": int(w.b.nbytes)}
         sv.close()

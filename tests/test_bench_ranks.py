@@ -1,0 +1,64 @@
+"""The benchmark's multi-rank host logic on CPU ranks (gloo, world size 2):
+the step time every rank reports is the slowest rank's, the whole-job rate
+sums the replicas' units over that time, and the reference arm prints only
+on rank 0."""
+import io
+import os
+import socket
+import sys
+from contextlib import redirect_stdout
+
+import pytest
+
+torch = pytest.importorskip("torch")
+mp = pytest.importorskip("torch.multiprocessing")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, times, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        got = bench.max_over_ranks(times[rank], dist)
+        rate = bench.whole_job_rate(1000, got, world)
+        buf = io.StringIO()
+        with redirect_stdout(buf):
+            bench.run_reference(None, rank) if rank != 0 else None
+        out.put((rank, got, rate, buf.getvalue()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_rate_with_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    times = [0.25, 0.75]
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, times, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, got, rate, printed in res:
+        assert got == 0.75                  # every rank sees the slowest rank's time
+        assert rate == pytest.approx(2 * 1000 / 0.75)
+        assert printed == ""                # the reference arm prints on rank 0 only
+
+
+def test_single_process_is_the_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(1.5) == 1.5
+    assert bench.whole_job_rate(4194304, 0.8, 1) == pytest.approx(4194304 / 0.8)
