@@ -97,6 +97,26 @@ __global__ void __launch_bounds__(256) k_conv3x3_tc(ConvTcArgs a) {
   const float *inb = a.in + (int64_t)n * a.Cin * plane;
   bool ok = true;
   int issued = 0;   // chunks whose MMAs were committed
+  // halo tile of 16 channels: items (plane cg, halo row, halo column), at
+  // most CT_ITEMS per thread; the loads of chunk c + 1 are issued before
+  // chunk c is converted and handed to the MMAs, so their latency overlaps
+  // the wait for the stage, the conversion and the barrier
+  float v[CT_ITEMS][8];
+  auto load_halo = [&](int c) {
+#pragma unroll
+    for (int u = 0; u < CT_ITEMS; ++u) {
+      const int it = tid + u * 256;
+      const int cg = it / (CT_HP * CT_HP), r = it % (CT_HP * CT_HP);
+      const int y = y0 - 1 + r / CT_HP, x = x0 - 1 + r % CT_HP;
+      const bool ok_item = c < ce && it < 2 * CT_HP * CT_HP && y >= 0 && y < a.H && x >= 0 && x < a.W;
+      const int ci0 = c * 16 + cg * 8;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        v[u][j] = (ok_item && ci0 + j < a.Cin) ? __ldg(inb + (int64_t)(ci0 + j) * plane + (int64_t)y * a.W + x)
+                                               : 0.f;
+    }
+  };
+  if (cb < ce) load_halo(cb);
   for (int c = cb; c < ce; ++c) {
     const int lc = c - cb;  // local chunk count: stages and barrier phases
     const int s = lc & 1;
@@ -112,31 +132,22 @@ __global__ void __launch_bounds__(256) k_conv3x3_tc(ConvTcArgs a) {
       tcx::mbar_expect_tx(bw(s), (uint32_t)wbytes);
       tcx::bulk_g2s(tcx::smem_u32(wst), a.wp + (size_t)c * (wbytes / 2), (uint32_t)wbytes, bw(s));
     }
-    // halo tile of 16 channels: items (plane cg, halo row, halo column),
-    // at most CT_ITEMS per thread; every load of a thread is issued before
-    // any is converted, so their latencies overlap
     {
-      float v[CT_ITEMS][8];
+      uint32_t pk[CT_ITEMS][4];
 #pragma unroll
       for (int u = 0; u < CT_ITEMS; ++u) {
-        const int it = tid + u * 256;
-        const int cg = it / (CT_HP * CT_HP), r = it % (CT_HP * CT_HP);
-        const int y = y0 - 1 + r / CT_HP, x = x0 - 1 + r % CT_HP;
-        const bool ok_item = it < 2 * CT_HP * CT_HP && y >= 0 && y < a.H && x >= 0 && x < a.W;
-        const int ci0 = c * 16 + cg * 8;
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          v[u][j] = (ok_item && ci0 + j < a.Cin) ? __ldg(inb + (int64_t)(ci0 + j) * plane + (int64_t)y * a.W + x)
-                                                 : 0.f;
+        pk[u][0] = pack_bf16x2(v[u][0], v[u][1]);
+        pk[u][1] = pack_bf16x2(v[u][2], v[u][3]);
+        pk[u][2] = pack_bf16x2(v[u][4], v[u][5]);
+        pk[u][3] = pack_bf16x2(v[u][6], v[u][7]);
       }
+      if (c + 1 < ce) load_halo(c + 1);
 #pragma unroll
       for (int u = 0; u < CT_ITEMS; ++u) {
         const int it = tid + u * 256;
         if (it < 2 * CT_HP * CT_HP) {
           const int cg = it / (CT_HP * CT_HP), r = it % (CT_HP * CT_HP);
-          *reinterpret_cast<uint4 *>(act + cg * CT_PLANE + r * 16) =
-              make_uint4(pack_bf16x2(v[u][0], v[u][1]), pack_bf16x2(v[u][2], v[u][3]),
-                         pack_bf16x2(v[u][4], v[u][5]), pack_bf16x2(v[u][6], v[u][7]));
+          *reinterpret_cast<uint4 *>(act + cg * CT_PLANE + r * 16) = make_uint4(pk[u][0], pk[u][1], pk[u][2], pk[u][3]);
         }
       }
     }
