@@ -336,8 +336,8 @@ stdd_status stdd_nd_analyze(int W, int H, int leaf_max, int *nfronts, long long 
  * Learned initial guess.  No counterpart in the paper: a convolutional
  * encoder-decoder maps (permittivity, Re b, Im b) on the grid to an initial
  * field for the Krylov iteration, which still runs to the same tolerance --
- * the zero-guess method remains both the fallback and the judge of the
- * guess.
+ * the zero-guess method remains both the fallback and the yardstick the
+ * guess is measured against.
  *
  * Network with L levels and channels c_l = min(c0 * 2^l, cmax):
  *   encoder level l: conv3x3 + ReLU, conv3x3 + ReLU (= skip_l); the input of

@@ -16,7 +16,7 @@ Unknown split (Eq. 15): I_k = owned nodes (this includes global PML at the
 domain ends), F_k = local nodes not owned (overlap band + interface PML),
 which lie in the neighbouring strips' owned columns.
 
-Readings of the paper used here (all listed again in the design doc):
+Readings of the paper used here:
 
 * Transfer operator (Eqs. 16-17): T_pi(e_i) = R_p^I A (E_i e_i): the global
   stencil applied to strip i's zero-extended local field (PML part included),
