@@ -105,8 +105,11 @@ def test_metalens_strip_shape_matches_derivation():
     assert max(d["level"] for d in fr) == 13
 
 
-def _multifrontal_solve(A, fronts, t):
-    """Dense-front elimination (no pivoting) with extend-add by node id."""
+def _multifrontal_solve(A, fronts, t, floor=0.0, raised=None, pivots=None):
+    """Dense-front elimination (no pivoting) with extend-add by node id.
+    With floor > 0 a pivot of modulus below it is replaced by floor times its
+    phase (static pivoting); (node, change) pairs go to ``raised`` and every
+    pivot's modulus to ``pivots``."""
     A = A.tocsr()
     schur = {}
     facs = []
@@ -125,6 +128,12 @@ def _multifrontal_solve(A, fronts, t):
         U = np.zeros_like(F11)
         G = F11.copy()
         for k in range(p):                    # right-looking LU, no pivoting
+            dv = G[k, k]
+            if pivots is not None:
+                pivots.append(abs(dv))
+            if floor > 0 and abs(dv) < floor:
+                G[k, k] = floor * dv / abs(dv) if abs(dv) > 0 else floor
+                raised.append((int(idx[k]), G[k, k] - dv))
             U[k, k:] = G[k, k:]
             L[k:, k] = G[k:, k] / G[k, k]
             G[k + 1:, k + 1:] -= np.outer(L[k + 1:, k], U[k, k + 1:])
@@ -158,3 +167,34 @@ def test_multifrontal_emulation_reproduces_direct_solve():
         x = _multifrontal_solve(A, fr, t)
         ref = D.local_solve(k, t)
         assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-11
+
+
+def test_static_pivoting_factors_a_diagonal_perturbation():
+    """Raising small pivots during the elimination (the library's optional
+    static pivoting) yields exactly the factors of A + E, E diagonal with
+    the raised pivots' changes, checked against SuperLU on A + E."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+    import workloads as W
+    from oracle.fdfd import Problem
+    from oracle.stddm import DDM
+    w = W.random_medium(60, 36, ppw=16, seed=2, npml=6, nsub=2, overlap=3, interface_pml=6)
+    P = Problem.from_workload(w)
+    D = DDM.from_workload(w, P)
+    s = D.strips[1]
+    fr = _fronts(s.width, P.ny, 16)
+    A = D.local_A(1).tocsc()
+    t = np.random.default_rng(5).standard_normal(A.shape[0]) + 0j
+    mags = []
+    _multifrontal_solve(A, fr, t, pivots=mags)
+    floor = float(np.quantile(mags, 0.2))       # raise about a fifth of the pivots
+    raised = []
+    x = _multifrontal_solve(A, fr, t, floor=floor, raised=raised)
+    assert 0.1 * len(mags) < len(raised) < 0.3 * len(mags)
+    E = np.zeros(A.shape[0], complex)
+    for node, delta in raised:
+        E[node] += delta
+    ref = sla.spsolve((A + sp.diags(E)).tocsc(), t)
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-10
+    # and it is not the unperturbed solve
+    assert np.linalg.norm(x - sla.spsolve(A, t)) > 1e-3 * np.linalg.norm(ref)
