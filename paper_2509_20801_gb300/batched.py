@@ -10,7 +10,7 @@ solve times (CUDA events), iterations, and the true residual of every field
 batch, MDoF/s = sum of nx * ny * nrhs / total time.
 
     python -m paper_2509_20801_gb300.batched [--count 48] [--nrhs 8] [--precision c64]
-        [--order additive|multiplicative|red-black] [--restart m] [--maxit k]
+        [--order additive|multiplicative|red-black] [--restart m] [--maxit k] [--static-pivot k]
 """
 from __future__ import annotations
 
@@ -36,7 +36,7 @@ def geometries(count=48, nrhs=8, shapes=SHAPES, seed=3):
 
 
 def run(count=48, nrhs=8, precision="c64", rtol=1e-8, restart=30, maxit=1000, device=0, shapes=SHAPES,
-        out=None, log=None, order="additive"):
+        out=None, log=None, order="additive", static_pivot=0):
     import torch
     from . import Solver
     dev = torch.device("cuda", device)
@@ -50,6 +50,7 @@ def run(count=48, nrhs=8, precision="c64", rtol=1e-8, restart=30, maxit=1000, de
         s = Solver.from_workload(w, eps=torch.from_numpy(w.eps_node).to(dev), precision=PRECISIONS[precision],
                                  device=device)
         _b.stdd_set_option(s.ctx, _b.STDD_OPT_ORDER, ORDERS[order])
+        _b.stdd_set_option(s.ctx, _b.STDD_OPT_STATIC_PIVOT, static_pivot)
         try:
             b = torch.from_numpy(w.b).to(dev)
             x = torch.empty_like(b)
@@ -68,7 +69,7 @@ def run(count=48, nrhs=8, precision="c64", rtol=1e-8, restart=30, maxit=1000, de
             row = dict(g=g, nx=w.nx, ny=w.ny, nsub=w.nsub, nrhs=w.nrhs, factor_ms=ev[0].elapsed_time(ev[1]),
                        solve_ms=ev[1].elapsed_time(ev[2]), iterations_max=max(its),
                        iterations_mean=float(np.mean(its)), converged=st == _b.STDD_OK,
-                       max_true_residual=float(max(res)))
+                       max_true_residual=float(max(res)), raised_pivots=s.stats()["raised_pivots"])
         finally:
             s.close()
         rows.append(row)
@@ -77,6 +78,7 @@ def run(count=48, nrhs=8, precision="c64", rtol=1e-8, restart=30, maxit=1000, de
     dof = sum(r["nx"] * r["ny"] * r["nrhs"] for r in rows)
     tms = sum(r["factor_ms"] + r["solve_ms"] for r in rows)
     summary = dict(geometries=len(rows), rhs_per_geometry=nrhs, precision=precision, order=order, restart=restart,
+                   static_pivot=static_pivot,
                    maxit=maxit, rtol=rtol,
                    unknowns=sum(r["nx"] * r["ny"] for r in rows), dof_rhs=dof, total_ms=tms,
                    factor_ms=sum(r["factor_ms"] for r in rows), solve_ms=sum(r["solve_ms"] for r in rows),
@@ -98,7 +100,8 @@ if __name__ == "__main__":
     ap.add_argument("--order", default="additive", choices=sorted(ORDERS))
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--maxit", type=int, default=1000)
+    ap.add_argument("--static-pivot", type=int, default=0)
     a = ap.parse_args()
     _, summ = run(a.count, a.nrhs, a.precision, a.rtol, a.restart, a.maxit, out=sys.stderr,
-                  log=lambda m: print(m, file=sys.stderr, flush=True), order=a.order)
+                  log=lambda m: print(m, file=sys.stderr, flush=True), order=a.order, static_pivot=a.static_pivot)
     print(json.dumps(summ))

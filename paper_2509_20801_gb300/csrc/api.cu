@@ -376,8 +376,18 @@ struct stdd_ctx {
   void check_red_black() const;
   template <typename R> void autotune();
   void ensure_solve_buffers(int nr);
-  // sweep launch configurations chosen by timing, keyed by the level shape
-  std::map<std::vector<int64_t>, int> tuned;
+  // sweep launch configurations chosen by timing, keyed by the device and
+  // the level shape; shared by every context of the process (contexts of
+  // the same grid and decomposition, or any with the same level shapes,
+  // reuse one tuning)
+  static std::map<std::vector<int64_t>, int> &tuned() {
+    static std::map<std::vector<int64_t>, int> m;
+    return m;
+  }
+  static std::mutex &tuned_mutex() {
+    static std::mutex m;
+    return m;
+  }
   bool autotune_on = true;
   MfArgs mf_args(int level_parity_cur, bool solve) const;
   void ensure_krylov(int m);
@@ -686,12 +696,19 @@ template <typename R> void stdd_ctx::autotune() {
       const int cols = dir == 0 ? li.max_p : li.max_n;
       const int nitems = dir == 0 ? li.n_up : li.n_down;
       if (nitems == 0) continue;
-      const std::vector<int64_t> key = {dir, (int64_t)sizeof(R), li.nf, li.max_p, li.max_b, li.min_n, nitems, rows};
-      auto hit = tuned.find(key);
+      const std::vector<int64_t> key = {device, dir, (int64_t)sizeof(R), li.nf, li.max_p, li.max_b, li.min_n,
+                                        nitems, rows};
       int best = dir == 0 ? li.split_up : li.split_down;
-      if (hit != tuned.end()) {
-        best = hit->second;
-      } else {
+      bool found = false;
+      {
+        std::lock_guard<std::mutex> lk(tuned_mutex());
+        auto hit = tuned().find(key);
+        if (hit != tuned().end()) {
+          best = hit->second;
+          found = true;
+        }
+      }
+      if (!found) {
         float best_ms = 1e30f;
         for (int sp = 1; sp <= 8; sp *= 2) {
           if (sp > 256 / rows) break;
@@ -713,7 +730,8 @@ template <typename R> void stdd_ctx::autotune() {
             best = sp;
           }
         }
-        tuned[key] = best;
+        std::lock_guard<std::mutex> lk(tuned_mutex());
+        tuned()[key] = best;
       }
       if (dir == 0) li.split_up = best;
       else li.split_down = best;
