@@ -24,8 +24,9 @@ inline int grid_for(int64_t n) {
   return (int)std::min<int64_t>((n + TPB - 1) / TPB, 152 * 16);
 }
 
-__device__ __forceinline__ double2 apply_row(const GridDev &g, const double2 *__restrict__ x, int64_t idx) {
-  const int i = (int)(idx / g.ny), j = (int)(idx - (int64_t)i * g.ny);
+// row idx = i * ny + j of the operator applied to x
+__device__ __forceinline__ double2 apply_row_ij(const GridDev &g, const double2 *__restrict__ x, int64_t idx, int i,
+                                                int j) {
   const double2 xm = g.cxm[i], xp = g.cxp[i], ym = g.cym[j], yp = g.cyp[j];
   double2 d;
   d.x = g.k0sq * g.eps[idx] - xm.x - xp.x - ym.x - yp.x;
@@ -38,17 +39,37 @@ __device__ __forceinline__ double2 apply_row(const GridDev &g, const double2 *__
   return acc;
 }
 
+__device__ __forceinline__ double2 apply_row(const GridDev &g, const double2 *__restrict__ x, int64_t idx) {
+  const int i = (int)(idx / g.ny), j = (int)(idx - (int64_t)i * g.ny);
+  return apply_row_ij(g, x, idx, i, j);
+}
+
+// grid-stride walk over all nodes with (i, j) advanced incrementally (no
+// division per node): f(idx, i, j) for every node of this thread
+template <typename F> __device__ __forceinline__ void for_nodes(const GridDev &g, F f) {
+  const int64_t n = (int64_t)g.nx * g.ny, stride = (int64_t)gridDim.x * TPB;
+  int64_t idx = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (idx >= n) return;
+  int i = (int)(idx / g.ny), j = (int)(idx - (int64_t)i * g.ny);
+  const int si = (int)(stride / g.ny), sj = (int)(stride - (int64_t)si * g.ny);
+  for (; idx < n; idx += stride) {
+    f(idx, i, j);
+    i += si;
+    j += sj;
+    if (j >= g.ny) {
+      j -= g.ny;
+      ++i;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(TPB) k_stencil(GridDev g, const double2 *__restrict__ x, double2 *__restrict__ y) {
-  const int64_t n = (int64_t)g.nx * g.ny;
-  for (int64_t idx = (int64_t)blockIdx.x * TPB + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * TPB)
-    y[idx] = apply_row(g, x, idx);
+  for_nodes(g, [&](int64_t idx, int i, int j) { y[idx] = apply_row_ij(g, x, idx, i, j); });
 }
 
 __global__ void __launch_bounds__(TPB) k_residual(GridDev g, const double2 *__restrict__ b,
                                                   const double2 *__restrict__ x, double2 *__restrict__ r) {
-  const int64_t n = (int64_t)g.nx * g.ny;
-  for (int64_t idx = (int64_t)blockIdx.x * TPB + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * TPB)
-    r[idx] = csub(b[idx], apply_row(g, x, idx));
+  for_nodes(g, [&](int64_t idx, int i, int j) { r[idx] = csub(b[idx], apply_row_ij(g, x, idx, i, j)); });
 }
 
 template <typename R>

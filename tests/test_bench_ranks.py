@@ -62,3 +62,18 @@ def test_single_process_is_the_identity():
     import bench
     assert bench.max_over_ranks(1.5) == 1.5
     assert bench.whole_job_rate(4194304, 0.8, 1) == pytest.approx(4194304 / 0.8)
+
+
+def test_stencil_phase_roofline():
+    """The stencil's figures from one measured call time: 40 B and 40 flops
+    per node; FP64-bound where the FP64 rate is below 1 flop per HBM byte."""
+    sys.path.insert(0, ROOT)
+    import bench
+    d = bench.stencil_phase(0.2, 36, 4194304, 6794.1, 1.0985)
+    assert d["bytes_per_call"] == d["flops_per_call"] == 40 * 4194304
+    assert d["gbs"] == pytest.approx(838.86, rel=1e-4)
+    assert d["tflops"] == pytest.approx(0.83886, rel=1e-4)
+    assert d["fp64_frac"] == pytest.approx(0.83886 / 1.0985, rel=1e-4)
+    assert d["bound"] == "alu"
+    assert bench.stencil_phase(0.2, 1, 100, 1000.0, 10.0)["bound"] == "hbm"
+    assert bench.stencil_phase(0.2, 1, 100, 1000.0, 1.0, measured_over="x")["measured_over"] == "x"
