@@ -137,3 +137,70 @@ def test_mode_propagates_with_the_predicted_phase_velocity():
     # the profile across the guide is the mode's
     prof = u[i2] / u[i2, jc]
     assert np.linalg.norm(prof - phi / phi[jc]) < 3e-2 * np.linalg.norm(phi / phi[jc])
+
+
+@pytest.mark.parametrize("shape,seed", [((512, 512), 3_000_000), ((1024, 512), 3_000_007), ((256, 256), 3_000_011)])
+def test_ellipse_geometry_properties(shape, seed):
+    """The batched / learned geometries: fill fraction drawn from [15 %, 30 %]
+    of the non-PML area (the area painted, measured on the node grid, is close
+    to the ellipses' summed area), permittivity only in {1} u [2, 12.1], vacuum
+    within half a wavelength of the PML, strips in [2, min(8, nx / 128)] and
+    every source at least half a wavelength inside the PML."""
+    nx, ny = shape
+    w = W.ellipses(nx, ny, seed=seed, nrhs=8, sources="mixed")
+    npml, d = w.npml[0], w.dx
+    area = ((nx - 1 - 2 * npml) * d) * ((ny - 1 - 2 * npml) * d)
+    fill = w.meta["fill"]
+    assert w.meta["n_ellipses"] >= 1
+    assert fill <= 0.30 + 1e-12
+    # the drawn target is at least 15 %; the loop stops once it is reached, or
+    # after 400 attempts on small grids where big ellipses no longer fit
+    painted = (w.eps_node > 1.0 + 1e-12).sum() * d * d / area
+    assert abs(painted - fill) < 0.25 * fill + 0.01
+    e = w.eps_node
+    assert e.min() == pytest.approx(1.0) and e.max() <= 12.1 + 1e-12
+    keep = int(np.ceil(0.5 / d))
+    margin = npml + keep - 2          # subcell averaging reaches one cell past the edge
+    core = np.zeros_like(e, bool)
+    core[margin:nx - margin, margin:ny - margin] = True
+    assert np.all(np.abs(e[~core] - 1.0) < 1e-12)
+    assert 2 <= w.nsub <= max(2, min(8, nx // 128))
+    for q in range(w.nrhs):
+        nz = np.argwhere(w.b[q] != 0)
+        if w.meta["sources"][q] == "point":
+            assert len(nz) == 1
+            i, j = nz[0]
+            assert npml + keep <= i <= nx - 1 - npml - keep and npml + keep <= j <= ny - 1 - npml - keep
+        else:
+            js = set(nz[:, 1])
+            assert len(js) == 1 and len(nz) == nx
+            j = js.pop()
+            assert npml + keep <= j <= ny - 1 - npml - keep
+
+
+def test_metalens_structure():
+    """The metalens workload as stated: substrate eps 2.085 on the lower 20 %
+    of the rows, pillars of eps 12.1, 14 cells high (0.6 lambda at lambda/24),
+    at a 0.5 lambda period with widths in [0.1, 0.4] lambda, and the line
+    source 10 rows above the bottom PML."""
+    w = W.metalens()
+    d, npml = w.dx, w.npml[0]
+    j_sub = w.meta["j_substrate"]
+    assert j_sub == round(0.2 * w.ny)
+    e = w.eps_node
+    assert np.allclose(e[:, 5:j_sub - 2], 2.085)           # substrate rows (away from the top interface)
+    # pillar rows: count the eps 12.1 runs along a row in the middle of the pillars
+    row = e[:, j_sub + 7]
+    m = row > 0.5 * (12.1 + 1.0)
+    starts = np.flatnonzero(m[1:] & ~m[:-1]) + 1
+    ends = np.flatnonzero(m[:-1] & ~m[1:]) + 1
+    assert len(starts) == w.meta["n_pillars"]
+    widths = (ends - starts) * d
+    assert widths.min() >= 0.1 - 2 * d and widths.max() <= 0.4 + 2 * d
+    period = np.diff(0.5 * (starts + ends)) * d
+    assert np.allclose(period, 0.5, atol=2 * d)
+    # pillar height: 14 rows above the substrate, vacuum further up
+    col = e[int(0.5 * (starts[0] + ends[0])), :]
+    assert np.all(col[j_sub + 1:j_sub + 13] > 6.0) and np.all(np.abs(col[j_sub + 16:w.ny - npml] - 1.0) < 1e-12)
+    nz = np.argwhere(w.b[0] != 0)
+    assert set(nz[:, 1]) == {npml + 10} and len(nz) == w.nx
