@@ -204,3 +204,34 @@ def test_metalens_structure():
     assert np.all(col[j_sub + 1:j_sub + 13] > 6.0) and np.all(np.abs(col[j_sub + 16:w.ny - npml] - 1.0) < 1e-12)
     nz = np.argwhere(w.b[0] != 0)
     assert set(nz[:, 1]) == {npml + 10} and len(nz) == w.nx
+
+
+def _mutated_mode(eps_line, dy, mutation):
+    """slab_mode with one planted mistake (test-local copy of the eigenproblem)."""
+    from scipy.linalg import eigh_tridiagonal
+    k0 = 2 * math.pi
+    n = eps_line.size
+    diag = (-1.0 if mutation == "half-diagonal" else -2.0) / dy ** 2 + \
+        (-1.0 if mutation == "k0-sign" else 1.0) * k0 ** 2 * eps_line
+    off = np.full(n - 1, 1.0 / dy ** 2)
+    pick = n - 2 if mutation == "second-mode" else n - 1
+    val, vec = eigh_tridiagonal(diag, off, select="i", select_range=(pick, pick))
+    phi = vec[:, 0] / vec[np.argmax(np.abs(vec[:, 0])), 0]
+    return math.sqrt(abs(val[0])), phi
+
+
+@pytest.mark.parametrize("mutation", ["half-diagonal", "second-mode", "k0-sign"])
+def test_mode_pins_catch_planted_mistakes(mutation):
+    """Each planted mistake in the mode eigenproblem fails a pin above: the
+    dispersion relation (within 2e-3 at lambda/48 for an off-grid core) or the
+    fundamental mode's shape (no sign change, peak on the core)."""
+    eps, d, yc = cross_section(48)
+    exact = slab_beta(0.45)
+    beta, phi = _mutated_mode(eps, d, mutation)
+    y = np.arange(eps.size) * d
+    dispersion_ok = abs(beta - exact) < 2e-3 * exact
+    shape_ok = phi.min() > -1e-12 and abs(y[np.argmax(phi)] - yc) <= d
+    assert not (dispersion_ok and shape_ok)
+    # the unmutated solver passes both
+    b0, p0 = W.slab_mode(eps, d, 1.0)
+    assert abs(b0 - exact) < 2e-3 * exact and p0.min() > -1e-12
