@@ -17,7 +17,11 @@
 // im2col copy is made.  The B operand (weights) is packed once per weight
 // update into the exact shared-memory order and arrives by one bulk copy per
 // chunk.  Activations and weights are double-buffered: chunk c+1 is staged
-// while the MMAs of chunk c run.  Every wait has an iteration limit; a
+// while the MMAs of chunk c run, and the FP32 halo loads of chunk c+1 are
+// issued before chunk c is converted.  When an image has too few tiles to
+// fill the GPU, the chunks are split over CTAs (blockIdx.z); their partial
+// sums go to a scratch buffer that k_splitk_finish adds in a fixed order
+// with the bias and the activation.  Every wait has an iteration limit; a
 // timeout sets the error flag and the CTA stops cleanly.
 #include <cuda_bf16.h>
 
