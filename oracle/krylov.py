@@ -31,14 +31,24 @@ def _givens(a, b):
     return c, s
 
 
-def gmres(matvec, precond, b, restart=30, rtol=1e-10, maxit=1000, x0=None, flexible=True):
+def gmres(matvec, precond, b, restart=30, rtol=1e-10, maxit=1000, x0=None, flexible=True, dot=None):
     """Restarted right-preconditioned (F)GMRES.
 
     Returns (x, history, iterations) with history the relative residual
-    estimate after every inner step (history[0] = initial true residual)."""
+    estimate after every inner step (history[0] = initial true residual).
+    ``dot`` (default: np.vdot over the whole vector) is the inner product
+    conj(a) . b; a vector split over processes passes one that sums the
+    processes' partial products, and norms are then sqrt(dot(w, w))."""
+    if dot is None:
+        vdot, norm = np.vdot, np.linalg.norm
+    else:
+        vdot = dot
+
+        def norm(w):
+            return float(np.sqrt(max(dot(w, w).real, 0.0)))
     b = np.asarray(b, dtype=np.complex128)
     n = b.shape[0]
-    bnorm = np.linalg.norm(b)
+    bnorm = norm(b)
     if bnorm == 0:
         return np.zeros_like(b), [0.0], 0
     x = np.zeros(n, np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
@@ -46,7 +56,7 @@ def gmres(matvec, precond, b, restart=30, rtol=1e-10, maxit=1000, x0=None, flexi
     its = 0
     while True:
         r = b - matvec(x)
-        beta = np.linalg.norm(r)
+        beta = norm(r)
         if not history:
             history.append(beta / bnorm)
         if beta / bnorm <= rtol or its >= maxit:
@@ -67,9 +77,9 @@ def gmres(matvec, precond, b, restart=30, rtol=1e-10, maxit=1000, x0=None, flexi
                 Z[j] = z
             w = matvec(z)
             for i in range(j + 1):                       # modified Gram-Schmidt
-                H[i, j] = np.vdot(V[i], w)
+                H[i, j] = vdot(V[i], w)
                 w = w - H[i, j] * V[i]
-            H[j + 1, j] = np.linalg.norm(w)
+            H[j + 1, j] = norm(w)
             for i in range(j):                           # earlier rotations
                 t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
                 H[i + 1, j] = -np.conj(sn[i]) * H[i, j] + cs[i] * H[i + 1, j]
@@ -87,7 +97,7 @@ def gmres(matvec, precond, b, restart=30, rtol=1e-10, maxit=1000, x0=None, flexi
             if abs(hjj) == 0:
                 breakdown = True
             else:
-                nrm = np.linalg.norm(w)
+                nrm = norm(w)
                 if nrm == 0:
                     breakdown = True
                 else:
