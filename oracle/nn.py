@@ -26,7 +26,10 @@ from the network field).
 Parity status: forward and backward are pinned by central finite
 differences, by an independent torch.nn.functional restatement with
 autograd, and by scipy's correlate2d for the convolution; the scaling by the
-closed-form least-squares solution.
+closed-form least-squares solution.  The tensor-core mode's operand rounding
+(conv3x3_tc, conv3x3_backward_tc) is pinned by a torch restatement whose
+autograd functions round with torch's own bfloat16 conversion at the same
+points (forward, input-gradient and weight-gradient operands).
 """
 from __future__ import annotations
 
@@ -135,6 +138,32 @@ def _conv_backward(x, W, gout):
     return conv3x3_backward(x, W, gout)
 
 
+# Tensor-core mode (round_act).  The network's convolutions run as matrix
+# products on BF16 operands with FP32 (here: exact) accumulation, so exactly
+# the values that enter a product as an operand are rounded to BF16, and
+# nothing else:
+#   forward            out = conv(bf16(x), W) + b      operands: layer input, weights
+#   input gradient     gx  = conv_T(bf16(g), W)        operands: output gradient, weights
+#   weight gradient    gW  = corr(bf16(x), bf16(g))    operands: layer input, output gradient
+#   bias gradient      gb  = sum(g)                    a plain sum, not a product: unrounded
+# (the weights W are the BF16 copy of the master weights in this mode).
+def conv3x3_tc(x, W, b):
+    """Forward convolution of the tensor-core mode: the layer input rounded
+    to BF16 before the product."""
+    return _conv(bf16_round(x), W, b)
+
+
+def conv3x3_backward_tc(x, W, gout):
+    """Backward convolution of the tensor-core mode: (gx, gW, gb) with the
+    output gradient rounded to BF16 in both gradient products, the layer
+    input rounded to BF16 in the weight-gradient product, and the bias
+    gradient summed from the unrounded output gradient."""
+    gr = bf16_round(gout)
+    gx, _, _ = _conv_backward(x, W, gr)
+    _, gW, _ = _conv_backward(bf16_round(x), W, gr)
+    return gx, gW, gout.sum(axis=(0, 2, 3))
+
+
 def forward(params, x, L, c0, cmax, round_bf16=False, round_act=False):
     """Network output [N, 2, H, W] and the cache the backward pass needs.
     round_bf16 rounds the weights to BF16; round_act also rounds every
@@ -142,11 +171,7 @@ def forward(params, x, L, c0, cmax, round_bf16=False, round_act=False):
     mode; it makes the loss piecewise constant, so finite differences do not
     apply to it)."""
     p = bf16_round(params) if round_bf16 else params
-    if round_act:
-        def conv3x3(v, W, b):
-            return _conv(bf16_round(v), W, b)
-    else:
-        conv3x3 = _conv
+    conv3x3 = conv3x3_tc if round_act else _conv
     layers = unpack(p, L, c0, cmax)
     enc = [(layers[2 * l], layers[2 * l + 1]) for l in range(L)]
     dec = {}
@@ -184,18 +209,7 @@ def backward(cache, gout, L):
     """Flat parameter gradient and input gradient for output gradient gout
     (the chain rule through forward() in reverse order)."""
     enc, dec, out_layer = cache["enc"], cache["dec"], cache["out_layer"]
-    if cache.get("round_act"):
-        # tensor-core mode: both gradient convolutions read BF16 output
-        # gradients; the weight gradient also reads the BF16-rounded layer
-        # input; the bias gradient sums the unrounded output gradients
-        def conv3x3_backward(x, W, gout):
-            gr = bf16_round(gout)
-            gx, _, _ = _conv_backward(x, W, gr)
-            _, gW, _ = _conv_backward(bf16_round(x), W, gr)
-            return gx, gW, gout.sum(axis=(0, 2, 3))
-
-    else:
-        conv3x3_backward = _conv_backward
+    conv3x3_backward = conv3x3_backward_tc if cache.get("round_act") else _conv_backward
     grads = {}
     gd, gW, gb = conv3x3_backward(cache["last"], out_layer[0], gout)
     grads["out"] = (gW, gb)

@@ -232,3 +232,138 @@ def test_images_layout():
     assert inp[0, 1, 2] == (eps[2, 1] - 1) / 10 and inp[0, 3, :].sum() == 0 and inp[0, :, 4:].sum() == 0
     assert inp[1, 1, 2] == -1.0 and inp[2, 1, 2] == 0.5
     assert tgt[0, 2, 3] == 1.0 / 2.0 and tgt[1, 2, 3] == -0.25
+
+
+# ------------------------------------------------ tensor-core operand rounding
+def _torch_net_tc(p, x, L, c0, cmax):
+    """Independent restatement of the tensor-core mode in torch float64: the
+    weights are the BF16 copy of the master weights (gradient passed straight
+    through to the masters), and every convolution is an autograd function
+    whose products read BF16-rounded operands -- forward: the layer input;
+    input gradient: the output gradient; weight gradient: the layer input and
+    the output gradient -- while the bias gradient sums the unrounded output
+    gradient.  Rounding is torch's own float64 -> bfloat16 conversion."""
+    import torch
+    import torch.nn.functional as F
+    from torch.nn.grad import conv2d_input, conv2d_weight
+
+    def bf(t):
+        return t.to(torch.bfloat16).to(torch.float64)
+
+    class RoundSTE(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, t):
+            return bf(t)
+
+        @staticmethod
+        def backward(ctx, g):
+            return g
+
+    class ConvTC(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, inp, w, b):
+            ctx.save_for_backward(inp, w)
+            return F.conv2d(bf(inp), w, b, padding=1)
+
+        @staticmethod
+        def backward(ctx, g):
+            inp, w = ctx.saved_tensors
+            gr = bf(g)
+            gx = conv2d_input(inp.shape, w, gr, padding=1)
+            gw = conv2d_weight(bf(inp), w.shape, gr, padding=1)
+            return gx, gw, g.sum(dim=(0, 2, 3))
+
+    ch = [min(cmax, c0 << l) for l in range(L)]
+    P = torch.tensor(p, requires_grad=True)
+    X = torch.tensor(x, requires_grad=True)
+    Pr = RoundSTE.apply(P)
+    off = [0]
+
+    def take(ci, co):
+        w = Pr[off[0]:off[0] + co * ci * 9].view(co, ci, 3, 3)
+        off[0] += co * ci * 9
+        b = Pr[off[0]:off[0] + co]
+        off[0] += co
+        return w, b
+
+    conv = ConvTC.apply
+    encw = [(take(3 if l == 0 else ch[l - 1], ch[l]), take(ch[l], ch[l])) for l in range(L)]
+    decw = {}
+    for l in range(L - 2, -1, -1):
+        decw[l] = (take(ch[l + 1], ch[l]), take(ch[l], ch[l]))
+    outw = take(ch[0], 2)
+    skips = []
+    h = X
+    for l in range(L):
+        if l > 0:
+            h = F.avg_pool2d(skips[-1], 2)
+        h = F.relu(conv(h, *encw[l][0]))
+        skips.append(F.relu(conv(h, *encw[l][1])))
+    d = skips[-1]
+    for l in range(L - 2, -1, -1):
+        u = F.interpolate(d, scale_factor=2, mode="nearest")
+        c = F.relu(conv(u, *decw[l][0]))
+        d = F.relu(conv(c + skips[l], *decw[l][1]))
+    return P, X, conv(d, *outw)
+
+
+def _tc_compare(L_, c0, cmax, H, W, seed=12):
+    import torch
+    p, x, t = _case(seed=seed, N=2, H=H, W=W, L=L_, c0=c0, cmax=cmax)
+    P, X, Y = _torch_net_tc(p, x, L_, c0, cmax)
+    loss = ((Y - torch.tensor(t)) ** 2).mean()
+    loss.backward()
+    out, _ = O.forward(p, x, L_, c0, cmax, round_bf16=True, round_act=True)
+    l2, gp, gx = O.loss_and_grad(p, x, t, L_, c0, cmax, round_bf16=True, round_act=True)
+    return (np.abs(out - Y.detach().numpy()).max() / np.abs(out).max(), abs(l2 - loss.item()) / loss.item(),
+            np.abs(gp - P.grad.numpy()).max() / np.abs(gp).max(),
+            np.abs(gx - X.grad.numpy()).max() / np.abs(gx).max())
+
+
+@pytest.mark.parametrize("L_,c0,cmax,H,W", [(2, 4, 4, 16, 16), (3, 2, 6, 8, 16), (1, 3, 3, 6, 5)])
+def test_tensor_core_rounding_matches_torch_restatement(L_, c0, cmax, H, W):
+    """The oracle's tensor-core mode (BF16 weights, BF16 operands of every
+    convolution product) equals the torch restatement with autograd functions
+    that round at the same operands: forward, loss, parameter and input
+    gradients."""
+    e_out, e_loss, e_gp, e_gx = _tc_compare(L_, c0, cmax, H, W)
+    assert e_out < 1e-12 and e_loss < 1e-12
+    assert e_gp < 1e-10 and e_gx < 1e-10
+
+
+def test_tensor_core_rounding_differs_from_unrounded():
+    """The rounding is visible: the unrounded network's gradients differ from
+    the tensor-core mode's by far more than the restatement's tolerance."""
+    p, x, t = _case(seed=12, N=2, H=16, W=16)
+    _, g_tc, _ = O.loss_and_grad(p, x, t, L, C0, CMAX, round_bf16=True, round_act=True)
+    _, g_w, _ = O.loss_and_grad(p, x, t, L, C0, CMAX, round_bf16=True)
+    assert np.abs(g_tc - g_w).max() / np.abs(g_w).max() > 1e-4
+
+
+@pytest.mark.parametrize("plant", ["bias_from_rounded", "input_grad_unrounded", "wgrad_input_unrounded",
+                                   "forward_unrounded"])
+def test_tensor_core_rounding_mutations_are_caught(monkeypatch, plant):
+    """Each rounding point moved in the oracle (planted here, on the CPU)
+    fails the torch restatement."""
+    real_bwd, real_conv = O.conv3x3_backward_tc, O._conv_backward
+
+    def bias_from_rounded(x, W, gout):
+        gx, gW, _ = real_bwd(x, W, gout)
+        return gx, gW, O.bf16_round(gout).sum(axis=(0, 2, 3))
+
+    def input_grad_unrounded(x, W, gout):
+        _, gW, gb = real_bwd(x, W, gout)
+        gx, _, _ = real_conv(x, W, gout)
+        return gx, gW, gb
+
+    def wgrad_input_unrounded(x, W, gout):
+        gx, _, gb = real_bwd(x, W, gout)
+        _, gW, _ = real_conv(x, W, O.bf16_round(gout))
+        return gx, gW, gb
+
+    if plant == "forward_unrounded":
+        monkeypatch.setattr(O, "conv3x3_tc", lambda x, W, b: O._conv(x, W, b))
+    else:
+        monkeypatch.setattr(O, "conv3x3_backward_tc", locals()[plant])
+    e_out, e_loss, e_gp, e_gx = _tc_compare(2, 4, 4, 16, 16)
+    assert max(e_out, e_loss, e_gp, e_gx) > 1e-6
