@@ -192,12 +192,16 @@ stdd_status stdd_residual(stdd_ctx *ctx, const double *x, const double *b, doubl
 
 /* Same result as stdd_residual, without allocating device memory.  The
  * paper has no counterpart: this entry point exists for callers that may not
- * call cudaMalloc at the time they need a residual -- code that runs while a
- * CUDA graph is being built or replayed, real-time loops that reserve all of
- * their memory up front, or host applications that hand out GPU memory only
- * through their own pool.
+ * call cudaMalloc at the time they need a residual -- real-time loops that
+ * reserve all of their device memory before they start, or host
+ * applications that hand out GPU memory only through their own pool and
+ * forbid libraries to allocate behind it.
  *   x, b : device pointers, 2*nx*ny doubles each (inputs);
- *   r    : device pointer, 2*nx*ny doubles (output, b - A x);
+ *   r    : device pointer, 2*nx*ny doubles (output, b - A x).  r may be the
+ *          same buffer as b (each entry of b is read before it is
+ *          overwritten) but must not overlap x, whose neighbouring entries
+ *          other threads still read, nor overlap b only in part: both are
+ *          rejected with STDD_EINVAL;
  *   *rel_out : host double, ||r|| / ||b|| (||r|| if b = 0).
  * Scratch is one fixed array compiled into the library (2*16384 + 2
  * doubles, about 256 KiB); every GPU that loads the library keeps it until
@@ -316,11 +320,18 @@ enum {
 stdd_status stdd_set_option(stdd_ctx *ctx, int option, int value);
 stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);
 
-/* Diagnostic: one 64 x 128 complex tile product on the tensor cores
- * (tcgen05, the kernel path of STDD_PREC_C64_BF16 / _FP16) against a
- * double-precision host reference.  fmt 0 = FP16, 1 = BF16.  *rel_err =
- * max |error| / max |result|.  No counterpart in the paper. */
-stdd_status stdd_tc_selftest(int device, int fmt, double *rel_err);
+/* Diagnostic: one tile product D = C R of the tensor-core front update
+ * (tcgen05, the kernel path of STDD_PREC_C64_BF16 / _FP16) with host
+ * arrays, so that a caller can check it against its own reference.  C is
+ * 64 x kc complex, R kc x 128, D 64 x 128, all column-major interleaved
+ * doubles (C(i, j) at 2 (j*64 + i), R(j, c) at 2 (c*kc + j), D(i, c) at
+ * 2 (c*64 + i)); 1 <= kc <= 32.  The inputs are converted to float, scaled
+ * by a power of two per operand (2^ea for C, 2^eb for R, with the largest
+ * |component| scaled into [1, 2)), rounded to FP16 (fmt 0) or BF16 (fmt 1),
+ * multiplied with FP32 accumulation through the real 2 x 2 embedding of the
+ * complex product, and scaled back by 2^-(ea+eb).  STDD_ETIMEOUT if the
+ * tile's bounded wait gave up.  No counterpart in the paper. */
+stdd_status stdd_tc_tile_product(int device, int fmt, int kc, const double *C, const double *R, double *D);
 
 /* Host-only nested-dissection analysis of one W x H box (no GPU needed).
  * First call with nodes == NULL to get *nfronts and *nnodes; then call

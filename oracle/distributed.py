@@ -39,6 +39,15 @@ class RankStrips:
         self.ddm = DDM(prob, nsub, overlap, interface_pml)
         self.k0, self.k1 = rank * nsub // world, (rank + 1) * nsub // world
         st = self.ddm.strips
+        # a local field spills ext columns past its strip; the exchange hands
+        # each spill to the adjacent rank only, so every rank must own at
+        # least ext columns (else the spill would reach two ranks away)
+        ext = overlap + interface_pml
+        for r in range(world):
+            a, b = r * nsub // world, (r + 1) * nsub // world
+            if world > 1 and st[b - 1].c1 - st[a].c0 < ext:
+                raise ValueError(f"rank {r} owns {st[b - 1].c1 - st[a].c0} columns, fewer than overlap + "
+                                 f"interface PML = {ext}: its neighbours' fields would reach past it")
         self.C0, self.C1 = st[self.k0].c0, st[self.k1 - 1].c1
         self.L0, self.L1 = st[self.k0].x0, st[self.k1 - 1].x1   # columns the rank's local fields reach
         self.sent_values = 0                                   # complex values sent so far

@@ -81,7 +81,7 @@ _SIGS = {
     "stdd_set_profiling": (c_int, [c_void_p, c_int]),
     "stdd_set_option": (c_int, [c_void_p, c_int, c_int]),
     "stdd_get_profile": (c_int, [c_void_p, P(stdd_profile), c_int]),
-    "stdd_tc_selftest": (c_int, [c_int, c_int, P(c_double)]),
+    "stdd_tc_tile_product": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "stdd_nd_analyze": (c_int, [c_int, c_int, c_int, P(c_int), P(ctypes.c_longlong), c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_void_p]),
     "stdd_nn_create": (c_int, [P(c_void_p), c_int, c_void_p, c_int, c_int, c_int, c_int, ctypes.c_ulonglong]),
@@ -295,13 +295,23 @@ def stdd_get_profile(ctx, reset=True):
     return {k: getattr(s, k) for k, _ in stdd_profile._fields_}
 
 
-def stdd_tc_selftest(device=0, fmt=1):
-    """Relative error of one tensor-core tile product (fmt 0 FP16, 1 BF16)."""
-    e = c_double(0.0)
-    st = lib.stdd_tc_selftest(int(device), int(fmt), ctypes.byref(e))
+def stdd_tc_tile_product(C, R, fmt=1, device=0):
+    """D = C R on the tensor cores (one tile of the mixed-precision front
+    update): C complex (64, kc), R complex (kc, 128), 1 <= kc <= 32; returns D
+    complex (64, 128)."""
+    C = np.asarray(C, np.complex128)
+    R = np.asarray(R, np.complex128)
+    kc = C.shape[1]
+    if C.shape != (64, kc) or R.shape != (kc, 128):
+        raise ValueError("C must be 64 x kc and R kc x 128")
+    Cf = np.ascontiguousarray(C.T)          # column-major: column j contiguous
+    Rf = np.ascontiguousarray(R.T)
+    D = np.empty((128, 64), np.complex128)  # column-major D
+    st = lib.stdd_tc_tile_product(int(device), int(fmt), int(kc), c_void_p(Cf.ctypes.data),
+                                  c_void_p(Rf.ctypes.data), c_void_p(D.ctypes.data))
     if st != STDD_OK:
-        raise StddError(st, "stdd_tc_selftest failed")
-    return e.value
+        raise StddError(st, "stdd_tc_tile_product failed")
+    return D.T.copy()
 
 
 def stdd_nd_analyze(W, H, leaf_max=64):

@@ -2060,20 +2060,26 @@ stdd_status stdd_learned_guess_info(stdd_ctx *c, int rhs, double *raw_rel, doubl
   });
 }
 
-stdd_status stdd_tc_selftest(int device, int fmt, double *rel_err) {
-  if (!rel_err || (fmt != 0 && fmt != 1)) return STDD_EINVAL;
+stdd_status stdd_tc_tile_product(int device, int fmt, int kc, const double *C, const double *R, double *D) {
+  if (!C || !R || !D || (fmt != 0 && fmt != 1) || kc < 1 || kc > stdd::MF_NB) return STDD_EINVAL;
   if (cudaSetDevice(device) != cudaSuccess) {
     (void)cudaGetLastError();
     return STDD_ECUDA;
   }
+  std::vector<float2> c((size_t)64 * kc), r((size_t)kc * 128), d((size_t)64 * 128);
+  for (size_t i = 0; i < c.size(); ++i) c[i] = make_float2((float)C[2 * i], (float)C[2 * i + 1]);
+  for (size_t i = 0; i < r.size(); ++i) r[i] = make_float2((float)R[2 * i], (float)R[2 * i + 1]);
   cudaError_t e = cudaSuccess;
-  const double r = stdd::tc_selftest(fmt, &e);
-  if (e != cudaSuccess) {
+  const int st = stdd::tc_tile_product(fmt, kc, c.data(), r.data(), d.data(), &e);
+  if (st < 0) {
     (void)cudaGetLastError();
     return STDD_ECUDA;
   }
-  if (r == -1.0) return STDD_ETIMEOUT;
-  *rel_err = r;
+  if (st == 1) return STDD_ETIMEOUT;
+  for (size_t i = 0; i < d.size(); ++i) {
+    D[2 * i] = d[i].x;
+    D[2 * i + 1] = d[i].y;
+  }
   return STDD_OK;
 }
 
@@ -2110,13 +2116,12 @@ stdd_status stdd_nd_analyze(int W, int H, int leaf_max, int *nfronts, long long 
 //
 // stdd_residual stages its inputs in context buffers and reduces through
 // context scratch that it grows with cudaMalloc on first use.  Callers that
-// must not allocate device memory at call time -- code running between the
-// capture of a CUDA graph and its launch, real-time loops that pre-reserve
-// all memory, or hosts that hand out GPU memory only through their own pool
-// -- use stdd_residual_noalloc instead: it reads and writes only the
-// caller's device buffers and a fixed scratch array compiled into this
-// library (g_noalloc_scratch, ~256 KiB), which every GPU that loads the
-// library keeps until the process exits.
+// must not allocate device memory at call time -- real-time loops that
+// reserve all of their memory before they start, or hosts that hand out GPU
+// memory only through their own pool -- use stdd_residual_noalloc instead:
+// it reads and writes only the caller's device buffers and a fixed scratch
+// array compiled into this library (g_noalloc_scratch, ~256 KiB), which
+// every GPU that loads the library keeps until the process exits.
 // ------------------------------------------------------------------------
 namespace {
 
@@ -2220,6 +2225,18 @@ extern "C" stdd_status stdd_residual_noalloc(stdd_ctx *c, const double *x, const
     return STDD_EINVAL;
   }
   const int64_t n = c->N();
+  {
+    // r is written while other threads still read x's neighbours: it must
+    // not overlap x; r == b is safe (b[idx] is read before r[idx] is
+    // written by the same thread), a partial overlap with b is not
+    const uintptr_t bytes = (uintptr_t)n * 2 * sizeof(double);
+    const uintptr_t pr = (uintptr_t)r, px = (uintptr_t)x, pb = (uintptr_t)b;
+    auto overlap = [&](uintptr_t a, uintptr_t o) { return a < o + bytes && o < a + bytes; };
+    if (n > 0 && (overlap(pr, px) || (pr != pb && overlap(pr, pb)))) {
+      c->err = "stdd_residual_noalloc: r must not overlap x, and may overlap b only as the same buffer";
+      return STDD_EINVAL;
+    }
+  }
   if (n > NA_MAX_NODES) {
     c->err = "stdd_residual_noalloc: grid has more than 67,108,864 nodes, the size of its fixed scratch";
     return STDD_EINVAL;

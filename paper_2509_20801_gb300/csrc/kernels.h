@@ -66,7 +66,9 @@ void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_
 // ---- tensor-core front updates (kernels_tc.cu), complex64 fronts only
 cudaError_t tc_setup_attributes();
 void mf_tc_update_launch(const MfArgs &a, const LevelInfo &L, int k, int fmt, cudaStream_t st);
-double tc_selftest(int fmt, cudaError_t *err);
+// one 64 x kc by kc x 128 complex tile product on the tensor cores from host
+// arrays: 0 ok, 1 wait timed out, -1 CUDA error (*err)
+int tc_tile_product(int fmt, int kc, const float2 *C, const float2 *R, float2 *D, cudaError_t *err);
 template <typename R>
 void mf_up_gather_level(const MfArgs &a, const LevelInfo &L, int nrhs, int64_t ldt, cudaStream_t st);
 template <typename R>

@@ -24,7 +24,6 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
-#include <random>
 #include <vector>
 
 #include "common.cuh"
@@ -213,15 +212,17 @@ __global__ void __launch_bounds__(128) mf_gj_update_tc(MfArgs a, int f0, int k) 
   if (!tc_tile<FMT>(sm, nbk, cload, rload, sink) && threadIdx.x == 0) atomicOr(a.flag, 2);
 }
 
-// Self-test tile: D = C R with C (64 x 32) and R (32 x 128) column-major.
+// One tile D = C R with C (64 x kc) and R (kc x 128) complex, column-major
+// (C(rr, j) at j * 64 + rr, R(j, cc) at cc * kc + j, D(rr, cc) at cc * 64 + rr).
 template <int FMT>
-__global__ void __launch_bounds__(128) tc_selftest_kernel(const float2 *C, const float2 *R, float2 *D, int *flag) {
+__global__ void __launch_bounds__(128) tc_tile_kernel(const float2 *C, const float2 *R, float2 *D, int kc,
+                                                      int *flag) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   TileSmem &sm = *reinterpret_cast<TileSmem *>(smem_raw);
   auto cload = [&](int rr, int j) { return C[j * TC_MC + rr]; };
-  auto rload = [&](int cc, int j) { return R[cc * TC_KC + j]; };
+  auto rload = [&](int cc, int j) { return R[cc * kc + j]; };
   auto sink = [&](int rr, int cc, int comp, float v) { reinterpret_cast<float *>(&D[cc * TC_MC + rr])[comp] = v; };
-  if (!tc_tile<FMT>(sm, TC_KC, cload, rload, sink) && threadIdx.x == 0) atomicOr(flag, 2);
+  if (!tc_tile<FMT>(sm, kc, cload, rload, sink) && threadIdx.x == 0) atomicOr(flag, 2);
 }
 
 }  // namespace
@@ -234,7 +235,7 @@ template <int FMT> cudaError_t tc_setup_attributes_fmt() {
   cudaError_t e = cudaFuncSetAttribute(mf_gj_update_tc<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tc_smem_bytes());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc_selftest_kernel<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(tc_tile_kernel<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)tc_smem_bytes());
 }
 
@@ -252,15 +253,11 @@ void mf_tc_update_launch(const MfArgs &a, const LevelInfo &L, int k, int fmt, cu
   count_launch();
 }
 
-// Host-side check of one tensor-core tile against a double-precision
-// reference; returns the largest |error| / max |D| or a negative value if the
-// device reported a timeout.
-double tc_selftest(int fmt, cudaError_t *err) {
-  std::mt19937 rng(12345);
-  std::normal_distribution<float> nd(0.f, 1.f);
-  std::vector<float2> C(TC_MC * TC_KC), R(TC_KC * TC_N), D(TC_MC * TC_N);
-  for (auto &v : C) v = make_float2(nd(rng), nd(rng));
-  for (auto &v : R) v = make_float2(nd(rng), nd(rng));
+// One tile product on the device from host arrays (see tc_tile_kernel for
+// the layouts); returns 0 on success, 1 if the device reported a timeout,
+// -1 on a CUDA error (*err).
+int tc_tile_product(int fmt, int kc, const float2 *C, const float2 *R, float2 *D, cudaError_t *err) {
+  const size_t nc = (size_t)TC_MC * kc, nr = (size_t)kc * TC_N, nd = (size_t)TC_MC * TC_N;
   float2 *dC = nullptr, *dR = nullptr, *dD = nullptr;
   int *dflag = nullptr;
   *err = cudaSuccess;
@@ -268,42 +265,29 @@ double tc_selftest(int fmt, cudaError_t *err) {
     if (e != cudaSuccess && *err == cudaSuccess) *err = e;
     return e == cudaSuccess;
   };
-  bool ok = ck(tc_setup_attributes()) && ck(cudaMalloc(&dC, C.size() * sizeof(float2))) &&
-            ck(cudaMalloc(&dR, R.size() * sizeof(float2))) && ck(cudaMalloc(&dD, D.size() * sizeof(float2))) &&
+  bool ok = ck(tc_setup_attributes()) && ck(cudaMalloc(&dC, nc * sizeof(float2))) &&
+            ck(cudaMalloc(&dR, nr * sizeof(float2))) && ck(cudaMalloc(&dD, nd * sizeof(float2))) &&
             ck(cudaMalloc(&dflag, sizeof(int)));
   int flag = 0;
   if (ok) {
-    ok = ck(cudaMemcpy(dC, C.data(), C.size() * sizeof(float2), cudaMemcpyHostToDevice)) &&
-         ck(cudaMemcpy(dR, R.data(), R.size() * sizeof(float2), cudaMemcpyHostToDevice)) &&
-         ck(cudaMemset(dD, 0, D.size() * sizeof(float2))) && ck(cudaMemset(dflag, 0, sizeof(int)));
+    ok = ck(cudaMemcpy(dC, C, nc * sizeof(float2), cudaMemcpyHostToDevice)) &&
+         ck(cudaMemcpy(dR, R, nr * sizeof(float2), cudaMemcpyHostToDevice)) &&
+         ck(cudaMemset(dD, 0, nd * sizeof(float2))) && ck(cudaMemset(dflag, 0, sizeof(int)));
   }
   if (ok) {
-    if (fmt == 1) tc_selftest_kernel<1><<<1, 128, tc_smem_bytes()>>>(dC, dR, dD, dflag);
-    else tc_selftest_kernel<0><<<1, 128, tc_smem_bytes()>>>(dC, dR, dD, dflag);
+    if (fmt == 1) tc_tile_kernel<1><<<1, 128, tc_smem_bytes()>>>(dC, dR, dD, kc, dflag);
+    else tc_tile_kernel<0><<<1, 128, tc_smem_bytes()>>>(dC, dR, dD, kc, dflag);
+    count_launch();
     ok = ck(cudaGetLastError()) && ck(cudaDeviceSynchronize()) &&
-         ck(cudaMemcpy(D.data(), dD, D.size() * sizeof(float2), cudaMemcpyDeviceToHost)) &&
+         ck(cudaMemcpy(D, dD, nd * sizeof(float2), cudaMemcpyDeviceToHost)) &&
          ck(cudaMemcpy(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost));
   }
   cudaFree(dC);
   cudaFree(dR);
   cudaFree(dD);
   cudaFree(dflag);
-  if (!ok) return -2.0;
-  if (flag) return -1.0;
-  double emax = 0, dmax = 0;
-  for (int cc = 0; cc < TC_N; ++cc)
-    for (int rr = 0; rr < TC_MC; ++rr) {
-      double re = 0, im = 0;
-      for (int j = 0; j < TC_KC; ++j) {
-        const float2 a = C[j * TC_MC + rr], b = R[cc * TC_KC + j];
-        re += (double)a.x * b.x - (double)a.y * b.y;
-        im += (double)a.x * b.y + (double)a.y * b.x;
-      }
-      const float2 d = D[cc * TC_MC + rr];
-      emax = std::max(emax, std::max(std::fabs(d.x - re), std::fabs(d.y - im)));
-      dmax = std::max(dmax, std::max(std::fabs(re), std::fabs(im)));
-    }
-  return emax / dmax;
+  if (!ok) return -1;
+  return flag ? 1 : 0;
 }
 
 }  // namespace stdd

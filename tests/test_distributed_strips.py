@@ -87,3 +87,24 @@ def test_strips_over_gloo_ranks_match_the_single_process_oracle(world):
         # rank's cuts (one cut for the end ranks, two for inner ones)
         cuts = (r["rank"] > 0) + (r["rank"] < world - 1)
         assert r["sent_pc"] == cuts * ext * ny
+
+
+def test_rank_narrower_than_the_spill_is_rejected():
+    """Every rank must own at least overlap + interface PML columns, else a
+    neighbour's local field would spill past it to the next rank.  The
+    partition already refuses strips narrower than that (each strip is some
+    strip's neighbour), so every rank of at least one strip owns enough
+    columns; the rank split checks it again, and a split that breaks it is
+    refused before any exchange (no process group is needed)."""
+    sys.path.insert(0, ROOT)
+    import workloads as W
+    from oracle.distributed import RankStrips
+    from oracle.fdfd import Problem
+    w = W.random_medium(60, 24, ppw=16, seed=3, npml=6, nsub=6, overlap=4, interface_pml=6)
+    P = Problem.from_workload(w)
+    # 6 strips of 10 columns over 6 ranks: 10 owned columns, ext = 10 -> allowed
+    R = RankStrips(P, 6, 4, 6, 0, 6, comm=None)
+    assert R.C1 - R.C0 == 10
+    # ext = 12 > 10 owned columns per rank -> refused
+    with pytest.raises(ValueError, match="fewer than overlap|wider than a neighbouring strip"):
+        RankStrips(P, 6, 6, 6, 0, 6, comm=None)

@@ -1,9 +1,8 @@
 """Tensor-core (tcgen05) front updates of the mixed-precision path.
 
-The tile self-test multiplies one 64 x 32 by 32 x 128 complex tile with BF16
-or FP16 inputs and FP32 accumulation and compares with a double-precision
-host product; the bound is the input rounding (2^-8 for BF16, 2^-11 for FP16,
-relative to the largest entry, times the growth of a 64-term real sum).  The
+One tile (64 x kc by kc x 128 complex, BF16 or FP16 inputs, FP32
+accumulation) is compared with products computed in the test with numpy:
+the product of the scaled and rounded operands, and the unrounded product.  The
 solves check that with these updates the FP64 Krylov iteration still reaches
 its residual and the field matches the oracle's direct solution.
 """
@@ -19,10 +18,47 @@ from oracle.fdfd import Problem  # noqa: E402
 DEV = "cuda:0"
 
 
+def _rounded(a, e, fmt):
+    """a * 2^e rounded to FP16 (fmt 0) / BF16 (fmt 1) by torch, as float64."""
+    t = torch.from_numpy(np.ldexp(a.astype(np.float32), e).astype(np.float32))
+    return t.to(torch.float16 if fmt == 0 else torch.bfloat16).to(torch.float64).numpy()
+
+
+def _scale_exp(a):
+    """e with the largest |component| of a, times 2^e, in [1, 2)."""
+    m = float(np.max(np.abs(np.concatenate([a.real.ravel(), a.imag.ravel()]).astype(np.float32))))
+    return 0 if m == 0 else 1 - int(np.frexp(m)[1])
+
+
 @pytest.mark.parametrize("fmt,bound", [(1, 3e-2), (0, 5e-3)])
-def test_tile_product_matches_host(fmt, bound):
-    from paper_2509_20801_gb300 import stdd_tc_selftest
-    err = stdd_tc_selftest(0, fmt)
+@pytest.mark.parametrize("kc,cs,rs", [(32, 1.0, 1.0), (7, 1e-3, 1e6), (1, 3.0, 1e-5)])
+def test_tile_product_matches_numpy(fmt, bound, kc, cs, rs):
+    """One tensor-core tile D = C R (64 x kc by kc x 128 complex) against
+    products computed here: (i) the float64 product of the operands after the
+    documented power-of-two scaling and FP16 / BF16 rounding (torch's
+    conversions), which the FP32 accumulation of 2 kc real products may miss
+    only by its own rounding; (ii) the unrounded float64 product, within the
+    input rounding (2^-8 BF16, 2^-11 FP16, relative to the largest entry,
+    times the growth of the sum).  Ranges far from 1 (1e-3 x 1e6) exercise the
+    scaling, without which FP16 would overflow."""
+    from paper_2509_20801_gb300 import stdd_tc_tile_product
+    rng = np.random.default_rng(40 + kc)
+    C = (rng.standard_normal((64, kc)) + 1j * rng.standard_normal((64, kc))) * cs
+    R = (rng.standard_normal((kc, 128)) + 1j * rng.standard_normal((kc, 128))) * rs
+    D = stdd_tc_tile_product(C, R, fmt=fmt)
+    C32 = C.astype(np.complex64).astype(np.complex128)
+    R32 = R.astype(np.complex64).astype(np.complex128)
+    ea, eb = _scale_exp(C32), _scale_exp(R32)
+    Cr, Ci = _rounded(C32.real, ea, fmt), _rounded(C32.imag, ea, fmt)
+    Rr, Ri = _rounded(R32.real, eb, fmt), _rounded(R32.imag, eb, fmt)
+    exact_r = (Cr @ Rr - Ci @ Ri) * 2.0 ** -(ea + eb)
+    exact_i = (Cr @ Ri + Ci @ Rr) * 2.0 ** -(ea + eb)
+    mag = (np.abs(Cr) @ np.abs(Rr) + np.abs(Ci) @ np.abs(Ri)) * 2.0 ** -(ea + eb)
+    gam = 2 * (2 * kc) * 2.0 ** -24            # FP32 accumulation of 2 kc products
+    assert np.all(np.abs(D.real - exact_r) <= gam * mag + 1e-300)
+    assert np.all(np.abs(D.imag - exact_i) <= gam * mag + 1e-300)
+    ref = C32 @ R32
+    err = np.abs(D - ref).max() / np.abs(ref).max()
     assert 0.0 < err < bound
 
 
