@@ -4,16 +4,23 @@
 One step = the whole hot path on one synthetic problem whose inputs are
 already in HBM: numeric multifrontal factorization of every strip, then
 flexible GMRES(50) preconditioned by the batched source-transfer sweep until
-the relative residual is <= 1e-8.  Default workload: the 4096 x 1024
-metalens-like strip at lambda/24 (30-cell PML, 16 strips, 12-cell overlap),
-complex128 factors (the plain-FP64 configuration); the complex64-factor
-variant of the same problem is measured beside it.
+the relative residual is <= 1e-8.  Default workload: the mixed-precision
+single large instance, a waveguide network of 8192 x 2048 nodes (16.8 M
+unknowns) at lambda/24 with 32-cell PML and 32 strips (overlap 16), excited
+by its input guide's fundamental mode; the main line is the plain FP64 form
+(complex128 factors, symmetric multiplicative strip order, the fastest FP64
+order on this workload), and the mixed forms (complex64 factors, FP32 or
+FP16 tensor-core front updates, FP64 Krylov) are measured beside it on the
+same problem with their difference from the FP64 field.
 
 Printed: one JSON line (rank 0).  value = MDoF/s = nx*ny*nrhs / (seconds per
 step) / 1e6, summed over ranks (replicas, weak scaling).
 
---impl reference times the CPU oracle (plain SuperLU strip solves + textbook
-FGMRES) on a bounded sample of the same workload on the host cores.
+The CPU baseline (and --impl reference) runs the CPU oracle -- SuperLU
+factors of every strip and the oracle's textbook FGMRES to 1e-8 with the
+additive (Algorithm 1) preconditioner -- on the host cores, one process per
+group of strips (the paper's parallel axis), on a shrunk instance of the same
+generator.
 """
 from __future__ import annotations
 
@@ -75,30 +82,53 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "c64", "bf16", "fp16"],
                     help="factor precision: complex128, complex64, or complex64 with tensor-core (tcgen05) "
                          "front updates from BF16 / FP16 inputs")
-    ap.add_argument("--workload", default="metalens", choices=["metalens", "metalens-small", "cylinder"],
-                    help="metalens: 4096x1024, 16 strips (the benchmark); metalens-small: 1024x1024, 4 strips "
-                         "(profiling captures); cylinder: 200x200, 2 strips")
-    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per step (line sources)")
+    ap.add_argument("--workload", default="waveguide",
+                    choices=["waveguide", "waveguide-small", "metalens", "metalens-small", "cylinder"],
+                    help="waveguide: 8192x2048 network, 32 strips (the benchmark); waveguide-small: 2048x512, "
+                         "8 strips (profiling captures); metalens: 4096x1024, 16 strips; metalens-small: "
+                         "1024x1024, 4 strips; cylinder: 200x200, 2 strips")
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per step (metalens: line sources)")
     ap.add_argument("--leaf", type=int, default=16, help="nested-dissection leaf size (nodes)")
-    ap.add_argument("--band", type=int, default=1, choices=[0, 1],
-                    help="1: band-space FGMRES (FP64 factors, additive order; same iterates, band-sized vectors)")
-    ap.add_argument("--order", default="additive", choices=["additive", "multiplicative", "red-black"],
-                    help="preconditioner order: additive (Algorithm 1, the benchmark), symmetric multiplicative, "
-                         "or red-black")
+    ap.add_argument("--band", type=int, default=None, choices=[0, 1],
+                    help="1: band-space FGMRES (FP64 factors, additive order; same iterates, band-sized "
+                         "vectors); default 1 where it applies")
+    ap.add_argument("--order", default=None, choices=["additive", "multiplicative", "red-black"],
+                    help="preconditioner order (default: multiplicative on the waveguide, additive -- "
+                         "Algorithm 1 -- elsewhere)")
+    ap.add_argument("--static-pivot", type=int, default=None,
+                    help="static-pivot exponent of the complex64 forms (default 2 on the waveguide, else 0)")
     ap.add_argument("--maxit", type=int, default=2000, help="FGMRES iteration limit per right-hand side")
-    ap.add_argument("--no-compare", action="store_true", help="skip the other-precision run")
+    ap.add_argument("--no-compare", action="store_true", help="skip the other-precision and other-order runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="timed steps of the end-to-end run")
     return ap.parse_args()
 
 
 def make_workload(name, nrhs=1):
     import workloads as W
+    if name == "waveguide":
+        return W.waveguide_network()
+    if name == "waveguide-small":
+        return W.waveguide_network(2048, 512, nsub=8)
     if name == "metalens":
         return W.metalens(nrhs=nrhs)
     if name == "metalens-small":
         return W.metalens(nx=1024, ny=1024, nsub=4, nrhs=nrhs)
     return W.cylinder()
+
+
+def cpu_sample_workload(name, small=False):
+    """(workload, description) of the CPU oracle's sample: the same generator
+    shrunk (strip widths kept, fewer strips and rows)."""
+    import workloads as W
+    if name.startswith("waveguide"):
+        nx, ny, ns = (1024, 384, 4) if small else (2048, 512, 8)
+        return W.waveguide_network(nx, ny, nsub=ns), f"waveguide network shrunk to {nx}x{ny}, {ns} strips"
+    if name.startswith("metalens"):
+        nx, ny, ns = (512, 256, 2) if small else (1024, 512, 4)
+        return W.metalens(nx=nx, ny=ny, nsub=ns), f"metalens shrunk to {nx}x{ny}, {ns} strips"
+    return W.cylinder(), "cylinder 200x200, 2 strips"
 
 
 def workload_desc(w):
@@ -198,48 +228,195 @@ def gemm_peak(torch, dtype, n, reps=3):
 
 
 # ------------------------------------------------------------- CPU oracle
-def oracle_sample(w, its, target_s=20.0):
-    """Time the oracle on a bounded sample of workload w: factor two strips
-    (an end strip and an interior strip) with SuperLU and apply each local
-    solve a few times; scale to all strips and to `its` FGMRES iterations,
-    adding the measured CPU cost of one global matvec + Gram-Schmidt step."""
+def _oracle_worker(conn, prob_kw, ddm_kw, strips, shm_in, shm_out, offs):
+    """One host process of the CPU baseline: it holds the oracle's strip
+    operators for `strips` and serves requests from the parent: "factor"
+    (assemble and SuperLU-factor its strips from scratch) and "solve" (local
+    solutions of the shared input vector into the shared output buffer)."""
     import numpy as np
+    from multiprocessing import shared_memory
 
     from oracle.fdfd import Problem
     from oracle.stddm import DDM
-    t0 = time.perf_counter()
-    P = Problem.from_workload(w)
-    D = DDM.from_workload(w, P)
-    ks = sorted({0, min(1, D.nsub - 1)})
-    t_fac, t_sol, nsol = {}, {}, 3
-    for k in ks:
-        t = time.perf_counter()
-        D.factor(k)
-        t_fac[k] = time.perf_counter() - t
-        v = np.ones(D.strips[k].width * P.ny, complex)
-        t = time.perf_counter()
-        for _ in range(nsol):
-            D.local_solve(k, v)
-        t_sol[k] = (time.perf_counter() - t) / nsol
-    A = P.A
-    x = np.ones(P.n, complex)
-    t = time.perf_counter()
-    for _ in range(3):
-        y = A @ x
-        float(np.vdot(y, x).real)
-    t_mv = (time.perf_counter() - t) / 3
-    sampled = time.perf_counter() - t0
-    end = ks[0]
-    mid = ks[-1]
-    fac_all = t_fac[end] * 2 + t_fac[mid] * max(0, D.nsub - 2) if D.nsub > 1 else t_fac[end]
-    sol_all = t_sol[end] * 2 + t_sol[mid] * max(0, D.nsub - 2) if D.nsub > 1 else t_sol[end]
-    # per FGMRES iteration: one sweep of local solves, one matvec, ~RESTART/2
-    # vectors of Gram-Schmidt (one dot + one axpy each, ~ one matvec of work)
-    per_it = sol_all + t_mv * (1 + RESTART / 2)
-    total = fac_all + its * per_it
-    return dict(total_s=total, factor_s=fac_all, per_iteration_s=per_it, sampled_s=sampled,
-                sample=(f"SuperLU factor of strips {ks} of {D.nsub} + {nsol} local solves each + 3 "
-                        f"matvecs, scaled to {D.nsub} strips and {its} FGMRES iterations"))
+    P = Problem(**prob_kw)
+    D = DDM(P, **ddm_kw)
+    si = shared_memory.SharedMemory(name=shm_in)
+    so = shared_memory.SharedMemory(name=shm_out)
+    vin = np.ndarray((P.n,), np.complex128, buffer=si.buf)
+    vout = np.ndarray((offs[-1],), np.complex128, buffer=so.buf)
+    conn.send("ready")
+    while True:
+        msg = conn.recv()
+        if msg == "factor":
+            for k in strips:
+                D._lu[k] = None
+                D._A_loc[k] = None
+                D.factor(k)
+            conn.send("done")
+        elif msg == "solve":
+            for k in strips:
+                vout[offs[k]:offs[k + 1]] = D.local_solve(k, D.restrict_owned(k, vin))
+            conn.send("done")
+        else:
+            break
+    del vin, vout
+    si.close()
+    so.close()
+
+
+class ParallelOracle:
+    """The CPU oracle's strip method on the host cores: SuperLU factors of
+    every strip (oracle.stddm.DDM) spread over worker processes (started with
+    spawn, before or after CUDA is initialised), the additive
+    preconditioner M^-1 v = sum_i E_i A_i^-1 R_i^I v with the strips' local
+    solves run in parallel, the global operator and FGMRES of the oracle
+    (oracle.krylov.gmres) in the parent."""
+
+    def __init__(self, w, procs=None):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+
+        import numpy as np
+
+        from oracle.fdfd import Problem
+        from oracle.stddm import DDM
+        self.w = w
+        prob_kw = dict(nx=w.nx, ny=w.ny, dx=w.dx, dy=w.dy, wavelength=w.wavelength, eps_node=w.eps_node,
+                       npml=w.npml, pml_order=w.pml_order, pml_R=w.pml_R)
+        ddm_kw = dict(nsub=w.nsub, overlap=w.overlap, interface_pml=w.interface_pml)
+        self.P = Problem(**prob_kw)
+        self.D = DDM(self.P, **ddm_kw)
+        self.A = self.P.A.tocsr()
+        ny = w.ny
+        self.offs = [0]
+        for st in self.D.strips:
+            self.offs.append(self.offs[-1] + st.width * ny)
+        ncpu = os.cpu_count() or 1
+        self.procs = max(1, min(w.nsub, ncpu if procs is None else procs))
+        self.shm_in = shared_memory.SharedMemory(create=True, size=16 * w.n)
+        self.shm_out = shared_memory.SharedMemory(create=True, size=16 * self.offs[-1])
+        self.vin = np.ndarray((w.n,), np.complex128, buffer=self.shm_in.buf)
+        self.vout = np.ndarray((self.offs[-1],), np.complex128, buffer=self.shm_out.buf)
+        ctx = mp.get_context("spawn")
+        self.conns, self.workers = [], []
+        # one thread per worker: SuperLU's BLAS threads in several processes
+        # at once oversubscribe the cores and stall (the spawned children
+        # read these variables when they load numpy)
+        saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+        os.environ.update({k: "1" for k in saved})
+        try:
+            self._start(ctx, prob_kw, ddm_kw)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        try:
+            for c in self.conns:
+                if self._recv(c, 600) != "ready":
+                    raise RuntimeError("oracle worker failed to start")
+        except Exception:
+            self.close()
+            raise
+
+    def _start(self, ctx, prob_kw, ddm_kw):
+        w = self.w
+        for r in range(self.procs):
+            ks = list(range(r, w.nsub, self.procs))
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, prob_kw, ddm_kw, ks, self.shm_in.name,
+                                                         self.shm_out.name, self.offs), daemon=True)
+            p.start()
+            b.close()          # the child holds its end: a dead child then ends recv() with EOFError
+            self.conns.append(a)
+            self.workers.append(p)
+
+    @staticmethod
+    def _recv(c, timeout):
+        if not c.poll(timeout):
+            raise RuntimeError("oracle worker did not answer within %d s" % timeout)
+        return c.recv()
+
+    def _all(self, msg):
+        for c in self.conns:
+            c.send(msg)
+        for c in self.conns:
+            self._recv(c, 3600)
+
+    def minv(self, v):
+        import numpy as np
+        self.vin[:] = v
+        self._all("solve")
+        out = np.zeros(self.w.n, np.complex128)
+        ny = self.w.ny
+        for k, st in enumerate(self.D.strips):
+            out[st.x0 * ny:st.x1 * ny] += self.vout[self.offs[k]:self.offs[k + 1]]
+        return out
+
+    def step(self, rtol=RTOL, restart=RESTART, maxit=2000):
+        """Factor every strip, then FGMRES to rtol; returns (seconds,
+        factor seconds, iterations, final true relative residual)."""
+        import numpy as np
+
+        from oracle.krylov import gmres
+        t0 = time.perf_counter()
+        self._all("factor")
+        t1 = time.perf_counter()
+        b = self.w.b[0].ravel()
+        x, hist, its = gmres(lambda z: self.A @ z, self.minv, b, restart=restart, rtol=rtol, maxit=maxit)
+        t2 = time.perf_counter()
+        res = float(np.linalg.norm(b - self.A @ x) / np.linalg.norm(b))
+        return t2 - t0, t1 - t0, its, res
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send("stop")
+            except (OSError, BrokenPipeError):
+                pass
+        for p in self.workers:
+            p.join(timeout=10)
+            if p.is_alive():
+                p.terminate()
+        del self.vin, self.vout
+        self.shm_in.close()
+        self.shm_in.unlink()
+        self.shm_out.close()
+        self.shm_out.unlink()
+
+
+def host_info():
+    ram = None
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemTotal:"):
+                    ram = round(int(ln.split()[1]) / 2 ** 20, 1)
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "host_ram_gib": ram}
+
+
+def cpu_baseline(name, small=False, steps=1, warmup=0):
+    """Time the CPU oracle (ParallelOracle) on the shrunk sample of workload
+    `name`: `warmup` untimed steps, then the median of `steps` timed ones."""
+    w, desc = cpu_sample_workload(name, small)
+    po = ParallelOracle(w)
+    try:
+        for _ in range(warmup):
+            po.step()
+        rows = [po.step() for _ in range(steps)]
+    finally:
+        po.close()
+    t = statistics.median(r[0] for r in rows)
+    last = rows[-1]
+    info = host_info()
+    return dict(value=w.n * w.nrhs / t / 1e6, unit="MDoF/s", cores=po.procs, kind="oracle",
+                sample=(f"{desc} ({w.n} DoF): SuperLU factors of every strip + the oracle's FGMRES("
+                        f"{RESTART}) with the additive preconditioner to {RTOL:g}, whole solve timed, "
+                        f"{po.procs} worker processes"),
+                seconds=t, factor_s=last[1], iterations=last[2], final_residual=last[3], **info)
 
 
 # ----------------------------------------------------------------- ours
@@ -295,6 +472,11 @@ def run_ours(args, rank, world, local_rank):
 
     w = make_workload(args.workload, args.nrhs)
     N = w.n * w.nrhs
+    wave = w.name.startswith("waveguide")
+    if args.order is None:
+        args.order = "multiplicative" if wave else "additive"
+    if args.static_pivot is None:
+        args.static_pivot = 2 if wave else 0
     peaks = measured_peaks()
     fp64_tf = gemm_peak(torch, torch.float64, 4096)
     fp32_tf = gemm_peak(torch, torch.float32, 8192)
@@ -307,14 +489,20 @@ def run_ours(args, rank, world, local_rank):
 
     orders = {"additive": 0, "multiplicative": 1, "red-black": 2}
 
+    def band_for(p, order, band):
+        if band is None:
+            band = 1 if args.band is None else args.band
+        return 1 if (band and p == S.STDD_PREC_FP64 and order == "additive") else 0
+
     def make_solver(p, order=None, band=None):
         sv = S.Solver.from_workload(w, eps=eps_d, precision=p, device=local_rank, stream=stream.cuda_stream)
         order = order or args.order
         S.stdd_set_option(sv.ctx, S.STDD_OPT_ORDER, orders[order])
         if args.leaf != 16:
             S.stdd_set_option(sv.ctx, S.STDD_OPT_LEAF, args.leaf)
-        band = args.band if band is None else band
-        S.stdd_set_option(sv.ctx, S.STDD_OPT_BAND, 1 if (band and p == S.STDD_PREC_FP64 and order == "additive") else 0)
+        S.stdd_set_option(sv.ctx, S.STDD_OPT_BAND, band_for(p, order, band))
+        if p != S.STDD_PREC_FP64 and args.static_pivot:
+            S.stdd_set_option(sv.ctx, S.STDD_OPT_STATIC_PIVOT, args.static_pivot)
         return sv
 
     def step(sv):
@@ -372,7 +560,7 @@ def run_ours(args, rank, world, local_rank):
 
     # phase rooflines (algorithmic bytes / flops per phase call)
     steps = args.steps
-    band_main = bool(args.band and prec == S.STDD_PREC_FP64 and args.order == "additive")
+    band_main = bool(band_for(prec, args.order, None))
     E = st["factor_entries"]
     elem = 16 if prec == S.STDD_PREC_FP64 else 8
     phases = {}
@@ -420,9 +608,11 @@ def run_ours(args, rank, world, local_rank):
     tensor = prec in (S.STDD_PREC_C64_BF16, S.STDD_PREC_C64_FP16)
     kernels = {}
 
-    def add_kernel(name, ms, calls, units, kind):
+    def add_kernel(name, ms, calls, units, kind, executed=None):
         # measured over one extra profiled step (kprof: one launch span per
-        # kernel launch), so per-step figures use steps = 1
+        # kernel launch), so per-step figures use steps = 1.  Elimination
+        # kernels: units = the LU flops of their trailing-block updates
+        # (algorithmic), executed = the Gauss-Jordan flops they run.
         if not calls:
             return
         t = ms * 1e-3 / calls
@@ -440,16 +630,20 @@ def run_ours(args, rank, world, local_rank):
                      peak_source=peaks["source_hbm"])
         k.update(frac=k["achieved"] / k["peak"], ms_per_step=ms, launches_per_step=calls,
                  units_per_launch=u, unit_kind=kind, ms_per_launch=t * 1e3)
+        if executed is not None:
+            k.update(unit_kind="LU flops (trailing-block updates)", executed_flops_per_launch=executed / calls,
+                     executed_tflops=executed / calls / t / 1e12)
         kernels[name] = k
 
     tname = "double" if prec == S.STDD_PREC_FP64 else "float"
     if tensor:
         add_kernel(f"mf_gj_update_tc<{args.precision}>", kprof["update_ms"], kprof["update_calls"],
-                   kprof["update_flops"], "tensor")
+                   kprof["update_flops"], "tensor", kprof["update_flops_executed"])
     else:
         add_kernel(f"mf_gj_update<{tname}>", kprof["update_ms"], kprof["update_calls"], kprof["update_flops"],
-                   "flops")
-    add_kernel(f"mf_gj_small<{tname}>", kprof["small_ms"], kprof["small_calls"], kprof["small_flops"], "flops")
+                   "flops", kprof["update_flops_executed"])
+    add_kernel(f"mf_gj_small<{tname}>", kprof["small_ms"], kprof["small_calls"], kprof["small_flops"], "flops",
+               kprof["small_flops_executed"])
     add_kernel(f"mf_down<{tname}>", kprof["down_ms"], kprof["down_calls"], kprof["down_bytes"], "bytes")
     add_kernel(f"mf_up<{tname}>", kprof["up_ms"], kprof["up_calls"], kprof["up_bytes"], "bytes")
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
@@ -457,6 +651,10 @@ def run_ours(args, rank, world, local_rank):
     roof = {k: d[k] for k in ("bound", "achieved", "peak", "unit", "frac", "peak_source")}
     roof["kernel"] = dom
     roof["units_per_launch"] = d["units_per_launch"]
+    roof["unit_kind"] = d["unit_kind"]
+    if "executed_flops_per_launch" in d:
+        roof["executed_flops_per_launch"] = d["executed_flops_per_launch"]
+        roof["executed_tflops"] = d["executed_tflops"]
     roof["measured_over"] = ("one extra step after the timed region with a CUDA-event span around every launch "
                              "(graphs bypassed); profiled step %.1f ms" % kprof["step_ms"])
     roof["traffic"] = ncu_traffic(dom, d["units_per_launch"])
@@ -478,7 +676,7 @@ def run_ours(args, rank, world, local_rank):
                   S.STDD_PREC_C64_FP16: "c64-factors(fp16 tensor-core updates)+c128-krylov"}[prec],
         "data": "synthetic",
         "config": {"workload": workload_desc(w), "precision": args.precision, "order": args.order,
-                   "krylov_space": "band" if args.band else "full", "leaf": args.leaf, "rtol": RTOL,
+                   "krylov_space": "band" if band_main else "full", "leaf": args.leaf, "rtol": RTOL,
                    "restart": RESTART, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (factors %.1f GB, Krylov basis %.1f GB)"
                          % (E * elem / 1e9, (2 * RESTART + 1) * w.n * 16 / 1e9)},
@@ -486,6 +684,8 @@ def run_ours(args, rank, world, local_rank):
         "converged": bool(st["final_residual"] <= RTOL),
         "final_residual": st["final_residual"],
         "true_residual_check": r_rel,
+        "factor_flops_lu": st["factor_flops_lu"],
+        "factor_flops_executed": st["factor_flops"],
         "t_factor_ms": prof["factor_ms"] / args.steps,
         "t_solve_ms": prof["solve_ms"] / args.steps,
         "phases": phases,
@@ -498,38 +698,44 @@ def run_ours(args, rank, world, local_rank):
     }
     sv.close()
 
-    if not args.no_compare:
-        other = S.STDD_PREC_C64 if prec == S.STDD_PREC_FP64 else S.STDD_PREC_FP64
-        sv2, ms2, prof2, _, st2, hist2, _, _ = timed(other, 1, 1, 1)
+    def summary(ms_, prof_, st_, hist_, **extra):
         diff = float(torch.linalg.vector_norm(x_d - x_main) / torch.linalg.vector_norm(x_main))
-        out["compare"] = {"precision": "c64" if other == S.STDD_PREC_C64 else "fp64",
-                          "ms_per_step": ms2, "value": N / (ms2 * 1e-3) / 1e6,
-                          "iterations": len(hist2) - 1, "final_residual": st2["final_residual"],
-                          "t_factor_ms": prof2["factor_ms"], "t_solve_ms": prof2["solve_ms"],
-                          "rel_diff_vs_main": diff}
-        sv2.close()
+        d_ = {"ms_per_step": ms_, "value": N / (ms_ * 1e-3) / 1e6, "iterations": len(hist_) - 1,
+              "final_residual": st_["final_residual"], "converged": bool(st_["final_residual"] <= RTOL),
+              "t_factor_ms": prof_["factor_ms"], "t_solve_ms": prof_["solve_ms"], "rel_diff_vs_main": diff}
+        d_.update(extra)
+        return d_
+
+    if not args.no_compare:
+        # the mixed forms on the same problem (FP64 Krylov iteration in all of
+        # them): complex64 factors with FP32 updates, and with FP16 tensor-core
+        # updates; or plain FP64 when the main line is a mixed form
+        others = ([S.STDD_PREC_C64, S.STDD_PREC_C64_FP16] if prec == S.STDD_PREC_FP64 else [S.STDD_PREC_FP64])
+        names = {S.STDD_PREC_FP64: "fp64", S.STDD_PREC_C64: "c64", S.STDD_PREC_C64_FP16: "fp16"}
+        out["compare_modes"] = {}
+        for other in others:
+            sv2, ms2, prof2, _, st2, hist2, _, _ = timed(other, 1, 1, 1)
+            out["compare_modes"][names[other]] = summary(
+                ms2, prof2, st2, hist2, precision=names[other],
+                static_pivot=args.static_pivot if other != S.STDD_PREC_FP64 else 0,
+                raised_pivots=st2["raised_pivots"], order=args.order)
+            sv2.close()
+        out["compare"] = out["compare_modes"][names[others[0]]]
         # the other strip orders of the same method (same precision as the
-        # main line): symmetric multiplicative and red-black, one step each
+        # main line), one step each
         out["orders"] = {}
         for name in orders:
             if name == args.order:
                 continue
             sv3, ms3, prof3, _, st3, hist3, _, _ = timed(prec, 1, 1, 1, order=name)
-            diff = float(torch.linalg.vector_norm(x_d - x_main) / torch.linalg.vector_norm(x_main))
-            out["orders"][name] = {"ms_per_step": ms3, "value": N / (ms3 * 1e-3) / 1e6,
-                                   "iterations": len(hist3) - 1, "final_residual": st3["final_residual"],
-                                   "t_factor_ms": prof3["factor_ms"], "t_solve_ms": prof3["solve_ms"],
-                                   "rel_diff_vs_main": diff}
+            out["orders"][name] = summary(ms3, prof3, st3, hist3,
+                                          krylov_space="band" if band_for(prec, name, None) else "full")
             sv3.close()
         # the same iteration in band space (FP64 additive) or not
         if prec == S.STDD_PREC_FP64 and args.order == "additive":
-            sv4, ms4, prof4, _, st4, hist4, _, _ = timed(prec, 1, 1, 1, band=0 if args.band else 1)
-            diff = float(torch.linalg.vector_norm(x_d - x_main) / torch.linalg.vector_norm(x_main))
-            out["band_space" if not args.band else "full_space"] = {
-                "ms_per_step": ms4, "value": N / (ms4 * 1e-3) / 1e6, "iterations": len(hist4) - 1,
-                "final_residual": st4["final_residual"], "t_factor_ms": prof4["factor_ms"],
-                "t_solve_ms": prof4["solve_ms"], "rel_diff_vs_main": diff}
-            if args.band and prof4["matvec_calls"]:
+            sv4, ms4, prof4, _, st4, hist4, _, _ = timed(prec, 1, 1, 1, band=0 if band_main else 1)
+            out["band_space" if not band_main else "full_space"] = summary(ms4, prof4, st4, hist4)
+            if band_main and prof4["matvec_calls"]:
                 # the full-space step's matvec spans hold only the stencil
                 # (inner steps) and the residual (restarts): 40 B per node
                 out["phases"]["stencil_matvec"] = stencil_phase(
@@ -549,24 +755,23 @@ def run_ours(args, rank, world, local_rank):
         sv.factor()
         sv.solve(x_h, restart=RESTART, rtol=RTOL, maxit=args.maxit, allow_noconv=True)
         barrier()
+        ne = max(1, min(args.steps, args.e2e_steps))
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(ne):
             S.stdd_set_permittivity(sv.ctx, eps_h)
             sv.factor()
             S.stdd_set_sources(sv.ctx, w.nrhs, b_h)
             sv.solve(x_h, restart=RESTART, rtol=RTOL, maxit=args.maxit, allow_noconv=True)
-        dt = (time.perf_counter() - t0) / args.steps
+        dt = (time.perf_counter() - t0) / ne
         dt = max_over_ranks(dt, dist, dev)
         out["e2e"] = {"value": whole_job_rate(N, dt, world) / 1e6, "unit": "MDoF/s", "ms_per_step": dt * 1e3,
+                      "steps": ne,
                       "h2d_bytes_per_step": int(w.eps_node.nbytes + w.b.nbytes),
                       "d2h_bytes_per_step": int(w.b.nbytes)}
         sv.close()
 
     if rank == 0 and not args.no_cpu:
-        smp = oracle_sample(w, its)
-        out["cpu_baseline"] = {"value": N / smp["total_s"] / 1e6, "unit": "MDoF/s", "cores": 1,
-                               "kind": "oracle", "sample": smp["sample"],
-                               "est_total_s": smp["total_s"], "sampled_s": smp["sampled_s"]}
+        out["cpu_baseline"] = cpu_baseline(args.workload)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -576,27 +781,34 @@ def run_ours(args, rank, world, local_rank):
 
 # ------------------------------------------------------------- reference
 def run_reference(args, rank):
+    """The CPU oracle on the host cores (the reference arm): each step factors
+    every strip of a shrunk instance of the benchmark's generator and runs the
+    oracle's FGMRES to 1e-8 with the additive preconditioner, local solves in
+    parallel worker processes; W untimed steps, then the median of K."""
     if rank != 0:
         return
-    w = make_workload(args.workload)
+    w, desc = cpu_sample_workload(args.workload, small=True)
     N = w.n * w.nrhs
-    # FGMRES(50) iteration count of this preconditioner on these workloads
-    # (the oracle's own GMRES gives the same count: 34 on the metalens strip,
-    # 4 on the cylinder); the sample is scaled to it
-    its_assumed = 34 if w.name == "metalens" else 4
-    vals = []
-    smp = None
-    for _ in range(args.steps):
-        smp = oracle_sample(w, its_assumed)
-        vals.append(smp["total_s"])
-    t = statistics.median(vals)
+    po = ParallelOracle(w)
+    try:
+        for _ in range(args.warmup):
+            po.step()
+        rows = [po.step() for _ in range(args.steps)]
+    finally:
+        po.close()
+    t = statistics.median(r[0] for r in rows)
     v = N / t / 1e6
+    info = host_info()
+    cb = {"value": v, "unit": "MDoF/s", "cores": po.procs, "kind": "oracle",
+          "sample": (f"{desc} ({w.n} DoF): SuperLU factors of every strip + the oracle's FGMRES({RESTART}) with "
+                     f"the additive preconditioner to {RTOL:g} per step, {po.procs} worker processes"),
+          "iterations": rows[-1][2], "final_residual": rows[-1][3], **info}
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MDoF/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-           "config": {"workload": workload_desc(w), "precision": "fp64", "rtol": RTOL, "restart": RESTART},
-           "cpu_baseline": {"value": v, "unit": "MDoF/s", "cores": 1, "kind": "oracle",
-                            "sample": smp["sample"]},
+           "config": {"workload": f"{desc} ({w.n} DoF), a bounded sample of {args.workload}", "precision": "fp64",
+                      "order": "additive", "rtol": RTOL, "restart": RESTART},
+           "cpu_baseline": cb,
            "e2e": {"value": v, "unit": "MDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

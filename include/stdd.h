@@ -171,7 +171,9 @@ typedef struct {
   int max_pivots;             /* largest separator / leaf pivot block       */
   int max_border;             /* largest front border                       */
   long long factor_entries;   /* complex entries stored in L and U          */
-  double factor_flops;        /* real flops of the numeric factorization    */
+  double factor_flops;        /* real flops the factorization executes (the
+                                 Gauss-Jordan sweep: sum p n^2 complex
+                                 multiply-adds over fronts)                 */
   double solve_flops;         /* real flops of one M^-1 application         */
   long long local_dofs;       /* sum of local box sizes                     */
   long long device_bytes;     /* device memory held by the context          */
@@ -180,6 +182,9 @@ typedef struct {
   double min_pivot;           /* smallest |pivot| seen by the factorization */
   int reorth_passes;          /* second Gram-Schmidt passes in the last solve */
   long long raised_pivots;    /* pivots raised to the static-pivot floor    */
+  double factor_flops_lu;     /* the same elimination counted as an LU
+                                 factorization (Eq. 22): pivot k of a front
+                                 of n updates the (n-k-1)^2 trailing block  */
 } stdd_stats;
 
 stdd_status stdd_get_stats(stdd_ctx *ctx, stdd_stats *out);
@@ -233,8 +238,9 @@ typedef struct {
   double solve_ms;        /* whole stdd_solve calls                        */
   long long launches;     /* kernels of this library launched             */
   /* the dominant kernels, launch by launch, with their algorithmic work:
-   * small-front and blocked-update eliminations (real flops), the upward
-   * and downward substitution sweeps (factor bytes read) */
+   * small-front and blocked-update eliminations (real flops of the LU
+   * trailing-block updates they stand for, Eq. 22), the upward and
+   * downward substitution sweeps (factor bytes read) */
   double small_ms, small_flops;
   int small_calls;
   double update_ms, update_flops;
@@ -243,6 +249,9 @@ typedef struct {
   int up_calls;
   double down_ms, down_bytes;
   int down_calls;
+  /* real flops the two elimination kernels execute (Gauss-Jordan: the
+   * updates also cover the eliminated pivot rows and columns) */
+  double small_flops_executed, update_flops_executed;
 } stdd_profile;
 
 /* level 0: off; 1: phase spans (factor, M^-1, matvec, Gram-Schmidt,

@@ -44,7 +44,8 @@ class stdd_stats(ctypes.Structure):
                 ("factor_flops", c_double), ("solve_flops", c_double),
                 ("local_dofs", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
                 ("iterations", c_int), ("final_residual", c_double), ("min_pivot", c_double),
-                ("reorth_passes", c_int), ("raised_pivots", ctypes.c_longlong)]
+                ("reorth_passes", c_int), ("raised_pivots", ctypes.c_longlong),
+                ("factor_flops_lu", c_double)]
 
 
 class stdd_profile(ctypes.Structure):
@@ -54,7 +55,8 @@ class stdd_profile(ctypes.Structure):
                 ("small_ms", c_double), ("small_flops", c_double), ("small_calls", c_int),
                 ("update_ms", c_double), ("update_flops", c_double), ("update_calls", c_int),
                 ("up_ms", c_double), ("up_bytes", c_double), ("up_calls", c_int),
-                ("down_ms", c_double), ("down_bytes", c_double), ("down_calls", c_int)]
+                ("down_ms", c_double), ("down_bytes", c_double), ("down_calls", c_int),
+                ("small_flops_executed", c_double), ("update_flops_executed", c_double)]
 
 
 _SIGS = {

@@ -163,7 +163,7 @@ struct stdd_ctx {
   DBuf d_fac, d_ws[2], d_ub[2], d_tloc, d_wloc, d_flag, d_minpiv, d_nraised, d_items;
   int64_t nloc = 0, nloc_max = 0, ub_elems[2] = {0, 0};
   int64_t nfronts = 0, factor_entries = 0;
-  double factor_cflops = 0, solve_cflops = 0;
+  double factor_cflops = 0, factor_cflops_lu = 0, solve_cflops = 0;
   int max_p = 0, max_b = 0, depth = 0;
   double min_pivot = 0;
   long long raised_pivots = 0;
@@ -221,9 +221,15 @@ struct stdd_ctx {
   // per-launch profiling of the dominant kernels: algorithmic work per
   // launch from the host front list (flops for the eliminations, factor
   // bytes for the substitution sweeps)
+  // Elimination kernels are credited with the LU flops of what they do (the
+  // trailing-block updates, Sec. 2.4, Eq. 22), and separately with the
+  // Gauss-Jordan flops they execute (which also update the eliminated pivot
+  // rows and columns).
   std::vector<double> unit_small, unit_up, unit_down;       // per level
   std::vector<std::vector<double>> unit_update;             // per level, per step
-  std::vector<double> span_units;                           // parallel to spans
+  std::vector<double> exec_small;                           // per level, Gauss-Jordan flops
+  std::vector<std::vector<double>> exec_update;             // per level, per step
+  std::vector<double> span_units, span_exec;                // parallel to spans
   std::vector<int> span_level;                              // parallel to spans
   struct Hook : stdd::LaunchHook {
     stdd_ctx *c = nullptr;
@@ -233,13 +239,22 @@ struct stdd_ctx {
       open = c->pbegin(PH_K0 + kind);
       c->span_level.resize(c->spans.size(), -1);
       c->span_level[open] = level;
-      double u = 0;
-      if (kind == stdd::K_SMALL) u = c->unit_small[level];
-      else if (kind == stdd::K_UPDATE) u = c->unit_update[level][k / stdd::MF_NB];
-      else if (kind == stdd::K_UP) u = c->unit_up[level];
-      else u = c->unit_down[level];
+      double u = 0, x = 0;
+      if (kind == stdd::K_SMALL) {
+        u = c->unit_small[level];
+        x = c->exec_small[level];
+      } else if (kind == stdd::K_UPDATE) {
+        u = c->unit_update[level][k / stdd::MF_NB];
+        x = c->exec_update[level][k / stdd::MF_NB];
+      } else if (kind == stdd::K_UP) {
+        u = x = c->unit_up[level];
+      } else {
+        u = x = c->unit_down[level];
+      }
       c->span_units.resize(c->spans.size(), 0.0);
+      c->span_exec.resize(c->spans.size(), 0.0);
       c->span_units[open] = u;
+      c->span_exec[open] = x;
     }
     void after(int, int, int) override {
       if (open >= 0) c->pend(open);
@@ -504,7 +519,7 @@ void stdd_ctx::build_structure() {
   int64_t vec = 0, fac = 0, coef = 0;
   depth = 0;
   max_p = max_b = 0;
-  factor_cflops = solve_cflops = 0;
+  factor_cflops = factor_cflops_lu = solve_cflops = 0;
   nloc_max = 0;
   for (int k = 0; k < nsub; ++k) {
     const StripHost &s = strips[k];
@@ -524,6 +539,7 @@ void stdd_ctx::build_structure() {
     max_p = std::max(max_p, sh.max_p);
     max_b = std::max(max_b, sh.max_b);
     factor_cflops += sh.factor_cflops;
+    factor_cflops_lu += sh.factor_cflops_lu;
     solve_cflops += sh.solve_cflops;
   }
   nloc = vec;
@@ -597,22 +613,27 @@ void stdd_ctx::build_structure() {
   {
     const double E = (double)elem();
     unit_small.assign(depth, 0.0);
+    exec_small.assign(depth, 0.0);
     unit_up.assign(depth, 0.0);
     unit_down.assign(depth, 0.0);
     unit_update.assign(depth, {});
+    exec_update.assign(depth, {});
     for (int L = 0; L < depth; ++L) {
       const LevelInfo &li = levels[L];
       unit_update[L].assign((li.max_p + stdd::MF_NB - 1) / stdd::MF_NB + 1, 0.0);
+      exec_update[L].assign(unit_update[L].size(), 0.0);
       for (int f = li.f0; f < li.f0 + li.nf; ++f) {
         const double p = fr[f].p, b = fr[f].b, n = p + b;
         unit_up[L] += E * b * p;
         unit_down[L] += E * p * n;
         if (n <= stdd::MF_SMALL) {
-          unit_small[L] += 8.0 * p * n * n;
+          exec_small[L] += 8.0 * p * n * n;
+          for (int k = 0; k < fr[f].p; ++k) unit_small[L] += 8.0 * (n - k - 1) * (n - k - 1);
         } else {
           for (int k = 0; k < fr[f].p; k += stdd::MF_NB) {
             const double nbk = std::min(stdd::MF_NB, fr[f].p - k);
-            unit_update[L][k / stdd::MF_NB] += 8.0 * (n - nbk) * (n - nbk) * nbk;
+            exec_update[L][k / stdd::MF_NB] += 8.0 * (n - nbk) * (n - nbk) * nbk;
+            unit_update[L][k / stdd::MF_NB] += 8.0 * (n - k - nbk) * (n - k - nbk) * nbk;
           }
         }
       }
@@ -1892,6 +1913,7 @@ stdd_status stdd_get_stats(stdd_ctx *c, stdd_stats *o) {
     o->max_border = c->max_b;
     o->factor_entries = c->factor_entries;
     o->factor_flops = 8.0 * c->factor_cflops;
+    o->factor_flops_lu = 8.0 * c->factor_cflops_lu;
     o->solve_flops = 8.0 * c->solve_cflops;
     o->local_dofs = c->nloc;
     o->device_bytes = c->device_bytes();
@@ -1979,9 +2001,10 @@ stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {
     if (!o) throw ArgError("null profile");
     std::memset(o, 0, sizeof(*o));
     CK(cudaStreamSynchronize(c->stream));
-    double t[stdd_ctx::PH_COUNT] = {0}, units[stdd_ctx::PH_COUNT] = {0};
+    double t[stdd_ctx::PH_COUNT] = {0}, units[stdd_ctx::PH_COUNT] = {0}, execu[stdd_ctx::PH_COUNT] = {0};
     int cnt[stdd_ctx::PH_COUNT] = {0};
     c->span_units.resize(c->spans.size(), 0.0);
+    c->span_exec.resize(c->spans.size(), 0.0);
     for (size_t si = 0; si < c->spans.size(); ++si) {
       const auto &sp = c->spans[si];
       float ms = 0;
@@ -1992,6 +2015,7 @@ stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {
       t[sp.phase] += ms;
       cnt[sp.phase] += 1;
       units[sp.phase] += c->span_units[si];
+      execu[sp.phase] += c->span_exec[si];
     }
     const int K0 = stdd_ctx::PH_K0;
     if (std::getenv("STDD_PROFILE_LEVELS")) {   // per-level breakdown on stderr
@@ -2026,6 +2050,8 @@ stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {
     o->down_ms = t[K0 + stdd::K_DOWN];
     o->down_bytes = units[K0 + stdd::K_DOWN];
     o->down_calls = cnt[K0 + stdd::K_DOWN];
+    o->small_flops_executed = execu[K0 + stdd::K_SMALL];
+    o->update_flops_executed = execu[K0 + stdd::K_UPDATE];
     o->factor_ms = t[stdd_ctx::PH_FACTOR];
     o->minv_ms = t[stdd_ctx::PH_MINV];
     o->minv_calls = cnt[stdd_ctx::PH_MINV];
@@ -2038,6 +2064,7 @@ stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {
     if (reset) {
       c->spans.clear();
       c->span_units.clear();
+      c->span_exec.clear();
       c->span_level.clear();
       c->ev_used = 0;
     }

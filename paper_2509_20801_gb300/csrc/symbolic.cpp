@@ -99,6 +99,9 @@ void nd_analyze(int W, int H, int leaf_max, Shape &S) {
     off += p * (p + 2 * b);
     // Gauss-Jordan sweep of p pivots over the whole n x n front
     S.factor_cflops += double(p) * double(n) * double(n);
+    // LU count: pivot k updates the (n-k-1)^2 trailing block, sum of m^2 for m = b .. n-1
+    auto sq = [](double x) { return x * (x + 1) * (2 * x + 1) / 6.0; };
+    S.factor_cflops_lu += sq(double(n - 1)) - sq(double(b - 1));
     S.solve_cflops += double(p) * double(p) + 2.0 * double(p) * double(b);
     if (f.level + 1 > S.depth) S.depth = f.level + 1;
     if (f.p > S.max_p) S.max_p = f.p;

@@ -36,6 +36,8 @@ struct Shape {
   int depth = 0;                    // number of levels
   int64_t factor_entries = 0;       // sum p*(p + 2b)
   double factor_cflops = 0;         // complex multiply-adds of the factorization (sum p n^2)
+  double factor_cflops_lu = 0;      // the same elimination counted as LU: sum over pivots of
+                                    // the trailing block, (n-k-1)^2 for pivot k
   double solve_cflops = 0;          // complex multiply-adds of one fwd+bwd solve
   int max_p = 0, max_b = 0;
 };
