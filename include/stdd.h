@@ -318,13 +318,26 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     the elimination's growth, harmless in FP64, can ruin
  *                     complex64 factors (high-index guided-wave geometries).
  *                     Invalidates the factors. */
+/*   STDD_OPT_PIVOTING (default 0): 1 = partial pivoting restricted to each
+ *                     front's pivot rows.  Before each pivot (each 32-pivot
+ *                     block of a large front) the not yet eliminated pivot
+ *                     row whose entry in the pivot column is largest in
+ *                     modulus is swapped in; rows are never exchanged with
+ *                     the front's border, so the nested-dissection order and
+ *                     the fronts stay as they are (Eq. 22's P is then the
+ *                     fill-reducing order times these interchanges).  It
+ *                     bounds the element growth of the unpivoted sweep
+ *                     inside a front, which complex64 factors of high-index
+ *                     guided-wave geometries cannot afford.  Invalidates the
+ *                     factors. */
 enum {
   STDD_OPT_GRAPHS = 1,
   STDD_OPT_AUTOTUNE = 2,
   STDD_OPT_LEAF = 3,
   STDD_OPT_ORDER = 4,
   STDD_OPT_BAND = 5,
-  STDD_OPT_STATIC_PIVOT = 6
+  STDD_OPT_STATIC_PIVOT = 6,
+  STDD_OPT_PIVOTING = 7
 };
 stdd_status stdd_set_option(stdd_ctx *ctx, int option, int value);
 stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);

@@ -161,7 +161,10 @@ struct stdd_ctx {
   std::vector<LevelInfo> levels;
   DBuf d_strips, d_fronts, d_nodes, d_cmap, d_inv, d_lcxm, d_lcxp, d_colstrip;
   DBuf d_fac, d_ws[2], d_ub[2], d_tloc, d_wloc, d_flag, d_minpiv, d_nraised, d_items;
-  int64_t nloc = 0, nloc_max = 0, ub_elems[2] = {0, 0};
+  int64_t nloc = 0, nloc_max = 0, ub_elems[2] = {0, 0}, panel_need = 0;
+  // partial pivoting restricted to each front's pivot rows (STDD_OPT_PIVOTING)
+  int pivoting = 0;
+  DBuf d_pcol, d_panel;
   int64_t nfronts = 0, factor_entries = 0;
   double factor_cflops = 0, factor_cflops_lu = 0, solve_cflops = 0;
   int max_p = 0, max_b = 0, depth = 0;
@@ -444,6 +447,8 @@ MfArgs stdd_ctx::mf_args(int par, bool solve) const {
   a.min_pivot = d_minpiv.as<double>();
   a.piv_floor = pivot_floor();
   a.n_raised = d_nraised.as<unsigned long long>();
+  a.pcol = pivoting ? d_pcol.as<int>() : nullptr;
+  a.panel = pivoting ? d_panel.p : nullptr;
   (void)solve;
   return a;
 }
@@ -558,11 +563,13 @@ void stdd_ctx::build_structure() {
   lvl_up.assign(depth, std::vector<int>(nsub + 1, 0));
   lvl_down.assign(depth, std::vector<int>(nsub + 1, 0));
   int64_t ws_need[2] = {0, 0};
+  int64_t piv_run = 0;
+  panel_need = 0;
   ub_elems[0] = ub_elems[1] = 0;
   for (int L = 0; L < depth; ++L) {
     LevelInfo &li = levels[L];
     li.f0 = (int)fr.size();
-    int64_t s_run = 0, u_run = 0;
+    int64_t s_run = 0, u_run = 0, pan_run = 0;
     lvl_front[L].assign(nsub + 1, 0);
     for (int j = 0; j < nsub; ++j) {
       const int k = perm[j];
@@ -585,6 +592,10 @@ void stdd_ctx::build_structure() {
         d.fac_off = sdev[k].fac_off + sf.fac_off;
         d.s_off = s_run;
         d.u_off = u_run;
+        d.piv_off = piv_run;
+        d.pan_off = pan_run;
+        piv_run += sf.p;
+        if (sf.p + sf.b > stdd::MF_SMALL) pan_run += (int64_t)sf.p * stdd::MF_NB;
         s_run += (int64_t)sf.b * sf.b;
         u_run += sf.b;
         li.max_p = std::max(li.max_p, sf.p);
@@ -597,6 +608,7 @@ void stdd_ctx::build_structure() {
     li.nf = (int)fr.size() - li.f0;
     lvl_front[L][nsub] = (int)fr.size();
     ws_need[L & 1] = std::max(ws_need[L & 1], s_run);
+    panel_need = std::max(panel_need, pan_run);
     ub_elems[L & 1] = std::max(ub_elems[L & 1], u_run);
   }
   // children ids (instances of children are at level + 1, already numbered)
@@ -764,6 +776,10 @@ template <typename R> void stdd_ctx::autotune() {
 }
 
 template <typename R> void stdd_ctx::factor_t() {
+  if (pivoting) {
+    d_pcol.alloc((size_t)std::max<int64_t>(1, nloc) * sizeof(int));
+    d_panel.alloc((size_t)std::max<int64_t>(1, panel_need) * elem());
+  }
   static bool attrs = false;
   if (!attrs) {
     CK(stdd::mf_setup_attributes<double>());
@@ -1527,7 +1543,7 @@ int64_t stdd_ctx::device_bytes() const {
   const DBuf *all[] = {&d_eps, &d_cxm, &d_cxp, &d_cym, &d_cyp, &d_strips, &d_fronts, &d_nodes, &d_cmap,
                        &d_inv, &d_lcxm, &d_lcxp, &d_colstrip, &d_fac, &d_ws[0], &d_ws[1], &d_ub[0],
                        &d_ub[1], &d_tloc, &d_wloc, &d_items, &d_flag, &d_minpiv, &d_b, &d_x, &d_r, &d_V, &d_Z, &d_w,
-                       &d_part, &d_h, &d_nrm, &d_y, &d_pre, &d_fpart, &d_guess, &d_gscr};
+                       &d_part, &d_h, &d_nrm, &d_y, &d_pre, &d_fpart, &d_guess, &d_gscr, &d_pcol, &d_panel};
   int64_t s = 0;
   for (auto *d : all) s += (int64_t)d->bytes;
   return s;
@@ -1974,6 +1990,14 @@ stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
       case STDD_OPT_BAND:
         c->use_band = value != 0;
         break;
+      case STDD_OPT_PIVOTING:
+        if (value < 0 || value > 1) throw ArgError("pivoting must be 0 (off) or 1 (partial, within fronts)");
+        if (value != c->pivoting) {
+          c->pivoting = value;
+          c->invalidate_factors();
+          c->clear_graphs();
+        }
+        break;
       case STDD_OPT_STATIC_PIVOT:
         if (value < 0 || value > 15) throw ArgError("static pivot exponent must be 0 .. 15");
         if (value != c->static_pivot) {
@@ -2252,6 +2276,10 @@ extern "C" stdd_status stdd_residual_noalloc(stdd_ctx *c, const double *x, const
     return STDD_EINVAL;
   }
   const int64_t n = c->N();
+  if (n > NA_MAX_NODES) {
+    c->err = "stdd_residual_noalloc: grid has more than 67,108,864 nodes, the size of its fixed scratch";
+    return STDD_EINVAL;
+  }
   {
     // r is written while other threads still read x's neighbours: it must
     // not overlap x; r == b is safe (b[idx] is read before r[idx] is
@@ -2263,10 +2291,6 @@ extern "C" stdd_status stdd_residual_noalloc(stdd_ctx *c, const double *x, const
       c->err = "stdd_residual_noalloc: r must not overlap x, and may overlap b only as the same buffer";
       return STDD_EINVAL;
     }
-  }
-  if (n > NA_MAX_NODES) {
-    c->err = "stdd_residual_noalloc: grid has more than 67,108,864 nodes, the size of its fixed scratch";
-    return STDD_EINVAL;
   }
   if (!c->op_ready || !c->have_eps || n == 0) {
     c->err = "stdd_residual_noalloc: operator not set up (call stdd_apply_operator, stdd_residual or "

@@ -100,6 +100,8 @@ struct FrontDev {
   int64_t fac_off;     // absolute offset of [F11 F12] (p x n, col-major, ld p) then F21 (b x p, ld b)
   int64_t s_off;       // offset of F22 (b x b, col-major) in the level-parity workspace
   int64_t u_off;       // update vector (b x nrhs) at u_off * nrhs in the solve parity buffer
+  int64_t piv_off;     // front-restricted pivoting: the front's p-entry column -> pivot map in MfArgs::pcol
+  int64_t pan_off;     // and its pivot-panel scratch (p x MF_NB complex, per level) in MfArgs::panel
 };
 
 }  // namespace stdd

@@ -38,6 +38,11 @@ struct MfArgs {
   double *min_pivot;          // min |pivot| (atomicMin on the bit pattern)
   double piv_floor;           // static pivoting: |pivot| < piv_floor is raised to it (0: off)
   unsigned long long *n_raised;  // pivots raised
+  // Partial pivoting restricted to each front's pivot rows (null: off).
+  // pcol[piv_off + j] = the pivot (0..p-1) whose value column j of the
+  // stored F11^-1 and -G21 blocks multiplies; panel: pivot-search scratch.
+  int *pcol;
+  void *panel;
 };
 
 struct LevelInfo {

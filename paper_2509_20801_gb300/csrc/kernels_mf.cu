@@ -23,6 +23,18 @@
 // (nested dissection eliminates each box with its separators held fixed,
 // i.e. a closed cavity, and high-index boxes can sit near a resonance).
 //
+// Optionally (partial pivoting, an option of the context) the sweep swaps
+// rows among the not yet eliminated pivot rows of a front before each pivot
+// (each 32-pivot block of a large front): the pivot of largest modulus in
+// the pivot column, searched over the front's pivot rows only, so the
+// nested-dissection order and the front structure stay as they are.  The
+// elimination then works on P F (P permutes pivot rows), which leaves
+//     [ F11^-1 P^T      F11^-1 F12 ]
+//     [ -F21 F11^-1 P^T S          ]
+// -- F12's block and S unchanged, the columns of the two blocks that
+// multiply w_p permuted -- so the substitutions only read w_p through the
+// stored column -> pivot map pcol (w_p[pcol[j]] for column j).
+//
 // Front storage (column-major, complex):
 //   rows 0..p-1, all n columns : p x n, leading dimension p ([Finv H12])
 //   rows p..n-1, columns < p   : b x p, leading dimension b (-G21)
@@ -161,6 +173,8 @@ __global__ void __launch_bounds__(256) mf_assemble(MfArgs a, int f0) {
     const int c = (int)(e / n), r = (int)(e - (int64_t)c * n);
     st_elem<C>(a, f, r, c, front_entry<C>(a, f, s, ch, has, r, c));
   }
+  if (a.pcol && blockIdx.y == 0)
+    for (int j = threadIdx.x; j < f.p; j += blockDim.x) a.pcol[f.piv_off + j] = j;
 }
 
 // ------------------------------------------------ small fronts, in smem
@@ -175,6 +189,35 @@ template <int TPF> __device__ __forceinline__ void front_sync() {
   else __syncthreads();
 }
 
+// argmax of |v|^2 over a group of TPF threads (ties: the smaller index)
+template <int TPF, typename T> __device__ __forceinline__ void group_argmax(T &v, int &i) {
+  __shared__ T red_v[8];
+  __shared__ int red_i[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) {
+      v = ov;
+      i = oi;
+    }
+  }
+  if (TPF > 32) {
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+      red_v[w] = v;
+      red_i[w] = i;
+    }
+    __syncthreads();
+    for (int u = 0; u < TPF / 32; ++u)
+      if (red_v[u] > v || (red_v[u] == v && red_i[u] < i)) {
+        v = red_v[u];
+        i = red_i[u];
+      }
+  }
+}
+
 template <typename R, int TPF>
 __global__ void __launch_bounds__(128) mf_gj_small(MfArgs a, int f0, int nf, int ldn) {
   using C = typename CT<R>::T;
@@ -184,6 +227,9 @@ __global__ void __launch_bounds__(128) mf_gj_small(MfArgs a, int f0, int nf, int
   C *F = reinterpret_cast<C *>(smem_raw) + (size_t)slot * (ldn * ldn + 2 * ldn);  // n x n, ld n
   C *rowk = F + ldn * ldn;
   C *colk = rowk + ldn;
+  // column -> pivot map of this front (partial pivoting), after all fronts' matrices
+  int *perm = reinterpret_cast<int *>(reinterpret_cast<C *>(smem_raw) + (size_t)fpc * (ldn * ldn + 2 * ldn)) +
+              (size_t)slot * ldn;
   const int fi = blockIdx.x * fpc + slot;
   bool live = fi < nf;
   FrontDev f;
@@ -208,10 +254,41 @@ __global__ void __launch_bounds__(128) mf_gj_small(MfArgs a, int f0, int nf, int
     const int c = idx / n, r = idx - c * n;
     F[idx] = front_entry<C>(a, f, s, ch, has, r, c);
   }
+  const bool piv = a.pcol != nullptr;
+  if (piv)
+    for (int j = t; j < p; j += TPF) perm[j] = j;
   front_sync<TPF>();
   double dmin = INFINITY;
   bool bad = false;
   for (int k = 0; k < p; ++k) {
+    if (piv) {
+      // largest |entry| of column k among the pivot rows k .. p-1
+      R bv = -1;
+      int bi = k;
+      for (int i = k + t; i < p; i += TPF) {
+        const R v = cabs2(F[k * n + i]);
+        if (v > bv) {
+          bv = v;
+          bi = i;
+        }
+      }
+      group_argmax<TPF>(bv, bi);
+      const bool sw = bi != k && bv > cabs2(F[k * n + k]);
+      front_sync<TPF>();          // every thread has read F(k, k) before any swap
+      if (sw) {
+        for (int c = t; c < n; c += TPF) {
+          const C u = F[c * n + k];
+          F[c * n + k] = F[c * n + bi];
+          F[c * n + bi] = u;
+        }
+        if (t == 0) {
+          const int u = perm[k];
+          perm[k] = perm[bi];
+          perm[bi] = u;
+        }
+      }
+      front_sync<TPF>();
+    }
     const C d0 = F[k * n + k];
     bool raised;
     const C d = floor_pivot(a, d0, raised);
@@ -240,6 +317,8 @@ __global__ void __launch_bounds__(128) mf_gj_small(MfArgs a, int f0, int nf, int
     const int c = idx / n, r = idx - c * n;
     st_elem<C>(a, f, r, c, F[idx]);
   }
+  if (piv)
+    for (int j = t; j < p; j += TPF) a.pcol[f.piv_off + j] = perm[j];
 }
 
 // ------------------------------------------- large fronts, blocked sweep
@@ -248,6 +327,83 @@ __global__ void __launch_bounds__(128) mf_gj_small(MfArgs a, int f0, int nf, int
 //   gj_col   : C <- -C D^-1    rows outside the band
 //   gj_update: A <- A + C R    rows and columns outside the band (R unscaled)
 //   gj_row   : R <- D^-1 R     columns outside the band
+// Pivot search of step k (partial pivoting within the front): LU with
+// partial pivoting of a copy of the panel, rows k .. p-1 x columns
+// k .. k+nbk-1 (the not yet eliminated pivot rows), in the level's panel
+// scratch; then its row interchanges applied, in order, to the whole rows
+// of [F11 F12] and to the column -> pivot map.  The blocked sweep that
+// follows eliminates the interchanged rows without further pivoting, which
+// takes the same pivots.  One CTA per front.
+template <typename R>
+__global__ void __launch_bounds__(256) mf_gj_pivot(MfArgs a, int f0, int k) {
+  using C = typename CT<R>::T;
+  constexpr int NB = MF_NB;
+  __shared__ int ipiv[NB];
+  const FrontDev f = a.fronts[f0 + blockIdx.x];
+  const int p = f.p, n = p + f.b;
+  if (n <= MF_SMALL || k >= p) return;
+  const int nbk = min(NB, p - k), m = p - k;
+  C *fac = reinterpret_cast<C *>(a.fac);
+  C *P = reinterpret_cast<C *>(a.panel) + f.pan_off;    // m x nbk, ld p
+  const int64_t fo = f.fac_off;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < m * nbk; idx += blockDim.x) {
+    const int i = idx % m, j = idx / m;
+    P[(int64_t)j * p + i] = fac[fo + (int64_t)(k + j) * p + k + i];
+  }
+  __syncthreads();
+  for (int q = 0; q < nbk; ++q) {
+    R bv = -1;
+    int bi = q;
+    for (int i = q + tid; i < m; i += blockDim.x) {
+      const R v = cabs2(P[(int64_t)q * p + i]);
+      if (v > bv) {
+        bv = v;
+        bi = i;
+      }
+    }
+    group_argmax<256>(bv, bi);
+    if (!(bv > cabs2(P[(int64_t)q * p + q]))) bi = q;   // keep the diagonal on ties
+    __syncthreads();                                    // every thread has read P(q, q)
+    if (tid == 0) ipiv[q] = bi;
+    if (bi != q && tid < nbk) {
+      const C u = P[(int64_t)tid * p + q];
+      P[(int64_t)tid * p + q] = P[(int64_t)tid * p + bi];
+      P[(int64_t)tid * p + bi] = u;
+    }
+    __syncthreads();
+    const C d = P[(int64_t)q * p + q];
+    if (cabs2(d) > 0) {
+      const C inv = crecip(d);
+      for (int i = q + 1 + tid; i < m; i += blockDim.x) P[(int64_t)q * p + i] = cmul(P[(int64_t)q * p + i], inv);
+      __syncthreads();
+      for (int idx = tid; idx < (m - q - 1) * (nbk - q - 1); idx += blockDim.x) {
+        const int i = q + 1 + idx % (m - q - 1), j = q + 1 + idx / (m - q - 1);
+        P[(int64_t)j * p + i] = cfms(P[(int64_t)q * p + i], P[(int64_t)j * p + q], P[(int64_t)j * p + i]);
+      }
+    }
+    __syncthreads();
+  }
+  // interchanges in order: rows k+q and k+ipiv[q] of the p x n block
+  for (int q = 0; q < nbk; ++q) {
+    const int r = ipiv[q];
+    if (r == q) continue;
+    for (int c = tid; c < n; c += blockDim.x) {
+      C *x = fac + fo + (int64_t)c * p;
+      const C u = x[k + q];
+      x[k + q] = x[k + r];
+      x[k + r] = u;
+    }
+    if (tid == 0) {
+      int *pc = a.pcol + f.piv_off;
+      const int u = pc[k + q];
+      pc[k + q] = pc[k + r];
+      pc[k + r] = u;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_diag(MfArgs a, int f0, int k) {
   using C = typename CT<R>::T;
@@ -586,7 +742,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_up(MfArgs a, c
   int p = 0, b = 0, r = 0, seg0 = 0, seg1 = 0, nseg = 0;
   bool row = false;
   const C *G = nullptr;
-  const int *nodes = nullptr;
+  const int *nodes = nullptr, *pc = nullptr;
   int64_t voff = 0;
   C *u = nullptr;
   if (active) {
@@ -600,6 +756,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_up(MfArgs a, c
     row = r < b;
     nodes = a.nodes + f.node_off;
     u = reinterpret_cast<C *>(a.ub_cur) + f.u_off * nrhs;
+    if (a.pcol) pc = a.pcol + f.piv_off;
     nseg = (p + MF_SEG - 1) / MF_SEG;
     seg0 = sidx * nseg / split;
     seg1 = (sidx + 1) * nseg / split;
@@ -615,7 +772,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_up(MfArgs a, c
         for (int q = 0; q < NR; ++q)
           if (q0 + q < nrhs) total[q] = u[(int64_t)(q0 + q) * b + r];
       auto gather = [&](int j, int q) {
-        return q0 + q < nrhs ? wl[(q0 + q) * ldt + voff + nodes[j]] : czero<C>();
+        return q0 + q < nrhs ? wl[(q0 + q) * ldt + voff + nodes[pc ? pc[j] : j]] : czero<C>();
       };
       for (int sg = seg0; sg < seg1; ++sg) {
         C sv[NR];
@@ -661,7 +818,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_down(MfArgs a,
   int p = 0, n = 0, r = 0, seg0 = 0, seg1 = 0, nseg = 0;
   bool row = false;
   const C *Fm = nullptr;
-  const int *nodes = nullptr;
+  const int *nodes = nullptr, *pc = nullptr;
   int64_t voff = 0;
   if (active) {
     const int2 item = items[it];
@@ -673,6 +830,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_down(MfArgs a,
     r = item.y * ROWS + lane;
     row = r < p;
     nodes = a.nodes + f.node_off;
+    if (a.pcol) pc = a.pcol + f.piv_off;
     nseg = (n + MF_SEG - 1) / MF_SEG;
     seg0 = sidx * nseg / split;
     seg1 = (sidx + 1) * nseg / split;
@@ -687,7 +845,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_down(MfArgs a,
       auto gather = [&](int c, int q) {
         if (q0 + q >= nrhs) return czero<C>();
         const int64_t base = (q0 + q) * ldt + voff;
-        return c < p ? wl[base + nodes[c]] : cneg(tv[base + nodes[c]]);
+        return c < p ? wl[base + nodes[pc ? pc[c] : c]] : cneg(tv[base + nodes[c]]);
       };
       for (int sg = seg0; sg < seg1; ++sg) {
         C sv[NR];
@@ -720,7 +878,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_down(MfArgs a,
 // 128-thread CTA per front above
 template <typename R> static size_t small_smem(int ldn, int fpc) {
   using C = typename CT<R>::T;
-  return sizeof(C) * fpc * (size_t)(ldn * ldn + 2 * ldn);
+  return sizeof(C) * fpc * (size_t)(ldn * ldn + 2 * ldn) + sizeof(int) * fpc * (size_t)ldn;
 }
 template <typename R> static size_t row_smem() {
   using C = typename CT<R>::T;
@@ -766,6 +924,10 @@ void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_
       const int m = L.max_n - std::min(MF_NB, std::max(1, L.max_p - k));
       const int tiles = std::max(1, (m + MF_PANEL_THREADS - 1) / MF_PANEL_THREADS);
       const int nt = std::max(1, (m + 63) / 64);
+      if (a.pcol) {
+        mf_gj_pivot<R><<<L.nf, 256, 0, st>>>(a, L.f0, k);
+        count_launch();
+      }
       mf_gj_diag<R><<<L.nf, MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
       mf_gj_col<R><<<dim3(L.nf, tiles), MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
       if (hook) hook->before(K_UPDATE, level, k);

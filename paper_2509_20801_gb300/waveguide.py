@@ -41,7 +41,7 @@ ORDERS = {"additive": 0, "multiplicative": 1, "red-black": 2}
 
 def run(nx=8192, ny=2048, nsub=32, precisions=("fp64", "c64", "fp16"), order="multiplicative", rtol=1e-8,
         restart=50, maxit=600, seed=2, device=0, out=sys.stdout, log=None, workload=None, keep_fields=False,
-        static_pivot=2):
+        static_pivot=2, pivoting=0):
     import torch
     import workloads as W
     from . import Solver
@@ -63,6 +63,7 @@ def run(nx=8192, ny=2048, nsub=32, precisions=("fp64", "c64", "fp16"), order="mu
         _b.stdd_set_option(s.ctx, _b.STDD_OPT_ORDER, ORDERS[order])
         sp = 0 if prec == "fp64" else static_pivot
         _b.stdd_set_option(s.ctx, _b.STDD_OPT_STATIC_PIVOT, sp)
+        _b.stdd_set_option(s.ctx, _b.STDD_OPT_PIVOTING, pivoting)
         try:
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             torch.cuda.synchronize(dev)
@@ -84,7 +85,8 @@ def run(nx=8192, ny=2048, nsub=32, precisions=("fp64", "c64", "fp16"), order="mu
             torch.cuda.synchronize(dev)
             row = dict(workload="waveguide-network", nx=w.nx, ny=w.ny, unknowns=w.n, nsub=w.nsub,
                        overlap=w.overlap, interface_pml=w.interface_pml, precision=prec, order=order,
-                       restart=w.restart, static_pivot=sp, raised_pivots=stats["raised_pivots"],
+                       restart=w.restart, static_pivot=sp, pivoting=pivoting,
+                       raised_pivots=stats["raised_pivots"],
                        factor_s=ev[0].elapsed_time(ev[1]) / 1e3,
                        factor_again_s=ev2[0].elapsed_time(ev2[1]) / 1e3,
                        solve_s=ev[1].elapsed_time(ev[2]) / 1e3, iterations=len(hist) - 1,
@@ -119,9 +121,11 @@ if __name__ == "__main__":
     ap.add_argument("--precisions", default="fp64,c64,fp16")
     ap.add_argument("--order", default="multiplicative", choices=sorted(ORDERS))
     ap.add_argument("--static-pivot", type=int, default=2)
+    ap.add_argument("--pivoting", type=int, default=0, choices=[0, 1],
+                    help="1: partial pivoting within each front's pivot rows")
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--restart", type=int, default=50)
     ap.add_argument("--maxit", type=int, default=600)
     a = ap.parse_args()
     run(a.nx, a.ny, a.nsub, tuple(a.precisions.split(",")), a.order, a.rtol, a.restart, a.maxit,
-        log=lambda m: print(m, file=sys.stderr, flush=True), static_pivot=a.static_pivot)
+        log=lambda m: print(m, file=sys.stderr, flush=True), static_pivot=a.static_pivot, pivoting=a.pivoting)

@@ -62,6 +62,37 @@ def test_static_pivoting_keeps_the_solution(small, precision, k, tol):
     assert _rel(fields[precision].ravel(), ref) <= tol
 
 
+@pytest.mark.parametrize("order", ["red-black", "multiplicative"])
+def test_small_network_pivoting_without_floor(small, order):
+    """Partial pivoting within the fronts, no static-pivot floor: complex64
+    factors with FP32, FP16 and BF16 updates reach a true residual of 1e-8
+    and the oracle's direct solution within 1e-7; FP64 factors within 1e-9."""
+    from paper_2509_20801_gb300 import waveguide
+    w, P, ref = small
+    rows, fields, _ = waveguide.run(workload=w, precisions=("fp64", "c64", "fp16", "bf16"), order=order,
+                                    rtol=1e-8, maxit=400, keep_fields=True, out=open("/dev/null", "w"),
+                                    static_pivot=0, pivoting=1)
+    for r in rows:
+        assert r["pivoting"] == 1 and r["static_pivot"] == 0 and r["raised_pivots"] == 0
+        assert r["converged"] and r["final_residual"] <= 1e-8, r
+        got = fields[r["precision"]].ravel()
+        rel_res = np.linalg.norm(w.b[0].ravel() - P.A @ got) / np.linalg.norm(w.b[0])
+        assert rel_res <= 1e-8 * (1 + 1e-6), (r["precision"], rel_res)
+        tol = 1e-9 if r["precision"] == "fp64" else 1e-7
+        assert _rel(got, ref) <= max(tol, 20 * rel_res), (r["precision"], _rel(got, ref))
+
+
+def test_pivoting_option_checks():
+    from paper_2509_20801_gb300 import STDD_OPT_PIVOTING, Solver, StddError, stdd_set_option
+    w = W.waveguide_network(768, 384, nsub=4, npml=24, overlap=8, interface_pml=24)
+    s = Solver.from_workload(w, eps=torch.from_numpy(w.eps_node).to("cuda:0"), precision=1)
+    for bad in (-1, 2):
+        with pytest.raises(StddError) as e:
+            stdd_set_option(s.ctx, STDD_OPT_PIVOTING, bad)
+        assert e.value.status == 1
+    s.close()
+
+
 def test_static_pivot_option_and_count():
     from paper_2509_20801_gb300 import STDD_OPT_STATIC_PIVOT, Solver, StddError, stdd_set_option
     w = W.waveguide_network(768, 384, nsub=4, npml=24, overlap=8, interface_pml=24)

@@ -65,14 +65,14 @@ def test_noalloc_residual_rejects_bad_use():
     from paper_2509_20801_gb300 import (Solver, StddError, stdd_create, stdd_destroy, stdd_residual_noalloc,
                                         stdd_set_grid)
     ctx = stdd_create(0)
-    x = torch.zeros(4, dtype=torch.complex128, device=DEV)
+    x, b, r = (torch.zeros(64, dtype=torch.complex128, device=DEV) for _ in range(3))
     stdd_set_grid(ctx, 8, 8, 0.1, 0.1)
     with pytest.raises(StddError) as e:    # operator not set up yet
-        stdd_residual_noalloc(ctx, x, x, x)
+        stdd_residual_noalloc(ctx, x, b, r)
     assert e.value.status == 2
     stdd_set_grid(ctx, 8192, 8193, 0.1, 0.1)   # 67,117,056 nodes > the fixed scratch
     with pytest.raises(StddError) as e:
-        stdd_residual_noalloc(ctx, x, x, x)
+        stdd_residual_noalloc(ctx, x, b, r)    # (refused before the buffers are touched)
     assert e.value.status == 1 and "67,108,864" in str(e.value)
     stdd_destroy(ctx)
     # output overlapping the field (in place, or shifted by one node) and a
