@@ -43,33 +43,41 @@ RTOL = 1e-8
 RESTART = 50
 FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor and tensor), NVIDIA's figure
 
-# DRAM bytes (read + write) per algorithmic unit of a kernel, from one ncu
-# capture of all its launches in one factorization of the benchmark workload
-# (summary in the named profile); used only while the kernel's source file
-# still has the recorded SHA-256, else the roofline's traffic is null.
+# DRAM bytes (read + write) of a kernel per flop it executes, from one ncu
+# capture of three launches of it on the 2048 x 512 waveguide network (the
+# update's traffic is the read-modify-write of the block it updates, which
+# grows with the executed flops, so it scales to the benchmark's launches);
+# used only while the kernel's source text (between the two markers) still
+# has the recorded SHA-256, else the roofline's traffic is null.
 NCU_TRAFFIC = {
     "mf_gj_update<double>": {
-        "bytes_per_unit": 75926832640 / 416732096864.0,  # DRAM bytes / algorithmic flops, 50 launches
+        "bytes_per_executed_flop": 1394.992640e6 / 11.533996032e9,  # 3 launches: DRAM bytes / executed flops
         "source": "paper_2509_20801_gb300/csrc/kernels_mf.cu",
-        "sha256": "bee4b8b5967dbffec7efd18af0d498f69fdbc008e90778d3446b16233da963a5",
-        "profile": "profiles/ncu_dram_mf_gj_update_fp64_metalens.md",
+        "begin": "// acc[4][4] += A(64 x K) B(K x 64)",
+        "end": "// ------------------------------------------------------- substitutions",
+        "sha256": "6decf2105b755b886e043790beeea94ba39fdd151acf1da500560430b40715db",
+        "profile": "profiles/ncu_dram_mf_gj_update_fp64_waveguide_2048x512.md",
     },
 }
 
 
-def ncu_traffic(kernel, units_per_launch):
+def ncu_traffic(kernel, executed_flops_per_launch):
     import hashlib
     rec = NCU_TRAFFIC.get(kernel)
-    if not rec:
+    if not rec or not executed_flops_per_launch:
         return None
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), rec["source"])
     try:
-        with open(path, "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
-                return None
-    except OSError:
+        with open(path) as f:
+            src = f.read()
+        a, b = src.index(rec["begin"]), src.index(rec["end"])
+        if hashlib.sha256(src[a:b].encode()).hexdigest() != rec["sha256"]:
+            return None
+    except (OSError, ValueError):
         return None
-    return rec["bytes_per_unit"] * units_per_launch
+    return rec["bytes_per_executed_flop"] * executed_flops_per_launch
+
+
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 
 
@@ -96,7 +104,11 @@ def parse():
                     help="preconditioner order (default: multiplicative on the waveguide, additive -- "
                          "Algorithm 1 -- elsewhere)")
     ap.add_argument("--static-pivot", type=int, default=None,
-                    help="static-pivot exponent of the complex64 forms (default 2 on the waveguide, else 0)")
+                    help="static-pivot exponent of the tensor-core (FP16 / BF16) forms (default 2 on the "
+                         "waveguide, else 0)")
+    ap.add_argument("--pivoting", type=int, default=None, choices=[0, 1],
+                    help="partial pivoting within the fronts for the complex64 forms (default 1 on the "
+                         "waveguide, else 0)")
     ap.add_argument("--maxit", type=int, default=2000, help="FGMRES iteration limit per right-hand side")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision and other-order runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -477,6 +489,20 @@ def run_ours(args, rank, world, local_rank):
         args.order = "multiplicative" if wave else "additive"
     if args.static_pivot is None:
         args.static_pivot = 2 if wave else 0
+    if args.pivoting is None:
+        args.pivoting = 1 if wave else 0
+
+    def pivots_for(p):
+        """(partial pivoting, static-pivot exponent) of a factor precision:
+        FP64 factors take neither; complex64 factors with FP32 updates take
+        partial pivoting within the fronts (no floor needed with it); the
+        tensor-core forms take the static-pivot floor, which suits their
+        coarser updates better than the interchanges."""
+        if p == S.STDD_PREC_FP64:
+            return 0, 0
+        if p == S.STDD_PREC_C64:
+            return args.pivoting, 0 if args.pivoting else args.static_pivot
+        return 0, args.static_pivot
     peaks = measured_peaks()
     fp64_tf = gemm_peak(torch, torch.float64, 4096)
     fp32_tf = gemm_peak(torch, torch.float32, 8192)
@@ -501,8 +527,9 @@ def run_ours(args, rank, world, local_rank):
         if args.leaf != 16:
             S.stdd_set_option(sv.ctx, S.STDD_OPT_LEAF, args.leaf)
         S.stdd_set_option(sv.ctx, S.STDD_OPT_BAND, band_for(p, order, band))
-        if p != S.STDD_PREC_FP64 and args.static_pivot:
-            S.stdd_set_option(sv.ctx, S.STDD_OPT_STATIC_PIVOT, args.static_pivot)
+        piv, sp = pivots_for(p)
+        S.stdd_set_option(sv.ctx, S.STDD_OPT_PIVOTING, piv)
+        S.stdd_set_option(sv.ctx, S.STDD_OPT_STATIC_PIVOT, sp)
         return sv
 
     def step(sv):
@@ -657,7 +684,7 @@ def run_ours(args, rank, world, local_rank):
         roof["executed_tflops"] = d["executed_tflops"]
     roof["measured_over"] = ("one extra step after the timed region with a CUDA-event span around every launch "
                              "(graphs bypassed); profiled step %.1f ms" % kprof["step_ms"])
-    roof["traffic"] = ncu_traffic(dom, d["units_per_launch"])
+    roof["traffic"] = ncu_traffic(dom, d.get("executed_flops_per_launch"))
     roof["traffic_source"] = NCU_TRAFFIC.get(dom, {}).get("profile") if roof["traffic"] is not None else None
 
     out = {
@@ -676,6 +703,7 @@ def run_ours(args, rank, world, local_rank):
                   S.STDD_PREC_C64_FP16: "c64-factors(fp16 tensor-core updates)+c128-krylov"}[prec],
         "data": "synthetic",
         "config": {"workload": workload_desc(w), "precision": args.precision, "order": args.order,
+                   "pivoting": pivots_for(prec)[0], "static_pivot": pivots_for(prec)[1],
                    "krylov_space": "band" if band_main else "full", "leaf": args.leaf, "rtol": RTOL,
                    "restart": RESTART, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (factors %.1f GB, Krylov basis %.1f GB)"
@@ -702,7 +730,9 @@ def run_ours(args, rank, world, local_rank):
         diff = float(torch.linalg.vector_norm(x_d - x_main) / torch.linalg.vector_norm(x_main))
         d_ = {"ms_per_step": ms_, "value": N / (ms_ * 1e-3) / 1e6, "iterations": len(hist_) - 1,
               "final_residual": st_["final_residual"], "converged": bool(st_["final_residual"] <= RTOL),
-              "t_factor_ms": prof_["factor_ms"], "t_solve_ms": prof_["solve_ms"], "rel_diff_vs_main": diff}
+              "t_factor_ms": prof_["factor_ms"], "t_solve_ms": prof_["solve_ms"], "rel_diff_vs_main": diff,
+              "solve_phases_ms": {"minv": prof_["minv_ms"], "minv_calls": prof_["minv_calls"],
+                                  "matvec": prof_["matvec_ms"], "gram_schmidt": prof_["ortho_ms"]}}
         d_.update(extra)
         return d_
 
@@ -715,9 +745,9 @@ def run_ours(args, rank, world, local_rank):
         out["compare_modes"] = {}
         for other in others:
             sv2, ms2, prof2, _, st2, hist2, _, _ = timed(other, 1, 1, 1)
+            piv2, sp2 = pivots_for(other)
             out["compare_modes"][names[other]] = summary(
-                ms2, prof2, st2, hist2, precision=names[other],
-                static_pivot=args.static_pivot if other != S.STDD_PREC_FP64 else 0,
+                ms2, prof2, st2, hist2, precision=names[other], pivoting=piv2, static_pivot=sp2,
                 raised_pivots=st2["raised_pivots"], order=args.order)
             sv2.close()
         out["compare"] = out["compare_modes"][names[others[0]]]

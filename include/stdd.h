@@ -105,6 +105,29 @@ stdd_status stdd_set_pml(stdd_ctx *ctx, const int npml[4], int order_m, double R
 stdd_status stdd_set_decomposition(stdd_ctx *ctx, int nsub, const int *x_cuts, int overlap,
                                    int interface_pml);
 
+/* Two-dimensional (checkerboard) decomposition: the strip construction of
+ * Sec. 2.3 applied along x (px parts, x_cuts as above) and, independently,
+ * along y (py parts, y_cuts: c_0 = 0 < ... < c_py = ny, or NULL for equal
+ * heights).  Box k = kx * py + ky owns the columns of x-part kx and the rows
+ * of y-part ky; its local box extends `overlap` nodes and then an
+ * `interface_pml`-cell PML past every side that has a neighbour, in x and in
+ * y, and keeps the global PML on the domain's sides; Dirichlet outside.  The
+ * preconditioner keeps its definition, M^-1 v = sum_k E_k A_k^-1 R_k^I v,
+ * summed over boxes (a node is covered by at most 9 local boxes).
+ * overlap + interface_pml must not exceed a neighbouring part's width or
+ * height.  py = 1 is stdd_set_decomposition.  With py > 1 only the additive
+ * order and full-space FGMRES apply (the other orders, band space and the
+ * Richardson mode return STDD_EINVAL).  Invalidates the factors.  (The paper
+ * partitions into x-strips only.) */
+stdd_status stdd_set_decomposition_2d(stdd_ctx *ctx, int px, const int *x_cuts, int py, const int *y_cuts,
+                                      int overlap, int interface_pml);
+
+/* Extents of box (or strip) k: out[0..7] = owned columns [c0, c1), owned
+ * rows [r0, r1), local box columns [x0, x1), local box rows [y0, y1).  The
+ * box's local fields (stdd_local_solve) are (x1 - x0) * (y1 - y0) complex
+ * values, local node (i - x0) * (y1 - y0) + (j - y0). */
+stdd_status stdd_box_info(const stdd_ctx *ctx, int box, int out[8]);
+
 /* One of STDD_PREC_*.  Invalidates the factors.  The Krylov iteration,
  * residuals and the returned fields are FP64 in every mode. */
 stdd_status stdd_set_precision(stdd_ctx *ctx, int mode);
@@ -158,8 +181,9 @@ stdd_status stdd_apply_operator(stdd_ctx *ctx, const double *x, double *y, int i
  * stdd_factor. */
 stdd_status stdd_apply_preconditioner(stdd_ctx *ctx, const double *v, double *z, int is_device);
 
-/* z = A_k^-1 t for strip k alone; t and z are local fields of
- * (x1 - x0) * ny complex values, local index (i - x0)*ny + j. */
+/* z = A_k^-1 t for strip (or box) k alone; t and z are local fields of
+ * (x1 - x0) * ny complex values, local index (i - x0)*ny + j (a box:
+ * (x1 - x0) * (y1 - y0) values, see stdd_box_info). */
 stdd_status stdd_local_solve(stdd_ctx *ctx, int strip, const double *t, double *z, int is_device);
 
 /* Columns of strip k: owned [c0, c1), local box [x0, x1). */

@@ -77,6 +77,8 @@ _SIGS = {
     "stdd_apply_preconditioner": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "stdd_local_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
     "stdd_strip_info": (c_int, [c_void_p, c_int, P(c_int), P(c_int), P(c_int), P(c_int)]),
+    "stdd_set_decomposition_2d": (c_int, [c_void_p, c_int, P(c_int), c_int, P(c_int), c_int, c_int]),
+    "stdd_box_info": (c_int, [c_void_p, c_int, P(c_int)]),
     "stdd_get_stats": (c_int, [c_void_p, P(stdd_stats)]),
     "stdd_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, P(c_double), c_int]),
     "stdd_residual_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, P(c_double)]),
@@ -244,6 +246,20 @@ def stdd_strip_info(ctx, strip):
     _check(ctx, lib.stdd_strip_info(ctx, int(strip), *[ctypes.byref(x) for x in v]))
     c0, c1, x0, x1 = (x.value for x in v)
     return dict(c0=c0, c1=c1, x0=x0, x1=x1)
+
+
+def stdd_set_decomposition_2d(ctx, px, py, overlap, interface_pml, x_cuts=None, y_cuts=None):
+    """px x py boxes (checkerboard); cuts as lists of px+1 / py+1 ints or None."""
+    xa = (c_int * (px + 1))(*[int(v) for v in x_cuts]) if x_cuts is not None else None
+    ya = (c_int * (py + 1))(*[int(v) for v in y_cuts]) if y_cuts is not None else None
+    return _check(ctx, lib.stdd_set_decomposition_2d(ctx, int(px), xa, int(py), ya, int(overlap),
+                                                     int(interface_pml)))
+
+
+def stdd_box_info(ctx, box):
+    v = (c_int * 8)()
+    _check(ctx, lib.stdd_box_info(ctx, int(box), v))
+    return dict(zip(("c0", "c1", "r0", "r1", "x0", "x1", "y0", "y1"), list(v)))
 
 
 def stdd_get_stats(ctx):

@@ -4,6 +4,7 @@
 // preconditioner is one Jacobi source-transfer sweep (Algorithm 1's loop
 // body in residual form, Eqs. 18-21).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -122,10 +123,40 @@ template <typename T> void upload(DBuf &d, const std::vector<T> &h, cudaStream_t
   if (!h.empty()) CK(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
 }
 
+// A subdomain: owned columns [c0, c1) and rows [r0, r1), local box
+// [x0, x1) x [y0, y1), local PML widths at its four sides.  Strips span all
+// rows (r0 = y0 = 0, r1 = y1 = ny, the global y-PML).
 struct StripHost {
   int c0, c1, x0, x1, Llo, Lhi;
+  int r0, r1, y0, y1, Lylo, Lyhi;
   int W() const { return x1 - x0; }
+  int H() const { return y1 - y0; }
 };
+
+// Strip partition of n nodes along one axis (Sec. 2.3): equal widths with
+// the remainder to the first parts, or explicit cuts; each part's local box
+// reaches ext = overlap + ipml nodes into each neighbour, whose width must
+// be at least ext.  Returns (owned begin, owned end, box begin, box end,
+// low PML, high PML) per part.
+std::vector<std::array<int, 6>> partition_axis(int n, int parts, const std::vector<int> &cuts, int overlap,
+                                               int ipml, int pml_lo, int pml_hi) {
+  const int ext = overlap + ipml;
+  std::vector<int> c = cuts;
+  if (c.empty()) {
+    c.push_back(0);
+    const int base = n / parts, rem = n % parts;
+    for (int k = 0; k < parts; ++k) c.push_back(c.back() + base + (k < rem ? 1 : 0));
+  }
+  std::vector<std::array<int, 6>> out;
+  for (int k = 0; k < parts; ++k) {
+    if (k > 0 && ext > c[k] - c[k - 1]) throw ArgError("overlap + interface PML wider than a neighbouring strip");
+    if (k < parts - 1 && ext > c[k + 2] - c[k + 1])
+      throw ArgError("overlap + interface PML wider than a neighbouring strip");
+    out.push_back({c[k], c[k + 1], k > 0 ? c[k] - ext : 0, k < parts - 1 ? c[k + 1] + ext : n,
+                   k > 0 ? ipml : pml_lo, k < parts - 1 ? ipml : pml_hi});
+  }
+  return out;
+}
 
 }  // namespace
 
@@ -145,6 +176,14 @@ struct stdd_ctx {
   bool have_pml = false;
   int nsub = 0, overlap = 0, ipml = 0;
   std::vector<int> cuts;
+  // 2-D (checkerboard) decomposition: nsx x nsy boxes, box k = kx * nsy + ky
+  // (nsy = 1: the strips of Sec. 2.3); nsub = nsx * nsy
+  int nsx = 0, nsy = 1;
+  std::vector<int> ycuts;
+  bool boxes() const { return nsy > 1; }
+  void require_strips(const char *what) const {
+    if (boxes()) throw ArgError(std::string(what) + " needs an x-strip decomposition (one box row)");
+  }
   int prec = STDD_PREC_FP64;
   int leaf_max = 16;
   int nrhs = 0;
@@ -157,9 +196,11 @@ struct stdd_ctx {
   // decomposition + factors
   bool factored = false;
   std::vector<StripHost> strips;
-  std::map<int, Shape> shapes;
+  std::map<std::pair<int, int>, Shape> shapes;   // ND analysis per local box shape (W, H)
   std::vector<LevelInfo> levels;
-  DBuf d_strips, d_fronts, d_nodes, d_cmap, d_inv, d_lcxm, d_lcxp, d_colstrip;
+  DBuf d_strips, d_fronts, d_nodes, d_cmap, d_inv, d_lcxm, d_lcxp, d_colstrip, d_lcym, d_lcyp, d_rowbox;
+  // distinct local y-coupling profiles (box height, low and high PML)
+  std::vector<std::array<int, 3>> ycoef_keys;
   DBuf d_fac, d_ws[2], d_ub[2], d_tloc, d_wloc, d_flag, d_minpiv, d_nraised, d_items;
   int64_t nloc = 0, nloc_max = 0, ub_elems[2] = {0, 0}, panel_need = 0;
   // partial pivoting restricted to each front's pivot rows (STDD_OPT_PIVOTING)
@@ -313,29 +354,56 @@ struct stdd_ctx {
 
   void build_strips() {
     if (nsub <= 0) throw StateError("decomposition not set");
-    const int ext = overlap + ipml;
-    std::vector<int> c = cuts;
-    if (c.empty()) {
-      c.push_back(0);
-      const int base = nx / nsub, rem = nx % nsub;
-      for (int k = 0; k < nsub; ++k) c.push_back(c.back() + base + (k < rem ? 1 : 0));
-    }
+    const auto xs = partition_axis(nx, nsx, cuts, overlap, ipml, npml[0], npml[1]);
+    const auto ys = nsy > 1 ? partition_axis(ny, nsy, ycuts, overlap, ipml, npml[2], npml[3])
+                            : std::vector<std::array<int, 6>>{{0, ny, 0, ny, npml[2], npml[3]}};
     strips.clear();
-    for (int k = 0; k < nsub; ++k) {
-      StripHost s;
-      s.c0 = c[k];
-      s.c1 = c[k + 1];
-      s.x0 = k > 0 ? s.c0 - ext : 0;
-      s.x1 = k < nsub - 1 ? s.c1 + ext : nx;
-      s.Llo = k > 0 ? ipml : npml[0];
-      s.Lhi = k < nsub - 1 ? ipml : npml[1];
-      if (k > 0 && ext > c[k] - c[k - 1]) throw ArgError("overlap + interface PML wider than a neighbouring strip");
-      if (k < nsub - 1 && ext > c[k + 2] - c[k + 1])
-        throw ArgError("overlap + interface PML wider than a neighbouring strip");
-      strips.push_back(s);
-    }
+    for (const auto &x : xs)
+      for (const auto &y : ys) {
+        StripHost s;
+        s.c0 = x[0];
+        s.c1 = x[1];
+        s.x0 = x[2];
+        s.x1 = x[3];
+        s.Llo = x[4];
+        s.Lhi = x[5];
+        s.r0 = y[0];
+        s.r1 = y[1];
+        s.y0 = y[2];
+        s.y1 = y[3];
+        s.Lylo = y[4];
+        s.Lyhi = y[5];
+        strips.push_back(s);
+      }
   }
 
+  // set a px x py decomposition (py = 1: strips), restoring the previous one
+  // if it is invalid
+  void set_boxes(int px, const std::vector<int> &xc, int py, const std::vector<int> &yc, int ov, int ip) {
+    const int o_n = nsub, o_x = nsx, o_y = nsy, o_o = overlap, o_p = ipml;
+    const auto o_c = cuts, o_yc = ycuts;
+    nsx = px;
+    nsy = py;
+    nsub = px * py;
+    cuts = xc;
+    ycuts = yc;
+    overlap = ov;
+    ipml = ip;
+    try {
+      build_strips();
+    } catch (...) {
+      nsub = o_n;
+      nsx = o_x;
+      nsy = o_y;
+      cuts = o_c;
+      ycuts = o_yc;
+      overlap = o_o;
+      ipml = o_p;
+      throw;
+    }
+    invalidate_factors();
+    clear_graphs();
+  }
   void factor();
   void build_structure();
   void upload_local_couplings();
@@ -350,6 +418,45 @@ struct stdd_ctx {
     long long kernels;
   };
   std::map<std::vector<const void *>, GraphEntry> minv_graphs;
+  // Capture the launches f() enqueues into an instantiated graph.  Any
+  // exception thrown while capturing (a refused argument, a CUDA error) ends
+  // the capture first, so the stream never stays in capture mode.  Kernels
+  // counted during capture are uncounted here and counted at each replay.
+  template <typename F> GraphEntry capture(F &&f) {
+    const long long before = __atomic_load_n(&stdd::g_launches, __ATOMIC_RELAXED);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      f();
+    } catch (...) {
+      cudaGraph_t dead = nullptr;
+      cudaStreamEndCapture(stream, &dead);
+      if (dead) cudaGraphDestroy(dead);
+      (void)cudaGetLastError();
+      const long long k = __atomic_load_n(&stdd::g_launches, __ATOMIC_RELAXED) - before;
+      __atomic_add_fetch(&stdd::g_launches, -k, __ATOMIC_RELAXED);
+      throw;
+    }
+    const cudaError_t ce = cudaStreamEndCapture(stream, &g);
+    if (ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      throw CudaError(std::string("graph capture: ") + cudaGetErrorString(ce));
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) throw CudaError(std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    const long long kernels = __atomic_load_n(&stdd::g_launches, __ATOMIC_RELAXED) - before;
+    __atomic_add_fetch(&stdd::g_launches, -kernels, __ATOMIC_RELAXED);
+    return GraphEntry{ex, kernels};
+  }
+
+  // captured graph of the numeric factorization, valid while every argument
+  // its launches were captured with (all levels' MfArgs bytes) is unchanged
+  cudaGraphExec_t factor_graph = nullptr;
+  long long factor_graph_kernels = 0;
+  std::vector<unsigned char> factor_graph_key;
+  template <typename R> void enqueue_factor();
   bool use_graphs = true;
   // preconditioner order: 0 additive (Algorithm 1), 1 symmetric
   // multiplicative, 2 red-black (even strips together, then odd strips)
@@ -385,6 +492,9 @@ struct stdd_ctx {
   void clear_graphs() {
     for (auto &kv : minv_graphs) cudaGraphExecDestroy(kv.second.exec);
     minv_graphs.clear();
+    if (factor_graph) cudaGraphExecDestroy(factor_graph);
+    factor_graph = nullptr;
+    factor_graph_key.clear();
   }
   template <typename R> void factor_t();
   template <typename R> void solve_levels(int nrhs_);
@@ -424,6 +534,7 @@ double stdd_ctx::pivot_floor() const {
 
 MfArgs stdd_ctx::mf_args(int par, bool solve) const {
   MfArgs a;
+  std::memset(&a, 0, sizeof a);  // padding too: the bytes key the factorization graph
   a.fronts = d_fronts.as<FrontDev>();
   a.strips = d_strips.as<StripDev>();
   a.nodes = d_nodes.as<int>();
@@ -431,8 +542,8 @@ MfArgs stdd_ctx::mf_args(int par, bool solve) const {
   a.inv = d_inv.as<int>();
   a.cxm = d_lcxm.as<double2>();
   a.cxp = d_lcxp.as<double2>();
-  a.cym = d_cym.as<double2>();
-  a.cyp = d_cyp.as<double2>();
+  a.cym = d_lcym.as<double2>();
+  a.cyp = d_lcyp.as<double2>();
   a.eps = d_eps.as<double>();
   a.k0sq = k0sq;
   a.H = ny;
@@ -470,6 +581,19 @@ void stdd_ctx::upload_local_couplings() {
   }
   upload(d_lcxm, lcxm, stream);
   upload(d_lcxp, lcxp, stream);
+  // local y couplings of the distinct box heights and PML widths (a strip
+  // decomposition has one: all rows with the global y-PML, the global ones)
+  std::vector<double2> lcym, lcyp;
+  for (const auto &yk : ycoef_keys) {
+    std::vector<cd> sy, syh;
+    stretch(yk[0], yk[1], yk[2], dy, k0, pml_m, pml_R, sy, syh);
+    std::vector<double2> cm, cp;
+    couplings(sy, syh, dy, cm, cp);
+    lcym.insert(lcym.end(), cm.begin(), cm.end());
+    lcyp.insert(lcyp.end(), cp.begin(), cp.end());
+  }
+  upload(d_lcym, lcym, stream);
+  upload(d_lcyp, lcyp, stream);
 }
 
 void stdd_ctx::factor() {
@@ -477,8 +601,10 @@ void stdd_ctx::factor() {
   build_strips();
   factored = false;
   clear_graphs();
-  std::vector<int64_t> key = {nx, ny, nsub, overlap, ipml, prec, leaf_max};
+  std::vector<int64_t> key = {nx, ny, nsub, nsx, nsy, overlap, ipml, prec, leaf_max};
   key.insert(key.end(), cuts.begin(), cuts.end());
+  key.push_back(-1);
+  key.insert(key.end(), ycuts.begin(), ycuts.end());
   if (!struct_ready || key != struct_key) {
     struct_ready = false;
     build_structure();
@@ -500,16 +626,18 @@ void stdd_ctx::factor() {
 // precision: symbolic analysis, strip and front descriptors, work items,
 // device buffers.  Cached across factorizations of the same structure.
 void stdd_ctx::build_structure() {
-  // ---- symbolic analysis per distinct strip width (host, cached)
+  // ---- symbolic analysis per distinct local box shape (host, cached)
   for (auto &s : strips) {
-    if (!shapes.count(s.W()) || shapes[s.W()].H != ny || shapes[s.W()].leaf_max != leaf_max) {
+    const std::pair<int, int> key{s.W(), s.H()};
+    if (!shapes.count(key) || shapes[key].leaf_max != leaf_max) {
       Shape sh;
-      stdd::nd_analyze(s.W(), ny, leaf_max, sh);
-      shapes[s.W()] = std::move(sh);
+      stdd::nd_analyze(s.W(), s.H(), leaf_max, sh);
+      shapes[key] = std::move(sh);
     }
   }
+  auto shape_of = [&](const StripHost &s) -> const Shape & { return shapes.at({s.W(), s.H()}); };
   // concatenated shape arrays
-  std::map<int, int64_t> node_base, cmap_base, inv_base;
+  std::map<std::pair<int, int>, int64_t> node_base, cmap_base, inv_base;
   std::vector<int> nodes, cmap, inv;
   for (auto &kv : shapes) {
     node_base[kv.first] = (int64_t)nodes.size();
@@ -526,18 +654,30 @@ void stdd_ctx::build_structure() {
   max_p = max_b = 0;
   factor_cflops = factor_cflops_lu = solve_cflops = 0;
   nloc_max = 0;
+  ycoef_keys.clear();
   for (int k = 0; k < nsub; ++k) {
     const StripHost &s = strips[k];
-    const Shape &sh = shapes[s.W()];
+    const Shape &sh = shape_of(s);
     sdev[k].x0 = s.x0;
     sdev[k].x1 = s.x1;
     sdev[k].c0 = s.c0;
     sdev[k].c1 = s.c1;
+    sdev[k].y0 = s.y0;
+    sdev[k].y1 = s.y1;
+    sdev[k].r0 = s.r0;
+    sdev[k].r1 = s.r1;
+    // local y couplings, one copy per distinct (height, low PML, high PML)
+    const std::array<int, 3> yk{s.H(), s.Lylo, s.Lyhi};
+    int64_t yoff = 0;
+    size_t q = 0;
+    for (; q < ycoef_keys.size() && ycoef_keys[q] != yk; ++q) yoff += ycoef_keys[q][0];
+    if (q == ycoef_keys.size()) ycoef_keys.push_back(yk);
+    sdev[k].ycoef_off = yoff;
     sdev[k].vec_off = vec;
     sdev[k].coef_off = coef;
     sdev[k].fac_off = fac;
-    vec += (int64_t)s.W() * ny;
-    nloc_max = std::max<int64_t>(nloc_max, (int64_t)s.W() * ny);
+    vec += (int64_t)s.W() * s.H();
+    nloc_max = std::max<int64_t>(nloc_max, (int64_t)s.W() * s.H());
     fac += sh.factor_entries;
     coef += s.W();
     depth = std::max(depth, sh.depth);
@@ -551,7 +691,7 @@ void stdd_ctx::build_structure() {
   factor_entries = fac;
   // ---- front instances, level-major
   std::vector<std::vector<int>> inst(nsub);
-  for (int k = 0; k < nsub; ++k) inst[k].assign(shapes[strips[k].W()].fronts.size(), -1);
+  for (int k = 0; k < nsub; ++k) inst[k].assign(shape_of(strips[k]).fronts.size(), -1);
   std::vector<FrontDev> fr;
   levels.assign(depth, LevelInfo{0, 0, 0, 0, 0, 1 << 30, 0, 0, 0, 0, 32, 32, 1, 1});
   perm.clear();
@@ -574,7 +714,8 @@ void stdd_ctx::build_structure() {
     for (int j = 0; j < nsub; ++j) {
       const int k = perm[j];
       lvl_front[L][j] = (int)fr.size();
-      const Shape &sh = shapes[strips[k].W()];
+      const Shape &sh = shape_of(strips[k]);
+      const std::pair<int, int> skey{sh.W, sh.H};
       for (size_t f = 0; f < sh.fronts.size(); ++f) {
         const auto &sf = sh.fronts[f];
         if (sf.level != L) continue;
@@ -584,10 +725,10 @@ void stdd_ctx::build_structure() {
         d.b = sf.b;
         d.strip = k;
         d.child[0] = d.child[1] = -1;
-        d.node_off = node_base[sh.W] + sf.node_off;
+        d.node_off = node_base[skey] + sf.node_off;
         for (int ci = 0; ci < 2; ++ci) {
-          d.cmap_off[ci] = sf.cmap_off[ci] >= 0 ? cmap_base[sh.W] + sf.cmap_off[ci] : -1;
-          d.inv_off[ci] = sf.inv_off[ci] >= 0 ? inv_base[sh.W] + sf.inv_off[ci] : -1;
+          d.cmap_off[ci] = sf.cmap_off[ci] >= 0 ? cmap_base[skey] + sf.cmap_off[ci] : -1;
+          d.inv_off[ci] = sf.inv_off[ci] >= 0 ? inv_base[skey] + sf.inv_off[ci] : -1;
         }
         d.fac_off = sdev[k].fac_off + sf.fac_off;
         d.s_off = s_run;
@@ -613,7 +754,7 @@ void stdd_ctx::build_structure() {
   }
   // children ids (instances of children are at level + 1, already numbered)
   for (int k = 0; k < nsub; ++k) {
-    const Shape &sh = shapes[strips[k].W()];
+    const Shape &sh = shape_of(strips[k]);
     for (size_t f = 0; f < sh.fronts.size(); ++f) {
       FrontDev &d = fr[inst[k][f]];
       for (int ci = 0; ci < 2; ++ci)
@@ -686,9 +827,13 @@ void stdd_ctx::build_structure() {
     }
     li.n_down = (int)((int64_t)items.size() - li.down_off);
   }
-  std::vector<int> colstrip(nx);
-  for (int k = 0; k < nsub; ++k)
-    for (int i = strips[k].c0; i < strips[k].c1; ++i) colstrip[i] = k;
+  // owner of every column (the strip, or the box column kx) and of every row
+  // (the box row ky)
+  std::vector<int> colstrip(nx), rowbox(ny);
+  for (int k = 0; k < nsub; ++k) {
+    for (int i = strips[k].c0; i < strips[k].c1; ++i) colstrip[i] = k / nsy;
+    for (int j = strips[k].r0; j < strips[k].r1; ++j) rowbox[j] = k % nsy;
+  }
 
   strips_host = sdev;
   fronts_host = fr;
@@ -700,6 +845,7 @@ void stdd_ctx::build_structure() {
   upload(d_cmap, cmap, stream);
   upload(d_inv, inv, stream);
   upload(d_colstrip, colstrip, stream);
+  upload(d_rowbox, rowbox, stream);
   upload(d_items, items, stream);
   const size_t E = elem();
   d_fac.alloc(std::max<int64_t>(1, factor_entries) * E);
@@ -787,16 +933,37 @@ template <typename R> void stdd_ctx::factor_t() {
     CK(stdd::tc_setup_attributes());
     attrs = true;
   }
-  CK(cudaMemsetAsync(d_flag.p, 0, sizeof(int), stream));
-  CK(cudaMemsetAsync(d_nraised.p, 0, sizeof(unsigned long long), stream));
-  const double inf = INFINITY;
-  CK(cudaMemcpyAsync(d_minpiv.p, &inf, sizeof(double), cudaMemcpyHostToDevice, stream));
   const int span = pbegin(PH_FACTOR);
-  for (int L = depth - 1; L >= 0; --L) {
-    MfArgs a = mf_args(L & 1, false);
-    hook.c = this;
-    stdd::mf_factor_level<R>(a, levels[L], L, stream, &hook, tc_fmt());
-    CK(cudaGetLastError());
+  if (use_graphs && prof < 2) {
+    // one replayed graph for all levels (captured again whenever a pointer
+    // or value the launches were captured with has changed)
+    std::vector<unsigned char> key;
+    auto put = [&](const void *p, size_t nb) {
+      const unsigned char *c = static_cast<const unsigned char *>(p);
+      key.insert(key.end(), c, c + nb);
+    };
+    const int tc = tc_fmt();
+    const size_t rs = sizeof(R);
+    put(&tc, sizeof tc);
+    put(&rs, sizeof rs);
+    put(&depth, sizeof depth);
+    for (int par = 0; par < 2; ++par) {
+      const MfArgs a = mf_args(par, false);
+      put(&a, sizeof a);
+    }
+    for (const LevelInfo &li : levels) put(&li, sizeof li);
+    if (!factor_graph || key != factor_graph_key) {
+      if (factor_graph) cudaGraphExecDestroy(factor_graph);
+      factor_graph = nullptr;
+      const GraphEntry ge = capture([&] { enqueue_factor<R>(); });
+      factor_graph_kernels = ge.kernels;
+      factor_graph = ge.exec;
+      factor_graph_key = key;
+    }
+    CK(cudaGraphLaunch(factor_graph, stream));
+    stdd::count_launch((int)factor_graph_kernels);
+  } else {
+    enqueue_factor<R>();
   }
   pend(span);
   int flag = 0;
@@ -808,6 +975,17 @@ template <typename R> void stdd_ctx::factor_t() {
   raised_pivots = (long long)nr;
   if (flag & 2) throw TimeoutError("a tensor-core tile did not complete within its wait limit");
   if (flag & 1) throw std::domain_error("zero or non-finite pivot in a front");
+}
+
+// The launches of one numeric factorization, leaves to root.
+template <typename R> void stdd_ctx::enqueue_factor() {
+  stdd::mf_factor_begin(mf_args(0, false), stream);
+  for (int L = depth - 1; L >= 0; --L) {
+    MfArgs a = mf_args(L & 1, false);
+    hook.c = this;
+    stdd::mf_factor_level<R>(a, levels[L], L, stream, &hook, tc_fmt());
+    CK(cudaGetLastError());
+  }
 }
 
 template <typename R> void stdd_ctx::solve_levels(int nr) {
@@ -1065,22 +1243,7 @@ void stdd_ctx::apply_op_band(const std::vector<const double2 *> &ss, const std::
     }
     auto it = minv_graphs.find(key);
     if (it == minv_graphs.end()) {
-      const long long before = __atomic_load_n(&stdd::g_launches, __ATOMIC_RELAXED);
-      cudaGraph_t g = nullptr;
-      CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-      enqueue_op_band(ss, ys);
-      const cudaError_t ce = cudaStreamEndCapture(stream, &g);
-      if (ce != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        throw CudaError(std::string("graph capture: ") + cudaGetErrorString(ce));
-      }
-      cudaGraphExec_t ex = nullptr;
-      const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
-      cudaGraphDestroy(g);
-      if (ie != cudaSuccess) throw CudaError(std::string("graph instantiate: ") + cudaGetErrorString(ie));
-      const long long kernels = __atomic_load_n(&stdd::g_launches, __ATOMIC_RELAXED) - before;
-      __atomic_add_fetch(&stdd::g_launches, -kernels, __ATOMIC_RELAXED);
-      it = minv_graphs.emplace(key, GraphEntry{ex, kernels}).first;
+      it = minv_graphs.emplace(key, capture([&] { enqueue_op_band(ss, ys); })).first;
     }
     CK(cudaGraphLaunch(it->second.exec, stream));
     stdd::count_launch((int)it->second.kernels);
@@ -1125,22 +1288,7 @@ void stdd_ctx::apply_minv_multi(const std::vector<const double2 *> &vs, const st
     }
     auto it = minv_graphs.find(key);
     if (it == minv_graphs.end()) {
-      const long long before = __atomic_load_n(&stdd::g_launches, __ATOMIC_RELAXED);
-      cudaGraph_t g = nullptr;
-      CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-      enqueue_minv(vs, zs);
-      const cudaError_t ce = cudaStreamEndCapture(stream, &g);
-      if (ce != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        throw CudaError(std::string("graph capture: ") + cudaGetErrorString(ce));
-      }
-      cudaGraphExec_t ex = nullptr;
-      const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
-      cudaGraphDestroy(g);
-      if (ie != cudaSuccess) throw CudaError(std::string("graph instantiate: ") + cudaGetErrorString(ie));
-      const long long kernels = __atomic_load_n(&stdd::g_launches, __ATOMIC_RELAXED) - before;
-      __atomic_add_fetch(&stdd::g_launches, -kernels, __ATOMIC_RELAXED);  // counted at replay
-      it = minv_graphs.emplace(key, GraphEntry{ex, kernels}).first;
+      it = minv_graphs.emplace(key, capture([&] { enqueue_minv(vs, zs); })).first;
     }
     CK(cudaGraphLaunch(it->second.exec, stream));
     stdd::count_launch((int)it->second.kernels);
@@ -1156,12 +1304,32 @@ void stdd_ctx::enqueue_minv(const std::vector<const double2 *> &vs, const std::v
   const int na = (int)vs.size();
   const size_t E = elem();
   if (order != 0) {
+    require_strips("the multiplicative and red-black orders");
     if (order == 2) check_red_black();
     if (prec == STDD_PREC_FP64) enqueue_minv_multiplicative<double>(vs, zs);
     else enqueue_minv_multiplicative<float>(vs, zs);
     return;
   }
   auto slot = [&](int i) { return static_cast<void *>(d_tloc.as<char>() + (size_t)i * nloc * E); };
+  if (boxes()) {
+    // 2-D boxes: owned blocks in, full local fields summed over <= 9 boxes out
+    const StripDev *bx = d_strips.as<StripDev>();
+    if (prec == STDD_PREC_FP64) {
+      for (int i = 0; i < na; ++i) stdd::launch_restrict_box<double>(bx, nsub, nloc_max, ny, vs[i], slot(i), stream);
+      solve_levels<double>(na);
+      for (int i = 0; i < na; ++i)
+        stdd::launch_synthesize_box<double>(bx, nsx, nsy, nx, ny, d_colstrip.as<int>(), d_rowbox.as<int>(), slot(i),
+                                            zs[i], stream);
+    } else {
+      for (int i = 0; i < na; ++i) stdd::launch_restrict_box<float>(bx, nsub, nloc_max, ny, vs[i], slot(i), stream);
+      solve_levels<float>(na);
+      for (int i = 0; i < na; ++i)
+        stdd::launch_synthesize_box<float>(bx, nsx, nsy, nx, ny, d_colstrip.as<int>(), d_rowbox.as<int>(), slot(i),
+                                           zs[i], stream);
+    }
+    CK(cudaGetLastError());
+    return;
+  }
   if (prec == STDD_PREC_FP64) {
     for (int i = 0; i < na; ++i)
       stdd::launch_restrict<double>(d_strips.as<StripDev>(), nsub, nloc_max, ny, nullptr, vs[i], slot(i), stream);
@@ -1541,7 +1709,7 @@ void stdd_ctx::richardson(int rhs, const stdd_solve_opts &o, double2 *x) {
 
 int64_t stdd_ctx::device_bytes() const {
   const DBuf *all[] = {&d_eps, &d_cxm, &d_cxp, &d_cym, &d_cyp, &d_strips, &d_fronts, &d_nodes, &d_cmap,
-                       &d_inv, &d_lcxm, &d_lcxp, &d_colstrip, &d_fac, &d_ws[0], &d_ws[1], &d_ub[0],
+                       &d_inv, &d_lcxm, &d_lcxp, &d_colstrip, &d_lcym, &d_lcyp, &d_rowbox, &d_fac, &d_ws[0], &d_ws[1], &d_ub[0],
                        &d_ub[1], &d_tloc, &d_wloc, &d_items, &d_flag, &d_minpiv, &d_b, &d_x, &d_r, &d_V, &d_Z, &d_w,
                        &d_part, &d_h, &d_nrm, &d_y, &d_pre, &d_fpart, &d_guess, &d_gscr, &d_pcol, &d_panel};
   int64_t s = 0;
@@ -1697,6 +1865,10 @@ stdd_status stdd_set_grid(stdd_ctx *c, int nx, int ny, double dx, double dy) {
     c->have_eps = false;
     c->nrhs = 0;
     c->nsub = 0;
+    c->nsx = 0;
+    c->nsy = 1;
+    c->cuts.clear();
+    c->ycuts.clear();
     c->shapes.clear();
     c->invalidate_operator();
   });
@@ -1748,22 +1920,40 @@ stdd_status stdd_set_decomposition(stdd_ctx *c, int nsub, const int *x_cuts, int
       for (int k = 0; k < nsub; ++k)
         if (cuts[k + 1] <= cuts[k]) throw ArgError("cuts must increase");
     }
-    const int old_n = c->nsub, old_o = c->overlap, old_p = c->ipml;
-    const auto old_c = c->cuts;
-    c->nsub = nsub;
-    c->cuts = cuts;
-    c->overlap = overlap;
-    c->ipml = ipml;
-    try {
-      c->build_strips();
-    } catch (...) {
-      c->nsub = old_n;
-      c->cuts = old_c;
-      c->overlap = old_o;
-      c->ipml = old_p;
-      throw;
-    }
-    c->invalidate_factors();
+    if (nsub > c->nx) throw ArgError("bad decomposition");
+    c->set_boxes(nsub, cuts, 1, {}, overlap, ipml);
+  });
+}
+
+stdd_status stdd_set_decomposition_2d(stdd_ctx *c, int px, const int *x_cuts, int py, const int *y_cuts, int overlap,
+                                      int ipml) {
+  return guarded(c, [&] {
+    if (c->nx <= 0) throw StateError("grid not set");
+    if (px < 1 || px > c->nx || py < 1 || py > c->ny || overlap < 0 || ipml < 0)
+      throw ArgError("bad decomposition");
+    auto take = [](const int *cu, int parts, int n, std::vector<int> &out) {
+      if (!cu) return;
+      out.assign(cu, cu + parts + 1);
+      if (out.front() != 0 || out.back() != n) throw ArgError("cuts must run from 0 to the grid size");
+      for (int k = 0; k < parts; ++k)
+        if (out[k + 1] <= out[k]) throw ArgError("cuts must increase");
+    };
+    std::vector<int> xc, yc;
+    take(x_cuts, px, c->nx, xc);
+    take(y_cuts, py, c->ny, yc);
+    c->set_boxes(px, xc, py, yc, overlap, ipml);
+  });
+}
+
+stdd_status stdd_box_info(const stdd_ctx *cc, int k, int out[8]) {
+  stdd_ctx *c = const_cast<stdd_ctx *>(cc);
+  return guarded(c, [&] {
+    if (!out) throw ArgError("null output");
+    if (c->strips.empty()) c->build_strips();
+    if (k < 0 || k >= (int)c->strips.size()) throw ArgError("bad box");
+    const StripHost &s = c->strips[k];
+    const int v[8] = {s.c0, s.c1, s.r0, s.r1, s.x0, s.x1, s.y0, s.y1};
+    std::memcpy(out, v, sizeof v);
   });
 }
 
@@ -1805,6 +1995,9 @@ stdd_status stdd_solve(stdd_ctx *c, const stdd_solve_opts *o, double *x_out, int
     if (o->x0_mode < STDD_X0_ZERO || o->x0_mode > STDD_X0_LEARNED) throw ArgError("bad x0_mode");
     if (c->use_band && !o->paper_richardson && (c->prec != STDD_PREC_FP64 || c->order != 0))
       throw ArgError("band-space FGMRES needs FP64 factors and the additive order");
+    if (c->use_band && !o->paper_richardson) c->require_strips("band-space FGMRES");
+    if (o->paper_richardson) c->require_strips("the paper's Richardson mode (Eq. 20 stopping test)");
+    if (c->order != 0) c->require_strips("the multiplicative and red-black orders");
     const int64_t n = c->N();
     c->history.assign(c->nrhs, {});
     c->lg_raw.assign(c->nrhs, 0.0);
@@ -1883,9 +2076,9 @@ stdd_status stdd_local_solve(stdd_ctx *c, int k, const double *t, double *z, int
     if (!t || !z) throw ArgError("null vector");
     if (!c->factored) throw StateError("not factored");
     if (k < 0 || k >= c->nsub) throw ArgError("bad strip");
-    const int64_t nl = (int64_t)c->strips[k].W() * c->ny;
+    const int64_t nl = (int64_t)c->strips[k].W() * c->strips[k].H();
     int64_t off = 0;
-    for (int kk = 0; kk < k; ++kk) off += (int64_t)c->strips[kk].W() * c->ny;
+    for (int kk = 0; kk < k; ++kk) off += (int64_t)c->strips[kk].W() * c->strips[kk].H();
     c->ensure_solve_buffers(1);
     c->d_w.alloc(nl * sizeof(double2));
     copy_in(c->d_w.p, t, nl * sizeof(double2), is_device, c->stream);

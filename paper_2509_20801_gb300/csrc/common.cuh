@@ -80,13 +80,18 @@ template <typename C> __device__ __forceinline__ C shfl(C v, int src) {
 }
 
 // ---------------------------------------------------------- descriptors
-// One strip (subdomain) of the decomposition.
+// One subdomain of the decomposition: an x-strip spanning every row, or a
+// box of a 2-D (checkerboard) decomposition.  Its local field is W x Hl
+// nodes, local node (lx, ly) at lx * Hl + ly, W = x1 - x0, Hl = y1 - y0.
 struct StripDev {
   int x0, x1;          // local box columns [x0, x1) of the global grid
   int c0, c1;          // owned columns [c0, c1)
   int64_t vec_off;     // offset of the strip's local field in the local buffer
   int64_t coef_off;    // offset of the strip's x coefficients (W entries)
   int64_t fac_off;     // offset of the strip's factor block (complex entries)
+  int y0, y1;          // local box rows [y0, y1) (0, ny for a strip)
+  int r0, r1;          // owned rows [r0, r1)
+  int64_t ycoef_off;   // offset of the local box's y coefficients (Hl entries)
 };
 
 // One front instance (a symbolic front of some strip shape in some strip).

@@ -23,10 +23,10 @@ struct MfArgs {
   const StripDev *strips;
   const int *nodes, *cmap, *inv;
   const double2 *cxm, *cxp;   // per-strip x couplings, indexed coef_off + local column
-  const double2 *cym, *cyp;   // y couplings, indexed by row
+  const double2 *cym, *cyp;   // per-box y couplings, indexed ycoef_off + local row
   const double *eps;          // global node permittivity
   double k0sq;
-  int H;                      // ny
+  int H;                      // ny (row stride of the global permittivity)
   void *fac;                  // factor storage (complex R)
   void *ws_cur;               // F22 of this level
   const void *ws_child;       // F22 of the level below
@@ -63,6 +63,9 @@ struct LaunchHook {
 };
 
 template <typename R> cudaError_t mf_setup_attributes();
+// start of a factorization: clear the pivot flag and the raised-pivot count,
+// set the smallest-pivot record to +inf (one kernel, so it can be captured)
+void mf_factor_begin(const MfArgs &a, cudaStream_t st);
 // tc_fmt: -1 CUDA-core updates; 0 / 1 tensor-core updates with FP16 / BF16 inputs
 template <typename R>
 void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_t st, LaunchHook *hook = nullptr,
@@ -103,6 +106,14 @@ void launch_restrict(const StripDev *strips_dev, int nsub, int64_t nloc, int ny,
 template <typename R>
 void launch_synthesize(const StripDev *strips_dev, int nsub, int nx, int ny, const int *col_strip,
                        const void *tloc, double2 *z, cudaStream_t st);
+// 2-D boxes (px x py, box id kx * py + ky): restriction to the owned blocks
+// and synthesis of the full local fields (<= 9 boxes per node)
+template <typename R>
+void launch_restrict_box(const StripDev *boxes_dev, int nbox, int64_t nloc_max, int ny, const double2 *v, void *tloc,
+                         cudaStream_t st);
+template <typename R>
+void launch_synthesize_box(const StripDev *boxes_dev, int px, int py, int nx, int ny, const int *col_box,
+                           const int *row_box, const void *tloc, double2 *z, cudaStream_t st);
 // out[2k] = ||e_k^F||^2, out[2k+1] = ||e_k||^2 of every strip's local field
 template <typename R>
 void launch_strip_norms(const StripDev *strips_dev, int nsub, int ny, const void *tloc, double *out,

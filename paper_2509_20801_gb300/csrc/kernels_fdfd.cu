@@ -104,6 +104,48 @@ __global__ void __launch_bounds__(TPB) k_synthesize(const StripDev *__restrict__
   }
 }
 
+// 2-D (checkerboard) boxes: local node (lx, ly) of box s is global node
+// (x0 + lx, y0 + ly); R_s^I keeps the owned block [c0, c1) x [r0, r1)
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_restrict_box(const StripDev *__restrict__ boxes, int ny,
+                                                      const double2 *__restrict__ v, void *tloc) {
+  using C = typename CT<R>::T;
+  const StripDev s = boxes[blockIdx.y];
+  const int Hl = s.y1 - s.y0;
+  const int64_t nl = (int64_t)(s.x1 - s.x0) * Hl;
+  C *t = reinterpret_cast<C *>(tloc) + s.vec_off;
+  for (int64_t l = (int64_t)blockIdx.x * TPB + threadIdx.x; l < nl; l += (int64_t)gridDim.x * TPB) {
+    const int lx = (int)(l / Hl), ly = (int)(l - (int64_t)lx * Hl);
+    const int gx = s.x0 + lx, gy = s.y0 + ly;
+    t[l] = (gx >= s.c0 && gx < s.c1 && gy >= s.r0 && gy < s.r1) ? to_c(v[(int64_t)gx * ny + gy], C()) : czero<C>();
+  }
+}
+
+// z = sum_k E_k local[k] over boxes: node (i, j) is covered by at most the
+// 3 x 3 boxes around its owner (col_box[i], row_box[j]); summed in box order
+// (x-major), each box id kx * py + ky
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_synthesize_box(const StripDev *__restrict__ boxes, int px, int py, int nx,
+                                                        int ny, const int *__restrict__ col_box,
+                                                        const int *__restrict__ row_box, const void *tloc,
+                                                        double2 *__restrict__ z) {
+  using C = typename CT<R>::T;
+  const C *t = reinterpret_cast<const C *>(tloc);
+  const int64_t n = (int64_t)nx * ny;
+  for (int64_t g = (int64_t)blockIdx.x * TPB + threadIdx.x; g < n; g += (int64_t)gridDim.x * TPB) {
+    const int i = (int)(g / ny), j = (int)(g - (int64_t)i * ny);
+    const int kx = col_box[i], ky = row_box[j];
+    double2 acc = make_double2(0.0, 0.0);
+    for (int bx = max(0, kx - 1); bx <= min(px - 1, kx + 1); ++bx)
+      for (int by = max(0, ky - 1); by <= min(py - 1, ky + 1); ++by) {
+        const StripDev s = boxes[bx * py + by];
+        if (i >= s.x0 && i < s.x1 && j >= s.y0 && j < s.y1)
+          acc = cadd(acc, to_d(t[s.vec_off + (int64_t)(i - s.x0) * (s.y1 - s.y0) + (j - s.y0)]));
+      }
+    z[g] = acc;
+  }
+}
+
 // one strip s: t = R_s^I (v - A z) on its local box (zero off the owned
 // columns), the source of its local solve in the multiplicative order
 template <typename R>
@@ -310,6 +352,28 @@ void launch_synthesize(const StripDev *strips_dev, int nsub, int nx, int ny, con
   k_synthesize<R><<<grid_for((int64_t)nx * ny), TPB, 0, st>>>(strips_dev, nsub, nx, ny, col_strip, tloc, z);
   count_launch();
 }
+
+template <typename R>
+void launch_restrict_box(const StripDev *boxes_dev, int nbox, int64_t nloc_max, int ny, const double2 *v, void *tloc,
+                         cudaStream_t st) {
+  const int gx = (int)std::min<int64_t>((nloc_max + TPB - 1) / TPB, 1024);
+  k_restrict_box<R><<<dim3(gx, nbox), TPB, 0, st>>>(boxes_dev, ny, v, tloc);
+  count_launch();
+}
+
+template <typename R>
+void launch_synthesize_box(const StripDev *boxes_dev, int px, int py, int nx, int ny, const int *col_box,
+                           const int *row_box, const void *tloc, double2 *z, cudaStream_t st) {
+  k_synthesize_box<R><<<grid_for((int64_t)nx * ny), TPB, 0, st>>>(boxes_dev, px, py, nx, ny, col_box, row_box, tloc,
+                                                                   z);
+  count_launch();
+}
+template void launch_restrict_box<double>(const StripDev *, int, int64_t, int, const double2 *, void *, cudaStream_t);
+template void launch_restrict_box<float>(const StripDev *, int, int64_t, int, const double2 *, void *, cudaStream_t);
+template void launch_synthesize_box<double>(const StripDev *, int, int, int, int, const int *, const int *,
+                                            const void *, double2 *, cudaStream_t);
+template void launch_synthesize_box<float>(const StripDev *, int, int, int, int, const int *, const int *,
+                                           const void *, double2 *, cudaStream_t);
 
 template <typename R> void launch_to_local(const double2 *t, void *tloc, int64_t n, cudaStream_t st) {
   k_to_local<R><<<grid_for(n), TPB, 0, st>>>(t, tloc, n);

@@ -120,24 +120,24 @@ __device__ __forceinline__ int unband(int i, int k, int nbk) { return i < k ? i 
 template <typename C>
 __device__ __forceinline__ C front_entry(const MfArgs &a, const FrontDev &f, const StripDev &s, const FrontDev *ch,
                                          const bool *has, int r, int c) {
-  const int p = f.p, H = a.H;
+  const int p = f.p, H = s.y1 - s.y0;   // local box height
   double2 v = make_double2(0.0, 0.0);
   if (r < p || c < p) {
     const int u = a.nodes[f.node_off + r], w = a.nodes[f.node_off + c];
     const int ux = u / H, uy = u - ux * H;
     if (u == w) {
       const double2 xm = a.cxm[s.coef_off + ux], xp = a.cxp[s.coef_off + ux];
-      const double2 ym = a.cym[uy], yp = a.cyp[uy];
-      v.x = a.k0sq * a.eps[(int64_t)(s.x0 + ux) * H + uy] - xm.x - xp.x - ym.x - yp.x;
+      const double2 ym = a.cym[s.ycoef_off + uy], yp = a.cyp[s.ycoef_off + uy];
+      v.x = a.k0sq * a.eps[(int64_t)(s.x0 + ux) * a.H + s.y0 + uy] - xm.x - xp.x - ym.x - yp.x;
       v.y = -xm.y - xp.y - ym.y - yp.y;
     } else if (w == u - H) {
       v = a.cxm[s.coef_off + ux];
     } else if (w == u + H) {
       v = a.cxp[s.coef_off + ux];
     } else if (w == u - 1 && uy > 0) {
-      v = a.cym[uy];
+      v = a.cym[s.ycoef_off + uy];
     } else if (w == u + 1 && uy < H - 1) {
-      v = a.cyp[uy];
+      v = a.cyp[s.ycoef_off + uy];
     }
   }
   C out = to_c(v, C());
@@ -980,6 +980,17 @@ void mf_down_level(const MfArgs &a, const int2 *items, int nitems, int rows, int
     if (nr == 4) STDD_DOWN(32, 4); else if (nr == 2) STDD_DOWN(32, 2); else STDD_DOWN(32, 1);
   }
 #undef STDD_DOWN
+  count_launch();
+}
+
+__global__ void k_factor_begin(int *flag, unsigned long long *n_raised, double *min_pivot) {
+  *flag = 0;
+  *n_raised = 0ull;
+  *min_pivot = INFINITY;
+}
+
+void mf_factor_begin(const MfArgs &a, cudaStream_t st) {
+  k_factor_begin<<<1, 1, 0, st>>>(a.flag, a.n_raised, a.min_pivot);
   count_launch();
 }
 

@@ -326,3 +326,40 @@ def test_pivoting_interchanges_rows_and_is_deterministic(cyl):
         s.close()
     assert not np.array_equal(outs[0], outs[1]) and _rel(outs[1], outs[0]) < 1e-10
     assert np.array_equal(outs[1], outs[2])
+
+
+def test_factorization_graph_follows_configuration_changes(rnd):
+    """The factorization replays a captured graph; after the permittivity
+    (same buffer, new values), the frequency (a value baked into the
+    launches) or the pivoting option changes, the next factorization still
+    gives the oracle's local solves for the new problem, and repeated
+    factorizations are bitwise equal to one without graphs."""
+    from paper_2509_20801_gb300 import (STDD_OPT_GRAPHS, STDD_OPT_PIVOTING, stdd_apply_preconditioner,
+                                        stdd_set_frequency, stdd_set_option, stdd_set_permittivity)
+    w, P, D = rnd
+    v_h = W.random_vector(P.n, seed=9)[0]
+    v = torch.from_numpy(v_h).to(DEV)
+    s = _solver(w)
+    ref = _solver(w)
+    stdd_set_option(ref.ctx, STDD_OPT_GRAPHS, 0)
+    z, zr = torch.empty_like(v), torch.empty_like(v)
+    for _ in range(3):                      # capture, then replays
+        s.factor()
+        stdd_apply_preconditioner(s.ctx, v, z)
+    ref.factor()
+    stdd_apply_preconditioner(ref.ctx, v, zr)
+    assert torch.equal(z, zr)
+    # new permittivity values in the same device buffer, then a new frequency
+    eps2 = w.eps_node * 1.1
+    stdd_set_permittivity(s.ctx, torch.from_numpy(eps2).to(DEV))
+    for wl in (w.wavelength, w.wavelength * 1.07):
+        stdd_set_frequency(s.ctx, wl)
+        for piv in (0, 1):
+            stdd_set_option(s.ctx, STDD_OPT_PIVOTING, piv)
+            s.factor()
+            stdd_apply_preconditioner(s.ctx, v, z)
+            P2 = Problem(P.nx, P.ny, P.dx, P.dy, wl, eps2, w.npml, w.pml_order, w.pml_R)
+            D2 = DDM(P2, w.nsub, w.overlap, w.interface_pml)
+            assert _rel(z.cpu().numpy(), D2.apply_Minv(v_h)) < 1e-10, (wl, piv)
+    s.close()
+    ref.close()
