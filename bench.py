@@ -100,7 +100,7 @@ def parse():
     ap.add_argument("--band", type=int, default=None, choices=[0, 1],
                     help="1: band-space FGMRES (FP64 factors, additive order; same iterates, band-sized "
                          "vectors); default 1 where it applies")
-    ap.add_argument("--order", default=None, choices=["additive", "multiplicative", "red-black"],
+    ap.add_argument("--order", default=None, choices=["additive", "multiplicative", "red-black", "forward"],
                     help="preconditioner order (default: multiplicative on the waveguide, additive -- "
                          "Algorithm 1 -- elsewhere)")
     ap.add_argument("--static-pivot", type=int, default=None,
@@ -110,6 +110,8 @@ def parse():
                     help="partial pivoting within the fronts for the complex64 forms (default 1 on the "
                          "waveguide, else 0)")
     ap.add_argument("--maxit", type=int, default=2000, help="FGMRES iteration limit per right-hand side")
+    ap.add_argument("--persistent", type=int, default=1, choices=[0, 1],
+                    help="1: one persistent launch per strip solve in the sequential orders")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision and other-order runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -513,7 +515,7 @@ def run_ours(args, rank, world, local_rank):
     prec = {"fp64": S.STDD_PREC_FP64, "c64": S.STDD_PREC_C64, "bf16": S.STDD_PREC_C64_BF16,
             "fp16": S.STDD_PREC_C64_FP16}[args.precision]
 
-    orders = {"additive": 0, "multiplicative": 1, "red-black": 2}
+    orders = {"additive": 0, "multiplicative": 1, "red-black": 2, "forward": 3}
 
     def band_for(p, order, band):
         if band is None:
@@ -528,6 +530,7 @@ def run_ours(args, rank, world, local_rank):
             S.stdd_set_option(sv.ctx, S.STDD_OPT_LEAF, args.leaf)
         S.stdd_set_option(sv.ctx, S.STDD_OPT_BAND, band_for(p, order, band))
         piv, sp = pivots_for(p)
+        S.stdd_set_option(sv.ctx, S.STDD_OPT_PERSISTENT, args.persistent)
         S.stdd_set_option(sv.ctx, S.STDD_OPT_PIVOTING, piv)
         S.stdd_set_option(sv.ctx, S.STDD_OPT_STATIC_PIVOT, sp)
         return sv
@@ -704,6 +707,7 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": workload_desc(w), "precision": args.precision, "order": args.order,
                    "pivoting": pivots_for(prec)[0], "static_pivot": pivots_for(prec)[1],
+                   "persistent_sweeps": args.persistent,
                    "krylov_space": "band" if band_main else "full", "leaf": args.leaf, "rtol": RTOL,
                    "restart": RESTART, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (factors %.1f GB, Krylov basis %.1f GB)"

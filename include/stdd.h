@@ -307,7 +307,10 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     local box never reaches the owned columns of the next
  *                     strip of its colour: needs every interior strip wider
  *                     than overlap + interface PML + 1, else STDD_EINVAL
- *                     when it is applied).  In paper_richardson mode the
+ *                     when it is applied); 3 = forward multiplicative, the
+ *                     strips once, k = 0..n-1 (half the local solves of
+ *                     order 1 per application; not symmetric, which flexible
+ *                     GMRES does not need).  In paper_richardson mode the
  *                     stationary iteration uses the chosen order.
  * and one that changes how FGMRES works (same iterates in exact arithmetic):
  *   STDD_OPT_BAND     (default 0): 1 = band-space FGMRES.  For the additive
@@ -342,7 +345,20 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     the elimination's growth, harmless in FP64, can ruin
  *                     complex64 factors (high-index guided-wave geometries).
  *                     Invalidates the factors. */
-/*   STDD_OPT_PIVOTING (default 0): 1 = partial pivoting restricted to each
+/*   STDD_OPT_PERSISTENT (default 1): in the sequential orders (1 and 3,
+ *                     one right-hand side at a time) each strip's solve --
+ *                     residual restriction, the upward and the downward
+ *                     sweep over all tree levels, the add-back -- runs as
+ *                     one cooperative launch whose levels are separated by
+ *                     grid-wide barriers instead of ~3 launches per level;
+ *                     0: one launch per level.  Same arithmetic, same
+ *                     results.
+ *   STDD_OPT_SWEEP_WAIT (default 0 = 4,194,304): polls a block spends at one
+ *                     grid barrier of a persistent sweep before it gives up;
+ *                     then every block returns, the call that applied the
+ *                     preconditioner returns STDD_ETIMEOUT, and the context
+ *                     stays usable.
+ *   STDD_OPT_PIVOTING (default 0): 1 = partial pivoting restricted to each
  *                     front's pivot rows.  Before each pivot (each 32-pivot
  *                     block of a large front) the not yet eliminated pivot
  *                     row whose entry in the pivot column is largest in
@@ -361,7 +377,9 @@ enum {
   STDD_OPT_ORDER = 4,
   STDD_OPT_BAND = 5,
   STDD_OPT_STATIC_PIVOT = 6,
-  STDD_OPT_PIVOTING = 7
+  STDD_OPT_PIVOTING = 7,
+  STDD_OPT_PERSISTENT = 8,
+  STDD_OPT_SWEEP_WAIT = 9
 };
 stdd_status stdd_set_option(stdd_ctx *ctx, int option, int value);
 stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);

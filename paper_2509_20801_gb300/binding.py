@@ -297,6 +297,8 @@ def stdd_residual_noalloc(ctx, x, b, r):
 STDD_OPT_GRAPHS, STDD_OPT_AUTOTUNE, STDD_OPT_LEAF, STDD_OPT_ORDER, STDD_OPT_BAND = 1, 2, 3, 4, 5
 STDD_OPT_STATIC_PIVOT = 6
 STDD_OPT_PIVOTING = 7
+STDD_OPT_PERSISTENT = 8
+STDD_OPT_SWEEP_WAIT = 9
 
 
 def stdd_set_profiling(ctx, level=1):

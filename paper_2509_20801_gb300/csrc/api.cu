@@ -304,6 +304,14 @@ struct stdd_ctx {
       if (open >= 0) c->pend(open);
       open = -1;
     }
+    // a launch over a fraction of a level's substitution items
+    void before_part(int kind, int level, double frac) {
+      before(kind, level, 0);
+      if (open >= 0) {
+        c->span_units[open] *= frac;
+        c->span_exec[open] *= frac;
+      }
+    }
   } hook;
 
   size_t elem() const { return prec == STDD_PREC_FP64 ? sizeof(double2) : sizeof(float2); }
@@ -519,6 +527,24 @@ struct stdd_ctx {
   bool autotune_on = true;
   MfArgs mf_args(int level_parity_cur, bool solve) const;
   void ensure_krylov(int m);
+  // persistent one-strip sweeps of the sequential orders (STDD_OPT_PERSISTENT):
+  // per strip position and level the strip's share of the sweep
+  bool persistent = true;
+  long long sweep_wait = 1ll << 22;   // polls of a grid-barrier wait before it gives up
+  DBuf d_striplv, d_bar, d_sweep_flag;
+  int sweep_flag_h = 0;
+  void build_strip_levels();
+  void poll_sweep_flag() {           // enqueue a copy of the flag (read after the next sync)
+    if (d_sweep_flag.p) CK(cudaMemcpyAsync(&sweep_flag_h, d_sweep_flag.p, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  }
+  void raise_sweep_flag() {          // after a sync: a persistent sweep gave up a barrier wait
+    if (sweep_flag_h & 1) {
+      sweep_flag_h = 0;
+      CK(cudaMemsetAsync(d_sweep_flag.p, 0, sizeof(int), stream));
+      CK(cudaStreamSynchronize(stream));
+      throw TimeoutError("a persistent substitution sweep gave up waiting at a grid barrier");
+    }
+  }
   void gmres_multi(const stdd_solve_opts &o);
   void richardson(int rhs, const stdd_solve_opts &o, double2 *x);
   void learned_guesses(double2 *X);  // all right-hand sides
@@ -620,6 +646,39 @@ void stdd_ctx::factor() {
     if (prec == STDD_PREC_FP64) autotune<double>();
     else autotune<float>();
   }
+  build_strip_levels();
+}
+
+// Each strip's share of every level, for the persistent sweeps (after the
+// autotuner: it carries the single-strip launch shapes).
+void stdd_ctx::build_strip_levels() {
+  std::vector<stdd::StripLevel> t((size_t)nsub * depth);
+  for (int j = 0; j < nsub; ++j)
+    for (int L = 0; L < depth; ++L) {
+      const LevelInfo &li = levels[L];
+      stdd::StripLevel &l = t[(size_t)j * depth + L];
+      l.f0 = lvl_front[L][j];
+      l.nf = lvl_front[L][j + 1] - lvl_front[L][j];
+      l.up_first = li.up_off + lvl_up[L][j];
+      l.up_n = lvl_up[L][j + 1] - lvl_up[L][j];
+      l.down_first = li.down_off + lvl_down[L][j];
+      l.down_n = lvl_down[L][j + 1] - lvl_down[L][j];
+      l.rows_up = li.rows_up;
+      l.rows_down = li.rows_down;
+      l.split_up = li.split_up1;
+      l.split_down = li.split_down1;
+    }
+  upload(d_striplv, t, stream);
+  stdd::mf_strip_sweep_grid();   // launch shape queried once, outside any capture
+  if (!d_bar.p) {
+    d_bar.alloc(2 * sizeof(unsigned));
+    CK(cudaMemsetAsync(d_bar.p, 0, 2 * sizeof(unsigned), stream));
+  }
+  if (!d_sweep_flag.p) {
+    d_sweep_flag.alloc(sizeof(int));
+    CK(cudaMemsetAsync(d_sweep_flag.p, 0, sizeof(int), stream));
+  }
+  CK(cudaStreamSynchronize(stream));
 }
 
 // Everything that depends only on the grid, the decomposition and the
@@ -693,7 +752,7 @@ void stdd_ctx::build_structure() {
   std::vector<std::vector<int>> inst(nsub);
   for (int k = 0; k < nsub; ++k) inst[k].assign(shape_of(strips[k]).fronts.size(), -1);
   std::vector<FrontDev> fr;
-  levels.assign(depth, LevelInfo{0, 0, 0, 0, 0, 1 << 30, 0, 0, 0, 0, 32, 32, 1, 1});
+  levels.assign(depth, LevelInfo{0, 0, 0, 0, 0, 1 << 30, 0, 0, 0, 0, 32, 32, 1, 1, 1, 1});
   perm.clear();
   for (int k = 0; k < nsub; k += 2) perm.push_back(k);
   for (int k = 1; k < nsub; k += 2) perm.push_back(k);
@@ -807,8 +866,8 @@ void stdd_ctx::build_structure() {
     LevelInfo &li = levels[L];
     li.rows_up = li.max_b <= 16 ? 16 : 32;
     li.rows_down = li.max_p <= 16 ? 16 : 32;
-    li.split_up = pow2_split(li.max_p, li.rows_up);
-    li.split_down = pow2_split(li.max_n, li.rows_down);
+    li.split_up = li.split_up1 = pow2_split(li.max_p, li.rows_up);
+    li.split_down = li.split_down1 = pow2_split(li.max_n, li.rows_down);
     li.up_off = (int64_t)items.size();
     for (int k = 0; k <= nsub; ++k) {
       lvl_up[L][k] = (int)((int64_t)items.size() - li.up_off);
@@ -862,58 +921,76 @@ void stdd_ctx::build_structure() {
 // split (1, 2, 4, 8 row groups per item) on the real fronts; the result is
 // cached per level shape and does not change the arithmetic (fixed
 // summation segments), only the speed.
+// Two launch shapes are tuned per level and direction: the launch over every
+// strip's fronts (additive order, band space) and the launch over one
+// strip's fronts (the sequential orders solve one strip at a time, with far
+// fewer work items, so a wider split pays there).
 template <typename R> void stdd_ctx::autotune() {
   ensure_solve_buffers(1);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   const int2 *items = d_items.as<int2>();
+  const int one = pos[std::min(1, nsub - 1)];   // an interior strip's position in the level lists
   for (int L = 0; L < depth; ++L) {
     LevelInfo &li = levels[L];
-    for (int dir = 0; dir < 2; ++dir) {
-      const int rows = dir == 0 ? li.rows_up : li.rows_down;
-      const int cols = dir == 0 ? li.max_p : li.max_n;
-      const int nitems = dir == 0 ? li.n_up : li.n_down;
-      if (nitems == 0) continue;
-      const std::vector<int64_t> key = {device, dir, (int64_t)sizeof(R), li.nf, li.max_p, li.max_b, li.min_n,
-                                        nitems, rows};
-      int best = dir == 0 ? li.split_up : li.split_down;
-      bool found = false;
-      {
-        std::lock_guard<std::mutex> lk(tuned_mutex());
-        auto hit = tuned().find(key);
-        if (hit != tuned().end()) {
-          best = hit->second;
-          found = true;
-        }
+    for (int range = 0; range < 2; ++range) {
+      if (range == 1 && nsub == 1) {
+        li.split_up1 = li.split_up;
+        li.split_down1 = li.split_down;
+        continue;
       }
-      if (!found) {
-        float best_ms = 1e30f;
-        for (int sp = 1; sp <= 8; sp *= 2) {
-          if (sp > 256 / rows) break;
-          if (sp > 1 && (cols + stdd::MF_SEG - 1) / stdd::MF_SEG > stdd::MF_MAXSEG) break;
-          float ms_min = 1e30f;
-          for (int rep = 0; rep < 3; ++rep) {
-            MfArgs a = mf_args(L & 1, true);
-            CK(cudaEventRecord(e0, stream));
-            if (dir == 0) stdd::mf_up_level<R>(a, items + li.up_off, nitems, rows, sp, 1, nloc, stream);
-            else stdd::mf_down_level<R>(a, items + li.down_off, nitems, rows, sp, 1, nloc, stream);
-            CK(cudaEventRecord(e1, stream));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            ms_min = std::min(ms_min, ms);
-          }
-          if (ms_min < best_ms) {
-            best_ms = ms_min;
-            best = sp;
+      for (int dir = 0; dir < 2; ++dir) {
+        const int rows = dir == 0 ? li.rows_up : li.rows_down;
+        const int cols = dir == 0 ? li.max_p : li.max_n;
+        int64_t first = dir == 0 ? li.up_off : li.down_off;
+        int nitems = dir == 0 ? li.n_up : li.n_down;
+        if (range == 1) {
+          const std::vector<int> &lv = dir == 0 ? lvl_up[L] : lvl_down[L];
+          first += lv[one];
+          nitems = lv[one + 1] - lv[one];
+        }
+        if (nitems == 0) continue;
+        const std::vector<int64_t> key = {device, dir, (int64_t)sizeof(R), li.nf, li.max_p, li.max_b, li.min_n,
+                                          nitems, rows, range};
+        int best = dir == 0 ? li.split_up : li.split_down;
+        bool found = false;
+        {
+          std::lock_guard<std::mutex> lk(tuned_mutex());
+          auto hit = tuned().find(key);
+          if (hit != tuned().end()) {
+            best = hit->second;
+            found = true;
           }
         }
-        std::lock_guard<std::mutex> lk(tuned_mutex());
-        tuned()[key] = best;
+        if (!found) {
+          float best_ms = 1e30f;
+          for (int sp = 1; sp <= 8; sp *= 2) {
+            if (sp > 256 / rows) break;
+            if (sp > 1 && (cols + stdd::MF_SEG - 1) / stdd::MF_SEG > stdd::MF_MAXSEG) break;
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+              MfArgs a = mf_args(L & 1, true);
+              CK(cudaEventRecord(e0, stream));
+              if (dir == 0) stdd::mf_up_level<R>(a, items + first, nitems, rows, sp, 1, nloc, stream);
+              else stdd::mf_down_level<R>(a, items + first, nitems, rows, sp, 1, nloc, stream);
+              CK(cudaEventRecord(e1, stream));
+              CK(cudaEventSynchronize(e1));
+              float ms = 0;
+              CK(cudaEventElapsedTime(&ms, e0, e1));
+              ms_min = std::min(ms_min, ms);
+            }
+            if (ms_min < best_ms) {
+              best_ms = ms_min;
+              best = sp;
+            }
+          }
+          std::lock_guard<std::mutex> lk(tuned_mutex());
+          tuned()[key] = best;
+        }
+        int &dst = range == 0 ? (dir == 0 ? li.split_up : li.split_down) : (dir == 0 ? li.split_up1 : li.split_down1);
+        dst = best;
       }
-      if (dir == 0) li.split_up = best;
-      else li.split_down = best;
     }
   }
   CK(cudaEventDestroy(e0));
@@ -1015,21 +1092,29 @@ template <typename R> void stdd_ctx::solve_levels(int nr) {
 // and work items.
 template <typename R> void stdd_ctx::solve_range_levels(int j0, int j1, int nr) {
   const int2 *items = d_items.as<int2>();
+  hook.c = this;
+  // per-launch spans (profiling level 2) credit each launch with its share
+  // of the level's factor bytes, by its fraction of the level's work items
   for (int L = depth - 1; L >= 0; --L) {
     LevelInfo li = levels[L];
     li.f0 = lvl_front[L][j0];
     li.nf = lvl_front[L][j1] - lvl_front[L][j0];
     if (li.nf == 0) continue;
+    const int cnt = lvl_up[L][j1] - lvl_up[L][j0];
     stdd::mf_up_gather_level<R>(mf_args(L & 1, true), li, nr, nloc, stream);
-    stdd::mf_up_level<R>(mf_args(L & 1, true), items + li.up_off + lvl_up[L][j0], lvl_up[L][j1] - lvl_up[L][j0],
-                         li.rows_up, li.split_up, nr, nloc, stream);
+    hook.before_part(stdd::K_UP, L, levels[L].n_up ? (double)cnt / levels[L].n_up : 0.0);
+    stdd::mf_up_level<R>(mf_args(L & 1, true), items + li.up_off + lvl_up[L][j0], cnt, li.rows_up,
+                         j1 - j0 == 1 ? li.split_up1 : li.split_up, nr, nloc, stream);
+    hook.after(stdd::K_UP, L, 0);
   }
   for (int L = 0; L < depth; ++L) {
     const LevelInfo &li = levels[L];
     const int cnt = lvl_down[L][j1] - lvl_down[L][j0];
     if (cnt == 0) continue;
+    hook.before_part(stdd::K_DOWN, L, li.n_down ? (double)cnt / li.n_down : 0.0);
     stdd::mf_down_level<R>(mf_args(L & 1, true), items + li.down_off + lvl_down[L][j0], cnt, li.rows_down,
-                           li.split_down, nr, nloc, stream);
+                           j1 - j0 == 1 ? li.split_down1 : li.split_down, nr, nloc, stream);
+    hook.after(stdd::K_DOWN, L, 0);
   }
   CK(cudaGetLastError());
 }
@@ -1064,7 +1149,22 @@ void stdd_ctx::enqueue_minv_multiplicative(const std::vector<const double2 *> &v
     if (nsub > 1) groups.push_back({ne, nsub});
   } else {
     for (int k = 0; k < nsub; ++k) groups.push_back({pos[k], pos[k] + 1});
-    for (int k = nsub - 2; k >= 0; --k) groups.push_back({pos[k], pos[k] + 1});
+    if (order == 1)  // symmetric: back again (order 3 is the forward sweep alone)
+      for (int k = nsub - 2; k >= 0; --k) groups.push_back({pos[k], pos[k] + 1});
+  }
+  if (persistent && na == 1 && order != 2 && d_striplv.p) {
+    // one cooperative launch per strip solve (the barrier counters are
+    // cleared before each, so a sweep that gave up leaves nothing behind)
+    MfArgs a = mf_args(0, true);
+    a.items_sweep = d_items.as<int2>();
+    for (const auto &gr : groups) {
+      const int j = gr.first;
+      CK(cudaMemsetAsync(d_bar.p, 0, 2 * sizeof(unsigned), stream));
+      CK(stdd::mf_strip_sweep_launch<R>(a, d_ub[0].p, d_ub[1].p, g, strips_host[perm[j]],
+                                        d_striplv.as<stdd::StripLevel>() + (size_t)j * depth, depth, vs[0], zs[0],
+                                        d_bar.as<unsigned>(), d_sweep_flag.as<int>(), sweep_wait, stream));
+    }
+    return;
   }
   for (const auto &gr : groups) {
     for (int j = gr.first; j < gr.second; ++j)
@@ -1564,7 +1664,9 @@ void stdd_ctx::gmres_multi(const stdd_solve_opts &o) {
         CK(cudaMemcpyAsync(S[q].hv.data(), h1(q), sizeof(double2) * (j + 2), cudaMemcpyDeviceToHost, stream));
         CK(cudaMemcpyAsync(&S[q].nrm2, nrmq(q), sizeof(double), cudaMemcpyDeviceToHost, stream));
       }
+      poll_sweep_flag();
       CK(cudaStreamSynchronize(stream));
+      raise_sweep_flag();
       std::vector<int> again;
       for (int q : inner) {
         St &t = S[q];
@@ -1711,7 +1813,8 @@ int64_t stdd_ctx::device_bytes() const {
   const DBuf *all[] = {&d_eps, &d_cxm, &d_cxp, &d_cym, &d_cyp, &d_strips, &d_fronts, &d_nodes, &d_cmap,
                        &d_inv, &d_lcxm, &d_lcxp, &d_colstrip, &d_lcym, &d_lcyp, &d_rowbox, &d_fac, &d_ws[0], &d_ws[1], &d_ub[0],
                        &d_ub[1], &d_tloc, &d_wloc, &d_items, &d_flag, &d_minpiv, &d_b, &d_x, &d_r, &d_V, &d_Z, &d_w,
-                       &d_part, &d_h, &d_nrm, &d_y, &d_pre, &d_fpart, &d_guess, &d_gscr, &d_pcol, &d_panel};
+                       &d_part, &d_h, &d_nrm, &d_y, &d_pre, &d_fpart, &d_guess, &d_gscr, &d_pcol, &d_panel,
+                       &d_striplv, &d_bar, &d_sweep_flag};
   int64_t s = 0;
   for (auto *d : all) s += (int64_t)d->bytes;
   return s;
@@ -2023,7 +2126,9 @@ stdd_status stdd_solve(stdd_ctx *c, const stdd_solve_opts *o, double *x_out, int
       noconv = c->last_noconv;
     }
     c->pend(span);
+    c->poll_sweep_flag();
     copy_out(x_out, X, (size_t)c->nrhs * n * sizeof(double2), is_device, c->stream);
+    c->raise_sweep_flag();
   });
   if (st == STDD_OK && noconv) {
     c->err = "maxit reached before rtol";
@@ -2067,7 +2172,9 @@ stdd_status stdd_apply_preconditioner(stdd_ctx *c, const double *v, double *z, i
     c->d_r.alloc(n * sizeof(double2));
     copy_in(c->d_w.p, v, n * sizeof(double2), is_device, c->stream);
     c->apply_minv(c->d_w.as<double2>(), c->d_r.as<double2>());
+    c->poll_sweep_flag();
     copy_out(z, c->d_r.p, n * sizeof(double2), is_device, c->stream);
+    c->raise_sweep_flag();
   });
 }
 
@@ -2173,8 +2280,9 @@ stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
         c->autotune_on = value != 0;
         break;
       case STDD_OPT_ORDER:
-        if (value < 0 || value > 2)
-          throw ArgError("order must be 0 (additive), 1 (symmetric multiplicative) or 2 (red-black)");
+        if (value < 0 || value > 3)
+          throw ArgError("order must be 0 (additive), 1 (symmetric multiplicative), 2 (red-black) or 3 (forward "
+                         "multiplicative)");
         if (value != c->order) {
           c->order = value;
           c->clear_graphs();
@@ -2182,6 +2290,17 @@ stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
         break;
       case STDD_OPT_BAND:
         c->use_band = value != 0;
+        break;
+      case STDD_OPT_PERSISTENT:
+        if (value != (int)c->persistent) {
+          c->persistent = value != 0;
+          c->clear_graphs();
+        }
+        break;
+      case STDD_OPT_SWEEP_WAIT:
+        if (value < 0) throw ArgError("wait limit must be >= 0 (0: the default)");
+        c->sweep_wait = value == 0 ? (1ll << 22) : (long long)value;
+        c->clear_graphs();
         break;
       case STDD_OPT_PIVOTING:
         if (value < 0 || value > 1) throw ArgError("pivoting must be 0 (off) or 1 (partial, within fronts)");

@@ -43,6 +43,7 @@ struct MfArgs {
   // stored F11^-1 and -G21 blocks multiplies; panel: pivot-search scratch.
   int *pcol;
   void *panel;
+  const int2 *items_sweep;    // the substitution work items (persistent sweep)
 };
 
 struct LevelInfo {
@@ -52,6 +53,7 @@ struct LevelInfo {
   int n_up, n_down;           // (front, row chunk) items going up / down
   int rows_up, rows_down;     // rows per item: 16 or 32
   int split_up, split_down;   // row groups sharing one item's columns (1..8)
+  int split_up1, split_down1; // the same for launches over one strip's fronts (sequential orders)
 };
 
 // Optional per-launch observer (phase profiling): kind is one of the K_*
@@ -79,6 +81,26 @@ void mf_tc_update_launch(const MfArgs &a, const LevelInfo &L, int k, int fmt, cu
 int tc_tile_product(int fmt, int kc, const float2 *C, const float2 *R, float2 *D, cudaError_t *err);
 template <typename R>
 void mf_up_gather_level(const MfArgs &a, const LevelInfo &L, int nrhs, int64_t ldt, cudaStream_t st);
+
+// One strip's share of one tree level, for the persistent sweep.
+struct StripLevel {
+  int f0, nf;                  // the strip's fronts at this level
+  int up_n, down_n;            // its upward / downward work items
+  int64_t up_first, down_first;
+  int rows_up, rows_down, split_up, split_down;
+};
+struct GridDev;
+// Persistent sweep of one strip (one right-hand side): t = R_s^I (v - A z),
+// the upward products leaves to root, the downward ones root to leaves,
+// then z += E_s t -- one cooperative launch, the levels separated by a
+// grid-wide barrier whose waits give up after wait_limit polls (then
+// *sweep_flag |= 1 and every block returns).  bar: two zeroed unsigned.
+template <typename R>
+cudaError_t mf_strip_sweep_launch(const MfArgs &a, const void *ub0, const void *ub1, const GridDev &g,
+                                  const StripDev &s, const StripLevel *lv_dev, int depth, const double2 *v,
+                                  double2 *z, unsigned *bar, int *sweep_flag, long long wait_limit,
+                                  cudaStream_t st);
+int mf_strip_sweep_grid();   // blocks of the persistent sweep (co-resident); call outside stream capture
 template <typename R>
 void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
                  cudaStream_t st);
@@ -94,6 +116,22 @@ struct GridDev {
   const double2 *cxm, *cxp;   // global x couplings (nx)
   const double2 *cym, *cyp;   // y couplings (ny)
 };
+
+// Row idx = i * ny + j of the global operator applied to x (the stretched
+// 5-point stencil of Eqs. 2, 9; zero field beyond the grid).
+__device__ __forceinline__ double2 grid_row(const GridDev &g, const double2 *__restrict__ x, int64_t idx, int i,
+                                            int j) {
+  const double2 xm = g.cxm[i], xp = g.cxp[i], ym = g.cym[j], yp = g.cyp[j];
+  double2 d;
+  d.x = g.k0sq * g.eps[idx] - xm.x - xp.x - ym.x - yp.x;
+  d.y = -xm.y - xp.y - ym.y - yp.y;
+  double2 acc = cmul(d, x[idx]);
+  if (i > 0) acc = cfma(xm, x[idx - g.ny], acc);
+  if (i < g.nx - 1) acc = cfma(xp, x[idx + g.ny], acc);
+  if (j > 0) acc = cfma(ym, x[idx - 1], acc);
+  if (j < g.ny - 1) acc = cfma(yp, x[idx + 1], acc);
+  return acc;
+}
 // y = A x (global stretched 5-point operator), nrhs vectors of nx*ny
 void launch_stencil(const GridDev &g, const double2 *x, double2 *y, cudaStream_t st);
 // r = b - A x

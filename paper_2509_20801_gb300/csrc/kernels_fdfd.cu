@@ -24,19 +24,9 @@ inline int grid_for(int64_t n) {
   return (int)std::min<int64_t>((n + TPB - 1) / TPB, 152 * 16);
 }
 
-// row idx = i * ny + j of the operator applied to x
 __device__ __forceinline__ double2 apply_row_ij(const GridDev &g, const double2 *__restrict__ x, int64_t idx, int i,
                                                 int j) {
-  const double2 xm = g.cxm[i], xp = g.cxp[i], ym = g.cym[j], yp = g.cyp[j];
-  double2 d;
-  d.x = g.k0sq * g.eps[idx] - xm.x - xp.x - ym.x - yp.x;
-  d.y = -xm.y - xp.y - ym.y - yp.y;
-  double2 acc = cmul(d, x[idx]);
-  if (i > 0) acc = cfma(xm, x[idx - g.ny], acc);
-  if (i < g.nx - 1) acc = cfma(xp, x[idx + g.ny], acc);
-  if (j > 0) acc = cfma(ym, x[idx - 1], acc);
-  if (j < g.ny - 1) acc = cfma(yp, x[idx + 1], acc);
-  return acc;
+  return grid_row(g, x, idx, i, j);
 }
 
 __device__ __forceinline__ double2 apply_row(const GridDev &g, const double2 *__restrict__ x, int64_t idx) {

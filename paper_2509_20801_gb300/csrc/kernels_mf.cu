@@ -679,12 +679,10 @@ __device__ __forceinline__ void seg_dot(const C *__restrict__ M, int64_t ld, int
 // the children's update vectors (inverse extend-add maps); w_p goes to the
 // pivot slots of wloc (kept for the way down) and w_b is the initial value
 // of the front's update vector.
-template <typename R>
-__global__ void __launch_bounds__(256) mf_up_gather(MfArgs a, int f0, int nf, int nrhs, int64_t ldt) {
+// one warp, front f0 + fi (the body of mf_up_gather)
+template <typename R> __device__ __forceinline__ void up_gather_front(const MfArgs &a, int f0, int fi, int nrhs,
+                                                                      int64_t ldt, int lane) {
   using C = typename CT<R>::T;
-  const int lane = threadIdx.x & 31;
-  const int fi = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (fi >= nf) return;
   const FrontDev f = a.fronts[f0 + fi];
   const int p = f.p, b = f.b, n = p + b;
   const int64_t voff = a.strips[f.strip].vec_off;
@@ -724,19 +722,26 @@ __global__ void __launch_bounds__(256) mf_up_gather(MfArgs a, int f0, int nf, in
   }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) mf_up_gather(MfArgs a, int f0, int nf, int nrhs, int64_t ldt) {
+  const int fi = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (fi >= nf) return;
+  up_gather_front<R>(a, f0, fi, nrhs, ldt, threadIdx.x & 31);
+}
+
 // Going up, part 2: lane = border row r;
 // u[r] = w_b[r] + sum_j (-G21)(r, j) w_p[j]  (w_b already in u).
 // NR right-hand sides share every matrix load (NR > 1 requires split == 1).
+// one (virtual) block of the upward products: the items of block vb
 template <typename R, int ROWS, int NR>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_up(MfArgs a, const int2 *__restrict__ items,
-                                                                     int nitems, int split, int nrhs, int64_t ldt) {
+__device__ __forceinline__ void up_block(const MfArgs &a, const int2 *__restrict__ items, int nitems, int split,
+                                         int nrhs, int64_t ldt, int vb, typename CT<R>::T *part) {
   using C = typename CT<R>::T;
   constexpr int GROUPS = 256 / ROWS;
-  __shared__ C part[MF_MAXSEG * 256 / 2];
   const int g = threadIdx.x / ROWS, lane = threadIdx.x % ROWS;
   const int ipc = GROUPS / split;
   const int il = g / split, sidx = g - il * split;
-  const int it = blockIdx.x * ipc + il;
+  const int it = vb * ipc + il;
   const bool active = it < nitems;
   const unsigned mask = ROWS == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
   int p = 0, b = 0, r = 0, seg0 = 0, seg1 = 0, nseg = 0;
@@ -802,17 +807,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_up(MfArgs a, c
 
 // Coming down: lane = pivot row r;
 // x[r] = sum_{c<p} Finv(r, c) w_p[c] - sum_{c>=p} H12(r, c) x_b[c].
+// one (virtual) block of the downward products: the items of block vb
 template <typename R, int ROWS, int NR>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_down(MfArgs a, const int2 *__restrict__ items,
-                                                                       int nitems, int split, int nrhs,
-                                                                       int64_t ldt) {
+__device__ __forceinline__ void down_block(const MfArgs &a, const int2 *__restrict__ items, int nitems, int split,
+                                           int nrhs, int64_t ldt, int vb, typename CT<R>::T *part) {
   using C = typename CT<R>::T;
   constexpr int GROUPS = 256 / ROWS;
-  __shared__ C part[MF_MAXSEG * 256 / 2];
   const int g = threadIdx.x / ROWS, lane = threadIdx.x % ROWS;
   const int ipc = GROUPS / split;
   const int il = g / split, sidx = g - il * split;
-  const int it = blockIdx.x * ipc + il;
+  const int it = vb * ipc + il;
   const bool active = it < nitems;
   const unsigned mask = ROWS == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
   int p = 0, n = 0, r = 0, seg0 = 0, seg1 = 0, nseg = 0;
@@ -871,6 +875,130 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_down(MfArgs a,
         if (q0 + q < nrhs) tv[(q0 + q) * ldt + voff + nodes[r]] = total[q];
     }
   }
+}
+
+template <typename R, int ROWS, int NR>
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_up(MfArgs a, const int2 *__restrict__ items,
+                                                                     int nitems, int split, int nrhs, int64_t ldt) {
+  __shared__ typename CT<R>::T part[MF_MAXSEG * 256 / 2];
+  up_block<R, ROWS, NR>(a, items, nitems, split, nrhs, ldt, blockIdx.x, part);
+}
+
+template <typename R, int ROWS, int NR>
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_down(MfArgs a, const int2 *__restrict__ items,
+                                                                       int nitems, int split, int nrhs,
+                                                                       int64_t ldt) {
+  __shared__ typename CT<R>::T part[MF_MAXSEG * 256 / 2];
+  down_block<R, ROWS, NR>(a, items, nitems, split, nrhs, ldt, blockIdx.x, part);
+}
+
+// ------------------------------------------- persistent one-strip sweep
+// Grid-wide barrier of a cooperative launch: bar[0] counts arrivals, bar[1]
+// is the generation.  A block that polls more than `limit` times sets bit 0
+// of *flag and gives up; a block that sees the flag gives up too.  Returns
+// false (uniformly across the block) if the barrier was abandoned.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *flag, long long limit) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *vb = bar;
+    volatile int *vf = flag;
+    ok = 1;
+    const unsigned gen = vb[1];
+    __threadfence();
+    if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicAdd(&bar[1], 1u);
+    } else {
+      long long it = 0;
+      while (vb[1] == gen) {
+        if (++it > limit || (*vf & 1)) {
+          atomicOr(flag, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename R, int ROWS>
+__device__ __forceinline__ void up_items(const MfArgs &a, const StripLevel &l, int64_t ldt,
+                                         typename CT<R>::T *part) {
+  const int ipc = (256 / ROWS) / l.split_up;
+  const int nvb = (l.up_n + ipc - 1) / ipc;
+  for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x)
+    up_block<R, ROWS, 1>(a, a.items_sweep + l.up_first, l.up_n, l.split_up, 1, ldt, vb, part);
+}
+
+template <typename R, int ROWS>
+__device__ __forceinline__ void down_items(const MfArgs &a, const StripLevel &l, int64_t ldt,
+                                           typename CT<R>::T *part) {
+  const int ipc = (256 / ROWS) / l.split_down;
+  const int nvb = (l.down_n + ipc - 1) / ipc;
+  for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x)
+    down_block<R, ROWS, 1>(a, a.items_sweep + l.down_first, l.down_n, l.split_down, 1, ldt, vb, part);
+}
+
+// The launches of one strip's solve in the sequential orders (residual
+// restriction, per level the gather and the upward products, per level the
+// downward products, the add-back) as one launch: the same device code, the
+// launch boundaries replaced by grid barriers.
+template <typename R>
+__global__ void __launch_bounds__(256, 2)
+    mf_strip_sweep(MfArgs a, const void *ub0, const void *ub1, GridDev g, StripDev s, const StripLevel *lv,
+                   int depth, const double2 *__restrict__ v, double2 *__restrict__ z, unsigned *bar, int *flag,
+                   long long limit, int64_t ldt) {
+  using C = typename CT<R>::T;
+  __shared__ C part[MF_MAXSEG * 256 / 2];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int Hl = s.y1 - s.y0;
+  const int64_t nl = (int64_t)(s.x1 - s.x0) * Hl;
+  C *t = reinterpret_cast<C *>(a.tloc) + s.vec_off;
+  // t = R_s^I (v - A z): the strip's owned columns, zero elsewhere
+  {
+    const int64_t lo = (int64_t)(s.c0 - s.x0) * g.ny, hi = (int64_t)(s.c1 - s.x0) * g.ny;
+    const int64_t g0 = (int64_t)s.x0 * g.ny;
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += stride) {
+      C val = czero<C>();
+      if (l >= lo && l < hi) {
+        const int64_t gi = g0 + l;
+        const int i = (int)(gi / g.ny), j = (int)(gi - (int64_t)i * g.ny);
+        val = to_c(csub(v[gi], grid_row(g, z, gi, i, j)), C());
+      }
+      t[l] = val;
+    }
+  }
+  if (!grid_barrier(bar, flag, limit)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int L = depth - 1; L >= 0; --L) {
+    const StripLevel l = lv[L];
+    if (l.nf == 0) continue;
+    MfArgs al = a;
+    al.ub_cur = const_cast<void *>(L & 1 ? ub1 : ub0);
+    al.ub_child = L & 1 ? ub0 : ub1;
+    for (int fi = blockIdx.x * 8 + warp; fi < l.nf; fi += gridDim.x * 8) up_gather_front<R>(al, l.f0, fi, 1, ldt, lane);
+    if (!grid_barrier(bar, flag, limit)) return;
+    if (l.rows_up == 16) up_items<R, 16>(al, l, ldt, part);
+    else up_items<R, 32>(al, l, ldt, part);
+    if (!grid_barrier(bar, flag, limit)) return;
+  }
+  for (int L = 0; L < depth; ++L) {
+    const StripLevel l = lv[L];
+    if (l.down_n == 0) continue;
+    if (l.rows_down == 16) down_items<R, 16>(a, l, ldt, part);
+    else down_items<R, 32>(a, l, ldt, part);
+    if (!grid_barrier(bar, flag, limit)) return;
+  }
+  // z += E_s t
+  double2 *zs = z + (int64_t)s.x0 * g.ny;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += stride)
+    zs[l] = cadd(zs[l], to_d(t[l]));
 }
 
 // ------------------------------------------------------------ launchers
@@ -982,6 +1110,53 @@ void mf_down_level(const MfArgs &a, const int2 *items, int nitems, int rows, int
 #undef STDD_DOWN
   count_launch();
 }
+
+static int g_sweep_grid[2] = {0, 0};
+
+template <typename R> static int sweep_grid_for() {
+  int &G = g_sweep_grid[sizeof(R) == 8 ? 1 : 0];
+  if (G == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mf_strip_sweep<R>, 256, 0);
+    G = std::max(1, sms * std::max(1, per));
+  }
+  return G;
+}
+
+int mf_strip_sweep_grid() {
+  sweep_grid_for<float>();
+  return sweep_grid_for<double>();
+}
+
+template <typename R>
+cudaError_t mf_strip_sweep_launch(const MfArgs &a, const void *ub0, const void *ub1, const GridDev &g,
+                                  const StripDev &s, const StripLevel *lv_dev, int depth, const double2 *v,
+                                  double2 *z, unsigned *bar, int *sweep_flag, long long wait_limit,
+                                  cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)sweep_grid_for<R>());
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident, or the launch fails
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int64_t ldt = 0;   // one right-hand side
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, mf_strip_sweep<R>, a, ub0, ub1, g, s, lv_dev, depth, v, z, bar, sweep_flag,
+                            wait_limit, ldt);
+}
+
+template cudaError_t mf_strip_sweep_launch<double>(const MfArgs &, const void *, const void *, const GridDev &,
+                                                   const StripDev &, const StripLevel *, int, const double2 *,
+                                                   double2 *, unsigned *, int *, long long, cudaStream_t);
+template cudaError_t mf_strip_sweep_launch<float>(const MfArgs &, const void *, const void *, const GridDev &,
+                                                  const StripDev &, const StripLevel *, int, const double2 *,
+                                                  double2 *, unsigned *, int *, long long, cudaStream_t);
 
 __global__ void k_factor_begin(int *flag, unsigned long long *n_raised, double *min_pivot) {
   *flag = 0;

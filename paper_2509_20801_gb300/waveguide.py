@@ -36,7 +36,7 @@ from . import binding as _b
 
 PRECISIONS = {"fp64": _b.STDD_PREC_FP64, "c64": _b.STDD_PREC_C64, "bf16": _b.STDD_PREC_C64_BF16,
               "fp16": _b.STDD_PREC_C64_FP16}
-ORDERS = {"additive": 0, "multiplicative": 1, "red-black": 2}
+ORDERS = {"additive": 0, "multiplicative": 1, "red-black": 2, "forward": 3}
 
 
 def run(nx=8192, ny=2048, nsub=32, precisions=("fp64", "c64", "fp16"), order="multiplicative", rtol=1e-8,

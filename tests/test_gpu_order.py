@@ -42,7 +42,7 @@ def strip6():
     return w, P, DDM.from_workload(w, P)
 
 
-@pytest.mark.parametrize("order,graphs", [(1, 1), (1, 0), (2, 1), (2, 0)])
+@pytest.mark.parametrize("order,graphs", [(1, 1), (1, 0), (2, 1), (2, 0), (3, 1), (3, 0)])
 def test_multiplicative_preconditioner_matches_oracle(rnd, order, graphs):
     from paper_2509_20801_gb300 import STDD_OPT_GRAPHS, stdd_apply_preconditioner, stdd_set_option
     w, P, D = rnd
@@ -52,7 +52,7 @@ def test_multiplicative_preconditioner_matches_oracle(rnd, order, graphs):
     v = W.random_vector(P.n, seed=6)[0]
     z = torch.empty(P.n, dtype=torch.complex128, device=DEV)
     stdd_apply_preconditioner(s.ctx, torch.from_numpy(v).to(DEV), z)
-    ref = D.apply_Minv_multiplicative(v, order=None if order == 1 else "red-black")
+    ref = D.apply_Minv_multiplicative(v, order={1: None, 2: "red-black", 3: list(range(w.nsub))}[order])
     assert _rel(z.cpu().numpy(), ref) < 1e-10
     s.close()
 
@@ -80,7 +80,7 @@ def test_fgmres_with_multiplicative_order(strip6, precision):
     b = torch.from_numpy(w.b).to(DEV)
     ref = P.solve(w.b[0].ravel())
     its = {}
-    for order in (0, 1, 2):
+    for order in (0, 1, 2, 3):
         s = _solver(w, precision=precision, order=order)
         s.factor()
         s.set_sources(b)
@@ -96,3 +96,50 @@ def test_fgmres_with_multiplicative_order(strip6, precision):
     if precision == 0:
         assert abs(its[1] - (len(oh) - 1)) <= 1
     assert its[1] < its[2] < its[0]
+    # the forward sweep alone: fewer iterations than the additive order, at
+    # most twice the symmetric sweep's (each application does half its work)
+    assert its[3] < its[0] and its[3] <= 2 * its[1] + 1
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_persistent_sweeps_equal_per_level_launches(rnd, order):
+    """The persistent one-strip sweep (one cooperative launch per strip solve,
+    levels separated by grid barriers) runs the same device code as the
+    per-level launches: bitwise equal results, with and without graphs."""
+    from paper_2509_20801_gb300 import (STDD_OPT_GRAPHS, STDD_OPT_PERSISTENT, stdd_apply_preconditioner,
+                                        stdd_set_option)
+    w, P, D = rnd
+    v = torch.from_numpy(W.random_vector(P.n, seed=15)[0]).to(DEV)
+    outs = []
+    for persistent, graphs in ((1, 1), (0, 1), (1, 0)):
+        s = _solver(w, order=order)
+        stdd_set_option(s.ctx, STDD_OPT_PERSISTENT, persistent)
+        stdd_set_option(s.ctx, STDD_OPT_GRAPHS, graphs)
+        s.factor()
+        z = torch.empty_like(v)
+        for _ in range(2):
+            stdd_apply_preconditioner(s.ctx, v, z)
+        outs.append(z.cpu().numpy())
+        s.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_persistent_sweep_wait_gives_up_and_recovers(rnd):
+    """A grid-barrier wait that runs out (one poll allowed) makes the
+    application return STDD_ETIMEOUT without faulting; with the default limit
+    the same context then applies the preconditioner correctly."""
+    from paper_2509_20801_gb300 import STDD_OPT_SWEEP_WAIT, StddError, stdd_apply_preconditioner, stdd_set_option
+    w, P, D = rnd
+    s = _solver(w, order=1)
+    s.factor()
+    v_h = W.random_vector(P.n, seed=16)[0]
+    v = torch.from_numpy(v_h).to(DEV)
+    z = torch.empty_like(v)
+    stdd_set_option(s.ctx, STDD_OPT_SWEEP_WAIT, 1)
+    with pytest.raises(StddError) as e:
+        stdd_apply_preconditioner(s.ctx, v, z)
+    assert e.value.status == 8
+    stdd_set_option(s.ctx, STDD_OPT_SWEEP_WAIT, 0)
+    stdd_apply_preconditioner(s.ctx, v, z)
+    assert _rel(z.cpu().numpy(), D.apply_Minv_multiplicative(v_h)) < 1e-10
+    s.close()
