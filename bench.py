@@ -110,6 +110,8 @@ def parse():
                     help="partial pivoting within the fronts for the complex64 forms (default 1 on the "
                          "waveguide, else 0)")
     ap.add_argument("--maxit", type=int, default=2000, help="FGMRES iteration limit per right-hand side")
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="1: replay captured CUDA graphs of the factorization and of M^-1")
     ap.add_argument("--persistent", type=int, default=1, choices=[0, 1],
                     help="1: one persistent launch per strip solve in the sequential orders")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision and other-order runs")
@@ -531,6 +533,7 @@ def run_ours(args, rank, world, local_rank):
         S.stdd_set_option(sv.ctx, S.STDD_OPT_BAND, band_for(p, order, band))
         piv, sp = pivots_for(p)
         S.stdd_set_option(sv.ctx, S.STDD_OPT_PERSISTENT, args.persistent)
+        S.stdd_set_option(sv.ctx, S.STDD_OPT_GRAPHS, args.graphs)
         S.stdd_set_option(sv.ctx, S.STDD_OPT_PIVOTING, piv)
         S.stdd_set_option(sv.ctx, S.STDD_OPT_STATIC_PIVOT, sp)
         return sv

@@ -345,7 +345,16 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     the elimination's growth, harmless in FP64, can ruin
  *                     complex64 factors (high-index guided-wave geometries).
  *                     Invalidates the factors. */
-/*   STDD_OPT_PERSISTENT (default 1): in the sequential orders (1 and 3,
+/*   STDD_OPT_UPDATE_TILE (default 0): tile edge of the blocked front
+ *                     update.  0: chosen per tree level by the autotuner (the
+ *                     first factorization of a level shape times the
+ *                     factorization with 64 x 64 and with 32 x 32 tiles and
+ *                     keeps the faster per level; cached for the process);
+ *                     64 or 32: that shape on every level.  Every entry sums
+ *                     its products in the same order on either shape, so
+ *                     results do not change.  (With STDD_OPT_AUTOTUNE 0 and
+ *                     this option 0 the shape is 64.)
+ *   STDD_OPT_PERSISTENT (default 1): in the sequential orders (1 and 3,
  *                     one right-hand side at a time) each strip's solve --
  *                     residual restriction, the upward and the downward
  *                     sweep over all tree levels, the add-back -- runs as
@@ -379,7 +388,8 @@ enum {
   STDD_OPT_STATIC_PIVOT = 6,
   STDD_OPT_PIVOTING = 7,
   STDD_OPT_PERSISTENT = 8,
-  STDD_OPT_SWEEP_WAIT = 9
+  STDD_OPT_SWEEP_WAIT = 9,
+  STDD_OPT_UPDATE_TILE = 10
 };
 stdd_status stdd_set_option(stdd_ctx *ctx, int option, int value);
 stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);

@@ -505,6 +505,9 @@ struct stdd_ctx {
     factor_graph_key.clear();
   }
   template <typename R> void factor_t();
+  template <typename R> void tune_update_tiles();
+  int forced_tile = 0;   // STDD_OPT_UPDATE_TILE: 0 = tuned, else 64 or 32 for every level
+  void factor_prepare();
   template <typename R> void solve_levels(int nrhs_);
   template <typename R> void solve_range_levels(int j0, int j1, int nrhs_);
   template <typename R> void enqueue_minv_multiplicative(const std::vector<const double2 *> &vs,
@@ -639,6 +642,12 @@ void stdd_ctx::factor() {
   }
   upload_local_couplings();
   CK(cudaStreamSynchronize(stream));
+  if (autotune_on || forced_tile) {
+    if (prec == STDD_PREC_FP64) tune_update_tiles<double>();
+    else tune_update_tiles<float>();
+  } else {
+    for (auto &li : levels) li.upd_tile = 64;
+  }
   if (prec == STDD_PREC_FP64) factor_t<double>();
   else factor_t<float>();
   factored = true;
@@ -752,7 +761,7 @@ void stdd_ctx::build_structure() {
   std::vector<std::vector<int>> inst(nsub);
   for (int k = 0; k < nsub; ++k) inst[k].assign(shape_of(strips[k]).fronts.size(), -1);
   std::vector<FrontDev> fr;
-  levels.assign(depth, LevelInfo{0, 0, 0, 0, 0, 1 << 30, 0, 0, 0, 0, 32, 32, 1, 1, 1, 1});
+  levels.assign(depth, LevelInfo{0, 0, 0, 0, 0, 1 << 30, 0, 0, 0, 0, 32, 32, 1, 1, 1, 1, 64, 0});
   perm.clear();
   for (int k = 0; k < nsub; k += 2) perm.push_back(k);
   for (int k = 1; k < nsub; k += 2) perm.push_back(k);
@@ -998,7 +1007,7 @@ template <typename R> void stdd_ctx::autotune() {
   CK(cudaGetLastError());
 }
 
-template <typename R> void stdd_ctx::factor_t() {
+void stdd_ctx::factor_prepare() {
   if (pivoting) {
     d_pcol.alloc((size_t)std::max<int64_t>(1, nloc) * sizeof(int));
     d_panel.alloc((size_t)std::max<int64_t>(1, panel_need) * elem());
@@ -1010,6 +1019,60 @@ template <typename R> void stdd_ctx::factor_t() {
     CK(stdd::tc_setup_attributes());
     attrs = true;
   }
+}
+
+// Front-update tile shape per level, chosen by timing: the factorization is
+// run level by level once with 64 x 64 and once with 32 x 32 update tiles
+// (the other kernels of a level are the same in both), and each level keeps
+// the faster.  Both shapes sum every entry's products in the same order, so
+// the choice changes no result.  Cached per device and level shape for every
+// context of the process (the first factorization of a new shape pays for
+// two extra ones).
+template <typename R> void stdd_ctx::tune_update_tiles() {
+  if (tc_fmt() >= 0) return;
+  if (forced_tile) {
+    for (auto &li : levels) li.upd_tile = forced_tile;
+    return;
+  }
+  factor_prepare();
+  std::vector<int> todo;
+  std::vector<std::vector<int64_t>> keys(depth);
+  for (int L = 0; L < depth; ++L) {
+    const LevelInfo &li = levels[L];
+    if (li.max_n <= stdd::MF_SMALL) continue;
+    keys[L] = {device, (int64_t)sizeof(R), 7, li.nf, li.max_p, li.max_b, li.max_n, li.min_n};
+    std::lock_guard<std::mutex> lk(tuned_mutex());
+    auto hit = tuned().find(keys[L]);
+    if (hit != tuned().end()) levels[L].upd_tile = hit->second;
+    else todo.push_back(L);
+  }
+  if (todo.empty()) return;
+  std::vector<cudaEvent_t> ev(2 * depth);
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  std::vector<float> t[2];
+  const int tiles[2] = {64, 32};
+  for (int v = 0; v < 2; ++v) {
+    for (int L : todo) levels[L].upd_tile = tiles[v];
+    stdd::mf_factor_begin(mf_args(0, false), stream);
+    for (int L = depth - 1; L >= 0; --L) {
+      CK(cudaEventRecord(ev[2 * L], stream));
+      stdd::mf_factor_level<R>(mf_args(L & 1, false), levels[L], L, stream, nullptr, -1);
+      CK(cudaEventRecord(ev[2 * L + 1], stream));
+    }
+    CK(cudaStreamSynchronize(stream));
+    t[v].assign(depth, 0.f);
+    for (int L : todo) CK(cudaEventElapsedTime(&t[v][L], ev[2 * L], ev[2 * L + 1]));
+  }
+  for (auto &e : ev) CK(cudaEventDestroy(e));
+  std::lock_guard<std::mutex> lk(tuned_mutex());
+  for (int L : todo) {
+    levels[L].upd_tile = t[1][L] < t[0][L] ? 32 : 64;
+    tuned()[keys[L]] = levels[L].upd_tile;
+  }
+}
+
+template <typename R> void stdd_ctx::factor_t() {
+  factor_prepare();
   const int span = pbegin(PH_FACTOR);
   if (use_graphs && prof < 2) {
     // one replayed graph for all levels (captured again whenever a pointer
@@ -2290,6 +2353,11 @@ stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
         break;
       case STDD_OPT_BAND:
         c->use_band = value != 0;
+        break;
+      case STDD_OPT_UPDATE_TILE:
+        if (value != 0 && value != 32 && value != 64) throw ArgError("update tile must be 0 (tuned), 32 or 64");
+        c->forced_tile = value;
+        c->invalidate_factors();
         break;
       case STDD_OPT_PERSISTENT:
         if (value != (int)c->persistent) {

@@ -54,6 +54,8 @@ struct LevelInfo {
   int rows_up, rows_down;     // rows per item: 16 or 32
   int split_up, split_down;   // row groups sharing one item's columns (1..8)
   int split_up1, split_down1; // the same for launches over one strip's fronts (sequential orders)
+  int upd_tile;               // blocked-update tile edge of the level: 64 or 32 (chosen by timing)
+  int pad_;
 };
 
 // Optional per-launch observer (phase profiling): kind is one of the K_*

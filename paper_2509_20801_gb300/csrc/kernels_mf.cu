@@ -289,18 +289,32 @@ __global__ void __launch_bounds__(128) mf_gj_small(MfArgs a, int f0, int nf, int
       }
       front_sync<TPF>();
     }
-    const C d0 = F[k * n + k];
-    bool raised;
-    const C d = floor_pivot(a, d0, raised);
-    const C inv = crecip(d);
+    // the pivot's reciprocal and its statistics, by one thread of the front
+    // (FP64 division and square root are long sequences on the FP64 pipe;
+    // every other thread takes the reciprocal from it)
+    C inv = czero<C>();
+    if (t == 0) {
+      const C d0 = F[k * n + k];
+      bool raised;
+      inv = crecip(floor_pivot(a, d0, raised));
+      const double ad = sqrt((double)cabs2(d0));
+      bad |= !(ad > 0.0) || !cfinite(d0);
+      dmin = fmin(dmin, ad);
+      if (raised) atomicAdd(a.n_raised, 1ull);
+    }
+    if (TPF == 32) {
+      inv.x = __shfl_sync(0xffffffffu, inv.x, 0);
+      inv.y = __shfl_sync(0xffffffffu, inv.y, 0);
+    } else {
+      __shared__ C inv_s;
+      if (t == 0) inv_s = inv;
+      __syncthreads();
+      inv = inv_s;
+    }
     for (int j = t; j < n; j += TPF) {
       rowk[j] = cmul(F[j * n + k], inv);
       colk[j] = F[k * n + j];
     }
-    const double ad = sqrt((double)cabs2(d0));
-    bad |= !(ad > 0.0) || !cfinite(d0);
-    dmin = fmin(dmin, ad);
-    if (raised && t == 0) atomicAdd(a.n_raised, 1ull);
     front_sync<TPF>();
     for (int idx = t; idx < n * n; idx += TPF) {
       const int c = idx / n, r = idx - c * n;
@@ -424,19 +438,24 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_diag(MfArgs a, int f0,
   __syncthreads();
   double dmin = INFINITY;
   bool bad = false;
+  __shared__ C inv_s;
   for (int q = 0; q < nbk; ++q) {
-    const C d0 = D[q][q];
-    bool raised;
-    const C d = floor_pivot(a, d0, raised);
-    const C inv = crecip(d);
+    // reciprocal and statistics of the pivot by one thread (see mf_gj_small)
+    if (tid == 0) {
+      const C d0 = D[q][q];
+      bool raised;
+      inv_s = crecip(floor_pivot(a, d0, raised));
+      const double ad = sqrt((double)cabs2(d0));
+      bad |= !(ad > 0.0) || !cfinite(d0);
+      dmin = fmin(dmin, ad);
+      if (raised) atomicAdd(a.n_raised, 1ull);
+    }
+    __syncthreads();
+    const C inv = inv_s;
     for (int j = tid; j < nbk; j += blockDim.x) {
       rowk[j] = cmul(D[q][j], inv);
       colk[j] = D[j][q];
     }
-    const double ad = sqrt((double)cabs2(d0));
-    bad |= !(ad > 0.0) || !cfinite(d0);
-    dmin = fmin(dmin, ad);
-    if (raised && tid == 0) atomicAdd(a.n_raised, 1ull);
     __syncthreads();
     for (int idx = tid; idx < nbk * nbk; idx += blockDim.x) {
       const int i = idx % nbk, j = idx / nbk;
@@ -540,6 +559,68 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_row(MfArgs a, int f0, 
   for (int idx = tid; idx < nbk * ncol; idx += blockDim.x) {
     const int i = idx % nbk, cc = idx / nbk;
     fac[fo + (int64_t)unband(cbase + cc, k, nbk) * p + k + i] = T[cc][i];
+  }
+}
+
+// The same update on 32 x 32 tiles (64 threads as 8 x 8, thread (tx, ty)
+// owns rows ty + 8 i and columns tx + 8 j): more, smaller blocks for levels
+// whose fronts are too small to fill 64 x 64 tiles.  Every entry accumulates
+// its K products in the same order as on 64 x 64 tiles, so the autotuner's
+// choice between the two never changes a result.
+template <typename R>
+__global__ void __launch_bounds__(64) mf_gj_update32(MfArgs a, int f0, int k) {
+  using C = typename CT<R>::T;
+  constexpr int NB = MF_NB, TM = 32;
+  __shared__ C As[TM][NB + 1];
+  __shared__ C Bs[NB][TM + 1];
+  const FrontDev f = a.fronts[f0 + blockIdx.x];
+  const int p = f.p, n = p + f.b;
+  if (n <= MF_SMALL || k >= p) return;
+  const int nbk = min(NB, p - k);
+  const int m = n - nbk;
+  const int nt = (m + TM - 1) / TM;
+  if ((int)blockIdx.y >= nt * nt) return;
+  const int i0 = (blockIdx.y % nt) * TM, j0 = (blockIdx.y / nt) * TM;
+  const C *fac = reinterpret_cast<const C *>(a.fac);
+  const int64_t fo = f.fac_off;
+  const int tid = threadIdx.x, tx = tid % 8, ty = tid / 8;
+  for (int idx = tid; idx < TM * nbk; idx += 64) {
+    const int rr = idx % TM, j = idx / TM, ri = i0 + rr;
+    As[rr][j] = ri < m ? ld_elem<C>(a, f, unband(ri, k, nbk), k + j) : czero<C>();
+  }
+  for (int idx = tid; idx < TM * nbk; idx += 64) {
+    const int j = idx % nbk, cc = idx / nbk, ci = j0 + cc;
+    Bs[j][cc] = ci < m ? fac[fo + (int64_t)unband(ci, k, nbk) * p + k + j] : czero<C>();
+  }
+  __syncthreads();
+  C acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = czero<C>();
+  for (int kk = 0; kk < nbk; ++kk) {
+    C av[4], bv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) av[i] = As[ty + 8 * i][kk];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 8 * j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = cfma(av[i], bv[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int ri = i0 + ty + 8 * i;
+    if (ri >= m) continue;
+    const int r = unband(ri, k, nbk);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int ci = j0 + tx + 8 * j;
+      if (ci >= m) continue;
+      const int c = unband(ci, k, nbk);
+      st_elem<C>(a, f, r, c, cadd(ld_elem<C>(a, f, r, c), acc[i][j]));
+    }
   }
 }
 
@@ -1059,8 +1140,14 @@ void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_
       mf_gj_diag<R><<<L.nf, MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
       mf_gj_col<R><<<dim3(L.nf, tiles), MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
       if (hook) hook->before(K_UPDATE, level, k);
-      if (tc_fmt >= 0 && sizeof(R) == 4) mf_tc_update_launch(a, L, k, tc_fmt, st);
-      else mf_gj_update<R><<<dim3(L.nf, nt * nt), 256, gemm_smem<R>(), st>>>(a, L.f0, k);
+      if (tc_fmt >= 0 && sizeof(R) == 4) {
+        mf_tc_update_launch(a, L, k, tc_fmt, st);
+      } else if (L.upd_tile == 32) {
+        const int nt32 = std::max(1, (m + 31) / 32);
+        mf_gj_update32<R><<<dim3(L.nf, nt32 * nt32), 64, 0, st>>>(a, L.f0, k);
+      } else {
+        mf_gj_update<R><<<dim3(L.nf, nt * nt), 256, gemm_smem<R>(), st>>>(a, L.f0, k);
+      }
       if (hook) hook->after(K_UPDATE, level, k);
       mf_gj_row<R><<<dim3(L.nf, tiles), MF_PANEL_THREADS, row_smem<R>(), st>>>(a, L.f0, k);
       count_launch(4);

@@ -363,3 +363,27 @@ def test_factorization_graph_follows_configuration_changes(rnd):
             assert _rel(z.cpu().numpy(), D2.apply_Minv(v_h)) < 1e-10, (wl, piv)
     s.close()
     ref.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_update_tile_shapes_give_identical_factors(cyl, precision):
+    """The front update on 64 x 64 and on 32 x 32 tiles (and whatever the
+    autotuner picks per level) sums every entry's products in the same order:
+    M^-1 bitwise equal, and equal to the oracle's (FP64)."""
+    from paper_2509_20801_gb300 import STDD_OPT_LEAF, STDD_OPT_UPDATE_TILE, stdd_apply_preconditioner, stdd_set_option
+    w, P, D = cyl
+    v_h = W.random_vector(P.n, seed=17)[0]
+    v = torch.from_numpy(v_h).to(DEV)
+    outs = []
+    for tile in (64, 32, 0):
+        s = _solver(w, precision=precision)
+        stdd_set_option(s.ctx, STDD_OPT_LEAF, 64)       # more blocked (n > 64) fronts
+        stdd_set_option(s.ctx, STDD_OPT_UPDATE_TILE, tile)
+        s.factor()
+        z = torch.empty_like(v)
+        stdd_apply_preconditioner(s.ctx, v, z)
+        outs.append(z.cpu().numpy())
+        s.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    if precision == 0:
+        assert _rel(outs[0], D.apply_Minv(v_h)) < 1e-10
