@@ -112,8 +112,8 @@ def parse():
     ap.add_argument("--maxit", type=int, default=2000, help="FGMRES iteration limit per right-hand side")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="1: replay captured CUDA graphs of the factorization and of M^-1")
-    ap.add_argument("--persistent", type=int, default=1, choices=[0, 1],
-                    help="1: one persistent launch per strip solve in the sequential orders")
+    ap.add_argument("--persistent", type=int, default=2, choices=[0, 1, 2],
+                    help="k > 0: one persistent launch (k blocks per SM) per strip solve in the sequential orders")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision and other-order runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")

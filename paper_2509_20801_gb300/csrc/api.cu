@@ -532,7 +532,7 @@ struct stdd_ctx {
   void ensure_krylov(int m);
   // persistent one-strip sweeps of the sequential orders (STDD_OPT_PERSISTENT):
   // per strip position and level the strip's share of the sweep
-  bool persistent = true;
+  int persistent = 2;                 // 0: per-level launches; k: persistent sweeps, k blocks per SM
   long long sweep_wait = 1ll << 22;   // polls of a grid-barrier wait before it gives up
   DBuf d_striplv, d_bar, d_sweep_flag;
   int sweep_flag_h = 0;
@@ -1225,7 +1225,8 @@ void stdd_ctx::enqueue_minv_multiplicative(const std::vector<const double2 *> &v
       CK(cudaMemsetAsync(d_bar.p, 0, 2 * sizeof(unsigned), stream));
       CK(stdd::mf_strip_sweep_launch<R>(a, d_ub[0].p, d_ub[1].p, g, strips_host[perm[j]],
                                         d_striplv.as<stdd::StripLevel>() + (size_t)j * depth, depth, vs[0], zs[0],
-                                        d_bar.as<unsigned>(), d_sweep_flag.as<int>(), sweep_wait, stream));
+                                        d_bar.as<unsigned>(), d_sweep_flag.as<int>(), sweep_wait, persistent,
+                                        stream));
     }
     return;
   }
@@ -2360,8 +2361,9 @@ stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
         c->invalidate_factors();
         break;
       case STDD_OPT_PERSISTENT:
-        if (value != (int)c->persistent) {
-          c->persistent = value != 0;
+        if (value < 0 || value > 8) throw ArgError("persistent must be 0 (off) or 1..8 blocks per SM");
+        if (value != c->persistent) {
+          c->persistent = value;
           c->clear_graphs();
         }
         break;

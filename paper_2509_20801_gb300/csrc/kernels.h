@@ -101,7 +101,7 @@ template <typename R>
 cudaError_t mf_strip_sweep_launch(const MfArgs &a, const void *ub0, const void *ub1, const GridDev &g,
                                   const StripDev &s, const StripLevel *lv_dev, int depth, const double2 *v,
                                   double2 *z, unsigned *bar, int *sweep_flag, long long wait_limit,
-                                  cudaStream_t st);
+                                  int blocks_per_sm, cudaStream_t st);
 int mf_strip_sweep_grid();   // blocks of the persistent sweep (co-resident); call outside stream capture
 template <typename R>
 void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,

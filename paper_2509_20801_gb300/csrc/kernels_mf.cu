@@ -1198,32 +1198,33 @@ void mf_down_level(const MfArgs &a, const int2 *items, int nitems, int rows, int
   count_launch();
 }
 
-static int g_sweep_grid[2] = {0, 0};
+static int g_sweep_sms = 0, g_sweep_per[2] = {0, 0};
 
-template <typename R> static int sweep_grid_for() {
-  int &G = g_sweep_grid[sizeof(R) == 8 ? 1 : 0];
-  if (G == 0) {
-    int dev = 0, sms = 0, per = 0;
+// SMs and co-resident blocks per SM of the persistent sweep (queried once)
+template <typename R> static int sweep_per_sm() {
+  int &per = g_sweep_per[sizeof(R) == 8 ? 1 : 0];
+  if (per == 0) {
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&g_sweep_sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mf_strip_sweep<R>, 256, 0);
-    G = std::max(1, sms * std::max(1, per));
+    per = std::max(1, per);
   }
-  return G;
+  return per;
 }
 
 int mf_strip_sweep_grid() {
-  sweep_grid_for<float>();
-  return sweep_grid_for<double>();
+  sweep_per_sm<float>();
+  return g_sweep_sms * sweep_per_sm<double>();
 }
 
 template <typename R>
 cudaError_t mf_strip_sweep_launch(const MfArgs &a, const void *ub0, const void *ub1, const GridDev &g,
                                   const StripDev &s, const StripLevel *lv_dev, int depth, const double2 *v,
                                   double2 *z, unsigned *bar, int *sweep_flag, long long wait_limit,
-                                  cudaStream_t st) {
+                                  int blocks_per_sm, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)sweep_grid_for<R>());
+  cfg.gridDim = dim3((unsigned)(g_sweep_sms * std::max(1, std::min(blocks_per_sm, sweep_per_sm<R>()))));
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
@@ -1240,10 +1241,10 @@ cudaError_t mf_strip_sweep_launch(const MfArgs &a, const void *ub0, const void *
 
 template cudaError_t mf_strip_sweep_launch<double>(const MfArgs &, const void *, const void *, const GridDev &,
                                                    const StripDev &, const StripLevel *, int, const double2 *,
-                                                   double2 *, unsigned *, int *, long long, cudaStream_t);
+                                                   double2 *, unsigned *, int *, long long, int, cudaStream_t);
 template cudaError_t mf_strip_sweep_launch<float>(const MfArgs &, const void *, const void *, const GridDev &,
                                                   const StripDev &, const StripLevel *, int, const double2 *,
-                                                  double2 *, unsigned *, int *, long long, cudaStream_t);
+                                                  double2 *, unsigned *, int *, long long, int, cudaStream_t);
 
 __global__ void k_factor_begin(int *flag, unsigned long long *n_raised, double *min_pivot) {
   *flag = 0;
