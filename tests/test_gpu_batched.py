@@ -29,3 +29,20 @@ def test_batched_driver_small():
     ref = Problem.from_workload(w).solve(w.b[0].ravel())
     assert np.linalg.norm(x[0].cpu().numpy().ravel() - ref) <= 1e-6 * np.linalg.norm(ref)
     s.close()
+
+
+def test_batched_driver_concurrent_streams_match_sequential():
+    """Geometries in flight at once (own contexts and streams, host threads)
+    converge like the one-after-another run, with the same iteration counts
+    (the same arithmetic per context; the autotuners' launch-shape choices do
+    not change results), and with partial pivoting in the fronts."""
+    from paper_2509_20801_gb300 import batched
+    shapes = ((256, 256), (384, 256), (512, 256))
+    rows_s, summ_s = batched.run(count=4, nrhs=2, precision="c64", shapes=shapes, pivoting=1)
+    rows_c, summ_c = batched.run_concurrent(count=4, nrhs=2, precision="c64", shapes=shapes, pivoting=1,
+                                            workers=3)
+    assert summ_c["all_converged"] and summ_c["max_true_residual"] <= 1e-8
+    assert [r["g"] for r in rows_c] == [r["g"] for r in rows_s]
+    for a, b in zip(rows_s, rows_c):
+        assert (a["nx"], a["ny"], a["iterations_max"]) == (b["nx"], b["ny"], b["iterations_max"])
+        assert abs(a["max_true_residual"] - b["max_true_residual"]) <= 1e-3 * a["max_true_residual"]
