@@ -58,6 +58,14 @@ NCU_TRAFFIC = {
         "sha256": "6decf2105b755b886e043790beeea94ba39fdd151acf1da500560430b40715db",
         "profile": "profiles/ncu_dram_mf_gj_update_fp64_waveguide_2048x512.md",
     },
+    "mf_gj_update_sym<double>": {
+        "bytes_per_executed_flop": 1037.244416e6 / 5.778714624e9,   # 3 launches: DRAM bytes / executed flops
+        "source": "paper_2509_20801_gb300/csrc/kernels_mf.cu",
+        "begin": "// Symmetric form: the update of step k",
+        "end": "// acc[4][4] += A(64 x K) B(K x 64)",
+        "sha256": "b96afa704f14f647b8b569781839b706a974e0464fd95b5c53efd5cfebf4cae2",
+        "profile": "profiles/ncu_dram_mf_gj_update_sym_fp64_waveguide_2048x512.md",
+    },
 }
 
 
@@ -109,6 +117,9 @@ def parse():
     ap.add_argument("--pivoting", type=int, default=None, choices=[0, 1],
                     help="partial pivoting within the fronts for the complex64 forms (default 1 on the "
                          "waveguide, else 0)")
+    ap.add_argument("--symmetric", type=int, default=1, choices=[0, 1],
+                    help="1: factor the symmetric form D A of each strip (lower-triangle front updates) "
+                         "wherever there is no partial pivoting")
     ap.add_argument("--maxit", type=int, default=2000, help="FGMRES iteration limit per right-hand side")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="1: replay captured CUDA graphs of the factorization and of M^-1")
@@ -536,6 +547,7 @@ def run_ours(args, rank, world, local_rank):
         S.stdd_set_option(sv.ctx, S.STDD_OPT_GRAPHS, args.graphs)
         S.stdd_set_option(sv.ctx, S.STDD_OPT_PIVOTING, piv)
         S.stdd_set_option(sv.ctx, S.STDD_OPT_STATIC_PIVOT, sp)
+        S.stdd_set_option(sv.ctx, S.STDD_OPT_SYMMETRIC, args.symmetric)
         return sv
 
     def step(sv):
@@ -664,7 +676,9 @@ def run_ours(args, rank, world, local_rank):
         k.update(frac=k["achieved"] / k["peak"], ms_per_step=ms, launches_per_step=calls,
                  units_per_launch=u, unit_kind=kind, ms_per_launch=t * 1e3)
         if executed is not None:
-            k.update(unit_kind="LU flops (trailing-block updates)", executed_flops_per_launch=executed / calls,
+            lu = "LDL^T flops (one triangle of each trailing-block update)" if name.startswith(
+                "mf_gj_update_sym") else "LU flops (trailing-block updates)"
+            k.update(unit_kind=lu, executed_flops_per_launch=executed / calls,
                      executed_tflops=executed / calls / t / 1e12)
         kernels[name] = k
 
@@ -673,8 +687,9 @@ def run_ours(args, rank, world, local_rank):
         add_kernel(f"mf_gj_update_tc<{args.precision}>", kprof["update_ms"], kprof["update_calls"],
                    kprof["update_flops"], "tensor", kprof["update_flops_executed"])
     else:
-        add_kernel(f"mf_gj_update<{tname}>", kprof["update_ms"], kprof["update_calls"], kprof["update_flops"],
-                   "flops", kprof["update_flops_executed"])
+        sym = args.symmetric and not pivots_for(prec)[0]
+        add_kernel(f"mf_gj_update{'_sym' if sym else ''}<{tname}>", kprof["update_ms"], kprof["update_calls"],
+                   kprof["update_flops"], "flops", kprof["update_flops_executed"])
     add_kernel(f"mf_gj_small<{tname}>", kprof["small_ms"], kprof["small_calls"], kprof["small_flops"], "flops",
                kprof["small_flops_executed"])
     add_kernel(f"mf_down<{tname}>", kprof["down_ms"], kprof["down_calls"], kprof["down_bytes"], "bytes")
@@ -710,6 +725,7 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": workload_desc(w), "precision": args.precision, "order": args.order,
                    "pivoting": pivots_for(prec)[0], "static_pivot": pivots_for(prec)[1],
+                   "symmetric_form": int(bool(args.symmetric and not pivots_for(prec)[0])),
                    "persistent_sweeps": args.persistent,
                    "krylov_space": "band" if band_main else "full", "leaf": args.leaf, "rtol": RTOL,
                    "restart": RESTART, "parallelism": f"replicas{world}" if world > 1 else "single",

@@ -354,14 +354,15 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     its products in the same order on either shape, so
  *                     results do not change.  (With STDD_OPT_AUTOTUNE 0 and
  *                     this option 0 the shape is 64.)
- *   STDD_OPT_PERSISTENT (default 1): in the sequential orders (1 and 3,
+ *   STDD_OPT_PERSISTENT (default 2): in the sequential orders (1 and 3,
  *                     one right-hand side at a time) each strip's solve --
  *                     residual restriction, the upward and the downward
  *                     sweep over all tree levels, the add-back -- runs as
  *                     one cooperative launch whose levels are separated by
  *                     grid-wide barriers instead of ~3 launches per level;
- *                     0: one launch per level.  Same arithmetic, same
- *                     results.
+ *                     0: one launch per level; k = 1..8: the cooperative
+ *                     grid holds k blocks per SM (at most what fits).  Same
+ *                     arithmetic, same results.
  *   STDD_OPT_SWEEP_WAIT (default 0 = 4,194,304): polls a block spends at one
  *                     grid barrier of a persistent sweep before it gives up;
  *                     then every block returns, the call that applied the
@@ -378,7 +379,21 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     bounds the element growth of the unpivoted sweep
  *                     inside a front, which complex64 factors of high-index
  *                     guided-wave geometries cannot afford.  Invalidates the
- *                     factors. */
+ *                     factors.
+ *   STDD_OPT_SYMMETRIC (default 1): factor each box's operator in its
+ *                     complex-symmetric form D A_i, D the diagonal of the
+ *                     box's stretch products s_x s_y at the nodes (Eqs.
+ *                     10-13: row u of the SC-PML operator times s_x s_y at
+ *                     u is symmetric), and solve A_i x = r as D A_i x = D r.
+ *                     The working matrix of the blocked Gauss-Jordan sweep
+ *                     is then symmetric within the eliminated and within the
+ *                     remaining rows and antisymmetric between them, so the
+ *                     large-front update (most of the factorization's
+ *                     arithmetic) computes one triangle and mirrors it.
+ *                     Used when STDD_OPT_PIVOTING is 0 (row interchanges
+ *                     break the symmetry); 0: the factors of A_i as
+ *                     assembled.  The two agree to rounding.  Invalidates
+ *                     the factors. */
 enum {
   STDD_OPT_GRAPHS = 1,
   STDD_OPT_AUTOTUNE = 2,
@@ -389,7 +404,8 @@ enum {
   STDD_OPT_PIVOTING = 7,
   STDD_OPT_PERSISTENT = 8,
   STDD_OPT_SWEEP_WAIT = 9,
-  STDD_OPT_UPDATE_TILE = 10
+  STDD_OPT_UPDATE_TILE = 10,
+  STDD_OPT_SYMMETRIC = 11
 };
 stdd_status stdd_set_option(stdd_ctx *ctx, int option, int value);
 stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);

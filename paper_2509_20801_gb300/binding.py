@@ -300,6 +300,7 @@ STDD_OPT_PIVOTING = 7
 STDD_OPT_PERSISTENT = 8
 STDD_OPT_SWEEP_WAIT = 9
 STDD_OPT_UPDATE_TILE = 10
+STDD_OPT_SYMMETRIC = 11
 
 
 def stdd_set_profiling(ctx, level=1):

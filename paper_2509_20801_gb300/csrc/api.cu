@@ -206,6 +206,11 @@ struct stdd_ctx {
   // partial pivoting restricted to each front's pivot rows (STDD_OPT_PIVOTING)
   int pivoting = 0;
   DBuf d_pcol, d_panel;
+  // symmetric form (STDD_OPT_SYMMETRIC): fronts of D A, D = the local
+  // stretch products s_x s_y, with lower-half updates; not with pivoting
+  int symmetric = 1;
+  bool sym_active() const { return symmetric && !pivoting; }
+  DBuf d_lsx, d_lsy;
   int64_t nfronts = 0, factor_entries = 0;
   double factor_cflops = 0, factor_cflops_lu = 0, solve_cflops = 0;
   int max_p = 0, max_b = 0, depth = 0;
@@ -273,6 +278,7 @@ struct stdd_ctx {
   std::vector<std::vector<double>> unit_update;             // per level, per step
   std::vector<double> exec_small;                           // per level, Gauss-Jordan flops
   std::vector<std::vector<double>> exec_update;             // per level, per step
+  std::vector<std::vector<double>> unit_update_sym, exec_update_sym;  // the symmetric form's
   std::vector<double> span_units, span_exec;                // parallel to spans
   std::vector<int> span_level;                              // parallel to spans
   struct Hook : stdd::LaunchHook {
@@ -288,8 +294,9 @@ struct stdd_ctx {
         u = c->unit_small[level];
         x = c->exec_small[level];
       } else if (kind == stdd::K_UPDATE) {
-        u = c->unit_update[level][k / stdd::MF_NB];
-        x = c->exec_update[level][k / stdd::MF_NB];
+        const bool sy = c->sym_active() && c->tc_fmt() < 0;
+        u = (sy ? c->unit_update_sym : c->unit_update)[level][k / stdd::MF_NB];
+        x = (sy ? c->exec_update_sym : c->exec_update)[level][k / stdd::MF_NB];
       } else if (kind == stdd::K_UP) {
         u = x = c->unit_up[level];
       } else {
@@ -589,6 +596,9 @@ MfArgs stdd_ctx::mf_args(int par, bool solve) const {
   a.n_raised = d_nraised.as<unsigned long long>();
   a.pcol = pivoting ? d_pcol.as<int>() : nullptr;
   a.panel = pivoting ? d_panel.p : nullptr;
+  a.sym = sym_active() ? 1 : 0;
+  a.lsx = a.sym ? d_lsx.as<double2>() : nullptr;
+  a.lsy = a.sym ? d_lsy.as<double2>() : nullptr;
   (void)solve;
   return a;
 }
@@ -598,7 +608,10 @@ MfArgs stdd_ctx::mf_args(int par, bool solve) const {
 // frequency and the PML, not on the structure).
 void stdd_ctx::upload_local_couplings() {
   const double k0 = 2.0 * M_PI / wavelength;
-  std::vector<double2> lcxm, lcxp;
+  std::vector<double2> lcxm, lcxp, lsx, lsy;
+  auto nodes_of = [](const std::vector<cd> &v, std::vector<double2> &out) {
+    for (const cd &z : v) out.push_back(make_double2(z.real(), z.imag()));
+  };
   for (int k = 0; k < nsub; ++k) {
     const StripHost &s = strips[k];
     std::vector<cd> sx, sxh;
@@ -607,9 +620,11 @@ void stdd_ctx::upload_local_couplings() {
     couplings(sx, sxh, dx, cm, cp);
     lcxm.insert(lcxm.end(), cm.begin(), cm.end());
     lcxp.insert(lcxp.end(), cp.begin(), cp.end());
+    nodes_of(sx, lsx);
   }
   upload(d_lcxm, lcxm, stream);
   upload(d_lcxp, lcxp, stream);
+  upload(d_lsx, lsx, stream);
   // local y couplings of the distinct box heights and PML widths (a strip
   // decomposition has one: all rows with the global y-PML, the global ones)
   std::vector<double2> lcym, lcyp;
@@ -620,9 +635,11 @@ void stdd_ctx::upload_local_couplings() {
     couplings(sy, syh, dy, cm, cp);
     lcym.insert(lcym.end(), cm.begin(), cm.end());
     lcyp.insert(lcyp.end(), cp.begin(), cp.end());
+    nodes_of(sy, lsy);
   }
   upload(d_lcym, lcym, stream);
   upload(d_lcyp, lcyp, stream);
+  upload(d_lsy, lsy, stream);
 }
 
 void stdd_ctx::factor() {
@@ -839,10 +856,14 @@ void stdd_ctx::build_structure() {
     unit_down.assign(depth, 0.0);
     unit_update.assign(depth, {});
     exec_update.assign(depth, {});
+    unit_update_sym.assign(depth, {});
+    exec_update_sym.assign(depth, {});
     for (int L = 0; L < depth; ++L) {
       const LevelInfo &li = levels[L];
       unit_update[L].assign((li.max_p + stdd::MF_NB - 1) / stdd::MF_NB + 1, 0.0);
       exec_update[L].assign(unit_update[L].size(), 0.0);
+      unit_update_sym[L].assign(unit_update[L].size(), 0.0);
+      exec_update_sym[L].assign(unit_update[L].size(), 0.0);
       for (int f = li.f0; f < li.f0 + li.nf; ++f) {
         const double p = fr[f].p, b = fr[f].b, n = p + b;
         unit_up[L] += E * b * p;
@@ -853,8 +874,12 @@ void stdd_ctx::build_structure() {
         } else {
           for (int k = 0; k < fr[f].p; k += stdd::MF_NB) {
             const double nbk = std::min(stdd::MF_NB, fr[f].p - k);
-            exec_update[L][k / stdd::MF_NB] += 8.0 * (n - nbk) * (n - nbk) * nbk;
-            unit_update[L][k / stdd::MF_NB] += 8.0 * (n - k - nbk) * (n - k - nbk) * nbk;
+            const double me = n - nbk, mt = n - k - nbk;
+            exec_update[L][k / stdd::MF_NB] += 8.0 * me * me * nbk;
+            unit_update[L][k / stdd::MF_NB] += 8.0 * mt * mt * nbk;
+            // symmetric form: one triangle with its diagonal
+            exec_update_sym[L][k / stdd::MF_NB] += 8.0 * me * (me + 1) / 2 * nbk;
+            unit_update_sym[L][k / stdd::MF_NB] += 8.0 * mt * (mt + 1) / 2 * nbk;
           }
         }
       }
@@ -1040,7 +1065,7 @@ template <typename R> void stdd_ctx::tune_update_tiles() {
   for (int L = 0; L < depth; ++L) {
     const LevelInfo &li = levels[L];
     if (li.max_n <= stdd::MF_SMALL) continue;
-    keys[L] = {device, (int64_t)sizeof(R), 7, li.nf, li.max_p, li.max_b, li.max_n, li.min_n};
+    keys[L] = {device, (int64_t)sizeof(R), 7, sym_active() ? 1 : 0, li.nf, li.max_p, li.max_b, li.max_n, li.min_n};
     std::lock_guard<std::mutex> lk(tuned_mutex());
     auto hit = tuned().find(keys[L]);
     if (hit != tuned().end()) levels[L].upd_tile = hit->second;
@@ -1878,7 +1903,7 @@ int64_t stdd_ctx::device_bytes() const {
                        &d_inv, &d_lcxm, &d_lcxp, &d_colstrip, &d_lcym, &d_lcyp, &d_rowbox, &d_fac, &d_ws[0], &d_ws[1], &d_ub[0],
                        &d_ub[1], &d_tloc, &d_wloc, &d_items, &d_flag, &d_minpiv, &d_b, &d_x, &d_r, &d_V, &d_Z, &d_w,
                        &d_part, &d_h, &d_nrm, &d_y, &d_pre, &d_fpart, &d_guess, &d_gscr, &d_pcol, &d_panel,
-                       &d_striplv, &d_bar, &d_sweep_flag};
+                       &d_striplv, &d_bar, &d_sweep_flag, &d_lsx, &d_lsy};
   int64_t s = 0;
   for (auto *d : all) s += (int64_t)d->bytes;
   return s;
@@ -2376,6 +2401,14 @@ stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
         if (value < 0 || value > 1) throw ArgError("pivoting must be 0 (off) or 1 (partial, within fronts)");
         if (value != c->pivoting) {
           c->pivoting = value;
+          c->invalidate_factors();
+          c->clear_graphs();
+        }
+        break;
+      case STDD_OPT_SYMMETRIC:
+        if (value < 0 || value > 1) throw ArgError("symmetric must be 0 (off) or 1 (on)");
+        if (value != c->symmetric) {
+          c->symmetric = value;
           c->invalidate_factors();
           c->clear_graphs();
         }

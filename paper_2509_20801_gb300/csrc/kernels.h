@@ -44,6 +44,13 @@ struct MfArgs {
   int *pcol;
   void *panel;
   const int2 *items_sweep;    // the substitution work items (persistent sweep)
+  // Symmetric form (sym = 1): the fronts hold D A_i, D = diag(s_x s_y) of the
+  // local stretches, which is complex symmetric; the Gauss-Jordan working
+  // matrix then stays symmetric up to the sign of its cross blocks and the
+  // update computes the lower half only.  lsx / lsy: local node stretches,
+  // indexed like cxm / cym.
+  const double2 *lsx, *lsy;
+  int sym;
 };
 
 struct LevelInfo {

@@ -122,7 +122,28 @@ __device__ __forceinline__ C front_entry(const MfArgs &a, const FrontDev &f, con
                                          const bool *has, int r, int c) {
   const int p = f.p, H = s.y1 - s.y0;   // local box height
   double2 v = make_double2(0.0, 0.0);
-  if (r < p || c < p) {
+  if ((r < p || c < p) && a.sym) {
+    // row u of D A: the diagonal times d_u = s_x s_y; each coupling between
+    // two nodes computed from the lower-indexed node of the pair, so that
+    // entries (u, w) and (w, u) are the same number
+    const int u = a.nodes[f.node_off + r], w = a.nodes[f.node_off + c];
+    const int ux = u / H, uy = u - ux * H;
+    const double2 sxu = a.lsx[s.coef_off + ux], syu = a.lsy[s.ycoef_off + uy];
+    if (u == w) {
+      const double2 xm = a.cxm[s.coef_off + ux], xp = a.cxp[s.coef_off + ux];
+      const double2 ym = a.cym[s.ycoef_off + uy], yp = a.cyp[s.ycoef_off + uy];
+      double2 d0;
+      d0.x = a.k0sq * a.eps[(int64_t)(s.x0 + ux) * a.H + s.y0 + uy] - xm.x - xp.x - ym.x - yp.x;
+      d0.y = -xm.y - xp.y - ym.y - yp.y;
+      v = cmul(cmul(sxu, syu), d0);
+    } else if (w == u - H || w == u + H) {
+      const int lx = w == u - H ? ux - 1 : ux;     // the pair's left column
+      v = cmul(cmul(a.lsx[s.coef_off + lx], a.cxp[s.coef_off + lx]), syu);
+    } else if ((w == u - 1 && uy > 0) || (w == u + 1 && uy < H - 1)) {
+      const int ly = w == u - 1 ? uy - 1 : uy;     // the pair's lower row
+      v = cmul(cmul(a.lsy[s.ycoef_off + ly], a.cyp[s.ycoef_off + ly]), sxu);
+    }
+  } else if (r < p || c < p) {
     const int u = a.nodes[f.node_off + r], w = a.nodes[f.node_off + c];
     const int ux = u / H, uy = u - ux * H;
     if (u == w) {
@@ -562,6 +583,43 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_row(MfArgs a, int f0, 
   }
 }
 
+// Symmetric form: the pivot rows after step k without the row product.
+// The working matrix after the step is symmetric within the eliminated and
+// within the remaining indices and antisymmetric between them, so pivot row
+// k + i at column c is the column just written by mf_gj_col at (c, k + i),
+// negated when c is not yet eliminated (c >= k + nbk) and kept when c < k.
+// A transpose through shared memory: reads along c, writes along i.
+template <typename R>
+__global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_row_mirror(MfArgs a, int f0, int k) {
+  using C = typename CT<R>::T;
+  constexpr int NB = MF_NB, TILE = MF_PANEL_THREADS, HALF = TILE / 2;
+  __shared__ C T[HALF][NB + 1];
+  const FrontDev f = a.fronts[f0 + blockIdx.x];
+  const int p = f.p, n = p + f.b;
+  if (n <= MF_SMALL || k >= p) return;
+  const int nbk = min(NB, p - k);
+  const int cols = n - nbk;
+  C *fac = reinterpret_cast<C *>(a.fac);
+  const int64_t fo = f.fac_off;
+  const int tid = threadIdx.x;
+  for (int h = 0; h < 2; ++h) {       // the block's TILE columns, HALF at a time
+    const int cbase = blockIdx.y * TILE + h * HALF;
+    if (cbase >= cols) return;
+    const int ncol = min(HALF, cols - cbase);
+    if (h) __syncthreads();
+    for (int idx = tid; idx < nbk * ncol; idx += TILE) {
+      const int cc = idx % ncol, i = idx / ncol, c = unband(cbase + cc, k, nbk);
+      const C v = ld_elem<C>(a, f, c, k + i);
+      T[cc][i] = c < k ? v : cneg(v);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nbk * ncol; idx += TILE) {
+      const int i = idx % nbk, cc = idx / nbk;
+      fac[fo + (int64_t)unband(cbase + cc, k, nbk) * p + k + i] = T[cc][i];
+    }
+  }
+}
+
 // The same update on 32 x 32 tiles (64 threads as 8 x 8, thread (tx, ty)
 // owns rows ty + 8 i and columns tx + 8 j): more, smaller blocks for levels
 // whose fronts are too small to fill 64 x 64 tiles.  Every entry accumulates
@@ -620,6 +678,101 @@ __global__ void __launch_bounds__(64) mf_gj_update32(MfArgs a, int f0, int k) {
       if (ci >= m) continue;
       const int c = unband(ci, k, nbk);
       st_elem<C>(a, f, r, c, cadd(ld_elem<C>(a, f, r, c), acc[i][j]));
+    }
+  }
+}
+
+// Symmetric form: the update of step k on the lower tile triangle only.
+// Between steps the working matrix of a symmetric front is
+//     [ X^-1        X^-1 M_ER           ]    E = eliminated pivots [0, k)
+//     [ -M_RE X^-1  M_RR - M_RE X^-1 M_ER ]    (X = M_EE, R the rest)
+// -- symmetric within the E and R blocks, antisymmetric between them -- so
+// every entry below the diagonal (row after column, in the order that skips
+// the pivot band) also writes its mirror, negated when exactly one of the
+// row and the column is eliminated.  Only tiles on or below the diagonal are
+// launched, and diagonal tiles store their lower half, so every entry comes
+// from the same lower-half sum whatever the tile size.  TM x TM tiles,
+// (TM / 4)^2 threads, each thread 4 x 4 entries.
+template <typename R, int TM>
+__global__ void __launch_bounds__((TM / 4) * (TM / 4)) mf_gj_update_sym(MfArgs a, int f0, int k) {
+  using C = typename CT<R>::T;
+  constexpr int NB = MF_NB, TS = TM / 4, NT = TS * TS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C(*As)[NB + 1] = reinterpret_cast<C(*)[NB + 1]>(smem_raw);
+  C(*Bs)[TM + 1] = reinterpret_cast<C(*)[TM + 1]>(smem_raw + sizeof(C) * TM * (NB + 1));
+  const FrontDev f = a.fronts[f0 + blockIdx.x];
+  const int p = f.p, n = p + f.b;
+  if (n <= MF_SMALL || k >= p) return;
+  const int nbk = min(NB, p - k);
+  const int m = n - nbk;
+  const int nt = (m + TM - 1) / TM;
+  const int y = blockIdx.y;
+  if (y >= nt * (nt + 1) / 2) return;
+  int ti = (int)((sqrtf(8.f * y + 1.f) - 1.f) * 0.5f);
+  while ((ti + 1) * (ti + 2) / 2 <= y) ++ti;
+  while (ti * (ti + 1) / 2 > y) --ti;
+  const int tj = y - ti * (ti + 1) / 2;
+  const int i0 = ti * TM, j0 = tj * TM;
+  const C *fac = reinterpret_cast<const C *>(a.fac);
+  const int64_t fo = f.fac_off;
+  const int tid = threadIdx.x, tx = tid % TS, ty = tid / TS;
+  for (int idx = tid; idx < TM * nbk; idx += NT) {
+    const int rr = idx % TM, j = idx / TM, ri = i0 + rr;
+    As[rr][j] = ri < m ? ld_elem<C>(a, f, unband(ri, k, nbk), k + j) : czero<C>();
+  }
+  for (int idx = tid; idx < TM * nbk; idx += NT) {
+    const int j = idx % nbk, cc = idx / nbk, ci = j0 + cc;
+    Bs[j][cc] = ci < m ? fac[fo + (int64_t)unband(ci, k, nbk) * p + k + j] : czero<C>();
+  }
+  __syncthreads();
+  C acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = czero<C>();
+  if (ti != tj) {
+    for (int kk = 0; kk < nbk; ++kk) {
+      C av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[ty + TS * i][kk];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + TS * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cfma(av[i], bv[j], acc[i][j]);
+    }
+  } else {
+    // diagonal tile: entry (i, j) of a thread is on or below the diagonal
+    // when j < i, or j == i and tx <= ty; the 6 entries with j > i never are
+    const bool mine = tx <= ty;
+    for (int kk = 0; kk < nbk; ++kk) {
+      C av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[ty + TS * i][kk];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + TS * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < i; ++j) acc[i][j] = cfma(av[i], bv[j], acc[i][j]);
+        if (mine) acc[i][i] = cfma(av[i], bv[i], acc[i][i]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int ri = i0 + ty + TS * i;
+    if (ri >= m) continue;
+    const int r = unband(ri, k, nbk);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int ci = j0 + tx + TS * j;
+      if (ci > ri) continue;      // upper entries of a diagonal tile: written as mirrors
+      const int c = unband(ci, k, nbk);
+      const C v = cadd(ld_elem<C>(a, f, r, c), acc[i][j]);
+      st_elem<C>(a, f, r, c, v);
+      if (ci < ri) st_elem<C>(a, f, c, r, (r < k) != (c < k) ? cneg(v) : v);
     }
   }
 }
@@ -766,7 +919,8 @@ template <typename R> __device__ __forceinline__ void up_gather_front(const MfAr
   using C = typename CT<R>::T;
   const FrontDev f = a.fronts[f0 + fi];
   const int p = f.p, b = f.b, n = p + b;
-  const int64_t voff = a.strips[f.strip].vec_off;
+  const StripDev st = a.strips[f.strip];
+  const int64_t voff = st.vec_off;
   const C *uc[2] = {nullptr, nullptr};
   int bc[2] = {0, 0};
   const int *inv[2] = {nullptr, nullptr};
@@ -790,6 +944,10 @@ template <typename R> __device__ __forceinline__ void up_gather_front(const MfAr
       if (k < p) {
         gi = q * ldt + voff + nodes[k];
         w = tv[gi];
+        if (a.sym) {   // the source of D A x = D t
+          const int Hl = st.y1 - st.y0, u = nodes[k], ux = u / Hl, uy = u - ux * Hl;
+          w = cmul(w, to_c(cmul(a.lsx[st.coef_off + ux], a.lsy[st.ycoef_off + uy]), C()));
+        }
       }
 #pragma unroll
       for (int ci = 0; ci < 2; ++ci)
@@ -1106,6 +1264,9 @@ template <typename R> cudaError_t mf_setup_attributes() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(mf_gj_row<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem<R>());
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(mf_gj_update_sym<R, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)gemm_smem<R>());
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(mf_gj_update<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<R>());
 }
 
@@ -1142,6 +1303,11 @@ void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_
       if (hook) hook->before(K_UPDATE, level, k);
       if (tc_fmt >= 0 && sizeof(R) == 4) {
         mf_tc_update_launch(a, L, k, tc_fmt, st);
+      } else if (a.sym) {
+        const int tm = L.upd_tile == 32 ? 32 : 64, nts = std::max(1, (m + tm - 1) / tm);
+        const size_t sm = sizeof(typename CT<R>::T) * (tm * (MF_NB + 1) + MF_NB * (tm + 1));
+        if (tm == 32) mf_gj_update_sym<R, 32><<<dim3(L.nf, nts * (nts + 1) / 2), 64, sm, st>>>(a, L.f0, k);
+        else mf_gj_update_sym<R, 64><<<dim3(L.nf, nts * (nts + 1) / 2), 256, sm, st>>>(a, L.f0, k);
       } else if (L.upd_tile == 32) {
         const int nt32 = std::max(1, (m + 31) / 32);
         mf_gj_update32<R><<<dim3(L.nf, nt32 * nt32), 64, 0, st>>>(a, L.f0, k);
@@ -1149,7 +1315,8 @@ void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_
         mf_gj_update<R><<<dim3(L.nf, nt * nt), 256, gemm_smem<R>(), st>>>(a, L.f0, k);
       }
       if (hook) hook->after(K_UPDATE, level, k);
-      mf_gj_row<R><<<dim3(L.nf, tiles), MF_PANEL_THREADS, row_smem<R>(), st>>>(a, L.f0, k);
+      if (a.sym) mf_gj_row_mirror<R><<<dim3(L.nf, tiles), MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
+      else mf_gj_row<R><<<dim3(L.nf, tiles), MF_PANEL_THREADS, row_smem<R>(), st>>>(a, L.f0, k);
       count_launch(4);
     }
   }

@@ -311,3 +311,34 @@ def test_band_space_system_gives_the_solution():
     x = x0 + ddm.apply_Minv(r0 + s)
     assert np.linalg.norm(A @ x - b) < 1e-10 * np.linalg.norm(b)
     assert np.linalg.norm(x - prob.solve(b)) < 1e-9 * np.linalg.norm(x)
+
+
+def _sym_defect(A, d):
+    """max |B - B^T| / max |B| for B = diag(d) A."""
+    import scipy.sparse as sp
+    B = (sp.diags(d) @ A).tocsr()
+    return abs(B - B.T).max() / abs(B).max()
+
+
+def test_local_operators_are_symmetric_after_stretch_scaling(rnd4):
+    """Row u of every local operator times s_x s_y at u -- the box's own
+    stretches, local interface PML included (Eqs. 10-13) -- is complex
+    symmetric; the factorization may therefore work on D A_k with one
+    triangle of each update.  The unscaled operator and the operator scaled
+    by the half-node stretches are not symmetric, so the pin tells the node
+    products from plausible other diagonals."""
+    from oracle.checkerboard import CheckerboardDDM
+    from oracle.fdfd import stretch_profile
+    w, P, D = rnd4
+    for k, s in enumerate(D.strips):
+        A = D.local_A(k)
+        sx, sxh = D.local_stretch_x(s)
+        d = np.outer(sx, P.sy).ravel()
+        assert _sym_defect(A, d) <= 1e-15
+        assert _sym_defect(A, np.ones_like(d)) > 1e-3
+        assert _sym_defect(A, np.outer(sxh[1:], P.syh[1:]).ravel()) > 1e-3
+    C = CheckerboardDDM(P, 3, 2, 3, 8)
+    for k, b in enumerate(C.boxes):
+        sx, _ = stretch_profile(b.width, b.Lx_lo, b.Lx_hi, P.dx, P.k0, P.m, P.R)
+        sy, _ = stretch_profile(b.height, b.Ly_lo, b.Ly_hi, P.dy, P.k0, P.m, P.R)
+        assert _sym_defect(C.local_A(k), np.outer(sx, sy).ravel()) <= 1e-15
