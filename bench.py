@@ -676,18 +676,17 @@ def run_ours(args, rank, world, local_rank):
         k.update(frac=k["achieved"] / k["peak"], ms_per_step=ms, launches_per_step=calls,
                  units_per_launch=u, unit_kind=kind, ms_per_launch=t * 1e3)
         if executed is not None:
-            lu = "LDL^T flops (one triangle of each trailing-block update)" if name.startswith(
-                "mf_gj_update_sym") else "LU flops (trailing-block updates)"
+            lu = "LDL^T flops (one triangle of each trailing-block update)" if sym else "LU flops (trailing-block updates)"
             k.update(unit_kind=lu, executed_flops_per_launch=executed / calls,
                      executed_tflops=executed / calls / t / 1e12)
         kernels[name] = k
 
     tname = "double" if prec == S.STDD_PREC_FP64 else "float"
+    sym = bool(args.symmetric and not pivots_for(prec)[0] and not tensor)
     if tensor:
         add_kernel(f"mf_gj_update_tc<{args.precision}>", kprof["update_ms"], kprof["update_calls"],
                    kprof["update_flops"], "tensor", kprof["update_flops_executed"])
     else:
-        sym = args.symmetric and not pivots_for(prec)[0]
         add_kernel(f"mf_gj_update{'_sym' if sym else ''}<{tname}>", kprof["update_ms"], kprof["update_calls"],
                    kprof["update_flops"], "flops", kprof["update_flops_executed"])
     add_kernel(f"mf_gj_small<{tname}>", kprof["small_ms"], kprof["small_calls"], kprof["small_flops"], "flops",
@@ -725,7 +724,7 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": workload_desc(w), "precision": args.precision, "order": args.order,
                    "pivoting": pivots_for(prec)[0], "static_pivot": pivots_for(prec)[1],
-                   "symmetric_form": int(bool(args.symmetric and not pivots_for(prec)[0])),
+                   "symmetric_form": int(bool(args.symmetric and not pivots_for(prec)[0] and not tensor)),
                    "persistent_sweeps": args.persistent,
                    "krylov_space": "band" if band_main else "full", "leaf": args.leaf, "rtol": RTOL,
                    "restart": RESTART, "parallelism": f"replicas{world}" if world > 1 else "single",

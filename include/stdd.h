@@ -391,7 +391,9 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     large-front update (most of the factorization's
  *                     arithmetic) computes one triangle and mirrors it.
  *                     Used when STDD_OPT_PIVOTING is 0 (row interchanges
- *                     break the symmetry); 0: the factors of A_i as
+ *                     break the symmetry) and the factors are not formed
+ *                     with tensor-core updates (STDD_PREC_C64_BF16 /
+ *                     _FP16 update whole tiles); 0: the factors of A_i as
  *                     assembled.  The two agree to rounding.  Invalidates
  *                     the factors. */
 enum {

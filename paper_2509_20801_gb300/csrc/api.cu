@@ -208,8 +208,9 @@ struct stdd_ctx {
   DBuf d_pcol, d_panel;
   // symmetric form (STDD_OPT_SYMMETRIC): fronts of D A, D = the local
   // stretch products s_x s_y, with lower-half updates; not with pivoting
+  // nor with the tensor-core updates (which update whole tiles)
   int symmetric = 1;
-  bool sym_active() const { return symmetric && !pivoting; }
+  bool sym_active() const { return symmetric && !pivoting && tc_fmt() < 0; }
   DBuf d_lsx, d_lsy;
   int64_t nfronts = 0, factor_entries = 0;
   double factor_cflops = 0, factor_cflops_lu = 0, solve_cflops = 0;
@@ -279,6 +280,7 @@ struct stdd_ctx {
   std::vector<double> exec_small;                           // per level, Gauss-Jordan flops
   std::vector<std::vector<double>> exec_update;             // per level, per step
   std::vector<std::vector<double>> unit_update_sym, exec_update_sym;  // the symmetric form's
+  std::vector<double> unit_small_sym, exec_small_sym;
   std::vector<double> span_units, span_exec;                // parallel to spans
   std::vector<int> span_level;                              // parallel to spans
   struct Hook : stdd::LaunchHook {
@@ -291,10 +293,11 @@ struct stdd_ctx {
       c->span_level[open] = level;
       double u = 0, x = 0;
       if (kind == stdd::K_SMALL) {
-        u = c->unit_small[level];
-        x = c->exec_small[level];
+        const bool sy = c->sym_active();
+        u = (sy ? c->unit_small_sym : c->unit_small)[level];
+        x = (sy ? c->exec_small_sym : c->exec_small)[level];
       } else if (kind == stdd::K_UPDATE) {
-        const bool sy = c->sym_active() && c->tc_fmt() < 0;
+        const bool sy = c->sym_active();
         u = (sy ? c->unit_update_sym : c->unit_update)[level][k / stdd::MF_NB];
         x = (sy ? c->exec_update_sym : c->exec_update)[level][k / stdd::MF_NB];
       } else if (kind == stdd::K_UP) {
@@ -852,6 +855,8 @@ void stdd_ctx::build_structure() {
     const double E = (double)elem();
     unit_small.assign(depth, 0.0);
     exec_small.assign(depth, 0.0);
+    unit_small_sym.assign(depth, 0.0);
+    exec_small_sym.assign(depth, 0.0);
     unit_up.assign(depth, 0.0);
     unit_down.assign(depth, 0.0);
     unit_update.assign(depth, {});
@@ -870,7 +875,11 @@ void stdd_ctx::build_structure() {
         unit_down[L] += E * p * n;
         if (n <= stdd::MF_SMALL) {
           exec_small[L] += 8.0 * p * n * n;
-          for (int k = 0; k < fr[f].p; ++k) unit_small[L] += 8.0 * (n - k - 1) * (n - k - 1);
+          exec_small_sym[L] += 8.0 * p * n * (n + 1) / 2;
+          for (int k = 0; k < fr[f].p; ++k) {
+            unit_small[L] += 8.0 * (n - k - 1) * (n - k - 1);
+            unit_small_sym[L] += 8.0 * (n - k - 1) * (n - k) / 2;
+          }
         } else {
           for (int k = 0; k < fr[f].p; k += stdd::MF_NB) {
             const double nbk = std::min(stdd::MF_NB, fr[f].p - k);

@@ -50,22 +50,51 @@ template <typename C> __host__ __device__ __forceinline__ C cconjmul(C a, C b) {
 template <typename C> __host__ __device__ __forceinline__ auto cabs2(C a) -> decltype(a.x) {
   return a.x * a.x + a.y * a.y;
 }
-// 1/a by Smith's algorithm (R. L. Smith, CACM 5(8), 1962): scale by the
-// larger component to avoid overflow and underflow.
-template <typename C> __host__ __device__ __forceinline__ C crecip(C a) {
-  C r;
-  if (fabs(a.x) >= fabs(a.y)) {
-    auto t = a.y / a.x;
-    auto d = a.x + a.y * t;
-    r.x = 1 / d;
+// 1/a in complex128: conj(a) / |a|^2, one real reciprocal and three
+// multiplies (the schoolbook complex division).  R. L. Smith's scaled form
+// (CACM 5(8), 1962) costs two more divisions, and on a part whose FP64 pipe
+// retires one warp instruction per 64 cycles per scheduler -- 1.25 TFLOP/s
+// over 152 SMs -- even one thread's scalar FP64 work costs what a full
+// warp's does.  |a|^2 must neither overflow nor underflow: |a| between
+// 2^-511 and 2^511, far outside the stencil scale of these operators;
+// callers flag pivots outside it (pivot_ok).
+__device__ __forceinline__ double2 crecip(double2 a) {
+  const double s = __drcp_rn(a.x * a.x + a.y * a.y);
+  return make_double2(a.x * s, -a.y * s);
+}
+// 1/a in complex64 by Smith's algorithm: the FP32 pipe is not the limit,
+// and the scaling keeps the reciprocal accurate over float's narrower range.
+__device__ __forceinline__ float2 crecip(float2 a) {
+  float2 r;
+  if (fabsf(a.x) >= fabsf(a.y)) {
+    const float t = a.y / a.x, d = a.x + a.y * t;
+    r.x = 1.0f / d;
     r.y = -t / d;
   } else {
-    auto t = a.x / a.y;
-    auto d = a.x * t + a.y;
+    const float t = a.x / a.y, d = a.x * t + a.y;
     r.x = t / d;
-    r.y = -1 / d;
+    r.y = -1.0f / d;
   }
   return r;
+}
+// v or -v by the sign bits alone (exactly -v: IEEE negation flips the sign)
+__device__ __forceinline__ double2 cneg_if(double2 v, bool neg) {
+  const long long m = neg ? (long long)(1ull << 63) : 0ll;
+  v.x = __longlong_as_double(__double_as_longlong(v.x) ^ m);
+  v.y = __longlong_as_double(__double_as_longlong(v.y) ^ m);
+  return v;
+}
+__device__ __forceinline__ float2 cneg_if(float2 v, bool neg) {
+  const int m = neg ? (int)(1u << 31) : 0;
+  v.x = __int_as_float(__float_as_int(v.x) ^ m);
+  v.y = __int_as_float(__float_as_int(v.y) ^ m);
+  return v;
+}
+// |a|^2 is a usable pivot modulus: positive and finite (in complex128 also
+// large enough for conj(a) / |a|^2 to stay finite)
+template <typename R> __device__ __forceinline__ bool pivot_ok(R d2) {
+  const R lo = sizeof(R) == 8 ? (R)1.0e-300 : (R)0;
+  return d2 > lo && d2 < (R)INFINITY;
 }
 
 __device__ __forceinline__ double2 to_c(double2 a, double2) { return a; }

@@ -245,11 +245,12 @@ __global__ void __launch_bounds__(128) mf_gj_small(MfArgs a, int f0, int nf, int
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int fpc = blockDim.x / TPF;                 // fronts per CTA
   const int slot = threadIdx.x / TPF, t = threadIdx.x % TPF;
-  C *F = reinterpret_cast<C *>(smem_raw) + (size_t)slot * (ldn * ldn + 2 * ldn);  // n x n, ld n
-  C *rowk = F + ldn * ldn;
+  const int slot_elems = ldn * (ldn + 1) + 2 * ldn;
+  C *F = reinterpret_cast<C *>(smem_raw) + (size_t)slot * slot_elems;  // n x n, column-major, ld below
+  C *rowk = F + ldn * (ldn + 1);
   C *colk = rowk + ldn;
   // column -> pivot map of this front (partial pivoting), after all fronts' matrices
-  int *perm = reinterpret_cast<int *>(reinterpret_cast<C *>(smem_raw) + (size_t)fpc * (ldn * ldn + 2 * ldn)) +
+  int *perm = reinterpret_cast<int *>(reinterpret_cast<C *>(smem_raw) + (size_t)fpc * slot_elems) +
               (size_t)slot * ldn;
   const int fi = blockIdx.x * fpc + slot;
   bool live = fi < nf;
@@ -264,6 +265,11 @@ __global__ void __launch_bounds__(128) mf_gj_small(MfArgs a, int f0, int nf, int
   if (TPF == 32 && !live) return;   // warp-private work: leaving is safe
   if (TPF > 32 && !live) return;    // whole CTA is this front
   const StripDev s = a.strips[f.strip];
+  // symmetric form: updates on the lower triangle, each entry also stored
+  // at its mirror (F's leading dimension odd so that the mirror stores, a
+  // stride apart, fall in different banks)
+  const bool sym = a.sym && a.pcol == nullptr;
+  const int ld = sym ? (n | 1) : n;
   FrontDev ch[2];
   bool has[2];
 #pragma unroll
@@ -271,15 +277,28 @@ __global__ void __launch_bounds__(128) mf_gj_small(MfArgs a, int f0, int nf, int
     has[ci] = f.child[ci] >= 0;
     if (has[ci]) ch[ci] = a.fronts[f.child[ci]];
   }
-  for (int idx = t; idx < n * n; idx += TPF) {
-    const int c = idx / n, r = idx - c * n;
-    F[idx] = front_entry<C>(a, f, s, ch, has, r, c);
+  if (sym) {
+    // the assembled front is exactly symmetric (pairwise-equal stencil
+    // entries, children's Schur complements stored symmetric): lower half
+    // and mirror, enumerated as in the update below
+    for (int e = t; e < n * (n + 1) / 2; e += TPF) {
+      const int g = e / (n + 1), j = e - g * (n + 1);
+      const int c = j < n - g ? g : n - 1 - g, r = j < n - g ? g + j : c + j - (n - g);
+      const C v = front_entry<C>(a, f, s, ch, has, r, c);
+      F[c * ld + r] = v;
+      F[r * ld + c] = v;
+    }
+  } else {
+    for (int idx = t; idx < n * n; idx += TPF) {
+      const int c = idx / n, r = idx - c * n;
+      F[c * ld + r] = front_entry<C>(a, f, s, ch, has, r, c);
+    }
   }
   const bool piv = a.pcol != nullptr;
   if (piv)
     for (int j = t; j < p; j += TPF) perm[j] = j;
   front_sync<TPF>();
-  double dmin = INFINITY;
+  double d2min = INFINITY;      // smallest |pivot|^2 (its square root taken once, at the end)
   bool bad = false;
   for (int k = 0; k < p; ++k) {
     if (piv) {
@@ -287,20 +306,20 @@ __global__ void __launch_bounds__(128) mf_gj_small(MfArgs a, int f0, int nf, int
       R bv = -1;
       int bi = k;
       for (int i = k + t; i < p; i += TPF) {
-        const R v = cabs2(F[k * n + i]);
+        const R v = cabs2(F[k * ld + i]);
         if (v > bv) {
           bv = v;
           bi = i;
         }
       }
       group_argmax<TPF>(bv, bi);
-      const bool sw = bi != k && bv > cabs2(F[k * n + k]);
+      const bool sw = bi != k && bv > cabs2(F[k * ld + k]);
       front_sync<TPF>();          // every thread has read F(k, k) before any swap
       if (sw) {
         for (int c = t; c < n; c += TPF) {
-          const C u = F[c * n + k];
-          F[c * n + k] = F[c * n + bi];
-          F[c * n + bi] = u;
+          const C u = F[c * ld + k];
+          F[c * ld + k] = F[c * ld + bi];
+          F[c * ld + bi] = u;
         }
         if (t == 0) {
           const int u = perm[k];
@@ -315,12 +334,12 @@ __global__ void __launch_bounds__(128) mf_gj_small(MfArgs a, int f0, int nf, int
     // every other thread takes the reciprocal from it)
     C inv = czero<C>();
     if (t == 0) {
-      const C d0 = F[k * n + k];
+      const C d0 = F[k * ld + k];
       bool raised;
       inv = crecip(floor_pivot(a, d0, raised));
-      const double ad = sqrt((double)cabs2(d0));
-      bad |= !(ad > 0.0) || !cfinite(d0);
-      dmin = fmin(dmin, ad);
+      const R d2 = cabs2(d0);
+      bad |= !pivot_ok(d2);
+      d2min = fmin(d2min, (double)d2);
       if (raised) atomicAdd(a.n_raised, 1ull);
     }
     if (TPF == 32) {
@@ -333,24 +352,47 @@ __global__ void __launch_bounds__(128) mf_gj_small(MfArgs a, int f0, int nf, int
       inv = inv_s;
     }
     for (int j = t; j < n; j += TPF) {
-      rowk[j] = cmul(F[j * n + k], inv);
-      colk[j] = F[k * n + j];
+      rowk[j] = cmul(F[j * ld + k], inv);
+      colk[j] = F[k * ld + j];
     }
     front_sync<TPF>();
-    for (int idx = t; idx < n * n; idx += TPF) {
-      const int c = idx / n, r = idx - c * n;
-      C v;
-      if (r == k) v = (c == k) ? inv : rowk[c];
-      else if (c == k) v = cneg(cmul(colk[r], inv));
-      else v = cfms(colk[r], rowk[c], F[idx]);
-      F[idx] = v;
+    if (sym) {
+      // the n (n + 1) / 2 entries with r >= c, enumerated by column pairs
+      // (c, n - 1 - c) of n + 1 entries each; the mirror of (r, c) is
+      // negated when exactly one of r and c is eliminated (<= k)
+      for (int e = t; e < n * (n + 1) / 2; e += TPF) {
+        const int g = e / (n + 1), j = e - g * (n + 1);
+        int r, c;
+        if (j < n - g) {
+          c = g;
+          r = g + j;
+        } else {
+          c = n - 1 - g;
+          r = c + j - (n - g);
+        }
+        C v;
+        if (r == k) v = (c == k) ? inv : rowk[c];
+        else if (c == k) v = cneg(cmul(colk[r], inv));
+        else v = cfms(colk[r], rowk[c], F[c * ld + r]);
+        F[c * ld + r] = v;
+        if (r != c) F[r * ld + c] = cneg_if(v, (r <= k) != (c <= k));
+      }
+    } else {
+      for (int idx = t; idx < n * n; idx += TPF) {
+        const int c = idx / n, r = idx - c * n;
+        C v;
+        if (r == k) v = (c == k) ? inv : rowk[c];
+        else if (c == k) v = cneg(cmul(colk[r], inv));
+        else v = cfms(colk[r], rowk[c], F[c * ld + r]);
+        F[c * ld + r] = v;
+      }
     }
     front_sync<TPF>();
   }
-  if (t == 0) note_pivot(a, bad ? 0.0 : dmin, !bad);
+  if (t == 0) note_pivot(a, bad ? 0.0 : sqrt(d2min), !bad);
   for (int idx = t; idx < n * n; idx += TPF) {
     const int c = idx / n, r = idx - c * n;
-    st_elem<C>(a, f, r, c, F[idx]);
+    st_elem<C>(a, f, r, c, F[c * ld + r]);
   }
   if (piv)
     for (int j = t; j < p; j += TPF) a.pcol[f.piv_off + j] = perm[j];
@@ -457,7 +499,7 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_diag(MfArgs a, int f0,
     D[i][j] = fac[fo + (int64_t)(k + j) * p + k + i];
   }
   __syncthreads();
-  double dmin = INFINITY;
+  double d2min = INFINITY;
   bool bad = false;
   __shared__ C inv_s;
   for (int q = 0; q < nbk; ++q) {
@@ -466,9 +508,9 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_diag(MfArgs a, int f0,
       const C d0 = D[q][q];
       bool raised;
       inv_s = crecip(floor_pivot(a, d0, raised));
-      const double ad = sqrt((double)cabs2(d0));
-      bad |= !(ad > 0.0) || !cfinite(d0);
-      dmin = fmin(dmin, ad);
+      const R d2 = cabs2(d0);
+      bad |= !pivot_ok(d2);
+      d2min = fmin(d2min, (double)d2);
       if (raised) atomicAdd(a.n_raised, 1ull);
     }
     __syncthreads();
@@ -488,7 +530,7 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_diag(MfArgs a, int f0,
     }
     __syncthreads();
   }
-  if (tid == 0) note_pivot(a, bad ? 0.0 : dmin, !bad);
+  if (tid == 0) note_pivot(a, bad ? 0.0 : sqrt(d2min), !bad);
   for (int idx = tid; idx < nbk * nbk; idx += blockDim.x) {
     const int i = idx % nbk, j = idx / nbk;
     fac[fo + (int64_t)(k + j) * p + k + i] = D[i][j];
@@ -610,7 +652,7 @@ __global__ void __launch_bounds__(MF_PANEL_THREADS) mf_gj_row_mirror(MfArgs a, i
     for (int idx = tid; idx < nbk * ncol; idx += TILE) {
       const int cc = idx % ncol, i = idx / ncol, c = unband(cbase + cc, k, nbk);
       const C v = ld_elem<C>(a, f, c, k + i);
-      T[cc][i] = c < k ? v : cneg(v);
+      T[cc][i] = cneg_if(v, c >= k);
     }
     __syncthreads();
     for (int idx = tid; idx < nbk * ncol; idx += TILE) {
@@ -772,7 +814,7 @@ __global__ void __launch_bounds__((TM / 4) * (TM / 4)) mf_gj_update_sym(MfArgs a
       const int c = unband(ci, k, nbk);
       const C v = cadd(ld_elem<C>(a, f, r, c), acc[i][j]);
       st_elem<C>(a, f, r, c, v);
-      if (ci < ri) st_elem<C>(a, f, c, r, (r < k) != (c < k) ? cneg(v) : v);
+      if (ci < ri) st_elem<C>(a, f, c, r, cneg_if(v, (r < k) != (c < k)));
     }
   }
 }
@@ -1245,7 +1287,7 @@ __global__ void __launch_bounds__(256, 2)
 // 128-thread CTA per front above
 template <typename R> static size_t small_smem(int ldn, int fpc) {
   using C = typename CT<R>::T;
-  return sizeof(C) * fpc * (size_t)(ldn * ldn + 2 * ldn) + sizeof(int) * fpc * (size_t)ldn;
+  return sizeof(C) * fpc * (size_t)(ldn * (ldn + 1) + 2 * ldn) + sizeof(int) * fpc * (size_t)ldn;
 }
 template <typename R> static size_t row_smem() {
   using C = typename CT<R>::T;
