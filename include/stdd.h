@@ -395,7 +395,21 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     with tensor-core updates (STDD_PREC_C64_BF16 /
  *                     _FP16 update whole tiles); 0: the factors of A_i as
  *                     assembled.  The two agree to rounding.  Invalidates
- *                     the factors. */
+ *                     the factors.
+ *   STDD_OPT_FP64_TC (default 1): complex128 factors in the symmetric form
+ *                     compute the large-front update products on the BF16
+ *                     tensor cores by exact splitting (the scheme of Ozaki,
+ *                     Ogita, Oishi and Rump, Numer. Algorithms 59, 2012):
+ *                     each real row of the pivot-column panel and each real
+ *                     column of the pivot-row panel is scaled by a power of
+ *                     two and cut into eight 7-bit slices (exact BF16
+ *                     numbers); the 36 slice products whose orders sum to at
+ *                     most 7 are accumulated exactly in FP32, combined in
+ *                     64-bit integers and rounded to FP64 once, so the
+ *                     product's error is bounded like an FP64 dot product's
+ *                     (relative to the row's and the column's largest
+ *                     entries).  0: the FP64 pipe.  The two agree to
+ *                     rounding.  Invalidates the factors. */
 enum {
   STDD_OPT_GRAPHS = 1,
   STDD_OPT_AUTOTUNE = 2,
@@ -407,7 +421,8 @@ enum {
   STDD_OPT_PERSISTENT = 8,
   STDD_OPT_SWEEP_WAIT = 9,
   STDD_OPT_UPDATE_TILE = 10,
-  STDD_OPT_SYMMETRIC = 11
+  STDD_OPT_SYMMETRIC = 11,
+  STDD_OPT_FP64_TC = 12
 };
 stdd_status stdd_set_option(stdd_ctx *ctx, int option, int value);
 stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);
@@ -424,6 +439,19 @@ stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);
  * complex product, and scaled back by 2^-(ea+eb).  STDD_ETIMEOUT if the
  * tile's bounded wait gave up.  No counterpart in the paper. */
 stdd_status stdd_tc_tile_product(int device, int fmt, int kc, const double *C, const double *R, double *D);
+
+/* Diagnostic: one 64 x 64 complex128 tile product D = C R through the
+ * exact-splitting tensor-core path of STDD_OPT_FP64_TC, with host arrays:
+ * C 64 x kc, R kc x 64, D 64 x 64, column-major interleaved doubles (C(i, j)
+ * at 2 (j*64 + i), R(j, c) at 2 (c*kc + j), D(i, c) at 2 (c*64 + i));
+ * 1 <= kc <= 32.  Each real row of the embedded C ([Re, -Im] and [Im, Re]
+ * rows of complex row i) and each complex column of R is scaled by the power
+ * of two just above its largest |component| and cut into eight 7-bit
+ * slices; D(i, c) is exact up to the dropped slice orders (below 2^-53 of
+ * the scales times 2 kc) and one rounding to FP64.  STDD_EINVAL for
+ * non-finite inputs or kc out of range, STDD_ETIMEOUT if the tile's bounded
+ * wait gave up.  No counterpart in the paper. */
+stdd_status stdd_tc_f64_tile_product(int device, int kc, const double *C, const double *R, double *D);
 
 /* Host-only nested-dissection analysis of one W x H box (no GPU needed).
  * First call with nodes == NULL to get *nfronts and *nnodes; then call

@@ -86,6 +86,7 @@ _SIGS = {
     "stdd_set_option": (c_int, [c_void_p, c_int, c_int]),
     "stdd_get_profile": (c_int, [c_void_p, P(stdd_profile), c_int]),
     "stdd_tc_tile_product": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "stdd_tc_f64_tile_product": (c_int, [c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "stdd_nd_analyze": (c_int, [c_int, c_int, c_int, P(c_int), P(ctypes.c_longlong), c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_void_p]),
     "stdd_nn_create": (c_int, [P(c_void_p), c_int, c_void_p, c_int, c_int, c_int, c_int, ctypes.c_ulonglong]),
@@ -301,6 +302,7 @@ STDD_OPT_PERSISTENT = 8
 STDD_OPT_SWEEP_WAIT = 9
 STDD_OPT_UPDATE_TILE = 10
 STDD_OPT_SYMMETRIC = 11
+STDD_OPT_FP64_TC = 12
 
 
 def stdd_set_profiling(ctx, level=1):
@@ -334,6 +336,25 @@ def stdd_tc_tile_product(C, R, fmt=1, device=0):
                                   c_void_p(Rf.ctypes.data), c_void_p(D.ctypes.data))
     if st != STDD_OK:
         raise StddError(st, "stdd_tc_tile_product failed")
+    return D.T.copy()
+
+
+def stdd_tc_f64_tile_product(C, R, device=0):
+    """D = C R in complex128 through the exact-splitting tensor-core path of
+    the complex128 front update: C complex (64, kc), R complex (kc, 64),
+    1 <= kc <= 32; returns D complex (64, 64)."""
+    C = np.asarray(C, np.complex128)
+    R = np.asarray(R, np.complex128)
+    kc = C.shape[1]
+    if C.shape != (64, kc) or R.shape != (kc, 64):
+        raise ValueError("C must be 64 x kc and R kc x 64")
+    Cf = np.ascontiguousarray(C.T)
+    Rf = np.ascontiguousarray(R.T)
+    D = np.empty((64, 64), np.complex128)   # column-major D (rows of this array are D's columns)
+    st = lib.stdd_tc_f64_tile_product(int(device), int(kc), c_void_p(Cf.ctypes.data), c_void_p(Rf.ctypes.data),
+                                      c_void_p(D.ctypes.data))
+    if st != STDD_OK:
+        raise StddError(st, "stdd_tc_f64_tile_product failed")
     return D.T.copy()
 
 

@@ -211,6 +211,10 @@ struct stdd_ctx {
   // nor with the tensor-core updates (which update whole tiles)
   int symmetric = 1;
   bool sym_active() const { return symmetric && !pivoting && tc_fmt() < 0; }
+  // complex128 symmetric form: large-front updates on the tensor cores by
+  // exact splitting (STDD_OPT_FP64_TC)
+  int fp64_tc = 1;
+  bool oz_active() const { return fp64_tc && sym_active() && prec == STDD_PREC_FP64; }
   DBuf d_lsx, d_lsy;
   int64_t nfronts = 0, factor_entries = 0;
   double factor_cflops = 0, factor_cflops_lu = 0, solve_cflops = 0;
@@ -281,6 +285,7 @@ struct stdd_ctx {
   std::vector<std::vector<double>> exec_update;             // per level, per step
   std::vector<std::vector<double>> unit_update_sym, exec_update_sym;  // the symmetric form's
   std::vector<double> unit_small_sym, exec_small_sym;
+  std::vector<std::vector<double>> exec_update_oz;          // BF16 tensor flops of the split update
   std::vector<double> span_units, span_exec;                // parallel to spans
   std::vector<int> span_level;                              // parallel to spans
   struct Hook : stdd::LaunchHook {
@@ -299,7 +304,7 @@ struct stdd_ctx {
       } else if (kind == stdd::K_UPDATE) {
         const bool sy = c->sym_active();
         u = (sy ? c->unit_update_sym : c->unit_update)[level][k / stdd::MF_NB];
-        x = (sy ? c->exec_update_sym : c->exec_update)[level][k / stdd::MF_NB];
+        x = (c->oz_active() ? c->exec_update_oz : sy ? c->exec_update_sym : c->exec_update)[level][k / stdd::MF_NB];
       } else if (kind == stdd::K_UP) {
         u = x = c->unit_up[level];
       } else {
@@ -600,6 +605,7 @@ MfArgs stdd_ctx::mf_args(int par, bool solve) const {
   a.pcol = pivoting ? d_pcol.as<int>() : nullptr;
   a.panel = pivoting ? d_panel.p : nullptr;
   a.sym = sym_active() ? 1 : 0;
+  a.fp64_tc = oz_active() ? 1 : 0;
   a.lsx = a.sym ? d_lsx.as<double2>() : nullptr;
   a.lsy = a.sym ? d_lsy.as<double2>() : nullptr;
   (void)solve;
@@ -863,12 +869,14 @@ void stdd_ctx::build_structure() {
     exec_update.assign(depth, {});
     unit_update_sym.assign(depth, {});
     exec_update_sym.assign(depth, {});
+    exec_update_oz.assign(depth, {});
     for (int L = 0; L < depth; ++L) {
       const LevelInfo &li = levels[L];
       unit_update[L].assign((li.max_p + stdd::MF_NB - 1) / stdd::MF_NB + 1, 0.0);
       exec_update[L].assign(unit_update[L].size(), 0.0);
       unit_update_sym[L].assign(unit_update[L].size(), 0.0);
       exec_update_sym[L].assign(unit_update[L].size(), 0.0);
+      exec_update_oz[L].assign(unit_update[L].size(), 0.0);
       for (int f = li.f0; f < li.f0 + li.nf; ++f) {
         const double p = fr[f].p, b = fr[f].b, n = p + b;
         unit_up[L] += E * b * p;
@@ -889,6 +897,10 @@ void stdd_ctx::build_structure() {
             // symmetric form: one triangle with its diagonal
             exec_update_sym[L][k / stdd::MF_NB] += 8.0 * me * (me + 1) / 2 * nbk;
             unit_update_sym[L][k / stdd::MF_NB] += 8.0 * mt * (mt + 1) / 2 * nbk;
+            // split tensor-core update: 64 x 64 complex tiles on and below the
+            // diagonal, each 36 BF16 products of 128 x 64 x 64 (real)
+            const double nto = std::ceil(me / 64.0);
+            exec_update_oz[L][k / stdd::MF_NB] += nto * (nto + 1) / 2 * 36.0 * 2.0 * 128 * 64 * 64;
           }
         }
       }
@@ -1064,6 +1076,10 @@ void stdd_ctx::factor_prepare() {
 // two extra ones).
 template <typename R> void stdd_ctx::tune_update_tiles() {
   if (tc_fmt() >= 0) return;
+  if (sizeof(R) == 8 && oz_active()) {   // one tile shape on the tensor cores
+    for (auto &li : levels) li.upd_tile = 64;
+    return;
+  }
   if (forced_tile) {
     for (auto &li : levels) li.upd_tile = forced_tile;
     return;
@@ -2422,6 +2438,14 @@ stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
           c->clear_graphs();
         }
         break;
+      case STDD_OPT_FP64_TC:
+        if (value < 0 || value > 1) throw ArgError("fp64 tensor-core updates must be 0 (off) or 1 (on)");
+        if (value != c->fp64_tc) {
+          c->fp64_tc = value;
+          c->invalidate_factors();
+          c->clear_graphs();
+        }
+        break;
       case STDD_OPT_STATIC_PIVOT:
         if (value < 0 || value > 15) throw ArgError("static pivot exponent must be 0 .. 15");
         if (value != c->static_pivot) {
@@ -2555,6 +2579,24 @@ stdd_status stdd_tc_tile_product(int device, int fmt, int kc, const double *C, c
     D[2 * i] = d[i].x;
     D[2 * i + 1] = d[i].y;
   }
+  return STDD_OK;
+}
+
+stdd_status stdd_tc_f64_tile_product(int device, int kc, const double *C, const double *R, double *D) {
+  if (!C || !R || !D || kc < 1 || kc > stdd::MF_NB) return STDD_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return STDD_ECUDA;
+  }
+  cudaError_t e = cudaSuccess;
+  const int st = stdd::oz_tile_product(kc, reinterpret_cast<const double2 *>(C),
+                                       reinterpret_cast<const double2 *>(R), reinterpret_cast<double2 *>(D), &e);
+  if (st < 0) {
+    (void)cudaGetLastError();
+    return STDD_ECUDA;
+  }
+  if (st == 1) return STDD_ETIMEOUT;
+  if (st == 2) return STDD_EINVAL;
   return STDD_OK;
 }
 

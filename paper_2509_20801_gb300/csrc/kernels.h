@@ -51,6 +51,9 @@ struct MfArgs {
   // indexed like cxm / cym.
   const double2 *lsx, *lsy;
   int sym;
+  // complex128 symmetric form: 1 = large-front updates on the tensor cores
+  // by exact splitting into BF16 slices (FP64 accuracy), 0 = FP64 pipe
+  int fp64_tc;
 };
 
 struct LevelInfo {
@@ -85,6 +88,9 @@ void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_
 // ---- tensor-core front updates (kernels_tc.cu), complex64 fronts only
 cudaError_t tc_setup_attributes();
 void mf_tc_update_launch(const MfArgs &a, const LevelInfo &L, int k, int fmt, cudaStream_t st);
+// symmetric form, complex128: the update on the BF16 tensor cores by exact splitting
+void mf_oz_update_launch(const MfArgs &a, const LevelInfo &L, int k, cudaStream_t st);
+int oz_tile_product(int kc, const double2 *C, const double2 *R, double2 *D, cudaError_t *err);
 // one 64 x kc by kc x 128 complex tile product on the tensor cores from host
 // arrays: 0 ok, 1 wait timed out, -1 CUDA error (*err)
 int tc_tile_product(int fmt, int kc, const float2 *C, const float2 *R, float2 *D, cudaError_t *err);

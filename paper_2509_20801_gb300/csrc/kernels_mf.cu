@@ -1345,6 +1345,8 @@ void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_
       if (hook) hook->before(K_UPDATE, level, k);
       if (tc_fmt >= 0 && sizeof(R) == 4) {
         mf_tc_update_launch(a, L, k, tc_fmt, st);
+      } else if (a.sym && a.fp64_tc && sizeof(R) == 8) {
+        mf_oz_update_launch(a, L, k, st);
       } else if (a.sym) {
         const int tm = L.upd_tile == 32 ? 32 : 64, nts = std::max(1, (m + tm - 1) / tm);
         const size_t sm = sizeof(typename CT<R>::T) * (tm * (MF_NB + 1) + MF_NB * (tm + 1));

@@ -212,6 +212,301 @@ __global__ void __launch_bounds__(128) mf_gj_update_tc(MfArgs a, int f0, int k) 
   if (!tc_tile<FMT>(sm, nbk, cload, rload, sink) && threadIdx.x == 0) atomicOr(a.flag, 2);
 }
 
+// ===================================================== FP64 on BF16 units
+// The complex128 front update C R (C: 64 x kc, R: kc x 64, kc <= 32) on the
+// BF16 tensor cores with FP64 accuracy, by exact splitting (the scheme of
+// Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59 (2012) 95-118): every
+// real row of the 2 x 2 embedding of C and every real column of R is scaled
+// by a power of two 2^-e (|x| < 2^e over the row / column) and cut into
+// OZ_S = 8 fixed-point slices of 7 bits,
+//     x = 2^e sum_{i<8} a_i 2^(-7 (i + 1)),   a_i integer, |a_i| <= 127,
+// each exactly a BF16 number.  A product of two slices is an integer below
+// 2^14 in modulus, a K = 64 dot product of them below 2^20, and the sum of
+// the g + 1 slice products of one order g = i + j (at most 8) below 2^23:
+// all exact in the FP32 accumulators.  Orders g = 0..7 keep everything down
+// to 2^-63 relative to the row and column scales (the dropped orders weigh
+// less than 2^-53 of them, as in an FP64 dot product's error bound), each
+// order summed in its own TMEM accumulator (8 x 64 columns = the SM's 512)
+// by its 4 (g + 1) MMAs of K = 16.  The eight FP32 sums, exact integers, are
+// combined in 64-bit integer arithmetic and rounded to FP64 once:
+//     hi = sum_{g<4} G_g 2^(7 (3 - g)),   lo = sum_{g>=4} G_g 2^(7 (7 - g)),
+//     V = hi 2^20 + floor(lo / 2^8),      value = V 2^(eA + eB - 55).
+// Only the epilogue's add to the front uses the FP64 pipe.
+constexpr int OZ_S = 8;                   // slices per operand value
+constexpr int OZ_MC = 64;                 // complex rows and complex columns per tile
+constexpr int OZ_ABYTES = 128 * 64 * 2;   // one A slice: 128 real rows x 64 real K, BF16
+constexpr int OZ_BBYTES = 64 * 64 * 2;    // one B slice: 64 columns x 64 real K, BF16
+constexpr uint32_t OZ_TMEM_COLS = 512;    // 8 accumulators x 64 columns
+constexpr int OZ_EMPTY = -2000;           // exponent of an all-zero row or column
+
+struct OzSmem {
+  uint8_t A[OZ_S][OZ_ABYTES];
+  uint8_t B[OZ_S][OZ_BBYTES];
+  int eA[OZ_MC], eB[OZ_MC];
+  int red[128];
+  unsigned long long mbar;
+  uint32_t tmem;
+  int bad;
+};
+
+// frexp exponent of x (|x| < 2^e) from its bits; OZ_EMPTY for zero and
+// subnormals (below every scale that matters here), 1025 for inf / NaN
+__device__ __forceinline__ int oz_exp(double x) {
+  const int ef = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+  return ef == 0 ? OZ_EMPTY : ef - 1022;
+}
+
+// the 8 slices of x / 2^er (|x| < 2^er) as BF16 bit patterns: the 56-bit
+// fixed-point magnitude Y = floor(|x| 2^(56 - er)) cut into 7-bit chunks
+// from the top, each converted exactly (2^23 + c - 2^23 in FP32, whose low
+// 16 bits are zero for c < 128), with the sign of x
+__device__ __forceinline__ void oz_slice(double x, int er, uint32_t (&s)[OZ_S]) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int ef = (int)((u >> 52) & 0x7ff);
+  unsigned long long Y = 0;
+  if (ef != 0 && ef != 0x7ff) {
+    const unsigned long long M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // |x| = M 2^(ef - 1075)
+    const int sh = er - (ef - 1022) - 3;                                   // Y = M 2^-sh, sh >= -3
+    Y = sh >= 0 ? (sh < 64 ? M >> sh : 0ull) : M << (-sh);
+  }
+  const uint32_t sgn = (uint32_t)(u >> 63) << 15;
+#pragma unroll
+  for (int i = 0; i < OZ_S; ++i) {
+    const int c = (int)((Y >> (49 - 7 * i)) & 127);
+    const float f = __int_as_float(0x4B000000 | c) - 8388608.0f;
+    s[i] = (__float_as_uint(f) >> 16) | sgn;
+  }
+}
+
+// One 64 x 64 complex tile of C R.  cload(rr, j) gives C(rr, j) and
+// rload(cc, j) R(j, cc) for j < kc (zero where the tile runs past the
+// matrix); sink(rr, cc, comp, V, e) receives component comp of (C R)(rr, cc)
+// as V 2^e (V a 64-bit integer; e meaningless when V = 0).  Returns false if
+// the completion wait timed out (then nothing reached the sink).
+template <typename CLoad, typename RLoad, typename Sink>
+__device__ bool oz_tile(OzSmem &sm, int kc, CLoad cload, RLoad rload, Sink sink) {
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int rr = t & 63, half = t >> 6;   // staging: row / column rr, pivots [16 half, 16 half + 16)
+  if (warp == 0) tcx::tmem_alloc(smem_u32(&sm.tmem), OZ_TMEM_COLS);
+  if (t == 0) {
+    tcx::mbar_init(smem_u32(&sm.mbar), 1);
+    sm.bad = 0;
+  }
+  // ---- A = the embedded C: real row 2rr = [Cr, -Ci], 2rr + 1 = [Ci, Cr]
+  {
+    double2 v[16];
+    int em = OZ_EMPTY;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int j = 16 * half + q;
+      v[q] = j < kc ? cload(rr, j) : make_double2(0.0, 0.0);
+      em = max(em, max(oz_exp(v[q].x), oz_exp(v[q].y)));
+    }
+    sm.red[t] = em;
+    __syncthreads();
+    const int er = max(sm.red[rr], sm.red[rr + 64]);
+    if (half == 0) sm.eA[rr] = er;
+    if (er > 1024) sm.bad = 1;
+#pragma unroll
+    for (int q0 = 0; q0 < 16; q0 += 4) {
+      uint32_t re[4][OZ_S], im[4][OZ_S];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        oz_slice(v[q0 + q].x, er, re[q]);
+        oz_slice(v[q0 + q].y, er, im[q]);
+      }
+      const int k0 = 2 * (16 * half + q0);   // real K of this 16-byte chunk (a multiple of 8)
+#pragma unroll
+      for (int i = 0; i < OZ_S; ++i) {
+        uint4 w0, w1;
+        w0.x = re[0][i] | ((im[0][i] ^ 0x8000u) << 16);
+        w0.y = re[1][i] | ((im[1][i] ^ 0x8000u) << 16);
+        w0.z = re[2][i] | ((im[2][i] ^ 0x8000u) << 16);
+        w0.w = re[3][i] | ((im[3][i] ^ 0x8000u) << 16);
+        w1.x = im[0][i] | (re[0][i] << 16);
+        w1.y = im[1][i] | (re[1][i] << 16);
+        w1.z = im[2][i] | (re[2][i] << 16);
+        w1.w = im[3][i] | (re[3][i] << 16);
+        *reinterpret_cast<uint4 *>(sm.A[i] + op_off(2 * rr, k0)) = w0;
+        *reinterpret_cast<uint4 *>(sm.A[i] + op_off(2 * rr + 1, k0)) = w1;
+      }
+    }
+  }
+  __syncthreads();   // sm.red is reused
+  // ---- B = R as 64 rows (complex columns cc) of K = [Rr, Ri] per pivot
+  {
+    double2 v[16];
+    int em = OZ_EMPTY;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int j = 16 * half + q;
+      v[q] = j < kc ? rload(rr, j) : make_double2(0.0, 0.0);
+      em = max(em, max(oz_exp(v[q].x), oz_exp(v[q].y)));
+    }
+    sm.red[t] = em;
+    __syncthreads();
+    const int ec = max(sm.red[rr], sm.red[rr + 64]);
+    if (half == 0) sm.eB[rr] = ec;
+    if (ec > 1024) sm.bad = 1;
+#pragma unroll
+    for (int q0 = 0; q0 < 16; q0 += 4) {
+      uint32_t re[4][OZ_S], im[4][OZ_S];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        oz_slice(v[q0 + q].x, ec, re[q]);
+        oz_slice(v[q0 + q].y, ec, im[q]);
+      }
+      const int k0 = 2 * (16 * half + q0);
+#pragma unroll
+      for (int i = 0; i < OZ_S; ++i) {
+        uint4 w;
+        w.x = re[0][i] | (im[0][i] << 16);
+        w.y = re[1][i] | (im[1][i] << 16);
+        w.z = re[2][i] | (im[2][i] << 16);
+        w.w = re[3][i] | (im[3][i] << 16);
+        *reinterpret_cast<uint4 *>(sm.B[i] + op_off(rr, k0)) = w;
+      }
+    }
+  }
+  tcx::fence_proxy_async();
+  tcx::fence_before();
+  __syncthreads();
+  tcx::fence_after();
+  const uint32_t tmem = sm.tmem;
+  if (t == 0) {
+    const uint32_t idesc = tcx::instr_desc_f16(1, 128, OZ_MC);
+#pragma unroll 1
+    for (int g = 0; g < OZ_S; ++g) {
+#pragma unroll 1
+      for (int i = 0; i <= g; ++i) {
+        const uint32_t a0 = smem_u32(sm.A[i]), b0 = smem_u32(sm.B[g - i]);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          tcx::mma_f16(tmem + (uint32_t)(OZ_MC * g), smem_desc(a0 + s * 256), smem_desc(b0 + s * 256), idesc,
+                       (i == 0 && s == 0) ? 0u : 1u);
+      }
+    }
+    tcx::mma_commit(smem_u32(&sm.mbar));
+  }
+  bool done = tcx::mbar_wait(smem_u32(&sm.mbar), 0, TC_WAIT_LIMIT);
+  tcx::fence_after();
+  if (done && !sm.bad) {
+    const int drow = warp * 32 + lane, er = drow >> 1, comp = drow & 1;
+#pragma unroll 1
+    for (int cb = 0; cb < OZ_MC; cb += 16) {
+      long long hi[16], lo[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) hi[u] = lo[u] = 0;
+#pragma unroll
+      for (int g = 0; g < OZ_S; ++g) {
+        uint32_t vv[16];
+        tcx::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(OZ_MC * g + cb), vv);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const long long G = __float2int_rn(__uint_as_float(vv[u]));
+          if (g < 4) hi[u] += G * (1ll << (7 * (3 - g)));
+          else lo[u] += G * (1ll << (7 * (7 - g)));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const long long V = hi[u] * (1ll << 20) + (lo[u] >> 8);   // arithmetic shift: floor
+        sink(er, cb + u, comp, V, sm.eA[er] + sm.eB[cb + u] - 55);
+      }
+    }
+  } else if (!done) {
+    // let the MMAs in flight finish (bounded) before the memory they write is freed
+    tcx::mbar_wait(smem_u32(&sm.mbar), 0, TC_WAIT_LIMIT);
+  }
+  tcx::fence_before();
+  __syncthreads();
+  if (warp == 0) tcx::tmem_dealloc(tmem, OZ_TMEM_COLS);
+  return done;
+}
+
+// V 2^e as a double (V = 0 gives 0): one rounding of V, then an exact scale
+__device__ __forceinline__ double oz_value(long long V, int e) {
+  if (V == 0) return 0.0;
+  e = max(-1022, min(1023, e));
+  return __ll2double_rn(V) * __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+__device__ __forceinline__ double2 *front_ptr64(const MfArgs &a, const FrontDev &f, int r, int c) {
+  const int p = f.p, b = f.b, n = p + b;
+  double2 *fac = reinterpret_cast<double2 *>(a.fac);
+  if (r < p) return fac + f.fac_off + (int64_t)c * p + r;
+  if (c < p) return fac + f.fac_off + (int64_t)p * n + (int64_t)c * b + (r - p);
+  return reinterpret_cast<double2 *>(a.ws_cur) + f.s_off + (int64_t)(c - p) * b + (r - p);
+}
+
+// Symmetric form, step k of every large front on the tensor cores: the
+// tiles on and below the diagonal of the trailing update (64 x 64 complex,
+// tile order skipping the pivot band), lower entries added to the front and
+// their signed mirrors stored, as mf_gj_update_sym does on the FP64 pipe.
+// grid = (fronts, nt (nt + 1) / 2 tiles).
+__global__ void __launch_bounds__(128, 1) mf_gj_update_oz(MfArgs a, int f0, int k) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  OzSmem &sm = *reinterpret_cast<OzSmem *>(smem_raw);
+  const FrontDev f = a.fronts[f0 + blockIdx.x];
+  const int p = f.p, n = p + f.b;
+  if (n <= MF_SMALL || k >= p) return;
+  const int nbk = min(MF_NB, p - k);
+  const int m = n - nbk;
+  const int nt = (m + OZ_MC - 1) / OZ_MC;
+  const int y = blockIdx.y;
+  if (y >= nt * (nt + 1) / 2) return;
+  int ti = (int)((sqrtf(8.f * y + 1.f) - 1.f) * 0.5f);
+  while ((ti + 1) * (ti + 2) / 2 <= y) ++ti;
+  while (ti * (ti + 1) / 2 > y) --ti;
+  const int tj = y - ti * (ti + 1) / 2;
+  const int i0 = ti * OZ_MC, j0 = tj * OZ_MC;
+  const double2 *fac = reinterpret_cast<const double2 *>(a.fac);
+  const int64_t fo = f.fac_off;
+  auto cload = [&](int rr, int j) -> double2 {
+    const int ri = i0 + rr;
+    return ri < m ? *front_ptr64(a, f, unband_tc(ri, k, nbk), k + j) : make_double2(0.0, 0.0);
+  };
+  auto rload = [&](int cc, int j) -> double2 {
+    const int ci = j0 + cc;
+    return ci < m ? fac[fo + (int64_t)unband_tc(ci, k, nbk) * p + k + j] : make_double2(0.0, 0.0);
+  };
+  auto sink = [&](int rr, int cc, int comp, long long V, int e) {
+    const int ri = i0 + rr, ci = j0 + cc;
+    if (ri >= m || ci > ri) return;   // past the front, or an upper entry of a diagonal tile
+    const int r = unband_tc(ri, k, nbk), c = unband_tc(ci, k, nbk);
+    double *x = reinterpret_cast<double *>(front_ptr64(a, f, r, c)) + comp;
+    const double v = *x + oz_value(V, e);
+    *x = v;
+    if (ci < ri) {
+      const bool neg = (r < k) != (c < k);
+      reinterpret_cast<double *>(front_ptr64(a, f, c, r))[comp] = neg ? -v : v;
+    }
+  };
+  const bool ok = oz_tile(sm, nbk, cload, rload, sink);
+  if (threadIdx.x == 0) {
+    if (!ok) atomicOr(a.flag, 2);
+    else if (sm.bad) atomicOr(a.flag, 1);
+  }
+}
+
+// One tile D = C R in complex128 (C(rr, j) at j * 64 + rr, R(j, cc) at
+// cc * kc + j, D(rr, cc) at cc * 64 + rr), through oz_tile.
+__global__ void __launch_bounds__(128, 1) oz_tile_kernel(const double2 *C, const double2 *R, double2 *D, int kc,
+                                                         int *flag) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  OzSmem &sm = *reinterpret_cast<OzSmem *>(smem_raw);
+  auto cload = [&](int rr, int j) { return C[j * OZ_MC + rr]; };
+  auto rload = [&](int cc, int j) { return R[cc * kc + j]; };
+  auto sink = [&](int rr, int cc, int comp, long long V, int e) {
+    reinterpret_cast<double *>(&D[cc * OZ_MC + rr])[comp] = oz_value(V, e);
+  };
+  const bool ok = oz_tile(sm, kc, cload, rload, sink);
+  if (threadIdx.x == 0) {
+    if (!ok) atomicOr(flag, 2);
+    else if (sm.bad) atomicOr(flag, 1);
+  }
+}
+
 // One tile D = C R with C (64 x kc) and R (kc x 128) complex, column-major
 // (C(rr, j) at j * 64 + rr, R(j, cc) at cc * kc + j, D(rr, cc) at cc * 64 + rr).
 template <int FMT>
@@ -239,10 +534,23 @@ template <int FMT> cudaError_t tc_setup_attributes_fmt() {
                               (int)tc_smem_bytes());
 }
 
+size_t oz_smem_bytes() { return sizeof(OzSmem) + 1024; }
+
 cudaError_t tc_setup_attributes() {
   cudaError_t e = tc_setup_attributes_fmt<0>();
   if (e != cudaSuccess) return e;
-  return tc_setup_attributes_fmt<1>();
+  e = tc_setup_attributes_fmt<1>();
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(mf_gj_update_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(oz_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+}
+
+void mf_oz_update_launch(const MfArgs &a, const LevelInfo &L, int k, cudaStream_t st) {
+  const int m = L.max_n - std::min(MF_NB, std::max(1, L.max_p - k));
+  const int nt = std::max(1, (m + OZ_MC - 1) / OZ_MC);
+  mf_gj_update_oz<<<dim3(L.nf, nt * (nt + 1) / 2), 128, oz_smem_bytes(), st>>>(a, L.f0, k);
+  count_launch();
 }
 
 void mf_tc_update_launch(const MfArgs &a, const LevelInfo &L, int k, int fmt, cudaStream_t st) {
@@ -251,6 +559,42 @@ void mf_tc_update_launch(const MfArgs &a, const LevelInfo &L, int k, int fmt, cu
   if (fmt == 1) mf_gj_update_tc<1><<<dim3(L.nf, tiles), 128, tc_smem_bytes(), st>>>(a, L.f0, k);
   else mf_gj_update_tc<0><<<dim3(L.nf, tiles), 128, tc_smem_bytes(), st>>>(a, L.f0, k);
   count_launch();
+}
+
+// One complex128 tile product through the exact-splitting tensor-core path
+// (see oz_tile_kernel for the layouts); returns 0 on success, 1 if the device
+// reported a timeout, 2 for a non-finite input, -1 on a CUDA error (*err).
+int oz_tile_product(int kc, const double2 *C, const double2 *R, double2 *D, cudaError_t *err) {
+  const size_t nc = (size_t)OZ_MC * kc, nr = (size_t)kc * OZ_MC, nd = (size_t)OZ_MC * OZ_MC;
+  double2 *dC = nullptr, *dR = nullptr, *dD = nullptr;
+  int *dflag = nullptr;
+  *err = cudaSuccess;
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess && *err == cudaSuccess) *err = e;
+    return e == cudaSuccess;
+  };
+  bool ok = ck(tc_setup_attributes()) && ck(cudaMalloc(&dC, std::max<size_t>(1, nc) * sizeof(double2))) &&
+            ck(cudaMalloc(&dR, std::max<size_t>(1, nr) * sizeof(double2))) &&
+            ck(cudaMalloc(&dD, nd * sizeof(double2))) && ck(cudaMalloc(&dflag, sizeof(int)));
+  int flag = 0;
+  if (ok) {
+    ok = (nc == 0 || ck(cudaMemcpy(dC, C, nc * sizeof(double2), cudaMemcpyHostToDevice))) &&
+         (nr == 0 || ck(cudaMemcpy(dR, R, nr * sizeof(double2), cudaMemcpyHostToDevice))) &&
+         ck(cudaMemset(dD, 0, nd * sizeof(double2))) && ck(cudaMemset(dflag, 0, sizeof(int)));
+  }
+  if (ok) {
+    oz_tile_kernel<<<1, 128, oz_smem_bytes()>>>(dC, dR, dD, kc, dflag);
+    count_launch();
+    ok = ck(cudaGetLastError()) && ck(cudaDeviceSynchronize()) &&
+         ck(cudaMemcpy(D, dD, nd * sizeof(double2), cudaMemcpyDeviceToHost)) &&
+         ck(cudaMemcpy(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost));
+  }
+  cudaFree(dC);
+  cudaFree(dR);
+  cudaFree(dD);
+  cudaFree(dflag);
+  if (!ok) return -1;
+  return (flag & 2) ? 1 : ((flag & 1) ? 2 : 0);
 }
 
 // One tile product on the device from host arrays (see tc_tile_kernel for

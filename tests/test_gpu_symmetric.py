@@ -24,11 +24,12 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def _solver(w, sym, precision=0, leaf=None, tile=None, pivoting=0):
-    from paper_2509_20801_gb300 import (STDD_OPT_LEAF, STDD_OPT_PIVOTING, STDD_OPT_SYMMETRIC,
+def _solver(w, sym, precision=0, leaf=None, tile=None, pivoting=0, fp64_tc=0):
+    from paper_2509_20801_gb300 import (STDD_OPT_FP64_TC, STDD_OPT_LEAF, STDD_OPT_PIVOTING, STDD_OPT_SYMMETRIC,
                                         STDD_OPT_UPDATE_TILE, Solver, stdd_set_option)
     s = Solver.from_workload(w, eps=torch.from_numpy(w.eps_node).to(DEV), precision=precision)
     stdd_set_option(s.ctx, STDD_OPT_SYMMETRIC, sym)
+    stdd_set_option(s.ctx, STDD_OPT_FP64_TC, fp64_tc)
     if leaf is not None:
         stdd_set_option(s.ctx, STDD_OPT_LEAF, leaf)
     if tile is not None:
@@ -52,11 +53,14 @@ def cyl():
     return w, P, DDM.from_workload(w, P)
 
 
+@pytest.mark.parametrize("fp64_tc", [0, 1])
 @pytest.mark.parametrize("which,leaf", [("rnd", None), ("cyl", None), ("cyl", 64)])
-def test_symmetric_local_solves_and_preconditioner_match_oracle(which, leaf, rnd, cyl):
+def test_symmetric_local_solves_and_preconditioner_match_oracle(which, leaf, fp64_tc, rnd, cyl):
+    """fp64_tc = 1: the large-front updates on the tensor cores by exact
+    splitting, to the same FP64 bars."""
     from paper_2509_20801_gb300 import stdd_apply_preconditioner, stdd_local_solve
     w, P, D = {"rnd": rnd, "cyl": cyl}[which]
-    s = _solver(w, 1, leaf=leaf)
+    s = _solver(w, 1, leaf=leaf, fp64_tc=fp64_tc)
     s.factor()
     for k, st in enumerate(D.strips):
         t = W.random_vector(st.width * P.ny, seed=50 + k)[0]
@@ -171,3 +175,30 @@ def test_symmetric_toggle_refactors_through_the_graph(rnd):
         stdd_set_option(s.ctx, STDD_OPT_SYMMETRIC, 2)
     assert e.value.status == 1
     s.close()
+
+
+def test_fp64_tensor_core_update_runs_and_is_deterministic(cyl):
+    """With STDD_OPT_FP64_TC the profile's executed update work is the BF16
+    tensor-core count (36 slice products per tile, far above the FP64
+    count); repeated factorizations are bitwise equal; M^-1 matches the
+    FP64-pipe factors to the FP64 bar."""
+    from paper_2509_20801_gb300 import stdd_apply_preconditioner, stdd_get_profile, stdd_set_profiling
+    w, P, D = cyl
+    v = torch.from_numpy(W.random_vector(P.n, seed=56)[0]).to(DEV)
+    outs, work = {}, {}
+    for tc in (1, 1, 0):
+        s = _solver(w, 1, leaf=64, fp64_tc=tc)
+        stdd_set_profiling(s.ctx, 2)
+        s.factor()
+        prof = stdd_get_profile(s.ctx, 1)
+        work[tc] = (prof["update_flops"], prof["update_flops_executed"])
+        z = torch.empty_like(v)
+        stdd_apply_preconditioner(s.ctx, v, z)
+        if tc in outs:
+            assert np.array_equal(outs[tc], z.cpu().numpy())
+        outs[tc] = z.cpu().numpy()
+        s.close()
+    assert work[1][0] == work[0][0]                      # same LDL^T units
+    assert work[1][1] > 10 * work[0][1]                  # tensor-core slice products executed
+    assert _rel(outs[1], outs[0]) < 1e-11
+    assert _rel(outs[1], D.apply_Minv(v.cpu().numpy())) < 1e-10

@@ -86,3 +86,61 @@ def test_solve_with_tensor_core_updates(mode):
     ref = P.solve(b)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-7
     s.close()
+
+
+# ---------------------------------------------------------------- complex128
+# The exact-splitting path of the complex128 update (STDD_OPT_FP64_TC):
+# eight 7-bit BF16 slices per value, scaled per real row of the embedded C
+# and per complex column of R; the expected values are computed here.
+
+def _row_col_scales(C, R):
+    """2^e per complex row of C and per complex column of R, |x| < 2^e over
+    both components (frexp exponents)."""
+    def e(v):
+        m = np.max(np.abs(np.concatenate([v.real, v.imag], axis=-1)), axis=-1)
+        return np.where(m > 0, np.frexp(m)[1], -1074).astype(np.float64)
+    return np.ldexp(1.0, e(C).astype(int)), np.ldexp(1.0, e(R.T).astype(int))
+
+
+def test_f64_tile_product_exact_on_integers():
+    """Integer entries (products and sums exact in binary64): the split
+    product loses nothing, so D equals the exact product bitwise."""
+    from paper_2509_20801_gb300 import stdd_tc_f64_tile_product
+    rng = np.random.default_rng(5)
+    C = rng.integers(-1000, 1000, (64, 32)) + 1j * rng.integers(-1000, 1000, (64, 32))
+    R = rng.integers(-1000, 1000, (32, 64)) + 1j * rng.integers(-1000, 1000, (32, 64))
+    D = stdd_tc_f64_tile_product(C, R)
+    assert np.array_equal(D, C @ R)
+    # the largest slice values in every position: all group sums at their bound
+    C2 = np.full((64, 32), 127.0 * (1 + 1j))
+    D2 = stdd_tc_f64_tile_product(C2, C2.T.copy())
+    assert np.array_equal(D2, C2 @ C2.T)
+
+
+@pytest.mark.parametrize("kc,spread", [(32, 0), (7, 6), (1, 3), (32, 12)])
+def test_f64_tile_product_error_bound(kc, spread):
+    """Random operands whose rows and columns span 10^+-spread: every entry of
+    D within 4 (2 kc) 2^-53 sC_i sR_j of the float64 product (sC, sR the row
+    and column power-of-two scales; the split product's bound and float64's
+    own rounding each contribute at most half of it), and the relative
+    Frobenius error at the level of float64, far below BF16 (2^-8)."""
+    from paper_2509_20801_gb300 import stdd_tc_f64_tile_product
+    rng = np.random.default_rng(6 + kc + spread)
+    C = (rng.standard_normal((64, kc)) + 1j * rng.standard_normal((64, kc))) * 10.0 ** rng.uniform(-spread, spread, (64, 1))
+    R = (rng.standard_normal((kc, 64)) + 1j * rng.standard_normal((kc, 64))) * 10.0 ** rng.uniform(-spread, spread, (1, 64))
+    D = stdd_tc_f64_tile_product(C, R)
+    ref = C @ R
+    sC, sR = _row_col_scales(C, R)
+    bound = 4 * (2 * kc) * 2.0 ** -53 * np.outer(sC, sR)
+    assert np.all(np.abs(D - ref) <= bound)
+    if spread == 0:
+        assert np.linalg.norm(D - ref) <= 1e-14 * np.linalg.norm(ref)
+
+
+def test_f64_tile_product_refuses_nonfinite_input():
+    from paper_2509_20801_gb300 import StddError, stdd_tc_f64_tile_product
+    C = np.ones((64, 4), complex)
+    C[3, 2] = np.inf
+    with pytest.raises(StddError) as e:
+        stdd_tc_f64_tile_product(C, np.ones((4, 64), complex))
+    assert e.value.status == 1
