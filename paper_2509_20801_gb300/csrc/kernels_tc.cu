@@ -151,6 +151,7 @@ __device__ bool tc_tile(TileSmem &sm, int kc, CLoad cload, RLoad rload, Sink sin
   }
   bool done = false;
   for (long long it = 0; it < TC_WAIT_LIMIT && !done; ++it) done = mbar_try_wait(smem_u32(&sm.mbar), 0);
+  done = __all_sync(0xffffffffu, done);   // the TMEM reads below are warp-collective
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (done) {
     const float inv = ldexpf(1.f, -(ea + eb));
@@ -232,21 +233,31 @@ __global__ void __launch_bounds__(128) mf_gj_update_tc(MfArgs a, int f0, int k) 
 //     hi = sum_{g<4} G_g 2^(7 (3 - g)),   lo = sum_{g>=4} G_g 2^(7 (7 - g)),
 //     V = hi 2^20 + floor(lo / 2^8),      value = V 2^(eA + eB - 55).
 // Only the epilogue's add to the front uses the FP64 pipe.
-constexpr int OZ_S = 8;                   // slices per operand value
-constexpr int OZ_MC = 64;                 // complex rows and complex columns per tile
-constexpr int OZ_ABYTES = 128 * 64 * 2;   // one A slice: 128 real rows x 64 real K, BF16
-constexpr int OZ_BBYTES = 64 * 64 * 2;    // one B slice: 64 columns x 64 real K, BF16
-constexpr uint32_t OZ_TMEM_COLS = 512;    // 8 accumulators x 64 columns
-constexpr int OZ_EMPTY = -2000;           // exponent of an all-zero row or column
+constexpr int OZ_S = 8;                      // slices per operand value
+constexpr int OZ_MR = 64;                    // complex rows per CTA (128 real rows, M = 128)
+constexpr int OZ_NC = 32;                    // complex columns per sub-tile (N = 32)
+constexpr int OZ_CHUNK = 8;                  // sub-tiles per CTA at most
+constexpr int OZ_ABYTES = 128 * 64 * 2;      // one A slice: 128 real rows x 64 real K, BF16
+constexpr int OZ_BBYTES = OZ_NC * 64 * 2;    // one B slice: 32 columns x 64 real K, BF16
+constexpr uint32_t OZ_TMEM_COLS = 512;       // 2 buffers x 8 accumulators x 32 columns
+constexpr int OZ_EMPTY = -2000;              // exponent of an all-zero row or column
+constexpr int OZ_WORKERS = 256;              // 8 warps stage and read out (w and w + 4: TMEM lanes 32 (w % 4))
+constexpr int OZ_THREADS = OZ_WORKERS + 32;  // plus one warp that issues the MMAs
+constexpr int OZ_SINK = 8;                   // columns a thread reads out at a time
 
+// One CTA: the 64 rows of C against up to OZ_CHUNK sub-tiles of 32 columns
+// of R.  C's slices stay in shared memory; R's are staged per sub-tile into
+// one of two buffers, and the MMAs of a sub-tile (into one of two TMEM
+// halves) run while the threads read out the previous sub-tile's sums.
 struct OzSmem {
   uint8_t A[OZ_S][OZ_ABYTES];
-  uint8_t B[OZ_S][OZ_BBYTES];
-  int eA[OZ_MC], eB[OZ_MC];
-  int red[128];
-  unsigned long long mbar;
+  uint8_t B[2][OZ_S][OZ_BBYTES];
+  int eA[OZ_MR];
+  int eB[2][OZ_NC];
+  int red[OZ_WORKERS];
+  unsigned long long bfull[2], tfull[2], tempty[2];
   uint32_t tmem;
-  int bad;
+  int bad;          // bit 0: non-finite operand, bit 1: a completion wait gave up
 };
 
 // frexp exponent of x (|x| < 2^e) from its bits; OZ_EMPTY for zero and
@@ -278,44 +289,62 @@ __device__ __forceinline__ void oz_slice(double x, int er, uint32_t (&s)[OZ_S]) 
   }
 }
 
-// One 64 x 64 complex tile of C R.  cload(rr, j) gives C(rr, j) and
-// rload(cc, j) R(j, cc) for j < kc (zero where the tile runs past the
-// matrix); sink(rr, cc, comp, V, e) receives component comp of (C R)(rr, cc)
-// as V 2^e (V a 64-bit integer; e meaningless when V = 0).  Returns false if
-// the completion wait timed out (then nothing reached the sink).
+// barrier over the 8 staging / read-out warps only (the MMA warp runs on)
+__device__ __forceinline__ void worker_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(OZ_WORKERS) : "memory"); }
+
+// V 2^e as a double: one rounding of V (|V| < 2^62), then the exact power of
+// two added to the exponent field (values below the normal range flush to 0)
+__device__ __forceinline__ double oz_value(long long V, int e) {
+  if (V == 0) return 0.0;
+  const long long b = __double_as_longlong(__ll2double_rn(V));
+  const int ef = (int)((b >> 52) & 0x7ff) + e;
+  if (ef <= 0) return 0.0;
+  if (ef >= 2047) return __longlong_as_double((b & (long long)(1ull << 63)) | 0x7ff0000000000000ll);
+  return __longlong_as_double(b + ((long long)e << 52));
+}
+
+// C R for the 64 rows of C and the columns [0, ncols) of R (ncols <= 256):
+// cload(rr, j) = C(rr, j), rload(cc, j) = R(j, cc) for j < kc (zero where
+// the matrix ends); sink(rr, c0, comp, produce) receives component comp of
+// (C R)(rr, c0 + u), u < OZ_SINK, as add[u] from produce(add) (called once,
+// after the sink has issued the loads it needs).  Returns the OzSmem::bad bits.
 template <typename CLoad, typename RLoad, typename Sink>
-__device__ bool oz_tile(OzSmem &sm, int kc, CLoad cload, RLoad rload, Sink sink) {
+__device__ int oz_rows(OzSmem &sm, int kc, int ncols, CLoad cload, RLoad rload, Sink sink) {
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int rr = t & 63, half = t >> 6;   // staging: row / column rr, pivots [16 half, 16 half + 16)
   if (warp == 0) tcx::tmem_alloc(smem_u32(&sm.tmem), OZ_TMEM_COLS);
   if (t == 0) {
-    tcx::mbar_init(smem_u32(&sm.mbar), 1);
+    for (int b = 0; b < 2; ++b) {
+      tcx::mbar_init(smem_u32(&sm.bfull[b]), OZ_WORKERS);
+      tcx::mbar_init(smem_u32(&sm.tfull[b]), 1);
+      tcx::mbar_init(smem_u32(&sm.tempty[b]), OZ_WORKERS);
+    }
     sm.bad = 0;
   }
   // ---- A = the embedded C: real row 2rr = [Cr, -Ci], 2rr + 1 = [Ci, Cr]
-  {
-    double2 v[16];
+  if (t < OZ_WORKERS) {
+    const int rr = t & 63, quarter = t >> 6;   // pivots [8 quarter, 8 quarter + 8) of row rr
+    double2 v[8];
     int em = OZ_EMPTY;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int j = 16 * half + q;
+    for (int q = 0; q < 8; ++q) {
+      const int j = 8 * quarter + q;
       v[q] = j < kc ? cload(rr, j) : make_double2(0.0, 0.0);
       em = max(em, max(oz_exp(v[q].x), oz_exp(v[q].y)));
     }
     sm.red[t] = em;
-    __syncthreads();
-    const int er = max(sm.red[rr], sm.red[rr + 64]);
-    if (half == 0) sm.eA[rr] = er;
+    worker_sync();
+    const int er = max(max(sm.red[rr], sm.red[rr + 64]), max(sm.red[rr + 128], sm.red[rr + 192]));
+    if (quarter == 0) sm.eA[rr] = er;
     if (er > 1024) sm.bad = 1;
 #pragma unroll
-    for (int q0 = 0; q0 < 16; q0 += 4) {
+    for (int q0 = 0; q0 < 8; q0 += 4) {
       uint32_t re[4][OZ_S], im[4][OZ_S];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         oz_slice(v[q0 + q].x, er, re[q]);
         oz_slice(v[q0 + q].y, er, im[q]);
       }
-      const int k0 = 2 * (16 * half + q0);   // real K of this 16-byte chunk (a multiple of 8)
+      const int k0 = 2 * (8 * quarter + q0);   // real K of this 16-byte chunk (a multiple of 8)
 #pragma unroll
       for (int i = 0; i < OZ_S; ++i) {
         uint4 w0, w1;
@@ -332,103 +361,150 @@ __device__ bool oz_tile(OzSmem &sm, int kc, CLoad cload, RLoad rload, Sink sink)
       }
     }
   }
-  __syncthreads();   // sm.red is reused
-  // ---- B = R as 64 rows (complex columns cc) of K = [Rr, Ri] per pivot
-  {
-    double2 v[16];
-    int em = OZ_EMPTY;
+  const int nsub = (ncols + OZ_NC - 1) / OZ_NC;
+  const uint32_t idesc = tcx::instr_desc_f16(1, 128, OZ_NC);
+  const int drow = (warp & 3) * 32 + lane, er = drow >> 1, comp = drow & 1;
+  const int hsel = warp >> 2;   // warps 0-3 read columns 0-15 of a sub-tile, warps 4-7 columns 16-31
+  // read out sub-tile s: the 8 order sums of 16 columns at a time
+  auto drain = [&](int s) {
+    const int buf = s & 1;
+    // one decision per warp: the reads below are warp-collective
+    const bool ok = __all_sync(0xffffffffu,
+                               tcx::mbar_wait(smem_u32(&sm.tfull[buf]), (uint32_t)((s >> 1) & 1), TC_WAIT_LIMIT));
+    tcx::fence_after();
+    if (!ok && lane == 0) atomicOr(&sm.bad, 2);
+    if (!ok || (__shfl_sync(0xffffffffu, sm.bad, 0) & 1)) return;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      const int h = 16 * hsel + OZ_SINK * pass;
+      // the sink loads what it adds to first, then asks for the values
+      auto produce = [&](double (&add)[OZ_SINK]) {
+        // pairs of orders first, in 32 bits: G_2q 2^7 + G_2q+1 stays below 2^31
+        int pr[4][OZ_SINK];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int j = 16 * half + q;
-      v[q] = j < kc ? rload(rr, j) : make_double2(0.0, 0.0);
-      em = max(em, max(oz_exp(v[q].x), oz_exp(v[q].y)));
+        for (int g = 0; g < OZ_S; ++g) {
+          uint32_t vv[OZ_SINK];
+          tcx::tmem_ld8(sm.tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(256 * buf + OZ_NC * g + h), vv);
+#pragma unroll
+          for (int u = 0; u < OZ_SINK; ++u) {
+            const int G = __float2int_rn(__uint_as_float(vv[u]));
+            if (g & 1) pr[g >> 1][u] += G;
+            else pr[g >> 1][u] = G * 128;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < OZ_SINK; ++u) {
+          const long long hi = (long long)pr[0][u] * (1ll << 14) + pr[1][u];
+          const long long lo = (long long)pr[2][u] * (1ll << 14) + pr[3][u];
+          add[u] = oz_value(hi * (1ll << 20) + (lo >> 8), sm.eA[er] + sm.eB[buf][h + u] - 55);
+        }
+      };
+      sink(er, OZ_NC * s + h, comp, produce);
     }
-    sm.red[t] = em;
-    __syncthreads();
-    const int ec = max(sm.red[rr], sm.red[rr + 64]);
-    if (half == 0) sm.eB[rr] = ec;
-    if (ec > 1024) sm.bad = 1;
+  };
+  tcx::fence_proxy_async();
+  __syncthreads();   // A staged, barriers initialised, TMEM allocated
+  if (warp == OZ_WORKERS / 32) {
+    // ---- the MMA warp: sub-tile s once its B slices are staged and its
+    // TMEM half has been read out (sub-tile s - 2)
+    if (lane == 0) {
+#pragma unroll 1
+      for (int s = 0; s < nsub; ++s) {
+        const int buf = s & 1;
+        bool ok = tcx::mbar_wait(smem_u32(&sm.bfull[buf]), (uint32_t)((s >> 1) & 1), TC_WAIT_LIMIT);
+        if (ok && s >= 2)
+          ok = tcx::mbar_wait(smem_u32(&sm.tempty[buf]), (uint32_t)(((s - 2) >> 1) & 1), TC_WAIT_LIMIT);
+        if (!ok) {
+          atomicOr(&sm.bad, 2);
+          break;
+        }
+        tcx::fence_after();
+        const uint32_t dcol = sm.tmem + (uint32_t)(256 * buf);
+        const uint64_t da = smem_desc(smem_u32(sm.A[0])), db = smem_desc(smem_u32(sm.B[buf][0]));
+#pragma unroll 1
+        for (int g = 0; g < OZ_S; ++g) {
+#pragma unroll 1
+          for (int i = 0; i <= g; ++i) {
+            // descriptor start fields advance by address / 16: a slice of A
+            // is 16 KiB, of B 4 KiB, a K step of 16 is 256 bytes
+            const uint64_t a0 = da + (uint64_t)(i * (OZ_ABYTES >> 4)), b0 = db + (uint64_t)((g - i) * (OZ_BBYTES >> 4));
 #pragma unroll
-    for (int q0 = 0; q0 < 16; q0 += 4) {
-      uint32_t re[4][OZ_S], im[4][OZ_S];
+            for (int k = 0; k < 4; ++k)
+              tcx::mma_f16(dcol + (uint32_t)(OZ_NC * g), a0 + (uint64_t)(16 * k), b0 + (uint64_t)(16 * k), idesc,
+                           (i == 0 && k == 0) ? 0u : 1u);
+          }
+        }
+        tcx::mma_commit(smem_u32(&sm.tfull[buf]));
+      }
+    }
+    __syncwarp();
+  } else {
+    const int cc = t & 31, oct = t >> 5;   // B staging: pivots [4 oct, 4 oct + 4) of column cc
+    double2 vn[4];                          // the next sub-tile's values, loaded ahead
+    auto load_b = [&](int s) {
+      const int col = OZ_NC * s + cc;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        oz_slice(v[q0 + q].x, ec, re[q]);
-        oz_slice(v[q0 + q].y, ec, im[q]);
+        const int j = 4 * oct + q;
+        vn[q] = (j < kc && col < ncols) ? rload(col, j) : make_double2(0.0, 0.0);
       }
-      const int k0 = 2 * (16 * half + q0);
-#pragma unroll
-      for (int i = 0; i < OZ_S; ++i) {
-        uint4 w;
-        w.x = re[0][i] | (im[0][i] << 16);
-        w.y = re[1][i] | (im[1][i] << 16);
-        w.z = re[2][i] | (im[2][i] << 16);
-        w.w = re[3][i] | (im[3][i] << 16);
-        *reinterpret_cast<uint4 *>(sm.B[i] + op_off(rr, k0)) = w;
-      }
-    }
-  }
-  tcx::fence_proxy_async();
-  tcx::fence_before();
-  __syncthreads();
-  tcx::fence_after();
-  const uint32_t tmem = sm.tmem;
-  if (t == 0) {
-    const uint32_t idesc = tcx::instr_desc_f16(1, 128, OZ_MC);
+    };
+    if (nsub > 0) load_b(0);
 #pragma unroll 1
-    for (int g = 0; g < OZ_S; ++g) {
-#pragma unroll 1
-      for (int i = 0; i <= g; ++i) {
-        const uint32_t a0 = smem_u32(sm.A[i]), b0 = smem_u32(sm.B[g - i]);
+    for (int s = 0; s < nsub; ++s) {
+      const int buf = s & 1;
+      // ---- B(s): 32 columns as rows of K = [Rr, Ri] per pivot (its buffer
+      // was last read by the MMAs of s - 2, finished before drain(s - 2))
+      {
+        double2 v[4];
+        int em = OZ_EMPTY;
 #pragma unroll
-        for (int s = 0; s < 4; ++s)
-          tcx::mma_f16(tmem + (uint32_t)(OZ_MC * g), smem_desc(a0 + s * 256), smem_desc(b0 + s * 256), idesc,
-                       (i == 0 && s == 0) ? 0u : 1u);
-      }
-    }
-    tcx::mma_commit(smem_u32(&sm.mbar));
-  }
-  bool done = tcx::mbar_wait(smem_u32(&sm.mbar), 0, TC_WAIT_LIMIT);
-  tcx::fence_after();
-  if (done && !sm.bad) {
-    const int drow = warp * 32 + lane, er = drow >> 1, comp = drow & 1;
-#pragma unroll 1
-    for (int cb = 0; cb < OZ_MC; cb += 16) {
-      long long hi[16], lo[16];
+        for (int q = 0; q < 4; ++q) {
+          v[q] = vn[q];
+          em = max(em, max(oz_exp(v[q].x), oz_exp(v[q].y)));
+        }
+        worker_sync();                 // red is free (A's reduction, or the previous B's)
+        sm.red[t] = em;
+        worker_sync();
+        int ec = sm.red[cc];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) hi[u] = lo[u] = 0;
+        for (int o = 1; o < 8; ++o) ec = max(ec, sm.red[cc + 32 * o]);
+        if (oct == 0) sm.eB[buf][cc] = ec;
+        if (ec > 1024) sm.bad = 1;
+        uint32_t re[4][OZ_S], im[4][OZ_S];
 #pragma unroll
-      for (int g = 0; g < OZ_S; ++g) {
-        uint32_t vv[16];
-        tcx::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(OZ_MC * g + cb), vv);
+        for (int q = 0; q < 4; ++q) {
+          oz_slice(v[q].x, ec, re[q]);
+          oz_slice(v[q].y, ec, im[q]);
+        }
+        const int k0 = 8 * oct;
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const long long G = __float2int_rn(__uint_as_float(vv[u]));
-          if (g < 4) hi[u] += G * (1ll << (7 * (3 - g)));
-          else lo[u] += G * (1ll << (7 * (7 - g)));
+        for (int i = 0; i < OZ_S; ++i) {
+          uint4 w;
+          w.x = re[0][i] | (im[0][i] << 16);
+          w.y = re[1][i] | (im[1][i] << 16);
+          w.z = re[2][i] | (im[2][i] << 16);
+          w.w = re[3][i] | (im[3][i] << 16);
+          *reinterpret_cast<uint4 *>(sm.B[buf][i] + op_off(cc, k0)) = w;
         }
       }
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const long long V = hi[u] * (1ll << 20) + (lo[u] >> 8);   // arithmetic shift: floor
-        sink(er, cb + u, comp, V, sm.eA[er] + sm.eB[cb + u] - 55);
+      tcx::fence_proxy_async();
+      tcx::mbar_arrive(smem_u32(&sm.bfull[buf]));
+      if (s + 1 < nsub) load_b(s + 1);   // in flight during the read-out below
+      if (s > 0) {
+        drain(s - 1);
+        tcx::fence_before();
+        tcx::mbar_arrive(smem_u32(&sm.tempty[(s - 1) & 1]));
       }
     }
-  } else if (!done) {
-    // let the MMAs in flight finish (bounded) before the memory they write is freed
-    tcx::mbar_wait(smem_u32(&sm.mbar), 0, TC_WAIT_LIMIT);
+    if (nsub > 0) drain(nsub - 1);
   }
+  if (nsub > 0 && (sm.bad & 2) && t == 0)   // let issued MMAs finish before TMEM is freed
+    tcx::mbar_wait(smem_u32(&sm.tfull[(nsub - 1) & 1]), (uint32_t)(((nsub - 1) >> 1) & 1), TC_WAIT_LIMIT);
   tcx::fence_before();
   __syncthreads();
-  if (warp == 0) tcx::tmem_dealloc(tmem, OZ_TMEM_COLS);
-  return done;
-}
-
-// V 2^e as a double (V = 0 gives 0): one rounding of V, then an exact scale
-__device__ __forceinline__ double oz_value(long long V, int e) {
-  if (V == 0) return 0.0;
-  e = max(-1022, min(1023, e));
-  return __ll2double_rn(V) * __longlong_as_double((long long)(e + 1023) << 52);
+  if (warp == 0) tcx::tmem_dealloc(sm.tmem, OZ_TMEM_COLS);
+  return sm.bad;
 }
 
 __device__ __forceinline__ double2 *front_ptr64(const MfArgs &a, const FrontDev &f, int r, int c) {
@@ -440,11 +516,12 @@ __device__ __forceinline__ double2 *front_ptr64(const MfArgs &a, const FrontDev 
 }
 
 // Symmetric form, step k of every large front on the tensor cores: the
-// tiles on and below the diagonal of the trailing update (64 x 64 complex,
-// tile order skipping the pivot band), lower entries added to the front and
-// their signed mirrors stored, as mf_gj_update_sym does on the FP64 pipe.
-// grid = (fronts, nt (nt + 1) / 2 tiles).
-__global__ void __launch_bounds__(128, 1) mf_gj_update_oz(MfArgs a, int f0, int k) {
+// trailing update on and below the diagonal (rows and columns in the order
+// that skips the pivot band), lower entries added to the front and their
+// signed mirrors stored, as mf_gj_update_sym does on the FP64 pipe.  CTA
+// (front, ti, chunk): rows [64 ti, 64 ti + 64) against the chunk's columns
+// (at most 256) up to the diagonal.  grid = (fronts, tile rows x chunks).
+__global__ void __launch_bounds__(OZ_THREADS, 1) mf_gj_update_oz(MfArgs a, int f0, int k, int nchunk) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   OzSmem &sm = *reinterpret_cast<OzSmem *>(smem_raw);
   const FrontDev f = a.fronts[f0 + blockIdx.x];
@@ -452,14 +529,11 @@ __global__ void __launch_bounds__(128, 1) mf_gj_update_oz(MfArgs a, int f0, int 
   if (n <= MF_SMALL || k >= p) return;
   const int nbk = min(MF_NB, p - k);
   const int m = n - nbk;
-  const int nt = (m + OZ_MC - 1) / OZ_MC;
-  const int y = blockIdx.y;
-  if (y >= nt * (nt + 1) / 2) return;
-  int ti = (int)((sqrtf(8.f * y + 1.f) - 1.f) * 0.5f);
-  while ((ti + 1) * (ti + 2) / 2 <= y) ++ti;
-  while (ti * (ti + 1) / 2 > y) --ti;
-  const int tj = y - ti * (ti + 1) / 2;
-  const int i0 = ti * OZ_MC, j0 = tj * OZ_MC;
+  const int ti = blockIdx.y / nchunk, ch = blockIdx.y - ti * nchunk;
+  const int i0 = ti * OZ_MR;
+  const int c0 = ch * OZ_NC * OZ_CHUNK;
+  const int cend = min(min(i0 + OZ_MR, m), c0 + OZ_NC * OZ_CHUNK);
+  if (i0 >= m || c0 >= cend) return;
   const double2 *fac = reinterpret_cast<const double2 *>(a.fac);
   const int64_t fo = f.fac_off;
   auto cload = [&](int rr, int j) -> double2 {
@@ -467,44 +541,85 @@ __global__ void __launch_bounds__(128, 1) mf_gj_update_oz(MfArgs a, int f0, int 
     return ri < m ? *front_ptr64(a, f, unband_tc(ri, k, nbk), k + j) : make_double2(0.0, 0.0);
   };
   auto rload = [&](int cc, int j) -> double2 {
-    const int ci = j0 + cc;
-    return ci < m ? fac[fo + (int64_t)unband_tc(ci, k, nbk) * p + k + j] : make_double2(0.0, 0.0);
+    return fac[fo + (int64_t)unband_tc(c0 + cc, k, nbk) * p + k + j];
   };
-  auto sink = [&](int rr, int cc, int comp, long long V, int e) {
-    const int ri = i0 + rr, ci = j0 + cc;
-    if (ri >= m || ci > ri) return;   // past the front, or an upper entry of a diagonal tile
-    const int r = unband_tc(ri, k, nbk), c = unband_tc(ci, k, nbk);
-    double *x = reinterpret_cast<double *>(front_ptr64(a, f, r, c)) + comp;
-    const double v = *x + oz_value(V, e);
-    *x = v;
-    if (ci < ri) {
-      const bool neg = (r < k) != (c < k);
-      reinterpret_cast<double *>(front_ptr64(a, f, c, r))[comp] = neg ? -v : v;
+  // element (r, c) of the front as a double pointer, component comp:
+  // column c < p or >= p picks the region, then base + c * stride
+  const int b = f.b;
+  double *facd = reinterpret_cast<double *>(a.fac), *wsd = reinterpret_cast<double *>(a.ws_cur);
+  auto sink = [&](int rr, int cb, int comp, auto &&produce) {
+    // produce() reads tensor memory with warp-collective loads: every lane
+    // calls it, rows past the front only skip their loads and stores
+    const int ri = i0 + rr;
+    const bool rowok = ri < m;
+    const int r = rowok ? unband_tc(ri, k, nbk) : 0;
+    // (r, c): r < p: [Finv H12] column-major, ld p; r >= p: -G21 (c < p,
+    // ld b) or S (c >= p, ld b, in the level workspace)
+    double *dlo, *dhi;
+    int64_t slo, shi;
+    // (c, r), the mirror: c < p: row c of [Finv H12] at column r; c >= p:
+    // -G21 (r < p) or S (r >= p) at row c - p
+    double *mlo, *mhi;
+    if (r < p) {
+      dlo = dhi = facd + 2 * (fo + r) + comp;
+      slo = shi = 2 * (int64_t)p;
+      mhi = facd + 2 * (fo + (int64_t)p * n + (int64_t)r * b - p) + comp;
+    } else {
+      dlo = facd + 2 * (fo + (int64_t)p * n + (r - p)) + comp;
+      dhi = wsd + 2 * (f.s_off + (r - p) - (int64_t)p * b) + comp;
+      slo = shi = 2 * (int64_t)b;
+      mhi = wsd + 2 * (f.s_off + (int64_t)(r - p) * b - p) + comp;
+    }
+    mlo = facd + 2 * (fo + (int64_t)r * p) + comp;
+    double *px[OZ_SINK];
+    double old[OZ_SINK];
+#pragma unroll
+    for (int u = 0; u < OZ_SINK; ++u) {
+      const int ci = c0 + cb + u;
+      px[u] = nullptr;
+      if (rowok && ci < cend && ci <= ri) {
+        const int c = unband_tc(ci, k, nbk);
+        px[u] = c < p ? dlo + c * slo : dhi + c * shi;
+        old[u] = *px[u];
+      }
+    }
+    double add[OZ_SINK];
+    produce(add);
+#pragma unroll
+    for (int u = 0; u < OZ_SINK; ++u) {
+      if (!px[u]) continue;
+      const int ci = c0 + cb + u, c = unband_tc(ci, k, nbk);
+      const double v = old[u] + add[u];
+      *px[u] = v;
+      if (ci < ri) {
+        const long long flip = ((r < k) != (c < k)) ? (long long)(1ull << 63) : 0ll;
+        *((c < p ? mlo : mhi) + 2 * c) = __longlong_as_double(__double_as_longlong(v) ^ flip);
+      }
     }
   };
-  const bool ok = oz_tile(sm, nbk, cload, rload, sink);
+  const int bad = oz_rows(sm, nbk, cend - c0, cload, rload, sink);
   if (threadIdx.x == 0) {
-    if (!ok) atomicOr(a.flag, 2);
-    else if (sm.bad) atomicOr(a.flag, 1);
+    if (bad & 2) atomicOr(a.flag, 2);
+    else if (bad & 1) atomicOr(a.flag, 1);
   }
 }
 
 // One tile D = C R in complex128 (C(rr, j) at j * 64 + rr, R(j, cc) at
-// cc * kc + j, D(rr, cc) at cc * 64 + rr), through oz_tile.
-__global__ void __launch_bounds__(128, 1) oz_tile_kernel(const double2 *C, const double2 *R, double2 *D, int kc,
+// cc * kc + j, D(rr, cc) at cc * 64 + rr) through oz_rows.
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_tile_kernel(const double2 *C, const double2 *R, double2 *D, int kc,
                                                          int *flag) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   OzSmem &sm = *reinterpret_cast<OzSmem *>(smem_raw);
-  auto cload = [&](int rr, int j) { return C[j * OZ_MC + rr]; };
+  auto cload = [&](int rr, int j) { return C[j * OZ_MR + rr]; };
   auto rload = [&](int cc, int j) { return R[cc * kc + j]; };
-  auto sink = [&](int rr, int cc, int comp, long long V, int e) {
-    reinterpret_cast<double *>(&D[cc * OZ_MC + rr])[comp] = oz_value(V, e);
+  auto sink = [&](int rr, int cb, int comp, auto &&produce) {
+    double add[OZ_SINK];
+    produce(add);
+#pragma unroll
+    for (int u = 0; u < OZ_SINK; ++u) reinterpret_cast<double *>(&D[(cb + u) * OZ_MR + rr])[comp] = add[u];
   };
-  const bool ok = oz_tile(sm, kc, cload, rload, sink);
-  if (threadIdx.x == 0) {
-    if (!ok) atomicOr(flag, 2);
-    else if (sm.bad) atomicOr(flag, 1);
-  }
+  const int bad = oz_rows(sm, kc, OZ_MR, cload, rload, sink);
+  if (threadIdx.x == 0 && bad) atomicOr(flag, (bad & 2) ? 2 : 1);
 }
 
 // One tile D = C R with C (64 x kc) and R (kc x 128) complex, column-major
@@ -548,8 +663,9 @@ cudaError_t tc_setup_attributes() {
 
 void mf_oz_update_launch(const MfArgs &a, const LevelInfo &L, int k, cudaStream_t st) {
   const int m = L.max_n - std::min(MF_NB, std::max(1, L.max_p - k));
-  const int nt = std::max(1, (m + OZ_MC - 1) / OZ_MC);
-  mf_gj_update_oz<<<dim3(L.nf, nt * (nt + 1) / 2), 128, oz_smem_bytes(), st>>>(a, L.f0, k);
+  const int nt = std::max(1, (m + OZ_MR - 1) / OZ_MR);
+  const int nchunk = std::max(1, (nt * OZ_MR + OZ_NC * OZ_CHUNK - 1) / (OZ_NC * OZ_CHUNK));
+  mf_gj_update_oz<<<dim3(L.nf, nt * nchunk), OZ_THREADS, oz_smem_bytes(), st>>>(a, L.f0, k, nchunk);
   count_launch();
 }
 
@@ -565,7 +681,7 @@ void mf_tc_update_launch(const MfArgs &a, const LevelInfo &L, int k, int fmt, cu
 // (see oz_tile_kernel for the layouts); returns 0 on success, 1 if the device
 // reported a timeout, 2 for a non-finite input, -1 on a CUDA error (*err).
 int oz_tile_product(int kc, const double2 *C, const double2 *R, double2 *D, cudaError_t *err) {
-  const size_t nc = (size_t)OZ_MC * kc, nr = (size_t)kc * OZ_MC, nd = (size_t)OZ_MC * OZ_MC;
+  const size_t nc = (size_t)OZ_MR * kc, nr = (size_t)kc * OZ_MR, nd = (size_t)OZ_MR * OZ_MR;
   double2 *dC = nullptr, *dR = nullptr, *dD = nullptr;
   int *dflag = nullptr;
   *err = cudaSuccess;
@@ -583,7 +699,7 @@ int oz_tile_product(int kc, const double2 *C, const double2 *R, double2 *D, cuda
          ck(cudaMemset(dD, 0, nd * sizeof(double2))) && ck(cudaMemset(dflag, 0, sizeof(int)));
   }
   if (ok) {
-    oz_tile_kernel<<<1, 128, oz_smem_bytes()>>>(dC, dR, dD, kc, dflag);
+    oz_tile_kernel<<<1, OZ_THREADS, oz_smem_bytes()>>>(dC, dR, dD, kc, dflag);
     count_launch();
     ok = ck(cudaGetLastError()) && ck(cudaDeviceSynchronize()) &&
          ck(cudaMemcpy(D, dD, nd * sizeof(double2), cudaMemcpyDeviceToHost)) &&
