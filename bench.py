@@ -120,11 +120,15 @@ def parse():
     ap.add_argument("--symmetric", type=int, default=1, choices=[0, 1],
                     help="1: factor the symmetric form D A of each strip (lower-triangle front updates) "
                          "wherever there is no partial pivoting")
+    ap.add_argument("--fp64-tc", type=int, default=1, choices=[0, 1],
+                    help="1: complex128 symmetric-form front updates and column panels on the BF16 tensor cores "
+                         "by exact splitting (FP64 accuracy); 0: the FP64 pipe")
     ap.add_argument("--maxit", type=int, default=2000, help="FGMRES iteration limit per right-hand side")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="1: replay captured CUDA graphs of the factorization and of M^-1")
-    ap.add_argument("--persistent", type=int, default=2, choices=[0, 1, 2],
-                    help="k > 0: one persistent launch (k blocks per SM) per strip solve in the sequential orders")
+    ap.add_argument("--persistent", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="k > 0: one persistent launch (k blocks per SM) per strip solve in the sequential orders; "
+                         "0: per-level launches; -1: the library's choice by precision")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision and other-order runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -548,6 +552,7 @@ def run_ours(args, rank, world, local_rank):
         S.stdd_set_option(sv.ctx, S.STDD_OPT_PIVOTING, piv)
         S.stdd_set_option(sv.ctx, S.STDD_OPT_STATIC_PIVOT, sp)
         S.stdd_set_option(sv.ctx, S.STDD_OPT_SYMMETRIC, args.symmetric)
+        S.stdd_set_option(sv.ctx, S.STDD_OPT_FP64_TC, args.fp64_tc)
         return sv
 
     def step(sv):
@@ -683,7 +688,20 @@ def run_ours(args, rank, world, local_rank):
 
     tname = "double" if prec == S.STDD_PREC_FP64 else "float"
     sym = bool(args.symmetric and not pivots_for(prec)[0] and not tensor)
-    if tensor:
+    oz = sym and args.fp64_tc and prec == S.STDD_PREC_FP64
+    if oz:
+        # the split products on the BF16 tensor pipe: their own flops against
+        # the measured BF16 peak; the FP64 (LDL^T) flops they stand for beside
+        add_kernel("mf_gj_update_oz", kprof["update_ms"], kprof["update_calls"], kprof["update_flops_executed"],
+                   "tensor")
+        ko = kernels.get("mf_gj_update_oz")
+        if ko:
+            ko["unit_kind"] = ("BF16 tensor flops of the exact-splitting products (36 slice products of "
+                               "128 x 32 x 64 real per 64 x 32 complex sub-tile)")
+            ko["fp64_equivalent_flops_per_launch"] = kprof["update_flops"] / kprof["update_calls"]
+            ko["fp64_equivalent_tflops"] = ko["fp64_equivalent_flops_per_launch"] / (ko["ms_per_launch"] * 1e-3) / 1e12
+            ko["fp64_equivalent_vs_dgemm"] = ko["fp64_equivalent_tflops"] / fp64_tf
+    elif tensor:
         add_kernel(f"mf_gj_update_tc<{args.precision}>", kprof["update_ms"], kprof["update_calls"],
                    kprof["update_flops"], "tensor", kprof["update_flops_executed"])
     else:
@@ -693,6 +711,7 @@ def run_ours(args, rank, world, local_rank):
                kprof["small_flops_executed"])
     add_kernel(f"mf_down<{tname}>", kprof["down_ms"], kprof["down_calls"], kprof["down_bytes"], "bytes")
     add_kernel(f"mf_up<{tname}>", kprof["up_ms"], kprof["up_calls"], kprof["up_bytes"], "bytes")
+    add_kernel(f"mf_strip_sweep<{tname}>", kprof["sweep_ms"], kprof["sweep_calls"], kprof["sweep_bytes"], "bytes")
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     d = kernels[dom]
     roof = {k: d[k] for k in ("bound", "achieved", "peak", "unit", "frac", "peak_source")}
@@ -704,7 +723,7 @@ def run_ours(args, rank, world, local_rank):
         roof["executed_tflops"] = d["executed_tflops"]
     roof["measured_over"] = ("one extra step after the timed region with a CUDA-event span around every launch "
                              "(graphs bypassed); profiled step %.1f ms" % kprof["step_ms"])
-    roof["traffic"] = ncu_traffic(dom, d.get("executed_flops_per_launch"))
+    roof["traffic"] = ncu_traffic(dom, d.get("executed_flops_per_launch", d["units_per_launch"]))
     roof["traffic_source"] = NCU_TRAFFIC.get(dom, {}).get("profile") if roof["traffic"] is not None else None
 
     out = {
@@ -725,7 +744,10 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": workload_desc(w), "precision": args.precision, "order": args.order,
                    "pivoting": pivots_for(prec)[0], "static_pivot": pivots_for(prec)[1],
                    "symmetric_form": int(bool(args.symmetric and not pivots_for(prec)[0] and not tensor)),
-                   "persistent_sweeps": args.persistent,
+                   "fp64_products": ("BF16 tensor cores, exact 8 x 7-bit splitting" if (
+                       args.fp64_tc and args.symmetric and prec == S.STDD_PREC_FP64) else "FP64 pipe"),
+                   "persistent_sweeps": (args.persistent if args.persistent >= 0 else
+                                         (0 if prec == S.STDD_PREC_FP64 else 2)),
                    "krylov_space": "band" if band_main else "full", "leaf": args.leaf, "rtol": RTOL,
                    "restart": RESTART, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (factors %.1f GB, Krylov basis %.1f GB)"

@@ -276,6 +276,10 @@ typedef struct {
   /* real flops the two elimination kernels execute (Gauss-Jordan: the
    * updates also cover the eliminated pivot rows and columns) */
   double small_flops_executed, update_flops_executed;
+  /* persistent one-strip solves (STDD_OPT_PERSISTENT): launches, time and
+   * the factor bytes they read */
+  double sweep_ms, sweep_bytes;
+  int sweep_calls;
 } stdd_profile;
 
 /* level 0: off; 1: phase spans (factor, M^-1, matvec, Gram-Schmidt,
@@ -354,14 +358,17 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     its products in the same order on either shape, so
  *                     results do not change.  (With STDD_OPT_AUTOTUNE 0 and
  *                     this option 0 the shape is 64.)
- *   STDD_OPT_PERSISTENT (default 2): in the sequential orders (1 and 3,
+ *   STDD_OPT_PERSISTENT (default -1): in the sequential orders (1 and 3,
  *                     one right-hand side at a time) each strip's solve --
  *                     residual restriction, the upward and the downward
  *                     sweep over all tree levels, the add-back -- runs as
  *                     one cooperative launch whose levels are separated by
  *                     grid-wide barriers instead of ~3 launches per level;
  *                     0: one launch per level; k = 1..8: the cooperative
- *                     grid holds k blocks per SM (at most what fits).  Same
+ *                     grid holds k blocks per SM (at most what fits); -1: 2
+ *                     for complex64 factors, 0 for complex128 ones (whose
+ *                     products are FP64-bound per warp and run faster in the
+ *                     per-level kernels' deeper load pipelines).  Same
  *                     arithmetic, same results.
  *   STDD_OPT_SWEEP_WAIT (default 0 = 4,194,304): polls a block spends at one
  *                     grid barrier of a persistent sweep before it gives up;

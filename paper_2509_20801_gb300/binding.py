@@ -56,7 +56,8 @@ class stdd_profile(ctypes.Structure):
                 ("update_ms", c_double), ("update_flops", c_double), ("update_calls", c_int),
                 ("up_ms", c_double), ("up_bytes", c_double), ("up_calls", c_int),
                 ("down_ms", c_double), ("down_bytes", c_double), ("down_calls", c_int),
-                ("small_flops_executed", c_double), ("update_flops_executed", c_double)]
+                ("small_flops_executed", c_double), ("update_flops_executed", c_double),
+                ("sweep_ms", c_double), ("sweep_bytes", c_double), ("sweep_calls", c_int)]
 
 
 _SIGS = {

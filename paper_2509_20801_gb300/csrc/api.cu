@@ -287,6 +287,7 @@ struct stdd_ctx {
   std::vector<double> unit_small_sym, exec_small_sym;
   std::vector<std::vector<double>> exec_update_oz;          // BF16 tensor flops of the split update
   std::vector<double> span_units, span_exec;                // parallel to spans
+  std::vector<int64_t> strip_fac_entries;                   // factor entries of each strip
   std::vector<int> span_level;                              // parallel to spans
   struct Hook : stdd::LaunchHook {
     stdd_ctx *c = nullptr;
@@ -305,6 +306,8 @@ struct stdd_ctx {
         const bool sy = c->sym_active();
         u = (sy ? c->unit_update_sym : c->unit_update)[level][k / stdd::MF_NB];
         x = (c->oz_active() ? c->exec_update_oz : sy ? c->exec_update_sym : c->exec_update)[level][k / stdd::MF_NB];
+      } else if (kind == stdd::K_SWEEP) {   // "level" is the strip
+        u = x = c->strip_fac_entries[level] * (double)c->elem();
       } else if (kind == stdd::K_UP) {
         u = x = c->unit_up[level];
       } else {
@@ -547,7 +550,11 @@ struct stdd_ctx {
   void ensure_krylov(int m);
   // persistent one-strip sweeps of the sequential orders (STDD_OPT_PERSISTENT):
   // per strip position and level the strip's share of the sweep
-  int persistent = 2;                 // 0: per-level launches; k: persistent sweeps, k blocks per SM
+  int persistent = -1;                // 0: per-level launches; k: persistent sweeps, k blocks per SM; -1: by precision
+  // automatic choice: complex64 sweeps run persistent (2 blocks per SM);
+  // complex128 ones are FP64-bound per warp and gain more from the per-level
+  // kernels' deeper load pipelines than from saving launches
+  int persistent_eff() const { return persistent >= 0 ? persistent : (prec == STDD_PREC_FP64 ? 0 : 2); }
   long long sweep_wait = 1ll << 22;   // polls of a grid-barrier wait before it gives up
   DBuf d_striplv, d_bar, d_sweep_flag;
   int sweep_flag_h = 0;
@@ -702,6 +709,8 @@ void stdd_ctx::build_strip_levels() {
       l.rows_down = li.rows_down;
       l.split_up = li.split_up1;
       l.split_down = li.split_down1;
+      l.max_n = li.max_n;
+      l.pad_ = 0;
     }
   upload(d_striplv, t, stream);
   stdd::mf_strip_sweep_grid();   // launch shape queried once, outside any capture
@@ -749,6 +758,7 @@ void stdd_ctx::build_structure() {
   factor_cflops = factor_cflops_lu = solve_cflops = 0;
   nloc_max = 0;
   ycoef_keys.clear();
+  strip_fac_entries.assign(nsub, 0);
   for (int k = 0; k < nsub; ++k) {
     const StripHost &s = strips[k];
     const Shape &sh = shape_of(s);
@@ -773,6 +783,7 @@ void stdd_ctx::build_structure() {
     vec += (int64_t)s.W() * s.H();
     nloc_max = std::max<int64_t>(nloc_max, (int64_t)s.W() * s.H());
     fac += sh.factor_entries;
+    strip_fac_entries[k] = sh.factor_entries;
     coef += s.W();
     depth = std::max(depth, sh.depth);
     max_p = std::max(max_p, sh.max_p);
@@ -1265,7 +1276,7 @@ void stdd_ctx::enqueue_minv_multiplicative(const std::vector<const double2 *> &v
     if (order == 1)  // symmetric: back again (order 3 is the forward sweep alone)
       for (int k = nsub - 2; k >= 0; --k) groups.push_back({pos[k], pos[k] + 1});
   }
-  if (persistent && na == 1 && order != 2 && d_striplv.p) {
+  if (persistent_eff() && na == 1 && order != 2 && d_striplv.p) {
     // one cooperative launch per strip solve (the barrier counters are
     // cleared before each, so a sweep that gave up leaves nothing behind)
     MfArgs a = mf_args(0, true);
@@ -1273,10 +1284,12 @@ void stdd_ctx::enqueue_minv_multiplicative(const std::vector<const double2 *> &v
     for (const auto &gr : groups) {
       const int j = gr.first;
       CK(cudaMemsetAsync(d_bar.p, 0, 2 * sizeof(unsigned), stream));
+      hook.before(stdd::K_SWEEP, perm[j], 0);
       CK(stdd::mf_strip_sweep_launch<R>(a, d_ub[0].p, d_ub[1].p, g, strips_host[perm[j]],
                                         d_striplv.as<stdd::StripLevel>() + (size_t)j * depth, depth, vs[0], zs[0],
-                                        d_bar.as<unsigned>(), d_sweep_flag.as<int>(), sweep_wait, persistent,
+                                        d_bar.as<unsigned>(), d_sweep_flag.as<int>(), sweep_wait, persistent_eff(),
                                         stream));
+      hook.after(stdd::K_SWEEP, perm[j], 0);
     }
     return;
   }
@@ -2411,7 +2424,8 @@ stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
         c->invalidate_factors();
         break;
       case STDD_OPT_PERSISTENT:
-        if (value < 0 || value > 8) throw ArgError("persistent must be 0 (off) or 1..8 blocks per SM");
+        if (value < -1 || value > 8)
+          throw ArgError("persistent must be -1 (by precision), 0 (off) or 1..8 blocks per SM");
         if (value != c->persistent) {
           c->persistent = value;
           c->clear_graphs();
@@ -2504,7 +2518,7 @@ stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {
         e.first += ms;
         e.second += c->span_units[si];
       }
-      static const char *names[] = {"small", "update", "up", "down"};
+      static const char *names[] = {"small", "update", "up", "down", "sweep"};
       for (auto &kv : lv)
         std::fprintf(stderr, "level-profile %s L%d ms %.3f units %.4g rate %.4g\n", names[kv.first.first],
                      kv.first.second, kv.second.first, kv.second.second,
@@ -2522,6 +2536,9 @@ stdd_status stdd_get_profile(stdd_ctx *c, stdd_profile *o, int reset) {
     o->down_ms = t[K0 + stdd::K_DOWN];
     o->down_bytes = units[K0 + stdd::K_DOWN];
     o->down_calls = cnt[K0 + stdd::K_DOWN];
+    o->sweep_ms = t[K0 + stdd::K_SWEEP];
+    o->sweep_bytes = units[K0 + stdd::K_SWEEP];
+    o->sweep_calls = cnt[K0 + stdd::K_SWEEP];
     o->small_flops_executed = execu[K0 + stdd::K_SMALL];
     o->update_flops_executed = execu[K0 + stdd::K_UPDATE];
     o->factor_ms = t[stdd_ctx::PH_FACTOR];

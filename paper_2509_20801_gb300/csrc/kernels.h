@@ -70,7 +70,7 @@ struct LevelInfo {
 
 // Optional per-launch observer (phase profiling): kind is one of the K_*
 // values, level the tree level, k the pivot-block step (factorization).
-enum { K_SMALL = 0, K_UPDATE = 1, K_UP = 2, K_DOWN = 3, K_COUNT = 4 };
+enum { K_SMALL = 0, K_UPDATE = 1, K_UP = 2, K_DOWN = 3, K_SWEEP = 4, K_COUNT = 5 };
 struct LaunchHook {
   virtual void before(int kind, int level, int k) = 0;
   virtual void after(int kind, int level, int k) = 0;
@@ -90,6 +90,7 @@ cudaError_t tc_setup_attributes();
 void mf_tc_update_launch(const MfArgs &a, const LevelInfo &L, int k, int fmt, cudaStream_t st);
 // symmetric form, complex128: the update on the BF16 tensor cores by exact splitting
 void mf_oz_update_launch(const MfArgs &a, const LevelInfo &L, int k, cudaStream_t st);
+void mf_oz_col_launch(const MfArgs &a, const LevelInfo &L, int k, cudaStream_t st);
 int oz_tile_product(int kc, const double2 *C, const double2 *R, double2 *D, cudaError_t *err);
 // one 64 x kc by kc x 128 complex tile product on the tensor cores from host
 // arrays: 0 ok, 1 wait timed out, -1 CUDA error (*err)
@@ -103,6 +104,7 @@ struct StripLevel {
   int up_n, down_n;            // its upward / downward work items
   int64_t up_first, down_first;
   int rows_up, rows_down, split_up, split_down;
+  int max_n, pad_;             // the level's largest front (entries per front in the gather)
 };
 struct GridDev;
 // Persistent sweep of one strip (one right-hand side): t = R_s^I (v - A z),

@@ -905,30 +905,63 @@ template <int W, typename C> __device__ __forceinline__ C shfl_w(unsigned mask, 
 // acc[q] = sum over columns [c0, c1) of M(r, c) * vec_q(c), q < NR, for one
 // segment; M(r, c) at M[c * ld + r]; vec_q(c) comes from gather(c, q).
 // Each matrix entry is loaded once for all NR right-hand sides.
-template <int ROWS, int NR, typename C, typename Gather>
+template <int ROWS, int NR, bool AHEAD, typename C, typename Gather>
 __device__ __forceinline__ void seg_dot(const C *__restrict__ M, int64_t ld, int r, bool row, int c0, int c1,
                                         int lane, unsigned mask, Gather gather, C (&acc)[NR]) {
+  // the next chunk's vector values are requested before this chunk's
+  // products (at the top tree levels a few warps carry a whole phase and
+  // would otherwise wait for the dependent gather once per chunk)
   constexpr int U0 = sizeof(C) == 16 ? 8 : 32;  // FP64 is ALU-bound: fewer loads, more warps
   constexpr int U = NR > 1 ? (U0 / NR > 4 ? U0 / NR : 4) : U0;
   constexpr int UU = U < ROWS ? U : ROWS;
 #pragma unroll
   for (int q = 0; q < NR; ++q) acc[q] = czero<C>();
+  C vn[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) vn[q] = c0 + lane < c1 ? gather(c0 + lane, q) : czero<C>();
+  // complex128, one right-hand side, AHEAD (the per-level kernels; the
+  // persistent sweep has no registers to spare): matrix loads run one block of UU
+  // columns ahead of the products (the block after a chunk's last one is
+  // the next chunk's first); complex64 and several right-hand sides keep
+  // one block in registers
+  constexpr bool PIPE = AHEAD && sizeof(C) == 16 && NR == 1;
+  C m[UU];
+  if (PIPE && c1 - c0 >= ROWS) {
+#pragma unroll
+    for (int u = 0; u < UU; ++u) m[u] = row ? M[(int64_t)(c0 + u) * ld + r] : czero<C>();
+  }
   for (int cb = c0; cb < c1; cb += ROWS) {
-    const int c = cb + lane;
     C v[NR];
 #pragma unroll
-    for (int q = 0; q < NR; ++q) v[q] = c < c1 ? gather(c, q) : czero<C>();
+    for (int q = 0; q < NR; ++q) v[q] = vn[q];
+    const int cn = cb + ROWS + lane;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) vn[q] = cn < c1 ? gather(cn, q) : czero<C>();
     const int nv = min(ROWS, c1 - cb);
     if (nv == ROWS) {
+      const bool next_full = c1 - (cb + ROWS) >= ROWS;
 #pragma unroll
       for (int u0 = 0; u0 < ROWS; u0 += UU) {
-        C m[UU];
+        if (PIPE) {
+          C mn[UU];
+          const int nb = u0 + UU < ROWS ? cb + u0 + UU : cb + ROWS;   // the block loaded ahead
+          const bool ahead = u0 + UU < ROWS || next_full;
 #pragma unroll
-        for (int u = 0; u < UU; ++u) m[u] = row ? M[(int64_t)(cb + u0 + u) * ld + r] : czero<C>();
+          for (int u = 0; u < UU; ++u) mn[u] = (row && ahead) ? M[(int64_t)(nb + u) * ld + r] : czero<C>();
 #pragma unroll
-        for (int u = 0; u < UU; ++u)
+          for (int u = 0; u < UU; ++u)
 #pragma unroll
-          for (int q = 0; q < NR; ++q) acc[q] = cfma(m[u], shfl_w<ROWS>(mask, v[q], u0 + u), acc[q]);
+            for (int q = 0; q < NR; ++q) acc[q] = cfma(m[u], shfl_w<ROWS>(mask, v[q], u0 + u), acc[q]);
+#pragma unroll
+          for (int u = 0; u < UU; ++u) m[u] = mn[u];
+        } else {
+#pragma unroll
+          for (int u = 0; u < UU; ++u) m[u] = row ? M[(int64_t)(cb + u0 + u) * ld + r] : czero<C>();
+#pragma unroll
+          for (int u = 0; u < UU; ++u)
+#pragma unroll
+            for (int q = 0; q < NR; ++q) acc[q] = cfma(m[u], shfl_w<ROWS>(mask, v[q], u0 + u), acc[q]);
+        }
       }
     } else {
       // ragged last chunk: only the valid columns (no multiply-adds by zero)
@@ -955,66 +988,71 @@ __device__ __forceinline__ void seg_dot(const C *__restrict__ M, int64_t ld, int
 // the children's update vectors (inverse extend-add maps); w_p goes to the
 // pivot slots of wloc (kept for the way down) and w_b is the initial value
 // of the front's update vector.
-// one warp, front f0 + fi (the body of mf_up_gather)
-template <typename R> __device__ __forceinline__ void up_gather_front(const MfArgs &a, int f0, int fi, int nrhs,
-                                                                      int64_t ldt, int lane) {
+// one entry k of front f0 + fi, every right-hand side (k >= n: nothing)
+template <typename R> __device__ __forceinline__ void up_gather_elem(const MfArgs &a, int f0, int fi, int k, int nrhs,
+                                                                     int64_t ldt) {
   using C = typename CT<R>::T;
   const FrontDev f = a.fronts[f0 + fi];
   const int p = f.p, b = f.b, n = p + b;
-  const StripDev st = a.strips[f.strip];
-  const int64_t voff = st.vec_off;
+  if (k >= n) return;
+  const int64_t voff = a.strips[f.strip].vec_off;
+  int t[2] = {-1, -1}, bc[2] = {0, 0};
   const C *uc[2] = {nullptr, nullptr};
-  int bc[2] = {0, 0};
-  const int *inv[2] = {nullptr, nullptr};
 #pragma unroll
   for (int ci = 0; ci < 2; ++ci) {
     if (f.child[ci] >= 0) {
-      const FrontDev ch = a.fronts[f.child[ci]];
-      bc[ci] = ch.b;
-      uc[ci] = reinterpret_cast<const C *>(a.ub_child) + ch.u_off * nrhs;
-      inv[ci] = a.inv + f.inv_off[ci];
+      t[ci] = a.inv[f.inv_off[ci] + k];
+      if (t[ci] >= 0) {
+        const FrontDev ch = a.fronts[f.child[ci]];
+        bc[ci] = ch.b;
+        uc[ci] = reinterpret_cast<const C *>(a.ub_child) + ch.u_off * nrhs;
+      }
     }
   }
-  const int *nodes = a.nodes + f.node_off;
+  int node = 0;
+  C scale = czero<C>();
+  if (k < p) {
+    node = a.nodes[f.node_off + k];
+    if (a.sym) {   // the source of D A x = D t
+      const StripDev st = a.strips[f.strip];
+      const int Hl = st.y1 - st.y0, ux = node / Hl, uy = node - ux * Hl;
+      scale = to_c(cmul(a.lsx[st.coef_off + ux], a.lsy[st.ycoef_off + uy]), C());
+    }
+  }
   const C *tv = reinterpret_cast<const C *>(a.tloc);
   C *wl = reinterpret_cast<C *>(a.wloc);
   C *u = reinterpret_cast<C *>(a.ub_cur) + f.u_off * nrhs;
   for (int q = 0; q < nrhs; ++q) {
-    for (int k = lane; k < n; k += 32) {
-      C w = czero<C>();
-      int64_t gi = 0;
-      if (k < p) {
-        gi = q * ldt + voff + nodes[k];
-        w = tv[gi];
-        if (a.sym) {   // the source of D A x = D t
-          const int Hl = st.y1 - st.y0, u = nodes[k], ux = u / Hl, uy = u - ux * Hl;
-          w = cmul(w, to_c(cmul(a.lsx[st.coef_off + ux], a.lsy[st.ycoef_off + uy]), C()));
-        }
-      }
-#pragma unroll
-      for (int ci = 0; ci < 2; ++ci)
-        if (uc[ci]) {
-          const int t = inv[ci][k];
-          if (t >= 0) w = cadd(w, uc[ci][(int64_t)q * bc[ci] + t]);
-        }
-      if (k < p) wl[gi] = w;
-      else u[(int64_t)q * b + (k - p)] = w;
+    C w = czero<C>();
+    const int64_t gi = q * ldt + voff + node;
+    if (k < p) {
+      w = tv[gi];
+      if (a.sym) w = cmul(w, scale);
     }
+#pragma unroll
+    for (int ci = 0; ci < 2; ++ci)
+      if (t[ci] >= 0) w = cadd(w, uc[ci][(int64_t)q * bc[ci] + t[ci]]);
+    if (k < p) wl[gi] = w;
+    else u[(int64_t)q * b + (k - p)] = w;
   }
 }
 
+// every entry of every front of a level, one thread per (front, entry):
+// the dependent loads of an entry (its node, source, the children's
+// update vectors) are short, and a front's entries run side by side
 template <typename R>
-__global__ void __launch_bounds__(256) mf_up_gather(MfArgs a, int f0, int nf, int nrhs, int64_t ldt) {
-  const int fi = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (fi >= nf) return;
-  up_gather_front<R>(a, f0, fi, nrhs, ldt, threadIdx.x & 31);
+__global__ void __launch_bounds__(256) mf_up_gather(MfArgs a, int f0, int nf, int nmax, int nrhs, int64_t ldt) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)nf * nmax) return;
+  const int fi = (int)(e / nmax), k = (int)(e - (int64_t)fi * nmax);
+  up_gather_elem<R>(a, f0, fi, k, nrhs, ldt);
 }
 
 // Going up, part 2: lane = border row r;
 // u[r] = w_b[r] + sum_j (-G21)(r, j) w_p[j]  (w_b already in u).
 // NR right-hand sides share every matrix load (NR > 1 requires split == 1).
 // one (virtual) block of the upward products: the items of block vb
-template <typename R, int ROWS, int NR>
+template <typename R, int ROWS, int NR, bool AHEAD = true>
 __device__ __forceinline__ void up_block(const MfArgs &a, const int2 *__restrict__ items, int nitems, int split,
                                          int nrhs, int64_t ldt, int vb, typename CT<R>::T *part) {
   using C = typename CT<R>::T;
@@ -1062,7 +1100,7 @@ __device__ __forceinline__ void up_block(const MfArgs &a, const int2 *__restrict
       };
       for (int sg = seg0; sg < seg1; ++sg) {
         C sv[NR];
-        seg_dot<ROWS, NR, C>(G, b, r, row, sg * MF_SEG, min(p, (sg + 1) * MF_SEG), lane, mask, gather, sv);
+        seg_dot<ROWS, NR, AHEAD, C>(G, b, r, row, sg * MF_SEG, min(p, (sg + 1) * MF_SEG), lane, mask, gather, sv);
         if (split == 1) {
 #pragma unroll
           for (int q = 0; q < NR; ++q) total[q] = cadd(total[q], sv[q]);
@@ -1089,7 +1127,7 @@ __device__ __forceinline__ void up_block(const MfArgs &a, const int2 *__restrict
 // Coming down: lane = pivot row r;
 // x[r] = sum_{c<p} Finv(r, c) w_p[c] - sum_{c>=p} H12(r, c) x_b[c].
 // one (virtual) block of the downward products: the items of block vb
-template <typename R, int ROWS, int NR>
+template <typename R, int ROWS, int NR, bool AHEAD = true>
 __device__ __forceinline__ void down_block(const MfArgs &a, const int2 *__restrict__ items, int nitems, int split,
                                            int nrhs, int64_t ldt, int vb, typename CT<R>::T *part) {
   using C = typename CT<R>::T;
@@ -1134,7 +1172,7 @@ __device__ __forceinline__ void down_block(const MfArgs &a, const int2 *__restri
       };
       for (int sg = seg0; sg < seg1; ++sg) {
         C sv[NR];
-        seg_dot<ROWS, NR, C>(Fm, p, r, row, sg * MF_SEG, min(n, (sg + 1) * MF_SEG), lane, mask, gather, sv);
+        seg_dot<ROWS, NR, AHEAD, C>(Fm, p, r, row, sg * MF_SEG, min(n, (sg + 1) * MF_SEG), lane, mask, gather, sv);
         if (split == 1) {
 #pragma unroll
           for (int q = 0; q < NR; ++q) total[q] = cadd(total[q], sv[q]);
@@ -1159,14 +1197,14 @@ __device__ __forceinline__ void down_block(const MfArgs &a, const int2 *__restri
 }
 
 template <typename R, int ROWS, int NR>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_up(MfArgs a, const int2 *__restrict__ items,
+__global__ void __launch_bounds__(256, 2) mf_up(MfArgs a, const int2 *__restrict__ items,
                                                                      int nitems, int split, int nrhs, int64_t ldt) {
   __shared__ typename CT<R>::T part[MF_MAXSEG * 256 / 2];
   up_block<R, ROWS, NR>(a, items, nitems, split, nrhs, ldt, blockIdx.x, part);
 }
 
 template <typename R, int ROWS, int NR>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 2) mf_down(MfArgs a, const int2 *__restrict__ items,
+__global__ void __launch_bounds__(256, 2) mf_down(MfArgs a, const int2 *__restrict__ items,
                                                                        int nitems, int split, int nrhs,
                                                                        int64_t ldt) {
   __shared__ typename CT<R>::T part[MF_MAXSEG * 256 / 2];
@@ -1214,7 +1252,7 @@ __device__ __forceinline__ void up_items(const MfArgs &a, const StripLevel &l, i
   const int ipc = (256 / ROWS) / l.split_up;
   const int nvb = (l.up_n + ipc - 1) / ipc;
   for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x)
-    up_block<R, ROWS, 1>(a, a.items_sweep + l.up_first, l.up_n, l.split_up, 1, ldt, vb, part);
+    up_block<R, ROWS, 1, false>(a, a.items_sweep + l.up_first, l.up_n, l.split_up, 1, ldt, vb, part);
 }
 
 template <typename R, int ROWS>
@@ -1223,7 +1261,7 @@ __device__ __forceinline__ void down_items(const MfArgs &a, const StripLevel &l,
   const int ipc = (256 / ROWS) / l.split_down;
   const int nvb = (l.down_n + ipc - 1) / ipc;
   for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x)
-    down_block<R, ROWS, 1>(a, a.items_sweep + l.down_first, l.down_n, l.split_down, 1, ldt, vb, part);
+    down_block<R, ROWS, 1, false>(a, a.items_sweep + l.down_first, l.down_n, l.split_down, 1, ldt, vb, part);
 }
 
 // The launches of one strip's solve in the sequential orders (residual
@@ -1256,14 +1294,16 @@ __global__ void __launch_bounds__(256, 2)
     }
   }
   if (!grid_barrier(bar, flag, limit)) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int L = depth - 1; L >= 0; --L) {
     const StripLevel l = lv[L];
     if (l.nf == 0) continue;
     MfArgs al = a;
     al.ub_cur = const_cast<void *>(L & 1 ? ub1 : ub0);
     al.ub_child = L & 1 ? ub0 : ub1;
-    for (int fi = blockIdx.x * 8 + warp; fi < l.nf; fi += gridDim.x * 8) up_gather_front<R>(al, l.f0, fi, 1, ldt, lane);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)l.nf * l.max_n; e += stride) {
+      const int fi = (int)(e / l.max_n);
+      up_gather_elem<R>(al, l.f0, fi, (int)(e - (int64_t)fi * l.max_n), 1, ldt);
+    }
     if (!grid_barrier(bar, flag, limit)) return;
     if (l.rows_up == 16) up_items<R, 16>(al, l, ldt, part);
     else up_items<R, 32>(al, l, ldt, part);
@@ -1341,7 +1381,8 @@ void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_
         count_launch();
       }
       mf_gj_diag<R><<<L.nf, MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
-      mf_gj_col<R><<<dim3(L.nf, tiles), MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
+      if (a.sym && a.fp64_tc && sizeof(R) == 8) mf_oz_col_launch(a, L, k, st);
+      else mf_gj_col<R><<<dim3(L.nf, tiles), MF_PANEL_THREADS, 0, st>>>(a, L.f0, k);
       if (hook) hook->before(K_UPDATE, level, k);
       if (tc_fmt >= 0 && sizeof(R) == 4) {
         mf_tc_update_launch(a, L, k, tc_fmt, st);
@@ -1369,7 +1410,8 @@ void mf_factor_level(const MfArgs &a, const LevelInfo &L, int level, cudaStream_
 template <typename R>
 void mf_up_gather_level(const MfArgs &a, const LevelInfo &L, int nrhs, int64_t ldt, cudaStream_t st) {
   if (L.nf == 0) return;
-  mf_up_gather<R><<<(L.nf + 7) / 8, 256, 0, st>>>(a, L.f0, L.nf, nrhs, ldt);
+  const int64_t ne = (int64_t)L.nf * L.max_n;
+  mf_up_gather<R><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(a, L.f0, L.nf, L.max_n, nrhs, ldt);
   count_launch();
 }
 

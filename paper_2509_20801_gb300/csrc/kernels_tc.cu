@@ -604,6 +604,48 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) mf_gj_update_oz(MfArgs a, int f
   }
 }
 
+// The column panel of step k on the tensor cores (symmetric form,
+// complex128): C(r, band) <- -C(r, band) D^-1 for the rows r outside the
+// pivot band, 64 rows per CTA, D^-1 (nbk x nbk, left in the band by
+// mf_gj_diag) the single 32-column sub-tile.  Each CTA slices its rows into
+// shared memory before any result is written, and CTAs own disjoint rows.
+// grid = (fronts, row tiles).
+__global__ void __launch_bounds__(OZ_THREADS, 1) mf_gj_col_oz(MfArgs a, int f0, int k) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  OzSmem &sm = *reinterpret_cast<OzSmem *>(smem_raw);
+  const FrontDev f = a.fronts[f0 + blockIdx.x];
+  const int p = f.p, n = p + f.b;
+  if (n <= MF_SMALL || k >= p) return;
+  const int nbk = min(MF_NB, p - k);
+  const int m = n - nbk;
+  const int i0 = blockIdx.y * OZ_MR;
+  if (i0 >= m) return;
+  const double2 *fac = reinterpret_cast<const double2 *>(a.fac);
+  const int64_t fo = f.fac_off;
+  auto cload = [&](int rr, int j) -> double2 {
+    const int ri = i0 + rr;
+    return ri < m ? *front_ptr64(a, f, unband_tc(ri, k, nbk), k + j) : make_double2(0.0, 0.0);
+  };
+  auto rload = [&](int cc, int j) -> double2 { return fac[fo + (int64_t)(k + cc) * p + k + j]; };
+  auto sink = [&](int rr, int cb, int comp, auto &&produce) {
+    double add[OZ_SINK];
+    produce(add);   // every lane (warp-collective reads)
+    const int ri = i0 + rr;
+    if (ri >= m) return;
+    const int r = unband_tc(ri, k, nbk);
+#pragma unroll
+    for (int u = 0; u < OZ_SINK; ++u) {
+      const int cc = cb + u;
+      if (cc < nbk) reinterpret_cast<double *>(front_ptr64(a, f, r, k + cc))[comp] = -add[u];
+    }
+  };
+  const int bad = oz_rows(sm, nbk, nbk, cload, rload, sink);
+  if (threadIdx.x == 0) {
+    if (bad & 2) atomicOr(a.flag, 2);
+    else if (bad & 1) atomicOr(a.flag, 1);
+  }
+}
+
 // One tile D = C R in complex128 (C(rr, j) at j * 64 + rr, R(j, cc) at
 // cc * kc + j, D(rr, cc) at cc * 64 + rr) through oz_rows.
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_tile_kernel(const double2 *C, const double2 *R, double2 *D, int kc,
@@ -658,7 +700,16 @@ cudaError_t tc_setup_attributes() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(mf_gj_update_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(mf_gj_col_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(oz_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+}
+
+void mf_oz_col_launch(const MfArgs &a, const LevelInfo &L, int k, cudaStream_t st) {
+  const int m = L.max_n - std::min(MF_NB, std::max(1, L.max_p - k));
+  const int nt = std::max(1, (m + OZ_MR - 1) / OZ_MR);
+  mf_gj_col_oz<<<dim3(L.nf, nt), OZ_THREADS, oz_smem_bytes(), st>>>(a, L.f0, k);
+  count_launch();
 }
 
 void mf_oz_update_launch(const MfArgs &a, const LevelInfo &L, int k, cudaStream_t st) {

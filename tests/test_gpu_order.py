@@ -128,9 +128,11 @@ def test_persistent_sweep_wait_gives_up_and_recovers(rnd):
     """A grid-barrier wait that runs out (one poll allowed) makes the
     application return STDD_ETIMEOUT without faulting; with the default limit
     the same context then applies the preconditioner correctly."""
-    from paper_2509_20801_gb300 import STDD_OPT_SWEEP_WAIT, StddError, stdd_apply_preconditioner, stdd_set_option
+    from paper_2509_20801_gb300 import (STDD_OPT_PERSISTENT, STDD_OPT_SWEEP_WAIT, StddError, stdd_apply_preconditioner,
+                                        stdd_set_option)
     w, P, D = rnd
     s = _solver(w, order=1)
+    stdd_set_option(s.ctx, STDD_OPT_PERSISTENT, 2)   # complex128 factors default to per-level launches
     s.factor()
     v_h = W.random_vector(P.n, seed=16)[0]
     v = torch.from_numpy(v_h).to(DEV)
