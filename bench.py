@@ -43,36 +43,59 @@ RTOL = 1e-8
 RESTART = 50
 FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor and tensor), NVIDIA's figure
 
-# DRAM bytes (read + write) of a kernel per flop it executes, from one ncu
-# capture of three launches of it on the 2048 x 512 waveguide network (the
-# update's traffic is the read-modify-write of the block it updates, which
-# grows with the executed flops, so it scales to the benchmark's launches);
-# used only while the kernel's source text (between the two markers) still
-# has the recorded SHA-256, else the roofline's traffic is null.
+# DRAM bytes (read + write) of a kernel per unit of its work -- per executed
+# flop for the elimination kernels, per algorithmic byte for the substitution
+# sweeps, per BF16 tensor flop for the split update -- from ncu captures on
+# the 2048 x 512 waveguide network (the traffic grows with the work, so it
+# scales to the benchmark's launches); used only while the kernel's source
+# text (between the two markers) still has the recorded SHA-256, else the
+# roofline's traffic is null.
+_MF = "paper_2509_20801_gb300/csrc/kernels_mf.cu"
+_SWEEP = ("// ------------------------------------------------------- substitutions",
+          "// ------------------------------------------- persistent one-strip sweep",
+          "47c9e6f78c16e1860f8bbced91945bf5c23798b825912bdfe5f192f0f4a48943")
 NCU_TRAFFIC = {
     "mf_gj_update<double>": {
-        "bytes_per_executed_flop": 1394.992640e6 / 11.533996032e9,  # 3 launches: DRAM bytes / executed flops
-        "source": "paper_2509_20801_gb300/csrc/kernels_mf.cu",
+        "dram_per_unit": 1394.992640e6 / 11.533996032e9,   # 3 launches: DRAM bytes / executed flops
+        "source": _MF,
         "begin": "// acc[4][4] += A(64 x K) B(K x 64)",
         "end": "// ------------------------------------------------------- substitutions",
         "sha256": "6decf2105b755b886e043790beeea94ba39fdd151acf1da500560430b40715db",
         "profile": "profiles/ncu_dram_mf_gj_update_fp64_waveguide_2048x512.md",
     },
     "mf_gj_update_sym<double>": {
-        "bytes_per_executed_flop": 1037.244416e6 / 5.778714624e9,   # 3 launches: DRAM bytes / executed flops
-        "source": "paper_2509_20801_gb300/csrc/kernels_mf.cu",
+        "dram_per_unit": 1036.804608e6 / 5.778714624e9,    # 3 launches: DRAM bytes / executed flops
+        "source": _MF,
         "begin": "// Symmetric form: the update of step k",
         "end": "// acc[4][4] += A(64 x K) B(K x 64)",
-        "sha256": "b96afa704f14f647b8b569781839b706a974e0464fd95b5c53efd5cfebf4cae2",
+        "sha256": "e5e1aff1ceb0885192828b398982ea8200ca281f09b33292924e2efb99982387",
         "profile": "profiles/ncu_dram_mf_gj_update_sym_fp64_waveguide_2048x512.md",
+    },
+    "mf_gj_update_oz": {
+        "dram_per_unit": 349.049344e6 / 86.06711808e9,     # 1 launch: DRAM bytes / BF16 tensor flops
+        "source": "paper_2509_20801_gb300/csrc/kernels_tc.cu",
+        "begin": "// ===================================================== FP64 on BF16 units",
+        "end": "// The column panel of step k on the tensor cores",
+        "sha256": "4c31819e1882c3b1aa455134b4bf67896c3454260ddbcf587c3c4b87e728a8c4",
+        "profile": "profiles/ncu_mf_gj_update_oz_fp64_waveguide_2048x512.md",
+    },
+    "mf_down<double>": {
+        "dram_per_unit": 67.64e6 / 66.270848e6,             # DRAM bytes / factor bytes of the launch
+        "source": _MF, "begin": _SWEEP[0], "end": _SWEEP[1], "sha256": _SWEEP[2],
+        "profile": "profiles/ncu_dram_mf_down_mf_up_fp64_waveguide_2048x512.md",
+    },
+    "mf_up<double>": {
+        "dram_per_unit": 6.499e6 / 6.357680e6,
+        "source": _MF, "begin": _SWEEP[0], "end": _SWEEP[1], "sha256": _SWEEP[2],
+        "profile": "profiles/ncu_dram_mf_down_mf_up_fp64_waveguide_2048x512.md",
     },
 }
 
 
-def ncu_traffic(kernel, executed_flops_per_launch):
+def ncu_traffic(kernel, units_per_launch):
     import hashlib
     rec = NCU_TRAFFIC.get(kernel)
-    if not rec or not executed_flops_per_launch:
+    if not rec or not units_per_launch:
         return None
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), rec["source"])
     try:
@@ -83,7 +106,7 @@ def ncu_traffic(kernel, executed_flops_per_launch):
             return None
     except (OSError, ValueError):
         return None
-    return rec["bytes_per_executed_flop"] * executed_flops_per_launch
+    return rec["dram_per_unit"] * units_per_launch
 
 
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
@@ -578,8 +601,12 @@ def run_ours(args, rank, world, local_rank):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
+        if kernel_step:   # the main line's timed steps, for profilers' NVTX filters
+            torch.cuda.nvtx.range_push("timed")
         for _ in range(steps):
             step(sv)
+        if kernel_step:
+            torch.cuda.nvtx.range_pop()
         e1.record(stream)
         torch.cuda.synchronize()
         ck = clocks.stop()
