@@ -146,6 +146,8 @@ def parse():
     ap.add_argument("--fp64-tc", type=int, default=1, choices=[0, 1],
                     help="1: complex128 symmetric-form front updates and column panels on the BF16 tensor cores "
                          "by exact splitting (FP64 accuracy); 0: the FP64 pipe")
+    ap.add_argument("--sweep-split", type=int, default=0, choices=[0, 1, 2, 4, 8, 16],
+                    help="substitution products: 0 tuned per level, k warps of a block per item, 16 across the grid")
     ap.add_argument("--maxit", type=int, default=2000, help="FGMRES iteration limit per right-hand side")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="1: replay captured CUDA graphs of the factorization and of M^-1")
@@ -576,6 +578,8 @@ def run_ours(args, rank, world, local_rank):
         S.stdd_set_option(sv.ctx, S.STDD_OPT_STATIC_PIVOT, sp)
         S.stdd_set_option(sv.ctx, S.STDD_OPT_SYMMETRIC, args.symmetric)
         S.stdd_set_option(sv.ctx, S.STDD_OPT_FP64_TC, args.fp64_tc)
+        if args.sweep_split:
+            S.stdd_set_option(sv.ctx, S.STDD_OPT_SWEEP_SPLIT, args.sweep_split)
         return sv
 
     def step(sv):

@@ -416,7 +416,18 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     product's error is bounded like an FP64 dot product's
  *                     (relative to the row's and the column's largest
  *                     entries).  0: the FP64 pipe.  The two agree to
- *                     rounding.  Invalidates the factors. */
+ *                     rounding.  Invalidates the factors.
+ *   STDD_OPT_SWEEP_SPLIT (default 0): how the substitution products of a
+ *                     work item (a front's 16 or 32 rows) share its columns,
+ *                     which are summed in fixed segments of 128 columns whose
+ *                     sums are added in column order.  0: chosen per level
+ *                     by the autotuner; 1, 2, 4, 8: that many warps of one
+ *                     block per item; 16: one warp per (item, segment)
+ *                     anywhere on the GPU, the segment sums added by a
+ *                     second launch (32-row items; the FP64 pipe of one SM
+ *                     no longer bounds a root-level item).  Every choice
+ *                     gives the same sums in the same order: results do not
+ *                     change.  Applied at the next stdd_factor. */
 enum {
   STDD_OPT_GRAPHS = 1,
   STDD_OPT_AUTOTUNE = 2,
@@ -429,7 +440,8 @@ enum {
   STDD_OPT_SWEEP_WAIT = 9,
   STDD_OPT_UPDATE_TILE = 10,
   STDD_OPT_SYMMETRIC = 11,
-  STDD_OPT_FP64_TC = 12
+  STDD_OPT_FP64_TC = 12,
+  STDD_OPT_SWEEP_SPLIT = 13
 };
 stdd_status stdd_set_option(stdd_ctx *ctx, int option, int value);
 stdd_status stdd_get_profile(stdd_ctx *ctx, stdd_profile *out, int reset);

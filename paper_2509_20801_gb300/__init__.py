@@ -13,7 +13,7 @@ from .binding import (STDD_PREC_C64, STDD_PREC_C64_BF16, STDD_PREC_C64_FP16, STD
                       stdd_get_profile, stdd_get_stats, stdd_last_error, stdd_residual,
                       stdd_residual_noalloc,
                       stdd_set_profiling, stdd_set_option, STDD_OPT_GRAPHS, STDD_OPT_AUTOTUNE,
-                      STDD_OPT_LEAF, STDD_OPT_ORDER, STDD_OPT_BAND, STDD_OPT_STATIC_PIVOT, STDD_OPT_PIVOTING, STDD_OPT_PERSISTENT, STDD_OPT_SWEEP_WAIT, STDD_OPT_UPDATE_TILE, STDD_OPT_SYMMETRIC, STDD_OPT_FP64_TC, stdd_local_solve, stdd_nd_analyze,
+                      STDD_OPT_LEAF, STDD_OPT_ORDER, STDD_OPT_BAND, STDD_OPT_STATIC_PIVOT, STDD_OPT_PIVOTING, STDD_OPT_PERSISTENT, STDD_OPT_SWEEP_WAIT, STDD_OPT_UPDATE_TILE, STDD_OPT_SYMMETRIC, STDD_OPT_FP64_TC, STDD_OPT_SWEEP_SPLIT, stdd_local_solve, stdd_nd_analyze,
                       stdd_residual_history, stdd_set_decomposition, stdd_set_frequency,
                       stdd_set_grid, stdd_set_permittivity, stdd_set_pml, stdd_set_precision,
                       stdd_set_sources, stdd_solve, stdd_strip_info, stdd_tc_tile_product, stdd_tc_f64_tile_product, stdd_set_decomposition_2d, stdd_box_info)

@@ -304,6 +304,7 @@ STDD_OPT_SWEEP_WAIT = 9
 STDD_OPT_UPDATE_TILE = 10
 STDD_OPT_SYMMETRIC = 11
 STDD_OPT_FP64_TC = 12
+STDD_OPT_SWEEP_SPLIT = 13
 
 
 def stdd_set_profiling(ctx, level=1):

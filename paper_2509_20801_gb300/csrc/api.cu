@@ -216,6 +216,8 @@ struct stdd_ctx {
   int fp64_tc = 1;
   bool oz_active() const { return fp64_tc && sym_active() && prec == STDD_PREC_FP64; }
   DBuf d_lsx, d_lsy;
+  DBuf d_segpart;   // partial sums of the grid-split substitution products
+  int forced_split = 0;   // STDD_OPT_SWEEP_SPLIT: 0 tuned, else 1, 2, 4, 8 or MF_SPLIT_GRID
   int64_t nfronts = 0, factor_entries = 0;
   double factor_cflops = 0, factor_cflops_lu = 0, solve_cflops = 0;
   int max_p = 0, max_b = 0, depth = 0;
@@ -612,6 +614,7 @@ MfArgs stdd_ctx::mf_args(int par, bool solve) const {
   a.pcol = pivoting ? d_pcol.as<int>() : nullptr;
   a.panel = pivoting ? d_panel.p : nullptr;
   a.sym = sym_active() ? 1 : 0;
+  a.segpart = d_segpart.p;
   a.fp64_tc = oz_active() ? 1 : 0;
   a.lsx = a.sym ? d_lsx.as<double2>() : nullptr;
   a.lsy = a.sym ? d_lsy.as<double2>() : nullptr;
@@ -688,6 +691,24 @@ void stdd_ctx::factor() {
     if (prec == STDD_PREC_FP64) autotune<double>();
     else autotune<float>();
   }
+  if (forced_split) {
+    // one split everywhere it is valid (32-row items for the grid split, at
+    // most MF_MAXSEG segments for an in-block one); results do not change
+    for (auto &li : levels) {
+      auto pick = [&](int rows, int cols) {
+        int sp = forced_split;
+        if (sp == stdd::MF_SPLIT_GRID) {
+          if (rows == 32) return sp;
+          sp = 8;
+        }
+        if (sp > 256 / rows) sp = 256 / rows;
+        if (sp > 1 && (cols + stdd::MF_SEG - 1) / stdd::MF_SEG > stdd::MF_MAXSEG) sp = 1;
+        return sp;
+      };
+      li.split_up = li.split_up1 = pick(li.rows_up, li.max_p);
+      li.split_down = li.split_down1 = pick(li.rows_down, li.max_n);
+    }
+  }
   build_strip_levels();
 }
 
@@ -707,8 +728,14 @@ void stdd_ctx::build_strip_levels() {
       l.down_n = lvl_down[L][j + 1] - lvl_down[L][j];
       l.rows_up = li.rows_up;
       l.rows_down = li.rows_down;
-      l.split_up = li.split_up1;
-      l.split_down = li.split_down1;
+      // (the persistent kernel splits within a block only; any split gives
+      // the same sums)
+      auto inblock = [](int sp, int cols) {
+        if (sp > 8) sp = 8;
+        return (sp > 1 && (cols + stdd::MF_SEG - 1) / stdd::MF_SEG > stdd::MF_MAXSEG) ? 1 : sp;
+      };
+      l.split_up = inblock(li.split_up1, li.max_p);
+      l.split_down = inblock(li.split_down1, li.max_n);
       l.max_n = li.max_n;
       l.pad_ = 0;
     }
@@ -952,6 +979,17 @@ void stdd_ctx::build_structure() {
     }
     li.n_down = (int)((int64_t)items.size() - li.down_off);
   }
+  {
+    // partial sums of the grid-split products: every item of a level times
+    // its segments (32 rows each), for the widest level
+    int64_t need = 1;
+    for (int L = 0; L < depth; ++L) {
+      const LevelInfo &li = levels[L];
+      const int64_t su = (li.max_p + stdd::MF_SUB - 1) / stdd::MF_SUB, sd = (li.max_n + stdd::MF_SUB - 1) / stdd::MF_SUB;
+      need = std::max(need, std::max((int64_t)li.n_up * su, (int64_t)li.n_down * sd) * 32);
+    }
+    d_segpart.alloc((size_t)need * sizeof(double2));
+  }
   // owner of every column (the strip, or the box column kx) and of every row
   // (the box row ky)
   std::vector<int> colstrip(nx), rowbox(ny);
@@ -1031,15 +1069,21 @@ template <typename R> void stdd_ctx::autotune() {
         }
         if (!found) {
           float best_ms = 1e30f;
-          for (int sp = 1; sp <= 8; sp *= 2) {
-            if (sp > 256 / rows) break;
-            if (sp > 1 && (cols + stdd::MF_SEG - 1) / stdd::MF_SEG > stdd::MF_MAXSEG) break;
+          // in-block splits 1, 2, 4, 8, then the grid split (one warp per
+          // segment anywhere on the GPU) for items of 32 rows and several segments
+          for (int sp = 1; sp <= stdd::MF_SPLIT_GRID; sp *= 2) {
+            if (sp == stdd::MF_SPLIT_GRID) {
+              if (rows != 32 || cols <= stdd::MF_SEG) break;
+            } else {
+              if (sp > 256 / rows) continue;
+              if (sp > 1 && (cols + stdd::MF_SEG - 1) / stdd::MF_SEG > stdd::MF_MAXSEG) continue;
+            }
             float ms_min = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
               MfArgs a = mf_args(L & 1, true);
               CK(cudaEventRecord(e0, stream));
-              if (dir == 0) stdd::mf_up_level<R>(a, items + first, nitems, rows, sp, 1, nloc, stream);
-              else stdd::mf_down_level<R>(a, items + first, nitems, rows, sp, 1, nloc, stream);
+              if (dir == 0) stdd::mf_up_level<R>(a, items + first, nitems, rows, sp, 1, nloc, stream, cols);
+              else stdd::mf_down_level<R>(a, items + first, nitems, rows, sp, 1, nloc, stream, cols);
               CK(cudaEventRecord(e1, stream));
               CK(cudaEventSynchronize(e1));
               float ms = 0;
@@ -1198,14 +1242,14 @@ template <typename R> void stdd_ctx::solve_levels(int nr) {
     stdd::mf_up_gather_level<R>(mf_args(L & 1, true), li, nr, nloc, stream);
     hook.before(stdd::K_UP, L, 0);
     stdd::mf_up_level<R>(mf_args(L & 1, true), items + li.up_off, li.n_up, li.rows_up, li.split_up, nr, nloc,
-                         stream);
+                         stream, li.max_p);
     hook.after(stdd::K_UP, L, 0);
   }
   for (int L = 0; L < depth; ++L) {
     const LevelInfo &li = levels[L];
     hook.before(stdd::K_DOWN, L, 0);
     stdd::mf_down_level<R>(mf_args(L & 1, true), items + li.down_off, li.n_down, li.rows_down, li.split_down, nr,
-                           nloc, stream);
+                           nloc, stream, li.max_n);
     hook.after(stdd::K_DOWN, L, 0);
   }
   CK(cudaGetLastError());
@@ -1228,7 +1272,7 @@ template <typename R> void stdd_ctx::solve_range_levels(int j0, int j1, int nr) 
     stdd::mf_up_gather_level<R>(mf_args(L & 1, true), li, nr, nloc, stream);
     hook.before_part(stdd::K_UP, L, levels[L].n_up ? (double)cnt / levels[L].n_up : 0.0);
     stdd::mf_up_level<R>(mf_args(L & 1, true), items + li.up_off + lvl_up[L][j0], cnt, li.rows_up,
-                         j1 - j0 == 1 ? li.split_up1 : li.split_up, nr, nloc, stream);
+                         j1 - j0 == 1 ? li.split_up1 : li.split_up, nr, nloc, stream, li.max_p);
     hook.after(stdd::K_UP, L, 0);
   }
   for (int L = 0; L < depth; ++L) {
@@ -1237,7 +1281,7 @@ template <typename R> void stdd_ctx::solve_range_levels(int j0, int j1, int nr) 
     if (cnt == 0) continue;
     hook.before_part(stdd::K_DOWN, L, li.n_down ? (double)cnt / li.n_down : 0.0);
     stdd::mf_down_level<R>(mf_args(L & 1, true), items + li.down_off + lvl_down[L][j0], cnt, li.rows_down,
-                           j1 - j0 == 1 ? li.split_down1 : li.split_down, nr, nloc, stream);
+                           j1 - j0 == 1 ? li.split_down1 : li.split_down, nr, nloc, stream, li.max_n);
     hook.after(stdd::K_DOWN, L, 0);
   }
   CK(cudaGetLastError());
@@ -1417,12 +1461,12 @@ template <typename R> void stdd_ctx::solve_levels_band(int nr) {
     const LevelInfo &li = levels[L];
     stdd::mf_up_gather_level<R>(mf_args(L & 1, true), li, nr, nloc, stream);
     stdd::mf_up_level<R>(mf_args(L & 1, true), items + lvl_bup_off[L], lvl_bup_n[L], li.rows_up, li.split_up, nr,
-                         nloc, stream);
+                         nloc, stream, li.max_p);
   }
   for (int L = 0; L < depth; ++L) {
     const LevelInfo &li = levels[L];
     stdd::mf_down_level<R>(mf_args(L & 1, true), items + lvl_bdown_off[L], lvl_bdown_n[L], li.rows_down,
-                           li.split_down, nr, nloc, stream);
+                           li.split_down, nr, nloc, stream, li.max_n);
   }
   CK(cudaGetLastError());
 }
@@ -1941,7 +1985,7 @@ int64_t stdd_ctx::device_bytes() const {
                        &d_inv, &d_lcxm, &d_lcxp, &d_colstrip, &d_lcym, &d_lcyp, &d_rowbox, &d_fac, &d_ws[0], &d_ws[1], &d_ub[0],
                        &d_ub[1], &d_tloc, &d_wloc, &d_items, &d_flag, &d_minpiv, &d_b, &d_x, &d_r, &d_V, &d_Z, &d_w,
                        &d_part, &d_h, &d_nrm, &d_y, &d_pre, &d_fpart, &d_guess, &d_gscr, &d_pcol, &d_panel,
-                       &d_striplv, &d_bar, &d_sweep_flag, &d_lsx, &d_lsy};
+                       &d_striplv, &d_bar, &d_sweep_flag, &d_lsx, &d_lsy, &d_segpart};
   int64_t s = 0;
   for (auto *d : all) s += (int64_t)d->bytes;
   return s;
@@ -2451,6 +2495,13 @@ stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
           c->invalidate_factors();
           c->clear_graphs();
         }
+        break;
+      case STDD_OPT_SWEEP_SPLIT:
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != stdd::MF_SPLIT_GRID)
+          throw ArgError("sweep split must be 0 (tuned), 1, 2, 4, 8 or 16 (across the grid)");
+        c->forced_split = value;
+        c->invalidate_factors();
+        c->clear_graphs();
         break;
       case STDD_OPT_FP64_TC:
         if (value < 0 || value > 1) throw ArgError("fp64 tensor-core updates must be 0 (off) or 1 (on)");

@@ -16,6 +16,9 @@ constexpr int MF_PANEL_THREADS = 128; // rows / columns per panel tile
 constexpr int MF_SMALL = 64;          // fronts with n <= MF_SMALL are swept in shared memory
 constexpr int MF_SEG = 128;           // columns per fixed summation segment of the sweeps
 constexpr int MF_MAXSEG = 16;         // segments an item may have when its columns are split
+constexpr int MF_SPLIT_GRID = 16;     // split value: one warp per (item, sub-segment) anywhere in the grid
+constexpr int MF_SUB = 32;            // columns per chain inside a segment (segment = chains added in order)
+static_assert(MF_SEG % MF_SUB == 0, "segments are whole sub-segments");
 
 // Everything a multifrontal kernel needs (device pointers).
 struct MfArgs {
@@ -54,6 +57,10 @@ struct MfArgs {
   // complex128 symmetric form: 1 = large-front updates on the tensor cores
   // by exact splitting into BF16 slices (FP64 accuracy), 0 = FP64 pipe
   int fp64_tc;
+  // substitution products split across the grid (split == MF_SPLIT_GRID):
+  // one partial sum per (work item, column segment, row), summed in segment
+  // order by a second launch
+  void *segpart;
 };
 
 struct LevelInfo {
@@ -120,10 +127,10 @@ cudaError_t mf_strip_sweep_launch(const MfArgs &a, const void *ub0, const void *
 int mf_strip_sweep_grid();   // blocks of the persistent sweep (co-resident); call outside stream capture
 template <typename R>
 void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
-                 cudaStream_t st);
+                 cudaStream_t st, int cols_max = 0);
 template <typename R>
 void mf_down_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
-                   cudaStream_t st);
+                   cudaStream_t st, int cols_max = 0);
 
 // ---- FDFD / DDM vector kernels (kernels_fdfd.cu)
 struct GridDev {

@@ -914,8 +914,12 @@ __device__ __forceinline__ void seg_dot(const C *__restrict__ M, int64_t ld, int
   constexpr int U0 = sizeof(C) == 16 ? 8 : 32;  // FP64 is ALU-bound: fewer loads, more warps
   constexpr int U = NR > 1 ? (U0 / NR > 4 ? U0 / NR : 4) : U0;
   constexpr int UU = U < ROWS ? U : ROWS;
+  static_assert(MF_SUB % ROWS == 0, "a sub-segment is a whole number of chunks");
+  // each MF_SUB columns form a chain of their own (sub), folded into the
+  // segment sum in column order: acc = ((s0 + s1) + s2) + s3
+  C sub[NR];
 #pragma unroll
-  for (int q = 0; q < NR; ++q) acc[q] = czero<C>();
+  for (int q = 0; q < NR; ++q) acc[q] = sub[q] = czero<C>();
   C vn[NR];
 #pragma unroll
   for (int q = 0; q < NR; ++q) vn[q] = c0 + lane < c1 ? gather(c0 + lane, q) : czero<C>();
@@ -931,6 +935,10 @@ __device__ __forceinline__ void seg_dot(const C *__restrict__ M, int64_t ld, int
     for (int u = 0; u < UU; ++u) m[u] = row ? M[(int64_t)(c0 + u) * ld + r] : czero<C>();
   }
   for (int cb = c0; cb < c1; cb += ROWS) {
+    if ((cb - c0) % MF_SUB == 0) {
+#pragma unroll
+      for (int q = 0; q < NR; ++q) sub[q] = czero<C>();
+    }
     C v[NR];
 #pragma unroll
     for (int q = 0; q < NR; ++q) v[q] = vn[q];
@@ -951,7 +959,7 @@ __device__ __forceinline__ void seg_dot(const C *__restrict__ M, int64_t ld, int
 #pragma unroll
           for (int u = 0; u < UU; ++u)
 #pragma unroll
-            for (int q = 0; q < NR; ++q) acc[q] = cfma(m[u], shfl_w<ROWS>(mask, v[q], u0 + u), acc[q]);
+            for (int q = 0; q < NR; ++q) sub[q] = cfma(m[u], shfl_w<ROWS>(mask, v[q], u0 + u), sub[q]);
 #pragma unroll
           for (int u = 0; u < UU; ++u) m[u] = mn[u];
         } else {
@@ -960,7 +968,7 @@ __device__ __forceinline__ void seg_dot(const C *__restrict__ M, int64_t ld, int
 #pragma unroll
           for (int u = 0; u < UU; ++u)
 #pragma unroll
-            for (int q = 0; q < NR; ++q) acc[q] = cfma(m[u], shfl_w<ROWS>(mask, v[q], u0 + u), acc[q]);
+            for (int q = 0; q < NR; ++q) sub[q] = cfma(m[u], shfl_w<ROWS>(mask, v[q], u0 + u), sub[q]);
         }
       }
     } else {
@@ -973,13 +981,18 @@ __device__ __forceinline__ void seg_dot(const C *__restrict__ M, int64_t ld, int
 #pragma unroll
         for (int t = 0; t < 4; ++t)
 #pragma unroll
-          for (int q = 0; q < NR; ++q) acc[q] = cfma(m[t], shfl_w<ROWS>(mask, v[q], u + t), acc[q]);
+          for (int q = 0; q < NR; ++q) sub[q] = cfma(m[t], shfl_w<ROWS>(mask, v[q], u + t), sub[q]);
       }
       for (; u < nv; ++u) {
         const C m = row ? M[(int64_t)(cb + u) * ld + r] : czero<C>();
 #pragma unroll
-        for (int q = 0; q < NR; ++q) acc[q] = cfma(m, shfl_w<ROWS>(mask, v[q], u), acc[q]);
+        for (int q = 0; q < NR; ++q) sub[q] = cfma(m, shfl_w<ROWS>(mask, v[q], u), sub[q]);
       }
+    }
+    if ((cb + ROWS - c0) % MF_SUB == 0 || cb + ROWS >= c1) {
+      const bool first = cb - c0 < MF_SUB;
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[q] = first ? sub[q] : cadd(acc[q], sub[q]);
     }
   }
 }
@@ -1211,6 +1224,85 @@ __global__ void __launch_bounds__(256, 2) mf_down(MfArgs a, const int2 *__restri
   down_block<R, ROWS, NR>(a, items, nitems, split, nrhs, ldt, blockIdx.x, part);
 }
 
+// Products split across the grid: one warp per (work item, MF_SUB-column
+// chain) anywhere in the grid writes the chain's sum per row, and a second
+// launch folds the chains into segment sums and the segment sums into the
+// total, in column order -- the association seg_dot and the in-block
+// split use, so the choice between them changes no result.  At the top tree levels a few fronts
+// carry a whole phase; an in-block split keeps an item on one SM, whose FP64
+// pipe then sets the phase time.
+template <typename R, bool UP>
+__global__ void __launch_bounds__(256) mf_seg_partial(MfArgs a, const int2 *__restrict__ items, int nitems,
+                                                      int nsubmax) {
+  using C = typename CT<R>::T;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t u = (int64_t)blockIdx.x * 8 + warp;
+  if (u >= (int64_t)nitems * nsubmax) return;
+  const int it = (int)(u / nsubmax), sg = (int)(u - (int64_t)it * nsubmax);
+  const int2 item = items[it];
+  const FrontDev f = a.fronts[item.x];
+  const int p = f.p, b = f.b, n = p + b;
+  const int cols = UP ? p : n;
+  if (sg * MF_SUB >= cols) return;
+  const int64_t voff = a.strips[f.strip].vec_off;
+  const int *nodes = a.nodes + f.node_off;
+  const int *pc = a.pcol ? a.pcol + f.piv_off : nullptr;
+  const C *wl = reinterpret_cast<const C *>(a.wloc);
+  const C *tv = reinterpret_cast<const C *>(a.tloc);
+  const C *fac = reinterpret_cast<const C *>(a.fac) + f.fac_off;
+  const int r = item.y * 32 + lane;
+  const bool row = r < (UP ? b : p);
+  C sv[1];
+  if (UP) {
+    auto gather = [&](int j, int) { return wl[voff + nodes[pc ? pc[j] : j]]; };
+    seg_dot<32, 1, true, C>(fac + (int64_t)p * n, b, r, row, sg * MF_SUB, min(cols, (sg + 1) * MF_SUB), lane,
+                            0xffffffffu, gather, sv);
+  } else {
+    auto gather = [&](int c, int) {
+      return c < p ? wl[voff + nodes[pc ? pc[c] : c]] : cneg(tv[voff + nodes[c]]);
+    };
+    seg_dot<32, 1, true, C>(fac, p, r, row, sg * MF_SUB, min(cols, (sg + 1) * MF_SUB), lane, 0xffffffffu, gather,
+                            sv);
+  }
+  reinterpret_cast<C *>(a.segpart)[u * 32 + lane] = sv[0];
+}
+
+template <typename R, bool UP>
+__global__ void __launch_bounds__(256) mf_seg_reduce(MfArgs a, const int2 *__restrict__ items, int nitems,
+                                                     int nsubmax) {
+  using C = typename CT<R>::T;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int it = (int)(t >> 5), lane = (int)(t & 31);
+  if (it >= nitems) return;
+  const int2 item = items[it];
+  const FrontDev f = a.fronts[item.x];
+  const int p = f.p, b = f.b;
+  const int r = item.y * 32 + lane;
+  if (r >= (UP ? b : p)) return;
+  const int cols = UP ? p : p + b;
+  const int nsub = (cols + MF_SUB - 1) / MF_SUB, per = MF_SEG / MF_SUB;
+  const C *P = reinterpret_cast<const C *>(a.segpart) + (int64_t)it * nsubmax * 32 + lane;
+  C *u = reinterpret_cast<C *>(a.ub_cur) + f.u_off;
+  C total = UP ? u[r] : czero<C>();
+  for (int k0 = 0; k0 < nsub; k0 += per) {
+    C seg = P[k0 * 32];
+    for (int k = k0 + 1; k < min(k0 + per, nsub); ++k) seg = cadd(seg, P[k * 32]);
+    total = cadd(total, seg);
+  }
+  if (UP) u[r] = total;
+  else reinterpret_cast<C *>(a.tloc)[a.strips[f.strip].vec_off + a.nodes[f.node_off + r]] = total;
+}
+
+template <typename R, bool UP>
+void mf_seg_launch(const MfArgs &a, const int2 *items, int nitems, int cols_max, int64_t ldt, cudaStream_t st) {
+  (void)ldt;   // one right-hand side
+  const int nsubmax = (cols_max + MF_SUB - 1) / MF_SUB;
+  const int64_t units = (int64_t)nitems * nsubmax;
+  mf_seg_partial<R, UP><<<(unsigned)((units + 7) / 8), 256, 0, st>>>(a, items, nitems, nsubmax);
+  mf_seg_reduce<R, UP><<<(unsigned)(((int64_t)nitems * 32 + 255) / 256), 256, 0, st>>>(a, items, nitems, nsubmax);
+  count_launch(2);
+}
+
 // ------------------------------------------- persistent one-strip sweep
 // Grid-wide barrier of a cooperative launch: bar[0] counts arrivals, bar[1]
 // is the generation.  A block that polls more than `limit` times sets bit 0
@@ -1417,9 +1509,17 @@ void mf_up_gather_level(const MfArgs &a, const LevelInfo &L, int nrhs, int64_t l
 
 template <typename R>
 void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
-                 cudaStream_t st) {
+                 cudaStream_t st, int cols_max) {
   if (nitems == 0) return;
   if (nrhs > 1) split = 1;  // several right-hand sides: every group keeps its segments in registers
+  if (split == MF_SPLIT_GRID) {
+    if (rows == 32 && a.segpart && cols_max > 0) {
+      mf_seg_launch<R, true>(a, items, nitems, cols_max, ldt, st);
+      return;
+    }
+    split = 1;
+  }
+  if (split > 1 && cols_max > 0 && (cols_max + MF_SEG - 1) / MF_SEG > MF_MAXSEG) split = 1;
   const int ipc = (256 / rows) / split;
   const int grid = (nitems + ipc - 1) / ipc;
   const int nr = (nrhs >= 4 && sizeof(R) == 4) ? 4 : (nrhs >= 2 ? 2 : 1);
@@ -1435,9 +1535,17 @@ void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int rows, int s
 
 template <typename R>
 void mf_down_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
-                   cudaStream_t st) {
+                   cudaStream_t st, int cols_max) {
   if (nitems == 0) return;
   if (nrhs > 1) split = 1;
+  if (split == MF_SPLIT_GRID) {
+    if (rows == 32 && a.segpart && cols_max > 0) {
+      mf_seg_launch<R, false>(a, items, nitems, cols_max, ldt, st);
+      return;
+    }
+    split = 1;
+  }
+  if (split > 1 && cols_max > 0 && (cols_max + MF_SEG - 1) / MF_SEG > MF_MAXSEG) split = 1;
   const int ipc = (256 / rows) / split;
   const int grid = (nitems + ipc - 1) / ipc;
   const int nr = (nrhs >= 4 && sizeof(R) == 4) ? 4 : (nrhs >= 2 ? 2 : 1);
@@ -1516,9 +1624,9 @@ template void mf_factor_level<double>(const MfArgs &, const LevelInfo &, int, cu
 template void mf_factor_level<float>(const MfArgs &, const LevelInfo &, int, cudaStream_t, LaunchHook *, int);
 template void mf_up_gather_level<double>(const MfArgs &, const LevelInfo &, int, int64_t, cudaStream_t);
 template void mf_up_gather_level<float>(const MfArgs &, const LevelInfo &, int, int64_t, cudaStream_t);
-template void mf_up_level<double>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t);
-template void mf_up_level<float>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t);
-template void mf_down_level<double>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t);
-template void mf_down_level<float>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t);
+template void mf_up_level<double>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t, int);
+template void mf_up_level<float>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t, int);
+template void mf_down_level<double>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t, int);
+template void mf_down_level<float>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t, int);
 
 }  // namespace stdd

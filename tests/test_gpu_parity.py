@@ -387,3 +387,38 @@ def test_update_tile_shapes_give_identical_factors(cyl, precision):
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
     if precision == 0:
         assert _rel(outs[0], D.apply_Minv(v_h)) < 1e-10
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_sweep_splits_give_identical_results(cyl, order):
+    """The substitution products summed by one warp per item, by up to eight
+    warps of a block, or by one warp per 128-column segment anywhere on the
+    GPU (partial sums added by a second launch) add the same segment sums in
+    the same order: M^-1 bitwise equal across the forced splits and the
+    tuned one, and equal to the oracle's (additive and multiplicative
+    orders, per-level and persistent sweeps)."""
+    from paper_2509_20801_gb300 import (STDD_OPT_ORDER, STDD_OPT_PERSISTENT, STDD_OPT_SWEEP_SPLIT, StddError,
+                                        stdd_apply_preconditioner, stdd_set_option)
+    w, P, D = cyl
+    v_h = W.random_vector(P.n, seed=18)[0]
+    v = torch.from_numpy(v_h).to(DEV)
+    outs = []
+    for split, persistent in ((1, 0), (8, 0), (16, 0), (0, 0), (16, 2)):
+        if persistent and order == 0:
+            continue
+        s = _solver(w)
+        stdd_set_option(s.ctx, STDD_OPT_ORDER, order)
+        stdd_set_option(s.ctx, STDD_OPT_PERSISTENT, persistent)
+        stdd_set_option(s.ctx, STDD_OPT_SWEEP_SPLIT, split)
+        s.factor()
+        z = torch.empty_like(v)
+        stdd_apply_preconditioner(s.ctx, v, z)
+        outs.append(z.cpu().numpy())
+        if split == 16:
+            with pytest.raises(StddError):
+                stdd_set_option(s.ctx, STDD_OPT_SWEEP_SPLIT, 3)
+        s.close()
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+    ref = D.apply_Minv(v_h) if order == 0 else D.apply_Minv_multiplicative(v_h)
+    assert _rel(outs[0], ref) < 1e-10
