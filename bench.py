@@ -53,7 +53,7 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor and tensor), NVIDIA's fi
 _MF = "paper_2509_20801_gb300/csrc/kernels_mf.cu"
 _SWEEP = ("// ------------------------------------------------------- substitutions",
           "// ------------------------------------------- persistent one-strip sweep",
-          "47c9e6f78c16e1860f8bbced91945bf5c23798b825912bdfe5f192f0f4a48943")
+          "ea9751078cfacf61ca83fc796e7d0770947114ba731f3a73251f76023d906944")
 NCU_TRAFFIC = {
     "mf_gj_update<double>": {
         "dram_per_unit": 1394.992640e6 / 11.533996032e9,   # 3 launches: DRAM bytes / executed flops
@@ -80,14 +80,9 @@ NCU_TRAFFIC = {
         "profile": "profiles/ncu_mf_gj_update_oz_fp64_waveguide_2048x512.md",
     },
     "mf_down<double>": {
-        "dram_per_unit": 67.64e6 / 66.270848e6,             # DRAM bytes / factor bytes of the launch
+        "dram_per_unit": 158.494e6 / 131.123e6,   # one strip solve's 14 launches: DRAM bytes / factor bytes
         "source": _MF, "begin": _SWEEP[0], "end": _SWEEP[1], "sha256": _SWEEP[2],
-        "profile": "profiles/ncu_dram_mf_down_mf_up_fp64_waveguide_2048x512.md",
-    },
-    "mf_up<double>": {
-        "dram_per_unit": 6.499e6 / 6.357680e6,
-        "source": _MF, "begin": _SWEEP[0], "end": _SWEEP[1], "sha256": _SWEEP[2],
-        "profile": "profiles/ncu_dram_mf_down_mf_up_fp64_waveguide_2048x512.md",
+        "profile": "profiles/ncu_dram_mf_down_fp64_waveguide_2048x512.md",
     },
 }
 
