@@ -135,9 +135,9 @@ def parse():
     ap.add_argument("--pivoting", type=int, default=None, choices=[0, 1],
                     help="partial pivoting within the fronts for the complex64 forms (default 1 on the "
                          "waveguide, else 0)")
-    ap.add_argument("--symmetric", type=int, default=1, choices=[0, 1],
-                    help="1: factor the symmetric form D A of each strip (lower-triangle front updates) "
-                         "wherever there is no partial pivoting")
+    ap.add_argument("--symmetric", type=int, default=1, choices=[0, 1, 2],
+                    help="1: factor the symmetric form D A of each strip (lower-triangle front updates) for "
+                         "complex128 factors without partial pivoting; 2: complex64 factors too")
     ap.add_argument("--fp64-tc", type=int, default=1, choices=[0, 1],
                     help="1: complex128 symmetric-form front updates and column panels on the BF16 tensor cores "
                          "by exact splitting (FP64 accuracy); 0: the FP64 pipe")
@@ -713,7 +713,8 @@ def run_ours(args, rank, world, local_rank):
         kernels[name] = k
 
     tname = "double" if prec == S.STDD_PREC_FP64 else "float"
-    sym = bool(args.symmetric and not pivots_for(prec)[0] and not tensor)
+    sym = bool(args.symmetric and not pivots_for(prec)[0] and not tensor and (
+        prec == S.STDD_PREC_FP64 or args.symmetric == 2))
     oz = sym and args.fp64_tc and prec == S.STDD_PREC_FP64
     if oz:
         # the split products on the BF16 tensor pipe: their own flops against
@@ -769,7 +770,8 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": workload_desc(w), "precision": args.precision, "order": args.order,
                    "pivoting": pivots_for(prec)[0], "static_pivot": pivots_for(prec)[1],
-                   "symmetric_form": int(bool(args.symmetric and not pivots_for(prec)[0] and not tensor)),
+                   "symmetric_form": int(bool(args.symmetric and not pivots_for(prec)[0] and not tensor and (
+                       prec == S.STDD_PREC_FP64 or args.symmetric == 2))),
                    "fp64_products": ("BF16 tensor cores, exact 8 x 7-bit splitting" if (
                        args.fp64_tc and args.symmetric and prec == S.STDD_PREC_FP64) else "FP64 pipe"),
                    "persistent_sweeps": (args.persistent if args.persistent >= 0 else

@@ -400,9 +400,16 @@ stdd_status stdd_set_profiling(stdd_ctx *ctx, int level);
  *                     Used when STDD_OPT_PIVOTING is 0 (row interchanges
  *                     break the symmetry) and the factors are not formed
  *                     with tensor-core updates (STDD_PREC_C64_BF16 /
- *                     _FP16 update whole tiles); 0: the factors of A_i as
- *                     assembled.  The two agree to rounding.  Invalidates
- *                     the factors.
+ *                     _FP16 update whole tiles).  1: complex128 factors;
+ *                     2: complex64 factors too (in single precision the
+ *                     scaling by D, up to the PML's largest |s_x s_y| apart
+ *                     between rows, adds element growth that the unpivoted
+ *                     sweep cannot afford on resonant geometries: the
+ *                     48-geometry ellipse batch then needs 192 instead of
+ *                     31 red-black iterations, 4 of its 2048-wide
+ *                     geometries no longer converging); 0: the factors of
+ *                     A_i as assembled.  The forms agree to rounding.
+ *                     Invalidates the factors.
  *   STDD_OPT_FP64_TC (default 1): complex128 factors in the symmetric form
  *                     compute the large-front update products on the BF16
  *                     tensor cores by exact splitting (the scheme of Ozaki,

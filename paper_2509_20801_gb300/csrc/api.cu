@@ -209,8 +209,10 @@ struct stdd_ctx {
   // symmetric form (STDD_OPT_SYMMETRIC): fronts of D A, D = the local
   // stretch products s_x s_y, with lower-half updates; not with pivoting
   // nor with the tensor-core updates (which update whole tiles)
-  int symmetric = 1;
-  bool sym_active() const { return symmetric && !pivoting && tc_fmt() < 0; }
+  int symmetric = 1;   // 1: complex128 factors, 2: complex64 ones too
+  bool sym_active() const {
+    return symmetric && !pivoting && tc_fmt() < 0 && (prec == STDD_PREC_FP64 || symmetric == 2);
+  }
   // complex128 symmetric form: large-front updates on the tensor cores by
   // exact splitting (STDD_OPT_FP64_TC)
   int fp64_tc = 1;
@@ -2489,7 +2491,8 @@ stdd_status stdd_set_option(stdd_ctx *c, int option, int value) {
         }
         break;
       case STDD_OPT_SYMMETRIC:
-        if (value < 0 || value > 1) throw ArgError("symmetric must be 0 (off) or 1 (on)");
+        if (value < 0 || value > 2)
+          throw ArgError("symmetric must be 0 (off), 1 (complex128 factors) or 2 (complex64 factors too)");
         if (value != c->symmetric) {
           c->symmetric = value;
           c->invalidate_factors();
