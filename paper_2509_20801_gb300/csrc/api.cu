@@ -1241,10 +1241,9 @@ template <typename R> void stdd_ctx::solve_levels(int nr) {
   hook.c = this;
   for (int L = depth - 1; L >= 0; --L) {
     const LevelInfo &li = levels[L];
-    stdd::mf_up_gather_level<R>(mf_args(L & 1, true), li, nr, nloc, stream);
     hook.before(stdd::K_UP, L, 0);
     stdd::mf_up_level<R>(mf_args(L & 1, true), items + li.up_off, li.n_up, li.rows_up, li.split_up, nr, nloc,
-                         stream, li.max_p);
+                         stream, li.max_p, true);
     hook.after(stdd::K_UP, L, 0);
   }
   for (int L = 0; L < depth; ++L) {
@@ -1271,10 +1270,9 @@ template <typename R> void stdd_ctx::solve_range_levels(int j0, int j1, int nr) 
     li.nf = lvl_front[L][j1] - lvl_front[L][j0];
     if (li.nf == 0) continue;
     const int cnt = lvl_up[L][j1] - lvl_up[L][j0];
-    stdd::mf_up_gather_level<R>(mf_args(L & 1, true), li, nr, nloc, stream);
     hook.before_part(stdd::K_UP, L, levels[L].n_up ? (double)cnt / levels[L].n_up : 0.0);
     stdd::mf_up_level<R>(mf_args(L & 1, true), items + li.up_off + lvl_up[L][j0], cnt, li.rows_up,
-                         j1 - j0 == 1 ? li.split_up1 : li.split_up, nr, nloc, stream, li.max_p);
+                         j1 - j0 == 1 ? li.split_up1 : li.split_up, nr, nloc, stream, li.max_p, true);
     hook.after(stdd::K_UP, L, 0);
   }
   for (int L = 0; L < depth; ++L) {

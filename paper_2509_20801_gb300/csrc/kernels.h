@@ -127,7 +127,7 @@ cudaError_t mf_strip_sweep_launch(const MfArgs &a, const void *ub0, const void *
 int mf_strip_sweep_grid();   // blocks of the persistent sweep (co-resident); call outside stream capture
 template <typename R>
 void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
-                 cudaStream_t st, int cols_max = 0);
+                 cudaStream_t st, int cols_max = 0, bool fused = false);
 template <typename R>
 void mf_down_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
                    cudaStream_t st, int cols_max = 0);

@@ -1001,6 +1001,67 @@ __device__ __forceinline__ void seg_dot(const C *__restrict__ M, int64_t ld, int
 // the children's update vectors (inverse extend-add maps); w_p goes to the
 // pivot slots of wloc (kept for the way down) and w_b is the initial value
 // of the front's update vector.
+// What the upward sweep gathers for front f: at pivot position k < p the
+// source entry (times s_x s_y in the symmetric form) plus the children's
+// update vectors there, at border position k >= p the children's update
+// vectors alone.  The same arithmetic serves the gather kernels and the
+// products that gather on the fly (fused).
+template <typename C> struct WSrc {
+  const int *nodes, *inv[2];
+  const C *uc[2];
+  int bc[2];
+  int64_t voff, coef_off, ycoef_off;
+  int Hl;
+  bool sym;
+};
+template <typename C>
+__device__ __forceinline__ WSrc<C> wsrc_make(const MfArgs &a, const FrontDev &f, int nrhs) {
+  WSrc<C> w;
+  const StripDev st = a.strips[f.strip];
+  w.nodes = a.nodes + f.node_off;
+  w.voff = st.vec_off;
+  w.coef_off = st.coef_off;
+  w.ycoef_off = st.ycoef_off;
+  w.Hl = st.y1 - st.y0;
+  w.sym = a.sym != 0;
+#pragma unroll
+  for (int ci = 0; ci < 2; ++ci) {
+    w.inv[ci] = nullptr;
+    w.uc[ci] = nullptr;
+    w.bc[ci] = 0;
+    if (f.child[ci] >= 0) {
+      const FrontDev ch = a.fronts[f.child[ci]];
+      w.inv[ci] = a.inv + f.inv_off[ci];
+      w.uc[ci] = reinterpret_cast<const C *>(a.ub_child) + ch.u_off * nrhs;
+      w.bc[ci] = ch.b;
+    }
+  }
+  return w;
+}
+// children's update vectors at position k, added to w in child order
+template <typename C>
+__device__ __forceinline__ C wsrc_children(const WSrc<C> &s, int k, int q, C w) {
+#pragma unroll
+  for (int ci = 0; ci < 2; ++ci)
+    if (s.uc[ci]) {
+      const int t = s.inv[ci][k];
+      if (t >= 0) w = cadd(w, s.uc[ci][(int64_t)q * s.bc[ci] + t]);
+    }
+  return w;
+}
+// pivot position k < p; *gi = its slot in tloc / wloc
+template <typename C>
+__device__ __forceinline__ C wsrc_pivot(const MfArgs &a, const WSrc<C> &s, int k, int q, int64_t ldt, int64_t *gi) {
+  const int node = s.nodes[k];
+  *gi = q * ldt + s.voff + node;
+  C w = reinterpret_cast<const C *>(a.tloc)[*gi];
+  if (s.sym) {   // the source of D A x = D t
+    const int ux = node / s.Hl, uy = node - ux * s.Hl;
+    w = cmul(w, to_c(cmul(a.lsx[s.coef_off + ux], a.lsy[s.ycoef_off + uy]), C()));
+  }
+  return wsrc_children(s, k, q, w);
+}
+
 // one entry k of front f0 + fi, every right-hand side (k >= n: nothing)
 template <typename R> __device__ __forceinline__ void up_gather_elem(const MfArgs &a, int f0, int fi, int k, int nrhs,
                                                                      int64_t ldt) {
@@ -1008,45 +1069,17 @@ template <typename R> __device__ __forceinline__ void up_gather_elem(const MfArg
   const FrontDev f = a.fronts[f0 + fi];
   const int p = f.p, b = f.b, n = p + b;
   if (k >= n) return;
-  const int64_t voff = a.strips[f.strip].vec_off;
-  int t[2] = {-1, -1}, bc[2] = {0, 0};
-  const C *uc[2] = {nullptr, nullptr};
-#pragma unroll
-  for (int ci = 0; ci < 2; ++ci) {
-    if (f.child[ci] >= 0) {
-      t[ci] = a.inv[f.inv_off[ci] + k];
-      if (t[ci] >= 0) {
-        const FrontDev ch = a.fronts[f.child[ci]];
-        bc[ci] = ch.b;
-        uc[ci] = reinterpret_cast<const C *>(a.ub_child) + ch.u_off * nrhs;
-      }
-    }
-  }
-  int node = 0;
-  C scale = czero<C>();
-  if (k < p) {
-    node = a.nodes[f.node_off + k];
-    if (a.sym) {   // the source of D A x = D t
-      const StripDev st = a.strips[f.strip];
-      const int Hl = st.y1 - st.y0, ux = node / Hl, uy = node - ux * Hl;
-      scale = to_c(cmul(a.lsx[st.coef_off + ux], a.lsy[st.ycoef_off + uy]), C());
-    }
-  }
-  const C *tv = reinterpret_cast<const C *>(a.tloc);
+  const WSrc<C> src = wsrc_make<C>(a, f, nrhs);
   C *wl = reinterpret_cast<C *>(a.wloc);
   C *u = reinterpret_cast<C *>(a.ub_cur) + f.u_off * nrhs;
   for (int q = 0; q < nrhs; ++q) {
-    C w = czero<C>();
-    const int64_t gi = q * ldt + voff + node;
     if (k < p) {
-      w = tv[gi];
-      if (a.sym) w = cmul(w, scale);
+      int64_t gi;
+      const C w = wsrc_pivot(a, src, k, q, ldt, &gi);
+      wl[gi] = w;
+    } else {
+      u[(int64_t)q * b + (k - p)] = wsrc_children(src, k, q, czero<C>());
     }
-#pragma unroll
-    for (int ci = 0; ci < 2; ++ci)
-      if (t[ci] >= 0) w = cadd(w, uc[ci][(int64_t)q * bc[ci] + t[ci]]);
-    if (k < p) wl[gi] = w;
-    else u[(int64_t)q * b + (k - p)] = w;
   }
 }
 
@@ -1065,7 +1098,11 @@ __global__ void __launch_bounds__(256) mf_up_gather(MfArgs a, int f0, int nf, in
 // u[r] = w_b[r] + sum_j (-G21)(r, j) w_p[j]  (w_b already in u).
 // NR right-hand sides share every matrix load (NR > 1 requires split == 1).
 // one (virtual) block of the upward products: the items of block vb
-template <typename R, int ROWS, int NR, bool AHEAD = true>
+// FUSED: no gather pass before -- the products form the gathered entries
+// themselves (WSrc, the gather's own arithmetic), the front's first row
+// chunk stores w_p for the way down, and each row starts from the
+// children's update vectors.
+template <typename R, int ROWS, int NR, bool AHEAD = true, bool FUSED = false>
 __device__ __forceinline__ void up_block(const MfArgs &a, const int2 *__restrict__ items, int nitems, int split,
                                          int nrhs, int64_t ldt, int vb, typename CT<R>::T *part) {
   using C = typename CT<R>::T;
@@ -1082,12 +1119,18 @@ __device__ __forceinline__ void up_block(const MfArgs &a, const int2 *__restrict
   const int *nodes = nullptr, *pc = nullptr;
   int64_t voff = 0;
   C *u = nullptr;
+  WSrc<C> src;
+  bool writer = false;
   if (active) {
     const int2 item = items[it];
     const FrontDev f = a.fronts[item.x];
     p = f.p;
     b = f.b;
     voff = a.strips[f.strip].vec_off;
+    if (FUSED) {
+      src = wsrc_make<C>(a, f, nrhs);
+      writer = item.y == 0;
+    }
     G = reinterpret_cast<const C *>(a.fac) + f.fac_off + (int64_t)p * (p + b);  // -G21, b x p, ld b
     r = item.y * ROWS + lane;
     row = r < b;
@@ -1098,7 +1141,7 @@ __device__ __forceinline__ void up_block(const MfArgs &a, const int2 *__restrict
     seg0 = sidx * nseg / split;
     seg1 = (sidx + 1) * nseg / split;
   }
-  const C *wl = reinterpret_cast<const C *>(a.wloc);
+  C *wl = reinterpret_cast<C *>(a.wloc);
   for (int q0 = 0; q0 < nrhs; q0 += NR) {
     C total[NR];
 #pragma unroll
@@ -1107,9 +1150,15 @@ __device__ __forceinline__ void up_block(const MfArgs &a, const int2 *__restrict
       if (row && sidx == 0)
 #pragma unroll
         for (int q = 0; q < NR; ++q)
-          if (q0 + q < nrhs) total[q] = u[(int64_t)(q0 + q) * b + r];
+          if (q0 + q < nrhs)
+            total[q] = FUSED ? wsrc_children(src, p + r, q0 + q, czero<C>()) : u[(int64_t)(q0 + q) * b + r];
       auto gather = [&](int j, int q) {
-        return q0 + q < nrhs ? wl[(q0 + q) * ldt + voff + nodes[pc ? pc[j] : j]] : czero<C>();
+        if (q0 + q >= nrhs) return czero<C>();
+        if (!FUSED) return wl[(q0 + q) * ldt + voff + nodes[pc ? pc[j] : j]];
+        int64_t gi;
+        const C w = wsrc_pivot(a, src, pc ? pc[j] : j, q0 + q, ldt, &gi);
+        if (writer) wl[gi] = w;
+        return w;
       };
       for (int sg = seg0; sg < seg1; ++sg) {
         C sv[NR];
@@ -1209,11 +1258,11 @@ __device__ __forceinline__ void down_block(const MfArgs &a, const int2 *__restri
   }
 }
 
-template <typename R, int ROWS, int NR>
+template <typename R, int ROWS, int NR, bool FUSED>
 __global__ void __launch_bounds__(256, 2) mf_up(MfArgs a, const int2 *__restrict__ items,
                                                                      int nitems, int split, int nrhs, int64_t ldt) {
   __shared__ typename CT<R>::T part[MF_MAXSEG * 256 / 2];
-  up_block<R, ROWS, NR>(a, items, nitems, split, nrhs, ldt, blockIdx.x, part);
+  up_block<R, ROWS, NR, true, FUSED>(a, items, nitems, split, nrhs, ldt, blockIdx.x, part);
 }
 
 template <typename R, int ROWS, int NR>
@@ -1231,9 +1280,9 @@ __global__ void __launch_bounds__(256, 2) mf_down(MfArgs a, const int2 *__restri
 // split use, so the choice between them changes no result.  At the top tree levels a few fronts
 // carry a whole phase; an in-block split keeps an item on one SM, whose FP64
 // pipe then sets the phase time.
-template <typename R, bool UP>
+template <typename R, bool UP, bool FUSED>
 __global__ void __launch_bounds__(256) mf_seg_partial(MfArgs a, const int2 *__restrict__ items, int nitems,
-                                                      int nsubmax) {
+                                                      int nsubmax, int64_t ldt) {
   using C = typename CT<R>::T;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t u = (int64_t)blockIdx.x * 8 + warp;
@@ -1254,7 +1303,15 @@ __global__ void __launch_bounds__(256) mf_seg_partial(MfArgs a, const int2 *__re
   const bool row = r < (UP ? b : p);
   C sv[1];
   if (UP) {
-    auto gather = [&](int j, int) { return wl[voff + nodes[pc ? pc[j] : j]]; };
+    WSrc<C> src;
+    if (FUSED) src = wsrc_make<C>(a, f, 1);
+    auto gather = [&](int j, int) {
+      if (!FUSED) return wl[voff + nodes[pc ? pc[j] : j]];
+      int64_t gi;
+      const C w = wsrc_pivot(a, src, pc ? pc[j] : j, 0, ldt, &gi);
+      if (item.y == 0) const_cast<C *>(wl)[gi] = w;
+      return w;
+    };
     seg_dot<32, 1, true, C>(fac + (int64_t)p * n, b, r, row, sg * MF_SUB, min(cols, (sg + 1) * MF_SUB), lane,
                             0xffffffffu, gather, sv);
   } else {
@@ -1267,7 +1324,7 @@ __global__ void __launch_bounds__(256) mf_seg_partial(MfArgs a, const int2 *__re
   reinterpret_cast<C *>(a.segpart)[u * 32 + lane] = sv[0];
 }
 
-template <typename R, bool UP>
+template <typename R, bool UP, bool FUSED>
 __global__ void __launch_bounds__(256) mf_seg_reduce(MfArgs a, const int2 *__restrict__ items, int nitems,
                                                      int nsubmax) {
   using C = typename CT<R>::T;
@@ -1283,7 +1340,8 @@ __global__ void __launch_bounds__(256) mf_seg_reduce(MfArgs a, const int2 *__res
   const int nsub = (cols + MF_SUB - 1) / MF_SUB, per = MF_SEG / MF_SUB;
   const C *P = reinterpret_cast<const C *>(a.segpart) + (int64_t)it * nsubmax * 32 + lane;
   C *u = reinterpret_cast<C *>(a.ub_cur) + f.u_off;
-  C total = UP ? u[r] : czero<C>();
+  C total = czero<C>();
+  if (UP) total = FUSED ? wsrc_children(wsrc_make<C>(a, f, 1), p + r, 0, czero<C>()) : u[r];
   for (int k0 = 0; k0 < nsub; k0 += per) {
     C seg = P[k0 * 32];
     for (int k = k0 + 1; k < min(k0 + per, nsub); ++k) seg = cadd(seg, P[k * 32]);
@@ -1293,13 +1351,13 @@ __global__ void __launch_bounds__(256) mf_seg_reduce(MfArgs a, const int2 *__res
   else reinterpret_cast<C *>(a.tloc)[a.strips[f.strip].vec_off + a.nodes[f.node_off + r]] = total;
 }
 
-template <typename R, bool UP>
+template <typename R, bool UP, bool FUSED = false>
 void mf_seg_launch(const MfArgs &a, const int2 *items, int nitems, int cols_max, int64_t ldt, cudaStream_t st) {
-  (void)ldt;   // one right-hand side
   const int nsubmax = (cols_max + MF_SUB - 1) / MF_SUB;
   const int64_t units = (int64_t)nitems * nsubmax;
-  mf_seg_partial<R, UP><<<(unsigned)((units + 7) / 8), 256, 0, st>>>(a, items, nitems, nsubmax);
-  mf_seg_reduce<R, UP><<<(unsigned)(((int64_t)nitems * 32 + 255) / 256), 256, 0, st>>>(a, items, nitems, nsubmax);
+  mf_seg_partial<R, UP, FUSED><<<(unsigned)((units + 7) / 8), 256, 0, st>>>(a, items, nitems, nsubmax, ldt);
+  mf_seg_reduce<R, UP, FUSED><<<(unsigned)(((int64_t)nitems * 32 + 255) / 256), 256, 0, st>>>(a, items, nitems,
+                                                                                              nsubmax);
   count_launch(2);
 }
 
@@ -1344,7 +1402,7 @@ __device__ __forceinline__ void up_items(const MfArgs &a, const StripLevel &l, i
   const int ipc = (256 / ROWS) / l.split_up;
   const int nvb = (l.up_n + ipc - 1) / ipc;
   for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x)
-    up_block<R, ROWS, 1, false>(a, a.items_sweep + l.up_first, l.up_n, l.split_up, 1, ldt, vb, part);
+    up_block<R, ROWS, 1, false, true>(a, a.items_sweep + l.up_first, l.up_n, l.split_up, 1, ldt, vb, part);
 }
 
 template <typename R, int ROWS>
@@ -1357,9 +1415,9 @@ __device__ __forceinline__ void down_items(const MfArgs &a, const StripLevel &l,
 }
 
 // The launches of one strip's solve in the sequential orders (residual
-// restriction, per level the gather and the upward products, per level the
-// downward products, the add-back) as one launch: the same device code, the
-// launch boundaries replaced by grid barriers.
+// restriction, per level the upward products -- gathering their own
+// entries -- per level the downward products, the add-back) as one launch:
+// the same device code, the launch boundaries replaced by grid barriers.
 template <typename R>
 __global__ void __launch_bounds__(256, 2)
     mf_strip_sweep(MfArgs a, const void *ub0, const void *ub1, GridDev g, StripDev s, const StripLevel *lv,
@@ -1392,11 +1450,7 @@ __global__ void __launch_bounds__(256, 2)
     MfArgs al = a;
     al.ub_cur = const_cast<void *>(L & 1 ? ub1 : ub0);
     al.ub_child = L & 1 ? ub0 : ub1;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)l.nf * l.max_n; e += stride) {
-      const int fi = (int)(e / l.max_n);
-      up_gather_elem<R>(al, l.f0, fi, (int)(e - (int64_t)fi * l.max_n), 1, ldt);
-    }
-    if (!grid_barrier(bar, flag, limit)) return;
+    // (the products gather their own entries: no gather phase, one barrier per level)
     if (l.rows_up == 16) up_items<R, 16>(al, l, ldt, part);
     else up_items<R, 32>(al, l, ldt, part);
     if (!grid_barrier(bar, flag, limit)) return;
@@ -1509,12 +1563,13 @@ void mf_up_gather_level(const MfArgs &a, const LevelInfo &L, int nrhs, int64_t l
 
 template <typename R>
 void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int rows, int split, int nrhs, int64_t ldt,
-                 cudaStream_t st, int cols_max) {
+                 cudaStream_t st, int cols_max, bool fused) {
   if (nitems == 0) return;
   if (nrhs > 1) split = 1;  // several right-hand sides: every group keeps its segments in registers
   if (split == MF_SPLIT_GRID) {
     if (rows == 32 && a.segpart && cols_max > 0) {
-      mf_seg_launch<R, true>(a, items, nitems, cols_max, ldt, st);
+      if (fused) mf_seg_launch<R, true, true>(a, items, nitems, cols_max, ldt, st);
+      else mf_seg_launch<R, true, false>(a, items, nitems, cols_max, ldt, st);
       return;
     }
     split = 1;
@@ -1523,7 +1578,11 @@ void mf_up_level(const MfArgs &a, const int2 *items, int nitems, int rows, int s
   const int ipc = (256 / rows) / split;
   const int grid = (nitems + ipc - 1) / ipc;
   const int nr = (nrhs >= 4 && sizeof(R) == 4) ? 4 : (nrhs >= 2 ? 2 : 1);
-#define STDD_UP(RW, NRV) mf_up<R, RW, NRV><<<grid, 256, 0, st>>>(a, items, nitems, split, nrhs, ldt)
+#define STDD_UP(RW, NRV)                                                                \
+  do {                                                                                  \
+    if (fused) mf_up<R, RW, NRV, true><<<grid, 256, 0, st>>>(a, items, nitems, split, nrhs, ldt);  \
+    else mf_up<R, RW, NRV, false><<<grid, 256, 0, st>>>(a, items, nitems, split, nrhs, ldt);       \
+  } while (0)
   if (rows == 16) {
     if (nr == 4) STDD_UP(16, 4); else if (nr == 2) STDD_UP(16, 2); else STDD_UP(16, 1);
   } else {
@@ -1624,8 +1683,9 @@ template void mf_factor_level<double>(const MfArgs &, const LevelInfo &, int, cu
 template void mf_factor_level<float>(const MfArgs &, const LevelInfo &, int, cudaStream_t, LaunchHook *, int);
 template void mf_up_gather_level<double>(const MfArgs &, const LevelInfo &, int, int64_t, cudaStream_t);
 template void mf_up_gather_level<float>(const MfArgs &, const LevelInfo &, int, int64_t, cudaStream_t);
-template void mf_up_level<double>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t, int);
-template void mf_up_level<float>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t, int);
+template void mf_up_level<double>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t, int,
+                                  bool);
+template void mf_up_level<float>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t, int, bool);
 template void mf_down_level<double>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t, int);
 template void mf_down_level<float>(const MfArgs &, const int2 *, int, int, int, int, int64_t, cudaStream_t, int);
 
