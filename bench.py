@@ -53,7 +53,7 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor and tensor), NVIDIA's fi
 _MF = "paper_2509_20801_gb300/csrc/kernels_mf.cu"
 _SWEEP = ("// ------------------------------------------------------- substitutions",
           "// ------------------------------------------- persistent one-strip sweep",
-          "ea9751078cfacf61ca83fc796e7d0770947114ba731f3a73251f76023d906944")
+          "56a3ddad56c1f20446e6d2e928c83d1a8237b30558a874c4064731bfcb59327c")
 NCU_TRAFFIC = {
     "mf_gj_update<double>": {
         "dram_per_unit": 1394.992640e6 / 11.533996032e9,   # 3 launches: DRAM bytes / executed flops
@@ -80,7 +80,7 @@ NCU_TRAFFIC = {
         "profile": "profiles/ncu_mf_gj_update_oz_fp64_waveguide_2048x512.md",
     },
     "mf_down<double>": {
-        "dram_per_unit": 158.494e6 / 131.123e6,   # one strip solve's 14 launches: DRAM bytes / factor bytes
+        "dram_per_unit": 158.460e6 / 131.123e6,   # one strip solve's 14 launches: DRAM bytes / factor bytes
         "source": _MF, "begin": _SWEEP[0], "end": _SWEEP[1], "sha256": _SWEEP[2],
         "profile": "profiles/ncu_dram_mf_down_fp64_waveguide_2048x512.md",
     },
