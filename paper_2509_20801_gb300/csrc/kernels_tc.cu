@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(128) mf_gj_update_tc(MfArgs a, int f0, int k) 
 constexpr int OZ_S = 8;                      // slices per operand value
 constexpr int OZ_MR = 64;                    // complex rows per CTA (128 real rows, M = 128)
 constexpr int OZ_NC = 32;                    // complex columns per sub-tile (N = 32)
-constexpr int OZ_CHUNK = 8;                  // sub-tiles per CTA at most
+constexpr int OZ_CHUNK = 16;                 // sub-tiles per CTA at most
 constexpr int OZ_ABYTES = 128 * 64 * 2;      // one A slice: 128 real rows x 64 real K, BF16
 constexpr int OZ_BBYTES = OZ_NC * 64 * 2;    // one B slice: 32 columns x 64 real K, BF16
 constexpr uint32_t OZ_TMEM_COLS = 512;       // 2 buffers x 8 accumulators x 32 columns
@@ -303,7 +303,7 @@ __device__ __forceinline__ double oz_value(long long V, int e) {
   return __longlong_as_double(b + ((long long)e << 52));
 }
 
-// C R for the 64 rows of C and the columns [0, ncols) of R (ncols <= 256):
+// C R for the 64 rows of C and the columns [0, ncols) of R (ncols <= 32 OZ_CHUNK):
 // cload(rr, j) = C(rr, j), rload(cc, j) = R(j, cc) for j < kc (zero where
 // the matrix ends); sink(rr, c0, comp, produce) receives component comp of
 // (C R)(rr, c0 + u), u < OZ_SINK, as add[u] from produce(add) (called once,
@@ -520,7 +520,7 @@ __device__ __forceinline__ double2 *front_ptr64(const MfArgs &a, const FrontDev 
 // that skips the pivot band), lower entries added to the front and their
 // signed mirrors stored, as mf_gj_update_sym does on the FP64 pipe.  CTA
 // (front, ti, chunk): rows [64 ti, 64 ti + 64) against the chunk's columns
-// (at most 256) up to the diagonal.  grid = (fronts, tile rows x chunks).
+// (at most 32 OZ_CHUNK) up to the diagonal.  grid = (fronts, tile rows x chunks).
 __global__ void __launch_bounds__(OZ_THREADS, 1) mf_gj_update_oz(MfArgs a, int f0, int k, int nchunk) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   OzSmem &sm = *reinterpret_cast<OzSmem *>(smem_raw);
