@@ -77,3 +77,28 @@ def test_stencil_phase_roofline():
     assert d["bound"] == "alu"
     assert bench.stencil_phase(0.2, 1, 100, 1000.0, 10.0)["bound"] == "hbm"
     assert bench.stencil_phase(0.2, 1, 100, 1000.0, 1.0, measured_over="x")["measured_over"] == "x"
+
+
+def test_traffic_records_follow_their_kernel_source(tmp_path, monkeypatch):
+    """roofline.traffic scales a recorded DRAM capture only while the
+    kernel's source text between the record's markers still hashes to the
+    recorded SHA-256; an edited kernel reports null instead of a stale
+    figure.  Every record's markers exist in its source file."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    for name, rec in bench.NCU_TRAFFIC.items():
+        src = open(os.path.join(ROOT, rec["source"])).read()
+        assert src.index(rec["begin"]) < src.index(rec["end"]), name
+        assert os.path.exists(os.path.join(ROOT, rec["profile"])), name
+    f = tmp_path / "k.cu"
+    f.write_text("head\n// BEGIN\nkernel body v1\n// END\ntail\n")
+    digest = hashlib.sha256("// BEGIN\nkernel body v1\n".encode()).hexdigest()
+    rec = {"dram_per_unit": 2.5, "source": str(f), "begin": "// BEGIN", "end": "// END", "sha256": digest,
+           "profile": "x"}
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "k<double>", rec)
+    assert bench.ncu_traffic("k<double>", 4.0) == 10.0
+    assert bench.ncu_traffic("k<double>", 0) is None
+    assert bench.ncu_traffic("unknown", 4.0) is None
+    f.write_text("head\n// BEGIN\nkernel body v2\n// END\ntail\n")
+    assert bench.ncu_traffic("k<double>", 4.0) is None
